@@ -1,0 +1,423 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+No GPU: these run on the CPU and check the oracle itself (hand-worked examples,
+closed forms, brute force, an independent ODE integration, library routines).
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2603_25762_gb300 import metrics, synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _frags_from_M(M, qual=None, porec=None):
+    M = np.asarray(M)
+    ptr, snp, al, q = [0], [], [], []
+    for i, row in enumerate(M):
+        nz = np.nonzero(row)[0]
+        snp += nz.tolist()
+        al += row[nz].tolist()
+        q += ([30] * nz.size) if qual is None else list(np.asarray(qual)[i][nz])
+        ptr.append(len(snp))
+    return synth.Fragments(M.shape[1], np.array(ptr, np.int64), np.array(snp, np.int32),
+                           np.array(al, np.int8), np.array(q, np.uint8),
+                           np.zeros(M.shape[0], np.uint8) if porec is None
+                           else np.asarray(porec, np.uint8),
+                           np.arange(M.shape[1], dtype=np.int64),
+                           np.ones(M.shape[1], np.int8))
+
+
+def _dense_M(fr):
+    M = np.zeros((fr.n_frags, fr.n_snps), np.int64)
+    rows = np.repeat(np.arange(fr.n_frags), np.diff(fr.frag_ptr))
+    M[rows, fr.snp] = fr.allele
+    return M
+
+
+def _brute_maxcut(W):
+    n = W.shape[0]
+    best = -np.inf
+    # spin 0 fixed to +1 (global flip symmetry); enumerate the rest in chunks
+    for bits in range(1 << (n - 1)):
+        s = np.ones(n)
+        for k in range(n - 1):
+            if bits >> k & 1:
+                s[k + 1] = -1
+        c = 0.25 * (W.sum() - s @ W @ s)
+        best = max(best, c)
+    return best
+
+
+def _brute_maxcut_fast(W):
+    n = W.shape[0]
+    idx = np.arange(1 << (n - 1), dtype=np.int64)
+    S = np.ones((idx.size, n))
+    for k in range(n - 1):
+        S[:, k + 1] = np.where((idx >> k) & 1, -1.0, 1.0)
+    vals = 0.25 * (W.sum() - np.einsum("ri,ij,rj->r", S, W, S))
+    return vals.max()
+
+
+# ----------------------------------------------------------------------------- RNG
+def test_splitmix64_published_vectors(oracle):
+    # SplitMix64 first output from state 0 and the published sequence for seed 1234567
+    assert oracle.splitmix64(0, 0) == 0xE220A8397B1DCDAF
+    assert [oracle.splitmix64(1234567, i) for i in range(5)] == [
+        6457827717110365317, 3203168211198807973, 9817491932198370423,
+        4593380528125082431, 16408922859458223821]
+
+
+def test_init_values_range_and_grid(oracle):
+    v = np.array([oracle.init_value(7, b, 0, r, i, w) for b in range(2) for r in range(4)
+                  for i in range(50) for w in range(2)])
+    assert v.min() >= -0.1 and v.max() < 0.1
+    u = (v + 0.1) / 0.2 * 2 ** 24
+    assert np.allclose(u, np.round(u), atol=1e-6)
+    assert len(np.unique(v)) > 0.99 * v.size
+
+
+# ----------------------------------------------------------------------------- read graph
+def test_read_graph_hand_example(oracle):
+    g = json.load(open(os.path.join(GOLD, "read_graph_hand.json")))
+    fr = _frags_from_M(g["M"])
+    assert (oracle.read_graph_dense(fr, oracle.READ_CONFLICT) == np.array(g["conflict"])).all()
+    W = oracle.read_graph_dense(fr, oracle.READ_SIGNED)
+    assert (W == np.array(g["signed"])).all()
+    csr = oracle.read_graph(fr, oracle.READ_SIGNED)
+    assert (csr.dense() == W).all()
+    s = np.array(g["argmax_spins"], np.int8)
+    assert oracle.cut(csr, s) == g["max_cut"]
+    assert W.sum() == g["sum_W_signed"]
+    assert s @ W @ s == g["sTWs_signed_at_argmax"]
+    assert _brute_maxcut(W.astype(float)) == g["max_cut"]
+    wc = oracle.CSR.from_dense(np.array(g["conflict"]))
+    assert _brute_maxcut(np.array(g["conflict"], float)) == g["max_cut"]
+    assert oracle.cut(wc, s) == g["max_cut"]
+    hap1, sb = oracle.vote(fr, s, np.zeros(3, np.int32), 1)
+    assert hap1.tolist() == g["vote_hap1_with_S1_r0_r2"]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_read_graph_matches_matrix_identities(oracle, seed):
+    fr = synth.tiny_reads(seed=seed, n_snps=120, n_reads=40, flip_p=0.1, miss_p=0.1)
+    M = _dense_M(fr)
+    Ws = oracle.read_graph_dense(fr, oracle.READ_SIGNED)
+    Wc = oracle.read_graph_dense(fr, oracle.READ_CONFLICT)
+    signed = -(M @ M.T)
+    np.fill_diagonal(signed, 0)
+    assert (Ws == signed).all()
+    overlap = np.abs(M) @ np.abs(M).T
+    np.fill_diagonal(overlap, 0)
+    agree = (overlap - signed) // 2
+    conflict = (overlap + signed) // 2
+    assert (Wc == conflict).all() and (agree >= 0).all()
+    for mode, Wd in ((oracle.READ_SIGNED, Ws), (oracle.READ_CONFLICT, Wc)):
+        csr = oracle.read_graph(fr, mode)
+        assert (csr.dense() == Wd).all()
+        assert np.all(np.diff(csr.row_ptr) >= 0)
+
+
+def test_read_graph_rejects_bad_input(oracle):
+    fr = _frags_from_M([[1, 1, 0], [0, -1, 1]])
+    fr.allele = fr.allele.copy()
+    fr.allele[0] = 2
+    with pytest.raises(ValueError):
+        oracle.read_graph_dense(fr)
+    fr2 = _frags_from_M([[1, 1, 0], [0, -1, 1]])
+    fr2.snp = fr2.snp.copy()
+    fr2.snp[1] = 0  # not strictly increasing inside a fragment
+    with pytest.raises(ValueError):
+        oracle.read_graph(fr2)
+
+
+def test_read_graph_empty_and_singleton_fragments(oracle):
+    fr = _frags_from_M([[0, 0, 0], [1, 0, 0], [0, 0, 0]])
+    W = oracle.read_graph_dense(fr)
+    assert (W == 0).all()
+    g = oracle.read_graph(fr)
+    assert g.nnz == 0
+    assert oracle.blocks_of(g) == []
+
+
+# ----------------------------------------------------------------------------- SNP graph
+def _llr_closed_form(qa, qb):
+    # P_cis + P_trans = 1 and P_cis - P_trans = (2 q_u - 1)(2 q_v - 1), so
+    # log10(P_cis / P_trans) = 2 atanh(d) / ln 10 with d = (1 - 2 e_u)(1 - 2 e_v), e = 10^(-Q/10)
+    d = (1 - 2 * 10 ** (-qa / 10)) * (1 - 2 * 10 ** (-qb / 10))
+    return 2 * math.atanh(d) / math.log(10)
+
+
+@pytest.mark.parametrize("qa,qb", [(10, 10), (20, 20), (30, 30), (7, 7), (10, 20), (4, 93),
+                                   (13, 29)])
+def test_snp_edge_two_snp_closed_form(oracle, qa, qb):
+    for sa, sb in ((1, 1), (1, -1), (-1, -1)):
+        fr = _frags_from_M([[sa, sb]], qual=[[qa, qb]])
+        g = oracle.snp_graph(fr)
+        W = g.dense()
+        expect = -(sa * sb) * _llr_closed_form(qa, qb)
+        assert W[0, 1] == pytest.approx(expect, rel=1e-13)
+        assert W[1, 0] == W[0, 1]
+
+
+def test_snp_edge_survey_reference_values(oracle):
+    # Q=10 equal alleles, and the three-SNP fragment normalised by |S_i| - 1 = 2
+    fr = _frags_from_M([[1, 1]], qual=[[10, 10]])
+    assert oracle.snp_graph(fr).dense()[0, 1] == pytest.approx(-0.6585413472804108, rel=1e-14)
+    fr3 = _frags_from_M([[1, 1, -1]], qual=[[10, 20, 30]])
+    W = oracle.snp_graph(fr3).dense()
+    assert W[0, 1] == pytest.approx(-_llr_closed_form(10, 20) / 2, rel=1e-13)
+    assert W[0, 2] == pytest.approx(+_llr_closed_form(10, 30) / 2, rel=1e-13)
+    assert W[1, 2] == pytest.approx(+_llr_closed_form(20, 30) / 2, rel=1e-13)
+
+
+def test_snp_edge_additivity_porec_alpha_and_linkage(oracle):
+    rng = np.random.default_rng(5)
+    M = np.array([[1, -1, 1, 1, -1]])
+    Q = rng.integers(7, 31, size=(1, 5))
+    one = oracle.snp_graph(_frags_from_M(M, qual=Q)).dense()
+    two = oracle.snp_graph(_frags_from_M(np.vstack([M, M]), qual=np.vstack([Q, Q]))).dense()
+    assert np.allclose(two, 2 * one, rtol=1e-15, atol=0)
+    pc = oracle.snp_graph(_frags_from_M(M, qual=Q, porec=[1]), porec_alpha=0.1).dense()
+    assert np.allclose(pc, 0.1 * one, rtol=1e-14, atol=0)
+    # linkage depth 5/10 on |S| = 5: each SNP links to the next floor(5*4/10) = 2 SNPs,
+    # normalisation stays |S| - 1
+    half = oracle.snp_graph(_frags_from_M(M, qual=Q), linkage_k=5).dense()
+    mask = np.zeros((5, 5), bool)
+    for u in range(5):
+        for v in range(u + 1, min(5, u + 3)):
+            mask[u, v] = mask[v, u] = True
+    assert np.array_equal(half != 0, mask)
+    assert np.allclose(half[mask], one[mask], rtol=1e-15)
+
+
+def test_snp_graph_rejects_bad_quality(oracle):
+    with pytest.raises(ValueError):
+        oracle.snp_graph(_frags_from_M([[1, 1]], qual=[[3, 20]]))
+    with pytest.raises(ValueError):
+        oracle.snp_graph(_frags_from_M([[1, 1]], qual=[[20, 94]]))
+
+
+def test_snp_graph_truth_signs_without_errors(oracle):
+    # error-free reads: cis pairs (same truth) get negative weight, trans pairs positive
+    fr = synth.region_reads(11, n_snps=200, region=60_000, n_reads=60, len_mean=8000,
+                            len_sd=2000, flip_p=0.0, miss_p=0.0, qual=(7, 30))
+    W = oracle.snp_graph(fr).dense()
+    t = fr.truth.astype(float)
+    nz = W != 0
+    assert np.all(np.sign(W[nz]) == -np.outer(t, t)[nz])
+
+
+# ----------------------------------------------------------------------------- components
+def test_components_match_scipy(oracle):
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+    fr = synth.region_reads(3, n_snps=600, region=400_000, n_reads=70, len_mean=6000,
+                            len_sd=3000, flip_p=0.05, miss_p=0.0)
+    g = oracle.read_graph(fr, oracle.READ_SIGNED)
+    nc, lab = oracle.components(g)
+    A = csr_matrix((np.ones(g.nnz), g.col, g.row_ptr), shape=(g.n, g.n))
+    nc2, lab2 = connected_components(A, directed=False)
+    assert nc == nc2
+    # same partition, numbered by smallest vertex
+    first = {}
+    for v, c in enumerate(lab2):
+        first.setdefault(c, len(first))
+    assert np.array_equal(lab, np.array([first[c] for c in lab2]))
+    assert nc > 1
+
+
+# ----------------------------------------------------------------------------- bSB dynamics
+def test_bsb_matches_ode_integration(oracle):
+    """Symplectic-Euler bSB converges (first order) to the bSB ODE solved by scipy."""
+    from scipy.integrate import solve_ivp
+    rng = np.random.default_rng(0)
+    n = 5
+    J = rng.normal(size=(n, n))  # deliberately asymmetric: catches a transposed product
+    np.fill_diagonal(J, 0)
+    g = oracle.CSR.from_dense(-J)  # w = -J
+    a0, c0, T = 1.0, 0.15, 6.0
+    x0 = rng.uniform(-0.05, 0.05, n)
+    y0 = rng.uniform(-0.05, 0.05, n)
+
+    def rhs2(t, u):
+        x, y = u[:n], u[n:]
+        at = a0 * t / T
+        dy = -(a0 - at) * x + c0 * (J @ x)
+        return np.concatenate([a0 * y, dy])
+
+    ref = solve_ivp(rhs2, (0, T), np.concatenate([x0, y0]), rtol=1e-11, atol=1e-13).y[:, -1]
+    assert np.abs(ref[:n]).max() < 1.0  # wall never reached: pure dynamics
+    errs = []
+    for steps in (3000, 6000):
+        dt = T / steps
+        x, y = oracle.bsb_run(g, x0[None], y0[None], 0, steps, steps, dt=dt, a0=a0, c0=c0)
+        errs.append(np.abs(np.concatenate([x[0], y[0]]) - ref).max() / np.abs(ref).max())
+    assert errs[1] < 2e-3
+    assert 1.6 < errs[0] / errs[1] < 2.4  # first-order convergence to the ODE
+
+
+def test_bsb_wall_invariant(oracle):
+    rng = np.random.default_rng(1)
+    W = synth.random_graph(3, 12, p=0.5)
+    g = oracle.CSR.from_dense(W)
+    x0 = rng.uniform(-0.1, 0.1, (4, 12))
+    y0 = rng.uniform(-0.1, 0.1, (4, 12))
+    x, y = oracle.bsb_run(g, x0, y0, 0, 150, 300, dt=1.0, a0=1.0, c0=0.3)
+    assert np.abs(x).max() <= 1.0
+    at_wall = np.abs(x) == 1.0
+    assert at_wall.any()
+    assert np.all(y[at_wall] == 0.0)
+
+
+def test_bsb_gauge_invariance_exact(oracle):
+    """Solving D J D from D x0 gives exactly D x(t): sign flips are exact in FP64."""
+    W = synth.random_graph(4, 14, p=0.4, integer=False)
+    g = oracle.CSR.from_dense(W)
+    rng = np.random.default_rng(2)
+    d = np.where(rng.random(14) < 0.5, -1.0, 1.0)
+    gd = oracle.CSR.from_dense(d[:, None] * W * d[None, :])
+    x0 = rng.uniform(-0.1, 0.1, (3, 14))
+    y0 = rng.uniform(-0.1, 0.1, (3, 14))
+    c0 = oracle.default_c0(g)
+    x1, y1 = oracle.bsb_run(g, x0, y0, 0, 400, 400, c0=c0)
+    x2, y2 = oracle.bsb_run(gd, x0 * d, y0 * d, 0, 400, 400, c0=c0)
+    assert np.array_equal(x2, x1 * d) and np.array_equal(y2, y1 * d)
+
+
+def test_default_c0_definition(oracle):
+    W = synth.random_graph(9, 10, p=0.6, integer=False)
+    g = oracle.CSR.from_dense(W)
+    n = 10
+    sigma = np.sqrt((W ** 2).sum() / (n * (n - 1)))
+    assert oracle.default_c0(g) == pytest.approx(0.5 / (sigma * np.sqrt(n)), rel=1e-14)
+
+
+# ----------------------------------------------------------------------------- cut / energy
+def test_cut_identity_and_energy(oracle):
+    W = synth.random_graph(5, 16, p=0.5, integer=False)
+    g = oracle.CSR.from_dense(W)
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        s = np.where(rng.random(16) < 0.5, -1, 1).astype(np.int8)
+        sf = s.astype(float)
+        assert oracle.cut(g, s) == pytest.approx(0.25 * (W.sum() - sf @ W @ sf), abs=1e-10)
+        assert oracle.ising_energy(g, s) == pytest.approx(-0.5 * sf @ (-W) @ sf, abs=1e-10)
+
+
+def _ring(n):
+    W = np.zeros((n, n))
+    for i in range(n):
+        W[i, (i + 1) % n] = W[(i + 1) % n, i] = 1
+    return W
+
+
+@pytest.mark.parametrize("name,W,opt", [
+    ("C8", _ring(8), 8), ("C9", _ring(9), 8), ("C12", _ring(12), 12), ("C13", _ring(13), 12),
+    ("K7", np.ones((7, 7)) - np.eye(7), 12), ("K10", np.ones((10, 10)) - np.eye(10), 25),
+    ("K34", np.block([[np.zeros((3, 3)), np.ones((3, 4))], [np.ones((4, 3)), np.zeros((4, 4))]]),
+     12),
+])
+def test_bsb_closed_form_maxcut(oracle, name, W, opt):
+    g = oracle.CSR.from_dense(W)
+    best, s, cuts, br = oracle.bsb_solve(g, list(range(32)), 1000, seed=17)
+    assert best == opt
+    assert _brute_maxcut_fast(W) == opt
+
+
+def test_bsb_brute_force(oracle):
+    hits, total = 0, 0
+    for seed in range(12):
+        n = 10 + seed % 7
+        W = synth.random_graph(100 + seed, n, p=0.5, integer=(seed % 2 == 0))
+        g = oracle.CSR.from_dense(W)
+        opt = _brute_maxcut_fast(W)
+        best, s, cuts, br = oracle.bsb_solve(g, list(range(32)), 2000, seed=seed)
+        assert best == pytest.approx(oracle.cut(g, s))
+        assert best >= 0.99 * opt - 1e-9
+        assert cuts[br] == best and np.all(cuts[:br] < best)  # ties -> lowest replica
+        hits += abs(best - opt) < 1e-9
+        total += 1
+    assert hits >= 0.9 * total
+
+
+def test_bsb_planted_partition_error_free(oracle):
+    fr = synth.tiny_reads(seed=21, flip_p=0.0)
+    res = oracle.phase_read(fr, oracle.READ_SIGNED, range(16), 1000, seed=3)
+    g = res["graph"]
+    for b, nodes in enumerate(res["blocks"]):
+        sub = g.subgraph(nodes)
+        planted = sub.w[sub.w > 0].sum() / 2
+        assert res["cuts"][b] == planted
+    se, he = metrics.switch_hamming(res["hap1"], res["snp_block"], fr.truth)
+    assert se == 0.0 and he == 0.0
+
+
+# ----------------------------------------------------------------------------- voting / parity
+def test_vote_rule_cases(oracle):
+    cases = json.load(open(os.path.join(GOLD, "vote_cases.json")))["cases"]
+    n = len(cases)
+    rows, spins = [], []
+    for j, c in enumerate(cases):
+        for a in c["S1"]:
+            r = np.zeros(n, np.int64)
+            r[j] = a
+            rows.append(r)
+            spins.append(1)
+        for a in c["S2"]:
+            r = np.zeros(n, np.int64)
+            r[j] = a
+            rows.append(r)
+            spins.append(-1)
+    fr = _frags_from_M(np.array(rows))
+    hap1, sb = oracle.vote(fr, np.array(spins, np.int8), np.zeros(len(rows), np.int32), 1)
+    assert hap1.tolist() == [c["hap1"] for c in cases]
+    assert sb.tolist() == [0 if c["hap1"] != 0 else -1 for c in cases]
+
+
+def test_vote_block_assignment_majority(oracle):
+    # SNP 0 covered by 2 reads of block 1 and 1 read of block 0 -> block 1 votes
+    fr = _frags_from_M([[1], [-1], [1]])
+    hap1, sb = oracle.vote(fr, np.array([1, 1, -1], np.int8), np.array([0, 1, 1], np.int32), 2)
+    assert sb.tolist() == [1] and hap1.tolist() == [-1]
+
+
+def test_parity_swap(oracle):
+    hap1 = oracle.parity(np.array([0, 1, 2, 3, 0]), np.array([1, 1, 1, 1, 0]))
+    assert hap1.tolist() == [1, -1, 1, -1, 0]
+
+
+def test_refinement_invariant_and_error_free_phase(oracle):
+    fr = synth.region_reads(31, n_snps=150, region=50_000, n_reads=50, len_mean=8000,
+                            len_sd=2000, flip_p=0.0, miss_p=0.0, qual=(10, 30))
+    res = oracle.phase_snp(fr, range(8), 300, seed=5, refine_max=15)
+    se, he = metrics.switch_hamming(res["hap1"], res["snp_block"], fr.truth)
+    assert se == 0.0 and he == 0.0
+    # noisy input: the final parity partition never cuts less of the ungauged graph
+    fr2 = synth.region_reads(32, n_snps=150, region=50_000, n_reads=40, len_mean=8000,
+                             len_sd=2000, flip_p=0.08, miss_p=0.0, qual=(7, 30))
+    res2 = oracle.phase_snp(fr2, range(4), 150, seed=6, refine_max=15)
+    g = res2["graph"]
+    for b, nodes in enumerate(res2["blocks"]):
+        sub = g.subgraph(nodes)
+        p = np.where(res2["C"][nodes] % 2 == 0, 1, -1).astype(np.int8)
+        assert oracle.cut(sub, p) >= res2["first_cuts"][b] - 1e-9
+        assert 1 <= res2["iters"][b] <= 15
+
+
+# ----------------------------------------------------------------------------- metrics
+def test_metrics_paper_example():
+    g = json.load(open(os.path.join(GOLD, "metrics_paper_example.json")))
+    se, he = metrics.string_example(g["inferred"], g["reference"])
+    assert se == pytest.approx(g["se"]) and he == pytest.approx(g["he"])
+
+
+def test_n50_hand_case():
+    assert metrics.n50([50_000, 30_000, 20_000]) == 50_000
+    assert metrics.n50([10, 10, 10, 10]) == 10
+    assert metrics.n50([]) == 0
