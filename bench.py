@@ -1,0 +1,315 @@
+"""Benchmark of the QHap bSB phasing hot path on GB300.
+
+One step = one pass of the whole path on one synthetic input already resident in HBM:
+read graph build -> components and J tiles -> batched bSB (all replicas, all steps) ->
+exact cut + replica pick -> read voting.  Workload (default): 12,000 het SNPs over 4 Mb,
+7,200 HiFi-like reads (15 +- 5 kb, 1% allele error, 2% missing), signed read graph,
+1,024 replicas x 1,000 bSB steps.
+
+Metric: bSB spin-updates/s = sum over blocks of N_b * R * steps / step time.
+`e2e` repeats the step through the C ABI with host buffers: fragments copied from pinned
+host memory and haplotypes + cut copied back inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
+                       [--impl ours|reference]
+Under torchrun each rank runs its own replica range (replica_base = rank * R): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+SPIN_BYTES = 16 + 2  # FP32 x, y read + write, BF16 X_hat write, per spin update
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device=0):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for k, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(k)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _workload(args):
+    from paper_2603_25762_gb300 import synth
+    fr = synth.hifi_region(1002)
+    cfg = {"workload": "hifi-region: 12,000 SNPs / 4 Mb, 7,200 reads, signed read graph",
+           "n_reads": fr.n_frags, "n_snps": fr.n_snps, "replicas": args.replicas,
+           "bsb_steps": args.bsb_steps, "precision": args.precision,
+           "l2": "flushed between timed steps (256 MiB write)"}
+    return fr, cfg
+
+
+def cpu_baseline(fr, replicas=64, steps=1000, seed=1):
+    """The FP64 oracle, as it stands, on the host cores: read graph, blocks, bSB on a
+    replica subset with the full step count, voting."""
+    from oracle import oracle as o
+    o.build()
+    t0 = time.perf_counter()
+    res = o.phase_read(fr, o.READ_SIGNED, range(replicas), steps, seed=seed)
+    dt = time.perf_counter() - t0
+    units = sum(len(b) for b in res["blocks"]) * replicas * steps
+    return {"value": units / dt, "unit": "spin-updates/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"full graph ({fr.n_frags} reads), {replicas} replicas x {steps} steps, "
+                      f"graph build + bSB + voting, {dt:.1f} s"}, res
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    fr, cfg = _workload(args)
+    times, value = [], None
+    for i in range(args.warmup + args.steps):
+        cb, _ = cpu_baseline(fr, replicas=args.ref_replicas, steps=args.bsb_steps)
+        if i >= args.warmup:
+            times.append(cb)
+    vals = [c["value"] for c in times]
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": "bSB spin-updates/s", "value": value,
+            "unit": "spin-updates/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": times[-1]["sample"]},
+            "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _count_kernels(fn):
+    """Kernel launches of one call, from the CUDA activity trace (torch.profiler)."""
+    try:
+        import torch
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
+        n = 0
+        for ev in prof.events():
+            if ev.device_type.name == "CUDA" and "qh::" in ev.name:
+                n += 1
+        return n if n > 0 else None
+    except Exception:
+        return None
+
+
+def run_ours(args):
+    import torch
+    ws, rank = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_2603_25762_gb300 import build, qhap
+    build.build()
+    fr, cfg = _workload(args)
+    prec = qhap.PREC_BF16 if args.precision == "bf16" else qhap.PREC_FP32
+    stream = torch.cuda.Stream()
+    ctx = qhap.Context(local, stream=stream.cuda_stream)
+    # inputs resident in HBM
+    dev = torch.device("cuda", local)
+    arrays_dev = (fr.n_snps, torch.from_numpy(fr.frag_ptr).to(dev), torch.from_numpy(fr.snp).to(dev),
+                  torch.from_numpy(fr.allele).to(dev), torch.from_numpy(fr.qual).to(dev),
+                  torch.from_numpy(fr.is_porec).to(dev))
+    outs = (torch.empty(fr.n_snps, dtype=torch.int8, device=dev),
+            torch.empty(fr.n_snps, dtype=torch.int8, device=dev),
+            torch.empty(fr.n_snps, dtype=torch.int32, device=dev))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    R, T = args.replicas, args.bsb_steps
+    base = rank * R
+    stats = {}
+
+    def one_step(host=False, pinned=None):
+        if host:
+            g = ctx.build_graph(arrays=pinned, on_device=False)
+        else:
+            g = ctx.build_graph(arrays=arrays_dev, on_device=True)
+        sol = ctx.solve(g, replicas=R, steps=T, precision=prec, seed=1, replica_base=base)
+        if host:
+            h = ctx.phase(g, sol, fr.n_snps)
+            cut = sol.block(0)["best_cut"] if g.n_blocks else 0.0
+        else:
+            h = ctx.phase(g, sol, fr.n_snps, out=outs)
+            cut = None
+        stats["timing"] = sol.timing()
+        stats["blocks"] = g.n_blocks
+        stats["units"] = sol.timing()["spin_updates"]
+        stats["nnz"] = g.nnz
+        sol.free()
+        g.free()
+        return h, cut
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step()
+        times, step_ms, launches = [], [], []
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            for _ in range(args.steps):
+                flush.fill_(1)
+                stream.synchronize()
+                ev0.record(stream)
+                one_step()
+                ev1.record(stream)
+                ev1.synchronize()
+                times.append(ev0.elapsed_time(ev1))
+                step_ms.append(stats["timing"]["step_ms"] / stats["timing"]["n_step_launches"])
+        torch.cuda.synchronize()
+        units = stats["units"]
+        # e2e through the C ABI with host buffers (pinned), copies inside the timed region
+        pinned = tuple([fr.n_snps] + [torch.from_numpy(a).pin_memory() for a in
+                                      (fr.frag_ptr, fr.snp, fr.allele, fr.qual, fr.is_porec)])
+        pinned_np = (pinned[0],) + tuple(t.numpy() for t in pinned[1:])
+        one_step(host=True, pinned=pinned_np)
+        e2e = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            one_step(host=True, pinned=pinned_np)
+            e2e.append((time.perf_counter() - t0) * 1e3)
+        n_kern = _count_kernels(lambda: one_step())
+    ms = statistics.mean(times)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, statistics.mean(e2e)], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+    else:
+        e2e_ms = statistics.mean(e2e)
+    if rank != 0:
+        return
+    hbm, bf16_tf, src = _peaks()
+    launch_us = statistics.mean(step_ms) * 1e3
+    # state traffic per spin update + each stored J nonzero read once (BF16: 2 B, FP32: 4 B)
+    per_launch_bytes = units / T * SPIN_BYTES + stats["nnz"] * (2 if prec else 4)
+    achieved = per_launch_bytes / (launch_us * 1e-6) / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic_step_tc.json")
+    if os.path.exists(tp):
+        traffic = json.load(open(tp)).get("bytes_per_launch")
+    h2d = sum(int(a.nbytes) for a in pinned_np[1:])
+    d2h = fr.n_snps * (1 + 1 + 4) + 8
+    line = {
+        "metric": "bSB spin-updates/s", "value": units * ws / (ms / 1e3),
+        "unit": "spin-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.precision, "data": "synthetic", "config": cfg,
+        "phasing_wall_ms": ms,
+        "e2e": {"value": units * ws / (e2e_ms / 1e3), "unit": "spin-updates/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "roofline": {"bound": "hbm", "kernel": "k_step_tc" if prec else "k_step_f32",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "peak_source": src, "avg_launch_us": launch_us,
+                     "algorithmic_bytes_per_launch": per_launch_bytes},
+        "gpu_launches": (n_kern * args.steps) if n_kern else None,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        cb, _ = cpu_baseline(fr, replicas=args.ref_replicas, steps=T)
+        line["cpu_baseline"] = cb
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--replicas", type=int, default=1024)
+    ap.add_argument("--bsb-steps", type=int, default=1000)
+    ap.add_argument("--ref-replicas", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,259 @@
+/*
+ * qhap.h -- C ABI of the GB300 (sm_103a) QHap phasing hot path.
+ *
+ * QHap ("Quantum-Inspired Haplotype Phasing") phases diploid haplotypes by
+ * turning read evidence into a weighted graph and solving Max-Cut on it with
+ * ballistic simulated bifurcation (bSB).  This library runs that path on one
+ * GPU with hand-written CUDA kernels:
+ *
+ *   qh_build_graph : fragments -> read graph or SNP graph (the coupling J = -A)
+ *                    -> connected components (phase blocks) -> J tiles
+ *   qh_bsb_solve   : multi-replica bSB on every block at once -> spins, cut
+ *                    (SNP graphs: iterative refinement with sign inversion)
+ *   qh_phase       : spins -> haplotypes (read voting or flip-count parity)
+ *
+ * Conventions for every call
+ *  - Status: every call returns qh_status; none aborts the process.  On error
+ *    qh_last_error(ctx) holds a one-line description.
+ *  - Streams: work is issued on the context's CUDA stream.  Calls that return
+ *    host data synchronise that stream before returning.
+ *  - Ownership: input arrays stay owned by the caller and are copied (host or
+ *    device) before the call returns.  Opaque handles (qh_ctx, qh_graph,
+ *    qh_solution) are owned by the library and released by their *_free /
+ *    qh_destroy call.  Output arrays are caller-allocated with the lengths
+ *    stated per argument.
+ *  - Pointers marked "host or device" are read from device memory when the
+ *    call's `on_device` flag is 1, from host memory otherwise.
+ *  - Thread safety: one context must not be used by two host threads at once.
+ */
+#ifndef QHAP_H
+#define QHAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QH_OK = 0,
+  QH_EINVAL = 1,       /* invalid argument or malformed input */
+  QH_ENOMEM = 2,       /* device or host allocation failed */
+  QH_ECUDA = 3,        /* a CUDA runtime/driver call failed */
+  QH_ETIMEOUT = 4,     /* a bounded device-side wait expired; context stays usable */
+  QH_EUNSUPPORTED = 5  /* valid request outside this build's limits */
+} qh_status;
+
+typedef struct qh_ctx qh_ctx;
+typedef struct qh_graph qh_graph;
+typedef struct qh_solution qh_solution;
+
+/* Graph modes (read-based / SNP-based method, Methods). */
+enum { QH_MODE_READ = 0, QH_MODE_SNP = 1 };
+/* Read-graph weights: CONFLICT = count of shared SNPs with opposing alleles
+ * (Eqs. delta and w_ab); SIGNED = conflicts - agreements, W = -M M^T. */
+enum { QH_WEIGHT_CONFLICT = 0, QH_WEIGHT_SIGNED = 1 };
+/* J x X product precision in the bSB step.  State x, y is FP32 in all modes.
+ * FP32: SIMT FP32 product.  BF16: tcgen05 BF16 x BF16 -> FP32 (J exact for
+ * integer |w| <= 256; larger integers and real weights are split J = hi + lo,
+ * both BF16, accumulated in the same FP32 accumulator). */
+enum { QH_PREC_FP32 = 0, QH_PREC_BF16 = 1 };
+/* Schedules: LINEAR = a(t) = a0 * t / steps with the given steps;
+ * AUTO = steps chosen from the block size as in the paper's SNP-based runs
+ * (500 iterations for < 5,000 nodes, 1,000 otherwise). */
+enum { QH_SCHED_LINEAR = 0, QH_SCHED_AUTO = 1 };
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to issue work on, or NULL to let the context create (and own) one.
+ * Errors: QH_EINVAL (out is NULL, bad device), QH_ECUDA. */
+qh_status qh_create(qh_ctx** out, int device, void* cuda_stream);
+/* Release the context (waits for its stream).  NULL is a no-op. */
+void qh_destroy(qh_ctx* ctx);
+/* Static English name of a status code. */
+const char* qh_status_str(int status);
+/* Description of the last error on this context ("" if none).  Valid until
+ * the next call on the context. */
+const char* qh_last_error(const qh_ctx* ctx);
+
+/* ---------------------------------------------------------------- inputs */
+
+/* Fragments: the paper's "sparse vector of phased allele observations with
+ * associated quality scores" per read (Methods, input preprocessing), as CSR.
+ *  n_frags, n_snps : m fragments over n heterozygous SNPs
+ *  frag_ptr  int64[m+1]  fragment i owns entries frag_ptr[i] .. frag_ptr[i+1]-1;
+ *                        frag_ptr[0] = 0, non-decreasing
+ *  snp       int32[nnz]  SNP index in [0, n), strictly increasing in a fragment
+ *  allele    int8[nnz]   +1 = allele of the initial H1, -1 = of the initial H2
+ *                        (ternary matrix M, read-based matrix construction)
+ *  qual      uint8[nnz]  Phred base quality Q in [4, 93]; required in SNP mode,
+ *                        may be NULL in read mode
+ *  is_porec  uint8[m]    1 = Pore-C fragment; NULL = none
+ * Fragment order matters only for speed: reads sorted by first SNP give banded
+ * J tiles. */
+typedef struct {
+  int32_t n_frags;
+  int32_t n_snps;
+  const int64_t* frag_ptr;
+  const int32_t* snp;
+  const int8_t* allele;
+  const uint8_t* qual;
+  const uint8_t* is_porec;
+  int32_t on_device; /* 1: the five arrays are device pointers */
+} qh_fragments;
+
+typedef struct {
+  int32_t mode;        /* QH_MODE_READ | QH_MODE_SNP */
+  int32_t weight_mode; /* READ mode: QH_WEIGHT_CONFLICT | QH_WEIGHT_SIGNED */
+  int32_t linkage_k;   /* SNP mode: linkage depth k/10, 1..10 (10 = all pairs) */
+  int32_t dense;       /* 1: store every J tile of each block (no zero-tile skipping) */
+  double porec_alpha;  /* SNP mode: Pore-C contribution factor (paper default 0.1) */
+} qh_graph_opts;
+
+/* Build the phasing graph and its phase blocks.
+ * READ mode: vertices = fragments; w_ab per weight_mode (read-based Max-Cut
+ * graph construction).  SNP mode: vertices = SNPs; w_uv = -sum_i alpha_i *
+ * sgn(W_iu W_iv) log10(P_cis / P_trans) / (|S_i| - 1) accumulated in FP64 in
+ * fragment order, with q~ = 1 - 10^(-Q/10) (SNP-based matrix and graph
+ * construction; Pore-C data support).  Edges are the pairs with w != 0;
+ * connected components with >= 2 vertices become phase blocks, numbered by
+ * their smallest vertex; single-vertex components are dropped.
+ * Errors: QH_EINVAL (malformed fragments, Q outside [4, 93] in SNP mode,
+ * bad options), QH_ENOMEM, QH_ECUDA, QH_EUNSUPPORTED (an SNP row gathering more
+ * than 8192 fragment terms). */
+qh_status qh_build_graph(qh_ctx* ctx, const qh_fragments* frags, const qh_graph_opts* opts,
+                         qh_graph** out);
+
+/* Graph summary.  Any output pointer may be NULL.
+ *  n_nodes     : vertices (fragments or SNPs)
+ *  n_blocks    : phase blocks
+ *  block_sizes : int32[cap] filled with min(cap, n_blocks) block sizes
+ *  nnz         : stored directed edges (2 per undirected edge)
+ *  n_tiles     : stored 128 x 128 J tiles */
+qh_status qh_graph_info(const qh_graph* g, int32_t* n_nodes, int32_t* n_blocks,
+                        int32_t* block_sizes, int32_t cap, int64_t* nnz, int64_t* n_tiles);
+
+/* Copy the edge list of the graph to host arrays (test and inspection hook).
+ * row_ptr int64[n_nodes+1], col int32[nnz], w float64[nnz] (exact integers in
+ * READ mode).  Rows list each vertex's neighbours. */
+qh_status qh_graph_edges(qh_ctx* ctx, const qh_graph* g, int64_t* row_ptr, int32_t* col,
+                         double* w);
+
+/* Block membership: block_of int32[n_nodes] (-1 for dropped singletons) and
+ * local int32[n_nodes] (index of the vertex inside its block, ascending vertex
+ * order).  Either may be NULL. */
+qh_status qh_graph_blocks(qh_ctx* ctx, const qh_graph* g, int32_t* block_of, int32_t* local);
+
+void qh_graph_free(qh_graph* g);
+
+/* ---------------------------------------------------------------- solver */
+
+/* bSB options (SB algorithm solution).  Each step, for every replica:
+ *   y <- y + dt * ( -(a0 - a(t)) x + c0 * J x ),   x <- x + dt * a0 * y,
+ *   |x| > 1  =>  x <- sgn(x), y <- 0,              a(t) = a0 * t / steps,
+ * with x, y drawn uniform on [-0.1, 0.1] from SplitMix64 keyed by
+ * (seed, block, refinement iteration, replica index, local vertex, x|y).
+ * Spins are s = sgn(x) with sgn(0) = +1. */
+typedef struct {
+  int32_t replicas;     /* R >= 1 (multiple of 16 for QH_PREC_BF16) */
+  int32_t steps;        /* >= 1 (LINEAR schedule) */
+  int32_t schedule;     /* QH_SCHED_LINEAR | QH_SCHED_AUTO */
+  int32_t precision;    /* QH_PREC_FP32 | QH_PREC_BF16 */
+  double dt;            /* time step (1.0) */
+  double a0;            /* bifurcation parameter target (1.0) */
+  double c0;            /* coupling scale; <= 0 selects 0.5 / (sigma sqrt(N)) per
+                           block, sigma^2 = sum_{a != b} J_ab^2 / (N (N - 1)) */
+  uint64_t seed;        /* RNG seed */
+  int32_t replica_base; /* first replica index (replicas are base .. base+R-1) */
+  int32_t check_every;  /* energy check period in steps for early stop (0 = off) */
+  int32_t patience;     /* stop a block after this many checks without a better
+                           best-replica energy (0 = never stop early) */
+  int32_t refine_max;   /* SNP mode: maximum refinement iterations (>= 1) */
+} qh_bsb_opts;
+
+/* Run multi-replica bSB on every block of the graph in one batched launch per
+ * step (the step loop is replayed from a CUDA graph).  Each replica's final
+ * spins are cut-evaluated exactly (FP64 reduction; exact for integer weights);
+ * the best replica per block wins, ties to the lowest replica index.
+ * SNP mode additionally runs the iterative refinement (flip counter C on the
+ * smaller subset, sign inversion of edges crossing the partition) until the
+ * cut is <= 0, the partition has a single subset, or refine_max iterations.
+ * Errors: QH_EINVAL, QH_ENOMEM, QH_ECUDA, QH_ETIMEOUT. */
+qh_status qh_bsb_solve(qh_ctx* ctx, const qh_graph* g, const qh_bsb_opts* opts,
+                       qh_solution** out);
+
+/* Per-block result.  Any output pointer may be NULL.
+ *  spins        : int8[block size], best replica's spins in local vertex order
+ *  best_cut     : cut of those spins on the block's original (ungauged) graph
+ *  best_replica : replica index (replica_base + r) of the winner
+ *  steps_run    : bSB steps actually run (early stop may shorten it)
+ *  iterations   : refinement iterations (1 in READ mode)
+ * Errors: QH_EINVAL (block out of range). */
+qh_status qh_solution_block(qh_ctx* ctx, const qh_solution* sol, int32_t block, int8_t* spins,
+                            double* best_cut, int32_t* best_replica, int32_t* steps_run,
+                            int32_t* iterations);
+
+/* Spins of the solution by vertex: int8[n_nodes], +1 / -1 for vertices in a
+ * block (READ mode: best replica; SNP mode: the flip-count parity partition,
+ * +1 where C is even), 0 for dropped singletons. */
+qh_status qh_solution_spins(qh_ctx* ctx, const qh_solution* sol, int8_t* spins);
+
+/* All replicas' final cuts of the first refinement iteration:
+ * cuts float64[n_blocks * R], row b = block b (values on the block's graph). */
+qh_status qh_solution_cuts(qh_ctx* ctx, const qh_solution* sol, double* cuts);
+
+/* Timing of the last solve in milliseconds (CUDA events on the context stream):
+ *  solve_ms : whole qh_bsb_solve device time
+ *  step_ms  : the bSB step launches only; n_step_launches launches
+ *  spin_updates : sum over blocks of N_b * R * steps_run_b (all iterations) */
+qh_status qh_solution_timing(const qh_solution* sol, double* solve_ms, double* step_ms,
+                             int64_t* n_step_launches, double* spin_updates);
+
+void qh_solution_free(qh_solution* sol);
+
+/* ---------------------------------------------------------------- phase */
+
+/* Haplotypes from the solution (consistency processing / SNP parity swap).
+ * READ mode: each SNP is voted on by the block holding the most reads that
+ * cover it (ties: lower block); with d_l = c_l^(+) - c_l^(-) for S_1 = {s=+1}
+ * and S_2 = {s=-1}: opposing majorities give S_1 the sign of d_1; otherwise the
+ * subset with the larger |d_l| (tie: S_1) keeps its majority and the other
+ * takes the complement; zero coverage or d_1 = d_2 = 0 leaves it unphased.
+ * SNP mode: H1' = H1 where C is even, swapped where C is odd.
+ * Outputs (host or device per on_device), each of length n_snps:
+ *  hap1 int8 : +1 = H1' carries the initial-H1 allele, -1 = the initial-H2
+ *              allele, 0 = unphased;   hap2 = -hap1 (0 where unphased)
+ *  block_id int32 : phase block of the SNP, -1 if unphased
+ * Errors: QH_EINVAL. */
+qh_status qh_phase(qh_ctx* ctx, const qh_graph* g, const qh_solution* sol, int8_t* hap1,
+                   int8_t* hap2, int32_t* block_id, int32_t on_device);
+
+/* ---------------------------------------------------------------- test hooks */
+
+/* One J x X product with the solver's operands, for precision checks.
+ * x  float32[R][n_pad] (device) : state, padded vertex layout
+ * z  float32[R][n_pad] (device) : output J_hat x X_hat (FP32 accumulate), where
+ *    J_hat, X_hat are the precision's operands (BF16 rounds x to BF16).
+ * n_pad is qh_debug_layout's value.  R multiple of 16 for BF16.
+ * Errors: QH_EINVAL, QH_ECUDA, QH_ETIMEOUT. */
+qh_status qh_debug_matvec(qh_ctx* ctx, const qh_graph* g, int32_t precision, int32_t R,
+                          const float* x, float* z);
+
+/* Run `nsteps` solver steps t0 .. t0+nsteps-1 of a `steps`-step schedule from a
+ * given state, in place: x, y float32[R][n_pad] (device), same layout.
+ * c0_per_block float64[n_blocks] (host) or NULL for the default c0. */
+qh_status qh_debug_steps(qh_ctx* ctx, const qh_graph* g, int32_t precision, int32_t R,
+                         float* x, float* y, int32_t t0, int32_t nsteps, int32_t steps, double dt,
+                         double a0, const double* c0_per_block);
+
+/* Padded layout: n_pad and padded_index int32[n_nodes] (-1 for vertices in no
+ * block): vertex v of block b sits at padded column pad_off[b] + local[v]. */
+qh_status qh_debug_layout(qh_ctx* ctx, const qh_graph* g, int32_t* n_pad, int32_t* padded_index,
+                          double* c0_default);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QHAP_H */

@@ -1,0 +1,810 @@
+// C ABI of libqhap: contexts, graph handles, the batched bSB solve (step loop
+// captured once into a CUDA graph and replayed), phasing and test hooks.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <new>
+
+#include "qh_internal.cuh"
+#include "util.cuh"
+
+struct qh_ctx {
+  qh::Ctx c;
+};
+struct qh_graph {
+  qh::Graph g;
+  qh_ctx* owner;
+};
+struct qh_solution {
+  qh::Solution s;
+};
+
+namespace qh {
+
+qh_status set_err(Ctx* ctx, qh_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+qh_status cuda_fail(Ctx* ctx, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (ctx) ctx->err = m;
+  return e == cudaErrorMemoryAllocation ? QH_ENOMEM : QH_ECUDA;
+}
+
+void* dalloc(Graph& g, size_t bytes) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  g.allocs.push_back(p);
+  return p;
+}
+
+void* Ctx::scratch(size_t bytes, int slot) {
+  if (slot >= (int)slots.size()) {
+    slots.resize(slot + 1, nullptr);
+    slot_bytes.resize(slot + 1, 0);
+  }
+  if (bytes == 0) bytes = 16;
+  if (slot_bytes[slot] < bytes) {
+    if (slots[slot]) {
+      cudaStreamSynchronize(stream);
+      cudaFree(slots[slot]);
+      slots[slot] = nullptr;
+      slot_bytes[slot] = 0;
+      if (loop_exec) {  // captured pointers may dangle now
+        cudaGraphExecDestroy(loop_exec);
+        loop_exec = nullptr;
+        loop_key.clear();
+      }
+    }
+    void* p = nullptr;
+    size_t want = bytes + bytes / 8;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return nullptr;
+    }
+    slots[slot] = p;
+    slot_bytes[slot] = want;
+  }
+  return slots[slot];
+}
+
+namespace {
+
+// Scratch slot ids used by the solver (graph build uses 0..20).
+enum {
+  S_X = 32, S_Y, S_X1, S_XH0, S_XH1, S_SIGNS, S_NODEVAL, S_CUTS, S_BESTR, S_BESTCUT, S_ACTIVE,
+  S_STEPSB, S_C0, S_SEEN, S_STALL, S_STEPSRUN, S_SPINS, S_C, S_WWORK, S_TBWORK, S_TFWORK,
+  S_SUMW, S_SUMJ2, S_NODETMP, S_SIGNS1, S_NODEVAL1, S_CUT1, S_DBG0, S_DBG1, S_DBG2, S_RUNNING
+};
+
+struct SolveBufs {
+  float *x, *y, *x1;
+  __nv_bfloat16 *xh0, *xh1;
+  int8_t* signs;
+  double *node_val, *cuts, *best_cut, *seen;
+  int32_t *best_r, *active, *running, *steps_b, *stall, *steps_run;
+  float* c0;
+  int8_t* spins;
+  int32_t* C;
+};
+
+qh_status run_step(Ctx* ctx, const Graph& g, int precision, const TcPlan& plan, StepArgs a,
+                   const float* x_cur_f32, float* x_next_f32, const __nv_bfloat16* xh_cur,
+                   __nv_bfloat16* xh_next) {
+  if (precision == QH_PREC_FP32) {
+    a.xin = x_cur_f32;
+    a.xout = x_next_f32;
+    launch_step_f32(ctx->stream, g, a);
+    return QH_OK;
+  }
+  a.xh_out = xh_next;
+  return launch_step_tc(ctx, g, a, xh_cur, plan);
+}
+
+qh_status check_err_word(Ctx* ctx) {
+  int32_t herr = 0;
+  QH_CUDA_TRY(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  QH_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (herr & ERR_TIMEOUT) {
+    cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), ctx->stream);
+    return set_err(ctx, QH_ETIMEOUT, "a bounded device wait expired in the bSB step kernel");
+  }
+  return QH_OK;
+}
+
+TcPlan pick_plan(int R) {
+  TcPlan p;
+  p.bn = (R % 128 == 0) ? 128 : 64;
+  p.stages = 3;
+  return p;
+}
+
+}  // namespace
+}  // namespace qh
+
+using namespace qh;
+
+extern "C" {
+
+const char* qh_status_str(int st) {
+  switch (st) {
+    case QH_OK: return "QH_OK";
+    case QH_EINVAL: return "QH_EINVAL";
+    case QH_ENOMEM: return "QH_ENOMEM";
+    case QH_ECUDA: return "QH_ECUDA";
+    case QH_ETIMEOUT: return "QH_ETIMEOUT";
+    case QH_EUNSUPPORTED: return "QH_EUNSUPPORTED";
+    default: return "QH_UNKNOWN";
+  }
+}
+
+const char* qh_last_error(const qh_ctx* ctx) { return ctx ? ctx->c.err.c_str() : ""; }
+
+qh_status qh_create(qh_ctx** out, int device, void* stream) {
+  if (!out) return QH_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    (void)cudaGetLastError();
+    return QH_EINVAL;
+  }
+  qh_ctx* h = new (std::nothrow) qh_ctx;
+  if (!h) return QH_ENOMEM;
+  Ctx* ctx = &h->c;
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete h;
+    return QH_ECUDA;
+  }
+  cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
+  if (stream) {
+    ctx->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return QH_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  if (cudaMalloc(&ctx->d_err, sizeof(int32_t)) != cudaSuccess ||
+      cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), ctx->stream) != cudaSuccess) {
+    delete h;
+    return QH_ECUDA;
+  }
+  for (auto& e : ctx->ev) cudaEventCreate(&e);
+  if (tc_prepare(ctx) != QH_OK) {
+    qh_status st = QH_ECUDA;
+    qh_destroy(h);
+    return st;
+  }
+  *out = h;
+  return QH_OK;
+}
+
+void qh_destroy(qh_ctx* h) {
+  if (!h) return;
+  Ctx* ctx = &h->c;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->loop_exec) cudaGraphExecDestroy(ctx->loop_exec);
+  for (void* p : ctx->slots)
+    if (p) cudaFree(p);
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete h;
+}
+
+void qh_graph_free(qh_graph* g) {
+  if (!g) return;
+  if (g->owner) cudaStreamSynchronize(g->owner->c.stream);
+  for (void* p : g->g.allocs) cudaFree(p);
+  delete g;
+}
+
+qh_status qh_build_graph(qh_ctx* h, const qh_fragments* f, const qh_graph_opts* o, qh_graph** out) {
+  if (!h) return QH_EINVAL;
+  Ctx* ctx = &h->c;
+  ctx->err.clear();
+  if (!f || !o || !out) return set_err(ctx, QH_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (f->n_frags < 0 || f->n_snps < 0 || !f->frag_ptr)
+    return set_err(ctx, QH_EINVAL, "bad fragment sizes or NULL frag_ptr");
+  if (o->mode != QH_MODE_READ && o->mode != QH_MODE_SNP) return set_err(ctx, QH_EINVAL, "bad mode");
+  if (o->mode == QH_MODE_READ && o->weight_mode != QH_WEIGHT_CONFLICT && o->weight_mode != QH_WEIGHT_SIGNED)
+    return set_err(ctx, QH_EINVAL, "bad weight_mode");
+  if (o->mode == QH_MODE_SNP) {
+    if (o->linkage_k < 1 || o->linkage_k > 10) return set_err(ctx, QH_EINVAL, "linkage_k must be 1..10");
+    if (!f->qual) return set_err(ctx, QH_EINVAL, "SNP mode needs qualities");
+    if (!(o->porec_alpha >= 0.0)) return set_err(ctx, QH_EINVAL, "porec_alpha must be >= 0");
+  }
+  cudaSetDevice(ctx->device);
+  qh_graph* gh = new (std::nothrow) qh_graph;
+  if (!gh) return QH_ENOMEM;
+  gh->owner = h;
+  qh_status st = build_graph_device(ctx, f, o, &gh->g);
+  if (st != QH_OK) {
+    cudaStreamSynchronize(ctx->stream);
+    (void)cudaGetLastError();
+    qh_graph_free(gh);
+    return st;
+  }
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    qh_graph_free(gh);
+    return cuda_fail(ctx, e, "graph build");
+  }
+  *out = gh;
+  return QH_OK;
+}
+
+qh_status qh_graph_info(const qh_graph* gh, int32_t* n_nodes, int32_t* n_blocks, int32_t* sizes,
+                        int32_t cap, int64_t* nnz, int64_t* n_tiles) {
+  if (!gh) return QH_EINVAL;
+  const Graph& g = gh->g;
+  if (n_nodes) *n_nodes = g.n_nodes;
+  if (n_blocks) *n_blocks = g.n_blocks;
+  if (sizes)
+    for (int32_t b = 0; b < std::min(cap, g.n_blocks); ++b) sizes[b] = g.h_block_size[b];
+  if (nnz) *nnz = g.nnz;
+  if (n_tiles) *n_tiles = g.n_tiles;
+  return QH_OK;
+}
+
+qh_status qh_graph_edges(qh_ctx* h, const qh_graph* gh, int64_t* rp, int32_t* col, double* w) {
+  if (!h || !gh) return QH_EINVAL;
+  Ctx* ctx = &h->c;
+  const Graph& g = gh->g;
+  cudaStream_t s = ctx->stream;
+  if (rp) QH_CUDA_TRY(cudaMemcpyAsync(rp, g.row_ptr, sizeof(int64_t) * (g.n_nodes + 1), cudaMemcpyDeviceToHost, s));
+  if (col && g.nnz) QH_CUDA_TRY(cudaMemcpyAsync(col, g.col, sizeof(int32_t) * g.nnz, cudaMemcpyDeviceToHost, s));
+  if (w && g.nnz) QH_CUDA_TRY(cudaMemcpyAsync(w, g.w, sizeof(double) * g.nnz, cudaMemcpyDeviceToHost, s));
+  QH_CUDA_TRY(cudaStreamSynchronize(s));
+  return QH_OK;
+}
+
+qh_status qh_graph_blocks(qh_ctx* h, const qh_graph* gh, int32_t* block_of, int32_t* local) {
+  if (!h || !gh) return QH_EINVAL;
+  Ctx* ctx = &h->c;
+  const Graph& g = gh->g;
+  cudaStream_t s = ctx->stream;
+  if (block_of && g.n_nodes)
+    QH_CUDA_TRY(cudaMemcpyAsync(block_of, g.block_of, sizeof(int32_t) * g.n_nodes, cudaMemcpyDeviceToHost, s));
+  if (local && g.n_nodes)
+    QH_CUDA_TRY(cudaMemcpyAsync(local, g.local, sizeof(int32_t) * g.n_nodes, cudaMemcpyDeviceToHost, s));
+  QH_CUDA_TRY(cudaStreamSynchronize(s));
+  return QH_OK;
+}
+
+qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_solution** out) {
+  if (!h) return QH_EINVAL;
+  Ctx* ctx = &h->c;
+  ctx->err.clear();
+  if (!gh || !o || !out) return set_err(ctx, QH_EINVAL, "NULL argument");
+  *out = nullptr;
+  const Graph& G = gh->g;
+  const int32_t R = o->replicas, nb = G.n_blocks;
+  if (R < 1) return set_err(ctx, QH_EINVAL, "replicas must be >= 1");
+  if (o->schedule != QH_SCHED_LINEAR && o->schedule != QH_SCHED_AUTO) return set_err(ctx, QH_EINVAL, "bad schedule");
+  if (o->schedule == QH_SCHED_LINEAR && o->steps < 1) return set_err(ctx, QH_EINVAL, "steps must be >= 1");
+  if (o->precision != QH_PREC_FP32 && o->precision != QH_PREC_BF16) return set_err(ctx, QH_EINVAL, "bad precision");
+  if (!(o->dt > 0.0) || !(o->a0 > 0.0)) return set_err(ctx, QH_EINVAL, "dt and a0 must be > 0");
+  if (o->check_every < 0 || o->patience < 0 || o->replica_base < 0) return set_err(ctx, QH_EINVAL, "negative option");
+  if ((int64_t)o->replica_base + R > (1 << 16)) return set_err(ctx, QH_EINVAL, "replica indices must stay below 65536");
+  const bool snp = G.mode == QH_MODE_SNP;
+  const int32_t refine_max = snp ? o->refine_max : 1;
+  if (refine_max < 1) return set_err(ctx, QH_EINVAL, "refine_max must be >= 1");
+  const TcPlan plan = pick_plan(R);
+  if (o->precision == QH_PREC_BF16 && !tc_plan_ok(R, plan))
+    return set_err(ctx, QH_EINVAL, "BF16 precision needs replicas to be a multiple of 64");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = ctx->stream;
+  qh_solution* sh = new (std::nothrow) qh_solution;
+  if (!sh) return QH_ENOMEM;
+  Solution& sol = sh->s;
+  sol.mode = G.mode;
+  sol.n_blocks = nb;
+  sol.R = R;
+  sol.replica_base = o->replica_base;
+  sol.n_nodes = G.n_nodes;
+  sol.block_size = G.h_block_size;
+  sol.block_ptr = G.h_block_ptr;
+  sol.best_r.assign(nb, 0);
+  sol.steps_run.assign(nb, 0);
+  sol.iters.assign(nb, 0);
+  sol.best_cut.assign(nb, 0.0);
+  sol.cuts_first.assign((size_t)nb * R, 0.0);
+  sol.spins.assign(G.n_nodes, 0);
+  sol.C.assign(G.n_nodes, 0);
+  if (nb == 0) {
+    *out = sh;
+    return QH_OK;
+  }
+  // ---- per-block schedule and coupling scale
+  std::vector<int32_t> h_steps(nb);
+  int32_t max_steps = 0;
+  for (int32_t b = 0; b < nb; ++b) {
+    h_steps[b] = o->schedule == QH_SCHED_AUTO ? (G.h_block_size[b] < 5000 ? 500 : 1000) : o->steps;
+    max_steps = std::max(max_steps, h_steps[b]);
+  }
+  std::vector<float> h_c0(nb);
+  for (int32_t b = 0; b < nb; ++b) h_c0[b] = (float)(o->c0 > 0.0 ? o->c0 : G.h_c0[b]);
+  // ---- buffers
+  const size_t NS = (size_t)R * G.n_pad;
+  SolveBufs B{};
+  auto sc = [&](size_t bytes, int slot) { return ctx->scratch(bytes, slot); };
+  B.x = (float*)sc(NS * 4, S_X);
+  B.y = (float*)sc(NS * 4, S_Y);
+  if (o->precision == QH_PREC_FP32) {
+    B.x1 = (float*)sc(NS * 4, S_X1);
+  } else {
+    B.xh0 = (__nv_bfloat16*)sc(NS * 2, S_XH0);
+    B.xh1 = (__nv_bfloat16*)sc(NS * 2, S_XH1);
+  }
+  B.signs = (int8_t*)sc(NS, S_SIGNS);
+  B.node_val = (double*)sc(NS * 8, S_NODEVAL);
+  B.cuts = (double*)sc((size_t)nb * R * 8, S_CUTS);
+  B.best_r = (int32_t*)sc(nb * 4, S_BESTR);
+  B.best_cut = (double*)sc(nb * 8, S_BESTCUT);
+  B.active = (int32_t*)sc(nb * 4, S_ACTIVE);
+  B.running = (int32_t*)sc(nb * 4, S_RUNNING);
+  B.steps_b = (int32_t*)sc(nb * 4, S_STEPSB);
+  B.c0 = (float*)sc(nb * 4, S_C0);
+  B.seen = (double*)sc(nb * 8, S_SEEN);
+  B.stall = (int32_t*)sc(nb * 4, S_STALL);
+  B.steps_run = (int32_t*)sc(nb * 4, S_STEPSRUN);
+  B.spins = (int8_t*)sc(G.n_nodes + 16, S_SPINS);
+  B.C = (int32_t*)sc((G.n_nodes + 1) * 4, S_C);
+  bool okb = B.x && B.y && B.signs && B.node_val && B.cuts && B.best_r && B.best_cut && B.active && B.running &&
+             B.steps_b && B.c0 && B.seen && B.stall && B.steps_run && B.spins && B.C &&
+             (o->precision == QH_PREC_FP32 ? B.x1 != nullptr : (B.xh0 && B.xh1));
+  // working copy of the graph for the SNP refinement (weights, tiles, sums are gauged)
+  Graph W = G;
+  W.allocs.clear();
+  double* sum_w_work = G.sum_w;
+  if (snp && okb) {
+    W.w = (double*)sc(std::max<int64_t>(G.nnz, 1) * 8, S_WWORK);
+    W.tile_bf16 = (__nv_bfloat16*)sc(std::max<int64_t>(G.n_tiles, 1) * TILE * TILE * 2, S_TBWORK);
+    W.tile_f32 = (float*)sc(std::max<int64_t>(G.n_tiles_hi, 1) * TILE * TILE * 4, S_TFWORK);
+    sum_w_work = (double*)sc(nb * 8, S_SUMW);
+    double* sj2 = (double*)sc(nb * 8, S_SUMJ2);
+    double* ntmp = (double*)sc((size_t)std::max(G.n_nodes, 1) * 16, S_NODETMP);
+    okb = W.w && W.tile_bf16 && W.tile_f32 && sum_w_work && sj2 && ntmp;
+    if (okb) {
+      if (G.nnz) cudaMemcpyAsync(W.w, G.w, G.nnz * 8, cudaMemcpyDeviceToDevice, s);
+      if (G.n_tiles) cudaMemcpyAsync(W.tile_bf16, G.tile_bf16, G.n_tiles * TILE * TILE * 2, cudaMemcpyDeviceToDevice, s);
+      if (G.n_tiles_hi) cudaMemcpyAsync(W.tile_f32, G.tile_f32, G.n_tiles_hi * TILE * TILE * 4, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(sum_w_work, G.sum_w, nb * 8, cudaMemcpyDeviceToDevice, s);
+    }
+  }
+  if (!okb) {
+    delete sh;
+    return set_err(ctx, QH_ENOMEM, "device allocation failed (solver state)");
+  }
+  QH_CUDA_TRY(cudaMemcpyAsync(B.steps_b, h_steps.data(), nb * 4, cudaMemcpyHostToDevice, s));
+  QH_CUDA_TRY(cudaMemcpyAsync(B.c0, h_c0.data(), nb * 4, cudaMemcpyHostToDevice, s));
+  QH_CUDA_TRY(cudaMemsetAsync(B.C, 0, (G.n_nodes + 1) * 4, s));
+  QH_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, 4, s));
+  std::vector<int32_t> ones(nb, 1);
+  QH_CUDA_TRY(cudaMemcpyAsync(B.active, ones.data(), nb * 4, cudaMemcpyHostToDevice, s));
+  QH_CUDA_TRY(cudaEventRecord(ctx->ev[0], s));
+
+  const bool early = o->check_every > 0 && o->patience > 0;
+  // ---- the step loop, captured once per shape and replayed
+  char key[512];
+  snprintf(key, sizeof key, "%d|%d|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%lld|%d|%.17g|%.17g",
+           o->precision, R, G.n_row_tiles, max_steps, early ? o->check_every : 0,
+           (void*)W.tile_bf16, (void*)W.tile_f32, (void*)W.w, (void*)B.x, (void*)B.y,
+           (void*)B.x1, (void*)B.xh0, (void*)G.rt, (long long)G.n_tiles, o->patience, o->dt,
+           o->a0);
+  std::string skey = std::string(key) + "|" + std::to_string((uintptr_t)sum_w_work) + "|" +
+                     std::to_string((uintptr_t)G.tile_col);
+  StepArgs a{};
+  a.rt = G.rt;
+  a.tile_col = G.tile_col;
+  a.tile_f32 = W.tile_f32;
+  a.x = B.x;
+  a.y = B.y;
+  a.c0 = B.c0;
+  a.active = B.running;
+  a.steps_b = B.steps_b;
+  a.n_pad = G.n_pad;
+  a.R = R;
+  a.dt = (float)o->dt;
+  a.a0 = o->a0;
+  a.dta0 = (float)(o->dt * o->a0);
+  a.err = ctx->d_err;
+  const float* x_final = B.x;
+  if (o->precision == QH_PREC_FP32 && (max_steps % 2 == 1)) x_final = B.x1;
+  if (ctx->loop_key != skey || !ctx->loop_exec) {
+    if (ctx->loop_exec) {
+      cudaGraphExecDestroy(ctx->loop_exec);
+      ctx->loop_exec = nullptr;
+    }
+    ctx->loop_key.clear();
+    cudaGraph_t graph;
+    QH_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    qh_status st = QH_OK;
+    for (int32_t t = 0; t < max_steps && st == QH_OK; ++t) {
+      a.t = t;
+      const bool even = (t % 2) == 0;
+      st = run_step(ctx, W, o->precision, plan, a, even ? B.x : B.x1, even ? B.x1 : B.x,
+                    even ? B.xh0 : B.xh1, even ? B.xh1 : B.xh0);
+      if (early && (t + 1) % o->check_every == 0 && t + 1 < max_steps) {
+        const float* xc = (o->precision == QH_PREC_FP32 && even) ? B.x1 : B.x;
+        launch_signs(s, W, R, xc, B.signs);
+        launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.running);
+        launch_pick_best(s, nb, R, B.cuts, B.best_r, B.best_cut, B.running);
+        launch_early_stop(s, nb, B.best_cut, B.seen, B.stall, B.running, B.steps_run, o->patience,
+                          t + 1);
+      }
+    }
+    cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    if (st != QH_OK) {
+      if (ce == cudaSuccess) cudaGraphDestroy(graph);
+      delete sh;
+      return st;
+    }
+    if (ce != cudaSuccess) {
+      delete sh;
+      return cuda_fail(ctx, ce, "cudaStreamEndCapture");
+    }
+    ce = cudaGraphInstantiate(&ctx->loop_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      ctx->loop_exec = nullptr;
+      delete sh;
+      return cuda_fail(ctx, ce, "cudaGraphInstantiate");
+    }
+    ctx->loop_key = skey;
+  }
+  double step_ms_total = 0.0, spin_updates = 0.0;
+  int64_t launches = 0;
+  std::vector<int32_t> h_active(nb, 1), h_steps_run(nb);
+  for (int32_t it = 0; it < refine_max; ++it) {
+    for (int32_t b = 0; b < nb; ++b)
+      if (h_active[b]) sol.iters[b] += 1;
+    // steps_run defaults to the block's schedule length; early stop lowers it
+    QH_CUDA_TRY(cudaMemcpyAsync(B.steps_run, h_steps.data(), nb * 4, cudaMemcpyHostToDevice, s));
+    if (early) {
+      std::vector<double> neg(nb, -INFINITY);
+      QH_CUDA_TRY(cudaMemcpyAsync(B.seen, neg.data(), nb * 8, cudaMemcpyHostToDevice, s));
+      QH_CUDA_TRY(cudaMemsetAsync(B.stall, 0, nb * 4, s));
+    }
+    QH_CUDA_TRY(cudaMemcpyAsync(B.running, B.active, nb * 4, cudaMemcpyDeviceToDevice, s));
+    launch_init_state(s, W, R, o->replica_base, o->seed, it, B.x, B.y,
+                      o->precision == QH_PREC_BF16 ? B.xh0 : nullptr, B.active);
+    QH_CUDA_TRY(cudaEventRecord(ctx->ev[2], s));
+    QH_CUDA_TRY(cudaGraphLaunch(ctx->loop_exec, s));
+    QH_CUDA_TRY(cudaEventRecord(ctx->ev[3], s));
+    launch_signs(s, W, R, x_final, B.signs);
+    launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.active);
+    launch_pick_best(s, nb, R, B.cuts, B.best_r, B.best_cut, B.active);
+    launch_extract_spins(s, W, R, B.signs, B.best_r, B.spins, B.active);
+    if (it == 0)
+      QH_CUDA_TRY(cudaMemcpyAsync(sol.cuts_first.data(), B.cuts, (size_t)nb * R * 8, cudaMemcpyDeviceToHost, s));
+    QH_CUDA_TRY(cudaMemcpyAsync(h_steps_run.data(), B.steps_run, nb * 4, cudaMemcpyDeviceToHost, s));
+    if (it == 0 || !snp) {
+      QH_CUDA_TRY(cudaMemcpyAsync(sol.best_r.data(), B.best_r, nb * 4, cudaMemcpyDeviceToHost, s));
+      QH_CUDA_TRY(cudaMemcpyAsync(sol.best_cut.data(), B.best_cut, nb * 8, cudaMemcpyDeviceToHost, s));
+    }
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+    {
+      qh_status st = check_err_word(ctx);
+      if (st != QH_OK) {
+        delete sh;
+        return st;
+      }
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
+    step_ms_total += ms;
+    launches += max_steps;
+    for (int32_t b = 0; b < nb; ++b)
+      if (h_active[b]) {
+        spin_updates += (double)G.h_block_size[b] * R * h_steps_run[b];
+        if (it == 0 || !snp) sol.steps_run[b] = h_steps_run[b];
+      }
+    if (!snp) break;
+    // ---- SNP refinement: termination test, flip counter, sign inversion
+    launch_refine_prepare(s, W, B.spins, B.best_cut, B.active, B.C);
+    QH_CUDA_TRY(cudaMemcpyAsync(h_active.data(), B.active, nb * 4, cudaMemcpyDeviceToHost, s));
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+    int32_t n_active = 0;
+    for (int32_t b = 0; b < nb; ++b) n_active += h_active[b] != 0;
+    if (n_active == 0 || it + 1 == refine_max) break;
+    launch_gauge(s, W, B.spins, W.w, B.active);
+    {
+      qh_status st = retile(ctx, &W, W.w, W.tile_bf16, W.tile_f32);
+      if (st != QH_OK) {
+        delete sh;
+        return st;
+      }
+    }
+    launch_block_sums(s, W, W.w, sum_w_work, (double*)ctx->scratch(nb * 8, S_SUMJ2),
+                      (double*)ctx->scratch((size_t)std::max(G.n_nodes, 1) * 16, S_NODETMP));
+  }
+  // ---- final spins and cut on the original graph
+  if (snp) {
+    // partition from the flip-count parity: +1 where C is even
+    std::vector<int32_t> hC(G.n_nodes);
+    std::vector<int32_t> blk(G.n_nodes);
+    if (G.n_nodes) {
+      QH_CUDA_TRY(cudaMemcpyAsync(hC.data(), B.C, G.n_nodes * 4, cudaMemcpyDeviceToHost, s));
+      QH_CUDA_TRY(cudaMemcpyAsync(blk.data(), G.block_of, G.n_nodes * 4, cudaMemcpyDeviceToHost, s));
+    }
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int32_t v = 0; v < G.n_nodes; ++v) {
+      sol.C[v] = hC[v];
+      sol.spins[v] = blk[v] >= 0 ? ((hC[v] % 2 == 0) ? 1 : -1) : 0;
+    }
+    // cut of the parity partition on the ungauged weights (one pseudo-replica)
+    int8_t* st1 = (int8_t*)ctx->scratch((size_t)std::max(G.n_pad, 1) + 16, S_SIGNS1);
+    double* nv1 = (double*)ctx->scratch((size_t)std::max(G.n_pad, 1) * 8, S_NODEVAL1);
+    double* cut1 = (double*)ctx->scratch((size_t)nb * 8, S_CUT1);
+    int32_t* pidx = (int32_t*)ctx->scratch((size_t)std::max(G.n_nodes, 1) * 4, S_DBG0);
+    if (!st1 || !nv1 || !cut1 || !pidx) {
+      delete sh;
+      return set_err(ctx, QH_ENOMEM, "allocation failed (final cut)");
+    }
+    std::vector<int32_t> hp(G.n_nodes);
+    if (G.n_nodes)
+      QH_CUDA_TRY(cudaMemcpyAsync(hp.data(), G.pad_index, G.n_nodes * 4, cudaMemcpyDeviceToHost, s));
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<int8_t> hs(std::max(G.n_pad, 1), 1);
+    for (int32_t v = 0; v < G.n_nodes; ++v)
+      if (hp[v] >= 0) hs[hp[v]] = sol.spins[v];
+    QH_CUDA_TRY(cudaMemcpyAsync(st1, hs.data(), G.n_pad, cudaMemcpyHostToDevice, s));
+    launch_cut(s, G, 1, st1, G.w, G.sum_w, nv1, cut1, nullptr);
+    QH_CUDA_TRY(cudaMemcpyAsync(sol.best_cut.data(), cut1, nb * 8, cudaMemcpyDeviceToHost, s));
+  } else {
+    if (G.n_nodes)
+      QH_CUDA_TRY(cudaMemcpyAsync(sol.spins.data(), B.spins, G.n_nodes, cudaMemcpyDeviceToHost, s));
+  }
+  QH_CUDA_TRY(cudaEventRecord(ctx->ev[1], s));
+  QH_CUDA_TRY(cudaStreamSynchronize(s));
+  // device copies of the spins / counts for qh_phase
+  sol.d_spins = (int8_t*)nullptr;
+  {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max(G.n_nodes, 1)) != cudaSuccess) {
+      delete sh;
+      return set_err(ctx, QH_ENOMEM, "allocation failed (solution)");
+    }
+    sol.allocs.push_back(p);
+    sol.d_spins = (int8_t*)p;
+    if (cudaMalloc(&p, std::max(G.n_nodes, 1) * 4) != cudaSuccess) {
+      cudaFree(sol.d_spins);
+      delete sh;
+      return set_err(ctx, QH_ENOMEM, "allocation failed (solution)");
+    }
+    sol.allocs.push_back(p);
+    sol.d_C = (int32_t*)p;
+    if (G.n_nodes) {
+      QH_CUDA_TRY(cudaMemcpyAsync(sol.d_spins, sol.spins.data(), G.n_nodes, cudaMemcpyHostToDevice, s));
+      QH_CUDA_TRY(cudaMemcpyAsync(sol.d_C, B.C, G.n_nodes * 4, cudaMemcpyDeviceToDevice, s));
+    }
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  sol.perm.assign(G.h_block_ptr[nb], 0);
+  if (!sol.perm.empty()) {
+    QH_CUDA_TRY(cudaMemcpyAsync(sol.perm.data(), G.perm, sol.perm.size() * 4, cudaMemcpyDeviceToHost, s));
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  float total = 0.f;
+  cudaEventElapsedTime(&total, ctx->ev[0], ctx->ev[1]);
+  sol.solve_ms = total;
+  sol.step_ms = step_ms_total;
+  sol.n_step_launches = launches;
+  sol.spin_updates = spin_updates;
+  *out = sh;
+  return QH_OK;
+}
+
+qh_status qh_solution_block(qh_ctx* h, const qh_solution* sh, int32_t b, int8_t* spins,
+                            double* best_cut, int32_t* best_replica, int32_t* steps_run,
+                            int32_t* iterations) {
+  if (!h || !sh) return QH_EINVAL;
+  Ctx* ctx = &h->c;
+  const Solution& s = sh->s;
+  if (b < 0 || b >= s.n_blocks) return set_err(ctx, QH_EINVAL, "block out of range");
+  if (spins)
+    for (int64_t k = s.block_ptr[b]; k < s.block_ptr[b + 1]; ++k)
+      spins[k - s.block_ptr[b]] = s.spins[s.perm[k]];
+  if (best_cut) *best_cut = s.best_cut[b];
+  if (best_replica) *best_replica = s.replica_base + s.best_r[b];
+  if (steps_run) *steps_run = s.steps_run[b];
+  if (iterations) *iterations = s.iters[b];
+  return QH_OK;
+}
+
+qh_status qh_solution_spins(qh_ctx* h, const qh_solution* sh, int8_t* spins) {
+  if (!h || !sh || !spins) return QH_EINVAL;
+  const Solution& s = sh->s;
+  if (s.n_nodes) memcpy(spins, s.spins.data(), s.n_nodes);
+  return QH_OK;
+}
+
+qh_status qh_solution_cuts(qh_ctx* h, const qh_solution* sh, double* cuts) {
+  if (!h || !sh || !cuts) return QH_EINVAL;
+  const Solution& s = sh->s;
+  memcpy(cuts, s.cuts_first.data(), s.cuts_first.size() * sizeof(double));
+  return QH_OK;
+}
+
+qh_status qh_solution_timing(const qh_solution* sh, double* solve_ms, double* step_ms,
+                             int64_t* n_step_launches, double* spin_updates) {
+  if (!sh) return QH_EINVAL;
+  const Solution& s = sh->s;
+  if (solve_ms) *solve_ms = s.solve_ms;
+  if (step_ms) *step_ms = s.step_ms;
+  if (n_step_launches) *n_step_launches = s.n_step_launches;
+  if (spin_updates) *spin_updates = s.spin_updates;
+  return QH_OK;
+}
+
+void qh_solution_free(qh_solution* sh) {
+  if (!sh) return;
+  for (void* p : sh->s.allocs) cudaFree(p);
+  delete sh;
+}
+
+qh_status qh_phase(qh_ctx* h, const qh_graph* gh, const qh_solution* sh, int8_t* hap1, int8_t* hap2,
+                   int32_t* block_id, int32_t on_device) {
+  if (!h) return QH_EINVAL;
+  Ctx* ctx = &h->c;
+  ctx->err.clear();
+  if (!gh || !sh || !hap1 || !hap2 || !block_id) return set_err(ctx, QH_EINVAL, "NULL argument");
+  const Graph& g = gh->g;
+  const Solution& sol = sh->s;
+  if (sol.n_nodes != g.n_nodes || sol.mode != g.mode)
+    return set_err(ctx, QH_EINVAL, "solution does not belong to this graph");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = ctx->stream;
+  const int32_t n = g.n_snps;
+  int8_t *d1 = hap1, *d2 = hap2;
+  int32_t* db = block_id;
+  if (!on_device) {
+    d1 = (int8_t*)ctx->scratch(std::max(n, 1), S_DBG0);
+    d2 = (int8_t*)ctx->scratch(std::max(n, 1), S_DBG1);
+    db = (int32_t*)ctx->scratch((size_t)std::max(n, 1) * 4, S_DBG2);
+    if (!d1 || !d2 || !db) return set_err(ctx, QH_ENOMEM, "allocation failed (phase)");
+  }
+  if (g.mode == QH_MODE_READ)
+    launch_vote(s, g, sol.d_spins, d1, d2, db);
+  else
+    launch_parity(s, g, sol.d_C, d1, d2, db);
+  QH_CUDA_TRY(cudaGetLastError());
+  if (!on_device && n > 0) {
+    QH_CUDA_TRY(cudaMemcpyAsync(hap1, d1, n, cudaMemcpyDeviceToHost, s));
+    QH_CUDA_TRY(cudaMemcpyAsync(hap2, d2, n, cudaMemcpyDeviceToHost, s));
+    QH_CUDA_TRY(cudaMemcpyAsync(block_id, db, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+  }
+  QH_CUDA_TRY(cudaStreamSynchronize(s));
+  return QH_OK;
+}
+
+// ------------------------------------------------------------------ test hooks
+qh_status qh_debug_layout(qh_ctx* h, const qh_graph* gh, int32_t* n_pad, int32_t* padded_index,
+                          double* c0_default) {
+  if (!h || !gh) return QH_EINVAL;
+  Ctx* ctx = &h->c;
+  const Graph& g = gh->g;
+  if (n_pad) *n_pad = g.n_pad;
+  if (padded_index && g.n_nodes) {
+    QH_CUDA_TRY(cudaMemcpyAsync(padded_index, g.pad_index, g.n_nodes * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    QH_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  }
+  if (c0_default)
+    for (int32_t b = 0; b < g.n_blocks; ++b) c0_default[b] = g.h_c0[b];
+  return QH_OK;
+}
+
+static qh_status debug_common(Ctx* ctx, const Graph& g, int precision, int32_t R, StepArgs& a,
+                              const double* c0_per_block, int32_t steps) {
+  if (precision != QH_PREC_FP32 && precision != QH_PREC_BF16) return set_err(ctx, QH_EINVAL, "bad precision");
+  if (R < 1) return set_err(ctx, QH_EINVAL, "R must be >= 1");
+  if (precision == QH_PREC_BF16 && !tc_plan_ok(R, pick_plan(R)))
+    return set_err(ctx, QH_EINVAL, "BF16 precision needs R to be a multiple of 64");
+  const int32_t nb = std::max(g.n_blocks, 1);
+  std::vector<float> c0(nb);
+  std::vector<int32_t> sb(nb, steps);
+  for (int32_t b = 0; b < g.n_blocks; ++b) c0[b] = (float)(c0_per_block ? c0_per_block[b] : g.h_c0[b]);
+  float* dc0 = (float*)ctx->scratch(nb * 4, S_C0);
+  int32_t* dsb = (int32_t*)ctx->scratch(nb * 4, S_STEPSB);
+  if (!dc0 || !dsb) return set_err(ctx, QH_ENOMEM, "allocation failed (debug)");
+  QH_CUDA_TRY(cudaMemcpyAsync(dc0, c0.data(), nb * 4, cudaMemcpyHostToDevice, ctx->stream));
+  QH_CUDA_TRY(cudaMemcpyAsync(dsb, sb.data(), nb * 4, cudaMemcpyHostToDevice, ctx->stream));
+  QH_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream));
+  a = StepArgs{};
+  a.rt = g.rt;
+  a.tile_col = g.tile_col;
+  a.tile_f32 = g.tile_f32;
+  a.c0 = dc0;
+  a.active = nullptr;
+  a.steps_b = dsb;
+  a.n_pad = g.n_pad;
+  a.R = R;
+  a.err = ctx->d_err;
+  return QH_OK;
+}
+
+qh_status qh_debug_matvec(qh_ctx* h, const qh_graph* gh, int32_t precision, int32_t R, const float* x,
+                          float* z) {
+  if (!h || !gh || !x || !z) return QH_EINVAL;
+  Ctx* ctx = &h->c;
+  const Graph& g = gh->g;
+  cudaSetDevice(ctx->device);
+  StepArgs a;
+  qh_status st = debug_common(ctx, g, precision, R, a, nullptr, 1 << 30);
+  if (st) return st;
+  a.z_out = z;
+  a.t = 0;
+  a.a0 = 1.0;
+  QH_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)R * g.n_pad * 4, ctx->stream));
+  if (precision == QH_PREC_FP32) {
+    a.xin = x;
+    a.xout = nullptr;
+    launch_step_f32(ctx->stream, g, a);
+  } else {
+    __nv_bfloat16* xh = (__nv_bfloat16*)ctx->scratch((size_t)R * g.n_pad * 2, S_XH0);
+    if (!xh) return set_err(ctx, QH_ENOMEM, "allocation failed (debug)");
+    launch_f32_to_bf16(ctx->stream, x, xh, (int64_t)R * g.n_pad);
+    st = launch_step_tc(ctx, g, a, xh, pick_plan(R));
+    if (st) return st;
+  }
+  QH_CUDA_TRY(cudaGetLastError());
+  return check_err_word(ctx);
+}
+
+qh_status qh_debug_steps(qh_ctx* h, const qh_graph* gh, int32_t precision, int32_t R, float* x,
+                         float* y, int32_t t0, int32_t nsteps, int32_t steps, double dt, double a0,
+                         const double* c0_per_block) {
+  if (!h || !gh || !x || !y || nsteps < 0 || steps < 1 || t0 < 0) return QH_EINVAL;
+  Ctx* ctx = &h->c;
+  const Graph& g = gh->g;
+  cudaSetDevice(ctx->device);
+  StepArgs a;
+  qh_status st = debug_common(ctx, g, precision, R, a, c0_per_block, steps);
+  if (st) return st;
+  a.x = x;
+  a.y = y;
+  a.dt = (float)dt;
+  a.a0 = a0;
+  a.dta0 = (float)(dt * a0);
+  const size_t NS = (size_t)R * g.n_pad;
+  cudaStream_t s = ctx->stream;
+  if (precision == QH_PREC_FP32) {
+    float* x1 = (float*)ctx->scratch(NS * 4, S_X1);
+    if (!x1) return set_err(ctx, QH_ENOMEM, "allocation failed (debug)");
+    QH_CUDA_TRY(cudaMemcpyAsync(x1, x, NS * 4, cudaMemcpyDeviceToDevice, s));
+    for (int32_t k = 0; k < nsteps; ++k) {
+      a.t = t0 + k;
+      a.xin = (k % 2 == 0) ? x : x1;
+      a.xout = (k % 2 == 0) ? x1 : x;
+      launch_step_f32(s, g, a);
+    }
+    if (nsteps % 2 == 1) QH_CUDA_TRY(cudaMemcpyAsync(x, x1, NS * 4, cudaMemcpyDeviceToDevice, s));
+  } else {
+    __nv_bfloat16* xh0 = (__nv_bfloat16*)ctx->scratch(NS * 2, S_XH0);
+    __nv_bfloat16* xh1 = (__nv_bfloat16*)ctx->scratch(NS * 2, S_XH1);
+    if (!xh0 || !xh1) return set_err(ctx, QH_ENOMEM, "allocation failed (debug)");
+    launch_f32_to_bf16(s, x, xh0, (int64_t)NS);
+    for (int32_t k = 0; k < nsteps; ++k) {
+      a.t = t0 + k;
+      a.xh_out = (k % 2 == 0) ? xh1 : xh0;
+      st = launch_step_tc(ctx, g, a, (k % 2 == 0) ? xh0 : xh1, pick_plan(R));
+      if (st) return st;
+    }
+  }
+  QH_CUDA_TRY(cudaGetLastError());
+  return check_err_word(ctx);
+}
+
+}  // extern "C"

@@ -1,0 +1,469 @@
+// SIMT kernels of the bSB solve and the phasing step:
+//  - initial state (SplitMix64 draws), FP32 tiled J x X step (the plain FP32
+//    GPU bSB), exact cut evaluation, replica selection, early stop,
+//  - SNP refinement (flip counter, sign inversion), read voting, parity swap.
+#include <algorithm>
+
+#include "qh_internal.cuh"
+#include "util.cuh"
+
+namespace qh {
+
+namespace {
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------------------ init
+__global__ void k_init_state(const RowTile* __restrict__ rt, const int32_t* __restrict__ pad_node,
+                             const int32_t* __restrict__ local, int32_t n_pad, int32_t R,
+                             int32_t replica_base, uint64_t seed, int32_t iter, float* x, float* y,
+                             __nv_bfloat16* xh, const int32_t* __restrict__ active) {
+  int32_t col = blockIdx.x * blockDim.x + threadIdx.x;
+  int32_t r = blockIdx.y;
+  if (col >= n_pad || r >= R) return;
+  int32_t b = rt[col / TILE].block;
+  if (active != nullptr && !active[b]) return;
+  int32_t v = pad_node[col];
+  float xv = 0.f, yv = 0.f;
+  if (v >= 0) {
+    uint64_t key = init_key(seed, b, iter);
+    xv = init_draw(key, replica_base + r, local[v], 0);
+    yv = init_draw(key, replica_base + r, local[v], 1);
+  }
+  size_t idx = (size_t)r * n_pad + col;
+  x[idx] = xv;
+  y[idx] = yv;
+  if (xh != nullptr) xh[idx] = __float2bfloat16_rn(xv);
+}
+
+__global__ void k_f32_to_bf16(const float* __restrict__ x, __nv_bfloat16* xh, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) xh[i] = __float2bfloat16_rn(x[i]);
+}
+
+// ------------------------------------------------------------------ FP32 step
+constexpr int F_RT = 64;   // replicas per CTA
+constexpr int F_KC = 32;   // K chunk staged in shared memory
+
+// bSB update of one element (same operation order as the tensor-core path).
+__device__ __forceinline__ void bsb_update(float z, float& x, float& y, float dt, float coef_x,
+                                           float dta0, float c0) {
+  y = y + dt * (coef_x * x + c0 * z);
+  x = x + dta0 * y;
+  if (fabsf(x) > 1.f) {
+    x = x > 0.f ? 1.f : -1.f;
+    y = 0.f;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_step_f32(StepArgs a) {
+  const int32_t t = a.t;
+  const double a0d = a.a0;
+  __shared__ __align__(16) float Js[F_KC][TILE + 4];
+  __shared__ __align__(16) float Xs[F_KC][F_RT + 4];
+  const RowTile rt = a.rt[blockIdx.x];
+  const int tid = threadIdx.x, lane = tid & 31, wg = tid >> 5;
+  const int32_t r0 = blockIdx.y * F_RT;
+  const int32_t sb = a.steps_b[rt.block];
+  const bool live = (a.active == nullptr || a.active[rt.block]) && t < sb;
+  if (!live) {
+    if (a.z_out == nullptr && a.xout != a.xin) {  // carry a frozen block to the next buffer
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 8; ++j) {
+          int32_t row = lane + 32 * i, r = r0 + wg * 8 + j;
+          if (row < rt.valid && r < a.R) {
+            size_t idx = (size_t)r * a.n_pad + rt.row0 + row;
+            a.xout[idx] = a.xin[idx];
+          }
+        }
+    }
+    return;
+  }
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  for (int32_t e = 0; e < rt.n_hi; ++e) {
+    const float* Jt = a.tile_f32 + (size_t)(rt.f32_begin + e) * (TILE * TILE);
+    const int32_t cbase = a.tile_col[rt.tile_begin + e] * TILE;
+    for (int kc = 0; kc < TILE; kc += F_KC) {
+      for (int idx = tid; idx < TILE * (F_KC / 4); idx += 256) {
+        int row = idx / (F_KC / 4), k4 = idx % (F_KC / 4);
+        float4 v = *reinterpret_cast<const float4*>(Jt + (size_t)row * TILE + kc + k4 * 4);
+        Js[k4 * 4 + 0][row] = v.x;
+        Js[k4 * 4 + 1][row] = v.y;
+        Js[k4 * 4 + 2][row] = v.z;
+        Js[k4 * 4 + 3][row] = v.w;
+      }
+      for (int idx = tid; idx < F_RT * (F_KC / 4); idx += 256) {
+        int rep = idx / (F_KC / 4), k4 = idx % (F_KC / 4);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r0 + rep < a.R)
+          v = *reinterpret_cast<const float4*>(a.xin + (size_t)(r0 + rep) * a.n_pad + cbase + kc +
+                                               k4 * 4);
+        Xs[k4 * 4 + 0][rep] = v.x;
+        Xs[k4 * 4 + 1][rep] = v.y;
+        Xs[k4 * 4 + 2][rep] = v.z;
+        Xs[k4 * 4 + 3][rep] = v.w;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int k = 0; k < F_KC; ++k) {
+        float av[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = Js[k][lane + 32 * i];
+        float4 b0 = *reinterpret_cast<const float4*>(&Xs[k][wg * 8]);
+        float4 b1 = *reinterpret_cast<const float4*>(&Xs[k][wg * 8 + 4]);
+        float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+  const double at = a0d * (double)t / (double)sb;
+  const float coef_x = (float)(-(a0d - at));
+  const float c0 = a.c0[rt.block];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      int32_t row = lane + 32 * i, r = r0 + wg * 8 + j;
+      if (row >= rt.valid || r >= a.R) continue;
+      size_t idx = (size_t)r * a.n_pad + rt.row0 + row;
+      if (a.z_out != nullptr) {
+        a.z_out[idx] = acc[i][j];
+        continue;
+      }
+      float x = a.xin[idx], y = a.y[idx];
+      bsb_update(acc[i][j], x, y, a.dt, coef_x, a.dta0, c0);
+      a.xout[idx] = x;
+      a.y[idx] = y;
+    }
+}
+
+// ------------------------------------------------------------------ signs / cut
+// signs_t[col][r] = sgn(x[r][col]) with sgn(0) = +1, via a 32 x 32 transpose tile.
+__global__ void k_signs_t(const float* __restrict__ x, int32_t n_pad, int32_t R, int8_t* st) {
+  __shared__ int8_t tile[32][33];
+  int32_t c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int k = ty; k < 32; k += 8) {
+    int32_t r = r0 + k, c = c0 + tx;
+    tile[k][tx] = (r < R && c < n_pad) ? (x[(size_t)r * n_pad + c] >= 0.f ? 1 : -1) : 1;
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    int32_t c = c0 + k, r = r0 + tx;
+    if (c < n_pad && r < R) st[(size_t)c * R + r] = tile[tx][k];
+  }
+}
+
+// Warp per vertex a: node_val[pad(a)][r] = s_a * sum_b w_ab s_b (FP64, exact for integers).
+__global__ void k_cut_nodes(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            const double* __restrict__ w, const int32_t* __restrict__ block_of,
+                            const int32_t* __restrict__ pad_index, const int8_t* __restrict__ st,
+                            int32_t R, double* node_val, const int32_t* __restrict__ active) {
+  int32_t a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (a >= n) return;
+  int32_t b = block_of[a];
+  if (b < 0 || (active != nullptr && !active[b])) return;
+  int32_t pa = pad_index[a];
+  for (int32_t r = lane; r < R; r += 32) {
+    double acc = 0.0;
+    for (int64_t e = rp[a]; e < rp[a + 1]; ++e) {
+      double we = w[e];
+      if (we == 0.0) continue;  // zero edges may reach vertices outside every block
+      acc += we * (double)st[(size_t)pad_index[col[e]] * R + r];
+    }
+    node_val[(size_t)pa * R + r] = (double)st[(size_t)pa * R + r] * acc;
+  }
+}
+
+// Thread per (block, replica): cut = (sum_w - s^T W s) / 4, summed over the block's
+// vertices in padded order (fixed order: deterministic).
+__global__ void k_cut_reduce(int32_t nb, const int32_t* __restrict__ pad_off,
+                             const int64_t* __restrict__ block_ptr, int32_t R,
+                             const double* __restrict__ node_val, const double* __restrict__ sum_w,
+                             double* cuts, const int32_t* __restrict__ active) {
+  int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  int32_t b = blockIdx.y;
+  if (r >= R || b >= nb) return;
+  if (active != nullptr && !active[b]) return;
+  int32_t p0 = pad_off[b];
+  int32_t sz = (int32_t)(block_ptr[b + 1] - block_ptr[b]);
+  double s = 0.0;
+  for (int32_t p = 0; p < sz; ++p) s += node_val[(size_t)(p0 + p) * R + r];
+  cuts[(size_t)b * R + r] = 0.25 * (sum_w[b] - s);
+}
+
+__global__ void k_pick_best(int32_t nb, int32_t R, const double* __restrict__ cuts, int32_t* best_r,
+                            double* best_cut, const int32_t* __restrict__ active) {
+  int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb || (active != nullptr && !active[b])) return;
+  double best = cuts[(size_t)b * R];
+  int32_t br = 0;
+  for (int32_t r = 1; r < R; ++r) {
+    double c = cuts[(size_t)b * R + r];
+    if (c > best) {
+      best = c;
+      br = r;
+    }
+  }
+  best_r[b] = br;
+  best_cut[b] = best;
+}
+
+__global__ void k_early_stop(int32_t nb, const double* __restrict__ best_cut, double* best_seen,
+                             int32_t* stall, int32_t* active, int32_t* steps_run, int32_t patience,
+                             int32_t t_done) {
+  int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb || !active[b]) return;
+  if (best_cut[b] > best_seen[b]) {
+    best_seen[b] = best_cut[b];
+    stall[b] = 0;
+  } else if (++stall[b] >= patience) {
+    active[b] = 0;
+    steps_run[b] = t_done;
+  }
+}
+
+__global__ void k_extract_spins(int32_t n, const int32_t* __restrict__ block_of,
+                                const int32_t* __restrict__ pad_index, const int8_t* __restrict__ st,
+                                int32_t R, const int32_t* __restrict__ best_r, int8_t* spins,
+                                const int32_t* __restrict__ active) {
+  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  int32_t b = block_of[a];
+  if (b < 0) {
+    spins[a] = 0;
+    return;
+  }
+  if (active != nullptr && !active[b]) return;
+  spins[a] = st[(size_t)pad_index[a] * R + best_r[b]];
+}
+
+// ------------------------------------------------------------------ block sums
+__global__ void k_node_sums(int32_t n, const int64_t* __restrict__ rp, const double* __restrict__ w,
+                            double* sw, double* sj2) {
+  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  double s = 0.0, q = 0.0;
+  for (int64_t e = rp[a]; e < rp[a + 1]; ++e) {
+    s += w[e];
+    q += w[e] * w[e];
+  }
+  sw[a] = s;
+  sj2[a] = q;
+}
+
+__global__ void k_block_sums(int32_t nb, const int64_t* __restrict__ block_ptr,
+                             const int32_t* __restrict__ perm, const double* __restrict__ sw,
+                             const double* __restrict__ sj2, double* sum_w, double* sum_j2) {
+  int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double s = 0.0, q = 0.0;
+  for (int64_t k = block_ptr[b]; k < block_ptr[b + 1]; ++k) {
+    s += sw[perm[k]];
+    q += sj2[perm[k]];
+  }
+  sum_w[b] = s;
+  sum_j2[b] = q;
+}
+
+// ------------------------------------------------------------------ SNP refinement
+// Per active block: stop if the best cut is <= 0 or all spins agree; otherwise
+// add 1 to C on the smaller subset (tie: the subset without the block's lowest
+// vertex).  Thread per block, vertices in ascending order.
+__global__ void k_refine_prepare(int32_t nb, const int64_t* __restrict__ block_ptr,
+                                 const int32_t* __restrict__ perm, const int8_t* __restrict__ spins,
+                                 const double* __restrict__ best_cut, int32_t* active, int32_t* C) {
+  int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb || !active[b]) return;
+  int64_t k0 = block_ptr[b], k1 = block_ptr[b + 1];
+  int64_t npos = 0;
+  for (int64_t k = k0; k < k1; ++k) npos += spins[perm[k]] > 0;
+  int64_t sz = k1 - k0;
+  if (best_cut[b] <= 0.0 || npos == 0 || npos == sz) {
+    active[b] = 0;
+    return;
+  }
+  int8_t small = (2 * npos < sz) ? 1 : (2 * npos > sz) ? -1 : (int8_t)(-spins[perm[k0]]);
+  for (int64_t k = k0; k < k1; ++k)
+    if (spins[perm[k]] == small) C[perm[k]] += 1;
+}
+
+// w'_ab = -w_ab for edges crossing the partition (s_a != s_b) of active blocks.
+__global__ void k_gauge(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                        const int32_t* __restrict__ block_of, const int8_t* __restrict__ spins,
+                        double* w, const int32_t* __restrict__ active) {
+  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  int32_t b = block_of[a];
+  if (b < 0 || !active[b]) return;
+  int8_t sa = spins[a];
+  for (int64_t e = rp[a]; e < rp[a + 1]; ++e)
+    if (spins[col[e]] != sa) w[e] = -w[e];
+}
+
+// ------------------------------------------------------------------ phase
+// Read voting (consistency processing), thread per SNP.
+__global__ void k_vote(int32_t n, const int64_t* __restrict__ cov_ptr, const int32_t* __restrict__ cov_frag,
+                       const int8_t* __restrict__ cov_allele, const int32_t* __restrict__ block_of,
+                       const int8_t* __restrict__ spins, int8_t* hap1, int8_t* hap2,
+                       int32_t* block_id) {
+  int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  int64_t b0 = cov_ptr[j], b1 = cov_ptr[j + 1];
+  int32_t best = -1, bestc = 0;
+  for (int64_t k = b0; k < b1; ++k) {
+    int32_t bk = block_of[cov_frag[k]];
+    if (bk < 0) continue;
+    int32_t c = 0;
+    for (int64_t q = b0; q < b1; ++q) c += block_of[cov_frag[q]] == bk;
+    if (c > bestc || (c == bestc && bk < best)) {
+      bestc = c;
+      best = bk;
+    }
+  }
+  int8_t h = 0;
+  if (best >= 0) {
+    int32_t c1p = 0, c1m = 0, c2p = 0, c2m = 0;
+    for (int64_t k = b0; k < b1; ++k) {
+      int32_t i = cov_frag[k];
+      if (block_of[i] != best) continue;
+      int8_t s = spins[i], al = cov_allele[k];
+      if (s > 0) {
+        if (al > 0) ++c1p; else ++c1m;
+      } else if (s < 0) {
+        if (al > 0) ++c2p; else ++c2m;
+      }
+    }
+    int32_t d1 = c1p - c1m, d2 = c2p - c2m;
+    if (!(c1p + c1m + c2p + c2m == 0 || (d1 == 0 && d2 == 0))) {
+      if ((d1 > 0 && d2 < 0) || (d1 < 0 && d2 > 0)) {
+        h = d1 > 0 ? 1 : -1;
+      } else {
+        int32_t a1 = d1 < 0 ? -d1 : d1, a2 = d2 < 0 ? -d2 : d2;
+        if (a1 >= a2)
+          h = d1 > 0 ? 1 : -1;
+        else
+          h = d2 > 0 ? -1 : 1;
+      }
+    }
+  }
+  hap1[j] = h;
+  hap2[j] = (int8_t)(-h);
+  block_id[j] = h != 0 ? best : -1;
+}
+
+__global__ void k_parity(int32_t n, const int32_t* __restrict__ block_of, const int32_t* __restrict__ C,
+                         int8_t* hap1, int8_t* hap2, int32_t* block_id) {
+  int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  int32_t b = block_of[u];
+  int8_t h = b >= 0 ? ((C[u] % 2 == 0) ? 1 : -1) : 0;
+  hap1[u] = h;
+  hap2[u] = (int8_t)(-h);
+  block_id[u] = b;
+}
+
+}  // namespace
+
+void launch_init_state(cudaStream_t s, const Graph& g, int32_t R, int32_t replica_base,
+                       uint64_t seed, int32_t iter, float* x, float* y, __nv_bfloat16* xh,
+                       const int32_t* active) {
+  if (g.n_pad == 0 || R == 0) return;
+  dim3 grid(nblk(g.n_pad), R);
+  k_init_state<<<grid, 256, 0, s>>>(g.rt, g.pad_node, g.local, g.n_pad, R, replica_base, seed, iter,
+                                    x, y, xh, active);
+}
+
+void launch_f32_to_bf16(cudaStream_t s, const float* x, __nv_bfloat16* xh, int64_t n) {
+  if (n > 0) k_f32_to_bf16<<<nblk(n), 256, 0, s>>>(x, xh, n);
+}
+
+void launch_step_f32(cudaStream_t s, const Graph& g, const StepArgs& a) {
+  if (g.n_row_tiles == 0) return;
+  dim3 grid(g.n_row_tiles, (a.R + F_RT - 1) / F_RT);
+  k_step_f32<<<grid, 256, 0, s>>>(a);
+}
+
+void launch_signs(cudaStream_t s, const Graph& g, int32_t R, const float* x, int8_t* signs_t) {
+  if (g.n_pad == 0) return;
+  dim3 grid((g.n_pad + 31) / 32, (R + 31) / 32);
+  k_signs_t<<<grid, 256, 0, s>>>(x, g.n_pad, R, signs_t);
+}
+
+void launch_cut(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t, const double* w,
+                const double* sum_w, double* node_val, double* cuts, const int32_t* active) {
+  if (g.n_blocks == 0) return;
+  k_cut_nodes<<<nblk((int64_t)g.n_nodes * 32), 256, 0, s>>>(g.n_nodes, g.row_ptr, g.col, w,
+                                                             g.block_of, g.pad_index, signs_t, R,
+                                                             node_val, active);
+  dim3 grid(nblk(R, 128), g.n_blocks);
+  k_cut_reduce<<<grid, 128, 0, s>>>(g.n_blocks, g.pad_off, g.block_ptr, R, node_val, sum_w, cuts,
+                                    active);
+}
+
+void launch_pick_best(cudaStream_t s, int32_t n_blocks, int32_t R, const double* cuts,
+                      int32_t* best_r, double* best_cut, const int32_t* active) {
+  if (n_blocks > 0) k_pick_best<<<nblk(n_blocks), 256, 0, s>>>(n_blocks, R, cuts, best_r, best_cut, active);
+}
+
+void launch_early_stop(cudaStream_t s, int32_t n_blocks, const double* best_cut, double* best_seen,
+                       int32_t* stall, int32_t* active, int32_t* steps_run, int32_t patience,
+                       int32_t t_done) {
+  if (n_blocks > 0)
+    k_early_stop<<<nblk(n_blocks), 256, 0, s>>>(n_blocks, best_cut, best_seen, stall, active,
+                                               steps_run, patience, t_done);
+}
+
+void launch_extract_spins(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t,
+                          const int32_t* best_r, int8_t* spins, const int32_t* active) {
+  if (g.n_nodes > 0)
+    k_extract_spins<<<nblk(g.n_nodes), 256, 0, s>>>(g.n_nodes, g.block_of, g.pad_index, signs_t, R,
+                                                    best_r, spins, active);
+}
+
+void launch_block_sums(cudaStream_t s, const Graph& g, const double* w, double* sum_w,
+                       double* sum_j2, double* node_tmp) {
+  if (g.n_blocks == 0) return;
+  k_node_sums<<<nblk(g.n_nodes), 256, 0, s>>>(g.n_nodes, g.row_ptr, w, node_tmp,
+                                              node_tmp + g.n_nodes);
+  k_block_sums<<<nblk(g.n_blocks), 256, 0, s>>>(g.n_blocks, g.block_ptr, g.perm, node_tmp,
+                                                node_tmp + g.n_nodes, sum_w, sum_j2);
+}
+
+void launch_refine_prepare(cudaStream_t s, const Graph& g, const int8_t* spins,
+                           const double* best_cut, int32_t* active, int32_t* C) {
+  if (g.n_blocks > 0)
+    k_refine_prepare<<<nblk(g.n_blocks, 64), 64, 0, s>>>(g.n_blocks, g.block_ptr, g.perm, spins,
+                                                        best_cut, active, C);
+}
+
+void launch_gauge(cudaStream_t s, const Graph& g, const int8_t* spins, double* w,
+                  const int32_t* active) {
+  if (g.n_nodes > 0)
+    k_gauge<<<nblk(g.n_nodes), 256, 0, s>>>(g.n_nodes, g.row_ptr, g.col, g.block_of, spins, w,
+                                            active);
+}
+
+void launch_vote(cudaStream_t s, const Graph& g, const int8_t* spins, int8_t* hap1, int8_t* hap2,
+                 int32_t* block_id) {
+  if (g.n_snps > 0)
+    k_vote<<<nblk(g.n_snps), 256, 0, s>>>(g.n_snps, g.cov_ptr, g.cov_frag, g.cov_allele,
+                                          g.block_of, spins, hap1, hap2, block_id);
+}
+
+void launch_parity(cudaStream_t s, const Graph& g, const int32_t* C, int8_t* hap1, int8_t* hap2,
+                   int32_t* block_id) {
+  if (g.n_snps > 0)
+    k_parity<<<nblk(g.n_snps), 256, 0, s>>>(g.n_snps, g.block_of, C, hap1, hap2, block_id);
+}
+
+}  // namespace qh

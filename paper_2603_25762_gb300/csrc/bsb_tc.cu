@@ -1,0 +1,347 @@
+// Fused bSB step on the 5th-generation tensor cores (sm_103a): one CTA per
+// (128-row tile of J, BN replicas).  For each nonzero 128 x 128 J tile of its
+// row slab, TMA stages the J tile and the matching X_hat tile (BF16, 128-byte
+// swizzle) into shared memory; one thread issues tcgen05.mma (BF16 x BF16 ->
+// FP32) into a TMEM accumulator; then all four warps read Z = J_hat X_hat back
+// with tcgen05.ld and apply the bSB update of the SB algorithm solution:
+//   y <- y + dt * ( -(a0 - a(t)) x + c0 * Z ),  x <- x + dt * a0 * y,
+//   |x| > 1 => x <- sgn(x), y <- 0,            X_hat_{t+1} <- bf16(x)
+// State x, y stays FP32 in HBM ([R][n_pad], vertex-contiguous, so each warp's
+// accesses are 128-byte coalesced).  Every mbarrier wait is bounded: on expiry
+// the kernel sets ERR_TIMEOUT in the error word and skips its update.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "qh_internal.cuh"
+
+namespace qh {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after 2^31 SM cycles (about one second) and flags it.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int32_t* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1ll << 31)) {
+      atomicOr(err, ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int32_t c0, int32_t c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulate (kind::f16).
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit columns: thread i of the warp receives row
+// (warp quarter base + i), columns col .. col+31.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes (64 BF16), 8-row core groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address (16-byte units)
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused when swizzled)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                    // layout: 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128.
+template <int BN>
+__device__ __forceinline__ constexpr uint32_t idesc_bf16() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(128 >> 4) << 24);
+}
+
+constexpr uint32_t A_BYTES = TILE * 64 * 2;  // one 128 x 64 BF16 K-slice of J
+
+template <int BN, int STAGES>
+struct TcSmem {
+  static constexpr uint32_t B_BYTES = BN * 64 * 2;
+  static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+  static constexpr uint32_t BAR_OFF = STAGES * STAGE;
+  static constexpr uint32_t BYTES = BAR_OFF + 8 * (2 * STAGES + 1) + 16 + 1024;  // + align slack
+};
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(128) k_step_tc(const __grid_constant__ CUtensorMap tmJ,
+                                                 const __grid_constant__ CUtensorMap tmX,
+                                                 StepArgs a) {
+  using L = TcSmem<BN, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES),
+                 accb = smem_u32(bars + 2 * STAGES);
+
+  const RowTile rt = a.rt[blockIdx.x];
+  const int32_t sb = a.steps_b[rt.block];
+  if ((a.active != nullptr && !a.active[rt.block]) || a.t >= sb) return;  // CTA-uniform
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = rt.n_all * 2;  // 64-wide K slices
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(accb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tmem_slot), (uint32_t)BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0 && nk > 0) {
+    // producer: TMA J slice and X_hat slice per stage
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, a.err)) break;
+      uint8_t* sa = smem + s * L::STAGE;
+      mbar_expect_tx(full0 + 8 * s, L::STAGE);
+      const int e = kb >> 1, half = kb & 1;
+      tma_load_2d(smem_u32(sa), &tmJ, full0 + 8 * s, half * 64, (rt.tile_begin + e) * TILE);
+      tma_load_2d(smem_u32(sa + A_BYTES), &tmX, full0 + 8 * s,
+                  a.tile_col[rt.tile_begin + e] * TILE + half * 64, (int32_t)blockIdx.y * BN);
+    }
+  } else if (warp == 1 && lane == 0 && nk > 0) {
+    // MMA issuer: 4 x (K = 16) per 64-wide slice
+    constexpr uint32_t idesc = idesc_bf16<BN>();
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(full0 + 8 * s, ph, a.err)) break;
+      tc_fence_after();
+      uint8_t* sa = smem + s * L::STAGE;
+      const uint64_t ad = sdesc_sw128(smem_u32(sa));
+      const uint64_t bd = sdesc_sw128(smem_u32(sa + A_BYTES));
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        mma_bf16(tmem, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc,
+                 (kb > 0 || k > 0) ? 1u : 0u);
+      mma_commit(empty0 + 8 * s);
+    }
+    mma_commit(accb);
+  }
+  __syncwarp();
+
+  // epilogue: thread <-> accumulator row (TMEM lane), 32 replica columns at a time
+  const bool ok = nk > 0 ? mbar_wait(accb, 0, a.err) : true;
+  tc_fence_after();
+  const int row = warp * 32 + lane;
+  const bool vrow = ok && row < rt.valid;
+  const double at = (double)a.a0 * (double)a.t / (double)sb;
+  const float coef_x = (float)(-((double)a.a0 - at));
+  const float c0 = a.c0[rt.block];
+  const size_t base = (size_t)blockIdx.y * BN * a.n_pad + rt.row0 + row;
+#pragma unroll
+  for (int c = 0; c < BN / 32; ++c) {
+    uint32_t v[32];
+    __syncwarp();  // tcgen05.ld is warp-collective: reconverge after the row guard below
+    if (nk > 0) {
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = 0u;
+    }
+    if (!vrow) continue;
+    const size_t b0 = base + (size_t)(c * 32) * a.n_pad;
+    if (a.z_out != nullptr) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) a.z_out[b0 + (size_t)j * a.n_pad] = __uint_as_float(v[j]);
+      continue;
+    }
+    float xs[32], ys[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      xs[j] = a.x[b0 + (size_t)j * a.n_pad];
+      ys[j] = a.y[b0 + (size_t)j * a.n_pad];
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      float x = xs[j], y = ys[j];
+      y = y + a.dt * (coef_x * x + c0 * __uint_as_float(v[j]));
+      x = x + a.dta0 * y;
+      if (fabsf(x) > 1.f) {
+        x = x > 0.f ? 1.f : -1.f;
+        y = 0.f;
+      }
+      const size_t idx = b0 + (size_t)j * a.n_pad;
+      a.x[idx] = x;
+      a.y[idx] = y;
+      a.xh_out[idx] = __float2bfloat16_rn(x);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, (uint32_t)BN);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2-D BF16 tensor map over a row-major [outer][inner] array, box = 64 x box_rows,
+// 128-byte swizzle (matches sdesc_sw128).
+bool make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer,
+              uint32_t box_rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {64, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN, int STAGES>
+qh_status launch_impl(Ctx* ctx, const Graph& g, const StepArgs& a, const __nv_bfloat16* xh_in) {
+  using L = TcSmem<BN, STAGES>;
+  CUtensorMap mJ, mX;
+  if (!make_map(&mJ, g.tile_bf16, TILE, (uint64_t)g.n_tiles * TILE, TILE) ||
+      !make_map(&mX, xh_in, (uint64_t)g.n_pad, (uint64_t)a.R, BN))
+    return set_err(ctx, QH_ECUDA, "cuTensorMapEncodeTiled failed");
+  dim3 grid(g.n_row_tiles, a.R / BN);
+  k_step_tc<BN, STAGES><<<grid, 128, L::BYTES, ctx->stream>>>(mJ, mX, a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_step_tc launch");
+  return QH_OK;
+}
+
+template <int BN, int STAGES>
+cudaError_t set_attr() {
+  return cudaFuncSetAttribute(k_step_tc<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)TcSmem<BN, STAGES>::BYTES);
+}
+
+}  // namespace
+
+// Once per process and device, outside any stream capture: shared-memory opt-in of
+// every kernel variant and the driver entry point for tensor-map encoding.
+qh_status tc_prepare(Ctx* ctx) {
+  cudaError_t e = set_attr<64, 4>();
+  if (e == cudaSuccess) e = set_attr<128, 3>();
+  if (e == cudaSuccess) e = set_attr<256, 2>();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute(k_step_tc)");
+  if (!get_encode()) return set_err(ctx, QH_ECUDA, "cuTensorMapEncodeTiled entry point not found");
+  return QH_OK;
+}
+
+bool tc_plan_ok(int R, const TcPlan& plan) {
+  if (plan.bn != 64 && plan.bn != 128 && plan.bn != 256) return false;
+  return R > 0 && R % plan.bn == 0;
+}
+
+qh_status launch_step_tc(Ctx* ctx, const Graph& g, const StepArgs& a, const __nv_bfloat16* xh_in,
+                         const TcPlan& plan) {
+  if (g.n_row_tiles == 0) return QH_OK;
+  if (plan.bn == 64) return launch_impl<64, 4>(ctx, g, a, xh_in);
+  if (plan.bn == 128) return launch_impl<128, 3>(ctx, g, a, xh_in);
+  return launch_impl<256, 2>(ctx, g, a, xh_in);
+}
+
+}  // namespace qh

@@ -1,0 +1,860 @@
+// Graph construction for the read-based and SNP-based methods, connected
+// components (phase blocks) and the padded 128 x 128 J tile layout.
+//
+// Read graph (read-based Max-Cut graph construction, Eqs. delta / w_ab): for
+// every pair of fragments whose SNP ranges intersect, walk the shared SNPs;
+// CONFLICT counts opposing alleles, SIGNED sums -M_aj M_bj (W = -M M^T).
+// Integer weights, exact.
+// SNP graph (SNP-based graph construction, Eq. edge_weight_SNP, Pore-C alpha,
+// linkage depth k/10): each SNP row gathers the terms of every fragment that
+// covers it, sorts them by (partner SNP, fragment) in shared memory and sums
+// each edge in fragment order in FP64 (deterministic, no atomics).
+// Components: lock-free union-find hooking the larger root under the smaller,
+// so every root is its component's smallest vertex (blocks are numbered in
+// that order; singletons are dropped).
+#include <algorithm>
+#include <cmath>
+
+#include "qh_internal.cuh"
+#include "util.cuh"
+
+namespace qh {
+
+namespace {
+
+// ------------------------------------------------------------------ validate
+__global__ void k_validate(int32_t m, int32_t n, const int64_t* __restrict__ fp,
+                           const int32_t* __restrict__ snp, const int8_t* __restrict__ allele,
+                           const uint8_t* __restrict__ qual, int check_qual, int32_t* err) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  int64_t b = fp[i], e = fp[i + 1];
+  if (e < b) {
+    atomicOr(err, ERR_INPUT);
+    return;
+  }
+  int32_t prev = -1;
+  for (int64_t k = b; k < e; ++k) {
+    int32_t s = snp[k];
+    int8_t a = allele[k];
+    if (s < 0 || s >= n || s <= prev || (a != 1 && a != -1)) atomicOr(err, ERR_INPUT);
+    if (check_qual) {
+      uint8_t q = qual[k];
+      if (q < 4 || q > 93) atomicOr(err, ERR_QUAL);
+    }
+    prev = s;
+  }
+}
+
+// ------------------------------------------------------------------ coverage (SNP -> fragments)
+__global__ void k_cov_count(int64_t nnz, const int32_t* __restrict__ snp, int32_t* cnt) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < nnz) atomicAdd(&cnt[snp[k]], 1);
+}
+
+__global__ void k_cov_fill(int32_t m, const int64_t* __restrict__ fp, const int32_t* __restrict__ snp,
+                           const int8_t* __restrict__ allele, const int64_t* __restrict__ cov_ptr,
+                           int32_t* cursor, int32_t* cov_frag, int8_t* cov_allele) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  for (int64_t k = fp[i]; k < fp[i + 1]; ++k) {
+    int32_t s = snp[k];
+    int64_t slot = cov_ptr[s] + atomicAdd(&cursor[s], 1);
+    cov_frag[slot] = i;
+    cov_allele[slot] = allele[k];
+  }
+}
+
+// Insertion sort of each SNP's covering list by fragment index (lists are short).
+__global__ void k_cov_sort(int32_t n, const int64_t* __restrict__ cov_ptr, int32_t* cov_frag,
+                           int8_t* cov_allele) {
+  int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int64_t b = cov_ptr[s], e = cov_ptr[s + 1];
+  for (int64_t i = b + 1; i < e; ++i) {
+    int32_t f = cov_frag[i];
+    int8_t a = cov_allele[i];
+    int64_t j = i - 1;
+    while (j >= b && cov_frag[j] > f) {
+      cov_frag[j + 1] = cov_frag[j];
+      cov_allele[j + 1] = cov_allele[j];
+      --j;
+    }
+    cov_frag[j + 1] = f;
+    cov_allele[j + 1] = a;
+  }
+}
+
+// ------------------------------------------------------------------ read graph
+__global__ void k_first_last(int32_t m, const int64_t* __restrict__ fp, const int32_t* __restrict__ snp,
+                             int32_t* first, int32_t* last, uint64_t* keys) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  int64_t b = fp[i], e = fp[i + 1];
+  int32_t f = (e > b) ? snp[b] : INT32_MAX;
+  int32_t l = (e > b) ? snp[e - 1] : -1;
+  first[i] = f;
+  last[i] = l;
+  keys[i] = ((uint64_t)(uint32_t)f << 32) | (uint32_t)i;
+}
+
+__global__ void k_unpack_order(int32_t m, const uint64_t* __restrict__ keys, const int32_t* __restrict__ last,
+                               int32_t* order, int32_t* sfirst, int32_t* slast) {
+  int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= m) return;
+  int32_t i = (int32_t)(keys[p] & 0xffffffffu);
+  order[p] = i;
+  sfirst[p] = (int32_t)(keys[p] >> 32);
+  slast[p] = last[i];
+}
+
+// Exact weight of one fragment pair by walking both sorted SNP lists.
+__device__ __forceinline__ int32_t pair_weight(const int32_t* __restrict__ snp,
+                                               const int8_t* __restrict__ allele, int64_t ab,
+                                               int64_t ae, int64_t bb, int64_t be, int mode) {
+  int32_t w = 0;
+  while (ab < ae && bb < be) {
+    int32_t sa = snp[ab], sb = snp[bb];
+    if (sa < sb) {
+      ++ab;
+    } else if (sa > sb) {
+      ++bb;
+    } else {
+      int prod = (int)allele[ab] * (int)allele[bb];
+      w += (mode == QH_WEIGHT_CONFLICT) ? (prod == -1 ? 1 : 0) : -prod;
+      ++ab;
+      ++bb;
+    }
+  }
+  return w;
+}
+
+// Candidate range of fragment a in first-SNP order: q in [lo, hi) with
+// sfirst[q] <= last_a (upper bound) and running max of slast >= first_a.
+__device__ __forceinline__ void cand_range(int32_t m, const int32_t* sfirst, const int32_t* pmax_last,
+                                           int32_t fa, int32_t la, int32_t* lo, int32_t* hi) {
+  int32_t l = 0, h = m;
+  while (l < h) {
+    int32_t mid = (l + h) >> 1;
+    if (sfirst[mid] <= la) l = mid + 1; else h = mid;
+  }
+  *hi = l;
+  l = 0;
+  h = m;
+  while (l < h) {
+    int32_t mid = (l + h) >> 1;
+    if (pmax_last[mid] >= fa) h = mid; else l = mid + 1;
+  }
+  *lo = l;
+}
+
+// Warp per fragment a: pass 0 counts w != 0 partners, pass 1 writes them in
+// first-SNP order (deterministic positions from warp ballots).
+template <int PASS>
+__global__ void k_read_edges(int32_t m, const int64_t* __restrict__ fp, const int32_t* __restrict__ snp,
+                             const int8_t* __restrict__ allele, const int32_t* __restrict__ first,
+                             const int32_t* __restrict__ last, const int32_t* __restrict__ order,
+                             const int32_t* __restrict__ sfirst, const int32_t* __restrict__ slast,
+                             const int32_t* __restrict__ pmax_last, int mode, int64_t* cnt,
+                             const int64_t* __restrict__ row_ptr, int32_t* col, double* w) {
+  int32_t a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (a >= m) return;
+  int64_t ab = fp[a], ae = fp[a + 1];
+  if (ae == ab) {
+    if (PASS == 0 && lane == 0) cnt[a] = 0;
+    return;
+  }
+  int32_t fa = first[a], la = last[a];
+  int32_t lo, hi;
+  cand_range(m, sfirst, pmax_last, fa, la, &lo, &hi);
+  int64_t count = 0;
+  int64_t out = PASS == 1 ? row_ptr[a] : 0;
+  for (int32_t q0 = lo; q0 < hi; q0 += 32) {
+    int32_t q = q0 + lane;
+    int32_t wv = 0;
+    int32_t b = -1;
+    if (q < hi) {
+      b = order[q];
+      if (b != a && slast[q] >= fa && sfirst[q] <= la)
+        wv = pair_weight(snp, allele, ab, ae, fp[b], fp[b + 1], mode);
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, wv != 0);
+    if (PASS == 1 && wv != 0) {
+      int64_t pos = out + __popc(mask & ((1u << lane) - 1));
+      col[pos] = b;
+      w[pos] = (double)wv;
+    }
+    out += __popc(mask);
+    count += __popc(mask);
+  }
+  if (PASS == 0 && lane == 0) cnt[a] = count;
+}
+
+// ------------------------------------------------------------------ SNP graph
+__global__ void k_llr_table(double* L) {
+  int qa = blockIdx.x, qb = threadIdx.x;
+  if (qa > 93 || qb > 93) return;
+  double ua = 1.0 - exp10(-(double)qa / 10.0);
+  double ub = 1.0 - exp10(-(double)qb / 10.0);
+  double pcis = ua * ub + (1.0 - ua) * (1.0 - ub);
+  double ptrans = ua * (1.0 - ub) + (1.0 - ua) * ub;
+  L[qa * 94 + qb] = log10(pcis / ptrans);
+}
+
+struct SnpRowSmem {
+  uint64_t key[SNP_ROW_CAP];   // (partner SNP << 32) | fragment
+  double val[SNP_ROW_CAP];
+};
+
+// CTA per SNP row u.  PASS 0: count distinct partners; PASS 1: write (v, w_uv).
+template <int PASS>
+__global__ void __launch_bounds__(512) k_snp_rows(
+    int32_t n, const int64_t* __restrict__ fp, const int32_t* __restrict__ snp,
+    const int8_t* __restrict__ allele, const uint8_t* __restrict__ qual,
+    const uint8_t* __restrict__ is_porec, const int64_t* __restrict__ cov_ptr,
+    const int32_t* __restrict__ cov_frag, const double* __restrict__ L, double alpha,
+    int linkage_k, int64_t* cnt, const int64_t* __restrict__ row_ptr, int32_t* col, double* w,
+    int32_t* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SnpRowSmem& sm = *reinterpret_cast<SnpRowSmem*>(smem_raw);
+  __shared__ int32_t s_off[1025];
+  __shared__ int32_t s_total;
+  __shared__ int32_t s_runs[512];
+  for (int32_t u = blockIdx.x; u < n; u += gridDim.x) {
+    int64_t cb = cov_ptr[u], ce = cov_ptr[u + 1];
+    int32_t ncov = (int32_t)(ce - cb);
+    // per covering fragment: number of partners inside the linkage window
+    if (threadIdx.x == 0) s_total = 0;
+    __syncthreads();
+    int32_t base = 0;
+    for (int32_t c0 = 0; c0 < ncov; c0 += 1024) {
+      int32_t cn = min(1024, ncov - c0);
+      for (int32_t c = threadIdx.x; c < cn; c += blockDim.x) {
+        int32_t i = cov_frag[cb + c0 + c];
+        int64_t fb = fp[i], fe = fp[i + 1];
+        int32_t S = (int32_t)(fe - fb);
+        int32_t depth = (int32_t)(((int64_t)linkage_k * (S - 1)) / 10);
+        // position of u inside fragment i (binary search, SNPs ascending)
+        int64_t l = fb, h = fe;
+        while (l < h) {
+          int64_t mid = (l + h) >> 1;
+          if (snp[mid] < u) l = mid + 1; else h = mid;
+        }
+        int32_t p = (int32_t)(l - fb);
+        int32_t lo = max(0, p - depth), hi = min(S - 1, p + depth);
+        s_off[c + 1] = hi - lo;  // partners (window minus u itself)
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        s_off[0] = 0;
+        for (int32_t c = 0; c < cn; ++c) s_off[c + 1] += s_off[c];
+      }
+      __syncthreads();
+      int32_t tot = s_off[cn];
+      if (base + tot > SNP_ROW_CAP) {
+        if (threadIdx.x == 0) atomicOr(err, ERR_ROWCAP);
+        base = SNP_ROW_CAP + 1;
+        __syncthreads();
+        break;
+      }
+      // fill terms: thread per (fragment, partner)
+      for (int32_t t = threadIdx.x; t < tot; t += blockDim.x) {
+        int32_t lo = 0, hi = cn;
+        while (hi - lo > 1) {
+          int32_t mid = (lo + hi) >> 1;
+          if (s_off[mid] <= t) lo = mid; else hi = mid;
+        }
+        int32_t c = lo, k = t - s_off[c];
+        int32_t i = cov_frag[cb + c0 + c];
+        int64_t fb = fp[i], fe = fp[i + 1];
+        int32_t S = (int32_t)(fe - fb);
+        int32_t depth = (int32_t)(((int64_t)linkage_k * (S - 1)) / 10);
+        int64_t l = fb, h = fe;
+        while (l < h) {
+          int64_t mid = (l + h) >> 1;
+          if (snp[mid] < u) l = mid + 1; else h = mid;
+        }
+        int32_t p = (int32_t)(l - fb);
+        int32_t wlo = max(0, p - depth);
+        int32_t pp = wlo + k;
+        if (pp >= p) ++pp;  // skip u itself
+        int64_t eu = fb + p, ev = fb + pp;
+        int32_t v = snp[ev];
+        double lv = L[(int)qual[eu] * 94 + (int)qual[ev]];
+        double sg = ((int)allele[eu] * (int)allele[ev] > 0) ? 1.0 : -1.0;
+        double a = (is_porec != nullptr && is_porec[i]) ? alpha : 1.0;
+        double term = -(a * (sg * lv)) / (double)(S - 1);
+        sm.key[base + t] = ((uint64_t)(uint32_t)v << 32) | (uint32_t)i;
+        sm.val[base + t] = term;
+      }
+      base += tot;
+      __syncthreads();
+    }
+    if (base > SNP_ROW_CAP) {
+      if (PASS == 0 && threadIdx.x == 0) cnt[u] = 0;
+      __syncthreads();
+      continue;
+    }
+    int32_t total = base;
+    int32_t N = 1;
+    while (N < total) N <<= 1;
+    for (int32_t t = total + threadIdx.x; t < N; t += blockDim.x) {
+      sm.key[t] = ~0ull;
+      sm.val[t] = 0.0;
+    }
+    __syncthreads();
+    // bitonic sort of (key, val) by key
+    for (int32_t k = 2; k <= N; k <<= 1) {
+      for (int32_t j = k >> 1; j > 0; j >>= 1) {
+        for (int32_t t = threadIdx.x; t < N; t += blockDim.x) {
+          int32_t l = t ^ j;
+          if (l > t) {
+            uint64_t ka = sm.key[t], kb = sm.key[l];
+            bool up = (t & k) == 0;
+            if ((ka > kb) == up) {
+              sm.key[t] = kb;
+              sm.key[l] = ka;
+              double va = sm.val[t];
+              sm.val[t] = sm.val[l];
+              sm.val[l] = va;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // runs of equal partner: run starts, counted in order
+    int64_t out = PASS == 1 ? row_ptr[u] : 0;
+    int32_t done = 0;
+    for (int32_t t0 = 0; t0 < total; t0 += blockDim.x) {
+      int32_t t = t0 + threadIdx.x;
+      bool start = t < total && (t == 0 || (sm.key[t] >> 32) != (sm.key[t - 1] >> 32));
+      unsigned bal = __ballot_sync(0xffffffffu, start);
+      if ((threadIdx.x & 31) == 0) s_runs[threadIdx.x >> 5] = __popc(bal);
+      __syncthreads();
+      int32_t before = 0, chunk_runs = 0;
+      for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) {
+        if (wi < (int)(threadIdx.x >> 5)) before += s_runs[wi];
+        chunk_runs += s_runs[wi];
+      }
+      before += __popc(bal & ((1u << (threadIdx.x & 31)) - 1));
+      if (PASS == 1 && start) {
+        double acc = 0.0;
+        uint32_t v = (uint32_t)(sm.key[t] >> 32);
+        for (int32_t q = t; q < total && (uint32_t)(sm.key[q] >> 32) == v; ++q) acc += sm.val[q];
+        col[out + done + before] = (int32_t)v;
+        w[out + done + before] = acc;
+      }
+      done += chunk_runs;
+      __syncthreads();
+    }
+    if (PASS == 0 && threadIdx.x == 0) cnt[u] = done;
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ components
+__device__ __forceinline__ int32_t uf_find(int32_t* parent, int32_t x) {
+  while (true) {
+    int32_t p = parent[x];
+    if (p == x) return x;
+    int32_t gp = parent[p];
+    if (gp != p) parent[x] = gp;  // path halving; gp is an ancestor, never larger
+    x = p;
+  }
+}
+
+__global__ void k_uf_init(int32_t n, int32_t* parent) {
+  int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) parent[v] = v;
+}
+
+__global__ void k_uf_hook(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                          const double* __restrict__ w, int32_t* parent) {
+  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  for (int64_t e = rp[a]; e < rp[a + 1]; ++e) {
+    int32_t b = col[e];
+    if (b <= a || w[e] == 0.0) continue;
+    int32_t x = a, y = b;
+    while (true) {
+      x = uf_find(parent, x);
+      y = uf_find(parent, y);
+      if (x == y) break;
+      if (x < y) {
+        int32_t t = x;
+        x = y;
+        y = t;
+      }
+      // x > y: hook root x under y
+      if (atomicCAS(&parent[x], x, y) == x) break;
+    }
+  }
+}
+
+__global__ void k_uf_compress(int32_t n, int32_t* parent, int32_t* label, int32_t* size) {
+  int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  int32_t r = uf_find(parent, v);
+  label[v] = r;
+  atomicAdd(&size[r], 1);
+}
+
+__global__ void k_block_roots(int32_t n, const int32_t* __restrict__ label, const int32_t* __restrict__ size,
+                              int32_t* is_root) {
+  int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) is_root[v] = (label[v] == v && size[v] >= 2) ? 1 : 0;
+}
+
+__global__ void k_block_of(int32_t n, const int32_t* __restrict__ label, const int32_t* __restrict__ size,
+                           const int64_t* __restrict__ root_rank, int32_t* block_of,
+                           uint64_t* keys) {
+  int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  int32_t r = label[v];
+  int32_t b = size[r] >= 2 ? (int32_t)root_rank[r] : -1;
+  block_of[v] = b;
+  keys[v] = b >= 0 ? (((uint64_t)(uint32_t)b << 32) | (uint32_t)v) : ~0ull;
+}
+
+__global__ void k_block_sizes(int32_t n, const int32_t* __restrict__ label, const int32_t* __restrict__ size,
+                              const int64_t* __restrict__ root_rank, int32_t* bsize) {
+  int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n && label[v] == v && size[v] >= 2) bsize[root_rank[v]] = size[v];
+}
+
+__global__ void k_perm_local(int64_t total, const uint64_t* __restrict__ keys,
+                             const int64_t* __restrict__ block_ptr, const int32_t* __restrict__ pad_off,
+                             int32_t* perm, int32_t* local, int32_t* pad_index, int32_t* pad_node) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= total) return;
+  int32_t v = (int32_t)(keys[k] & 0xffffffffu);
+  int32_t b = (int32_t)(keys[k] >> 32);
+  int32_t l = (int32_t)(k - block_ptr[b]);
+  perm[k] = v;
+  local[v] = l;
+  pad_index[v] = pad_off[b] + l;
+  pad_node[pad_off[b] + l] = v;
+}
+
+// ------------------------------------------------------------------ tiles
+__global__ void k_tile_flags(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                             const double* __restrict__ w, const int32_t* __restrict__ block_of,
+                             const int32_t* __restrict__ local, const int64_t* __restrict__ slot_off,
+                             const int32_t* __restrict__ tiles_per_block, int32_t* flags) {
+  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  int32_t b = block_of[a];
+  if (b < 0) return;
+  int32_t T = tiles_per_block[b];
+  int32_t ra = local[a] / TILE;
+  for (int64_t e = rp[a]; e < rp[a + 1]; ++e) {
+    if (w[e] == 0.0) continue;
+    int32_t cb = local[col[e]] / TILE;
+    flags[slot_off[b] + (int64_t)ra * T + cb] = 1;
+  }
+}
+
+}  // namespace
+
+// Tile fill (also used after a refinement sign inversion): J = -w into the
+// FP32 tiles and the BF16 hi (+ lo remainder) tiles.
+__global__ void k_tile_fill(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            const double* __restrict__ w, const int32_t* __restrict__ block_of,
+                            const int32_t* __restrict__ local, const int64_t* __restrict__ slot_off,
+                            const int32_t* __restrict__ tiles_per_block,
+                            const int64_t* __restrict__ slot_tile, const RowTile* __restrict__ rt,
+                            const int32_t* __restrict__ rt_of_block, int has_lo,
+                            __nv_bfloat16* tb, float* tf) {
+  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  int32_t b = block_of[a];
+  if (b < 0) return;
+  int32_t T = tiles_per_block[b];
+  int32_t la = local[a];
+  int32_t ra = la / TILE;
+  const RowTile& r = rt[rt_of_block[b] + ra];
+  for (int64_t e = rp[a]; e < rp[a + 1]; ++e) {
+    double wv = w[e];
+    if (wv == 0.0) continue;
+    int32_t lb = local[col[e]];
+    int64_t slot = slot_off[b] + (int64_t)ra * T + lb / TILE;
+    int64_t h = slot_tile[slot];                  // hi tile id (FP32 tiles)
+    int64_t j = h - slot_tile[slot_off[b] + (int64_t)ra * T];  // index inside the row
+    int64_t off = (int64_t)(la % TILE) * TILE + (lb % TILE);
+    double J = -wv;
+    tf[h * (int64_t)(TILE * TILE) + off] = (float)J;
+    __nv_bfloat16 hi = __double2bfloat16(J);
+    tb[(r.tile_begin + j) * (int64_t)(TILE * TILE) + off] = hi;
+    if (has_lo) {
+      __nv_bfloat16 lo = __double2bfloat16(J - (double)__bfloat162float(hi));
+      tb[(r.tile_begin + r.n_hi + j) * (int64_t)(TILE * TILE) + off] = lo;
+    }
+  }
+}
+
+namespace {
+
+__global__ void k_abs_max(int64_t nnz, const double* __restrict__ w, unsigned long long* out,
+                          int32_t* nonint) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  double v = fabs(w[e]);
+  atomicMax(out, (unsigned long long)__double_as_longlong(v));  // non-negative doubles order as ints
+  if (v != floor(v)) atomicOr(nonint, 1);
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opts* o, Graph* g) {
+  cudaStream_t s = ctx->stream;
+  const int32_t m = f->n_frags, n = f->n_snps;
+  g->mode = o->mode;
+  g->weight_mode = o->weight_mode;
+  g->linkage_k = o->linkage_k;
+  g->porec_alpha = o->porec_alpha;
+  g->n_frags = m;
+  g->n_snps = n;
+  // ---- copy fragments to the device
+  cudaMemcpyKind kind = f->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  int64_t nnz_f = 0;
+  QH_CUDA_TRY(cudaMemcpyAsync(&nnz_f, f->frag_ptr + m, sizeof(int64_t),
+                              f->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+  int64_t fp0 = 0;
+  QH_CUDA_TRY(cudaMemcpyAsync(&fp0, f->frag_ptr, sizeof(int64_t),
+                              f->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+  QH_CUDA_TRY(cudaStreamSynchronize(s));
+  if (fp0 != 0 || nnz_f < 0) return set_err(ctx, QH_EINVAL, "frag_ptr[0] must be 0 and frag_ptr[m] >= 0");
+  g->nnz_frag = nnz_f;
+  g->frag_ptr = (int64_t*)dalloc(*g, sizeof(int64_t) * (m + 1));
+  g->snp = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max<int64_t>(nnz_f, 1));
+  g->allele = (int8_t*)dalloc(*g, std::max<int64_t>(nnz_f, 1));
+  g->qual = (uint8_t*)dalloc(*g, std::max<int64_t>(nnz_f, 1));
+  g->is_porec = (uint8_t*)dalloc(*g, std::max<int32_t>(m, 1));
+  if (!g->frag_ptr || !g->snp || !g->allele || !g->qual || !g->is_porec)
+    return set_err(ctx, QH_ENOMEM, "device allocation failed (fragments)");
+  QH_CUDA_TRY(cudaMemcpyAsync(g->frag_ptr, f->frag_ptr, sizeof(int64_t) * (m + 1), kind, s));
+  if (nnz_f > 0) {
+    QH_CUDA_TRY(cudaMemcpyAsync(g->snp, f->snp, sizeof(int32_t) * nnz_f, kind, s));
+    QH_CUDA_TRY(cudaMemcpyAsync(g->allele, f->allele, nnz_f, kind, s));
+    if (f->qual)
+      QH_CUDA_TRY(cudaMemcpyAsync(g->qual, f->qual, nnz_f, kind, s));
+    else
+      QH_CUDA_TRY(cudaMemsetAsync(g->qual, 30, nnz_f, s));
+  }
+  if (f->is_porec && m > 0)
+    QH_CUDA_TRY(cudaMemcpyAsync(g->is_porec, f->is_porec, m, kind, s));
+  else
+    QH_CUDA_TRY(cudaMemsetAsync(g->is_porec, 0, std::max<int32_t>(m, 1), s));
+  // ---- validate
+  QH_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), s));
+  if (m > 0)
+    k_validate<<<nblk(m), 256, 0, s>>>(m, n, g->frag_ptr, g->snp, g->allele, g->qual,
+                                       o->mode == QH_MODE_SNP && f->qual != nullptr ? 1 : 0,
+                                       ctx->d_err);
+  int32_t herr = 0;
+  QH_CUDA_TRY(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  QH_CUDA_TRY(cudaStreamSynchronize(s));
+  if (herr & ERR_INPUT)
+    return set_err(ctx, QH_EINVAL,
+                   "malformed fragments (SNP out of range, not strictly increasing, or allele not +-1)");
+  if (herr & ERR_QUAL) return set_err(ctx, QH_EINVAL, "Phred quality outside [4, 93]");
+  // ---- SNP -> fragment coverage lists (used by SNP rows and by voting)
+  {
+    int32_t* cnt = (int32_t*)ctx->scratch(sizeof(int32_t) * (n + 1), 0);
+    QH_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), s));
+    if (nnz_f > 0) k_cov_count<<<nblk(nnz_f), 256, 0, s>>>(nnz_f, g->snp, cnt);
+    g->cov_ptr = (int64_t*)dalloc(*g, sizeof(int64_t) * (n + 1));
+    g->cov_frag = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max<int64_t>(nnz_f, 1));
+    g->cov_allele = (int8_t*)dalloc(*g, std::max<int64_t>(nnz_f, 1));
+    if (!g->cov_ptr || !g->cov_frag || !g->cov_allele) return set_err(ctx, QH_ENOMEM, "allocation failed (coverage)");
+    scan_i32_to_i64(s, cnt, g->cov_ptr, n);
+    QH_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), s));
+    if (m > 0)
+      k_cov_fill<<<nblk(m), 256, 0, s>>>(m, g->frag_ptr, g->snp, g->allele, g->cov_ptr, cnt,
+                                         g->cov_frag, g->cov_allele);
+    if (n > 0) k_cov_sort<<<nblk(n), 256, 0, s>>>(n, g->cov_ptr, g->cov_frag, g->cov_allele);
+  }
+  // ---- edges
+  if (o->mode == QH_MODE_READ) {
+    g->n_nodes = m;
+    int64_t cap = next_pow2(std::max<int64_t>(m, 2048));
+    int32_t* first = (int32_t*)ctx->scratch(sizeof(int32_t) * std::max(m, 1), 1);
+    int32_t* last = (int32_t*)ctx->scratch(sizeof(int32_t) * std::max(m, 1), 2);
+    uint64_t* keys = (uint64_t*)ctx->scratch(sizeof(uint64_t) * cap, 3);
+    int32_t* order = (int32_t*)ctx->scratch(sizeof(int32_t) * std::max(m, 1), 4);
+    int32_t* sfirst = (int32_t*)ctx->scratch(sizeof(int32_t) * std::max(m, 1), 5);
+    int32_t* slast = (int32_t*)ctx->scratch(sizeof(int32_t) * std::max(m, 1), 6);
+    int32_t* pmax = (int32_t*)ctx->scratch(sizeof(int32_t) * std::max(m, 1), 7);
+    int64_t* cnt = (int64_t*)ctx->scratch(sizeof(int64_t) * (m + 1), 8);
+    if (!first || !last || !keys || !order || !sfirst || !slast || !pmax || !cnt)
+      return set_err(ctx, QH_ENOMEM, "allocation failed (read graph scratch)");
+    g->row_ptr = (int64_t*)dalloc(*g, sizeof(int64_t) * (m + 1));
+    if (m > 0) {
+      k_first_last<<<nblk(m), 256, 0, s>>>(m, g->frag_ptr, g->snp, first, last, keys);
+      sort_u64(s, keys, m, cap);
+      k_unpack_order<<<nblk(m), 256, 0, s>>>(m, keys, last, order, sfirst, slast);
+      scan_max_i32(s, slast, pmax, m);
+      k_read_edges<0><<<nblk((int64_t)m * 32), 256, 0, s>>>(
+          m, g->frag_ptr, g->snp, g->allele, first, last, order, sfirst, slast, pmax,
+          o->weight_mode, cnt, nullptr, nullptr, nullptr);
+    }
+    scan_i64(s, cnt, g->row_ptr, m);
+    QH_CUDA_TRY(cudaMemcpyAsync(&g->nnz, g->row_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+    g->col = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max<int64_t>(g->nnz, 1));
+    g->w = (double*)dalloc(*g, sizeof(double) * std::max<int64_t>(g->nnz, 1));
+    if (!g->row_ptr || !g->col || !g->w) return set_err(ctx, QH_ENOMEM, "allocation failed (edges)");
+    if (m > 0 && g->nnz > 0)
+      k_read_edges<1><<<nblk((int64_t)m * 32), 256, 0, s>>>(
+          m, g->frag_ptr, g->snp, g->allele, first, last, order, sfirst, slast, pmax,
+          o->weight_mode, nullptr, g->row_ptr, g->col, g->w);
+  } else {
+    g->n_nodes = n;
+    double* L = (double*)ctx->scratch(sizeof(double) * 94 * 94, 1);
+    int64_t* cnt = (int64_t*)ctx->scratch(sizeof(int64_t) * (n + 1), 2);
+    if (!L || !cnt) return set_err(ctx, QH_ENOMEM, "allocation failed (SNP graph scratch)");
+    k_llr_table<<<94, 94, 0, s>>>(L);
+    QH_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), s));
+    size_t smem = sizeof(SnpRowSmem);
+    QH_CUDA_TRY(cudaFuncSetAttribute(k_snp_rows<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    QH_CUDA_TRY(cudaFuncSetAttribute(k_snp_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    unsigned grid = (unsigned)std::max(1, std::min(n, ctx->n_sm * 4));
+    g->row_ptr = (int64_t*)dalloc(*g, sizeof(int64_t) * (n + 1));
+    if (!g->row_ptr) return set_err(ctx, QH_ENOMEM, "allocation failed (edges)");
+    if (n > 0)
+      k_snp_rows<0><<<grid, 512, smem, s>>>(n, g->frag_ptr, g->snp, g->allele, g->qual,
+                                           g->is_porec, g->cov_ptr, g->cov_frag, L,
+                                           o->porec_alpha, o->linkage_k, cnt, nullptr, nullptr,
+                                           nullptr, ctx->d_err);
+    scan_i64(s, cnt, g->row_ptr, n);
+    QH_CUDA_TRY(cudaMemcpyAsync(&g->nnz, g->row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    QH_CUDA_TRY(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+    if (herr & ERR_ROWCAP)
+      return set_err(ctx, QH_EUNSUPPORTED, "an SNP row gathers more than 8192 fragment terms");
+    g->col = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max<int64_t>(g->nnz, 1));
+    g->w = (double*)dalloc(*g, sizeof(double) * std::max<int64_t>(g->nnz, 1));
+    if (!g->col || !g->w) return set_err(ctx, QH_ENOMEM, "allocation failed (edges)");
+    if (n > 0 && g->nnz > 0)
+      k_snp_rows<1><<<grid, 512, smem, s>>>(n, g->frag_ptr, g->snp, g->allele, g->qual,
+                                           g->is_porec, g->cov_ptr, g->cov_frag, L,
+                                           o->porec_alpha, o->linkage_k, nullptr, g->row_ptr,
+                                           g->col, g->w, ctx->d_err);
+  }
+  const int32_t N = g->n_nodes;
+  // ---- weight range: integer weights up to 256 are exact in one BF16 operand
+  {
+    unsigned long long* amax = (unsigned long long*)ctx->scratch(16, 9);
+    int32_t* nonint = (int32_t*)(amax + 1);
+    QH_CUDA_TRY(cudaMemsetAsync(amax, 0, 16, s));
+    if (g->nnz > 0) k_abs_max<<<nblk(g->nnz), 256, 0, s>>>(g->nnz, g->w, amax, nonint);
+    unsigned long long hv[2] = {0, 0};
+    QH_CUDA_TRY(cudaMemcpyAsync(hv, amax, 16, cudaMemcpyDeviceToHost, s));
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+    double mx;
+    memcpy(&mx, &hv[0], sizeof(double));
+    g->max_abs_w = mx;
+    g->integer_weights = ((int32_t)hv[1] == 0);
+    g->has_lo = !(g->integer_weights && mx <= 256.0);
+  }
+  // ---- components
+  int32_t* parent = (int32_t*)ctx->scratch(sizeof(int32_t) * std::max(N, 1), 10);
+  int32_t* label = (int32_t*)ctx->scratch(sizeof(int32_t) * std::max(N, 1), 11);
+  int32_t* csize = (int32_t*)ctx->scratch(sizeof(int32_t) * std::max(N, 1), 12);
+  int32_t* isroot = (int32_t*)ctx->scratch(sizeof(int32_t) * std::max(N, 1), 13);
+  int64_t* rrank = (int64_t*)ctx->scratch(sizeof(int64_t) * (N + 1), 14);
+  int64_t kcap = next_pow2(std::max<int64_t>(N, 2048));
+  uint64_t* bkeys = (uint64_t*)ctx->scratch(sizeof(uint64_t) * kcap, 15);
+  if (!parent || !label || !csize || !isroot || !rrank || !bkeys)
+    return set_err(ctx, QH_ENOMEM, "allocation failed (components)");
+  g->block_of = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max(N, 1));
+  g->local = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max(N, 1));
+  g->pad_index = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max(N, 1));
+  if (!g->block_of || !g->local || !g->pad_index) return set_err(ctx, QH_ENOMEM, "allocation failed (blocks)");
+  QH_CUDA_TRY(cudaMemsetAsync(csize, 0, sizeof(int32_t) * std::max(N, 1), s));
+  QH_CUDA_TRY(cudaMemsetAsync(g->local, 0xff, sizeof(int32_t) * std::max(N, 1), s));
+  QH_CUDA_TRY(cudaMemsetAsync(g->pad_index, 0xff, sizeof(int32_t) * std::max(N, 1), s));
+  if (N > 0) {
+    k_uf_init<<<nblk(N), 256, 0, s>>>(N, parent);
+    k_uf_hook<<<nblk(N), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, parent);
+    k_uf_compress<<<nblk(N), 256, 0, s>>>(N, parent, label, csize);
+    k_block_roots<<<nblk(N), 256, 0, s>>>(N, label, csize, isroot);
+  }
+  scan_i32_to_i64(s, isroot, rrank, N);
+  int64_t nb64 = 0;
+  QH_CUDA_TRY(cudaMemcpyAsync(&nb64, rrank + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  QH_CUDA_TRY(cudaStreamSynchronize(s));
+  const int32_t nb = (int32_t)nb64;
+  g->n_blocks = nb;
+  int32_t* bsize = (int32_t*)ctx->scratch(sizeof(int32_t) * std::max(nb, 1), 16);
+  if (!bsize) return set_err(ctx, QH_ENOMEM, "allocation failed (block sizes)");
+  if (N > 0) {
+    k_block_of<<<nblk(N), 256, 0, s>>>(N, label, csize, rrank, g->block_of, bkeys);
+    k_block_sizes<<<nblk(N), 256, 0, s>>>(N, label, csize, rrank, bsize);
+    sort_u64(s, bkeys, N, kcap);
+  }
+  g->h_block_size.assign(nb, 0);
+  if (nb > 0)
+    QH_CUDA_TRY(cudaMemcpyAsync(g->h_block_size.data(), bsize, sizeof(int32_t) * nb,
+                                cudaMemcpyDeviceToHost, s));
+  QH_CUDA_TRY(cudaStreamSynchronize(s));
+  // host: block offsets, padded offsets, row tiles, tile slots
+  std::vector<int64_t> h_block_ptr(nb + 1, 0);
+  g->h_pad_off.assign(nb + 1, 0);
+  std::vector<int64_t> h_slot_off(nb + 1, 0);
+  std::vector<int32_t> h_T(std::max(nb, 1), 0);
+  for (int32_t b = 0; b < nb; ++b) {
+    int32_t sz = g->h_block_size[b];
+    int32_t T = (sz + TILE - 1) / TILE;
+    h_T[b] = T;
+    h_block_ptr[b + 1] = h_block_ptr[b] + sz;
+    g->h_pad_off[b + 1] = g->h_pad_off[b] + T * TILE;
+    h_slot_off[b + 1] = h_slot_off[b] + (int64_t)T * T;
+  }
+  g->n_pad = g->h_pad_off[nb];
+  const int64_t n_slots = h_slot_off[nb];
+  const int64_t total_in_blocks = h_block_ptr[nb];
+  g->block_ptr = (int64_t*)dalloc(*g, sizeof(int64_t) * (nb + 1));
+  g->pad_off = (int32_t*)dalloc(*g, sizeof(int32_t) * (nb + 1));
+  g->perm = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max<int64_t>(total_in_blocks, 1));
+  g->pad_node = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max(g->n_pad, 1));
+  int64_t* d_slot_off = (int64_t*)ctx->scratch(sizeof(int64_t) * (nb + 1), 17);
+  int32_t* d_T = (int32_t*)ctx->scratch(sizeof(int32_t) * std::max(nb, 1), 18);
+  int32_t* flags = (int32_t*)ctx->scratch(sizeof(int32_t) * std::max<int64_t>(n_slots, 1), 19);
+  int64_t* slot_tile = (int64_t*)ctx->scratch(sizeof(int64_t) * (n_slots + 1), 20);
+  if (!g->block_ptr || !g->pad_off || !g->perm || !g->pad_node || !d_slot_off || !d_T || !flags ||
+      !slot_tile)
+    return set_err(ctx, QH_ENOMEM, "allocation failed (layout)");
+  QH_CUDA_TRY(cudaMemcpyAsync(g->block_ptr, h_block_ptr.data(), sizeof(int64_t) * (nb + 1),
+                              cudaMemcpyHostToDevice, s));
+  QH_CUDA_TRY(cudaMemcpyAsync(g->pad_off, g->h_pad_off.data(), sizeof(int32_t) * (nb + 1),
+                              cudaMemcpyHostToDevice, s));
+  QH_CUDA_TRY(cudaMemcpyAsync(d_slot_off, h_slot_off.data(), sizeof(int64_t) * (nb + 1),
+                              cudaMemcpyHostToDevice, s));
+  if (nb > 0)
+    QH_CUDA_TRY(cudaMemcpyAsync(d_T, h_T.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
+  QH_CUDA_TRY(cudaMemsetAsync(g->pad_node, 0xff, sizeof(int32_t) * std::max(g->n_pad, 1), s));
+  if (total_in_blocks > 0)
+    k_perm_local<<<nblk(total_in_blocks), 256, 0, s>>>(total_in_blocks, bkeys, g->block_ptr,
+                                                        g->pad_off, g->perm, g->local,
+                                                        g->pad_index, g->pad_node);
+  // ---- tile slots: flag nonzero 128 x 128 tiles (all of them in dense mode)
+  if (o->dense) {
+    std::vector<int32_t> ones(std::max<int64_t>(n_slots, 1), 1);
+    QH_CUDA_TRY(cudaMemcpyAsync(flags, ones.data(), sizeof(int32_t) * std::max<int64_t>(n_slots, 1),
+                                cudaMemcpyHostToDevice, s));
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+  } else {
+    QH_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int32_t) * std::max<int64_t>(n_slots, 1), s));
+    if (N > 0)
+      k_tile_flags<<<nblk(N), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, g->block_of, g->local,
+                                          d_slot_off, d_T, flags);
+  }
+  scan_i32_to_i64(s, flags, slot_tile, n_slots);
+  std::vector<int64_t> h_slot_tile(n_slots + 1);
+  QH_CUDA_TRY(cudaMemcpyAsync(h_slot_tile.data(), slot_tile, sizeof(int64_t) * (n_slots + 1),
+                              cudaMemcpyDeviceToHost, s));
+  QH_CUDA_TRY(cudaStreamSynchronize(s));
+  g->n_tiles_hi = h_slot_tile[n_slots];
+  // row tiles: hi entries then (if needed) lo entries, contiguous per row tile
+  g->h_rt.clear();
+  std::vector<int32_t> h_rt_of_block(std::max(nb, 1), 0);
+  std::vector<int32_t> h_tile_col;
+  int64_t entry = 0;
+  for (int32_t b = 0; b < nb; ++b) {
+    h_rt_of_block[b] = (int32_t)g->h_rt.size();
+    int32_t T = h_T[b];
+    for (int32_t r = 0; r < T; ++r) {
+      int64_t s0 = h_slot_off[b] + (int64_t)r * T;
+      RowTile rt;
+      rt.block = b;
+      rt.row0 = g->h_pad_off[b] + r * TILE;
+      rt.valid = std::min(TILE, g->h_block_size[b] - r * TILE);
+      rt.tile_begin = (int32_t)entry;
+      rt.n_hi = (int32_t)(h_slot_tile[s0 + T] - h_slot_tile[s0]);
+      rt.n_all = g->has_lo ? 2 * rt.n_hi : rt.n_hi;
+      rt.f32_begin = (int32_t)h_slot_tile[s0];
+      int32_t ct0 = g->h_pad_off[b] / TILE;
+      std::vector<int32_t> cols;
+      for (int32_t c = 0; c < T; ++c)
+        if (h_slot_tile[s0 + c + 1] > h_slot_tile[s0 + c]) cols.push_back(ct0 + c);
+      for (int rep = 0; rep < (g->has_lo ? 2 : 1); ++rep)
+        h_tile_col.insert(h_tile_col.end(), cols.begin(), cols.end());
+      entry += rt.n_all;
+      g->h_rt.push_back(rt);
+    }
+  }
+  g->n_tiles = entry;
+  g->n_row_tiles = (int32_t)g->h_rt.size();
+  g->rt = (RowTile*)dalloc(*g, sizeof(RowTile) * std::max(g->n_row_tiles, 1));
+  g->tile_col = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max<int64_t>(g->n_tiles, 1));
+  g->tile_bf16 = (__nv_bfloat16*)dalloc(*g, sizeof(__nv_bfloat16) * TILE * TILE * std::max<int64_t>(g->n_tiles, 1));
+  g->tile_f32 = (float*)dalloc(*g, sizeof(float) * TILE * TILE * std::max<int64_t>(g->n_tiles_hi, 1));
+  g->rt_of_block = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max(nb, 1));
+  g->slot_off = (int64_t*)dalloc(*g, sizeof(int64_t) * (nb + 1));
+  g->tiles_per_block = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max(nb, 1));
+  g->slot_tile = (int64_t*)dalloc(*g, sizeof(int64_t) * (n_slots + 1));
+  if (!g->rt || !g->tile_col || !g->tile_bf16 || !g->tile_f32 || !g->rt_of_block || !g->slot_off ||
+      !g->tiles_per_block || !g->slot_tile)
+    return set_err(ctx, QH_ENOMEM, "allocation failed (tiles)");
+  if (g->n_row_tiles > 0)
+    QH_CUDA_TRY(cudaMemcpyAsync(g->rt, g->h_rt.data(), sizeof(RowTile) * g->n_row_tiles,
+                                cudaMemcpyHostToDevice, s));
+  if (g->n_tiles > 0)
+    QH_CUDA_TRY(cudaMemcpyAsync(g->tile_col, h_tile_col.data(), sizeof(int32_t) * g->n_tiles,
+                                cudaMemcpyHostToDevice, s));
+  QH_CUDA_TRY(cudaMemcpyAsync(g->rt_of_block, h_rt_of_block.data(), sizeof(int32_t) * std::max(nb, 1),
+                              cudaMemcpyHostToDevice, s));
+  QH_CUDA_TRY(cudaMemcpyAsync(g->slot_off, d_slot_off, sizeof(int64_t) * (nb + 1),
+                              cudaMemcpyDeviceToDevice, s));
+  QH_CUDA_TRY(cudaMemcpyAsync(g->tiles_per_block, d_T, sizeof(int32_t) * std::max(nb, 1),
+                              cudaMemcpyDeviceToDevice, s));
+  QH_CUDA_TRY(cudaMemcpyAsync(g->slot_tile, slot_tile, sizeof(int64_t) * (n_slots + 1),
+                              cudaMemcpyDeviceToDevice, s));
+  {
+    qh_status st = retile(ctx, g, g->w, g->tile_bf16, g->tile_f32);
+    if (st != QH_OK) return st;
+  }
+  // ---- per-block sums (sum of w over both triangles, sum of J^2) and default c0
+  g->sum_w = (double*)dalloc(*g, sizeof(double) * std::max(nb, 1));
+  g->sum_j2 = (double*)dalloc(*g, sizeof(double) * std::max(nb, 1));
+  double* node_tmp = (double*)ctx->scratch(sizeof(double) * 2 * std::max(N, 1), 21);
+  if (!g->sum_w || !g->sum_j2 || !node_tmp) return set_err(ctx, QH_ENOMEM, "allocation failed (block sums)");
+  launch_block_sums(s, *g, g->w, g->sum_w, g->sum_j2, node_tmp);
+  std::vector<double> sj2(std::max(nb, 1));
+  g->h_sum_w.assign(std::max(nb, 1), 0.0);
+  if (nb > 0) {
+    QH_CUDA_TRY(cudaMemcpyAsync(sj2.data(), g->sum_j2, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+    QH_CUDA_TRY(cudaMemcpyAsync(g->h_sum_w.data(), g->sum_w, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+  }
+  QH_CUDA_TRY(cudaStreamSynchronize(s));
+  g->h_c0.assign(std::max(nb, 1), 0.0);
+  for (int32_t b = 0; b < nb; ++b) {
+    double Nb = (double)g->h_block_size[b];
+    double sigma = std::sqrt(sj2[b] / (Nb * (Nb - 1.0)));
+    g->h_c0[b] = sigma > 0 ? 0.5 / (sigma * std::sqrt(Nb)) : 0.0;
+  }
+  g->h_block_ptr = h_block_ptr;
+  return QH_OK;
+}
+
+qh_status retile(Ctx* ctx, Graph* g, const double* w, __nv_bfloat16* tb, float* tf) {
+  cudaStream_t s = ctx->stream;
+  if (g->n_tiles > 0)
+    QH_CUDA_TRY(cudaMemsetAsync(tb, 0, sizeof(__nv_bfloat16) * TILE * TILE * g->n_tiles, s));
+  if (g->n_tiles_hi > 0)
+    QH_CUDA_TRY(cudaMemsetAsync(tf, 0, sizeof(float) * TILE * TILE * g->n_tiles_hi, s));
+  if (g->n_nodes > 0 && g->n_tiles > 0)
+    k_tile_fill<<<nblk(g->n_nodes), 256, 0, s>>>(g->n_nodes, g->row_ptr, g->col, w, g->block_of,
+                                                 g->local, g->slot_off, g->tiles_per_block,
+                                                 g->slot_tile, g->rt, g->rt_of_block,
+                                                 g->has_lo ? 1 : 0, tb, tf);
+  QH_CUDA_TRY(cudaGetLastError());
+  return QH_OK;
+}
+
+}  // namespace qh

@@ -1,0 +1,199 @@
+// Internal declarations shared by the CUDA translation units of libqhap.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "qhap.h"
+
+namespace qh {
+
+constexpr int TILE = 128;           // J tile edge (rows = MMA M, columns = 2 x 64 K-slices)
+constexpr int SNP_ROW_CAP = 8192;   // max fragment terms gathered for one SNP row
+
+// Device error word bits (set by kernels, read back by the host).
+enum : int32_t {
+  ERR_INPUT = 1,        // malformed fragments
+  ERR_QUAL = 2,         // Phred quality outside [4, 93]
+  ERR_ROWCAP = 4,       // SNP row over SNP_ROW_CAP terms
+  ERR_TIMEOUT = 8,      // bounded wait expired (mbarrier)
+};
+
+struct RowTile {           // one 128-row slab of a block in the padded layout
+  int32_t block;           // phase block
+  int32_t row0;            // first padded row (multiple of 128)
+  int32_t valid;           // rows < valid are real vertices
+  int32_t tile_begin;      // first entry in tile_col / BF16 tile data
+  int32_t n_hi;            // entries carrying J (FP32 path uses these only)
+  int32_t n_all;           // hi entries followed by lo (BF16 remainder) entries
+  int32_t f32_begin;       // first FP32 tile of this row tile
+  int32_t pad_;
+};
+
+struct Graph {
+  int mode = 0, weight_mode = 1, linkage_k = 10;
+  double porec_alpha = 0.1;
+  int32_t n_frags = 0, n_snps = 0, n_nodes = 0;
+  int64_t nnz_frag = 0;
+  // fragments (device)
+  int64_t* frag_ptr = nullptr;
+  int32_t* snp = nullptr;
+  int8_t* allele = nullptr;
+  uint8_t* qual = nullptr;
+  uint8_t* is_porec = nullptr;
+  // SNP -> covering fragments (device), fragments ascending per SNP
+  int64_t* cov_ptr = nullptr;
+  int32_t* cov_frag = nullptr;
+  int8_t* cov_allele = nullptr;
+  // edges (device), both directions
+  int64_t nnz = 0;
+  int64_t* row_ptr = nullptr;
+  int32_t* col = nullptr;
+  double* w = nullptr;         // weights A (exact integers in READ mode)
+  bool integer_weights = true;
+  double max_abs_w = 0.0;
+  // components / blocks
+  int32_t n_blocks = 0;
+  int32_t* block_of = nullptr;    // [n_nodes], -1 = dropped
+  int32_t* local = nullptr;       // [n_nodes]
+  int32_t* pad_index = nullptr;   // [n_nodes], -1 = dropped
+  int32_t* pad_node = nullptr;    // [n_pad] -> vertex or -1
+  int64_t* block_ptr = nullptr;   // [n_blocks+1] into perm
+  int32_t* perm = nullptr;        // vertices of each block, ascending
+  int32_t* pad_off = nullptr;     // [n_blocks+1] padded offsets (device)
+  std::vector<int32_t> h_block_size, h_pad_off;
+  std::vector<int64_t> h_block_ptr;
+  int32_t n_pad = 0;
+  // tiles
+  int32_t n_row_tiles = 0;
+  int64_t n_tiles = 0;            // all BF16 entries (hi + lo)
+  int64_t n_tiles_hi = 0;         // FP32 tiles
+  bool has_lo = false;
+  RowTile* rt = nullptr;          // [n_row_tiles]
+  int32_t* rt_of_block = nullptr; // [n_blocks] first row tile of the block
+  int32_t* tile_col = nullptr;    // [n_tiles] column tile (padded col / 128)
+  int64_t* slot_off = nullptr;    // [n_blocks+1] tile-slot offsets (T_b^2 slots per block)
+  int32_t* tiles_per_block = nullptr;  // [n_blocks] T_b
+  int64_t* slot_tile = nullptr;   // [slots+1] exclusive scan of nonzero slots
+  __nv_bfloat16* tile_bf16 = nullptr;  // [n_tiles][128][128] row-major
+  float* tile_f32 = nullptr;           // [n_tiles_hi][128][128] row-major
+  std::vector<RowTile> h_rt;
+  // per-block constants
+  double* sum_w = nullptr;        // [n_blocks] sum_{a,b} w_ab (both triangles)
+  double* sum_j2 = nullptr;       // [n_blocks]
+  std::vector<double> h_c0;       // default c0 per block
+  std::vector<double> h_sum_w;
+  // all device allocations of this graph, freed together
+  std::vector<void*> allocs;
+};
+
+struct Solution {
+  int mode = 0;
+  int32_t n_blocks = 0, R = 0, replica_base = 0, n_nodes = 0;
+  std::vector<int32_t> best_r, steps_run, iters;
+  std::vector<double> best_cut;
+  std::vector<double> cuts_first;        // [n_blocks * R]
+  std::vector<int8_t> spins;             // [n_nodes] best spins by vertex (0 = dropped)
+  std::vector<int32_t> C;                // SNP mode flip counts [n_nodes]
+  double solve_ms = 0, step_ms = 0, spin_updates = 0;
+  int64_t n_step_launches = 0;
+  std::vector<int32_t> block_size;
+  std::vector<int64_t> block_ptr;        // host copy for per-block extraction
+  std::vector<int32_t> perm;             // vertices of each block, ascending (host copy)
+  int8_t* d_spins = nullptr;             // device [n_nodes]
+  int32_t* d_C = nullptr;                // device [n_nodes]
+  std::vector<void*> allocs;
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int n_sm = 148;
+  std::string err;
+  int32_t* d_err = nullptr;
+  std::vector<void*> slots;         // grow-only scratch buffers
+  std::vector<size_t> slot_bytes;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // one captured step loop, replayed while its shape is unchanged
+  cudaGraphExec_t loop_exec = nullptr;
+  std::string loop_key;
+  void* scratch(size_t bytes, int slot);
+};
+
+// Device-side view handed to the step kernels.
+struct StepArgs {
+  const RowTile* rt;
+  const int32_t* tile_col;
+  const float* tile_f32;
+  float* x;               // [R][n_pad]  (BF16 path: in place)
+  float* y;               // [R][n_pad]
+  const float* xin;       // FP32 path: x_t operand (double-buffered)
+  float* xout;            // FP32 path: x_{t+1}
+  __nv_bfloat16* xh_out;  // BF16 path: X_hat_{t+1}
+  float* z_out;           // debug matvec: Z output (nullptr in solver steps)
+  const float* c0;        // [n_blocks]
+  const int32_t* active;  // [n_blocks] or nullptr
+  const int32_t* steps_b;  // [n_blocks] schedule length per block (a(t) = a0 t / steps_b)
+  int32_t n_pad, R;
+  int32_t t;              // step index
+  float dt, dta0;         // dta0 = dt * a0
+  double a0;
+  int32_t* err;
+};
+
+qh_status set_err(Ctx* ctx, qh_status st, const std::string& msg);
+qh_status cuda_fail(Ctx* ctx, cudaError_t e, const char* what);
+void* dalloc(Graph& g, size_t bytes);
+qh_status retile(Ctx* ctx, Graph* g, const double* w, __nv_bfloat16* tb, float* tf);
+qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opts* o, Graph* g);
+
+// ---- launchers (bsb_simt.cu)
+void launch_init_state(cudaStream_t s, const Graph& g, int32_t R, int32_t replica_base,
+                       uint64_t seed, int32_t iter, float* x, float* y, __nv_bfloat16* xh,
+                       const int32_t* active);
+void launch_step_f32(cudaStream_t s, const Graph& g, const StepArgs& a);
+void launch_signs(cudaStream_t s, const Graph& g, int32_t R, const float* x, int8_t* signs_t);
+void launch_cut(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t, const double* w,
+                const double* sum_w, double* node_val, double* cuts, const int32_t* active);
+void launch_pick_best(cudaStream_t s, int32_t n_blocks, int32_t R, const double* cuts,
+                      int32_t* best_r, double* best_cut, const int32_t* active);
+void launch_early_stop(cudaStream_t s, int32_t n_blocks, const double* best_cut, double* best_seen,
+                       int32_t* stall, int32_t* active, int32_t* steps_run, int32_t patience,
+                       int32_t t_done);
+void launch_extract_spins(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t,
+                          const int32_t* best_r, int8_t* spins, const int32_t* active);
+void launch_block_sums(cudaStream_t s, const Graph& g, const double* w, double* sum_w,
+                       double* sum_j2, double* node_tmp /* 2 * n_nodes */);
+void launch_refine_prepare(cudaStream_t s, const Graph& g, const int8_t* spins,
+                           const double* best_cut, int32_t* active, int32_t* C);
+void launch_gauge(cudaStream_t s, const Graph& g, const int8_t* spins, double* w,
+                  const int32_t* active);
+void launch_vote(cudaStream_t s, const Graph& g, const int8_t* spins, int8_t* hap1, int8_t* hap2,
+                 int32_t* block_id);
+void launch_parity(cudaStream_t s, const Graph& g, const int32_t* C, int8_t* hap1, int8_t* hap2,
+                   int32_t* block_id);
+void launch_f32_to_bf16(cudaStream_t s, const float* x, __nv_bfloat16* xh, int64_t n);
+
+// ---- launchers (bsb_tc.cu)
+struct TcPlan {
+  int bn = 128;     // replicas per CTA (MMA N)
+  int stages = 3;   // TMA/MMA pipeline depth
+};
+qh_status launch_step_tc(Ctx* ctx, const Graph& g, const StepArgs& a,
+                         const __nv_bfloat16* xh_in, const TcPlan& plan);
+bool tc_plan_ok(int R, const TcPlan& plan);
+qh_status tc_prepare(Ctx* ctx);
+
+}  // namespace qh
+
+#define QH_CUDA_TRY(expr)                                        \
+  do {                                                           \
+    cudaError_t _e = (expr);                                     \
+    if (_e != cudaSuccess) return qh::cuda_fail(ctx, _e, #expr); \
+  } while (0)

@@ -1,0 +1,278 @@
+"""Python binding of libqhap (ctypes).  Argument marshalling only: every step of the
+phasing path runs in the library's CUDA kernels.
+
+The raw C functions are exposed under their C names (``qh_create``, ``qh_build_graph``,
+``qh_bsb_solve``, ``qh_phase`` ...) through :func:`lib`.  The classes below wrap them
+with numpy / torch arrays:
+
+    ctx = Context(device=0)
+    g = ctx.build_graph(frags, mode=MODE_READ, weight_mode=WEIGHT_SIGNED)
+    sol = ctx.solve(g, replicas=1024, steps=1000, precision=PREC_BF16, seed=1)
+    hap1, hap2, block_id = ctx.phase(g, sol)
+
+Importing succeeds without a GPU; creating a Context needs the CUDA library
+(``libqhap.so``, built by ``paper_2603_25762_gb300.build.build()``) and raises if it
+is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqhap.so")
+
+QH_OK, QH_EINVAL, QH_ENOMEM, QH_ECUDA, QH_ETIMEOUT, QH_EUNSUPPORTED = range(6)
+MODE_READ, MODE_SNP = 0, 1
+WEIGHT_CONFLICT, WEIGHT_SIGNED = 0, 1
+PREC_FP32, PREC_BF16 = 0, 1
+SCHED_LINEAR, SCHED_AUTO = 0, 1
+
+
+class QhFragments(C.Structure):
+    _fields_ = [("n_frags", C.c_int32), ("n_snps", C.c_int32), ("frag_ptr", C.c_void_p),
+                ("snp", C.c_void_p), ("allele", C.c_void_p), ("qual", C.c_void_p),
+                ("is_porec", C.c_void_p), ("on_device", C.c_int32)]
+
+
+class QhGraphOpts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("weight_mode", C.c_int32), ("linkage_k", C.c_int32),
+                ("dense", C.c_int32), ("porec_alpha", C.c_double)]
+
+
+class QhBsbOpts(C.Structure):
+    _fields_ = [("replicas", C.c_int32), ("steps", C.c_int32), ("schedule", C.c_int32),
+                ("precision", C.c_int32), ("dt", C.c_double), ("a0", C.c_double),
+                ("c0", C.c_double), ("seed", C.c_uint64), ("replica_base", C.c_int32),
+                ("check_every", C.c_int32), ("patience", C.c_int32), ("refine_max", C.c_int32)]
+
+
+class QhError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_STATUS = {0: "QH_OK", 1: "QH_EINVAL", 2: "QH_ENOMEM", 3: "QH_ECUDA", 4: "QH_ETIMEOUT",
+           5: "QH_EUNSUPPORTED"}
+
+P, PP = C.c_void_p, C.POINTER(C.c_void_p)
+I32, I64, D = C.c_int32, C.c_int64, C.c_double
+_SIGS = {
+    "qh_create": (C.c_int, [PP, C.c_int, P]),
+    "qh_destroy": (None, [P]),
+    "qh_status_str": (C.c_char_p, [C.c_int]),
+    "qh_last_error": (C.c_char_p, [P]),
+    "qh_build_graph": (C.c_int, [P, C.POINTER(QhFragments), C.POINTER(QhGraphOpts), PP]),
+    "qh_graph_info": (C.c_int, [P, P, P, P, I32, P, P]),
+    "qh_graph_edges": (C.c_int, [P, P, P, P, P]),
+    "qh_graph_blocks": (C.c_int, [P, P, P, P]),
+    "qh_graph_free": (None, [P]),
+    "qh_bsb_solve": (C.c_int, [P, P, C.POINTER(QhBsbOpts), PP]),
+    "qh_solution_block": (C.c_int, [P, P, I32, P, P, P, P, P]),
+    "qh_solution_spins": (C.c_int, [P, P, P]),
+    "qh_solution_cuts": (C.c_int, [P, P, P]),
+    "qh_solution_timing": (C.c_int, [P, P, P, P, P]),
+    "qh_solution_free": (None, [P]),
+    "qh_phase": (C.c_int, [P, P, P, P, P, P, I32]),
+    "qh_debug_matvec": (C.c_int, [P, P, I32, I32, P, P]),
+    "qh_debug_steps": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P]),
+    "qh_debug_layout": (C.c_int, [P, P, P, P, P]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libqhap.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"libqhap.so not found at {LIB_PATH}; run "
+                          "paper_2603_25762_gb300.build.build() first (no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def __getattr__(name):
+    if name in _SIGS:
+        return getattr(lib(), name)
+    raise AttributeError(name)
+
+
+def _ptr(a):
+    """Host numpy array or device torch tensor -> raw address (None stays NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _np(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class Graph:
+    def __init__(self, ctx, handle):
+        self.ctx = ctx
+        self.h = handle
+        n, nb, nnz, nt = I32(), I32(), I64(), I64()
+        lib().qh_graph_info(handle, C.byref(n), C.byref(nb), None, 0, C.byref(nnz), C.byref(nt))
+        self.n_nodes, self.n_blocks, self.nnz, self.n_tiles = n.value, nb.value, nnz.value, nt.value
+
+    def block_sizes(self):
+        out = np.zeros(max(self.n_blocks, 1), np.int32)
+        lib().qh_graph_info(self.h, None, None, _ptr(out), self.n_blocks, None, None)
+        return out[: self.n_blocks]
+
+    def edges(self):
+        rp = np.zeros(self.n_nodes + 1, np.int64)
+        col = np.zeros(max(self.nnz, 1), np.int32)
+        w = np.zeros(max(self.nnz, 1), np.float64)
+        self.ctx._check(lib().qh_graph_edges(self.ctx.h, self.h, _ptr(rp), _ptr(col), _ptr(w)))
+        return rp, col[: self.nnz], w[: self.nnz]
+
+    def blocks(self):
+        bo = np.zeros(max(self.n_nodes, 1), np.int32)
+        lo = np.zeros(max(self.n_nodes, 1), np.int32)
+        self.ctx._check(lib().qh_graph_blocks(self.ctx.h, self.h, _ptr(bo), _ptr(lo)))
+        return bo[: self.n_nodes], lo[: self.n_nodes]
+
+    def layout(self):
+        n_pad = I32()
+        pidx = np.zeros(max(self.n_nodes, 1), np.int32)
+        c0 = np.zeros(max(self.n_blocks, 1), np.float64)
+        self.ctx._check(lib().qh_debug_layout(self.ctx.h, self.h, C.byref(n_pad), _ptr(pidx),
+                                              _ptr(c0)))
+        return n_pad.value, pidx[: self.n_nodes], c0[: self.n_blocks]
+
+    def free(self):
+        if self.h:
+            lib().qh_graph_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Solution:
+    def __init__(self, ctx, handle, n_blocks, R):
+        self.ctx, self.h, self.n_blocks, self.R = ctx, handle, n_blocks, R
+
+    def block(self, b, size=None):
+        cut, br, sr, it = D(), I32(), I32(), I32()
+        sp = np.zeros(max(size or 0, 1), np.int8)
+        self.ctx._check(lib().qh_solution_block(self.ctx.h, self.h, b, _ptr(sp) if size else None,
+                                                C.byref(cut), C.byref(br), C.byref(sr),
+                                                C.byref(it)))
+        return {"best_cut": cut.value, "best_replica": br.value, "steps_run": sr.value,
+                "iterations": it.value, "spins": sp[:size] if size else None}
+
+    def spins(self, n_nodes):
+        s = np.zeros(max(n_nodes, 1), np.int8)
+        self.ctx._check(lib().qh_solution_spins(self.ctx.h, self.h, _ptr(s)))
+        return s[:n_nodes]
+
+    def cuts(self):
+        c = np.zeros(max(self.n_blocks * self.R, 1))
+        self.ctx._check(lib().qh_solution_cuts(self.ctx.h, self.h, _ptr(c)))
+        return c[: self.n_blocks * self.R].reshape(self.n_blocks, self.R)
+
+    def timing(self):
+        a, b, n, su = D(), D(), I64(), D()
+        lib().qh_solution_timing(self.h, C.byref(a), C.byref(b), C.byref(n), C.byref(su))
+        return {"solve_ms": a.value, "step_ms": b.value, "n_step_launches": n.value,
+                "spin_updates": su.value}
+
+    def free(self):
+        if self.h:
+            lib().qh_solution_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """One library context on one CUDA device (optionally on a caller's stream)."""
+
+    def __init__(self, device=0, stream=None):
+        h = C.c_void_p()
+        st = lib().qh_create(C.byref(h), device, C.c_void_p(stream) if stream else None)
+        if st != QH_OK:
+            raise QhError(st, "qh_create failed")
+        self.h = h
+
+    def _check(self, st):
+        if st != QH_OK:
+            raise QhError(st, lib().qh_last_error(self.h).decode())
+
+    def build_graph(self, fr=None, mode=MODE_READ, weight_mode=WEIGHT_SIGNED, linkage_k=10,
+                    dense=False, porec_alpha=0.1, arrays=None, on_device=False):
+        """fr: a synth.Fragments (host); or arrays=(n_snps, frag_ptr, snp, allele, qual, is_porec)
+        as numpy (host) or torch CUDA tensors with on_device=True."""
+        if arrays is None:
+            arrays = (fr.n_snps, _np(fr.frag_ptr, np.int64), _np(fr.snp, np.int32),
+                      _np(fr.allele, np.int8), _np(fr.qual, np.uint8), _np(fr.is_porec, np.uint8))
+        n_snps, fp, snp, al, q, pc = arrays
+        f = QhFragments(int(fp.shape[0]) - 1, int(n_snps), _ptr(fp), _ptr(snp), _ptr(al), _ptr(q),
+                        _ptr(pc), 1 if on_device else 0)
+        o = QhGraphOpts(mode, weight_mode, linkage_k, 1 if dense else 0, porec_alpha)
+        g = C.c_void_p()
+        self._check(lib().qh_build_graph(self.h, C.byref(f), C.byref(o), C.byref(g)))
+        return Graph(self, g)
+
+    def solve(self, g, replicas=32, steps=1000, precision=PREC_FP32, seed=1, dt=1.0, a0=1.0,
+              c0=0.0, schedule=SCHED_LINEAR, replica_base=0, check_every=0, patience=0,
+              refine_max=15):
+        o = QhBsbOpts(replicas, steps, schedule, precision, dt, a0, c0, seed, replica_base,
+                      check_every, patience, refine_max)
+        s = C.c_void_p()
+        self._check(lib().qh_bsb_solve(self.h, g.h, C.byref(o), C.byref(s)))
+        return Solution(self, s, g.n_blocks, replicas)
+
+    def phase(self, g, sol, n_snps, out=None):
+        """Host outputs by default; pass out=(hap1, hap2, block_id) torch CUDA tensors to keep
+        them on the device."""
+        if out is None:
+            hap1 = np.zeros(max(n_snps, 1), np.int8)
+            hap2 = np.zeros(max(n_snps, 1), np.int8)
+            bid = np.zeros(max(n_snps, 1), np.int32)
+            self._check(lib().qh_phase(self.h, g.h, sol.h, _ptr(hap1), _ptr(hap2), _ptr(bid), 0))
+            return hap1[:n_snps], hap2[:n_snps], bid[:n_snps]
+        hap1, hap2, bid = out
+        self._check(lib().qh_phase(self.h, g.h, sol.h, _ptr(hap1), _ptr(hap2), _ptr(bid), 1))
+        return hap1, hap2, bid
+
+    def debug_matvec(self, g, precision, R, x, z):
+        self._check(lib().qh_debug_matvec(self.h, g.h, precision, R, _ptr(x), _ptr(z)))
+
+    def debug_steps(self, g, precision, R, x, y, t0, nsteps, steps, dt=1.0, a0=1.0, c0=None):
+        c0a = None if c0 is None else _np(c0, np.float64)
+        self._check(lib().qh_debug_steps(self.h, g.h, precision, R, _ptr(x), _ptr(y), t0, nsteps,
+                                         steps, dt, a0, _ptr(c0a) if c0a is not None else None))
+
+    def close(self):
+        if self.h:
+            lib().qh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

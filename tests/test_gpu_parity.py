@@ -1,0 +1,370 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Bars: integer graph weights and cuts bit-exact; SNP-graph weights within 1e-12
+relative (FP64 in both, summation in the same fragment order, log10/exp10 from two
+math libraries); per-step J x X relative Frobenius error <= 1e-5 (FP32 path) and
+<= 1e-2 (BF16 path); best cut >= 0.999 x the oracle's on the same seed, steps and
+replica indices.
+"""
+import numpy as np
+import pytest
+
+from paper_2603_25762_gb300 import metrics, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_25762_gb300 import build, qhap
+    build.build()
+    return qhap
+
+
+@pytest.fixture(scope="module")
+def ctx(q):
+    return q.Context(0)
+
+
+def _sorted_csr(rp, col, w):
+    rows = np.repeat(np.arange(rp.shape[0] - 1), np.diff(rp))
+    order = np.lexsort((col, rows))
+    return rows[order], col[order], w[order]
+
+
+def _oracle_edges(g):
+    rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    return rows, g.col.astype(np.int64), g.w
+
+
+def _small_region(seed=7, scale=0.1, **kw):
+    return synth.hifi_region(seed=seed, scale=scale)
+
+
+# ----------------------------------------------------------------------------- graph build
+@pytest.mark.parametrize("make", [lambda: synth.tiny_reads(1001),
+                                  lambda: synth.hifi_region(1002, scale=0.08),
+                                  lambda: synth.tiny_reads(5, n_snps=60, n_reads=200, flip_p=0.2)])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_read_graph_bitexact(q, ctx, oracle, make, mode):
+    fr = make()
+    g = ctx.build_graph(fr, mode=q.MODE_READ, weight_mode=mode)
+    r1, c1, w1 = _sorted_csr(*g.edges())
+    og = oracle.read_graph(fr, mode)
+    r2, c2, w2 = _oracle_edges(og)
+    assert np.array_equal(r1, r2) and np.array_equal(c1, c2)
+    assert np.array_equal(w1, w2)
+
+
+@pytest.mark.parametrize("k", [10, 4])
+def test_snp_graph_parity(q, ctx, oracle, k):
+    fr = synth.ont_region(1003, scale=0.06)
+    g = ctx.build_graph(fr, mode=q.MODE_SNP, linkage_k=k)
+    r1, c1, w1 = _sorted_csr(*g.edges())
+    og = oracle.snp_graph(fr, 0.1, k)
+    r2, c2, w2 = _oracle_edges(og)
+    assert np.array_equal(r1, r2) and np.array_equal(c1, c2)
+    np.testing.assert_allclose(w1, w2, rtol=1e-12, atol=1e-15)
+
+
+def test_snp_graph_porec_parity(q, ctx, oracle):
+    fr = synth.chromosome_porec(1005, scale=0.004)
+    assert fr.is_porec.sum() > 0
+    g = ctx.build_graph(fr, mode=q.MODE_SNP, porec_alpha=0.1)
+    r1, c1, w1 = _sorted_csr(*g.edges())
+    og = oracle.snp_graph(fr, 0.1, 10)
+    r2, c2, w2 = _oracle_edges(og)
+    assert np.array_equal(r1, r2) and np.array_equal(c1, c2)
+    np.testing.assert_allclose(w1, w2, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("mode", ["read", "snp"])
+def test_components_match_oracle(q, ctx, oracle, mode):
+    fr = synth.region_reads(77, n_snps=800, region=600_000, n_reads=90, len_mean=6000,
+                            len_sd=3000, flip_p=0.05, qual=(7, 30))
+    if mode == "read":
+        g = ctx.build_graph(fr, mode=q.MODE_READ)
+        og = oracle.read_graph(fr, oracle.READ_SIGNED)
+    else:
+        g = ctx.build_graph(fr, mode=q.MODE_SNP)
+        og = oracle.snp_graph(fr)
+    blocks = oracle.blocks_of(og)
+    bo, lo = g.blocks()
+    assert g.n_blocks == len(blocks) and g.n_blocks > 1
+    exp_b = -np.ones(og.n, np.int32)
+    exp_l = np.zeros(og.n, np.int32)
+    for b, nodes in enumerate(blocks):
+        exp_b[nodes] = b
+        exp_l[nodes] = np.arange(len(nodes))
+    assert np.array_equal(bo, exp_b)
+    assert np.array_equal(lo[exp_b >= 0], exp_l[exp_b >= 0])
+
+
+def test_invalid_inputs_rejected(q, ctx):
+    fr = synth.tiny_reads(3, n_snps=40, n_reads=10)
+    bad = synth.Fragments(fr.n_snps, fr.frag_ptr, fr.snp.copy(), fr.allele, fr.qual, fr.is_porec,
+                          fr.positions, fr.truth)
+    bad.snp[3] = fr.n_snps + 5
+    with pytest.raises(q.QhError) as e:
+        ctx.build_graph(bad)
+    assert e.value.status == q.QH_EINVAL
+    bad2 = synth.Fragments(fr.n_snps, fr.frag_ptr, fr.snp, fr.allele.copy(), fr.qual,
+                           fr.is_porec, fr.positions, fr.truth)
+    bad2.allele[0] = 0
+    with pytest.raises(q.QhError):
+        ctx.build_graph(bad2)
+    bad3 = synth.Fragments(fr.n_snps, fr.frag_ptr, fr.snp, fr.allele, fr.qual.copy(),
+                           fr.is_porec, fr.positions, fr.truth)
+    bad3.qual[2] = 3
+    with pytest.raises(q.QhError):
+        ctx.build_graph(bad3, mode=q.MODE_SNP)
+    # the context stays usable after rejected inputs
+    g = ctx.build_graph(fr)
+    assert g.n_nodes == fr.n_frags
+
+
+def test_empty_and_edgeless_inputs(q, ctx):
+    empty = synth.Fragments(10, np.zeros(1, np.int64), np.zeros(0, np.int32),
+                            np.zeros(0, np.int8), np.zeros(0, np.uint8), np.zeros(0, np.uint8),
+                            np.arange(10), np.ones(10, np.int8))
+    g = ctx.build_graph(empty)
+    assert g.n_nodes == 0 and g.n_blocks == 0
+    sol = ctx.solve(g, replicas=64, steps=10, precision=q.PREC_BF16)
+    h1, h2, bid = ctx.phase(g, sol, 10)
+    assert (h1 == 0).all() and (bid == -1).all()
+    lone = synth.Fragments(10, np.array([0, 1, 2, 2], np.int64), np.array([1, 5], np.int32),
+                           np.array([1, -1], np.int8), np.array([30, 30], np.uint8),
+                           np.zeros(3, np.uint8), np.arange(10), np.ones(10, np.int8))
+    g = ctx.build_graph(lone)
+    assert g.n_blocks == 0
+    sol = ctx.solve(g, replicas=32, steps=10)
+    h1, _, bid = ctx.phase(g, sol, 10)
+    assert (h1 == 0).all()
+
+
+# ----------------------------------------------------------------------------- J x X precision
+def _rel_frob(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _matvec_case(q, ctx, oracle, fr, mode, precision, R, dense=False, seed=0, bf16_x=False):
+    import torch
+    if mode == q.MODE_READ:
+        g = ctx.build_graph(fr, mode=mode, dense=dense)
+        og = oracle.read_graph(fr, oracle.READ_SIGNED)
+    else:
+        g = ctx.build_graph(fr, mode=mode, dense=dense)
+        og = oracle.snp_graph(fr)
+    n_pad, pidx, _ = g.layout()
+    rng = np.random.default_rng(seed)
+    xv = rng.uniform(-1, 1, size=(R, og.n)).astype(np.float32)
+    if bf16_x:  # values exactly representable in BF16: only J's representation errs
+        import torch
+        xv = torch.from_numpy(xv).to(torch.bfloat16).float().numpy()
+    x = np.zeros((R, n_pad), np.float32)
+    inb = pidx >= 0
+    x[:, pidx[inb]] = xv[:, inb]
+    xd = torch.from_numpy(x).cuda()
+    zd = torch.zeros_like(xd)
+    ctx.debug_matvec(g, precision, R, xd, zd)
+    z = zd.cpu().numpy()[:, pidx[inb]]
+    from scipy.sparse import csr_matrix
+    J = -csr_matrix((og.w, og.col, og.row_ptr), shape=(og.n, og.n))
+    zref = (J @ xv.astype(np.float64).T).T[:, inb]
+    return _rel_frob(z.astype(np.float64), zref)
+
+
+@pytest.mark.parametrize("dense", [False, True])
+def test_matvec_read_graph(q, ctx, oracle, dense):
+    fr = synth.hifi_region(1002, scale=0.08)
+    e32 = _matvec_case(q, ctx, oracle, fr, q.MODE_READ, q.PREC_FP32, 64, dense)
+    e16 = _matvec_case(q, ctx, oracle, fr, q.MODE_READ, q.PREC_BF16, 128, dense)
+    assert e32 <= 1e-5, e32
+    assert e16 <= 1e-2, e16
+
+
+def test_matvec_exact_operands(q, ctx, oracle):
+    # integer |w| <= 256 is exact in one BF16 operand; real SNP weights use J = hi + lo
+    fr = synth.hifi_region(1002, scale=0.08)
+    e_read = _matvec_case(q, ctx, oracle, fr, q.MODE_READ, q.PREC_BF16, 64, bf16_x=True)
+    assert e_read <= 1e-6, e_read
+    fs = synth.ont_region(1003, scale=0.06)
+    e_snp = _matvec_case(q, ctx, oracle, fs, q.MODE_SNP, q.PREC_BF16, 64, bf16_x=True)
+    assert e_snp <= 3e-5, e_snp
+
+
+def test_matvec_snp_graph_hilo(q, ctx, oracle):
+    fr = synth.ont_region(1003, scale=0.06)
+    e32 = _matvec_case(q, ctx, oracle, fr, q.MODE_SNP, q.PREC_FP32, 64)
+    e16 = _matvec_case(q, ctx, oracle, fr, q.MODE_SNP, q.PREC_BF16, 64)
+    assert e32 <= 1e-5, e32
+    assert e16 <= 1e-2, e16
+
+
+# ----------------------------------------------------------------------------- one bSB step
+@pytest.mark.parametrize("precision,tol", [(0, 1e-5), (1, 1e-2)])
+def test_steps_match_oracle(q, ctx, oracle, precision, tol):
+    import torch
+    fr = synth.hifi_region(1002, scale=0.06)
+    g = ctx.build_graph(fr, mode=q.MODE_READ)
+    og = oracle.read_graph(fr, oracle.READ_SIGNED)
+    blocks = oracle.blocks_of(og)
+    n_pad, pidx, c0 = g.layout()
+    R, steps, nsteps, t0 = 64, 200, 3, 50
+    x = np.zeros((R, n_pad), np.float32)
+    y = np.zeros((R, n_pad), np.float32)
+    refs = []
+    rng = np.random.default_rng(4)
+    # FP32 starts anywhere in the box (walls included); BF16 starts at the solver's
+    # initial amplitude, where no element reaches the wall within three steps, so a
+    # rounding difference cannot flip a clamp decision
+    amp = (0.9, 0.2) if precision == 0 else (0.1, 0.1)
+    for b, nodes in enumerate(blocks):
+        xb = rng.uniform(-amp[0], amp[0], (R, len(nodes)))
+        yb = rng.uniform(-amp[1], amp[1], (R, len(nodes)))
+        x[:, pidx[nodes]] = xb
+        y[:, pidx[nodes]] = yb
+        sub = og.subgraph(nodes)
+        x1, y1 = oracle.bsb_run(sub, x[:, pidx[nodes]].astype(np.float64),
+                                y[:, pidx[nodes]].astype(np.float64), t0, t0 + nsteps, steps,
+                                c0=float(c0[b]))
+        refs.append((nodes, x1, y1))
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    ctx.debug_steps(g, precision, R, xd, yd, t0, nsteps, steps, c0=c0)
+    xg, yg = xd.cpu().numpy(), yd.cpu().numpy()
+    for nodes, x1, y1 in refs:
+        dx = xg[:, pidx[nodes]] - x[:, pidx[nodes]]
+        dxr = x1 - x[:, pidx[nodes]]
+        assert _rel_frob(dx.astype(np.float64), dxr) <= tol
+        assert _rel_frob(yg[:, pidx[nodes]].astype(np.float64), y1) <= tol
+
+
+# ----------------------------------------------------------------------------- full solve
+def _check_solve(q, ctx, oracle, fr, precision, R, steps, seed, n_oracle=None):
+    g = ctx.build_graph(fr, mode=q.MODE_READ)
+    sol = ctx.solve(g, replicas=R, steps=steps, precision=precision, seed=seed)
+    og = oracle.read_graph(fr, oracle.READ_SIGNED)
+    blocks = oracle.blocks_of(og)
+    spins = sol.spins(g.n_nodes)
+    ridx = list(range(n_oracle or R))
+    for b, nodes in enumerate(blocks):
+        sub = og.subgraph(nodes)
+        info = sol.block(b, len(nodes))
+        # exact cut evaluation of the GPU's chosen spins
+        assert info["best_cut"] == oracle.cut(sub, spins[nodes])
+        assert np.array_equal(info["spins"], spins[nodes])
+        best, _, _, _ = oracle.bsb_solve(sub, ridx, steps, seed, b)
+        assert info["best_cut"] >= 0.999 * best, (b, info["best_cut"], best)
+    return g, sol
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_tiny_vs_oracle(q, ctx, oracle, precision):
+    fr = synth.tiny_reads(1001)
+    R = 32 if precision == 0 else 64
+    _check_solve(q, ctx, oracle, fr, precision, R, 2000, seed=11)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_region_vs_oracle(q, ctx, oracle, precision):
+    fr = synth.hifi_region(1002, scale=0.1)
+    _check_solve(q, ctx, oracle, fr, precision, 128, 1000, seed=3, n_oracle=16)
+
+
+def test_batched_blocks_vs_oracle(q, ctx, oracle):
+    fr = synth.batched_blocks(1004, n_blocks=10, n_min=20, n_max=400)
+    g, sol = _check_solve(q, ctx, oracle, fr, q.PREC_BF16, 64, 600, seed=5, n_oracle=16)
+    assert g.n_blocks >= 10
+
+
+def test_solution_cuts_are_exact_and_deterministic(q, ctx, oracle):
+    fr = synth.tiny_reads(1001)
+    g = ctx.build_graph(fr)
+    s1 = ctx.solve(g, replicas=64, steps=500, precision=q.PREC_BF16, seed=9)
+    s2 = ctx.solve(g, replicas=64, steps=500, precision=q.PREC_BF16, seed=9)
+    assert np.array_equal(s1.cuts(), s2.cuts())
+    assert np.array_equal(s1.spins(g.n_nodes), s2.spins(g.n_nodes))
+    c = s1.cuts()
+    for b in range(g.n_blocks):
+        info = s1.block(b)
+        assert info["best_cut"] == c[b].max()
+        assert info["best_replica"] == int(np.argmax(c[b]))
+
+
+def test_early_stop_and_auto_schedule(q, ctx):
+    fr = synth.tiny_reads(1001)
+    g = ctx.build_graph(fr)
+    sol = ctx.solve(g, replicas=64, steps=3000, precision=q.PREC_BF16, seed=2, check_every=50,
+                    patience=3)
+    runs = [sol.block(b)["steps_run"] for b in range(g.n_blocks)]
+    assert all(50 <= r <= 3000 for r in runs)
+    assert min(runs) < 3000
+    sol2 = ctx.solve(g, replicas=64, precision=q.PREC_FP32, seed=2, schedule=q.SCHED_AUTO)
+    assert all(sol2.block(b)["steps_run"] == 500 for b in range(g.n_blocks))
+
+
+# ----------------------------------------------------------------------------- phase
+@pytest.mark.parametrize("precision", [0, 1])
+def test_phase_read_matches_oracle_and_truth(q, ctx, oracle, precision):
+    fr = synth.tiny_reads(21, flip_p=0.0)
+    g = ctx.build_graph(fr)
+    sol = ctx.solve(g, replicas=64, steps=1000, precision=precision, seed=3)
+    h1, h2, bid = ctx.phase(g, sol, fr.n_snps)
+    se, he = metrics.switch_hamming(h1, bid, fr.truth)
+    assert se == 0.0 and he == 0.0
+    assert np.array_equal(h2, -h1)
+    # voting on the GPU's spins equals the oracle's voting on the same spins
+    bo, _ = g.blocks()
+    oh1, osb = oracle.vote(fr, sol.spins(g.n_nodes), bo, g.n_blocks)
+    assert np.array_equal(h1, oh1) and np.array_equal(bid, osb)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_phase_snp_refinement(q, ctx, oracle, precision):
+    fr = synth.region_reads(31, n_snps=150, region=50_000, n_reads=50, len_mean=8000,
+                            len_sd=2000, flip_p=0.0, miss_p=0.0, qual=(10, 30))
+    g = ctx.build_graph(fr, mode=q.MODE_SNP)
+    sol = ctx.solve(g, replicas=64, steps=300, precision=precision, seed=5, refine_max=15)
+    h1, h2, bid = ctx.phase(g, sol, fr.n_snps)
+    se, he = metrics.switch_hamming(h1, bid, fr.truth)
+    assert se == 0.0 and he == 0.0
+    # noisy input: the parity partition's cut matches the oracle's refinement within 0.999
+    fr2 = synth.region_reads(32, n_snps=150, region=50_000, n_reads=40, len_mean=8000,
+                             len_sd=2000, flip_p=0.08, miss_p=0.0, qual=(7, 30))
+    g2 = ctx.build_graph(fr2, mode=q.MODE_SNP)
+    sol2 = ctx.solve(g2, replicas=64, steps=300, precision=precision, seed=6, refine_max=15)
+    res = oracle.phase_snp(fr2, range(64), 300, seed=6, refine_max=15)
+    og = res["graph"]
+    for b, nodes in enumerate(res["blocks"]):
+        sub = og.subgraph(nodes)
+        p_or = np.where(res["C"][nodes] % 2 == 0, 1, -1).astype(np.int8)
+        info = sol2.block(b, len(nodes))
+        p_gpu = info["spins"]
+        assert info["best_cut"] == pytest.approx(oracle.cut(sub, p_gpu), rel=1e-12, abs=1e-9)
+        assert info["best_cut"] >= 0.999 * oracle.cut(sub, p_or) - 1e-9
+        assert info["best_cut"] >= 0.999 * res["first_cuts"][b] - 1e-9
+
+
+# ----------------------------------------------------------------------------- full size
+@pytest.mark.slow
+def test_full_size_hifi_region(q, ctx, oracle):
+    """The 7,200-read / 12,000-SNP workload at 1,024 replicas: exact graph, BF16 and FP32
+    J x X precision on all rows, and exact cut evaluation of the solve's spins."""
+    fr = synth.hifi_region(1002)
+    g = ctx.build_graph(fr)
+    og = oracle.read_graph(fr, oracle.READ_SIGNED)
+    r1, c1, w1 = _sorted_csr(*g.edges())
+    r2, c2, w2 = _oracle_edges(og)
+    assert np.array_equal(c1, c2) and np.array_equal(w1, w2)
+    e16 = _matvec_case(q, ctx, oracle, fr, q.MODE_READ, q.PREC_BF16, 1024)
+    e32 = _matvec_case(q, ctx, oracle, fr, q.MODE_READ, q.PREC_FP32, 256)
+    assert e16 <= 1e-2 and e32 <= 1e-5
+    sol = ctx.solve(g, replicas=1024, steps=1000, precision=q.PREC_BF16, seed=1)
+    spins = sol.spins(g.n_nodes)
+    for b, nodes in enumerate(oracle.blocks_of(og)):
+        sub = og.subgraph(nodes)
+        info = sol.block(b)
+        assert info["best_cut"] == oracle.cut(sub, spins[nodes])
