@@ -8,17 +8,6 @@
 #include "qh_internal.cuh"
 #include "util.cuh"
 
-struct qh_ctx {
-  qh::Ctx c;
-};
-struct qh_graph {
-  qh::Graph g;
-  qh_ctx* owner;
-};
-struct qh_solution {
-  qh::Solution s;
-};
-
 namespace qh {
 
 qh_status set_err(Ctx* ctx, qh_status st, const std::string& msg) {
@@ -202,7 +191,8 @@ void qh_destroy(qh_ctx* h) {
 
 void qh_graph_free(qh_graph* g) {
   if (!g) return;
-  if (g->owner) cudaStreamSynchronize(g->owner->c.stream);
+  // cudaFree waits for work in flight on the device; the owning context may already
+  // be gone, so nothing of it is touched here
   for (void* p : g->g.allocs) cudaFree(p);
   delete g;
 }

@@ -192,6 +192,18 @@ qh_status tc_prepare(Ctx* ctx);
 
 }  // namespace qh
 
+// Opaque handles of the C ABI.
+struct qh_ctx {
+  qh::Ctx c;
+};
+struct qh_graph {
+  qh::Graph g;
+  qh_ctx* owner;
+};
+struct qh_solution {
+  qh::Solution s;
+};
+
 #define QH_CUDA_TRY(expr)                                        \
   do {                                                           \
     cudaError_t _e = (expr);                                     \
