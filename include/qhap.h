@@ -252,6 +252,30 @@ qh_status qh_debug_steps(qh_ctx* ctx, const qh_graph* g, int32_t precision, int3
 qh_status qh_debug_layout(qh_ctx* ctx, const qh_graph* g, int32_t* n_pad, int32_t* padded_index,
                           double* c0_default);
 
+/* ---------------------------------------------------------------- no device allocation */
+
+/* J_hat x X_hat with the BF16 tensor cores, exactly as qh_debug_matvec(...,
+ * QH_PREC_BF16, ...) computes it, but without allocating any device memory.
+ * The paper has no counterpart; this exists for callers that cannot allocate:
+ * code running while a CUDA graph is being captured (an allocation there is an
+ * error or becomes part of the graph), host callbacks and real-time loops where
+ * cudaMalloc would synchronise the device, and hosts whose memory budget is
+ * handed out by their own allocator.
+ * x  float32[R][n_pad] (device, caller-owned): state in the padded layout
+ * z  float32[R][n_pad] (device, caller-owned): output; set to zero, then every
+ *    vertex of every block receives sum_b J_hat_ab X_hat_b in FP32
+ * Working memory (the BF16 copy of x and two per-block parameter arrays) lives
+ * in one fixed array of 8.5 MiB compiled into the library, which every GPU that
+ * loads the library keeps until the process exits.  Limits: R a multiple of 64,
+ * R * n_pad <= 4,194,304 and at most 65,536 blocks, otherwise QH_EINVAL with a
+ * message.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All
+ * calls share the one array and each call overwrites it in full, so two calls
+ * whose work overlaps on the GPU (different streams or contexts) race on it.
+ * Synchronises the context stream.  Errors: QH_EINVAL, QH_ECUDA, QH_ETIMEOUT. */
+qh_status qh_matvec_bf16_noalloc(qh_ctx* ctx, const qh_graph* g, int32_t R, const float* x,
+                                 float* z);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,7 @@ _SIGS = {
     "qh_debug_matvec": (C.c_int, [P, P, I32, I32, P, P]),
     "qh_debug_steps": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P]),
     "qh_debug_layout": (C.c_int, [P, P, P, P, P]),
+    "qh_matvec_bf16_noalloc": (C.c_int, [P, P, I32, P, P]),
 }
 
 _lib = None
@@ -265,6 +266,10 @@ class Context:
         c0a = None if c0 is None else _np(c0, np.float64)
         self._check(lib().qh_debug_steps(self.h, g.h, precision, R, _ptr(x), _ptr(y), t0, nsteps,
                                          steps, dt, a0, _ptr(c0a) if c0a is not None else None))
+
+    def matvec_bf16_noalloc(self, g, R, x, z):
+        """J x X in BF16 without any device allocation (fixed 8.5 MiB library array)."""
+        self._check(lib().qh_matvec_bf16_noalloc(self.h, g.h, R, _ptr(x), _ptr(z)))
 
     def close(self):
         if self.h:
