@@ -127,6 +127,26 @@ def cpu_baseline(fr, replicas=64, steps=1000, seed=1):
                       f"graph build + bSB + voting, {dt:.1f} s"}, res
 
 
+def _profiled_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, or None once the kernel
+    (its variant or its source file) differs from the one that was profiled."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "step_kernel_hifi_region.md")
+    src = os.path.join(ROOT, "paper_2603_25762_gb300", "csrc", "bsb_tc.cu")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch", "kernel",
+                                                   "source_sha256_16"):
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if fields.get("kernel") != kernel or fields.get("source_sha256_16") != sha:
+        return None
+    return int(fields["traffic_bytes_per_launch"])
+
+
 def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
@@ -163,7 +183,8 @@ def _count_kernels(fn):
             if ev.device_type.name == "CUDA" and "qh::" in ev.name:
                 n += 1
         return n if n > 0 else None
-    except Exception:
+    except Exception as e:  # the activity trace is optional: report why it is missing
+        print(f"kernel count unavailable: {e!r}", file=sys.stderr)
         return None
 
 
@@ -200,7 +221,8 @@ def run_ours(args):
             g = ctx.build_graph(arrays=pinned, on_device=False)
         else:
             g = ctx.build_graph(arrays=arrays_dev, on_device=True)
-        sol = ctx.solve(g, replicas=R, steps=T, precision=prec, seed=1, replica_base=base)
+        sol = ctx.solve(g, replicas=R, steps=T, precision=prec, seed=1, replica_base=base,
+                        step_kernel=args.step_kernel)
         if host:
             h = ctx.phase(g, sol, fr.n_snps)
             cut = sol.block(0)["best_cut"] if g.n_blocks else 0.0
@@ -223,6 +245,7 @@ def run_ours(args):
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+        k0 = qhap.kernel_launches()
         with ClockSampler(local) as clk:
             for _ in range(args.steps):
                 flush.fill_(1)
@@ -234,6 +257,7 @@ def run_ours(args):
                 times.append(ev0.elapsed_time(ev1))
                 step_ms.append(stats["timing"]["step_ms"] / stats["timing"]["n_step_launches"])
         torch.cuda.synchronize()
+        n_launched = qhap.kernel_launches() - k0
         units = stats["units"]
         # e2e through the C ABI with host buffers (pinned), copies inside the timed region
         pinned = tuple([fr.n_snps] + [torch.from_numpy(a).pin_memory() for a in
@@ -247,7 +271,7 @@ def run_ours(args):
             t0 = time.perf_counter()
             one_step(host=True, pinned=pinned_np)
             e2e.append((time.perf_counter() - t0) * 1e3)
-        n_kern = _count_kernels(lambda: one_step())
+        n_kern = _count_kernels(lambda: one_step())  # cross-check from the CUDA activity trace
     ms = statistics.mean(times)
     if ws > 1:
         import torch.distributed as dist
@@ -263,10 +287,7 @@ def run_ours(args):
     # state traffic per spin update + each stored J nonzero read once (BF16: 2 B, FP32: 4 B)
     per_launch_bytes = units / T * SPIN_BYTES + stats["nnz"] * (2 if prec else 4)
     achieved = per_launch_bytes / (launch_us * 1e-6) / 1e9
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "traffic_step_tc.json")
-    if os.path.exists(tp):
-        traffic = json.load(open(tp)).get("bytes_per_launch")
+    traffic = _profiled_traffic(stats["timing"]["kernel"])
     h2d = sum(int(a.nbytes) for a in pinned_np[1:])
     d2h = fr.n_snps * (1 + 1 + 4) + 8
     line = {
@@ -277,13 +298,15 @@ def run_ours(args):
         "phasing_wall_ms": ms,
         "e2e": {"value": units * ws / (e2e_ms / 1e3), "unit": "spin-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-        "roofline": {"bound": "hbm", "kernel": "k_step_tc" if prec else "k_step_f32",
+        "roofline": {"bound": "hbm", "kernel": stats["timing"]["kernel"],
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
                      "peak_source": src, "avg_launch_us": launch_us,
                      "algorithmic_bytes_per_launch": per_launch_bytes},
-        "gpu_launches": (n_kern * args.steps) if n_kern else None,
+        "gpu_launches": n_launched,
+        "gpu_launches_trace_per_step": n_kern,
         "clocks": clk.summary(),
+        "step_kernel_tuning": ctx.tuning_report(),
     }
     if not args.no_cpu_baseline:
         cb, _ = cpu_baseline(fr, replicas=args.ref_replicas, steps=T)
@@ -302,8 +325,10 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--replicas", type=int, default=1024)
     ap.add_argument("--bsb-steps", type=int, default=1000)
-    ap.add_argument("--ref-replicas", type=int, default=128)
+    ap.add_argument("--ref-replicas", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--step-kernel", default=None,
+                    help="pin the BF16 step-kernel variant (default: autotune)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

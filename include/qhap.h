@@ -170,6 +170,8 @@ typedef struct {
   int32_t patience;     /* stop a block after this many checks without a better
                            best-replica energy (0 = never stop early) */
   int32_t refine_max;   /* SNP mode: maximum refinement iterations (>= 1) */
+  int32_t step_kernel;  /* BF16: -1 = autotune, else a variant index 0..5 (see
+                           qh_solution_kernel for names); invalid choices -> QH_EINVAL */
 } qh_bsb_opts;
 
 /* Run multi-replica bSB on every block of the graph in one batched launch per
@@ -209,6 +211,20 @@ qh_status qh_solution_cuts(qh_ctx* ctx, const qh_solution* sol, double* cuts);
  *  spin_updates : sum over blocks of N_b * R * steps_run_b (all iterations) */
 qh_status qh_solution_timing(const qh_solution* sol, double* solve_ms, double* step_ms,
                              int64_t* n_step_launches, double* spin_updates);
+
+/* Name of the bSB step kernel the solve ran ("k_step_f32" for FP32; for BF16 the
+ * tensor-core variant the autotuner chose for this graph shape). */
+const char* qh_solution_kernel(const qh_solution* sol);
+
+/* Step-kernel autotuning of the context's latest new graph shape, as
+ * "variant=microseconds;..." ("" until a BF16 solve has tuned).  Tuning runs once
+ * per (replicas, tile layout) shape and context: each valid variant runs a few
+ * steps on the solve's own state, which is then re-initialised. */
+const char* qh_tuning_report(const qh_ctx* ctx);
+
+/* Number of CUDA kernels this library has launched in the process so far (every
+ * context; each replay of a captured step loop counts all of its kernels). */
+int64_t qh_kernel_launches(void);
 
 void qh_solution_free(qh_solution* sol);
 

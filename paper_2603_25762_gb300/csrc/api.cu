@@ -105,6 +105,55 @@ qh_status check_err_word(Ctx* ctx) {
   return QH_OK;
 }
 
+// Time every valid step-kernel variant on the live state for a few steps and keep
+// the fastest for this graph shape.  The state is re-initialised afterwards.
+qh_status autotune(Ctx* ctx, const Graph& g, StepArgs a, const SolveBufs& B, int R, TcPlan* plan) {
+  char kb[160];
+  snprintf(kb, sizeof kb, "%d|%d|%lld|%d|%d", R, g.n_row_tiles, (long long)g.n_tiles,
+           g.max_tiles_per_row, g.n_pad);
+  for (auto& kv : ctx->tuned)
+    if (kv.first == kb) {
+      plan->variant = kv.second;
+      return QH_OK;
+    }
+  cudaStream_t s = ctx->stream;
+  float best = 1e30f;
+  int best_v = -1;
+  std::string rep;
+  for (int v = 0; v < tc_n_variants(); ++v) {
+    if (!tc_variant_ok(v, g, R)) continue;
+    TcPlan p = *plan;
+    p.variant = v;
+    float ms = 0.f;
+    for (int rep_i = 0; rep_i < 2; ++rep_i) {  // warm-up pass, then the timed pass
+      QH_CUDA_TRY(cudaEventRecord(ctx->ev[2], s));
+      for (int k = 0; k < 6; ++k) {
+        a.t = k;
+        a.xh_out = (k % 2 == 0) ? B.xh1 : B.xh0;
+        qh_status st = launch_step_tc(ctx, g, a, (k % 2 == 0) ? B.xh0 : B.xh1, p);
+        if (st != QH_OK) return st;
+      }
+      QH_CUDA_TRY(cudaEventRecord(ctx->ev[3], s));
+      QH_CUDA_TRY(cudaEventSynchronize(ctx->ev[3]));
+      QH_CUDA_TRY(cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]));
+    }
+    ms /= 6.f;
+    char line[96];
+    snprintf(line, sizeof line, "%s%s=%.2fus", rep.empty() ? "" : ";", tc_variant_name(v), ms * 1e3f);
+    rep += line;
+    if (ms < best) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  qh_status st = check_err_word(ctx);
+  if (st != QH_OK) return st;
+  plan->variant = best_v;
+  ctx->tuned.emplace_back(kb, best_v);
+  ctx->tune_report = rep;
+  return QH_OK;
+}
+
 TcPlan pick_plan(int R) {
   TcPlan p;
   p.bn = (R % 128 == 0) ? 128 : 64;
@@ -287,6 +336,9 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   if (!(o->dt > 0.0) || !(o->a0 > 0.0)) return set_err(ctx, QH_EINVAL, "dt and a0 must be > 0");
   if (o->check_every < 0 || o->patience < 0 || o->replica_base < 0) return set_err(ctx, QH_EINVAL, "negative option");
   if ((int64_t)o->replica_base + R > (1 << 16)) return set_err(ctx, QH_EINVAL, "replica indices must stay below 65536");
+  if (o->precision == QH_PREC_BF16 && o->step_kernel >= 0 &&
+      (o->step_kernel >= tc_n_variants() || !tc_variant_ok(o->step_kernel, G, R)))
+    return set_err(ctx, QH_EINVAL, "step_kernel variant not valid for this graph and replica count");
   const bool snp = G.mode == QH_MODE_SNP;
   const int32_t refine_max = snp ? o->refine_max : 1;
   if (refine_max < 1) return set_err(ctx, QH_EINVAL, "refine_max must be >= 1");
@@ -380,6 +432,12 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   QH_CUDA_TRY(cudaMemcpyAsync(B.steps_b, h_steps.data(), nb * 4, cudaMemcpyHostToDevice, s));
   QH_CUDA_TRY(cudaMemcpyAsync(B.c0, h_c0.data(), nb * 4, cudaMemcpyHostToDevice, s));
   QH_CUDA_TRY(cudaMemsetAsync(B.C, 0, (G.n_nodes + 1) * 4, s));
+  // the second operand buffer is written at real vertices only: its padding columns
+  // must hold zeros (they meet the zero columns of J, and 0 * NaN would not vanish)
+  if (o->precision == QH_PREC_FP32)
+    QH_CUDA_TRY(cudaMemsetAsync(B.x1, 0, NS * 4, s));
+  else
+    QH_CUDA_TRY(cudaMemsetAsync(B.xh1, 0, NS * 2, s));
   QH_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, 4, s));
   std::vector<int32_t> ones(nb, 1);
   QH_CUDA_TRY(cudaMemcpyAsync(B.active, ones.data(), nb * 4, cudaMemcpyHostToDevice, s));
@@ -412,6 +470,22 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   a.err = ctx->d_err;
   const float* x_final = B.x;
   if (o->precision == QH_PREC_FP32 && (max_steps % 2 == 1)) x_final = B.x1;
+  TcPlan tplan = plan;
+  if (o->precision == QH_PREC_BF16) {
+    QH_CUDA_TRY(cudaMemcpyAsync(B.running, B.active, nb * 4, cudaMemcpyDeviceToDevice, s));
+    launch_init_state(s, W, R, o->replica_base, o->seed, 0, B.x, B.y, B.xh0, B.active);
+    qh_status st = QH_OK;
+    if (o->step_kernel >= 0)
+      tplan.variant = o->step_kernel;
+    else
+      st = autotune(ctx, W, a, B, R, &tplan);
+    if (st != QH_OK) {
+      delete sh;
+      return st;
+    }
+  }
+  sol.kernel = o->precision == QH_PREC_BF16 ? tc_variant_name(tplan.variant) : "k_step_f32";
+  skey += "|v" + std::to_string(tplan.variant);
   if (ctx->loop_key != skey || !ctx->loop_exec) {
     if (ctx->loop_exec) {
       cudaGraphExecDestroy(ctx->loop_exec);
@@ -419,12 +493,13 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     }
     ctx->loop_key.clear();
     cudaGraph_t graph;
+    const int64_t before = launches();
     QH_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     qh_status st = QH_OK;
     for (int32_t t = 0; t < max_steps && st == QH_OK; ++t) {
       a.t = t;
       const bool even = (t % 2) == 0;
-      st = run_step(ctx, W, o->precision, plan, a, even ? B.x : B.x1, even ? B.x1 : B.x,
+      st = run_step(ctx, W, o->precision, tplan, a, even ? B.x : B.x1, even ? B.x1 : B.x,
                     even ? B.xh0 : B.xh1, even ? B.xh1 : B.xh0);
       if (early && (t + 1) % o->check_every == 0 && t + 1 < max_steps) {
         const float* xc = (o->precision == QH_PREC_FP32 && even) ? B.x1 : B.x;
@@ -453,6 +528,9 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
       return cuda_fail(ctx, ce, "cudaGraphInstantiate");
     }
     ctx->loop_key = skey;
+    // the captured launches run on each replay, not at capture time
+    ctx->loop_kernels = launches() - before;
+    note_launch(-ctx->loop_kernels);
   }
   double step_ms_total = 0.0, spin_updates = 0.0;
   int64_t launches = 0;
@@ -472,6 +550,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
                       o->precision == QH_PREC_BF16 ? B.xh0 : nullptr, B.active);
     QH_CUDA_TRY(cudaEventRecord(ctx->ev[2], s));
     QH_CUDA_TRY(cudaGraphLaunch(ctx->loop_exec, s));
+    note_launch(ctx->loop_kernels);
     QH_CUDA_TRY(cudaEventRecord(ctx->ev[3], s));
     launch_signs(s, W, R, x_final, B.signs);
     launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.active);
@@ -639,6 +718,12 @@ qh_status qh_solution_timing(const qh_solution* sh, double* solve_ms, double* st
   return QH_OK;
 }
 
+const char* qh_solution_kernel(const qh_solution* sh) { return sh ? sh->s.kernel.c_str() : ""; }
+
+int64_t qh_kernel_launches(void) { return launches(); }
+
+const char* qh_tuning_report(const qh_ctx* h) { return h ? h->c.tune_report.c_str() : ""; }
+
 void qh_solution_free(qh_solution* sh) {
   if (!sh) return;
   for (void* p : sh->s.allocs) cudaFree(p);
@@ -786,6 +871,7 @@ qh_status qh_debug_steps(qh_ctx* h, const qh_graph* gh, int32_t precision, int32
     __nv_bfloat16* xh1 = (__nv_bfloat16*)ctx->scratch(NS * 2, S_XH1);
     if (!xh0 || !xh1) return set_err(ctx, QH_ENOMEM, "allocation failed (debug)");
     launch_f32_to_bf16(s, x, xh0, (int64_t)NS);
+    QH_CUDA_TRY(cudaMemsetAsync(xh1, 0, NS * 2, s));
     for (int32_t k = 0; k < nsteps; ++k) {
       a.t = t0 + k;
       a.xh_out = (k % 2 == 0) ? xh1 : xh0;

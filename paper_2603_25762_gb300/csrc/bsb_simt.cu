@@ -3,6 +3,7 @@
 //    GPU bSB), exact cut evaluation, replica selection, early stop,
 //  - SNP refinement (flip counter, sign inversion), read voting, parity swap.
 #include <algorithm>
+#include <type_traits>
 
 #include "qh_internal.cuh"
 #include "util.cuh"
@@ -162,7 +163,11 @@ __global__ void k_signs_t(const float* __restrict__ x, int32_t n_pad, int32_t R,
   }
 }
 
-// Warp per vertex a: node_val[pad(a)][r] = s_a * sum_b w_ab s_b (FP64, exact for integers).
+// Warp per vertex a: node_val[pad(a)][r] = s_a * sum_b w_ab s_b.  One pass over the
+// vertex's edges covers up to 1,024 replicas: lane l owns replicas 32 l .. 32 l + 31
+// (eight 4-byte sign loads per edge, the warp reading 1 KiB contiguous).  Integer
+// weights accumulate in int32 (row sums stay far below 2^31), real ones in FP64.
+template <bool INT>
 __global__ void k_cut_nodes(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                             const double* __restrict__ w, const int32_t* __restrict__ block_of,
                             const int32_t* __restrict__ pad_index, const int8_t* __restrict__ st,
@@ -172,50 +177,110 @@ __global__ void k_cut_nodes(int32_t n, const int64_t* __restrict__ rp, const int
   if (a >= n) return;
   int32_t b = block_of[a];
   if (b < 0 || (active != nullptr && !active[b])) return;
-  int32_t pa = pad_index[a];
-  for (int32_t r = lane; r < R; r += 32) {
-    double acc = 0.0;
-    for (int64_t e = rp[a]; e < rp[a + 1]; ++e) {
-      double we = w[e];
+  const int32_t pa = pad_index[a];
+  const int64_t e0 = rp[a], e1 = rp[a + 1];
+  const bool vec = (R & 3) == 0;
+  using Acc = typename std::conditional<INT, int32_t, double>::type;
+  for (int32_t r0 = 0; r0 < R; r0 += 1024) {
+    const int32_t r = r0 + 32 * lane;
+    const int nr = max(0, min(32, R - r));
+    Acc acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0;
+    for (int64_t e = e0; e < e1; ++e) {
+      const double we = w[e];
       if (we == 0.0) continue;  // zero edges may reach vertices outside every block
-      acc += we * (double)st[(size_t)pad_index[col[e]] * R + r];
+      if (nr == 0) continue;
+      const int8_t* sb = st + (size_t)pad_index[col[e]] * R + r;
+      if (vec && nr == 32) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          char4 c = *reinterpret_cast<const char4*>(sb + 4 * q);
+          if (INT) {
+            const int32_t wi = (int32_t)we;
+            acc[4 * q + 0] += wi * c.x;
+            acc[4 * q + 1] += wi * c.y;
+            acc[4 * q + 2] += wi * c.z;
+            acc[4 * q + 3] += wi * c.w;
+          } else {
+            acc[4 * q + 0] += we * (double)c.x;
+            acc[4 * q + 1] += we * (double)c.y;
+            acc[4 * q + 2] += we * (double)c.z;
+            acc[4 * q + 3] += we * (double)c.w;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+          if (k < nr) acc[k] += (Acc)(INT ? (double)(int32_t)we * sb[k] : we * (double)sb[k]);
+      }
     }
-    node_val[(size_t)pa * R + r] = (double)st[(size_t)pa * R + r] * acc;
+    const int8_t* sa = st + (size_t)pa * R + r;
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      if (k < nr) node_val[(size_t)pa * R + r + k] = (double)sa[k] * (double)acc[k];
   }
 }
 
-// Thread per (block, replica): cut = (sum_w - s^T W s) / 4, summed over the block's
-// vertices in padded order (fixed order: deterministic).
-__global__ void k_cut_reduce(int32_t nb, const int32_t* __restrict__ pad_off,
-                             const int64_t* __restrict__ block_ptr, int32_t R,
-                             const double* __restrict__ node_val, const double* __restrict__ sum_w,
-                             double* cuts, const int32_t* __restrict__ active) {
-  int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-  int32_t b = blockIdx.y;
-  if (r >= R || b >= nb) return;
+// CTA per (block, 32 replicas): 32 vertex slices per replica summed in a fixed
+// order, then the 32 slice sums in order: cut = (sum_w - s^T W s) / 4.
+__global__ void __launch_bounds__(1024) k_cut_reduce(int32_t nb, const int32_t* __restrict__ pad_off,
+                                                     const int64_t* __restrict__ block_ptr, int32_t R,
+                                                     const double* __restrict__ node_val,
+                                                     const double* __restrict__ sum_w, double* cuts,
+                                                     const int32_t* __restrict__ active) {
+  __shared__ double part[32][33];
+  const int32_t b = blockIdx.y;
   if (active != nullptr && !active[b]) return;
-  int32_t p0 = pad_off[b];
-  int32_t sz = (int32_t)(block_ptr[b + 1] - block_ptr[b]);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int32_t r = blockIdx.x * 32 + tx;
+  const int32_t p0 = pad_off[b];
+  const int32_t sz = (int32_t)(block_ptr[b + 1] - block_ptr[b]);
   double s = 0.0;
-  for (int32_t p = 0; p < sz; ++p) s += node_val[(size_t)(p0 + p) * R + r];
-  cuts[(size_t)b * R + r] = 0.25 * (sum_w[b] - s);
+  if (r < R)
+    for (int32_t p = ty; p < sz; p += 32) s += node_val[(size_t)(p0 + p) * R + r];
+  part[ty][tx] = s;
+  __syncthreads();
+  if (ty == 0 && r < R) {
+    double t = 0.0;
+    for (int k = 0; k < 32; ++k) t += part[k][tx];
+    cuts[(size_t)b * R + r] = 0.25 * (sum_w[b] - t);
+  }
 }
 
 __global__ void k_pick_best(int32_t nb, int32_t R, const double* __restrict__ cuts, int32_t* best_r,
                             double* best_cut, const int32_t* __restrict__ active) {
-  int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double sv[256];
+  __shared__ int32_t si[256];
+  const int32_t b = blockIdx.x;
   if (b >= nb || (active != nullptr && !active[b])) return;
-  double best = cuts[(size_t)b * R];
-  int32_t br = 0;
-  for (int32_t r = 1; r < R; ++r) {
+  double best = -INFINITY;
+  int32_t bi = INT32_MAX;
+  for (int32_t r = threadIdx.x; r < R; r += blockDim.x) {
     double c = cuts[(size_t)b * R + r];
-    if (c > best) {
+    if (c > best) {  // r ascends per thread: ties keep the lower replica
       best = c;
-      br = r;
+      bi = r;
     }
   }
-  best_r[b] = br;
-  best_cut[b] = best;
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      double v2 = sv[threadIdx.x + off];
+      int32_t i2 = si[threadIdx.x + off];
+      if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
+        sv[threadIdx.x] = v2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    best_r[b] = si[0];
+    best_cut[b] = sv[0];
+  }
 }
 
 __global__ void k_early_stop(int32_t nb, const double* __restrict__ best_cut, double* best_seen,
@@ -264,15 +329,28 @@ __global__ void k_node_sums(int32_t n, const int64_t* __restrict__ rp, const dou
 __global__ void k_block_sums(int32_t nb, const int64_t* __restrict__ block_ptr,
                              const int32_t* __restrict__ perm, const double* __restrict__ sw,
                              const double* __restrict__ sj2, double* sum_w, double* sum_j2) {
-  int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double ps[256], pq[256];
+  const int32_t b = blockIdx.x;
   if (b >= nb) return;
   double s = 0.0, q = 0.0;
-  for (int64_t k = block_ptr[b]; k < block_ptr[b + 1]; ++k) {
+  for (int64_t k = block_ptr[b] + threadIdx.x; k < block_ptr[b + 1]; k += blockDim.x) {
     s += sw[perm[k]];
     q += sj2[perm[k]];
   }
-  sum_w[b] = s;
-  sum_j2[b] = q;
+  ps[threadIdx.x] = s;
+  pq[threadIdx.x] = q;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      ps[threadIdx.x] += ps[threadIdx.x + off];
+      pq[threadIdx.x] += pq[threadIdx.x + off];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sum_w[b] = ps[0];
+    sum_j2[b] = pq[0];
+  }
 }
 
 // ------------------------------------------------------------------ SNP refinement
@@ -379,91 +457,94 @@ void launch_init_state(cudaStream_t s, const Graph& g, int32_t R, int32_t replic
                        const int32_t* active) {
   if (g.n_pad == 0 || R == 0) return;
   dim3 grid(nblk(g.n_pad), R);
-  k_init_state<<<grid, 256, 0, s>>>(g.rt, g.pad_node, g.local, g.n_pad, R, replica_base, seed, iter,
+  k_init_state<<<::qh::counted(grid), 256, 0, s>>>(g.rt, g.pad_node, g.local, g.n_pad, R, replica_base, seed, iter,
                                     x, y, xh, active);
 }
 
 void launch_f32_to_bf16(cudaStream_t s, const float* x, __nv_bfloat16* xh, int64_t n) {
-  if (n > 0) k_f32_to_bf16<<<nblk(n), 256, 0, s>>>(x, xh, n);
+  if (n > 0) k_f32_to_bf16<<<::qh::counted(nblk(n)), 256, 0, s>>>(x, xh, n);
 }
 
 void launch_step_f32(cudaStream_t s, const Graph& g, const StepArgs& a) {
   if (g.n_row_tiles == 0) return;
   dim3 grid(g.n_row_tiles, (a.R + F_RT - 1) / F_RT);
-  k_step_f32<<<grid, 256, 0, s>>>(a);
+  k_step_f32<<<::qh::counted(grid), 256, 0, s>>>(a);
 }
 
 void launch_signs(cudaStream_t s, const Graph& g, int32_t R, const float* x, int8_t* signs_t) {
   if (g.n_pad == 0) return;
   dim3 grid((g.n_pad + 31) / 32, (R + 31) / 32);
-  k_signs_t<<<grid, 256, 0, s>>>(x, g.n_pad, R, signs_t);
+  k_signs_t<<<::qh::counted(grid), 256, 0, s>>>(x, g.n_pad, R, signs_t);
 }
 
 void launch_cut(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t, const double* w,
                 const double* sum_w, double* node_val, double* cuts, const int32_t* active) {
   if (g.n_blocks == 0) return;
-  k_cut_nodes<<<nblk((int64_t)g.n_nodes * 32), 256, 0, s>>>(g.n_nodes, g.row_ptr, g.col, w,
-                                                             g.block_of, g.pad_index, signs_t, R,
-                                                             node_val, active);
-  dim3 grid(nblk(R, 128), g.n_blocks);
-  k_cut_reduce<<<grid, 128, 0, s>>>(g.n_blocks, g.pad_off, g.block_ptr, R, node_val, sum_w, cuts,
-                                    active);
+  if (g.integer_weights)
+    k_cut_nodes<true><<<::qh::counted(nblk((int64_t)g.n_nodes * 32)), 256, 0, s>>>(
+        g.n_nodes, g.row_ptr, g.col, w, g.block_of, g.pad_index, signs_t, R, node_val, active);
+  else
+    k_cut_nodes<false><<<::qh::counted(nblk((int64_t)g.n_nodes * 32)), 256, 0, s>>>(
+        g.n_nodes, g.row_ptr, g.col, w, g.block_of, g.pad_index, signs_t, R, node_val, active);
+  dim3 grid((R + 31) / 32, g.n_blocks);
+  k_cut_reduce<<<::qh::counted(grid), 1024, 0, s>>>(g.n_blocks, g.pad_off, g.block_ptr, R, node_val, sum_w, cuts,
+                                     active);
 }
 
 void launch_pick_best(cudaStream_t s, int32_t n_blocks, int32_t R, const double* cuts,
                       int32_t* best_r, double* best_cut, const int32_t* active) {
-  if (n_blocks > 0) k_pick_best<<<nblk(n_blocks), 256, 0, s>>>(n_blocks, R, cuts, best_r, best_cut, active);
+  if (n_blocks > 0) k_pick_best<<<::qh::counted(n_blocks), 256, 0, s>>>(n_blocks, R, cuts, best_r, best_cut, active);
 }
 
 void launch_early_stop(cudaStream_t s, int32_t n_blocks, const double* best_cut, double* best_seen,
                        int32_t* stall, int32_t* active, int32_t* steps_run, int32_t patience,
                        int32_t t_done) {
   if (n_blocks > 0)
-    k_early_stop<<<nblk(n_blocks), 256, 0, s>>>(n_blocks, best_cut, best_seen, stall, active,
+    k_early_stop<<<::qh::counted(nblk(n_blocks)), 256, 0, s>>>(n_blocks, best_cut, best_seen, stall, active,
                                                steps_run, patience, t_done);
 }
 
 void launch_extract_spins(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t,
                           const int32_t* best_r, int8_t* spins, const int32_t* active) {
   if (g.n_nodes > 0)
-    k_extract_spins<<<nblk(g.n_nodes), 256, 0, s>>>(g.n_nodes, g.block_of, g.pad_index, signs_t, R,
+    k_extract_spins<<<::qh::counted(nblk(g.n_nodes)), 256, 0, s>>>(g.n_nodes, g.block_of, g.pad_index, signs_t, R,
                                                     best_r, spins, active);
 }
 
 void launch_block_sums(cudaStream_t s, const Graph& g, const double* w, double* sum_w,
                        double* sum_j2, double* node_tmp) {
   if (g.n_blocks == 0) return;
-  k_node_sums<<<nblk(g.n_nodes), 256, 0, s>>>(g.n_nodes, g.row_ptr, w, node_tmp,
+  k_node_sums<<<::qh::counted(nblk(g.n_nodes)), 256, 0, s>>>(g.n_nodes, g.row_ptr, w, node_tmp,
                                               node_tmp + g.n_nodes);
-  k_block_sums<<<nblk(g.n_blocks), 256, 0, s>>>(g.n_blocks, g.block_ptr, g.perm, node_tmp,
-                                                node_tmp + g.n_nodes, sum_w, sum_j2);
+  k_block_sums<<<::qh::counted(g.n_blocks), 256, 0, s>>>(g.n_blocks, g.block_ptr, g.perm, node_tmp,
+                                          node_tmp + g.n_nodes, sum_w, sum_j2);
 }
 
 void launch_refine_prepare(cudaStream_t s, const Graph& g, const int8_t* spins,
                            const double* best_cut, int32_t* active, int32_t* C) {
   if (g.n_blocks > 0)
-    k_refine_prepare<<<nblk(g.n_blocks, 64), 64, 0, s>>>(g.n_blocks, g.block_ptr, g.perm, spins,
+    k_refine_prepare<<<::qh::counted(nblk(g.n_blocks, 64)), 64, 0, s>>>(g.n_blocks, g.block_ptr, g.perm, spins,
                                                         best_cut, active, C);
 }
 
 void launch_gauge(cudaStream_t s, const Graph& g, const int8_t* spins, double* w,
                   const int32_t* active) {
   if (g.n_nodes > 0)
-    k_gauge<<<nblk(g.n_nodes), 256, 0, s>>>(g.n_nodes, g.row_ptr, g.col, g.block_of, spins, w,
+    k_gauge<<<::qh::counted(nblk(g.n_nodes)), 256, 0, s>>>(g.n_nodes, g.row_ptr, g.col, g.block_of, spins, w,
                                             active);
 }
 
 void launch_vote(cudaStream_t s, const Graph& g, const int8_t* spins, int8_t* hap1, int8_t* hap2,
                  int32_t* block_id) {
   if (g.n_snps > 0)
-    k_vote<<<nblk(g.n_snps), 256, 0, s>>>(g.n_snps, g.cov_ptr, g.cov_frag, g.cov_allele,
+    k_vote<<<::qh::counted(nblk(g.n_snps)), 256, 0, s>>>(g.n_snps, g.cov_ptr, g.cov_frag, g.cov_allele,
                                           g.block_of, spins, hap1, hap2, block_id);
 }
 
 void launch_parity(cudaStream_t s, const Graph& g, const int32_t* C, int8_t* hap1, int8_t* hap2,
                    int32_t* block_id) {
   if (g.n_snps > 0)
-    k_parity<<<nblk(g.n_snps), 256, 0, s>>>(g.n_snps, g.block_of, C, hap1, hap2, block_id);
+    k_parity<<<::qh::counted(nblk(g.n_snps)), 256, 0, s>>>(g.n_snps, g.block_of, C, hap1, hap2, block_id);
 }
 
 }  // namespace qh

@@ -65,12 +65,51 @@ __global__ void k_cov_fill(int32_t m, const int64_t* __restrict__ fp, const int3
   }
 }
 
-// Insertion sort of each SNP's covering list by fragment index (lists are short).
-__global__ void k_cov_sort(int32_t n, const int64_t* __restrict__ cov_ptr, int32_t* cov_frag,
-                           int8_t* cov_allele) {
-  int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+// Sort each SNP's covering list by fragment index.  Warp per SNP: lists of up to
+// 256 entries are sorted in the warp's shared-memory slice (bitonic, keys
+// fragment << 8 | allele); longer ones (rare) by lane 0 in place.
+constexpr int COV_SORT_MAX = 256;
+
+__global__ void __launch_bounds__(256) k_cov_sort(int32_t n, const int64_t* __restrict__ cov_ptr,
+                                                  int32_t* cov_frag, int8_t* cov_allele) {
+  __shared__ int64_t keys[8][COV_SORT_MAX];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (s >= n) return;
   int64_t b = cov_ptr[s], e = cov_ptr[s + 1];
+  int32_t len = (int32_t)(e - b);
+  if (len <= 1) return;
+  if (len <= COV_SORT_MAX) {
+    int32_t N = 2;
+    while (N < len) N <<= 1;
+    int64_t* k = keys[w];
+    for (int i = lane; i < N; i += 32)
+      k[i] = i < len ? (((int64_t)cov_frag[b + i] << 8) | (int64_t)(uint8_t)(cov_allele[b + i] + 1))
+                     : INT64_MAX;
+    __syncwarp();
+    for (int kk = 2; kk <= N; kk <<= 1) {
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        for (int i = lane; i < N; i += 32) {
+          int l = i ^ j;
+          if (l > i) {
+            int64_t a0 = k[i], a1 = k[l];
+            bool up = (i & kk) == 0;
+            if ((a0 > a1) == up) {
+              k[i] = a1;
+              k[l] = a0;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    for (int i = lane; i < len; i += 32) {
+      cov_frag[b + i] = (int32_t)(k[i] >> 8);
+      cov_allele[b + i] = (int8_t)((int32_t)(k[i] & 0xff) - 1);
+    }
+    return;
+  }
+  if (lane != 0) return;
   for (int64_t i = b + 1; i < e; ++i) {
     int32_t f = cov_frag[i];
     int8_t a = cov_allele[i];
@@ -496,13 +535,31 @@ __global__ void k_tile_fill(int32_t n, const int64_t* __restrict__ rp, const int
 
 namespace {
 
+// Largest |w| and whether any weight is non-integer: block reduction, one atomic per CTA.
 __global__ void k_abs_max(int64_t nnz, const double* __restrict__ w, unsigned long long* out,
                           int32_t* nonint) {
-  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= nnz) return;
-  double v = fabs(w[e]);
-  atomicMax(out, (unsigned long long)__double_as_longlong(v));  // non-negative doubles order as ints
-  if (v != floor(v)) atomicOr(nonint, 1);
+  __shared__ double sm[256];
+  __shared__ int32_t sn;
+  if (threadIdx.x == 0) sn = 0;
+  double m = 0.0;
+  int32_t ni = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double v = fabs(w[e]);
+    m = fmax(m, v);
+    ni |= (v != floor(v)) ? 1 : 0;
+  }
+  sm[threadIdx.x] = m;
+  __syncthreads();
+  if (ni) sn = 1;
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + off]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicMax(out, (unsigned long long)__double_as_longlong(sm[0]));  // non-negative doubles order as ints
+    if (sn) atomicOr(nonint, 1);
+  }
 }
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -552,7 +609,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
   // ---- validate
   QH_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), s));
   if (m > 0)
-    k_validate<<<nblk(m), 256, 0, s>>>(m, n, g->frag_ptr, g->snp, g->allele, g->qual,
+    k_validate<<<::qh::counted(nblk(m)), 256, 0, s>>>(m, n, g->frag_ptr, g->snp, g->allele, g->qual,
                                        o->mode == QH_MODE_SNP && f->qual != nullptr ? 1 : 0,
                                        ctx->d_err);
   int32_t herr = 0;
@@ -566,7 +623,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
   {
     int32_t* cnt = (int32_t*)ctx->scratch(sizeof(int32_t) * (n + 1), 0);
     QH_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), s));
-    if (nnz_f > 0) k_cov_count<<<nblk(nnz_f), 256, 0, s>>>(nnz_f, g->snp, cnt);
+    if (nnz_f > 0) k_cov_count<<<::qh::counted(nblk(nnz_f)), 256, 0, s>>>(nnz_f, g->snp, cnt);
     g->cov_ptr = (int64_t*)dalloc(*g, sizeof(int64_t) * (n + 1));
     g->cov_frag = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max<int64_t>(nnz_f, 1));
     g->cov_allele = (int8_t*)dalloc(*g, std::max<int64_t>(nnz_f, 1));
@@ -574,9 +631,9 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     scan_i32_to_i64(s, cnt, g->cov_ptr, n);
     QH_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), s));
     if (m > 0)
-      k_cov_fill<<<nblk(m), 256, 0, s>>>(m, g->frag_ptr, g->snp, g->allele, g->cov_ptr, cnt,
+      k_cov_fill<<<::qh::counted(nblk(m)), 256, 0, s>>>(m, g->frag_ptr, g->snp, g->allele, g->cov_ptr, cnt,
                                          g->cov_frag, g->cov_allele);
-    if (n > 0) k_cov_sort<<<nblk(n), 256, 0, s>>>(n, g->cov_ptr, g->cov_frag, g->cov_allele);
+    if (n > 0) k_cov_sort<<<::qh::counted(nblk((int64_t)n * 32)), 256, 0, s>>>(n, g->cov_ptr, g->cov_frag, g->cov_allele);
   }
   // ---- edges
   if (o->mode == QH_MODE_READ) {
@@ -594,11 +651,11 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
       return set_err(ctx, QH_ENOMEM, "allocation failed (read graph scratch)");
     g->row_ptr = (int64_t*)dalloc(*g, sizeof(int64_t) * (m + 1));
     if (m > 0) {
-      k_first_last<<<nblk(m), 256, 0, s>>>(m, g->frag_ptr, g->snp, first, last, keys);
+      k_first_last<<<::qh::counted(nblk(m)), 256, 0, s>>>(m, g->frag_ptr, g->snp, first, last, keys);
       sort_u64(s, keys, m, cap);
-      k_unpack_order<<<nblk(m), 256, 0, s>>>(m, keys, last, order, sfirst, slast);
+      k_unpack_order<<<::qh::counted(nblk(m)), 256, 0, s>>>(m, keys, last, order, sfirst, slast);
       scan_max_i32(s, slast, pmax, m);
-      k_read_edges<0><<<nblk((int64_t)m * 32), 256, 0, s>>>(
+      k_read_edges<0><<<::qh::counted(nblk((int64_t)m * 32)), 256, 0, s>>>(
           m, g->frag_ptr, g->snp, g->allele, first, last, order, sfirst, slast, pmax,
           o->weight_mode, cnt, nullptr, nullptr, nullptr);
     }
@@ -609,7 +666,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     g->w = (double*)dalloc(*g, sizeof(double) * std::max<int64_t>(g->nnz, 1));
     if (!g->row_ptr || !g->col || !g->w) return set_err(ctx, QH_ENOMEM, "allocation failed (edges)");
     if (m > 0 && g->nnz > 0)
-      k_read_edges<1><<<nblk((int64_t)m * 32), 256, 0, s>>>(
+      k_read_edges<1><<<::qh::counted(nblk((int64_t)m * 32)), 256, 0, s>>>(
           m, g->frag_ptr, g->snp, g->allele, first, last, order, sfirst, slast, pmax,
           o->weight_mode, nullptr, g->row_ptr, g->col, g->w);
   } else {
@@ -617,7 +674,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     double* L = (double*)ctx->scratch(sizeof(double) * 94 * 94, 1);
     int64_t* cnt = (int64_t*)ctx->scratch(sizeof(int64_t) * (n + 1), 2);
     if (!L || !cnt) return set_err(ctx, QH_ENOMEM, "allocation failed (SNP graph scratch)");
-    k_llr_table<<<94, 94, 0, s>>>(L);
+    k_llr_table<<<::qh::counted(94), 94, 0, s>>>(L);
     QH_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), s));
     size_t smem = sizeof(SnpRowSmem);
     QH_CUDA_TRY(cudaFuncSetAttribute(k_snp_rows<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -626,7 +683,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     g->row_ptr = (int64_t*)dalloc(*g, sizeof(int64_t) * (n + 1));
     if (!g->row_ptr) return set_err(ctx, QH_ENOMEM, "allocation failed (edges)");
     if (n > 0)
-      k_snp_rows<0><<<grid, 512, smem, s>>>(n, g->frag_ptr, g->snp, g->allele, g->qual,
+      k_snp_rows<0><<<::qh::counted(grid), 512, smem, s>>>(n, g->frag_ptr, g->snp, g->allele, g->qual,
                                            g->is_porec, g->cov_ptr, g->cov_frag, L,
                                            o->porec_alpha, o->linkage_k, cnt, nullptr, nullptr,
                                            nullptr, ctx->d_err);
@@ -640,7 +697,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     g->w = (double*)dalloc(*g, sizeof(double) * std::max<int64_t>(g->nnz, 1));
     if (!g->col || !g->w) return set_err(ctx, QH_ENOMEM, "allocation failed (edges)");
     if (n > 0 && g->nnz > 0)
-      k_snp_rows<1><<<grid, 512, smem, s>>>(n, g->frag_ptr, g->snp, g->allele, g->qual,
+      k_snp_rows<1><<<::qh::counted(grid), 512, smem, s>>>(n, g->frag_ptr, g->snp, g->allele, g->qual,
                                            g->is_porec, g->cov_ptr, g->cov_frag, L,
                                            o->porec_alpha, o->linkage_k, nullptr, g->row_ptr,
                                            g->col, g->w, ctx->d_err);
@@ -651,7 +708,8 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     unsigned long long* amax = (unsigned long long*)ctx->scratch(16, 9);
     int32_t* nonint = (int32_t*)(amax + 1);
     QH_CUDA_TRY(cudaMemsetAsync(amax, 0, 16, s));
-    if (g->nnz > 0) k_abs_max<<<nblk(g->nnz), 256, 0, s>>>(g->nnz, g->w, amax, nonint);
+    if (g->nnz > 0)
+      k_abs_max<<<::qh::counted((unsigned)std::min<int64_t>(nblk(g->nnz), ctx->n_sm * 4)), 256, 0, s>>>(g->nnz, g->w, amax, nonint);
     unsigned long long hv[2] = {0, 0};
     QH_CUDA_TRY(cudaMemcpyAsync(hv, amax, 16, cudaMemcpyDeviceToHost, s));
     QH_CUDA_TRY(cudaStreamSynchronize(s));
@@ -679,10 +737,10 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
   QH_CUDA_TRY(cudaMemsetAsync(g->local, 0xff, sizeof(int32_t) * std::max(N, 1), s));
   QH_CUDA_TRY(cudaMemsetAsync(g->pad_index, 0xff, sizeof(int32_t) * std::max(N, 1), s));
   if (N > 0) {
-    k_uf_init<<<nblk(N), 256, 0, s>>>(N, parent);
-    k_uf_hook<<<nblk(N), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, parent);
-    k_uf_compress<<<nblk(N), 256, 0, s>>>(N, parent, label, csize);
-    k_block_roots<<<nblk(N), 256, 0, s>>>(N, label, csize, isroot);
+    k_uf_init<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, parent);
+    k_uf_hook<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, parent);
+    k_uf_compress<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, parent, label, csize);
+    k_block_roots<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, label, csize, isroot);
   }
   scan_i32_to_i64(s, isroot, rrank, N);
   int64_t nb64 = 0;
@@ -693,8 +751,8 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
   int32_t* bsize = (int32_t*)ctx->scratch(sizeof(int32_t) * std::max(nb, 1), 16);
   if (!bsize) return set_err(ctx, QH_ENOMEM, "allocation failed (block sizes)");
   if (N > 0) {
-    k_block_of<<<nblk(N), 256, 0, s>>>(N, label, csize, rrank, g->block_of, bkeys);
-    k_block_sizes<<<nblk(N), 256, 0, s>>>(N, label, csize, rrank, bsize);
+    k_block_of<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, label, csize, rrank, g->block_of, bkeys);
+    k_block_sizes<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, label, csize, rrank, bsize);
     sort_u64(s, bkeys, N, kcap);
   }
   g->h_block_size.assign(nb, 0);
@@ -739,7 +797,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     QH_CUDA_TRY(cudaMemcpyAsync(d_T, h_T.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
   QH_CUDA_TRY(cudaMemsetAsync(g->pad_node, 0xff, sizeof(int32_t) * std::max(g->n_pad, 1), s));
   if (total_in_blocks > 0)
-    k_perm_local<<<nblk(total_in_blocks), 256, 0, s>>>(total_in_blocks, bkeys, g->block_ptr,
+    k_perm_local<<<::qh::counted(nblk(total_in_blocks)), 256, 0, s>>>(total_in_blocks, bkeys, g->block_ptr,
                                                         g->pad_off, g->perm, g->local,
                                                         g->pad_index, g->pad_node);
   // ---- tile slots: flag nonzero 128 x 128 tiles (all of them in dense mode)
@@ -751,7 +809,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
   } else {
     QH_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int32_t) * std::max<int64_t>(n_slots, 1), s));
     if (N > 0)
-      k_tile_flags<<<nblk(N), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, g->block_of, g->local,
+      k_tile_flags<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, g->block_of, g->local,
                                           d_slot_off, d_T, flags);
   }
   scan_i32_to_i64(s, flags, slot_tile, n_slots);
@@ -785,6 +843,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
       for (int rep = 0; rep < (g->has_lo ? 2 : 1); ++rep)
         h_tile_col.insert(h_tile_col.end(), cols.begin(), cols.end());
       entry += rt.n_all;
+      g->max_tiles_per_row = std::max(g->max_tiles_per_row, rt.n_all);
       g->h_rt.push_back(rt);
     }
   }
@@ -849,7 +908,7 @@ qh_status retile(Ctx* ctx, Graph* g, const double* w, __nv_bfloat16* tb, float* 
   if (g->n_tiles_hi > 0)
     QH_CUDA_TRY(cudaMemsetAsync(tf, 0, sizeof(float) * TILE * TILE * g->n_tiles_hi, s));
   if (g->n_nodes > 0 && g->n_tiles > 0)
-    k_tile_fill<<<nblk(g->n_nodes), 256, 0, s>>>(g->n_nodes, g->row_ptr, g->col, w, g->block_of,
+    k_tile_fill<<<::qh::counted(nblk(g->n_nodes)), 256, 0, s>>>(g->n_nodes, g->row_ptr, g->col, w, g->block_of,
                                                  g->local, g->slot_off, g->tiles_per_block,
                                                  g->slot_tile, g->rt, g->rt_of_block,
                                                  g->has_lo ? 1 : 0, tb, tf);

@@ -86,7 +86,7 @@ extern "C" qh_status qh_matvec_bf16_noalloc(qh_ctx* h, const qh_graph* gh, int32
   e = cudaMemsetAsync(ctx->d_err, 0, 4, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(err)");
   if (g.n_blocks > 0)
-    k_fill_block_params<<<(g.n_blocks + 255) / 256, 256, 0, s>>>(g.n_blocks, steps_b, c0);
+    k_fill_block_params<<<::qh::counted((g.n_blocks + 255) / 256), 256, 0, s>>>(g.n_blocks, steps_b, c0);
   // X_hat = bf16(x) over the whole R x n_pad extent: nothing of a previous call survives
   launch_f32_to_bf16(s, x, xh, elems);
   StepArgs a{};

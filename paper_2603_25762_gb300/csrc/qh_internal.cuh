@@ -13,6 +13,16 @@
 
 namespace qh {
 
+// Kernel-launch counter of this process (every launch site wraps its grid in
+// counted(); replays of a captured step loop add the loop's kernel count).
+void note_launch(int64_t n = 1);
+int64_t launches();
+template <class G>
+inline G counted(G grid) {
+  note_launch();
+  return grid;
+}
+
 constexpr int TILE = 128;           // J tile edge (rows = MMA M, columns = 2 x 64 K-slices)
 constexpr int SNP_ROW_CAP = 8192;   // max fragment terms gathered for one SNP row
 
@@ -74,6 +84,7 @@ struct Graph {
   int64_t n_tiles = 0;            // all BF16 entries (hi + lo)
   int64_t n_tiles_hi = 0;         // FP32 tiles
   bool has_lo = false;
+  int32_t max_tiles_per_row = 0;  // largest n_all over row tiles
   RowTile* rt = nullptr;          // [n_row_tiles]
   int32_t* rt_of_block = nullptr; // [n_blocks] first row tile of the block
   int32_t* tile_col = nullptr;    // [n_tiles] column tile (padded col / 128)
@@ -102,6 +113,7 @@ struct Solution {
   std::vector<int32_t> C;                // SNP mode flip counts [n_nodes]
   double solve_ms = 0, step_ms = 0, spin_updates = 0;
   int64_t n_step_launches = 0;
+  std::string kernel;                    // step kernel that ran
   std::vector<int32_t> block_size;
   std::vector<int64_t> block_ptr;        // host copy for per-block extraction
   std::vector<int32_t> perm;             // vertices of each block, ascending (host copy)
@@ -123,6 +135,10 @@ struct Ctx {
   // one captured step loop, replayed while its shape is unchanged
   cudaGraphExec_t loop_exec = nullptr;
   std::string loop_key;
+  int64_t loop_kernels = 0;  // kernels launched by one replay of loop_exec
+  // step-kernel autotuning: shape key -> chosen variant, and the last report
+  std::vector<std::pair<std::string, int>> tuned;
+  std::string tune_report;
   void* scratch(size_t bytes, int slot);
 };
 
@@ -184,10 +200,14 @@ void launch_f32_to_bf16(cudaStream_t s, const float* x, __nv_bfloat16* xh, int64
 struct TcPlan {
   int bn = 128;     // replicas per CTA (MMA N)
   int stages = 3;   // TMA/MMA pipeline depth
+  int variant = -1;  // solver-step kernel variant (autotuned); -1 = the plain kernel
 };
 qh_status launch_step_tc(Ctx* ctx, const Graph& g, const StepArgs& a,
                          const __nv_bfloat16* xh_in, const TcPlan& plan);
 bool tc_plan_ok(int R, const TcPlan& plan);
+int tc_n_variants();
+const char* tc_variant_name(int v);
+bool tc_variant_ok(int v, const Graph& g, int R);
 qh_status tc_prepare(Ctx* ctx);
 
 }  // namespace qh

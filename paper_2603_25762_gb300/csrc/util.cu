@@ -1,7 +1,14 @@
 // Scans and a bitonic sort used by the graph build (single-pass, deterministic).
+#include <atomic>
+
+#include "qh_internal.cuh"
 #include "util.cuh"
 
 namespace qh {
+
+static std::atomic<int64_t> g_launches{0};
+void note_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
@@ -109,27 +116,27 @@ int64_t next_pow2(int64_t n) {
 }
 
 void scan_i64(cudaStream_t s, const int64_t* in, int64_t* out, int64_t n) {
-  k_scan_excl<int64_t><<<1, SCAN_THREADS, 0, s>>>(in, out, n);
+  k_scan_excl<int64_t><<<::qh::counted(1), SCAN_THREADS, 0, s>>>(in, out, n);
 }
 void scan_i32_to_i64(cudaStream_t s, const int32_t* in, int64_t* out, int64_t n) {
-  k_scan_excl<int32_t><<<1, SCAN_THREADS, 0, s>>>(in, out, n);
+  k_scan_excl<int32_t><<<::qh::counted(1), SCAN_THREADS, 0, s>>>(in, out, n);
 }
 void scan_max_i32(cudaStream_t s, const int32_t* in, int32_t* out, int64_t n) {
-  if (n > 0) k_scan_max<<<1, SCAN_THREADS, 0, s>>>(in, out, n);
+  if (n > 0) k_scan_max<<<::qh::counted(1), SCAN_THREADS, 0, s>>>(in, out, n);
 }
 
 void sort_u64(cudaStream_t s, uint64_t* keys, int64_t n, int64_t cap) {
   if (n <= 1) return;
   int64_t N = next_pow2(n < BSORT_LOCAL ? BSORT_LOCAL : n);
   (void)cap;
-  if (N > n) k_fill_u64<<<(unsigned)((N - n + 255) / 256), 256, 0, s>>>(keys, n, N, ~0ull);
+  if (N > n) k_fill_u64<<<::qh::counted((unsigned)((N - n + 255) / 256)), 256, 0, s>>>(keys, n, N, ~0ull);
   unsigned nb_local = (unsigned)(N / BSORT_LOCAL);
   // all stages with k <= BSORT_LOCAL in shared memory
-  k_bitonic_local<<<nb_local, 512, 0, s>>>(keys, N, 0, 0);
+  k_bitonic_local<<<::qh::counted(nb_local), 512, 0, s>>>(keys, N, 0, 0);
   for (int64_t k = 2 * BSORT_LOCAL; k <= N; k <<= 1) {
     for (int64_t j = k >> 1; j >= BSORT_LOCAL; j >>= 1)
-      k_bitonic_global<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(keys, N, k, j);
-    k_bitonic_local<<<nb_local, 512, 0, s>>>(keys, N, k, BSORT_LOCAL >> 1);
+      k_bitonic_global<<<::qh::counted((unsigned)((N + 255) / 256)), 256, 0, s>>>(keys, N, k, j);
+    k_bitonic_local<<<::qh::counted(nb_local), 512, 0, s>>>(keys, N, k, BSORT_LOCAL >> 1);
   }
 }
 

@@ -46,7 +46,11 @@ class QhBsbOpts(C.Structure):
     _fields_ = [("replicas", C.c_int32), ("steps", C.c_int32), ("schedule", C.c_int32),
                 ("precision", C.c_int32), ("dt", C.c_double), ("a0", C.c_double),
                 ("c0", C.c_double), ("seed", C.c_uint64), ("replica_base", C.c_int32),
-                ("check_every", C.c_int32), ("patience", C.c_int32), ("refine_max", C.c_int32)]
+                ("check_every", C.c_int32), ("patience", C.c_int32), ("refine_max", C.c_int32),
+                ("step_kernel", C.c_int32)]
+
+STEP_KERNELS = ["cta-bn128-s3", "cta-bn128-s2-x3", "cta-bn64-s2-x4", "cta-bn256-s2-x2",
+                "persistent-bn128", "persistent-bn64-tma-state"]
 
 
 class QhError(RuntimeError):
@@ -81,6 +85,9 @@ _SIGS = {
     "qh_debug_steps": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P]),
     "qh_debug_layout": (C.c_int, [P, P, P, P, P]),
     "qh_matvec_bf16_noalloc": (C.c_int, [P, P, I32, P, P]),
+    "qh_solution_kernel": (C.c_char_p, [P]),
+    "qh_tuning_report": (C.c_char_p, [P]),
+    "qh_kernel_launches": (C.c_int64, []),
 }
 
 _lib = None
@@ -106,6 +113,11 @@ def __getattr__(name):
     if name in _SIGS:
         return getattr(lib(), name)
     raise AttributeError(name)
+
+
+def kernel_launches():
+    """CUDA kernels libqhap has launched in this process."""
+    return int(lib().qh_kernel_launches())
 
 
 def _ptr(a):
@@ -193,7 +205,8 @@ class Solution:
     def timing(self):
         a, b, n, su = D(), D(), I64(), D()
         lib().qh_solution_timing(self.h, C.byref(a), C.byref(b), C.byref(n), C.byref(su))
-        return {"solve_ms": a.value, "step_ms": b.value, "n_step_launches": n.value,
+        return {"kernel": lib().qh_solution_kernel(self.h).decode(),
+                "solve_ms": a.value, "step_ms": b.value, "n_step_launches": n.value,
                 "spin_updates": su.value}
 
     def free(self):
@@ -239,9 +252,11 @@ class Context:
 
     def solve(self, g, replicas=32, steps=1000, precision=PREC_FP32, seed=1, dt=1.0, a0=1.0,
               c0=0.0, schedule=SCHED_LINEAR, replica_base=0, check_every=0, patience=0,
-              refine_max=15):
+              refine_max=15, step_kernel=None):
+        """step_kernel: None = autotune, or a name from STEP_KERNELS (BF16 only)."""
+        sk = -1 if step_kernel is None else STEP_KERNELS.index(step_kernel)
         o = QhBsbOpts(replicas, steps, schedule, precision, dt, a0, c0, seed, replica_base,
-                      check_every, patience, refine_max)
+                      check_every, patience, refine_max, sk)
         s = C.c_void_p()
         self._check(lib().qh_bsb_solve(self.h, g.h, C.byref(o), C.byref(s)))
         return Solution(self, s, g.n_blocks, replicas)
@@ -270,6 +285,9 @@ class Context:
     def matvec_bf16_noalloc(self, g, R, x, z):
         """J x X in BF16 without any device allocation (fixed 8.5 MiB library array)."""
         self._check(lib().qh_matvec_bf16_noalloc(self.h, g.h, R, _ptr(x), _ptr(z)))
+
+    def tuning_report(self):
+        return lib().qh_tuning_report(self.h).decode()
 
     def close(self):
         if self.h:
