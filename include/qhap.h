@@ -120,8 +120,8 @@ typedef struct {
  * connected components with >= 2 vertices become phase blocks, numbered by
  * their smallest vertex; single-vertex components are dropped.
  * Errors: QH_EINVAL (malformed fragments, Q outside [4, 93] in SNP mode,
- * bad options), QH_ENOMEM, QH_ECUDA, QH_EUNSUPPORTED (an SNP row gathering more
- * than 8192 fragment terms). */
+ * bad options), QH_ENOMEM, QH_ECUDA, QH_EUNSUPPORTED (an SNP row whose covering
+ * fragments span more than 12,288 SNPs and gather more than 8,192 terms). */
 qh_status qh_build_graph(qh_ctx* ctx, const qh_fragments* frags, const qh_graph_opts* opts,
                          qh_graph** out);
 

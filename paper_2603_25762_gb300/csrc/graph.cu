@@ -260,12 +260,100 @@ __global__ void __launch_bounds__(512) k_snp_rows(
   __shared__ int32_t s_off[1025];
   __shared__ int32_t s_total;
   __shared__ int32_t s_runs[512];
+  __shared__ int32_t s_w0, s_w1;
   for (int32_t u = blockIdx.x; u < n; u += gridDim.x) {
     int64_t cb = cov_ptr[u], ce = cov_ptr[u + 1];
     int32_t ncov = (int32_t)(ce - cb);
-    // per covering fragment: number of partners inside the linkage window
-    if (threadIdx.x == 0) s_total = 0;
+    // SNP window spanned by the covering fragments
+    if (threadIdx.x == 0) {
+      s_w0 = INT32_MAX;
+      s_w1 = -1;
+      s_total = 0;
+    }
     __syncthreads();
+    {
+      int32_t w0 = INT32_MAX, w1 = -1;
+      for (int32_t c = threadIdx.x; c < ncov; c += blockDim.x) {
+        int32_t i = cov_frag[cb + c];
+        w0 = min(w0, snp[fp[i]]);
+        w1 = max(w1, snp[fp[i + 1] - 1]);
+      }
+      if (w1 >= 0) {
+        atomicMin(&s_w0, w0);
+        atomicMax(&s_w1, w1);
+      }
+    }
+    __syncthreads();
+    const int32_t w0 = s_w0, W = s_w1 - s_w0 + 1;
+    if (ncov > 0 && W <= SNP_DENSE_CAP) {
+      // Dense window: acc[v - w0] summed fragment by fragment in fragment order (the
+      // partners of one fragment are distinct, so its terms go in parallel).
+      double* acc = reinterpret_cast<double*>(smem_raw);
+      uint8_t* touched = reinterpret_cast<uint8_t*>(acc + SNP_DENSE_CAP);
+      for (int32_t t = threadIdx.x; t < W; t += blockDim.x) {
+        acc[t] = 0.0;
+        touched[t] = 0;
+      }
+      __syncthreads();
+      for (int32_t c = 0; c < ncov; ++c) {
+        const int32_t i = cov_frag[cb + c];
+        const int64_t fb = fp[i], fe = fp[i + 1];
+        const int32_t S = (int32_t)(fe - fb);
+        const int32_t depth = (int32_t)(((int64_t)linkage_k * (S - 1)) / 10);
+        int64_t l = fb, h = fe;
+        while (l < h) {
+          int64_t mid = (l + h) >> 1;
+          if (snp[mid] < u) l = mid + 1; else h = mid;
+        }
+        const int32_t p = (int32_t)(l - fb);
+        const int32_t lo = max(0, p - depth), hi = min(S - 1, p + depth);
+        const int64_t eu = fb + p;
+        const double a = (is_porec != nullptr && is_porec[i]) ? alpha : 1.0;
+        for (int32_t pp = lo + threadIdx.x; pp <= hi; pp += blockDim.x) {
+          if (pp == p) continue;
+          const int64_t ev = fb + pp;
+          const double lv = L[(int)qual[eu] * 94 + (int)qual[ev]];
+          const double sg = ((int)allele[eu] * (int)allele[ev] > 0) ? 1.0 : -1.0;
+          const double term = -(a * (sg * lv)) / (double)(S - 1);
+          const int32_t k = snp[ev] - w0;
+          acc[k] += term;
+          touched[k] = 1;
+        }
+        __syncthreads();
+      }
+      // compaction in ascending partner order: per-thread contiguous chunk + block scan
+      const int32_t chunk = (W + blockDim.x - 1) / blockDim.x;
+      const int32_t t0 = threadIdx.x * chunk, t1 = min(W, t0 + chunk);
+      int32_t mine = 0;
+      for (int32_t t = t0; t < t1; ++t) mine += touched[t];
+      // block exclusive scan of `mine` (warp shuffles, then the warp totals)
+      int32_t incl = mine;
+      for (int off = 1; off < 32; off <<= 1) {
+        int32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+        if ((threadIdx.x & 31) >= off) incl += v;
+      }
+      if ((threadIdx.x & 31) == 31) s_runs[threadIdx.x >> 5] = incl;
+      __syncthreads();
+      int32_t warp_before = 0, total = 0;
+      for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) {
+        if (wi < (int)(threadIdx.x >> 5)) warp_before += s_runs[wi];
+        total += s_runs[wi];
+      }
+      if (PASS == 1) {
+        int64_t out = row_ptr[u] + warp_before + incl - mine;
+        for (int32_t t = t0; t < t1; ++t)
+          if (touched[t]) {
+            col[out] = w0 + t;
+            w[out] = acc[t];
+            ++out;
+          }
+      } else if (threadIdx.x == 0) {
+        cnt[u] = total;
+      }
+      __syncthreads();
+      continue;
+    }
+    // per covering fragment: number of partners inside the linkage window
     int32_t base = 0;
     for (int32_t c0 = 0; c0 < ncov; c0 += 1024) {
       int32_t cn = min(1024, ncov - c0);

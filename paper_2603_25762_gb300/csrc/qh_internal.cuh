@@ -24,7 +24,8 @@ inline G counted(G grid) {
 }
 
 constexpr int TILE = 128;           // J tile edge (rows = MMA M, columns = 2 x 64 K-slices)
-constexpr int SNP_ROW_CAP = 8192;   // max fragment terms gathered for one SNP row
+constexpr int SNP_ROW_CAP = 8192;   // max fragment terms gathered for one SNP row (sort path)
+constexpr int SNP_DENSE_CAP = 12288;  // max SNP window of one row for the dense path
 
 // Device error word bits (set by kernels, read back by the host).
 enum : int32_t {

@@ -81,6 +81,29 @@ def test_snp_graph_porec_parity(q, ctx, oracle):
     np.testing.assert_allclose(w1, w2, rtol=1e-12, atol=1e-15)
 
 
+def test_snp_graph_wide_rows_parity(q, ctx, oracle):
+    # contacts spanning more than 12,288 SNP indices: those rows take the sorting path
+    rng = np.random.default_rng(8)
+    n = 30_000
+    rows = []
+    for i in range(300):
+        k = int(rng.integers(2, 7))
+        snps = np.sort(rng.choice(n, size=k, replace=False))
+        rows.append(snps)
+    ptr = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    snp = np.concatenate(rows).astype(np.int32)
+    allele = np.where(rng.random(snp.size) < 0.5, 1, -1).astype(np.int8)
+    qual = rng.integers(7, 31, size=snp.size).astype(np.uint8)
+    porec = (rng.random(len(rows)) < 0.5).astype(np.uint8)
+    fr = synth.Fragments(n, ptr, snp, allele, qual, porec, np.arange(n), np.ones(n, np.int8))
+    g = ctx.build_graph(fr, mode=q.MODE_SNP, porec_alpha=0.1)
+    r1, c1, w1 = _sorted_csr(*g.edges())
+    og = oracle.snp_graph(fr, 0.1, 10)
+    r2, c2, w2 = _oracle_edges(og)
+    assert np.array_equal(r1, r2) and np.array_equal(c1, c2)
+    np.testing.assert_allclose(w1, w2, rtol=1e-12, atol=1e-15)
+
+
 @pytest.mark.parametrize("mode", ["read", "snp"])
 def test_components_match_oracle(q, ctx, oracle, mode):
     fr = synth.region_reads(77, n_snps=800, region=600_000, n_reads=90, len_mean=6000,
