@@ -102,29 +102,58 @@ def _dist():
     return ws, rank
 
 
+WORKLOADS = {
+    # name: (generator, mode, replicas, bsb steps, description)
+    "hifi-region": ("hifi_region", "read", 1024, 1000,
+                    "hifi-region: 12,000 SNPs / 4 Mb, 7,200 reads, signed read graph"),
+    "ont-snp": ("ont_region", "snp", 512, 2000,
+                "ont-snp: 12,000 SNPs / 4 Mb, 3,600 ONT-like reads, SNP graph + refinement"),
+    "batched-blocks": ("batched_blocks", "read", 256, 1000,
+                       "batched-blocks: 512 HiFi-like blocks of 50-6,000 reads, one launch per step"),
+}
+SEEDS = {"hifi_region": 1002, "ont_region": 1003, "batched_blocks": 1004}
+
+
 def _workload(args):
     from paper_2603_25762_gb300 import synth
-    fr = synth.hifi_region(1002)
-    cfg = {"workload": "hifi-region: 12,000 SNPs / 4 Mb, 7,200 reads, signed read graph",
-           "n_reads": fr.n_frags, "n_snps": fr.n_snps, "replicas": args.replicas,
-           "bsb_steps": args.bsb_steps, "precision": args.precision,
+    gen, mode, R, T, desc = WORKLOADS[args.workload]
+    fr = getattr(synth, gen)(SEEDS[gen])
+    R = args.replicas or R
+    T = args.bsb_steps or T
+    cfg = {"workload": desc, "mode": mode, "n_reads": fr.n_frags, "n_snps": fr.n_snps,
+           "replicas": R, "bsb_steps": T, "precision": args.precision,
            "l2": "flushed between timed steps (256 MiB write)"}
-    return fr, cfg
+    return fr, cfg, mode, R, T
 
 
-def cpu_baseline(fr, replicas=64, steps=1000, seed=1):
-    """The FP64 oracle, as it stands, on the host cores: read graph, blocks, bSB on a
-    replica subset with the full step count, voting."""
+def cpu_baseline(args, fr, mode, steps, seed=1):
+    """The FP64 oracle, as it stands, on the host cores: graph, blocks, bSB on a replica
+    subset with the full step count, then voting or refinement + parity."""
     from oracle import oracle as o
+    from paper_2603_25762_gb300 import synth
     o.build()
+    reps = args.ref_replicas
+    if args.workload == "hifi-region":
+        sample_fr, what = fr, f"full graph ({fr.n_frags} reads)"
+    elif args.workload == "ont-snp":
+        sample_fr = synth.ont_region(1003, scale=0.25)
+        what = f"quarter-size region ({sample_fr.n_frags} reads, {sample_fr.n_snps} SNPs)"
+        reps = min(reps, 32)
+    else:
+        sample_fr = synth.batched_blocks(1004, n_blocks=16)
+        what = "first 16 of the 512 blocks"
+        reps = min(reps, 64)
     t0 = time.perf_counter()
-    res = o.phase_read(fr, o.READ_SIGNED, range(replicas), steps, seed=seed)
+    if mode == "read":
+        res = o.phase_read(sample_fr, o.READ_SIGNED, range(reps), steps, seed=seed)
+        units = sum(len(b) for b in res["blocks"]) * reps * steps
+    else:
+        res = o.phase_snp(sample_fr, range(reps), steps, seed=seed, refine_max=args.refine_max)
+        units = sum(len(b) * int(it) for b, it in zip(res["blocks"], res["iters"])) * reps * steps
     dt = time.perf_counter() - t0
-    units = sum(len(b) for b in res["blocks"]) * replicas * steps
     return {"value": units / dt, "unit": "spin-updates/s", "cores": os.cpu_count(),
             "kind": "oracle",
-            "sample": f"full graph ({fr.n_frags} reads), {replicas} replicas x {steps} steps, "
-                      f"graph build + bSB + voting, {dt:.1f} s"}, res
+            "sample": f"{what}, {reps} replicas x {steps} steps, whole path, {dt:.1f} s"}, res
 
 
 def _profiled_traffic(kernel):
@@ -151,20 +180,19 @@ def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
         return
-    fr, cfg = _workload(args)
-    times, value = [], None
+    fr, cfg, mode, R, T = _workload(args)
+    runs = []
     for i in range(args.warmup + args.steps):
-        cb, _ = cpu_baseline(fr, replicas=args.ref_replicas, steps=args.bsb_steps)
+        cb, _ = cpu_baseline(args, fr, mode, T)
         if i >= args.warmup:
-            times.append(cb)
-    vals = [c["value"] for c in times]
-    value = statistics.median(vals)
+            runs.append(cb)
+    value = statistics.median([c["value"] for c in runs])
     line = {"impl": "reference", "metric": "bSB spin-updates/s", "value": value,
             "unit": "spin-updates/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": os.cpu_count(),
-                             "kind": "oracle", "sample": times[-1]["sample"]},
+                             "kind": "oracle", "sample": runs[-1]["sample"]},
             "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -198,8 +226,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     from paper_2603_25762_gb300 import build, qhap
     build.build()
-    fr, cfg = _workload(args)
-    prec = qhap.PREC_BF16 if args.precision == "bf16" else qhap.PREC_FP32
+    fr, cfg, mode, R, T = _workload(args)
+    prec = {"bf16": qhap.PREC_BF16, "bf16x2": qhap.PREC_BF16X2, "fp32": qhap.PREC_FP32}[args.precision]
+    gmode = qhap.MODE_READ if mode == "read" else qhap.MODE_SNP
     stream = torch.cuda.Stream()
     ctx = qhap.Context(local, stream=stream.cuda_stream)
     # inputs resident in HBM
@@ -212,17 +241,16 @@ def run_ours(args):
             torch.empty(fr.n_snps, dtype=torch.int32, device=dev))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
-    R, T = args.replicas, args.bsb_steps
     base = rank * R
     stats = {}
 
     def one_step(host=False, pinned=None):
         if host:
-            g = ctx.build_graph(arrays=pinned, on_device=False)
+            g = ctx.build_graph(arrays=pinned, on_device=False, mode=gmode)
         else:
-            g = ctx.build_graph(arrays=arrays_dev, on_device=True)
+            g = ctx.build_graph(arrays=arrays_dev, on_device=True, mode=gmode)
         sol = ctx.solve(g, replicas=R, steps=T, precision=prec, seed=1, replica_base=base,
-                        step_kernel=args.step_kernel)
+                        step_kernel=args.step_kernel, refine_max=args.refine_max)
         if host:
             h = ctx.phase(g, sol, fr.n_snps)
             cut = sol.block(0)["best_cut"] if g.n_blocks else 0.0
@@ -285,9 +313,10 @@ def run_ours(args):
     hbm, bf16_tf, src = _peaks()
     launch_us = statistics.mean(step_ms) * 1e3
     # state traffic per spin update + each stored J nonzero read once (BF16: 2 B, FP32: 4 B)
-    per_launch_bytes = units / T * SPIN_BYTES + stats["nnz"] * (2 if prec else 4)
+    n_launch = max(1, stats["timing"]["n_step_launches"])
+    per_launch_bytes = units / n_launch * SPIN_BYTES + stats["nnz"] * (2 if prec else 4)
     achieved = per_launch_bytes / (launch_us * 1e-6) / 1e9
-    traffic = _profiled_traffic(stats["timing"]["kernel"])
+    traffic = _profiled_traffic(stats["timing"]["kernel"]) if args.workload == "hifi-region" else None
     h2d = sum(int(a.nbytes) for a in pinned_np[1:])
     d2h = fr.n_snps * (1 + 1 + 4) + 8
     line = {
@@ -309,7 +338,7 @@ def run_ours(args):
         "step_kernel_tuning": ctx.tuning_report(),
     }
     if not args.no_cpu_baseline:
-        cb, _ = cpu_baseline(fr, replicas=args.ref_replicas, steps=T)
+        cb, _ = cpu_baseline(args, fr, mode, T)
         line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -322,9 +351,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
-    ap.add_argument("--replicas", type=int, default=1024)
-    ap.add_argument("--bsb-steps", type=int, default=1000)
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16x2", "fp32"])
+    ap.add_argument("--workload", default="hifi-region", choices=sorted(WORKLOADS))
+    ap.add_argument("--replicas", type=int, default=0, help="0 = the workload's")
+    ap.add_argument("--bsb-steps", type=int, default=0, help="0 = the workload's")
+    ap.add_argument("--refine-max", type=int, default=15)
     ap.add_argument("--ref-replicas", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--step-kernel", default=None,

@@ -54,10 +54,12 @@ enum { QH_MODE_READ = 0, QH_MODE_SNP = 1 };
  * (Eqs. delta and w_ab); SIGNED = conflicts - agreements, W = -M M^T. */
 enum { QH_WEIGHT_CONFLICT = 0, QH_WEIGHT_SIGNED = 1 };
 /* J x X product precision in the bSB step.  State x, y is FP32 in all modes.
- * FP32: SIMT FP32 product.  BF16: tcgen05 BF16 x BF16 -> FP32 (J exact for
- * integer |w| <= 256; larger integers and real weights are split J = hi + lo,
- * both BF16, accumulated in the same FP32 accumulator). */
-enum { QH_PREC_FP32 = 0, QH_PREC_BF16 = 1 };
+ * FP32: SIMT FP32 product.
+ * BF16: tcgen05 BF16 x BF16 -> FP32 accumulate, X_hat = bf16(x).  J is rounded to
+ *   BF16 (exact for integer |w| <= 256; larger integers are split J = hi + lo,
+ *   both BF16, in the same accumulator, so integer J stays exact).
+ * BF16X2: as BF16, with real weights also split into hi + lo (J to ~2^-17). */
+enum { QH_PREC_FP32 = 0, QH_PREC_BF16 = 1, QH_PREC_BF16X2 = 2 };
 /* Schedules: LINEAR = a(t) = a0 * t / steps with the given steps;
  * AUTO = steps chosen from the block size as in the paper's SNP-based runs
  * (500 iterations for < 5,000 nodes, 1,000 otherwise). */

@@ -332,18 +332,18 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   if (R < 1) return set_err(ctx, QH_EINVAL, "replicas must be >= 1");
   if (o->schedule != QH_SCHED_LINEAR && o->schedule != QH_SCHED_AUTO) return set_err(ctx, QH_EINVAL, "bad schedule");
   if (o->schedule == QH_SCHED_LINEAR && o->steps < 1) return set_err(ctx, QH_EINVAL, "steps must be >= 1");
-  if (o->precision != QH_PREC_FP32 && o->precision != QH_PREC_BF16) return set_err(ctx, QH_EINVAL, "bad precision");
+  if (o->precision != QH_PREC_FP32 && !is_tc_precision(o->precision)) return set_err(ctx, QH_EINVAL, "bad precision");
   if (!(o->dt > 0.0) || !(o->a0 > 0.0)) return set_err(ctx, QH_EINVAL, "dt and a0 must be > 0");
   if (o->check_every < 0 || o->patience < 0 || o->replica_base < 0) return set_err(ctx, QH_EINVAL, "negative option");
   if ((int64_t)o->replica_base + R > (1 << 16)) return set_err(ctx, QH_EINVAL, "replica indices must stay below 65536");
-  if (o->precision == QH_PREC_BF16 && o->step_kernel >= 0 &&
+  if (is_tc_precision(o->precision) && o->step_kernel >= 0 &&
       (o->step_kernel >= tc_n_variants() || !tc_variant_ok(o->step_kernel, G, R)))
     return set_err(ctx, QH_EINVAL, "step_kernel variant not valid for this graph and replica count");
   const bool snp = G.mode == QH_MODE_SNP;
   const int32_t refine_max = snp ? o->refine_max : 1;
   if (refine_max < 1) return set_err(ctx, QH_EINVAL, "refine_max must be >= 1");
   const TcPlan plan = pick_plan(R);
-  if (o->precision == QH_PREC_BF16 && !tc_plan_ok(R, plan))
+  if (is_tc_precision(o->precision) && !tc_plan_ok(R, plan))
     return set_err(ctx, QH_EINVAL, "BF16 precision needs replicas to be a multiple of 64");
   cudaSetDevice(ctx->device);
   cudaStream_t s = ctx->stream;
@@ -471,7 +471,8 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   const float* x_final = B.x;
   if (o->precision == QH_PREC_FP32 && (max_steps % 2 == 1)) x_final = B.x1;
   TcPlan tplan = plan;
-  if (o->precision == QH_PREC_BF16) {
+  a.use_lo = use_lo_for(G, o->precision);
+  if (is_tc_precision(o->precision)) {
     QH_CUDA_TRY(cudaMemcpyAsync(B.running, B.active, nb * 4, cudaMemcpyDeviceToDevice, s));
     launch_init_state(s, W, R, o->replica_base, o->seed, 0, B.x, B.y, B.xh0, B.active);
     qh_status st = QH_OK;
@@ -484,7 +485,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
       return st;
     }
   }
-  sol.kernel = o->precision == QH_PREC_BF16 ? tc_variant_name(tplan.variant) : "k_step_f32";
+  sol.kernel = is_tc_precision(o->precision) ? tc_variant_name(tplan.variant) : "k_step_f32";
   skey += "|v" + std::to_string(tplan.variant);
   if (ctx->loop_key != skey || !ctx->loop_exec) {
     if (ctx->loop_exec) {
@@ -547,7 +548,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     }
     QH_CUDA_TRY(cudaMemcpyAsync(B.running, B.active, nb * 4, cudaMemcpyDeviceToDevice, s));
     launch_init_state(s, W, R, o->replica_base, o->seed, it, B.x, B.y,
-                      o->precision == QH_PREC_BF16 ? B.xh0 : nullptr, B.active);
+                      is_tc_precision(o->precision) ? B.xh0 : nullptr, B.active);
     QH_CUDA_TRY(cudaEventRecord(ctx->ev[2], s));
     QH_CUDA_TRY(cudaGraphLaunch(ctx->loop_exec, s));
     note_launch(ctx->loop_kernels);
@@ -783,9 +784,9 @@ qh_status qh_debug_layout(qh_ctx* h, const qh_graph* gh, int32_t* n_pad, int32_t
 
 static qh_status debug_common(Ctx* ctx, const Graph& g, int precision, int32_t R, StepArgs& a,
                               const double* c0_per_block, int32_t steps) {
-  if (precision != QH_PREC_FP32 && precision != QH_PREC_BF16) return set_err(ctx, QH_EINVAL, "bad precision");
+  if (precision != QH_PREC_FP32 && !is_tc_precision(precision)) return set_err(ctx, QH_EINVAL, "bad precision");
   if (R < 1) return set_err(ctx, QH_EINVAL, "R must be >= 1");
-  if (precision == QH_PREC_BF16 && !tc_plan_ok(R, pick_plan(R)))
+  if (is_tc_precision(precision) && !tc_plan_ok(R, pick_plan(R)))
     return set_err(ctx, QH_EINVAL, "BF16 precision needs R to be a multiple of 64");
   const int32_t nb = std::max(g.n_blocks, 1);
   std::vector<float> c0(nb);
@@ -807,6 +808,7 @@ static qh_status debug_common(Ctx* ctx, const Graph& g, int precision, int32_t R
   a.n_pad = g.n_pad;
   a.R = R;
   a.err = ctx->d_err;
+  a.use_lo = use_lo_for(g, precision);
   return QH_OK;
 }
 

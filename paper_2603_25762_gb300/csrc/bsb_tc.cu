@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(128) k_step_tc(const __grid_constant__ CUtenso
   const int32_t sb = a.steps_b[rt.block];
   if ((a.active != nullptr && !a.active[rt.block]) || a.t >= sb) return;  // CTA-uniform
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nk = rt.n_all * 2;  // 64-wide K slices
+  const int nk = (a.use_lo ? rt.n_all : rt.n_hi) * 2;  // 64-wide K slices
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(128, MINB) k_step_tc_v(const __grid_constant__
   const int32_t sb = a.steps_b[rt.block];
   if ((a.active != nullptr && !a.active[rt.block]) || a.t >= sb) return;  // CTA-uniform
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nk = rt.n_all * 2;
+  const int nk = (a.use_lo ? rt.n_all : rt.n_hi) * 2;
   const int row = warp * 32 + lane;
   const bool vrow = row < rt.valid;
   const size_t base = (size_t)blockIdx.y * BN * a.n_pad + rt.row0 + row;
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(192, 1)
         mbar_expect_tx(sfull0 + 8 * sb, 2 * L::STILE);
         tma_load_2d(smem_u32(sx), &tmSx, sfull0 + 8 * sb, rt.row0, rn * BN);
         tma_load_2d(smem_u32(sx + L::STILE), &tmSy, sfull0 + 8 * sb, rt.row0, rn * BN);
-        const int nk = rt.n_all * 2;
+        const int nk = (a.use_lo ? rt.n_all : rt.n_hi) * 2;
         for (int kb = 0; kb < nk; ++kb, ++kg) {
           const uint32_t st = kg % OSTAGES, ph = (kg / OSTAGES) & 1u;
           if (!(ok = mbar_wait(empty0 + 8 * st, ph ^ 1u, a.err))) break;
@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(192, 1)
         if (!(ok = mbar_wait(aempty0 + 8 * ab, aph ^ 1u, a.err))) break;
         tc_fence_after();
         const uint32_t dcol = tmem + ab * BN;
-        const int nk = rt.n_all * 2;
+        const int nk = (a.use_lo ? rt.n_all : rt.n_hi) * 2;
         for (int kb = 0; kb < nk; ++kb, ++kg) {
           const uint32_t st = kg % OSTAGES, ph = (kg / OSTAGES) & 1u;
           if (!(ok = mbar_wait(full0 + 8 * st, ph, a.err))) break;
@@ -715,8 +715,9 @@ __global__ void __launch_bounds__(384, 1)
         if (!item_live(a, rt)) continue;
         // stage this item's column tiles (independent loads, one latency)
         int32_t* cols = scol + (it & 1u) * P2_MAX_TILES;
-        for (int e = 0; e < rt.n_all; ++e) cols[e] = a.tile_col[rt.tile_begin + e];
-        const int nk = rt.n_all * 2;
+        const int ne = a.use_lo ? rt.n_all : rt.n_hi;
+        for (int e = 0; e < ne; ++e) cols[e] = a.tile_col[rt.tile_begin + e];
+        const int nk = ne * 2;
         for (int kb = 0; kb < nk; ++kb, ++kg) {
           const uint32_t st = kg % P2_STAGES, ph = (kg / P2_STAGES) & 1u;
           if (!(ok = mbar_wait(empty0 + 8 * st, ph ^ 1u, a.err))) break;
@@ -742,7 +743,7 @@ __global__ void __launch_bounds__(384, 1)
         if (!(ok = mbar_wait(aempty0 + 8 * ab, aph ^ 1u, a.err))) break;
         tc_fence_after();
         const uint32_t dcol = tmem + ab * BN;
-        const int nk = rt.n_all * 2;
+        const int nk = (a.use_lo ? rt.n_all : rt.n_hi) * 2;
         for (int kb = 0; kb < nk; ++kb, ++kg) {
           const uint32_t st = kg % P2_STAGES, ph = (kg / P2_STAGES) & 1u;
           if (!(ok = mbar_wait(full0 + 8 * st, ph, a.err))) break;

@@ -102,6 +102,7 @@ extern "C" qh_status qh_matvec_bf16_noalloc(qh_ctx* h, const qh_graph* gh, int32
   a.a0 = 1.0;
   a.z_out = z;
   a.err = ctx->d_err;
+  a.use_lo = use_lo_for(g, QH_PREC_BF16);
   st = launch_step_tc(ctx, g, a, xh, TcPlan{R % 128 == 0 ? 128 : 64, 3});
   if (st != QH_OK) return st;
   int32_t herr = 0;

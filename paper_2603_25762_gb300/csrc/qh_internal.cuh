@@ -159,10 +159,18 @@ struct StepArgs {
   const int32_t* steps_b;  // [n_blocks] schedule length per block (a(t) = a0 t / steps_b)
   int32_t n_pad, R;
   int32_t t;              // step index
+  int32_t use_lo;         // BF16 paths: also accumulate the lo (remainder) tiles
   float dt, dta0;         // dta0 = dt * a0
   double a0;
   int32_t* err;
 };
+
+// Tensor-core precisions use the BF16 hi tiles; the lo (remainder) tiles join when
+// asked for (QH_PREC_BF16X2) or when integer weights above 256 need them to stay exact.
+inline bool is_tc_precision(int p) { return p == QH_PREC_BF16 || p == QH_PREC_BF16X2; }
+inline int32_t use_lo_for(const Graph& g, int precision) {
+  return g.has_lo && (precision == QH_PREC_BF16X2 || g.integer_weights) ? 1 : 0;
+}
 
 qh_status set_err(Ctx* ctx, qh_status st, const std::string& msg);
 qh_status cuda_fail(Ctx* ctx, cudaError_t e, const char* what);

@@ -215,16 +215,20 @@ def test_matvec_exact_operands(q, ctx, oracle):
     e_read = _matvec_case(q, ctx, oracle, fr, q.MODE_READ, q.PREC_BF16, 64, bf16_x=True)
     assert e_read <= 1e-6, e_read
     fs = synth.ont_region(1003, scale=0.06)
-    e_snp = _matvec_case(q, ctx, oracle, fs, q.MODE_SNP, q.PREC_BF16, 64, bf16_x=True)
+    e_snp = _matvec_case(q, ctx, oracle, fs, q.MODE_SNP, q.PREC_BF16X2, 64, bf16_x=True)
     assert e_snp <= 3e-5, e_snp
+    e_hi = _matvec_case(q, ctx, oracle, fs, q.MODE_SNP, q.PREC_BF16, 64, bf16_x=True)
+    assert 3e-5 < e_hi <= 1e-2, e_hi  # hi tiles only: J itself rounded to BF16
 
 
 def test_matvec_snp_graph_hilo(q, ctx, oracle):
     fr = synth.ont_region(1003, scale=0.06)
     e32 = _matvec_case(q, ctx, oracle, fr, q.MODE_SNP, q.PREC_FP32, 64)
     e16 = _matvec_case(q, ctx, oracle, fr, q.MODE_SNP, q.PREC_BF16, 64)
+    e2 = _matvec_case(q, ctx, oracle, fr, q.MODE_SNP, q.PREC_BF16X2, 64)
     assert e32 <= 1e-5, e32
     assert e16 <= 1e-2, e16
+    assert e2 <= e16 and e2 <= 1e-2, (e2, e16)
 
 
 # ----------------------------------------------------------------------------- one bSB step
@@ -350,7 +354,7 @@ def test_phase_read_matches_oracle_and_truth(q, ctx, oracle, precision):
     assert np.array_equal(h1, oh1) and np.array_equal(bid, osb)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_phase_snp_refinement(q, ctx, oracle, precision):
     fr = synth.region_reads(31, n_snps=150, region=50_000, n_reads=50, len_mean=8000,
                             len_sd=2000, flip_p=0.0, miss_p=0.0, qual=(10, 30))
