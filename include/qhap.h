@@ -110,8 +110,16 @@ typedef struct {
   int32_t weight_mode; /* READ mode: QH_WEIGHT_CONFLICT | QH_WEIGHT_SIGNED */
   int32_t linkage_k;   /* SNP mode: linkage depth k/10, 1..10 (10 = all pairs) */
   int32_t dense;       /* 1: store every J tile of each block (no zero-tile skipping) */
+  int32_t storage;     /* J for the solver: QH_STORAGE_AUTO | _TILES | _CSR */
   double porec_alpha;  /* SNP mode: Pore-C contribution factor (paper default 0.1) */
 } qh_graph_opts;
+
+/* J storage for the solver.  TILES: nonzero 128 x 128 tiles, tensor-core steps,
+ * state [R][n_pad].  CSR: one row per padded vertex, warp-per-vertex gather steps,
+ * state [n_pad][R] (graphs whose edges scatter over most tiles, e.g. long-range
+ * Pore-C contacts).  AUTO picks CSR when the nonzero tiles would hold more than
+ * 64 stored entries per edge and exceed 4,096 tiles, TILES otherwise. */
+enum { QH_STORAGE_AUTO = 0, QH_STORAGE_TILES = 1, QH_STORAGE_CSR = 2 };
 
 /* Build the phasing graph and its phase blocks.
  * READ mode: vertices = fragments; w_ab per weight_mode (read-based Max-Cut
@@ -250,7 +258,8 @@ qh_status qh_phase(qh_ctx* ctx, const qh_graph* g, const qh_solution* sol, int8_
 /* ---------------------------------------------------------------- test hooks */
 
 /* One J x X product with the solver's operands, for precision checks.
- * x  float32[R][n_pad] (device) : state, padded vertex layout
+ * x  float32[R][n_pad] (device) : state, padded vertex layout (for CSR storage
+ *    the hook transposes to the solver's [n_pad][R] layout and back)
  * z  float32[R][n_pad] (device) : output J_hat x X_hat (FP32 accumulate), where
  *    J_hat, X_hat are the precision's operands (BF16 rounds x to BF16).
  * n_pad is qh_debug_layout's value.  R multiple of 16 for BF16.

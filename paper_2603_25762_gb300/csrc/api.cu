@@ -67,7 +67,8 @@ namespace {
 enum {
   S_X = 32, S_Y, S_X1, S_XH0, S_XH1, S_SIGNS, S_NODEVAL, S_CUTS, S_BESTR, S_BESTCUT, S_ACTIVE,
   S_STEPSB, S_C0, S_SEEN, S_STALL, S_STEPSRUN, S_SPINS, S_C, S_WWORK, S_TBWORK, S_TFWORK,
-  S_SUMW, S_SUMJ2, S_NODETMP, S_SIGNS1, S_NODEVAL1, S_CUT1, S_DBG0, S_DBG1, S_DBG2, S_RUNNING
+  S_SUMW, S_SUMJ2, S_NODETMP, S_SIGNS1, S_NODEVAL1, S_CUT1, S_DBG0, S_DBG1, S_DBG2, S_RUNNING,
+  S_PVWORK, S_TR0, S_TR1
 };
 
 struct SolveBufs {
@@ -87,11 +88,28 @@ qh_status run_step(Ctx* ctx, const Graph& g, int precision, const TcPlan& plan, 
   if (precision == QH_PREC_FP32) {
     a.xin = x_cur_f32;
     a.xout = x_next_f32;
-    launch_step_f32(ctx->stream, g, a);
+    if (g.csr_mode)
+      launch_step_csr(ctx->stream, g, a, g.pval, nullptr);
+    else
+      launch_step_f32(ctx->stream, g, a);
     return QH_OK;
   }
   a.xh_out = xh_next;
+  if (g.csr_mode) {
+    launch_step_csr(ctx->stream, g, a, g.pval, xh_cur);
+    return QH_OK;
+  }
   return launch_step_tc(ctx, g, a, xh_cur, plan);
+}
+
+// The CUDA runtime is shared with the host application (for example PyTorch): its
+// per-thread last-error slot may hold an error from someone else's call.  Entry
+// points clear it so that stage checks report only this library's launches; the
+// cleared error is kept in the context's message for diagnosis.
+void clear_foreign_error(Ctx* ctx) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) ctx->err = std::string("cleared a pending error from an earlier call: ") +
+                                   cudaGetErrorString(e);
 }
 
 qh_status check_err_word(Ctx* ctx) {
@@ -250,6 +268,7 @@ qh_status qh_build_graph(qh_ctx* h, const qh_fragments* f, const qh_graph_opts* 
   if (!h) return QH_EINVAL;
   Ctx* ctx = &h->c;
   ctx->err.clear();
+  clear_foreign_error(ctx);
   if (!f || !o || !out) return set_err(ctx, QH_EINVAL, "NULL argument");
   *out = nullptr;
   if (f->n_frags < 0 || f->n_snps < 0 || !f->frag_ptr)
@@ -325,6 +344,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   if (!h) return QH_EINVAL;
   Ctx* ctx = &h->c;
   ctx->err.clear();
+  clear_foreign_error(ctx);
   if (!gh || !o || !out) return set_err(ctx, QH_EINVAL, "NULL argument");
   *out = nullptr;
   const Graph& G = gh->g;
@@ -336,14 +356,16 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   if (!(o->dt > 0.0) || !(o->a0 > 0.0)) return set_err(ctx, QH_EINVAL, "dt and a0 must be > 0");
   if (o->check_every < 0 || o->patience < 0 || o->replica_base < 0) return set_err(ctx, QH_EINVAL, "negative option");
   if ((int64_t)o->replica_base + R > (1 << 16)) return set_err(ctx, QH_EINVAL, "replica indices must stay below 65536");
-  if (is_tc_precision(o->precision) && o->step_kernel >= 0 &&
+  if (is_tc_precision(o->precision) && o->step_kernel >= 0 && !G.csr_mode &&
       (o->step_kernel >= tc_n_variants() || !tc_variant_ok(o->step_kernel, G, R)))
     return set_err(ctx, QH_EINVAL, "step_kernel variant not valid for this graph and replica count");
   const bool snp = G.mode == QH_MODE_SNP;
   const int32_t refine_max = snp ? o->refine_max : 1;
   if (refine_max < 1) return set_err(ctx, QH_EINVAL, "refine_max must be >= 1");
   const TcPlan plan = pick_plan(R);
-  if (is_tc_precision(o->precision) && !tc_plan_ok(R, plan))
+  if (G.csr_mode && R % 4 != 0)
+    return set_err(ctx, QH_EINVAL, "CSR storage needs replicas to be a multiple of 4");
+  if (is_tc_precision(o->precision) && !G.csr_mode && !tc_plan_ok(R, plan))
     return set_err(ctx, QH_EINVAL, "BF16 precision needs replicas to be a multiple of 64");
   cudaSetDevice(ctx->device);
   cudaStream_t s = ctx->stream;
@@ -414,15 +436,24 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     W.w = (double*)sc(std::max<int64_t>(G.nnz, 1) * 8, S_WWORK);
     W.tile_bf16 = (__nv_bfloat16*)sc(std::max<int64_t>(G.n_tiles, 1) * TILE * TILE * 2, S_TBWORK);
     W.tile_f32 = (float*)sc(std::max<int64_t>(G.n_tiles_hi, 1) * TILE * TILE * 4, S_TFWORK);
+    if (G.csr_mode) {
+      W.pval = (float*)sc(std::max<int64_t>(G.pnnz, 1) * 4, S_PVWORK);
+      if (W.pval && G.pnnz)
+        QH_CUDA_TRY(cudaMemcpyAsync(W.pval, G.pval, G.pnnz * 4, cudaMemcpyDeviceToDevice, s));
+    }
     sum_w_work = (double*)sc(nb * 8, S_SUMW);
     double* sj2 = (double*)sc(nb * 8, S_SUMJ2);
     double* ntmp = (double*)sc((size_t)std::max(G.n_nodes, 1) * 16, S_NODETMP);
-    okb = W.w && W.tile_bf16 && W.tile_f32 && sum_w_work && sj2 && ntmp;
+    okb = W.w && W.tile_bf16 && W.tile_f32 && sum_w_work && sj2 && ntmp && W.pval;
     if (okb) {
-      if (G.nnz) cudaMemcpyAsync(W.w, G.w, G.nnz * 8, cudaMemcpyDeviceToDevice, s);
-      if (G.n_tiles) cudaMemcpyAsync(W.tile_bf16, G.tile_bf16, G.n_tiles * TILE * TILE * 2, cudaMemcpyDeviceToDevice, s);
-      if (G.n_tiles_hi) cudaMemcpyAsync(W.tile_f32, G.tile_f32, G.n_tiles_hi * TILE * TILE * 4, cudaMemcpyDeviceToDevice, s);
-      cudaMemcpyAsync(sum_w_work, G.sum_w, nb * 8, cudaMemcpyDeviceToDevice, s);
+      if (G.nnz) QH_CUDA_TRY(cudaMemcpyAsync(W.w, G.w, G.nnz * 8, cudaMemcpyDeviceToDevice, s));
+      if (G.n_tiles)
+        QH_CUDA_TRY(cudaMemcpyAsync(W.tile_bf16, G.tile_bf16, G.n_tiles * TILE * TILE * 2,
+                                    cudaMemcpyDeviceToDevice, s));
+      if (G.n_tiles_hi)
+        QH_CUDA_TRY(cudaMemcpyAsync(W.tile_f32, G.tile_f32, G.n_tiles_hi * TILE * TILE * 4,
+                                    cudaMemcpyDeviceToDevice, s));
+      QH_CUDA_TRY(cudaMemcpyAsync(sum_w_work, G.sum_w, nb * 8, cudaMemcpyDeviceToDevice, s));
     }
   }
   if (!okb) {
@@ -475,17 +506,19 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   if (is_tc_precision(o->precision)) {
     QH_CUDA_TRY(cudaMemcpyAsync(B.running, B.active, nb * 4, cudaMemcpyDeviceToDevice, s));
     launch_init_state(s, W, R, o->replica_base, o->seed, 0, B.x, B.y, B.xh0, B.active);
+    QH_STAGE_CHECK("solve: state init (tuning)");
     qh_status st = QH_OK;
     if (o->step_kernel >= 0)
       tplan.variant = o->step_kernel;
-    else
+    else if (!G.csr_mode)
       st = autotune(ctx, W, a, B, R, &tplan);
     if (st != QH_OK) {
       delete sh;
       return st;
     }
   }
-  sol.kernel = is_tc_precision(o->precision) ? tc_variant_name(tplan.variant) : "k_step_f32";
+  sol.kernel = G.csr_mode ? (is_tc_precision(o->precision) ? "csr-warp-bf16" : "csr-warp-fp32")
+              : is_tc_precision(o->precision) ? tc_variant_name(tplan.variant) : "k_step_f32";
   skey += "|v" + std::to_string(tplan.variant);
   if (ctx->loop_key != skey || !ctx->loop_exec) {
     if (ctx->loop_exec) {
@@ -495,6 +528,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     ctx->loop_key.clear();
     cudaGraph_t graph;
     const int64_t before = launches();
+    QH_STAGE_CHECK("solve: before step-loop capture");
     QH_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     qh_status st = QH_OK;
     for (int32_t t = 0; t < max_steps && st == QH_OK; ++t) {
@@ -549,6 +583,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     QH_CUDA_TRY(cudaMemcpyAsync(B.running, B.active, nb * 4, cudaMemcpyDeviceToDevice, s));
     launch_init_state(s, W, R, o->replica_base, o->seed, it, B.x, B.y,
                       is_tc_precision(o->precision) ? B.xh0 : nullptr, B.active);
+    QH_STAGE_CHECK("solve: state init");
     QH_CUDA_TRY(cudaEventRecord(ctx->ev[2], s));
     QH_CUDA_TRY(cudaGraphLaunch(ctx->loop_exec, s));
     note_launch(ctx->loop_kernels);
@@ -557,6 +592,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.active);
     launch_pick_best(s, nb, R, B.cuts, B.best_r, B.best_cut, B.active);
     launch_extract_spins(s, W, R, B.signs, B.best_r, B.spins, B.active);
+    QH_STAGE_CHECK("solve: signs, cut, replica pick");
     if (it == 0)
       QH_CUDA_TRY(cudaMemcpyAsync(sol.cuts_first.data(), B.cuts, (size_t)nb * R * 8, cudaMemcpyDeviceToHost, s));
     QH_CUDA_TRY(cudaMemcpyAsync(h_steps_run.data(), B.steps_run, nb * 4, cudaMemcpyDeviceToHost, s));
@@ -584,6 +620,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     if (!snp) break;
     // ---- SNP refinement: termination test, flip counter, sign inversion
     launch_refine_prepare(s, W, B.spins, B.best_cut, B.active, B.C);
+    QH_STAGE_CHECK("solve: refinement test");
     QH_CUDA_TRY(cudaMemcpyAsync(h_active.data(), B.active, nb * 4, cudaMemcpyDeviceToHost, s));
     QH_CUDA_TRY(cudaStreamSynchronize(s));
     int32_t n_active = 0;
@@ -591,7 +628,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     if (n_active == 0 || it + 1 == refine_max) break;
     launch_gauge(s, W, B.spins, W.w, B.active);
     {
-      qh_status st = retile(ctx, &W, W.w, W.tile_bf16, W.tile_f32);
+      qh_status st = retile(ctx, &W, W.w, W.tile_bf16, W.tile_f32, W.csr_mode ? W.pval : nullptr);
       if (st != QH_OK) {
         delete sh;
         return st;
@@ -632,6 +669,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
       if (hp[v] >= 0) hs[hp[v]] = sol.spins[v];
     QH_CUDA_TRY(cudaMemcpyAsync(st1, hs.data(), G.n_pad, cudaMemcpyHostToDevice, s));
     launch_cut(s, G, 1, st1, G.w, G.sum_w, nv1, cut1, nullptr);
+    QH_STAGE_CHECK("solve: final parity cut");
     QH_CUDA_TRY(cudaMemcpyAsync(sol.best_cut.data(), cut1, nb * 8, cudaMemcpyDeviceToHost, s));
   } else {
     if (G.n_nodes)
@@ -736,6 +774,7 @@ qh_status qh_phase(qh_ctx* h, const qh_graph* gh, const qh_solution* sh, int8_t*
   if (!h) return QH_EINVAL;
   Ctx* ctx = &h->c;
   ctx->err.clear();
+  clear_foreign_error(ctx);
   if (!gh || !sh || !hap1 || !hap2 || !block_id) return set_err(ctx, QH_EINVAL, "NULL argument");
   const Graph& g = gh->g;
   const Solution& sol = sh->s;
@@ -786,7 +825,7 @@ static qh_status debug_common(Ctx* ctx, const Graph& g, int precision, int32_t R
                               const double* c0_per_block, int32_t steps) {
   if (precision != QH_PREC_FP32 && !is_tc_precision(precision)) return set_err(ctx, QH_EINVAL, "bad precision");
   if (R < 1) return set_err(ctx, QH_EINVAL, "R must be >= 1");
-  if (is_tc_precision(precision) && !tc_plan_ok(R, pick_plan(R)))
+  if (is_tc_precision(precision) && !g.csr_mode && !tc_plan_ok(R, pick_plan(R)))
     return set_err(ctx, QH_EINVAL, "BF16 precision needs R to be a multiple of 64");
   const int32_t nb = std::max(g.n_blocks, 1);
   std::vector<float> c0(nb);
@@ -825,6 +864,27 @@ qh_status qh_debug_matvec(qh_ctx* h, const qh_graph* gh, int32_t precision, int3
   a.t = 0;
   a.a0 = 1.0;
   QH_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)R * g.n_pad * 4, ctx->stream));
+  if (g.csr_mode) {  // API layout [R][n_pad] <-> solver layout [n_pad][R]
+    if (R % 4 != 0) return set_err(ctx, QH_EINVAL, "CSR storage needs R to be a multiple of 4");
+    const size_t NS = (size_t)R * g.n_pad;
+    float* xt = (float*)ctx->scratch(NS * 4, S_TR0);
+    float* zt = (float*)ctx->scratch(NS * 4, S_TR1);
+    __nv_bfloat16* xh = (__nv_bfloat16*)ctx->scratch(NS * 2, S_XH0);
+    if (!xt || !zt || !xh) return set_err(ctx, QH_ENOMEM, "allocation failed (debug)");
+    QH_CUDA_TRY(cudaMemsetAsync(zt, 0, NS * 4, ctx->stream));
+    launch_transpose(ctx->stream, x, xt, R, g.n_pad);
+    a.z_out = zt;
+    if (precision == QH_PREC_FP32) {
+      a.xin = xt;
+      launch_step_csr(ctx->stream, g, a, g.pval, nullptr);
+    } else {
+      launch_f32_to_bf16(ctx->stream, xt, xh, (int64_t)NS);
+      launch_step_csr(ctx->stream, g, a, g.pval, xh);
+    }
+    launch_transpose(ctx->stream, zt, z, g.n_pad, R);
+    QH_CUDA_TRY(cudaGetLastError());
+    return check_err_word(ctx);
+  }
   if (precision == QH_PREC_FP32) {
     a.xin = x;
     a.xout = nullptr;
@@ -857,6 +917,18 @@ qh_status qh_debug_steps(qh_ctx* h, const qh_graph* gh, int32_t precision, int32
   a.dta0 = (float)(dt * a0);
   const size_t NS = (size_t)R * g.n_pad;
   cudaStream_t s = ctx->stream;
+  float* xu = x;  // user buffers in [R][n_pad]
+  float* yu = y;
+  if (g.csr_mode) {
+    if (R % 4 != 0) return set_err(ctx, QH_EINVAL, "CSR storage needs R to be a multiple of 4");
+    x = (float*)ctx->scratch(NS * 4, S_TR0);
+    y = (float*)ctx->scratch(NS * 4, S_TR1);
+    if (!x || !y) return set_err(ctx, QH_ENOMEM, "allocation failed (debug)");
+    launch_transpose(s, xu, x, R, g.n_pad);
+    launch_transpose(s, yu, y, R, g.n_pad);
+    a.x = x;
+    a.y = y;
+  }
   if (precision == QH_PREC_FP32) {
     float* x1 = (float*)ctx->scratch(NS * 4, S_X1);
     if (!x1) return set_err(ctx, QH_ENOMEM, "allocation failed (debug)");
@@ -865,7 +937,10 @@ qh_status qh_debug_steps(qh_ctx* h, const qh_graph* gh, int32_t precision, int32
       a.t = t0 + k;
       a.xin = (k % 2 == 0) ? x : x1;
       a.xout = (k % 2 == 0) ? x1 : x;
-      launch_step_f32(s, g, a);
+      if (g.csr_mode)
+        launch_step_csr(s, g, a, g.pval, nullptr);
+      else
+        launch_step_f32(s, g, a);
     }
     if (nsteps % 2 == 1) QH_CUDA_TRY(cudaMemcpyAsync(x, x1, NS * 4, cudaMemcpyDeviceToDevice, s));
   } else {
@@ -877,9 +952,17 @@ qh_status qh_debug_steps(qh_ctx* h, const qh_graph* gh, int32_t precision, int32
     for (int32_t k = 0; k < nsteps; ++k) {
       a.t = t0 + k;
       a.xh_out = (k % 2 == 0) ? xh1 : xh0;
+      if (g.csr_mode) {
+        launch_step_csr(s, g, a, g.pval, (k % 2 == 0) ? xh0 : xh1);
+        continue;
+      }
       st = launch_step_tc(ctx, g, a, (k % 2 == 0) ? xh0 : xh1, pick_plan(R));
       if (st) return st;
     }
+  }
+  if (g.csr_mode) {
+    launch_transpose(s, x, xu, g.n_pad, R);
+    launch_transpose(s, y, yu, g.n_pad, R);
   }
   QH_CUDA_TRY(cudaGetLastError());
   return check_err_word(ctx);

@@ -146,6 +146,133 @@ __global__ void __launch_bounds__(256) k_step_f32(StepArgs a) {
     }
 }
 
+// ------------------------------------------------------------------ CSR storage
+// Vertex-major state ([n_pad][R]): initial draws, thread per (vertex, replica).
+__global__ void k_init_state_vm(const RowTile* __restrict__ rt, const int32_t* __restrict__ pad_node,
+                                const int32_t* __restrict__ local, int32_t n_pad, int32_t R,
+                                int32_t replica_base, uint64_t seed, int32_t iter, float* x,
+                                float* y, __nv_bfloat16* xh, const int32_t* __restrict__ active) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n_pad * R) return;
+  const int32_t col = (int32_t)(i / R), r = (int32_t)(i % R);
+  const int32_t b = rt[col / TILE].block;
+  if (active != nullptr && !active[b]) return;
+  const int32_t v = pad_node[col];
+  float xv = 0.f, yv = 0.f;
+  if (v >= 0) {
+    uint64_t key = init_key(seed, b, iter);
+    xv = init_draw(key, replica_base + r, local[v], 0);
+    yv = init_draw(key, replica_base + r, local[v], 1);
+  }
+  x[i] = xv;
+  y[i] = yv;
+  if (xh != nullptr) xh[i] = __float2bfloat16_rn(xv);
+}
+
+__global__ void k_signs_vm(const float* __restrict__ x, int64_t n, int8_t* st) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) st[i] = x[i] >= 0.f ? 1 : -1;
+}
+
+// One bSB step on CSR storage: warp per padded vertex; lane l owns replicas
+// 4l .. 4l+3 of every 128-replica chunk.  The row's (column, J) pairs are read 32 at
+// a time and broadcast by shuffle; each neighbour costs one 8-byte (BF16) or 16-byte
+// (FP32) load per lane, i.e. a contiguous replica slice per warp.
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_step_csr(StepArgs a, const int64_t* __restrict__ prow,
+                                                  const int32_t* __restrict__ pcol,
+                                                  const float* __restrict__ pval,
+                                                  const __nv_bfloat16* __restrict__ xh_in) {
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= a.n_pad) return;
+  const RowTile rt = a.rt[row / TILE];
+  const int32_t sb = a.steps_b[rt.block];
+  const bool live = (a.active == nullptr || a.active[rt.block]) && a.t < sb;
+  if (row - rt.row0 >= rt.valid) return;  // padding vertex: state stays zero
+  const size_t rbase = (size_t)row * a.R;
+  if (!live) {
+    if (!BF16 && a.z_out == nullptr && a.xout != a.xin)  // carry a frozen block forward
+      for (int32_t r = 4 * lane; r < a.R; r += 128)
+        *reinterpret_cast<float4*>(a.xout + rbase + r) =
+            *reinterpret_cast<const float4*>(a.xin + rbase + r);
+    return;
+  }
+  const int64_t e0 = prow[row], e1 = prow[row + 1];
+  const double at = a.a0 * (double)a.t / (double)sb;
+  const float coef_x = (float)(-(a.a0 - at));
+  const float c0 = a.c0[rt.block];
+  for (int32_t r0 = 0; r0 < a.R; r0 += 128) {
+    const int32_t r = r0 + 4 * lane;
+    const bool on = r < a.R;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t e = e0; e < e1; e += 32) {
+      const int ne = (e1 - e) < 32 ? (int)(e1 - e) : 32;
+      const int32_t cl = lane < ne ? pcol[e + lane] : 0;
+      const float vl = lane < ne ? pval[e + lane] : 0.f;
+      for (int k = 0; k < ne; ++k) {
+        const int32_t cc = __shfl_sync(0xffffffffu, cl, k);
+        const float jv = __shfl_sync(0xffffffffu, vl, k);
+        if (!on) continue;
+        const size_t off = (size_t)cc * a.R + r;
+        if (BF16) {
+          const uint2 u = *reinterpret_cast<const uint2*>(xh_in + off);
+          const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&u.x);
+          const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&u.y);
+          acc[0] = fmaf(jv, __low2float(lo), acc[0]);
+          acc[1] = fmaf(jv, __high2float(lo), acc[1]);
+          acc[2] = fmaf(jv, __low2float(hi), acc[2]);
+          acc[3] = fmaf(jv, __high2float(hi), acc[3]);
+        } else {
+          const float4 xv = *reinterpret_cast<const float4*>(a.xin + off);
+          acc[0] = fmaf(jv, xv.x, acc[0]);
+          acc[1] = fmaf(jv, xv.y, acc[1]);
+          acc[2] = fmaf(jv, xv.z, acc[2]);
+          acc[3] = fmaf(jv, xv.w, acc[3]);
+        }
+      }
+    }
+    if (!on) continue;
+    const size_t idx = rbase + r;
+    if (a.z_out != nullptr) {
+      *reinterpret_cast<float4*>(a.z_out + idx) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      continue;
+    }
+    const float* xsrc = BF16 ? a.x : a.xin;
+    float4 xv = *reinterpret_cast<const float4*>(xsrc + idx);
+    float4 yv = *reinterpret_cast<const float4*>(a.y + idx);
+    float xs[4] = {xv.x, xv.y, xv.z, xv.w}, ys[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) bsb_update(acc[j], xs[j], ys[j], a.dt, coef_x, a.dta0, c0);
+    float* xdst = BF16 ? a.x : a.xout;
+    *reinterpret_cast<float4*>(xdst + idx) = make_float4(xs[0], xs[1], xs[2], xs[3]);
+    *reinterpret_cast<float4*>(a.y + idx) = make_float4(ys[0], ys[1], ys[2], ys[3]);
+    if (BF16) {
+      __nv_bfloat162 p0 = __floats2bfloat162_rn(xs[0], xs[1]);
+      __nv_bfloat162 p1 = __floats2bfloat162_rn(xs[2], xs[3]);
+      uint2 u;
+      u.x = *reinterpret_cast<uint32_t*>(&p0);
+      u.y = *reinterpret_cast<uint32_t*>(&p1);
+      *reinterpret_cast<uint2*>(a.xh_out + idx) = u;
+    }
+  }
+}
+
+__global__ void k_transpose(const float* __restrict__ in, float* out, int64_t rows, int64_t cols) {
+  __shared__ float t[32][33];
+  const int64_t c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int k = ty; k < 32; k += 8) {
+    int64_t r = r0 + k, c = c0 + tx;
+    if (r < rows && c < cols) t[k][tx] = in[r * cols + c];
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    int64_t c = c0 + k, r = r0 + tx;
+    if (r < rows && c < cols) out[c * rows + r] = t[tx][k];
+  }
+}
+
 // ------------------------------------------------------------------ signs / cut
 // signs_t[col][r] = sgn(x[r][col]) with sgn(0) = +1, via a 32 x 32 transpose tile.
 __global__ void k_signs_t(const float* __restrict__ x, int32_t n_pad, int32_t R, int8_t* st) {
@@ -456,6 +583,13 @@ void launch_init_state(cudaStream_t s, const Graph& g, int32_t R, int32_t replic
                        uint64_t seed, int32_t iter, float* x, float* y, __nv_bfloat16* xh,
                        const int32_t* active) {
   if (g.n_pad == 0 || R == 0) return;
+  if (g.csr_mode) {
+    const int64_t n = (int64_t)g.n_pad * R;
+    k_init_state_vm<<<::qh::counted(nblk(n)), 256, 0, s>>>(g.rt, g.pad_node, g.local, g.n_pad, R,
+                                                          replica_base, seed, iter, x, y, xh,
+                                                          active);
+    return;
+  }
   dim3 grid(nblk(g.n_pad), R);
   k_init_state<<<::qh::counted(grid), 256, 0, s>>>(g.rt, g.pad_node, g.local, g.n_pad, R, replica_base, seed, iter,
                                     x, y, xh, active);
@@ -471,8 +605,29 @@ void launch_step_f32(cudaStream_t s, const Graph& g, const StepArgs& a) {
   k_step_f32<<<::qh::counted(grid), 256, 0, s>>>(a);
 }
 
+void launch_step_csr(cudaStream_t s, const Graph& g, const StepArgs& a, const float* pval,
+                     const __nv_bfloat16* xh_in) {
+  if (g.n_pad == 0) return;
+  const unsigned grid = nblk((int64_t)g.n_pad * 32);
+  if (xh_in != nullptr)
+    k_step_csr<true><<<::qh::counted(grid), 256, 0, s>>>(a, g.prow_ptr, g.pcol, pval, xh_in);
+  else
+    k_step_csr<false><<<::qh::counted(grid), 256, 0, s>>>(a, g.prow_ptr, g.pcol, pval, nullptr);
+}
+
+void launch_transpose(cudaStream_t s, const float* in, float* out, int64_t rows, int64_t cols) {
+  if (rows == 0 || cols == 0) return;
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  k_transpose<<<::qh::counted(grid), 256, 0, s>>>(in, out, rows, cols);
+}
+
 void launch_signs(cudaStream_t s, const Graph& g, int32_t R, const float* x, int8_t* signs_t) {
   if (g.n_pad == 0) return;
+  if (g.csr_mode) {  // state already vertex-major
+    const int64_t n = (int64_t)g.n_pad * R;
+    k_signs_vm<<<::qh::counted(nblk(n)), 256, 0, s>>>(x, n, signs_t);
+    return;
+  }
   dim3 grid((g.n_pad + 31) / 32, (R + 31) / 32);
   k_signs_t<<<::qh::counted(grid), 256, 0, s>>>(x, g.n_pad, R, signs_t);
 }

@@ -585,6 +585,30 @@ __global__ void k_tile_flags(int32_t n, const int64_t* __restrict__ rp, const in
 
 }  // namespace
 
+// Padded CSR of J = -w: rows in padded order, columns as padded indices.
+__global__ void k_pcsr_count(int32_t n, const int64_t* __restrict__ rp, const double* __restrict__ w,
+                             const int32_t* __restrict__ pad_index, int64_t* cnt) {
+  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n || pad_index[a] < 0) return;
+  int64_t c = 0;
+  for (int64_t e = rp[a]; e < rp[a + 1]; ++e) c += w[e] != 0.0;
+  cnt[pad_index[a]] = c;
+}
+
+__global__ void k_pcsr_fill(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            const double* __restrict__ w, const int32_t* __restrict__ pad_index,
+                            const int64_t* __restrict__ prow, int32_t* pcol, float* pval) {
+  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n || pad_index[a] < 0) return;
+  int64_t o = prow[pad_index[a]];
+  for (int64_t e = rp[a]; e < rp[a + 1]; ++e) {
+    if (w[e] == 0.0) continue;
+    if (pcol != nullptr) pcol[o] = pad_index[col[e]];
+    pval[o] = (float)(-w[e]);
+    ++o;
+  }
+}
+
 // Tile fill (also used after a refinement sign inversion): J = -w into the
 // FP32 tiles and the BF16 hi (+ lo remainder) tiles.
 __global__ void k_tile_fill(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
@@ -707,6 +731,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     return set_err(ctx, QH_EINVAL,
                    "malformed fragments (SNP out of range, not strictly increasing, or allele not +-1)");
   if (herr & ERR_QUAL) return set_err(ctx, QH_EINVAL, "Phred quality outside [4, 93]");
+  QH_STAGE_CHECK("graph build: validate");
   // ---- SNP -> fragment coverage lists (used by SNP rows and by voting)
   {
     int32_t* cnt = (int32_t*)ctx->scratch(sizeof(int32_t) * (n + 1), 0);
@@ -723,6 +748,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
                                          g->cov_frag, g->cov_allele);
     if (n > 0) k_cov_sort<<<::qh::counted(nblk((int64_t)n * 32)), 256, 0, s>>>(n, g->cov_ptr, g->cov_frag, g->cov_allele);
   }
+  QH_STAGE_CHECK("graph build: coverage lists");
   // ---- edges
   if (o->mode == QH_MODE_READ) {
     g->n_nodes = m;
@@ -791,6 +817,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
                                            g->col, g->w, ctx->d_err);
   }
   const int32_t N = g->n_nodes;
+  QH_STAGE_CHECK("graph build: edges");
   // ---- weight range: integer weights up to 256 are exact in one BF16 operand
   {
     unsigned long long* amax = (unsigned long long*)ctx->scratch(16, 9);
@@ -807,6 +834,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     g->integer_weights = ((int32_t)hv[1] == 0);
     g->has_lo = !(g->integer_weights && mx <= 256.0);
   }
+  QH_STAGE_CHECK("graph build: weight range");
   // ---- components
   int32_t* parent = (int32_t*)ctx->scratch(sizeof(int32_t) * std::max(N, 1), 10);
   int32_t* label = (int32_t*)ctx->scratch(sizeof(int32_t) * std::max(N, 1), 11);
@@ -888,6 +916,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     k_perm_local<<<::qh::counted(nblk(total_in_blocks)), 256, 0, s>>>(total_in_blocks, bkeys, g->block_ptr,
                                                         g->pad_off, g->perm, g->local,
                                                         g->pad_index, g->pad_node);
+  QH_STAGE_CHECK("graph build: components and layout");
   // ---- tile slots: flag nonzero 128 x 128 tiles (all of them in dense mode)
   if (o->dense) {
     std::vector<int32_t> ones(std::max<int64_t>(n_slots, 1), 1);
@@ -906,6 +935,15 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
                               cudaMemcpyDeviceToHost, s));
   QH_CUDA_TRY(cudaStreamSynchronize(s));
   g->n_tiles_hi = h_slot_tile[n_slots];
+  // storage: CSR when the nonzero tiles would be mostly empty and numerous
+  g->csr_mode = o->storage == QH_STORAGE_CSR ||
+                (o->storage == QH_STORAGE_AUTO && !o->dense && g->n_tiles_hi > 4096 &&
+                 g->n_tiles_hi * (int64_t)TILE * TILE > 64 * std::max<int64_t>(g->nnz, 1));
+  if (g->csr_mode) {
+    g->n_tiles_hi = 0;
+    g->has_lo = false;
+    std::fill(h_slot_tile.begin(), h_slot_tile.end(), 0);
+  }
   // row tiles: hi entries then (if needed) lo entries, contiguous per row tile
   g->h_rt.clear();
   std::vector<int32_t> h_rt_of_block(std::max(nb, 1), 0);
@@ -962,10 +1000,31 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
                               cudaMemcpyDeviceToDevice, s));
   QH_CUDA_TRY(cudaMemcpyAsync(g->slot_tile, slot_tile, sizeof(int64_t) * (n_slots + 1),
                               cudaMemcpyDeviceToDevice, s));
+  // padded CSR of J
   {
-    qh_status st = retile(ctx, g, g->w, g->tile_bf16, g->tile_f32);
+    int64_t* pcnt = (int64_t*)ctx->scratch(sizeof(int64_t) * (g->n_pad + 1), 22);
+    g->prow_ptr = (int64_t*)dalloc(*g, sizeof(int64_t) * (g->n_pad + 1));
+    if (!pcnt || !g->prow_ptr) return set_err(ctx, QH_ENOMEM, "allocation failed (padded CSR)");
+    QH_CUDA_TRY(cudaMemsetAsync(pcnt, 0, sizeof(int64_t) * (g->n_pad + 1), s));
+    if (N > 0)
+      k_pcsr_count<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->w, g->pad_index, pcnt);
+    scan_i64(s, pcnt, g->prow_ptr, g->n_pad);
+    int64_t pnnz = 0;
+    QH_CUDA_TRY(cudaMemcpyAsync(&pnnz, g->prow_ptr + g->n_pad, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+    g->pnnz = pnnz;
+    g->pcol = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max<int64_t>(pnnz, 1));
+    g->pval = (float*)dalloc(*g, sizeof(float) * std::max<int64_t>(pnnz, 1));
+    if (!g->pcol || !g->pval) return set_err(ctx, QH_ENOMEM, "allocation failed (padded CSR)");
+    if (N > 0)
+      k_pcsr_fill<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, g->pad_index,
+                                                         g->prow_ptr, g->pcol, g->pval);
+  }
+  {
+    qh_status st = retile(ctx, g, g->w, g->tile_bf16, g->tile_f32, nullptr);
     if (st != QH_OK) return st;
   }
+  QH_STAGE_CHECK("graph build: tiles and padded CSR");
   // ---- per-block sums (sum of w over both triangles, sum of J^2) and default c0
   g->sum_w = (double*)dalloc(*g, sizeof(double) * std::max(nb, 1));
   g->sum_j2 = (double*)dalloc(*g, sizeof(double) * std::max(nb, 1));
@@ -986,11 +1045,16 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     g->h_c0[b] = sigma > 0 ? 0.5 / (sigma * std::sqrt(Nb)) : 0.0;
   }
   g->h_block_ptr = h_block_ptr;
+  QH_STAGE_CHECK("graph build: block sums");
   return QH_OK;
 }
 
-qh_status retile(Ctx* ctx, Graph* g, const double* w, __nv_bfloat16* tb, float* tf) {
+qh_status retile(Ctx* ctx, Graph* g, const double* w, __nv_bfloat16* tb, float* tf, float* pval) {
   cudaStream_t s = ctx->stream;
+  if (pval != nullptr && g->n_nodes > 0)  // padded CSR values (pattern unchanged)
+    k_pcsr_fill<<<::qh::counted(nblk(g->n_nodes)), 256, 0, s>>>(g->n_nodes, g->row_ptr, g->col, w,
+                                                              g->pad_index, g->prow_ptr, nullptr,
+                                                              pval);
   if (g->n_tiles > 0)
     QH_CUDA_TRY(cudaMemsetAsync(tb, 0, sizeof(__nv_bfloat16) * TILE * TILE * g->n_tiles, s));
   if (g->n_tiles_hi > 0)

@@ -63,6 +63,7 @@ extern "C" qh_status qh_matvec_bf16_noalloc(qh_ctx* h, const qh_graph* gh, int32
   ctx->err.clear();
   if (!gh || !x || !z) return set_err(ctx, QH_EINVAL, "NULL argument");
   const Graph& g = gh->g;
+  if (g.csr_mode) return set_err(ctx, QH_EUNSUPPORTED, "the graph is stored as CSR, not as J tiles");
   if (R < 1 || !tc_plan_ok(R, TcPlan{R % 128 == 0 ? 128 : 64, 3}))
     return set_err(ctx, QH_EINVAL, "R must be a positive multiple of 64");
   const int64_t elems = (int64_t)R * g.n_pad;

@@ -95,6 +95,12 @@ struct Graph {
   __nv_bfloat16* tile_bf16 = nullptr;  // [n_tiles][128][128] row-major
   float* tile_f32 = nullptr;           // [n_tiles_hi][128][128] row-major
   std::vector<RowTile> h_rt;
+  // padded CSR of J (always built; the solver's operand when csr_mode)
+  bool csr_mode = false;
+  int64_t pnnz = 0;             // stored entries (w != 0 only)
+  int64_t* prow_ptr = nullptr;  // [n_pad+1]
+  int32_t* pcol = nullptr;      // [nnz] padded column
+  float* pval = nullptr;        // [nnz] J = -w (FP32)
   // per-block constants
   double* sum_w = nullptr;        // [n_blocks] sum_{a,b} w_ab (both triangles)
   double* sum_j2 = nullptr;       // [n_blocks]
@@ -175,7 +181,7 @@ inline int32_t use_lo_for(const Graph& g, int precision) {
 qh_status set_err(Ctx* ctx, qh_status st, const std::string& msg);
 qh_status cuda_fail(Ctx* ctx, cudaError_t e, const char* what);
 void* dalloc(Graph& g, size_t bytes);
-qh_status retile(Ctx* ctx, Graph* g, const double* w, __nv_bfloat16* tb, float* tf);
+qh_status retile(Ctx* ctx, Graph* g, const double* w, __nv_bfloat16* tb, float* tf, float* pval);
 qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opts* o, Graph* g);
 
 // ---- launchers (bsb_simt.cu)
@@ -183,6 +189,11 @@ void launch_init_state(cudaStream_t s, const Graph& g, int32_t R, int32_t replic
                        uint64_t seed, int32_t iter, float* x, float* y, __nv_bfloat16* xh,
                        const int32_t* active);
 void launch_step_f32(cudaStream_t s, const Graph& g, const StepArgs& a);
+// CSR storage: warp per padded vertex, state [n_pad][R]; xh_in != nullptr selects the
+// BF16 X_hat operand, otherwise a.xin (FP32).
+void launch_step_csr(cudaStream_t s, const Graph& g, const StepArgs& a, const float* pval,
+                     const __nv_bfloat16* xh_in);
+void launch_transpose(cudaStream_t s, const float* in, float* out, int64_t rows, int64_t cols);
 void launch_signs(cudaStream_t s, const Graph& g, int32_t R, const float* x, int8_t* signs_t);
 void launch_cut(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t, const double* w,
                 const double* sum_w, double* node_val, double* cuts, const int32_t* active);
@@ -232,6 +243,13 @@ struct qh_graph {
 struct qh_solution {
   qh::Solution s;
 };
+
+// Launch-error check at a stage boundary (kernel launches are not checked one by one).
+#define QH_STAGE_CHECK(name)                                      \
+  do {                                                            \
+    cudaError_t _e = cudaGetLastError();                          \
+    if (_e != cudaSuccess) return qh::cuda_fail(ctx, _e, name);   \
+  } while (0)
 
 #define QH_CUDA_TRY(expr)                                        \
   do {                                                           \

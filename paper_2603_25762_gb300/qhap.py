@@ -29,6 +29,7 @@ MODE_READ, MODE_SNP = 0, 1
 WEIGHT_CONFLICT, WEIGHT_SIGNED = 0, 1
 PREC_FP32, PREC_BF16, PREC_BF16X2 = 0, 1, 2
 SCHED_LINEAR, SCHED_AUTO = 0, 1
+STORAGE_AUTO, STORAGE_TILES, STORAGE_CSR = 0, 1, 2
 
 
 class QhFragments(C.Structure):
@@ -39,7 +40,7 @@ class QhFragments(C.Structure):
 
 class QhGraphOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("weight_mode", C.c_int32), ("linkage_k", C.c_int32),
-                ("dense", C.c_int32), ("porec_alpha", C.c_double)]
+                ("dense", C.c_int32), ("storage", C.c_int32), ("porec_alpha", C.c_double)]
 
 
 class QhBsbOpts(C.Structure):
@@ -236,7 +237,8 @@ class Context:
             raise QhError(st, lib().qh_last_error(self.h).decode())
 
     def build_graph(self, fr=None, mode=MODE_READ, weight_mode=WEIGHT_SIGNED, linkage_k=10,
-                    dense=False, porec_alpha=0.1, arrays=None, on_device=False):
+                    dense=False, porec_alpha=0.1, arrays=None, on_device=False,
+                    storage=STORAGE_AUTO):
         """fr: a synth.Fragments (host); or arrays=(n_snps, frag_ptr, snp, allele, qual, is_porec)
         as numpy (host) or torch CUDA tensors with on_device=True."""
         if arrays is None:
@@ -245,7 +247,7 @@ class Context:
         n_snps, fp, snp, al, q, pc = arrays
         f = QhFragments(int(fp.shape[0]) - 1, int(n_snps), _ptr(fp), _ptr(snp), _ptr(al), _ptr(q),
                         _ptr(pc), 1 if on_device else 0)
-        o = QhGraphOpts(mode, weight_mode, linkage_k, 1 if dense else 0, porec_alpha)
+        o = QhGraphOpts(mode, weight_mode, linkage_k, 1 if dense else 0, storage, porec_alpha)
         g = C.c_void_p()
         self._check(lib().qh_build_graph(self.h, C.byref(f), C.byref(o), C.byref(g)))
         return Graph(self, g)

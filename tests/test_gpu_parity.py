@@ -173,13 +173,14 @@ def _rel_frob(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-def _matvec_case(q, ctx, oracle, fr, mode, precision, R, dense=False, seed=0, bf16_x=False):
+def _matvec_case(q, ctx, oracle, fr, mode, precision, R, dense=False, seed=0, bf16_x=False,
+                 storage=0):
     import torch
     if mode == q.MODE_READ:
-        g = ctx.build_graph(fr, mode=mode, dense=dense)
+        g = ctx.build_graph(fr, mode=mode, dense=dense, storage=storage)
         og = oracle.read_graph(fr, oracle.READ_SIGNED)
     else:
-        g = ctx.build_graph(fr, mode=mode, dense=dense)
+        g = ctx.build_graph(fr, mode=mode, dense=dense, storage=storage)
         og = oracle.snp_graph(fr)
     n_pad, pidx, _ = g.layout()
     rng = np.random.default_rng(seed)
@@ -232,11 +233,12 @@ def test_matvec_snp_graph_hilo(q, ctx, oracle):
 
 
 # ----------------------------------------------------------------------------- one bSB step
+@pytest.mark.parametrize("storage", [1, 2])
 @pytest.mark.parametrize("precision,tol", [(0, 1e-5), (1, 1e-2)])
-def test_steps_match_oracle(q, ctx, oracle, precision, tol):
+def test_steps_match_oracle(q, ctx, oracle, precision, tol, storage):
     import torch
     fr = synth.hifi_region(1002, scale=0.06)
-    g = ctx.build_graph(fr, mode=q.MODE_READ)
+    g = ctx.build_graph(fr, mode=q.MODE_READ, storage=storage)
     og = oracle.read_graph(fr, oracle.READ_SIGNED)
     blocks = oracle.blocks_of(og)
     n_pad, pidx, c0 = g.layout()
@@ -275,8 +277,8 @@ def test_steps_match_oracle(q, ctx, oracle, precision, tol):
 
 
 # ----------------------------------------------------------------------------- full solve
-def _check_solve(q, ctx, oracle, fr, precision, R, steps, seed, n_oracle=None):
-    g = ctx.build_graph(fr, mode=q.MODE_READ)
+def _check_solve(q, ctx, oracle, fr, precision, R, steps, seed, n_oracle=None, storage=0):
+    g = ctx.build_graph(fr, mode=q.MODE_READ, storage=storage)
     sol = ctx.solve(g, replicas=R, steps=steps, precision=precision, seed=seed)
     og = oracle.read_graph(fr, oracle.READ_SIGNED)
     blocks = oracle.blocks_of(og)
@@ -336,6 +338,65 @@ def test_early_stop_and_auto_schedule(q, ctx):
     assert min(runs) < 3000
     sol2 = ctx.solve(g, replicas=64, precision=q.PREC_FP32, seed=2, schedule=q.SCHED_AUTO)
     assert all(sol2.block(b)["steps_run"] == 500 for b in range(g.n_blocks))
+
+
+# ----------------------------------------------------------------------------- CSR storage
+@pytest.mark.parametrize("mode", ["read", "snp"])
+def test_csr_storage_matvec(q, ctx, oracle, mode):
+    if mode == "read":
+        fr, m = synth.hifi_region(1002, scale=0.08), q.MODE_READ
+    else:
+        fr, m = synth.ont_region(1003, scale=0.06), q.MODE_SNP
+    e32 = _matvec_case(q, ctx, oracle, fr, m, q.PREC_FP32, 64, storage=q.STORAGE_CSR)
+    e16 = _matvec_case(q, ctx, oracle, fr, m, q.PREC_BF16, 64, storage=q.STORAGE_CSR)
+    assert e32 <= 1e-5, e32
+    assert e16 <= 1e-2, e16
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_csr_storage_solve_vs_oracle(q, ctx, oracle, precision):
+    _check_solve(q, ctx, oracle, synth.tiny_reads(1001), precision, 64, 2000, seed=11,
+                 storage=q.STORAGE_CSR)
+    g, sol = _check_solve(q, ctx, oracle, synth.hifi_region(1002, scale=0.1), precision, 128,
+                          1000, seed=3, n_oracle=16, storage=q.STORAGE_CSR)
+    assert g.n_tiles == 0 and sol.timing()["kernel"].startswith("csr-warp")
+
+
+def test_csr_storage_early_stop(q, ctx):
+    fr = synth.tiny_reads(1001)
+    g = ctx.build_graph(fr, storage=q.STORAGE_CSR)
+    for prec in (0, 1):
+        sol = ctx.solve(g, replicas=64, steps=3000, precision=prec, seed=2, check_every=50,
+                        patience=3)
+        runs = [sol.block(b)["steps_run"] for b in range(g.n_blocks)]
+        assert all(50 <= r <= 3000 for r in runs) and min(runs) < 3000
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_csr_storage_snp_refinement(q, ctx, oracle, precision):
+    fr = synth.region_reads(32, n_snps=150, region=50_000, n_reads=40, len_mean=8000,
+                            len_sd=2000, flip_p=0.08, miss_p=0.0, qual=(7, 30))
+    g = ctx.build_graph(fr, mode=q.MODE_SNP, storage=q.STORAGE_CSR)
+    sol = ctx.solve(g, replicas=64, steps=300, precision=precision, seed=6, refine_max=15)
+    res = oracle.phase_snp(fr, range(64), 300, seed=6, refine_max=15)
+    og = res["graph"]
+    for b, nodes in enumerate(res["blocks"]):
+        sub = og.subgraph(nodes)
+        info = sol.block(b, len(nodes))
+        p_or = np.where(res["C"][nodes] % 2 == 0, 1, -1).astype(np.int8)
+        assert info["best_cut"] == pytest.approx(oracle.cut(sub, info["spins"]), rel=1e-12, abs=1e-9)
+        assert info["best_cut"] >= 0.999 * oracle.cut(sub, p_or) - 1e-9
+
+
+def test_chromosome_porec_picks_csr(q, ctx):
+    fr = synth.chromosome_porec(1005, scale=0.5)
+    g = ctx.build_graph(fr, mode=q.MODE_SNP, porec_alpha=0.1)
+    assert g.n_tiles == 0, "long-range contacts scatter over most tiles: CSR expected"
+    assert g.n_blocks >= 1 and g.block_sizes().max() > 0.9 * fr.n_snps
+    sol = ctx.solve(g, replicas=64, steps=50, precision=q.PREC_BF16, seed=1, refine_max=1)
+    h1, h2, bid = ctx.phase(g, sol, fr.n_snps)
+    assert sol.timing()["kernel"] == "csr-warp-bf16"
+    assert (h1 != 0).mean() > 0.9
 
 
 # ----------------------------------------------------------------------------- phase
