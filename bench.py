@@ -110,8 +110,13 @@ WORKLOADS = {
                 "ont-snp: 12,000 SNPs / 4 Mb, 3,600 ONT-like reads, SNP graph + refinement"),
     "batched-blocks": ("batched_blocks", "read", 256, 1000,
                        "batched-blocks: 512 HiFi-like blocks of 50-6,000 reads, one launch per step"),
+    "chromosome-porec": ("chromosome_porec", "snp", 128, 2000,
+                         "chromosome-porec: 200,000 SNPs / 250 Mb, 250,000 ONT-like reads + 2M "
+                         "Pore-C contacts, SNP graph (CSR storage), 2 refinement iterations"),
 }
-SEEDS = {"hifi_region": 1002, "ont_region": 1003, "batched_blocks": 1004}
+SEEDS = {"hifi_region": 1002, "ont_region": 1003, "batched_blocks": 1004,
+         "chromosome_porec": 1005}
+REFINE_DEFAULT = {"ont-snp": 15, "chromosome-porec": 2}
 
 
 def _workload(args):
@@ -120,8 +125,11 @@ def _workload(args):
     fr = getattr(synth, gen)(SEEDS[gen])
     R = args.replicas or R
     T = args.bsb_steps or T
+    if args.refine_max <= 0:
+        args.refine_max = REFINE_DEFAULT.get(args.workload, 15)
     cfg = {"workload": desc, "mode": mode, "n_reads": fr.n_frags, "n_snps": fr.n_snps,
            "replicas": R, "bsb_steps": T, "precision": args.precision,
+           "refine_max": REFINE_DEFAULT.get(args.workload, 15) if mode == "snp" else None,
            "l2": "flushed between timed steps (256 MiB write)"}
     return fr, cfg, mode, R, T
 
@@ -135,6 +143,10 @@ def cpu_baseline(args, fr, mode, steps, seed=1):
     reps = args.ref_replicas
     if args.workload == "hifi-region":
         sample_fr, what = fr, f"full graph ({fr.n_frags} reads)"
+    elif args.workload == "chromosome-porec":
+        sample_fr = synth.chromosome_porec(1005, scale=0.05)
+        what = f"1/20-scale chromosome ({sample_fr.n_frags} fragments, {sample_fr.n_snps} SNPs)"
+        reps = min(reps, 16)
     elif args.workload == "ont-snp":
         sample_fr = synth.ont_region(1003, scale=0.25)
         what = f"quarter-size region ({sample_fr.n_frags} reads, {sample_fr.n_snps} SNPs)"
@@ -355,7 +367,7 @@ def main():
     ap.add_argument("--workload", default="hifi-region", choices=sorted(WORKLOADS))
     ap.add_argument("--replicas", type=int, default=0, help="0 = the workload's")
     ap.add_argument("--bsb-steps", type=int, default=0, help="0 = the workload's")
-    ap.add_argument("--refine-max", type=int, default=15)
+    ap.add_argument("--refine-max", type=int, default=0, help="0 = the workload's (SNP graphs)")
     ap.add_argument("--ref-replicas", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--step-kernel", default=None,

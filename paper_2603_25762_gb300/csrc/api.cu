@@ -476,14 +476,35 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
 
   const bool early = o->check_every > 0 && o->patience > 0;
   // ---- the step loop, captured once per shape and replayed
-  char key[512];
-  snprintf(key, sizeof key, "%d|%d|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%lld|%d|%.17g|%.17g",
-           o->precision, R, G.n_row_tiles, max_steps, early ? o->check_every : 0,
-           (void*)W.tile_bf16, (void*)W.tile_f32, (void*)W.w, (void*)B.x, (void*)B.y,
-           (void*)B.x1, (void*)B.xh0, (void*)G.rt, (long long)G.n_tiles, o->patience, o->dt,
-           o->a0);
-  std::string skey = std::string(key) + "|" + std::to_string((uintptr_t)sum_w_work) + "|" +
-                     std::to_string((uintptr_t)G.tile_col);
+  // The captured step loop bakes in pointers and sizes; it is replayed only when every
+  // one of them is unchanged (a rebuilt graph at other addresses is captured anew).
+  std::string skey;
+  {
+    auto add = [&skey](const void* p) { skey += std::to_string((uintptr_t)p) + "|"; };
+    auto addi = [&skey](long long v) { skey += std::to_string(v) + "|"; };
+    addi(o->precision); addi(R); addi(max_steps); addi(early ? o->check_every : 0);
+    addi(o->patience);
+    char d[64];
+    snprintf(d, sizeof d, "%.17g|%.17g|", o->dt, o->a0);
+    skey += d;
+    addi(G.n_nodes); addi(G.n_pad); addi(G.n_blocks); addi(G.n_row_tiles); addi(G.n_tiles);
+    addi(G.n_tiles_hi); addi(G.has_lo); addi(G.csr_mode); addi(G.integer_weights);
+    addi(G.max_tiles_per_row); addi(G.pnnz); addi(G.nnz);
+    for (const void* p : {(const void*)G.rt, (const void*)G.tile_col, (const void*)W.tile_bf16,
+                          (const void*)W.tile_f32, (const void*)G.prow_ptr, (const void*)G.pcol,
+                          (const void*)W.pval, (const void*)G.row_ptr, (const void*)G.col,
+                          (const void*)W.w, (const void*)G.block_of, (const void*)G.pad_index,
+                          (const void*)G.pad_node, (const void*)G.local, (const void*)G.pad_off,
+                          (const void*)G.block_ptr, (const void*)G.perm, (const void*)sum_w_work})
+      add(p);
+    for (const void* p : {(const void*)B.x, (const void*)B.y, (const void*)B.x1, (const void*)B.xh0,
+                          (const void*)B.xh1, (const void*)B.signs, (const void*)B.node_val,
+                          (const void*)B.cuts, (const void*)B.best_r, (const void*)B.best_cut,
+                          (const void*)B.running, (const void*)B.steps_b, (const void*)B.c0,
+                          (const void*)B.seen, (const void*)B.stall, (const void*)B.steps_run,
+                          (const void*)ctx->d_err})
+      add(p);
+  }
   StepArgs a{};
   a.rt = G.rt;
   a.tile_col = G.tile_col;

@@ -210,25 +210,43 @@ __global__ void __launch_bounds__(256) k_step_csr(StepArgs a, const int64_t* __r
       const int ne = (e1 - e) < 32 ? (int)(e1 - e) : 32;
       const int32_t cl = lane < ne ? pcol[e + lane] : 0;
       const float vl = lane < ne ? pval[e + lane] : 0.f;
-      for (int k = 0; k < ne; ++k) {
-        const int32_t cc = __shfl_sync(0xffffffffu, cl, k);
-        const float jv = __shfl_sync(0xffffffffu, vl, k);
+      // lanes >= ne hold column 0 and J = 0: a valid address contributing nothing
+      for (int k = 0; k < ne; k += 4) {
+        int32_t cc[4];
+        float jv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          cc[q] = __shfl_sync(0xffffffffu, cl, (k + q) & 31);
+          jv[q] = __shfl_sync(0xffffffffu, vl, (k + q) & 31);
+          if (k + q >= ne) jv[q] = 0.f;
+        }
         if (!on) continue;
-        const size_t off = (size_t)cc * a.R + r;
         if (BF16) {
-          const uint2 u = *reinterpret_cast<const uint2*>(xh_in + off);
-          const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&u.x);
-          const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&u.y);
-          acc[0] = fmaf(jv, __low2float(lo), acc[0]);
-          acc[1] = fmaf(jv, __high2float(lo), acc[1]);
-          acc[2] = fmaf(jv, __low2float(hi), acc[2]);
-          acc[3] = fmaf(jv, __high2float(hi), acc[3]);
+          uint2 u[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            u[q] = *reinterpret_cast<const uint2*>(xh_in + (size_t)cc[q] * a.R + r);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&u[q].x);
+            const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&u[q].y);
+            acc[0] = fmaf(jv[q], __low2float(lo), acc[0]);
+            acc[1] = fmaf(jv[q], __high2float(lo), acc[1]);
+            acc[2] = fmaf(jv[q], __low2float(hi), acc[2]);
+            acc[3] = fmaf(jv[q], __high2float(hi), acc[3]);
+          }
         } else {
-          const float4 xv = *reinterpret_cast<const float4*>(a.xin + off);
-          acc[0] = fmaf(jv, xv.x, acc[0]);
-          acc[1] = fmaf(jv, xv.y, acc[1]);
-          acc[2] = fmaf(jv, xv.z, acc[2]);
-          acc[3] = fmaf(jv, xv.w, acc[3]);
+          float4 xv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            xv[q] = *reinterpret_cast<const float4*>(a.xin + (size_t)cc[q] * a.R + r);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            acc[0] = fmaf(jv[q], xv[q].x, acc[0]);
+            acc[1] = fmaf(jv[q], xv[q].y, acc[1]);
+            acc[2] = fmaf(jv[q], xv[q].z, acc[2]);
+            acc[3] = fmaf(jv[q], xv[q].w, acc[3]);
+          }
         }
       }
     }
@@ -290,15 +308,16 @@ __global__ void k_signs_t(const float* __restrict__ x, int32_t n_pad, int32_t R,
   }
 }
 
-// Warp per vertex a: node_val[pad(a)][r] = s_a * sum_b w_ab s_b.  One pass over the
-// vertex's edges covers up to 1,024 replicas: lane l owns replicas 32 l .. 32 l + 31
-// (eight 4-byte sign loads per edge, the warp reading 1 KiB contiguous).  Integer
-// weights accumulate in int32 (row sums stay far below 2^31), real ones in FP64.
+// Warp per vertex a: node_val[pad(a)][r] = s_a * sum_b w_ab s_b.  Lane l owns `per`
+// consecutive replicas (a multiple of 4, at most 32, sized so the warp spans R), so one
+// pass over the vertex's edges covers up to 1,024 replicas with 4-byte sign loads.
+// Integer weights accumulate in int32 (row sums stay far below 2^31), real in FP64.
 template <bool INT>
 __global__ void k_cut_nodes(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                             const double* __restrict__ w, const int32_t* __restrict__ block_of,
                             const int32_t* __restrict__ pad_index, const int8_t* __restrict__ st,
-                            int32_t R, double* node_val, const int32_t* __restrict__ active) {
+                            int32_t R, int32_t per, double* node_val,
+                            const int32_t* __restrict__ active) {
   int32_t a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (a >= n) return;
@@ -308,38 +327,40 @@ __global__ void k_cut_nodes(int32_t n, const int64_t* __restrict__ rp, const int
   const int64_t e0 = rp[a], e1 = rp[a + 1];
   const bool vec = (R & 3) == 0;
   using Acc = typename std::conditional<INT, int32_t, double>::type;
-  for (int32_t r0 = 0; r0 < R; r0 += 1024) {
-    const int32_t r = r0 + 32 * lane;
-    const int nr = max(0, min(32, R - r));
+  for (int32_t r0 = 0; r0 < R; r0 += 32 * per) {
+    const int32_t r = r0 + per * lane;
+    const int nr = max(0, min(per, R - r));
     Acc acc[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) acc[k] = 0;
-    for (int64_t e = e0; e < e1; ++e) {
-      const double we = w[e];
-      if (we == 0.0) continue;  // zero edges may reach vertices outside every block
-      if (nr == 0) continue;
-      const int8_t* sb = st + (size_t)pad_index[col[e]] * R + r;
-      if (vec && nr == 32) {
+    if (nr > 0) {
+      for (int64_t e = e0; e < e1; ++e) {
+        const double we = w[e];
+        if (we == 0.0) continue;  // zero edges may reach vertices outside every block
+        const int8_t* sb = st + (size_t)pad_index[col[e]] * R + r;
+        if (vec && nr == per) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          char4 c = *reinterpret_cast<const char4*>(sb + 4 * q);
-          if (INT) {
-            const int32_t wi = (int32_t)we;
-            acc[4 * q + 0] += wi * c.x;
-            acc[4 * q + 1] += wi * c.y;
-            acc[4 * q + 2] += wi * c.z;
-            acc[4 * q + 3] += wi * c.w;
-          } else {
-            acc[4 * q + 0] += we * (double)c.x;
-            acc[4 * q + 1] += we * (double)c.y;
-            acc[4 * q + 2] += we * (double)c.z;
-            acc[4 * q + 3] += we * (double)c.w;
+          for (int q = 0; q < 8; ++q) {
+            if (4 * q >= per) break;
+            char4 c = *reinterpret_cast<const char4*>(sb + 4 * q);
+            if (INT) {
+              const int32_t wi = (int32_t)we;
+              acc[4 * q + 0] += wi * c.x;
+              acc[4 * q + 1] += wi * c.y;
+              acc[4 * q + 2] += wi * c.z;
+              acc[4 * q + 3] += wi * c.w;
+            } else {
+              acc[4 * q + 0] += we * (double)c.x;
+              acc[4 * q + 1] += we * (double)c.y;
+              acc[4 * q + 2] += we * (double)c.z;
+              acc[4 * q + 3] += we * (double)c.w;
+            }
           }
-        }
-      } else {
+        } else {
 #pragma unroll
-        for (int k = 0; k < 32; ++k)
-          if (k < nr) acc[k] += (Acc)(INT ? (double)(int32_t)we * sb[k] : we * (double)sb[k]);
+          for (int k = 0; k < 32; ++k)
+            if (k < nr) acc[k] += (Acc)(INT ? (double)(int32_t)we * sb[k] : we * (double)sb[k]);
+        }
       }
     }
     const int8_t* sa = st + (size_t)pa * R + r;
@@ -635,12 +656,15 @@ void launch_signs(cudaStream_t s, const Graph& g, int32_t R, const float* x, int
 void launch_cut(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t, const double* w,
                 const double* sum_w, double* node_val, double* cuts, const int32_t* active) {
   if (g.n_blocks == 0) return;
+  // replicas per lane: a multiple of 4 in [4, 32] so that one warp pass spans R
+  int32_t per = (((R + 31) / 32) + 3) / 4 * 4;
+  per = per < 4 ? 4 : (per > 32 ? 32 : per);
   if (g.integer_weights)
     k_cut_nodes<true><<<::qh::counted(nblk((int64_t)g.n_nodes * 32)), 256, 0, s>>>(
-        g.n_nodes, g.row_ptr, g.col, w, g.block_of, g.pad_index, signs_t, R, node_val, active);
+        g.n_nodes, g.row_ptr, g.col, w, g.block_of, g.pad_index, signs_t, R, per, node_val, active);
   else
     k_cut_nodes<false><<<::qh::counted(nblk((int64_t)g.n_nodes * 32)), 256, 0, s>>>(
-        g.n_nodes, g.row_ptr, g.col, w, g.block_of, g.pad_index, signs_t, R, node_val, active);
+        g.n_nodes, g.row_ptr, g.col, w, g.block_of, g.pad_index, signs_t, R, per, node_val, active);
   dim3 grid((R + 31) / 32, g.n_blocks);
   k_cut_reduce<<<::qh::counted(grid), 1024, 0, s>>>(g.n_blocks, g.pad_off, g.block_ptr, R, node_val, sum_w, cuts,
                                      active);

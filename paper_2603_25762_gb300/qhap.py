@@ -22,7 +22,7 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libqhap.so")
+LIB_PATH = os.environ.get("QHAP_LIB") or os.path.join(HERE, "libqhap.so")
 
 QH_OK, QH_EINVAL, QH_ENOMEM, QH_ECUDA, QH_ETIMEOUT, QH_EUNSUPPORTED = range(6)
 MODE_READ, MODE_SNP = 0, 1

@@ -388,6 +388,28 @@ def test_csr_storage_snp_refinement(q, ctx, oracle, precision):
         assert info["best_cut"] >= 0.999 * oracle.cut(sub, p_or) - 1e-9
 
 
+@pytest.mark.parametrize("storage", [1, 2])
+def test_rebuilt_graphs_never_replay_stale_loops(q, ctx, storage):
+    # the captured step loop is reused only while every pointer it bakes in is unchanged:
+    # rebuild the same input with device allocations in between (addresses shift), with
+    # the early-stop cut kernels inside the loop, and expect identical results
+    import torch
+    fr = synth.hifi_region(1002, scale=0.06)
+    ref, pads = None, []
+    for i in range(4):
+        pads.append(torch.empty((i + 1) * 3_000_000, dtype=torch.uint8, device="cuda"))
+        g = ctx.build_graph(fr, storage=storage)
+        pads.append(torch.empty(1_000_000 * (4 - i), dtype=torch.uint8, device="cuda"))
+        sol = ctx.solve(g, replicas=64, steps=200, precision=q.PREC_BF16, seed=4, check_every=40,
+                        patience=50)
+        cuts = sol.cuts()
+        sol.free()
+        g.free()
+        if ref is None:
+            ref = cuts
+        assert np.array_equal(cuts, ref), i
+
+
 def test_chromosome_porec_picks_csr(q, ctx):
     fr = synth.chromosome_porec(1005, scale=0.5)
     g = ctx.build_graph(fr, mode=q.MODE_SNP, porec_alpha=0.1)
