@@ -125,15 +125,25 @@ qh_status check_err_word(Ctx* ctx) {
 
 // Time every valid step-kernel variant on the live state for a few steps and keep
 // the fastest for this graph shape.  The state is re-initialised afterwards.
-qh_status autotune(Ctx* ctx, const Graph& g, StepArgs a, const SolveBufs& B, int R, TcPlan* plan) {
+std::string tune_key(const Graph& g, int R, int use_lo) {
   char kb[160];
-  snprintf(kb, sizeof kb, "%d|%d|%lld|%d|%d", R, g.n_row_tiles, (long long)g.n_tiles,
-           g.max_tiles_per_row, g.n_pad);
+  snprintf(kb, sizeof kb, "%d|%d|%lld|%d|%d|%d", R, g.n_row_tiles, (long long)g.n_tiles,
+           g.max_tiles_per_row, g.n_pad, use_lo);
+  return kb;
+}
+
+bool tuned_variant(Ctx* ctx, const Graph& g, int R, TcPlan* plan) {
+  const std::string kb = tune_key(g, R, 0);
   for (auto& kv : ctx->tuned)
     if (kv.first == kb) {
       plan->variant = kv.second;
-      return QH_OK;
+      return true;
     }
+  return false;
+}
+
+qh_status autotune(Ctx* ctx, const Graph& g, StepArgs a, const SolveBufs& B, int R, TcPlan* plan) {
+  const std::string kb = tune_key(g, R, 0);
   cudaStream_t s = ctx->stream;
   float best = 1e30f;
   int best_v = -1;
@@ -525,14 +535,17 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   TcPlan tplan = plan;
   a.use_lo = use_lo_for(G, o->precision);
   if (is_tc_precision(o->precision)) {
-    QH_CUDA_TRY(cudaMemcpyAsync(B.running, B.active, nb * 4, cudaMemcpyDeviceToDevice, s));
-    launch_init_state(s, W, R, o->replica_base, o->seed, 0, B.x, B.y, B.xh0, B.active);
-    QH_STAGE_CHECK("solve: state init (tuning)");
     qh_status st = QH_OK;
-    if (o->step_kernel >= 0)
+    if (o->step_kernel >= 0) {
       tplan.variant = o->step_kernel;
-    else if (!G.csr_mode)
-      st = autotune(ctx, W, a, B, R, &tplan);
+    } else if (!G.csr_mode) {
+      if (!tuned_variant(ctx, G, R, &tplan)) {  // first solve of this shape: time the variants
+        QH_CUDA_TRY(cudaMemcpyAsync(B.running, B.active, nb * 4, cudaMemcpyDeviceToDevice, s));
+        launch_init_state(s, W, R, o->replica_base, o->seed, 0, B.x, B.y, B.xh0, B.active);
+        QH_STAGE_CHECK("solve: state init (tuning)");
+        st = autotune(ctx, W, a, B, R, &tplan);
+      }
+    }
     if (st != QH_OK) {
       delete sh;
       return st;
