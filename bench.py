@@ -239,7 +239,8 @@ def run_ours(args):
     from paper_2603_25762_gb300 import build, qhap
     build.build()
     fr, cfg, mode, R, T = _workload(args)
-    prec = {"bf16": qhap.PREC_BF16, "bf16x2": qhap.PREC_BF16X2, "fp32": qhap.PREC_FP32}[args.precision]
+    prec = {"bf16": qhap.PREC_BF16, "bf16x2": qhap.PREC_BF16X2, "fp8": qhap.PREC_FP8,
+            "fp32": qhap.PREC_FP32}[args.precision]
     gmode = qhap.MODE_READ if mode == "read" else qhap.MODE_SNP
     stream = torch.cuda.Stream()
     ctx = qhap.Context(local, stream=stream.cuda_stream)
@@ -327,7 +328,7 @@ def run_ours(args):
     launch_us = statistics.mean(step_ms) * 1e3
     # state traffic per spin update + each stored J nonzero read once (BF16: 2 B, FP32: 4 B)
     n_launch = max(1, stats["timing"]["n_step_launches"])
-    per_launch_bytes = units / n_launch * SPIN_BYTES + stats["nnz"] * (2 if prec else 4)
+    per_launch_bytes = units / n_launch * SPIN_BYTES + stats["nnz"] * (4 if prec == qhap.PREC_FP32 else 2)
     achieved = per_launch_bytes / (launch_us * 1e-6) / 1e9
     traffic = _profiled_traffic(stats["timing"]["kernel"]) if args.workload == "hifi-region" else None
     h2d = sum(int(a.nbytes) for a in pinned_np[1:])
@@ -368,7 +369,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16x2", "fp32"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16x2", "fp8", "fp32"])
     ap.add_argument("--workload", default="hifi-region", choices=sorted(WORKLOADS))
     ap.add_argument("--replicas", type=int, default=0, help="0 = the workload's")
     ap.add_argument("--bsb-steps", type=int, default=0, help="0 = the workload's")

@@ -58,8 +58,11 @@ enum { QH_WEIGHT_CONFLICT = 0, QH_WEIGHT_SIGNED = 1 };
  * BF16: tcgen05 BF16 x BF16 -> FP32 accumulate, X_hat = bf16(x).  J is rounded to
  *   BF16 (exact for integer |w| <= 256; larger integers are split J = hi + lo,
  *   both BF16, in the same accumulator, so integer J stays exact).
- * BF16X2: as BF16, with real weights also split into hi + lo (J to ~2^-17). */
-enum { QH_PREC_FP32 = 0, QH_PREC_BF16 = 1, QH_PREC_BF16X2 = 2 };
+ * BF16X2: as BF16, with real weights also split into hi + lo (J to ~2^-17).
+ * FP8: tcgen05 kind::f8f6f4 (e4m3) with FP32 accumulate: s*J = Jh + Jl and
+ *   x = xh + xl in e4m3 (s a power of two: 1 for integer |w| < 256, else scaled to
+ *   240), Z = (Jh Xh + Jh Xl + Jl Xh) / s (tile storage only). */
+enum { QH_PREC_FP32 = 0, QH_PREC_BF16 = 1, QH_PREC_BF16X2 = 2, QH_PREC_FP8 = 3 };
 /* Schedules: LINEAR = a(t) = a0 * t / steps with the given steps;
  * AUTO = steps chosen from the block size as in the paper's SNP-based runs
  * (500 iterations for < 5,000 nodes, 1,000 otherwise). */

@@ -68,7 +68,7 @@ enum {
   S_X = 32, S_Y, S_X1, S_XH0, S_XH1, S_SIGNS, S_NODEVAL, S_CUTS, S_BESTR, S_BESTCUT, S_ACTIVE,
   S_STEPSB, S_C0, S_SEEN, S_STALL, S_STEPSRUN, S_SPINS, S_C, S_WWORK, S_TBWORK, S_TFWORK,
   S_SUMW, S_SUMJ2, S_NODETMP, S_SIGNS1, S_NODEVAL1, S_CUT1, S_DBG0, S_DBG1, S_DBG2, S_RUNNING,
-  S_PVWORK, S_TR0, S_TR1
+  S_PVWORK, S_TR0, S_TR1, S_F8H, S_F8L, S_F8FLAG, S_X8
 };
 
 struct SolveBufs {
@@ -84,7 +84,15 @@ struct SolveBufs {
 
 qh_status run_step(Ctx* ctx, const Graph& g, int precision, const TcPlan& plan, StepArgs a,
                    const float* x_cur_f32, float* x_next_f32, const __nv_bfloat16* xh_cur,
-                   __nv_bfloat16* xh_next) {
+                   __nv_bfloat16* xh_next, const Fp8Operands* f8 = nullptr, int64_t ns = 0) {
+  if (precision == QH_PREC_FP8) {  // X_hat buffers hold the e4m3 hi part, then the lo part
+    Fp8Operands op = *f8;
+    op.xh_in = reinterpret_cast<const uint8_t*>(xh_cur);
+    op.xl_in = op.xh_in + ns;
+    a.x8h_out = reinterpret_cast<uint8_t*>(xh_next);
+    a.x8l_out = a.x8h_out + ns;
+    return launch_step_f8(ctx, g, a, op);
+  }
   if (precision == QH_PREC_FP32) {
     a.xin = x_cur_f32;
     a.xout = x_next_f32;
@@ -362,7 +370,12 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   if (R < 1) return set_err(ctx, QH_EINVAL, "replicas must be >= 1");
   if (o->schedule != QH_SCHED_LINEAR && o->schedule != QH_SCHED_AUTO) return set_err(ctx, QH_EINVAL, "bad schedule");
   if (o->schedule == QH_SCHED_LINEAR && o->steps < 1) return set_err(ctx, QH_EINVAL, "steps must be >= 1");
-  if (o->precision != QH_PREC_FP32 && !is_tc_precision(o->precision)) return set_err(ctx, QH_EINVAL, "bad precision");
+  if (o->precision != QH_PREC_FP32 && !is_tc_precision(o->precision) && o->precision != QH_PREC_FP8)
+    return set_err(ctx, QH_EINVAL, "bad precision");
+  if (o->precision == QH_PREC_FP8 && G.csr_mode)
+    return set_err(ctx, QH_EUNSUPPORTED, "FP8 needs tile storage (the graph is stored as CSR)");
+  if (o->precision == QH_PREC_FP8 && R % 64 != 0)
+    return set_err(ctx, QH_EINVAL, "FP8 precision needs replicas to be a multiple of 64");
   if (!(o->dt > 0.0) || !(o->a0 > 0.0)) return set_err(ctx, QH_EINVAL, "dt and a0 must be > 0");
   if (o->check_every < 0 || o->patience < 0 || o->replica_base < 0) return set_err(ctx, QH_EINVAL, "negative option");
   if ((int64_t)o->replica_base + R > (1 << 16)) return set_err(ctx, QH_EINVAL, "replica indices must stay below 65536");
@@ -470,6 +483,38 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     delete sh;
     return set_err(ctx, QH_ENOMEM, "device allocation failed (solver state)");
   }
+  // FP8: e4m3 hi / lo tiles of s*J from the (working) FP32 tiles
+  const bool fp8 = o->precision == QH_PREC_FP8;
+  Fp8Operands f8{};
+  const float f8_s = fp8 ? fp8_scale(G) : 1.f;
+  uint8_t *f8_jh = nullptr, *f8_jl = nullptr;
+  int32_t* f8_flag = nullptr;
+  const int64_t f8_n = G.n_tiles_hi * (int64_t)TILE * TILE;
+  auto convert_fp8_tiles = [&]() -> qh_status {
+    QH_CUDA_TRY(cudaMemsetAsync(f8_flag, 0, 4, s));
+    launch_tiles_to_e4m3(s, W.tile_f32, f8_n, f8_s, f8_jh, f8_jl, f8_flag);
+    int32_t hl = 0;
+    QH_CUDA_TRY(cudaMemcpyAsync(&hl, f8_flag, 4, cudaMemcpyDeviceToHost, s));
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+    f8.n_slices = hl ? 3 : 2;
+    return QH_OK;
+  };
+  if (fp8) {
+    f8_jh = (uint8_t*)sc(std::max<int64_t>(f8_n, 1), S_F8H);
+    f8_jl = (uint8_t*)sc(std::max<int64_t>(f8_n, 1), S_F8L);
+    f8_flag = (int32_t*)sc(16, S_F8FLAG);
+    if (!f8_jh || !f8_jl || !f8_flag) {
+      delete sh;
+      return set_err(ctx, QH_ENOMEM, "device allocation failed (FP8 tiles)");
+    }
+    qh_status st = convert_fp8_tiles();
+    if (st != QH_OK) {
+      delete sh;
+      return st;
+    }
+    f8.jh = f8_jh;
+    f8.jl = f8_jl;
+  }
   QH_CUDA_TRY(cudaMemcpyAsync(B.steps_b, h_steps.data(), nb * 4, cudaMemcpyHostToDevice, s));
   QH_CUDA_TRY(cudaMemcpyAsync(B.c0, h_c0.data(), nb * 4, cudaMemcpyHostToDevice, s));
   QH_CUDA_TRY(cudaMemsetAsync(B.C, 0, (G.n_nodes + 1) * 4, s));
@@ -500,6 +545,8 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     addi(G.n_nodes); addi(G.n_pad); addi(G.n_blocks); addi(G.n_row_tiles); addi(G.n_tiles);
     addi(G.n_tiles_hi); addi(G.has_lo); addi(G.csr_mode); addi(G.integer_weights);
     addi(G.max_tiles_per_row); addi(G.pnnz); addi(G.nnz);
+    addi(f8.n_slices); add(f8_jh); add(f8_jl);
+    skey += std::to_string(f8_s) + "|";
     for (const void* p : {(const void*)G.rt, (const void*)G.tile_col, (const void*)W.tile_bf16,
                           (const void*)W.tile_f32, (const void*)G.prow_ptr, (const void*)G.pcol,
                           (const void*)W.pval, (const void*)G.row_ptr, (const void*)G.col,
@@ -534,6 +581,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   if (o->precision == QH_PREC_FP32 && (max_steps % 2 == 1)) x_final = B.x1;
   TcPlan tplan = plan;
   a.use_lo = use_lo_for(G, o->precision);
+  a.inv_scale = 1.f / f8_s;
   if (is_tc_precision(o->precision)) {
     qh_status st = QH_OK;
     if (o->step_kernel >= 0) {
@@ -552,6 +600,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     }
   }
   sol.kernel = G.csr_mode ? (is_tc_precision(o->precision) ? "csr-warp-bf16" : "csr-warp-fp32")
+              : fp8 ? (R % 128 == 0 ? "e4m3-bn128-s2-x3" : "e4m3-bn64-s2-x4")
               : is_tc_precision(o->precision) ? tc_variant_name(tplan.variant) : "k_step_f32";
   skey += "|v" + std::to_string(tplan.variant);
   if (ctx->loop_key != skey || !ctx->loop_exec) {
@@ -569,7 +618,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
       a.t = t;
       const bool even = (t % 2) == 0;
       st = run_step(ctx, W, o->precision, tplan, a, even ? B.x : B.x1, even ? B.x1 : B.x,
-                    even ? B.xh0 : B.xh1, even ? B.xh1 : B.xh0);
+                    even ? B.xh0 : B.xh1, even ? B.xh1 : B.xh0, &f8, (int64_t)NS);
       if (early && (t + 1) % o->check_every == 0 && t + 1 < max_steps) {
         const float* xc = (o->precision == QH_PREC_FP32 && even) ? B.x1 : B.x;
         launch_signs(s, W, R, xc, B.signs);
@@ -617,6 +666,9 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     QH_CUDA_TRY(cudaMemcpyAsync(B.running, B.active, nb * 4, cudaMemcpyDeviceToDevice, s));
     launch_init_state(s, W, R, o->replica_base, o->seed, it, B.x, B.y,
                       is_tc_precision(o->precision) ? B.xh0 : nullptr, B.active);
+    if (fp8)
+      launch_x_to_e4m3(s, B.x, (int64_t)NS, reinterpret_cast<uint8_t*>(B.xh0),
+                       reinterpret_cast<uint8_t*>(B.xh0) + NS);
     QH_STAGE_CHECK("solve: state init");
     QH_CUDA_TRY(cudaEventRecord(ctx->ev[2], s));
     QH_CUDA_TRY(cudaGraphLaunch(ctx->loop_exec, s));
@@ -663,6 +715,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     launch_gauge(s, W, B.spins, W.w, B.active);
     {
       qh_status st = retile(ctx, &W, W.w, W.tile_bf16, W.tile_f32, W.csr_mode ? W.pval : nullptr);
+      if (st == QH_OK && fp8) st = convert_fp8_tiles();
       if (st != QH_OK) {
         delete sh;
         return st;
@@ -855,9 +908,30 @@ qh_status qh_debug_layout(qh_ctx* h, const qh_graph* gh, int32_t* n_pad, int32_t
   return QH_OK;
 }
 
+static qh_status debug_fp8_tiles(Ctx* ctx, const Graph& g, Fp8Operands* f8, float* scale) {
+  const int64_t n = g.n_tiles_hi * (int64_t)TILE * TILE;
+  uint8_t* jh = (uint8_t*)ctx->scratch(std::max<int64_t>(n, 1), S_F8H);
+  uint8_t* jl = (uint8_t*)ctx->scratch(std::max<int64_t>(n, 1), S_F8L);
+  int32_t* flag = (int32_t*)ctx->scratch(16, S_F8FLAG);
+  if (!jh || !jl || !flag) return set_err(ctx, QH_ENOMEM, "allocation failed (FP8 tiles)");
+  *scale = fp8_scale(g);
+  QH_CUDA_TRY(cudaMemsetAsync(flag, 0, 4, ctx->stream));
+  launch_tiles_to_e4m3(ctx->stream, g.tile_f32, n, *scale, jh, jl, flag);
+  int32_t hl = 0;
+  QH_CUDA_TRY(cudaMemcpyAsync(&hl, flag, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  QH_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  f8->jh = jh;
+  f8->jl = jl;
+  f8->n_slices = hl ? 3 : 2;
+  return QH_OK;
+}
+
 static qh_status debug_common(Ctx* ctx, const Graph& g, int precision, int32_t R, StepArgs& a,
                               const double* c0_per_block, int32_t steps) {
-  if (precision != QH_PREC_FP32 && !is_tc_precision(precision)) return set_err(ctx, QH_EINVAL, "bad precision");
+  if (precision != QH_PREC_FP32 && !is_tc_precision(precision) && precision != QH_PREC_FP8)
+    return set_err(ctx, QH_EINVAL, "bad precision");
+  if (precision == QH_PREC_FP8 && (g.csr_mode || R % 64 != 0))
+    return set_err(ctx, QH_EINVAL, "FP8 needs tile storage and R a multiple of 64");
   if (R < 1) return set_err(ctx, QH_EINVAL, "R must be >= 1");
   if (is_tc_precision(precision) && !g.csr_mode && !tc_plan_ok(R, pick_plan(R)))
     return set_err(ctx, QH_EINVAL, "BF16 precision needs R to be a multiple of 64");
@@ -919,7 +993,21 @@ qh_status qh_debug_matvec(qh_ctx* h, const qh_graph* gh, int32_t precision, int3
     QH_CUDA_TRY(cudaGetLastError());
     return check_err_word(ctx);
   }
-  if (precision == QH_PREC_FP32) {
+  if (precision == QH_PREC_FP8) {
+    Fp8Operands f8{};
+    float sc8 = 1.f;
+    st = debug_fp8_tiles(ctx, g, &f8, &sc8);
+    if (st) return st;
+    const int64_t NS = (int64_t)R * g.n_pad;
+    uint8_t* x8 = (uint8_t*)ctx->scratch((size_t)NS * 2, S_X8);
+    if (!x8) return set_err(ctx, QH_ENOMEM, "allocation failed (debug)");
+    launch_x_to_e4m3(ctx->stream, x, NS, x8, x8 + NS);
+    f8.xh_in = x8;
+    f8.xl_in = x8 + NS;
+    a.inv_scale = 1.f / sc8;
+    st = launch_step_f8(ctx, g, a, f8);
+    if (st) return st;
+  } else if (precision == QH_PREC_FP32) {
     a.xin = x;
     a.xout = nullptr;
     launch_step_f32(ctx->stream, g, a);
@@ -981,8 +1069,31 @@ qh_status qh_debug_steps(qh_ctx* h, const qh_graph* gh, int32_t precision, int32
     __nv_bfloat16* xh0 = (__nv_bfloat16*)ctx->scratch(NS * 2, S_XH0);
     __nv_bfloat16* xh1 = (__nv_bfloat16*)ctx->scratch(NS * 2, S_XH1);
     if (!xh0 || !xh1) return set_err(ctx, QH_ENOMEM, "allocation failed (debug)");
-    launch_f32_to_bf16(s, x, xh0, (int64_t)NS);
     QH_CUDA_TRY(cudaMemsetAsync(xh1, 0, NS * 2, s));
+    if (precision == QH_PREC_FP8) {
+      Fp8Operands f8{};
+      float sc8 = 1.f;
+      st = debug_fp8_tiles(ctx, g, &f8, &sc8);
+      if (st) return st;
+      a.inv_scale = 1.f / sc8;
+      uint8_t* b0 = reinterpret_cast<uint8_t*>(xh0);
+      uint8_t* b1 = reinterpret_cast<uint8_t*>(xh1);
+      launch_x_to_e4m3(s, x, (int64_t)NS, b0, b0 + NS);
+      for (int32_t k = 0; k < nsteps; ++k) {
+        a.t = t0 + k;
+        uint8_t* cur = (k % 2 == 0) ? b0 : b1;
+        uint8_t* nxt = (k % 2 == 0) ? b1 : b0;
+        f8.xh_in = cur;
+        f8.xl_in = cur + NS;
+        a.x8h_out = nxt;
+        a.x8l_out = nxt + NS;
+        st = launch_step_f8(ctx, g, a, f8);
+        if (st) return st;
+      }
+      QH_CUDA_TRY(cudaGetLastError());
+      return check_err_word(ctx);
+    }
+    launch_f32_to_bf16(s, x, xh0, (int64_t)NS);
     for (int32_t k = 0; k < nsteps; ++k) {
       a.t = t0 + k;
       a.xh_out = (k % 2 == 0) ? xh1 : xh0;

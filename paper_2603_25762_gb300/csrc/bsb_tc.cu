@@ -13,6 +13,7 @@
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp8.h>
 
 #include "qh_internal.cuh"
 
@@ -420,6 +421,201 @@ __global__ void __launch_bounds__(128, MINB) k_step_tc_v(const __grid_constant__
     tc_fence_after();
     tmem_dealloc(tmem, (uint32_t)BN);
   }
+}
+
+// ---------------------------------------------------------------------------
+// FP8 (e4m3) variant.  With J' = s J split as J' = Jh + Jl and x = xh + xl (all e4m3,
+// s a power of two), each nonzero tile contributes the slices (Jh, Xh), (Jh, Xl) and,
+// when J' has a remainder, (Jl, Xh) -- the dropped Jl Xl term is ~2^-8 relative.  A
+// slice is one 128 x 128-byte K-slice of A and B (four K = 32 kind::f8f6f4 MMAs), so
+// stages, descriptors and smem layout are those of the BF16 kernel.  Z = acc / s.
+__device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3, both K-major, M = 128.
+template <int BN>
+__device__ __forceinline__ constexpr uint32_t idesc_e4m3() {
+  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void split_e4m3(float x, uint8_t& h, uint8_t& l) {
+  __nv_fp8_e4m3 hi(x);
+  __nv_fp8_e4m3 lo(x - static_cast<float>(hi));
+  h = hi.__x;
+  l = lo.__x;
+}
+
+template <int BN, int STAGES, int MINB>
+__global__ void __launch_bounds__(128, MINB)
+    k_step_tc_f8(const __grid_constant__ CUtensorMap tmJh, const __grid_constant__ CUtensorMap tmJl,
+                 const __grid_constant__ CUtensorMap tmXh, const __grid_constant__ CUtensorMap tmXl,
+                 StepArgs a, int32_t n_slices) {
+  using L = TcSmem<BN, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES),
+                 accb = smem_u32(bars + 2 * STAGES);
+
+  const RowTile rt = a.rt[blockIdx.x];
+  const int32_t sb = a.steps_b[rt.block];
+  if ((a.active != nullptr && !a.active[rt.block]) || a.t >= sb) return;  // CTA-uniform
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = rt.n_hi * n_slices;
+  const int row = warp * 32 + lane;
+  const bool vrow = row < rt.valid;
+  const size_t base = (size_t)blockIdx.y * BN * a.n_pad + rt.row0 + row;
+  constexpr int CH = 16;
+  float xs[CH], ys[CH];
+  if (vrow && a.z_out == nullptr) {
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      xs[j] = a.x[base + (size_t)j * a.n_pad];
+      ys[j] = a.y[base + (size_t)j * a.n_pad];
+    }
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(accb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tmem_slot), (uint32_t)BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0 && nk > 0) {
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, a.err)) break;
+      uint8_t* sa = smem + s * L::STAGE;
+      mbar_expect_tx(full0 + 8 * s, L::STAGE);
+      const int e = kb / n_slices, sl = kb % n_slices;  // slice: 0 (Jh,Xh) 1 (Jh,Xl) 2 (Jl,Xh)
+      const CUtensorMap* mj = sl == 2 ? &tmJl : &tmJh;
+      const CUtensorMap* mx = sl == 1 ? &tmXl : &tmXh;
+      tma_load_2d(smem_u32(sa), mj, full0 + 8 * s, 0, (rt.f32_begin + e) * TILE);
+      tma_load_2d(smem_u32(sa + A_BYTES), mx, full0 + 8 * s,
+                  a.tile_col[rt.tile_begin + e] * TILE, (int32_t)blockIdx.y * BN);
+    }
+  } else if (warp == 1 && lane == 0 && nk > 0) {
+    constexpr uint32_t idesc = idesc_e4m3<BN>();
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(full0 + 8 * s, ph, a.err)) break;
+      tc_fence_after();
+      uint8_t* sa = smem + s * L::STAGE;
+      const uint64_t ad = sdesc_sw128(smem_u32(sa));
+      const uint64_t bd = sdesc_sw128(smem_u32(sa + A_BYTES));
+#pragma unroll
+      for (int k = 0; k < 4; ++k)  // K = 32 e4m3 = 32 bytes per MMA
+        mma_f8(tmem, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc,
+               (kb > 0 || k > 0) ? 1u : 0u);
+      mma_commit(empty0 + 8 * s);
+    }
+    mma_commit(accb);
+  }
+  __syncwarp();
+
+  const bool ok = nk > 0 ? mbar_wait(accb, 0, a.err) : true;
+  tc_fence_after();
+  const double at = a.a0 * (double)a.t / (double)sb;
+  const float coef_x = (float)(-(a.a0 - at));
+  const float c0 = a.c0[rt.block];
+  const float inv_s = a.inv_scale;
+#pragma unroll
+  for (int c = 0; c < BN / CH; ++c) {
+    uint32_t v[CH];
+    __syncwarp();
+    if (nk > 0) {
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * CH), v);
+    } else {
+#pragma unroll
+      for (int j = 0; j < CH; ++j) v[j] = 0u;
+    }
+    const size_t b0 = base + (size_t)(c * CH) * a.n_pad;
+    if (a.z_out != nullptr) {
+      if (vrow && ok)
+#pragma unroll
+        for (int j = 0; j < CH; ++j)
+          a.z_out[b0 + (size_t)j * a.n_pad] = __uint_as_float(v[j]) * inv_s;
+      continue;
+    }
+    const bool more = c + 1 < BN / CH;
+    float xn[CH], yn[CH];
+    if (vrow && more) {
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        xn[j] = a.x[b0 + (size_t)(CH + j) * a.n_pad];
+        yn[j] = a.y[b0 + (size_t)(CH + j) * a.n_pad];
+      }
+    }
+    if (vrow && ok) {
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        float x = xs[j], y = ys[j];
+        y = y + a.dt * (coef_x * x + c0 * (__uint_as_float(v[j]) * inv_s));
+        x = x + a.dta0 * y;
+        if (fabsf(x) > 1.f) {
+          x = x > 0.f ? 1.f : -1.f;
+          y = 0.f;
+        }
+        const size_t idx = b0 + (size_t)j * a.n_pad;
+        a.x[idx] = x;
+        a.y[idx] = y;
+        uint8_t h8, l8;
+        split_e4m3(x, h8, l8);
+        a.x8h_out[idx] = h8;
+        a.x8l_out[idx] = l8;
+      }
+    }
+    if (more) {
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        xs[j] = xn[j];
+        ys[j] = yn[j];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, (uint32_t)BN);
+  }
+}
+
+// J' = s J (FP32 tiles) -> e4m3 hi / lo tiles; flag = 1 if any remainder is nonzero.
+__global__ void k_tiles_to_e4m3(const float* __restrict__ tf, int64_t n, float s, uint8_t* th,
+                                uint8_t* tl, int32_t* has_lo) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint8_t h, l;
+  split_e4m3(tf[i] * s, h, l);
+  th[i] = h;
+  tl[i] = l;
+  if (l != 0 && (l & 0x7f) != 0) atomicOr(has_lo, 1);
+}
+
+__global__ void k_x_to_e4m3(const float* __restrict__ x, int64_t n, uint8_t* h, uint8_t* l) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) split_e4m3(x[i], h[i], l[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -856,15 +1052,17 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 // box_inner x box_rows elements (BF16 operands: 64-wide boxes with the 128-byte
 // swizzle that sdesc_sw128 describes; FP32 state tiles: 128-wide, unswizzled).
 bool make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer,
-              uint32_t box_rows, bool fp32 = false) {
+              uint32_t box_rows, bool fp32 = false, bool bytes = false) {
   auto enc = get_encode();
   if (!enc) return false;
-  const uint32_t esz = fp32 ? 4 : 2;
+  const uint32_t esz = fp32 ? 4 : (bytes ? 1 : 2);
   cuuint64_t dims[2] = {inner, outer};
   cuuint64_t strides[1] = {inner * esz};
-  cuuint32_t box[2] = {fp32 ? 128u : 64u, box_rows};
+  cuuint32_t box[2] = {fp32 ? 128u : (bytes ? 128u : 64u), box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+  CUresult r = enc(map,
+                   fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                        : (bytes ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16),
                    2, const_cast<void*>(base), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE,
                    fp32 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
@@ -890,6 +1088,30 @@ cudaError_t set_attr_v() {
   return cudaFuncSetAttribute(k_step_tc_v<BN, STAGES, MINB>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)TcSmem<BN, STAGES>::BYTES);
+}
+
+template <int BN, int STAGES, int MINB>
+cudaError_t set_attr_f8() {
+  return cudaFuncSetAttribute(k_step_tc_f8<BN, STAGES, MINB>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)TcSmem<BN, STAGES>::BYTES);
+}
+
+template <int BN, int STAGES, int MINB>
+qh_status launch_f8_impl(Ctx* ctx, const Graph& g, const StepArgs& a, const Fp8Operands& op) {
+  CUtensorMap mJh, mJl, mXh, mXl;
+  const uint64_t jrows = (uint64_t)std::max<int64_t>(g.n_tiles_hi, 1) * TILE;
+  if (!make_map(&mJh, op.jh, TILE, jrows, TILE, false, true) ||
+      !make_map(&mJl, op.jl, TILE, jrows, TILE, false, true) ||
+      !make_map(&mXh, op.xh_in, (uint64_t)g.n_pad, (uint64_t)a.R, BN, false, true) ||
+      !make_map(&mXl, op.xl_in, (uint64_t)g.n_pad, (uint64_t)a.R, BN, false, true))
+    return set_err(ctx, QH_ECUDA, "cuTensorMapEncodeTiled failed (e4m3)");
+  dim3 grid(g.n_row_tiles, a.R / BN);
+  k_step_tc_f8<BN, STAGES, MINB><<<::qh::counted(grid), 128, TcSmem<BN, STAGES>::BYTES,
+                                   ctx->stream>>>(mJh, mJl, mXh, mXl, a, op.n_slices);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_step_tc_f8 launch");
+  return QH_OK;
 }
 
 qh_status launch_persistent2(Ctx* ctx, const Graph& g, const StepArgs& a,
@@ -969,12 +1191,32 @@ qh_status tc_prepare(Ctx* ctx) {
   if (e == cudaSuccess) e = set_attr_v<128, 2, 3>();
   if (e == cudaSuccess) e = set_attr_v<64, 2, 4>();
   if (e == cudaSuccess) e = set_attr_v<256, 2, 2>();
+  if (e == cudaSuccess) e = set_attr_f8<128, 2, 3>();
+  if (e == cudaSuccess) e = set_attr_f8<64, 2, 4>();
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_step_tc_p2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)P2Smem::BYTES);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute(k_step_tc)");
   if (!get_encode()) return set_err(ctx, QH_ECUDA, "cuTensorMapEncodeTiled entry point not found");
   return QH_OK;
+}
+
+qh_status launch_step_f8(Ctx* ctx, const Graph& g, const StepArgs& a, const Fp8Operands& op) {
+  if (g.n_row_tiles == 0) return QH_OK;
+  if (a.R % 128 == 0) return launch_f8_impl<128, 2, 3>(ctx, g, a, op);
+  return launch_f8_impl<64, 2, 4>(ctx, g, a, op);
+}
+
+void launch_tiles_to_e4m3(cudaStream_t s, const float* tf, int64_t n, float scale, uint8_t* th,
+                          uint8_t* tl, int32_t* has_lo) {
+  if (n > 0)
+    k_tiles_to_e4m3<<<::qh::counted((unsigned)((n + 255) / 256)), 256, 0, s>>>(tf, n, scale, th,
+                                                                              tl, has_lo);
+}
+
+void launch_x_to_e4m3(cudaStream_t s, const float* x, int64_t n, uint8_t* h, uint8_t* l) {
+  if (n > 0)
+    k_x_to_e4m3<<<::qh::counted((unsigned)((n + 255) / 256)), 256, 0, s>>>(x, n, h, l);
 }
 
 bool tc_plan_ok(int R, const TcPlan& plan) {

@@ -166,6 +166,9 @@ struct StepArgs {
   int32_t n_pad, R;
   int32_t t;              // step index
   int32_t use_lo;         // BF16 paths: also accumulate the lo (remainder) tiles
+  uint8_t* x8h_out;       // FP8 path: e4m3 hi / lo parts of X_{t+1}
+  uint8_t* x8l_out;
+  float inv_scale;        // FP8 path: 1 / s of the scaled J tiles
   float dt, dta0;         // dta0 = dt * a0
   double a0;
   int32_t* err;
@@ -174,6 +177,16 @@ struct StepArgs {
 // Tensor-core precisions use the BF16 hi tiles; the lo (remainder) tiles join when
 // asked for (QH_PREC_BF16X2) or when integer weights above 256 need them to stay exact.
 inline bool is_tc_precision(int p) { return p == QH_PREC_BF16 || p == QH_PREC_BF16X2; }
+// Power-of-two scale of J for e4m3 tiles: 1 for integer weights below 256 (exact as
+// hi + lo), else the largest 2^k with max|J| * 2^k <= 240.
+inline float fp8_scale(const Graph& g) {
+  if (g.integer_weights && g.max_abs_w < 256.0) return 1.f;
+  if (!(g.max_abs_w > 0.0)) return 1.f;
+  float s = 1.f;
+  while (g.max_abs_w * s * 2.0 <= 240.0) s *= 2.f;
+  while (g.max_abs_w * s > 240.0) s *= 0.5f;
+  return s;
+}
 inline int32_t use_lo_for(const Graph& g, int precision) {
   return g.has_lo && (precision == QH_PREC_BF16X2 || g.integer_weights) ? 1 : 0;
 }
@@ -225,6 +238,17 @@ struct TcPlan {
 qh_status launch_step_tc(Ctx* ctx, const Graph& g, const StepArgs& a,
                          const __nv_bfloat16* xh_in, const TcPlan& plan);
 bool tc_plan_ok(int R, const TcPlan& plan);
+struct Fp8Operands {
+  const uint8_t* jh;      // e4m3 hi / lo tiles of s*J, indexed like the FP32 tiles
+  const uint8_t* jl;
+  const uint8_t* xh_in;   // e4m3 hi / lo parts of X_t, [R][n_pad]
+  const uint8_t* xl_in;
+  int32_t n_slices;       // 2, or 3 when s*J has a nonzero remainder
+};
+qh_status launch_step_f8(Ctx* ctx, const Graph& g, const StepArgs& a, const Fp8Operands& op);
+void launch_tiles_to_e4m3(cudaStream_t s, const float* tf, int64_t n, float scale, uint8_t* th,
+                          uint8_t* tl, int32_t* has_lo);
+void launch_x_to_e4m3(cudaStream_t s, const float* x, int64_t n, uint8_t* h, uint8_t* l);
 int tc_n_variants();
 const char* tc_variant_name(int v);
 bool tc_variant_ok(int v, const Graph& g, int R);

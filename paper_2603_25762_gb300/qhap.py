@@ -27,7 +27,7 @@ LIB_PATH = os.environ.get("QHAP_LIB") or os.path.join(HERE, "libqhap.so")
 QH_OK, QH_EINVAL, QH_ENOMEM, QH_ECUDA, QH_ETIMEOUT, QH_EUNSUPPORTED = range(6)
 MODE_READ, MODE_SNP = 0, 1
 WEIGHT_CONFLICT, WEIGHT_SIGNED = 0, 1
-PREC_FP32, PREC_BF16, PREC_BF16X2 = 0, 1, 2
+PREC_FP32, PREC_BF16, PREC_BF16X2, PREC_FP8 = 0, 1, 2, 3
 SCHED_LINEAR, SCHED_AUTO = 0, 1
 STORAGE_AUTO, STORAGE_TILES, STORAGE_CSR = 0, 1, 2
 
