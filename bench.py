@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 SPIN_BYTES = 16 + 2  # FP32 x, y read + write, BF16 X_hat write, per spin update
+# multi-step kernels hold y on chip for a whole launch: x read + write, X_hat write per
+# spin update, and y read + written once per launch
+SPIN_BYTES_MULTISTEP = 8 + 2
 
 
 def _peaks():
@@ -331,9 +334,17 @@ def run_ours(args):
         return
     hbm, bf16_tf, src = _peaks()
     launch_us = statistics.mean(step_ms) * 1e3
-    # state traffic per spin update + each stored J nonzero read once (BF16: 2 B, FP32: 4 B)
+    # state traffic per spin update + each stored J nonzero read once per step (BF16: 2 B,
+    # FP32: 4 B)
     n_launch = max(1, stats["timing"]["n_step_launches"])
-    per_launch_bytes = units / n_launch * SPIN_BYTES + stats["nnz"] * (4 if prec == qhap.PREC_FP32 else 2)
+    jb = stats["nnz"] * (4 if prec == qhap.PREC_FP32 else 2)
+    upd = units / n_launch  # spin updates per launch
+    if stats["timing"]["kernel"].startswith("multistep"):
+        steps_per_launch = T
+        per_launch_bytes = upd * SPIN_BYTES_MULTISTEP + 8 * upd / T + jb * steps_per_launch
+    else:
+        steps_per_launch = 1
+        per_launch_bytes = upd * SPIN_BYTES + jb
     achieved = per_launch_bytes / (launch_us * 1e-6) / 1e9
     traffic = _profiled_traffic(stats["timing"]["kernel"]) if args.workload == "hifi-region" else None
     h2d = sum(int(a.nbytes) for a in pinned_np[1:])
@@ -351,6 +362,8 @@ def run_ours(args):
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
                      "peak_source": src, "avg_launch_us": launch_us,
+                     "steps_per_launch": steps_per_launch,
+                     "avg_step_us": launch_us / steps_per_launch,
                      "algorithmic_bytes_per_launch": per_launch_bytes},
         "gpu_launches": n_launched,
         "gpu_launches_trace_per_step": n_kern,

@@ -183,12 +183,15 @@ typedef struct {
   int32_t patience;     /* stop a block after this many checks without a better
                            best-replica energy (0 = never stop early) */
   int32_t refine_max;   /* SNP mode: maximum refinement iterations (>= 1) */
-  int32_t step_kernel;  /* BF16: -1 = autotune, else a variant index 0..5 (see
-                           qh_solution_kernel for names); invalid choices -> QH_EINVAL */
+  int32_t step_kernel;  /* BF16: -1 = autotune, else a variant index 0..7 (see
+                           qh_solution_kernel for names; 6 and 7 are the multi-step
+                           kernels that keep y on chip and launch once per step
+                           range); invalid choices -> QH_EINVAL */
 } qh_bsb_opts;
 
 /* Run multi-replica bSB on every block of the graph in one batched launch per
- * step (the step loop is replayed from a CUDA graph).  Each replica's final
+ * step (the step loop is replayed from a CUDA graph), or, with the multi-step
+ * kernels, in one launch per range of steps (per early-stop check period).  Each replica's final
  * spins are cut-evaluated exactly (FP64 reduction; exact for integer weights);
  * the best replica per block wins, ties to the lowest replica index.
  * SNP mode additionally runs the iterative refinement (flip counter C on the
@@ -276,6 +279,15 @@ qh_status qh_debug_matvec(qh_ctx* ctx, const qh_graph* g, int32_t precision, int
 qh_status qh_debug_steps(qh_ctx* ctx, const qh_graph* g, int32_t precision, int32_t R,
                          float* x, float* y, int32_t t0, int32_t nsteps, int32_t steps, double dt,
                          double a0, const double* c0_per_block);
+
+/* qh_debug_steps with an explicit step kernel (BF16 / BF16X2 tile storage only):
+ * step_kernel = -1 is the default; otherwise an index into the solver's kernel
+ * variants (qh_bsb_opts.step_kernel).  The multi-step variants run all `nsteps`
+ * steps in ONE launch, the momentum y held on chip between steps.  QH_EINVAL when
+ * the variant does not fit the graph, precision or R. */
+qh_status qh_debug_steps_v(qh_ctx* ctx, const qh_graph* g, int32_t precision, int32_t R,
+                           float* x, float* y, int32_t t0, int32_t nsteps, int32_t steps,
+                           double dt, double a0, const double* c0_per_block, int32_t step_kernel);
 
 /* Padded layout: n_pad and padded_index int32[n_nodes] (-1 for vertices in no
  * block): vertex v of block b sits at padded column pad_off[b] + local[v]. */

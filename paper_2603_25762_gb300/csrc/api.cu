@@ -150,20 +150,41 @@ bool tuned_variant(Ctx* ctx, const Graph& g, int R, TcPlan* plan) {
   return false;
 }
 
-qh_status autotune(Ctx* ctx, const Graph& g, StepArgs a, const SolveBufs& B, int R, TcPlan* plan) {
+// The multi-step kernel keeps y / (dt c0) on chip: every block's dt * c0 must be a
+// normal float with a finite reciprocal.
+bool run_c0_ok(const float* c0, int32_t nb, float dt) {
+  for (int32_t b = 0; b < nb; ++b) {
+    const float d = dt * c0[b];
+    if (!std::isnormal(d) || !std::isfinite(1.0f / d)) return false;
+  }
+  return true;
+}
+
+qh_status autotune(Ctx* ctx, const Graph& g, StepArgs a, const SolveBufs& B, int R, TcPlan* plan,
+                   bool allow_run) {
   const std::string kb = tune_key(g, R, 0);
   cudaStream_t s = ctx->stream;
   float best = 1e30f;
   int best_v = -1;
   std::string rep;
   for (int v = 0; v < tc_n_variants(); ++v) {
-    if (!tc_variant_ok(v, g, R)) continue;
+    if (!tc_variant_ok(v, g, R, ctx->n_sm, a.use_lo != 0)) continue;
+    if (run_variant(v) && !allow_run) continue;
     TcPlan p = *plan;
     p.variant = v;
+    RunBufs rb;
+    if (run_variant(v)) {
+      qh_status st = run_prepare(ctx, g, R, v == RUN_VARIANT_JRES, a.use_lo != 0, &rb);
+      if (st != QH_OK) return st;
+    }
     float ms = 0.f;
     for (int rep_i = 0; rep_i < 2; ++rep_i) {  // warm-up pass, then the timed pass
       QH_CUDA_TRY(cudaEventRecord(ctx->ev[2], s));
-      for (int k = 0; k < 6; ++k) {
+      if (run_variant(v)) {  // the six steps in one launch
+        qh_status st = launch_run(ctx, g, a, rb, B.xh0, B.xh1, 0, 6);
+        if (st != QH_OK) return st;
+      }
+      for (int k = 0; k < 6 && !run_variant(v); ++k) {
         a.t = k;
         a.xh_out = (k % 2 == 0) ? B.xh1 : B.xh0;
         qh_status st = launch_step_tc(ctx, g, a, (k % 2 == 0) ? B.xh0 : B.xh1, p);
@@ -380,7 +401,8 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   if (o->check_every < 0 || o->patience < 0 || o->replica_base < 0) return set_err(ctx, QH_EINVAL, "negative option");
   if ((int64_t)o->replica_base + R > (1 << 16)) return set_err(ctx, QH_EINVAL, "replica indices must stay below 65536");
   if (is_tc_precision(o->precision) && o->step_kernel >= 0 && !G.csr_mode &&
-      (o->step_kernel >= tc_n_variants() || !tc_variant_ok(o->step_kernel, G, R)))
+      (o->step_kernel >= tc_n_variants() ||
+       !tc_variant_ok(o->step_kernel, G, R, ctx->n_sm, use_lo_for(G, o->precision))))
     return set_err(ctx, QH_EINVAL, "step_kernel variant not valid for this graph and replica count");
   const bool snp = G.mode == QH_MODE_SNP;
   const int32_t refine_max = snp ? o->refine_max : 1;
@@ -591,7 +613,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
         QH_CUDA_TRY(cudaMemcpyAsync(B.running, B.active, nb * 4, cudaMemcpyDeviceToDevice, s));
         launch_init_state(s, W, R, o->replica_base, o->seed, 0, B.x, B.y, B.xh0, B.active);
         QH_STAGE_CHECK("solve: state init (tuning)");
-        st = autotune(ctx, W, a, B, R, &tplan);
+        st = autotune(ctx, W, a, B, R, &tplan, run_c0_ok(h_c0.data(), nb, a.dt));
       }
     }
     if (st != QH_OK) {
@@ -603,7 +625,21 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
               : fp8 ? (R % 128 == 0 ? "e4m3-bn128-s2-x3" : "e4m3-bn64-s2-x4")
               : is_tc_precision(o->precision) ? tc_variant_name(tplan.variant) : "k_step_f32";
   skey += "|v" + std::to_string(tplan.variant);
-  if (ctx->loop_key != skey || !ctx->loop_exec) {
+  // the multi-step kernel runs whole step ranges: a few direct launches, no capture
+  const bool multistep = is_tc_precision(o->precision) && !G.csr_mode && run_variant(tplan.variant);
+  RunBufs rb;
+  if (multistep && !run_c0_ok(h_c0.data(), nb, a.dt)) {
+    delete sh;
+    return set_err(ctx, QH_EINVAL, "multi-step kernel needs dt * c0 to be a normal float in every block");
+  }
+  if (multistep) {
+    qh_status st = run_prepare(ctx, W, R, tplan.variant == RUN_VARIANT_JRES, a.use_lo != 0, &rb);
+    if (st != QH_OK) {
+      delete sh;
+      return st;
+    }
+  }
+  if (!multistep && (ctx->loop_key != skey || !ctx->loop_exec)) {
     if (ctx->loop_exec) {
       cudaGraphExecDestroy(ctx->loop_exec);
       ctx->loop_exec = nullptr;
@@ -671,8 +707,27 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
                        reinterpret_cast<uint8_t*>(B.xh0) + NS);
     QH_STAGE_CHECK("solve: state init");
     QH_CUDA_TRY(cudaEventRecord(ctx->ev[2], s));
-    QH_CUDA_TRY(cudaGraphLaunch(ctx->loop_exec, s));
-    note_launch(ctx->loop_kernels);
+    if (multistep) {
+      const int32_t chunk = early ? o->check_every : max_steps;
+      for (int32_t t0 = 0; t0 < max_steps; t0 += chunk) {
+        const int32_t t1 = std::min(max_steps, t0 + chunk);
+        qh_status st = launch_run(ctx, W, a, rb, B.xh0, B.xh1, t0, t1);
+        if (st != QH_OK) {
+          delete sh;
+          return st;
+        }
+        if (early && t1 < max_steps) {
+          launch_signs(s, W, R, B.x, B.signs);
+          launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.running);
+          launch_pick_best(s, nb, R, B.cuts, B.best_r, B.best_cut, B.running);
+          launch_early_stop(s, nb, B.best_cut, B.seen, B.stall, B.running, B.steps_run,
+                            o->patience, t1);
+        }
+      }
+    } else {
+      QH_CUDA_TRY(cudaGraphLaunch(ctx->loop_exec, s));
+      note_launch(ctx->loop_kernels);
+    }
     QH_CUDA_TRY(cudaEventRecord(ctx->ev[3], s));
     launch_signs(s, W, R, x_final, B.signs);
     launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.active);
@@ -697,7 +752,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
     step_ms_total += ms;
-    launches += max_steps;
+    launches += multistep ? (early ? (max_steps + o->check_every - 1) / o->check_every : 1) : max_steps;
     for (int32_t b = 0; b < nb; ++b)
       if (h_active[b]) {
         spin_updates += (double)G.h_block_size[b] * R * h_steps_run[b];
@@ -927,7 +982,8 @@ static qh_status debug_fp8_tiles(Ctx* ctx, const Graph& g, Fp8Operands* f8, floa
 }
 
 static qh_status debug_common(Ctx* ctx, const Graph& g, int precision, int32_t R, StepArgs& a,
-                              const double* c0_per_block, int32_t steps) {
+                              const double* c0_per_block, int32_t steps,
+                              std::vector<float>* c0_out = nullptr) {
   if (precision != QH_PREC_FP32 && !is_tc_precision(precision) && precision != QH_PREC_FP8)
     return set_err(ctx, QH_EINVAL, "bad precision");
   if (precision == QH_PREC_FP8 && (g.csr_mode || R % 64 != 0))
@@ -956,6 +1012,7 @@ static qh_status debug_common(Ctx* ctx, const Graph& g, int precision, int32_t R
   a.R = R;
   a.err = ctx->d_err;
   a.use_lo = use_lo_for(g, precision);
+  if (c0_out) *c0_out = c0;
   return QH_OK;
 }
 
@@ -1025,13 +1082,27 @@ qh_status qh_debug_matvec(qh_ctx* h, const qh_graph* gh, int32_t precision, int3
 qh_status qh_debug_steps(qh_ctx* h, const qh_graph* gh, int32_t precision, int32_t R, float* x,
                          float* y, int32_t t0, int32_t nsteps, int32_t steps, double dt, double a0,
                          const double* c0_per_block) {
+  return qh_debug_steps_v(h, gh, precision, R, x, y, t0, nsteps, steps, dt, a0, c0_per_block, -1);
+}
+
+qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int32_t R, float* x,
+                           float* y, int32_t t0, int32_t nsteps, int32_t steps, double dt,
+                           double a0, const double* c0_per_block, int32_t step_kernel) {
   if (!h || !gh || !x || !y || nsteps < 0 || steps < 1 || t0 < 0) return QH_EINVAL;
   Ctx* ctx = &h->c;
   const Graph& g = gh->g;
   cudaSetDevice(ctx->device);
   StepArgs a;
-  qh_status st = debug_common(ctx, g, precision, R, a, c0_per_block, steps);
+  std::vector<float> c0h;
+  qh_status st = debug_common(ctx, g, precision, R, a, c0_per_block, steps, &c0h);
   if (st) return st;
+  if (step_kernel >= 0) {
+    if (!is_tc_precision(precision) || g.csr_mode || step_kernel >= tc_n_variants() ||
+        !tc_variant_ok(step_kernel, g, R, ctx->n_sm, a.use_lo != 0))
+      return set_err(ctx, QH_EINVAL, "step_kernel variant not valid for this graph, precision and R");
+    if (run_variant(step_kernel) && !run_c0_ok(c0h.data(), g.n_blocks, (float)dt))
+      return set_err(ctx, QH_EINVAL, "multi-step kernel needs dt * c0 to be a normal float in every block");
+  }
   a.x = x;
   a.y = y;
   a.dt = (float)dt;
@@ -1093,6 +1164,23 @@ qh_status qh_debug_steps(qh_ctx* h, const qh_graph* gh, int32_t precision, int32
       QH_CUDA_TRY(cudaGetLastError());
       return check_err_word(ctx);
     }
+    if (step_kernel >= 0 && run_variant(step_kernel)) {  // one launch for all nsteps
+      RunBufs rb;
+      st = run_prepare(ctx, g, R, step_kernel == RUN_VARIANT_JRES, a.use_lo != 0, &rb);
+      if (st) return st;
+      if (t0 % 2 == 1) {  // X_hat_t lives in xh0 for even t, xh1 for odd t
+        QH_CUDA_TRY(cudaMemsetAsync(xh0, 0, NS * 2, s));
+        launch_f32_to_bf16(s, x, xh1, (int64_t)NS);
+      } else {
+        launch_f32_to_bf16(s, x, xh0, (int64_t)NS);
+      }
+      st = launch_run(ctx, g, a, rb, xh0, xh1, t0, t0 + nsteps);
+      if (st) return st;
+      QH_CUDA_TRY(cudaGetLastError());
+      return check_err_word(ctx);
+    }
+    TcPlan plan = pick_plan(R);
+    if (step_kernel >= 0) plan.variant = step_kernel;
     launch_f32_to_bf16(s, x, xh0, (int64_t)NS);
     for (int32_t k = 0; k < nsteps; ++k) {
       a.t = t0 + k;
@@ -1101,7 +1189,7 @@ qh_status qh_debug_steps(qh_ctx* h, const qh_graph* gh, int32_t precision, int32
         launch_step_csr(s, g, a, g.pval, (k % 2 == 0) ? xh0 : xh1);
         continue;
       }
-      st = launch_step_tc(ctx, g, a, (k % 2 == 0) ? xh0 : xh1, pick_plan(R));
+      st = launch_step_tc(ctx, g, a, (k % 2 == 0) ? xh0 : xh1, plan);
       if (st) return st;
     }
   }

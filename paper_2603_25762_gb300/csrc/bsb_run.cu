@@ -1,0 +1,590 @@
+// Multi-step bSB on the tensor cores: one persistent launch runs steps t0 .. t1-1
+// of the SB algorithm solution's update
+//   y <- y + dt * ( -(a0 - a(t)) x + c0 * J_hat X_hat ),  x <- x + dt * a0 * y,
+//   |x| > 1 => x <- sgn(x), y <- 0,                       X_hat_{t+1} <- bf16(x)
+// with the momentum y held on chip for the whole launch.
+//
+// Work item = (128-row tile of J, 128 replicas).  A CTA owns up to four items and
+// gives each its own 128 TMEM columns.  Those columns are the MMA accumulator and
+// hold y / (dt c0) between steps: every MMA accumulates J_hat X_hat onto it, so
+//   dt c0 * acc = y + dt c0 Z,   y_{t+1} = dt c0 * acc - dt (a0 - a(t)) x.
+// y therefore never leaves the SM between t0 and t1: it is read from HBM before the
+// first step and written back after the last one.  Per spin-update the state costs
+// 4 + 4 bytes (x) + 2 bytes (X_hat) of memory traffic instead of 16 + 2.
+//
+// X_hat_t of a block is read by every row tile of that block, so step t+1 of item
+// (row tile, replica tile k) may start only when all row tiles of its block have
+// written X_hat_{t+1} for replica tile k.  Per (block, k) a counter in global memory
+// counts finished items; a dedicated warp releases it (gpu scope) after the item's
+// epilogue, and the TMA producer acquires it before it loads X_hat of the next step.
+// All CTAs are co-resident (cooperative launch), so these waits always end; every
+// wait is nevertheless bounded and sets ERR_TIMEOUT in the error word when it
+// expires, after which all CTAs stop and drain their copies in flight.
+//
+// Roles (352 threads): warp 0 = TMA producer, warp 1 = MMA issuer (one thread
+// each), warps 2-9 = epilogue (TMEM lane quarter = warp % 4, two warps per quarter
+// split the 128 columns), warp 10 = signal.  With JRES the J tiles of the CTA's
+// single row tile stay in shared memory for the whole launch and only X_hat
+// streams; otherwise J and X_hat K-slices stream through the ring together.
+#include <algorithm>
+#include <vector>
+
+#include "qh_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace qh {
+
+namespace {
+
+constexpr int RB = 128;          // replicas per item (MMA N)
+constexpr int MAX_ITEMS = 4;     // 4 items x 128 TMEM columns = 512
+constexpr int EPI_WARPS = 8;
+constexpr int RUN_THREADS = 32 * (3 + EPI_WARPS);
+constexpr int SIGNAL_WARP = 2 + EPI_WARPS;
+constexpr uint32_t SLICE = TILE * 64 * 2;  // a 128 x 64 BF16 K-slice (16 KB)
+constexpr int JRES_TILES = 4;              // resident J tiles (hi + lo entries) per CTA
+
+struct ItemInfo {
+  int32_t row0, valid, tile_begin, nk;  // nk = K-slices (2 per J tile entry)
+  int32_t block, k, last_t, steps_b;    // last_t < t0: nothing to do this launch
+  uint32_t rows_b;                      // row tiles of the block
+  float dtc0, inv_dtc0;                 // dt * c0 and its reciprocal
+  int32_t pad_;
+};
+
+template <bool JRES>
+struct RunSmem {
+  static constexpr int ST = 6;                                  // operand ring slots
+  static constexpr uint32_t SLOT = JRES ? SLICE : 2 * SLICE;    // X_hat (+ J) per slot
+  static constexpr uint32_t RING_OFF = JRES ? JRES_TILES * 2 * SLICE : 0;
+  static constexpr uint32_t BAR_OFF = RING_OFF + ST * SLOT;
+  static constexpr int N_BARS = 2 * ST + 2 * MAX_ITEMS + 2;
+  static constexpr uint32_t INFO_OFF = BAR_OFF + 8 * N_BARS;
+  static constexpr uint32_t BYTES = INFO_OFF + sizeof(ItemInfo) * MAX_ITEMS + 16 + 1024;
+};
+
+struct RunArgs {
+  const RowTile* rt;
+  const int32_t* tile_col;
+  float* x;                 // [R][n_pad]
+  float* y;                 // [R][n_pad]
+  __nv_bfloat16* xh0;       // X_hat_t for even t
+  __nv_bfloat16* xh1;       // X_hat_t for odd t
+  const float* c0;          // [n_blocks]
+  const int32_t* active;    // [n_blocks] or nullptr
+  const int32_t* steps_b;   // [n_blocks]
+  const int32_t* rows_b;    // [n_blocks] row tiles per block
+  uint32_t* done;           // [n_blocks][n_kt], zero at launch
+  const int2* work;         // [grid] {first item, item count}
+  int32_t n_pad, n_kt, t0, t1, use_lo;
+  float dt, dta0;
+  double a0;
+  int32_t* err;
+};
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+      "r"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+// Issue a 32-lane x 16-column TMEM load without waiting for it.
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+// Wait for outstanding TMEM loads; the registers are threaded through so that no
+// use of them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                 "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
+                 "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+               :
+               : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_gpu_add(uint32_t* p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Orders generic-proxy global accesses against later async-proxy (TMA) ones.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+constexpr long long WAIT_LIMIT = 1ll << 31;  // SM cycles, about one second
+
+// Bounded mbarrier wait that also gives up when another role has aborted.
+__device__ __forceinline__ bool rwait(uint32_t bar, uint32_t parity, int32_t* err,
+                                      volatile int32_t* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > WAIT_LIMIT) {
+      atomicOr(err, ERR_TIMEOUT);
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+// Bounded wait until a release counter reaches `target`; gives up on an abort of
+// this CTA or a timeout reported by any other CTA.
+__device__ __forceinline__ bool wait_count(const uint32_t* p, uint32_t target, int32_t* err,
+                                           volatile int32_t* abort) {
+  if (ld_acquire_gpu(p) >= target) return true;
+  const long long t0 = clock64();
+  while (ld_acquire_gpu(p) < target) {
+    if (*abort) return false;
+    if (*reinterpret_cast<volatile int32_t*>(err) & ERR_TIMEOUT) {
+      *abort = 1;
+      return false;
+    }
+    if (clock64() - t0 > WAIT_LIMIT) {
+      atomicOr(err, ERR_TIMEOUT);
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+// Position in the CTA's sequence of (step, item) pairs that have work.
+struct Cursor {
+  int u, i;
+};
+__device__ __forceinline__ Cursor next_live(Cursor c, const ItemInfo* info, int n_items,
+                                            int t0, int n_steps) {
+  while (true) {
+    if (++c.i == n_items) {
+      c.i = 0;
+      if (++c.u >= n_steps) return Cursor{n_steps, 0};
+    }
+    if (t0 + c.u <= info[c.i].last_t) return c;
+  }
+}
+
+template <bool JRES>
+__global__ void __launch_bounds__(RUN_THREADS, 1)
+    k_bsb_run(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmX0,
+              const __grid_constant__ CUtensorMap tmX1, RunArgs a) {
+  using L = RunSmem<JRES>;
+  constexpr int ST = L::ST;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+  ItemInfo* info = reinterpret_cast<ItemInfo*>(smem + L::INFO_OFF);
+  __shared__ uint32_t tmem_slot;
+  __shared__ int32_t abort_s;
+  volatile int32_t* abort_flag = &abort_s;
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * ST, accf0 = empty0 + 8 * ST,
+                 edone0 = accf0 + 8 * MAX_ITEMS, jbar = edone0 + 8 * MAX_ITEMS, drain = jbar + 8;
+
+  const int2 wk = a.work[blockIdx.x];
+  const int n_items = wk.y;
+  const int n_steps = a.t1 - a.t0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (warp == 2 && lane < n_items) {
+    const int item = wk.x + lane;
+    const RowTile rt = a.rt[item / a.n_kt];
+    ItemInfo it;
+    it.row0 = rt.row0;
+    it.valid = rt.valid;
+    it.tile_begin = rt.tile_begin;
+    it.nk = 2 * (a.use_lo ? rt.n_all : rt.n_hi);
+    it.block = rt.block;
+    it.k = item % a.n_kt;
+    it.steps_b = a.steps_b[rt.block];
+    const bool on = a.active == nullptr || a.active[rt.block] != 0;
+    it.last_t = on ? min(a.t1, it.steps_b) - 1 : a.t0 - 1;
+    it.rows_b = (uint32_t)a.rows_b[rt.block];
+    it.dtc0 = a.dt * a.c0[rt.block];
+    it.inv_dtc0 = 1.0f / it.dtc0;
+    it.pad_ = 0;
+    info[lane] = it;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int i = 0; i < MAX_ITEMS; ++i) {
+      mbar_init(accf0 + 8 * i, 1);
+      mbar_init(edone0 + 8 * i, EPI_WARPS);
+    }
+    mbar_init(jbar, 1);
+    mbar_init(drain, 1);
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(&tmem_slot), 512u);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0 && n_items > 0) {
+      uint32_t q = 0;
+      bool jissued = false;
+      if (JRES) {  // all items of the CTA share one row tile
+        const ItemInfo& it = info[0];
+        mbar_expect_tx(jbar, (uint32_t)it.nk * SLICE);
+        for (int kb = 0; kb < it.nk; ++kb)
+          tma_load_2d(smem_u32(smem + kb * SLICE), &tmJ, jbar, (kb & 1) * 64,
+                      (it.tile_begin + (kb >> 1)) * TILE);
+        jissued = true;
+      }
+      bool ok = true;
+      for (int u = 0; ok && u < n_steps; ++u) {
+        const int t = a.t0 + u;
+        const CUtensorMap* mx = (t & 1) ? &tmX1 : &tmX0;
+        for (int i = 0; ok && i < n_items; ++i) {
+          const ItemInfo& it = info[i];
+          if (t > it.last_t) continue;
+          if (u > 0) {  // X_hat_t of the whole block, replica tile k, is written
+            ok = wait_count(a.done + (size_t)it.block * a.n_kt + it.k, (uint32_t)u * it.rows_b,
+                            a.err, abort_flag);
+            if (!ok) break;
+            fence_proxy_async_global();
+          }
+          for (int kb = 0; kb < it.nk; ++kb) {
+            const int s = (int)(q % ST);
+            const uint32_t ph = (q / ST) & 1u;
+            if (!(ok = rwait(empty0 + 8 * s, ph ^ 1u, a.err, abort_flag))) break;
+            uint8_t* slot = smem + L::RING_OFF + s * L::SLOT;
+            mbar_expect_tx(full0 + 8 * s, L::SLOT);
+            const int e = kb >> 1, half = kb & 1;
+            const uint32_t xdst = JRES ? smem_u32(slot) : smem_u32(slot + SLICE);
+            tma_load_2d(xdst, mx, full0 + 8 * s, a.tile_col[it.tile_begin + e] * TILE + half * 64,
+                        it.k * RB);
+            if (!JRES)
+              tma_load_2d(smem_u32(slot), &tmJ, full0 + 8 * s, half * 64,
+                          (it.tile_begin + e) * TILE);
+            ++q;
+          }
+        }
+      }
+      // copies still in flight must land before the CTA exits: the last load of
+      // every ring slot, and the resident J tiles
+      for (uint32_t j = q > (uint32_t)ST ? q - ST : 0u; j < q; ++j)
+        mbar_wait(full0 + 8 * (j % ST), (j / ST) & 1u, a.err);
+      if (jissued) mbar_wait(jbar, 0, a.err);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0 && n_items > 0) {
+      constexpr uint32_t idesc = idesc_bf16<RB>();
+      bool ok = true;
+      if (JRES) ok = rwait(jbar, 0, a.err, abort_flag);
+      uint32_t q = 0;
+      for (int u = 0; ok && u < n_steps; ++u) {
+        const int t = a.t0 + u;
+        for (int i = 0; ok && i < n_items; ++i) {
+          const ItemInfo& it = info[i];
+          if (t > it.last_t) continue;
+          // the epilogue has stored y / (dt c0) of the previous step into the columns
+          if (!(ok = rwait(edone0 + 8 * i, (uint32_t)u & 1u, a.err, abort_flag))) break;
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(i * RB);
+          for (int kb = 0; kb < it.nk; ++kb) {
+            const int s = (int)(q % ST);
+            const uint32_t ph = (q / ST) & 1u;
+            if (!(ok = rwait(full0 + 8 * s, ph, a.err, abort_flag))) break;
+            tc_fence_after();
+            uint8_t* slot = smem + L::RING_OFF + s * L::SLOT;
+            const uint64_t ad = sdesc_sw128(JRES ? smem_u32(smem + kb * SLICE) : smem_u32(slot));
+            const uint64_t bd = sdesc_sw128(JRES ? smem_u32(slot) : smem_u32(slot + SLICE));
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, 1u);
+            mma_commit(empty0 + 8 * s);
+            ++q;
+          }
+          if (ok) mma_commit(accf0 + 8 * i);
+        }
+      }
+      mma_commit(drain);  // every MMA of this thread has completed once this fires
+      mbar_wait(drain, 0, a.err);
+    }
+  } else if (warp < SIGNAL_WARP) {
+    // ------------------------------------------------------------ epilogue
+    const int qd = warp & 3, hh = (warp - 2) >> 2;
+    const int r = qd * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(hh * 64);
+    // y -> y / (dt c0) into the item's TMEM columns
+    for (int i = 0; i < n_items; ++i) {
+      const ItemInfo& it = info[i];
+      if (a.t0 > it.last_t) continue;
+      const bool vr = r < it.valid;
+      const size_t base = (size_t)(it.k * RB + hh * 64) * a.n_pad + it.row0 + r;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        uint32_t v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          v[j] = vr ? __float_as_uint(a.y[base + (size_t)(c * 16 + j) * a.n_pad] * it.inv_dtc0)
+                    : 0u;
+        __syncwarp();
+        tmem_st16(lane_base + (uint32_t)(i * RB + c * 16), v);
+      }
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(edone0 + 8 * i);
+    }
+    // x is prefetched three 16-column chunks ahead along the (step, item) sequence;
+    // chunk c of any item always lands in xb[c]
+    float xb[4][16];
+    Cursor cur{0, -1};
+    cur = next_live(cur, info, n_items, a.t0, n_steps);
+    auto load_x = [&](float (&dst)[16], Cursor c, int chunk) {
+      if (c.u >= n_steps) return;
+      const ItemInfo& it = info[c.i];
+      if (r >= it.valid) return;
+      const size_t b0 = (size_t)(it.k * RB + hh * 64 + chunk * 16) * a.n_pad + it.row0 + r;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) dst[j] = a.x[b0 + (size_t)j * a.n_pad];
+    };
+    load_x(xb[0], cur, 0);
+    load_x(xb[1], cur, 1);
+    load_x(xb[2], cur, 2);
+    while (cur.u < n_steps) {
+      const ItemInfo& it = info[cur.i];
+      const int t = a.t0 + cur.u;
+      const Cursor nxt = next_live(cur, info, n_items, a.t0, n_steps);
+      const bool vr = r < it.valid, last = t == it.last_t;
+      const size_t base = (size_t)(it.k * RB + hh * 64) * a.n_pad + it.row0 + r;
+      __nv_bfloat16* xh_out = (t & 1) ? a.xh0 : a.xh1;  // X_hat_{t+1}
+      const double at = a.a0 * (double)t / (double)it.steps_b;
+      const float dtcx = a.dt * (float)(-(a.a0 - at));
+      const bool ok = __all_sync(0xffffffffu, rwait(accf0 + 8 * cur.i, (uint32_t)cur.u & 1u,
+                                                    a.err, abort_flag));
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t col0 = lane_base + (uint32_t)(cur.i * RB);
+      uint32_t va[16], vb[16];
+      __syncwarp();
+      tmem_ld16_async(col0, va);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        uint32_t(&v)[16] = (c & 1) ? vb : va;
+        uint32_t(&vn)[16] = (c & 1) ? va : vb;
+        tmem_wait_ld(v);
+        if (c < 3) {
+          __syncwarp();
+          tmem_ld16_async(col0 + (uint32_t)((c + 1) * 16), vn);
+        }
+        // chunk c + 3 of the sequence: chunk 3 of this item, else 0..2 of the next
+        if (c == 0)
+          load_x(xb[3], cur, 3);
+        else
+          load_x(xb[c - 1], nxt, c - 1);
+        uint32_t out[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          float x = xb[c][j];
+          float y = fmaf(it.dtc0, __uint_as_float(v[j]), dtcx * x);
+          x = x + a.dta0 * y;
+          if (fabsf(x) > 1.f) {
+            x = x > 0.f ? 1.f : -1.f;
+            y = 0.f;
+          }
+          out[j] = vr ? __float_as_uint(y * it.inv_dtc0) : 0u;
+          if (vr) {
+            const size_t idx = base + (size_t)(c * 16 + j) * a.n_pad;
+            a.x[idx] = x;
+            xh_out[idx] = __float2bfloat16_rn(x);
+            if (last) a.y[idx] = y;
+          }
+        }
+        if (!last) {
+          __syncwarp();
+          tmem_st16(col0 + (uint32_t)(c * 16), out);
+        }
+      }
+      if (!last) tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(edone0 + 8 * cur.i);
+      cur = nxt;
+    }
+  } else {
+    // ------------------------------------------------------------ signal
+    // After the epilogue of an item, release its X_hat_{t+1} to the other CTAs.
+    if (lane == 0) {
+      // A parity wait also succeeds on the previous phase of that parity, so every
+      // phase of edone is observed in order: first phase 0 (the initial y store).
+      bool ok = true;
+      for (int i = 0; ok && i < n_items; ++i)
+        if (a.t0 <= info[i].last_t) ok = rwait(edone0 + 8 * i, 0u, a.err, abort_flag);
+      for (int u = 0; ok && u < n_steps; ++u) {
+        const int t = a.t0 + u;
+        for (int i = 0; i < n_items; ++i) {
+          const ItemInfo& it = info[i];
+          if (t > it.last_t) continue;
+          // phase 0 of edone is the initial y store; step u completes phase u + 1
+          if (!(ok = rwait(edone0 + 8 * i, (uint32_t)(u + 1) & 1u, a.err, abort_flag))) break;
+          if (t == it.last_t) continue;  // nobody waits for X_hat beyond this launch
+          fence_proxy_async_global();
+          __threadfence();
+          red_release_gpu_add(a.done + (size_t)it.block * a.n_kt + it.k, 1u);
+        }
+        if (!ok) break;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512u);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side.
+
+bool run_variant(int v) { return v == RUN_VARIANT_JRES || v == RUN_VARIANT_STREAM; }
+
+// Work split: items are numbered row-tile-major (item = row_tile * n_kt + k).
+// JRES: every CTA takes up to MAX_ITEMS replica tiles of ONE row tile (its J tiles
+// stay resident).  Stream: the item list is cut into min(n_sm, items) near-equal
+// contiguous pieces.  False when the split does not fit one CTA per SM.
+bool run_plan(const Graph& g, int R, int n_sm, bool jres, bool use_lo, std::vector<int2>* work) {
+  if (R % RB != 0 || g.n_row_tiles == 0 || g.csr_mode) return false;
+  const int n_kt = R / RB;
+  const int64_t n_items = (int64_t)g.n_row_tiles * n_kt;
+  std::vector<int2> w;
+  if (jres) {
+    for (const RowTile& rt : g.h_rt)
+      if ((use_lo ? rt.n_all : rt.n_hi) > JRES_TILES) return false;
+    const int cpr = (n_kt + MAX_ITEMS - 1) / MAX_ITEMS;
+    if ((int64_t)g.n_row_tiles * cpr > n_sm) return false;
+    for (int32_t r = 0; r < g.n_row_tiles; ++r)
+      for (int c = 0; c < cpr; ++c) {
+        const int b = (int)((int64_t)n_kt * c / cpr), e = (int)((int64_t)n_kt * (c + 1) / cpr);
+        w.push_back(make_int2(r * n_kt + b, e - b));
+      }
+  } else {
+    if (n_items > (int64_t)MAX_ITEMS * n_sm) return false;
+    const int64_t grid = std::min<int64_t>(n_sm, n_items);
+    for (int64_t c = 0; c < grid; ++c) {
+      const int64_t b = n_items * c / grid, e = n_items * (c + 1) / grid;
+      w.push_back(make_int2((int)b, (int)(e - b)));
+    }
+  }
+  if (work) *work = std::move(w);
+  return true;
+}
+
+qh_status run_prepare(Ctx* ctx, const Graph& g, int R, bool jres, bool use_lo, RunBufs* rb) {
+  std::vector<int2> work;
+  if (!run_plan(g, R, ctx->n_sm, jres, use_lo, &work))
+    return set_err(ctx, QH_EINVAL, "multi-step kernel: split does not fit one CTA per SM");
+  std::vector<int32_t> rows(std::max(g.n_blocks, 1), 0);
+  for (const RowTile& rt : g.h_rt) rows[rt.block] += 1;
+  const int n_kt = R / RB;
+  rb->work = (int2*)ctx->scratch(work.size() * sizeof(int2), S_RUN_WORK);
+  rb->rows_b = (int32_t*)ctx->scratch(rows.size() * 4, S_RUN_ROWS);
+  rb->done = (uint32_t*)ctx->scratch((size_t)rows.size() * n_kt * 4, S_RUN_DONE);
+  if (!rb->work || !rb->rows_b || !rb->done)
+    return set_err(ctx, QH_ENOMEM, "allocation failed (multi-step kernel)");
+  QH_CUDA_TRY(cudaMemcpyAsync(rb->work, work.data(), work.size() * sizeof(int2),
+                              cudaMemcpyHostToDevice, ctx->stream));
+  QH_CUDA_TRY(cudaMemcpyAsync(rb->rows_b, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice,
+                              ctx->stream));
+  rb->grid = (int)work.size();
+  rb->n_done = (int64_t)rows.size() * n_kt;
+  rb->jres = jres;
+  return QH_OK;
+}
+
+template <bool JRES>
+qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const RunBufs& rb,
+                          __nv_bfloat16* xh0, __nv_bfloat16* xh1, int t0, int t1) {
+  using L = RunSmem<JRES>;
+  CUtensorMap mJ, mX0, mX1;
+  if (!make_map(&mJ, g.tile_bf16, TILE, (uint64_t)std::max<int64_t>(g.n_tiles, 1) * TILE, TILE) ||
+      !make_map(&mX0, xh0, (uint64_t)g.n_pad, (uint64_t)s.R, RB) ||
+      !make_map(&mX1, xh1, (uint64_t)g.n_pad, (uint64_t)s.R, RB))
+    return set_err(ctx, QH_ECUDA, "cuTensorMapEncodeTiled failed (multi-step kernel)");
+  RunArgs a{};
+  a.rt = s.rt;
+  a.tile_col = s.tile_col;
+  a.x = s.x;
+  a.y = s.y;
+  a.xh0 = xh0;
+  a.xh1 = xh1;
+  a.c0 = s.c0;
+  a.active = s.active;
+  a.steps_b = s.steps_b;
+  a.rows_b = rb.rows_b;
+  a.done = rb.done;
+  a.work = rb.work;
+  a.n_pad = s.n_pad;
+  a.n_kt = s.R / RB;
+  a.t0 = t0;
+  a.t1 = t1;
+  a.use_lo = s.use_lo;
+  a.dt = s.dt;
+  a.dta0 = s.dta0;
+  a.a0 = s.a0;
+  a.err = s.err;
+  QH_CUDA_TRY(cudaMemsetAsync(rb.done, 0, (size_t)rb.n_done * 4, ctx->stream));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)rb.grid);
+  cfg.blockDim = dim3(RUN_THREADS);
+  cfg.dynamicSmemBytes = L::BYTES;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs resident: the waits always end
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  note_launch(1);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_bsb_run<JRES>, mJ, mX0, mX1, a);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_bsb_run launch");
+  return QH_OK;
+}
+
+qh_status launch_run(Ctx* ctx, const Graph& g, const StepArgs& s, const RunBufs& rb,
+                     __nv_bfloat16* xh0, __nv_bfloat16* xh1, int t0, int t1) {
+  if (g.n_row_tiles == 0 || t1 <= t0) return QH_OK;
+  return rb.jres ? launch_run_impl<true>(ctx, g, s, rb, xh0, xh1, t0, t1)
+                 : launch_run_impl<false>(ctx, g, s, rb, xh0, xh1, t0, t1);
+}
+
+cudaError_t run_set_attrs() {
+  cudaError_t e = cudaFuncSetAttribute(k_bsb_run<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)RunSmem<true>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_bsb_run<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)RunSmem<false>::BYTES);
+  return e;
+}
+
+}  // namespace qh

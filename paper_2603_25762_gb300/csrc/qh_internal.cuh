@@ -251,8 +251,30 @@ void launch_tiles_to_e4m3(cudaStream_t s, const float* tf, int64_t n, float scal
 void launch_x_to_e4m3(cudaStream_t s, const float* x, int64_t n, uint8_t* h, uint8_t* l);
 int tc_n_variants();
 const char* tc_variant_name(int v);
-bool tc_variant_ok(int v, const Graph& g, int R);
+bool tc_variant_ok(int v, const Graph& g, int R, int n_sm, bool use_lo);
 qh_status tc_prepare(Ctx* ctx);
+
+// Multi-step tensor-core kernel (bsb_run.cu): one launch runs a range of steps with
+// the momentum y held in TMEM.  Two of the autotuner's variants select it.
+constexpr int RUN_VARIANT_JRES = 6;    // J tiles of the CTA's row tile resident in smem
+constexpr int RUN_VARIANT_STREAM = 7;  // J and X_hat K-slices streamed
+constexpr int S_RUN_WORK = 96, S_RUN_ROWS = 97, S_RUN_DONE = 98;  // scratch slots
+struct RunBufs {
+  int2* work = nullptr;       // [grid] {first item, item count}
+  int32_t* rows_b = nullptr;  // [n_blocks] row tiles per block
+  uint32_t* done = nullptr;   // [n_blocks][R/128] per-step release counters
+  int grid = 0;
+  int64_t n_done = 0;
+  bool jres = false;
+};
+bool run_variant(int v);
+bool run_plan(const Graph& g, int R, int n_sm, bool jres, bool use_lo, std::vector<int2>* work);
+qh_status run_prepare(Ctx* ctx, const Graph& g, int R, bool jres, bool use_lo, RunBufs* rb);
+// Steps t0 .. t1-1 in one launch.  X_hat_t is read from xh0 (t even) or xh1 (t odd);
+// x, y of `s` are updated in place.
+qh_status launch_run(Ctx* ctx, const Graph& g, const StepArgs& s, const RunBufs& rb,
+                     __nv_bfloat16* xh0, __nv_bfloat16* xh1, int t0, int t1);
+cudaError_t run_set_attrs();
 
 }  // namespace qh
 

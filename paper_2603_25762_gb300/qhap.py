@@ -51,7 +51,8 @@ class QhBsbOpts(C.Structure):
                 ("step_kernel", C.c_int32)]
 
 STEP_KERNELS = ["cta-bn128-s3", "cta-bn128-s2-x3", "cta-bn64-s2-x4", "cta-bn256-s2-x2",
-                "persistent-bn128", "persistent-bn64-tma-state"]
+                "persistent-bn128", "persistent-bn64-tma-state",
+                "multistep-y-tmem-jres", "multistep-y-tmem-stream"]
 
 
 class QhError(RuntimeError):
@@ -84,6 +85,7 @@ _SIGS = {
     "qh_phase": (C.c_int, [P, P, P, P, P, P, I32]),
     "qh_debug_matvec": (C.c_int, [P, P, I32, I32, P, P]),
     "qh_debug_steps": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P]),
+    "qh_debug_steps_v": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P, I32]),
     "qh_debug_layout": (C.c_int, [P, P, P, P, P]),
     "qh_matvec_bf16_noalloc": (C.c_int, [P, P, I32, P, P]),
     "qh_solution_kernel": (C.c_char_p, [P]),
@@ -279,10 +281,14 @@ class Context:
     def debug_matvec(self, g, precision, R, x, z):
         self._check(lib().qh_debug_matvec(self.h, g.h, precision, R, _ptr(x), _ptr(z)))
 
-    def debug_steps(self, g, precision, R, x, y, t0, nsteps, steps, dt=1.0, a0=1.0, c0=None):
+    def debug_steps(self, g, precision, R, x, y, t0, nsteps, steps, dt=1.0, a0=1.0, c0=None,
+                    step_kernel=None):
+        """step_kernel: None = default kernel, or a name from STEP_KERNELS."""
         c0a = None if c0 is None else _np(c0, np.float64)
-        self._check(lib().qh_debug_steps(self.h, g.h, precision, R, _ptr(x), _ptr(y), t0, nsteps,
-                                         steps, dt, a0, _ptr(c0a) if c0a is not None else None))
+        sk = -1 if step_kernel is None else STEP_KERNELS.index(step_kernel)
+        self._check(lib().qh_debug_steps_v(self.h, g.h, precision, R, _ptr(x), _ptr(y), t0,
+                                           nsteps, steps, dt, a0,
+                                           _ptr(c0a) if c0a is not None else None, sk))
 
     def matvec_bf16_noalloc(self, g, R, x, z):
         """J x X in BF16 without any device allocation (fixed 8.5 MiB library array)."""
