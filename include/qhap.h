@@ -183,8 +183,8 @@ typedef struct {
   int32_t patience;     /* stop a block after this many checks without a better
                            best-replica energy (0 = never stop early) */
   int32_t refine_max;   /* SNP mode: maximum refinement iterations (>= 1) */
-  int32_t step_kernel;  /* BF16: -1 = autotune, else a variant index 0..7 (see
-                           qh_solution_kernel for names; 6 and 7 are the multi-step
+  int32_t step_kernel;  /* BF16: -1 = autotune, else a variant index 0..9 (see
+                           qh_solution_kernel for names; 6..9 are the multi-step
                            kernels that keep y on chip and launch once per step
                            range); invalid choices -> QH_EINVAL */
 } qh_bsb_opts;

@@ -174,7 +174,7 @@ qh_status autotune(Ctx* ctx, const Graph& g, StepArgs a, const SolveBufs& B, int
     p.variant = v;
     RunBufs rb;
     if (run_variant(v)) {
-      qh_status st = run_prepare(ctx, g, R, v == RUN_VARIANT_JRES, a.use_lo != 0, &rb);
+      qh_status st = run_prepare(ctx, g, R, v, a.use_lo != 0, &rb);
       if (st != QH_OK) return st;
     }
     float ms = 0.f;
@@ -633,7 +633,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     return set_err(ctx, QH_EINVAL, "multi-step kernel needs dt * c0 to be a normal float in every block");
   }
   if (multistep) {
-    qh_status st = run_prepare(ctx, W, R, tplan.variant == RUN_VARIANT_JRES, a.use_lo != 0, &rb);
+    qh_status st = run_prepare(ctx, W, R, tplan.variant, a.use_lo != 0, &rb);
     if (st != QH_OK) {
       delete sh;
       return st;
@@ -1166,7 +1166,7 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
     }
     if (step_kernel >= 0 && run_variant(step_kernel)) {  // one launch for all nsteps
       RunBufs rb;
-      st = run_prepare(ctx, g, R, step_kernel == RUN_VARIANT_JRES, a.use_lo != 0, &rb);
+      st = run_prepare(ctx, g, R, step_kernel, a.use_lo != 0, &rb);
       if (st) return st;
       if (t0 % 2 == 1) {  // X_hat_t lives in xh0 for even t, xh1 for odd t
         QH_CUDA_TRY(cudaMemsetAsync(xh0, 0, NS * 2, s));

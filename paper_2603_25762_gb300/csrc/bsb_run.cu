@@ -12,18 +12,24 @@
 // first step and written back after the last one.  Per spin-update the state costs
 // 4 + 4 bytes (x) + 2 bytes (X_hat) of memory traffic instead of 16 + 2.
 //
-// X_hat_t of a block is read by every row tile of that block, so step t+1 of item
-// (row tile, replica tile k) may start only when all row tiles of its block have
-// written X_hat_{t+1} for replica tile k.  Per (block, k) a counter in global memory
-// counts finished items; a dedicated warp releases it (gpu scope) after the item's
-// epilogue, and the TMA producer acquires it before it loads X_hat of the next step.
+// Hand-off between steps, through release counters in global memory that a dedicated
+// warp releases (gpu scope) after each item's epilogue and the TMA producer acquires
+// before it loads X_hat of the next step.  Two modes:
+//  * tile: item (row tile r, replica tile k) reads X_hat only in the column tiles of
+//    r's nonzero J tiles; per item a counter counts its finished steps, and column
+//    tile c of X_hat_t is loaded once counter (c, k) reaches the steps done.
+//  * group: one counter per (block, k) counts the finished items of all row tiles of
+//    the block; step t+1 of any of them starts when all have finished step t.
+// J's tile pattern is symmetric, so in both modes the same waits also guarantee that
+// every reader of r's column has finished step t-1 before item r overwrites the
+// buffer that held X_hat_{t-1} with X_hat_{t+1}.
 // All CTAs are co-resident (cooperative launch), so these waits always end; every
 // wait is nevertheless bounded and sets ERR_TIMEOUT in the error word when it
 // expires, after which all CTAs stop and drain their copies in flight.
 //
 // Roles (352 threads): warp 0 = TMA producer, warp 1 = MMA issuer (one thread
-// each), warps 2-9 = epilogue (TMEM lane quarter = warp % 4, two warps per quarter
-// split the 128 columns), warp 10 = signal.  With JRES the J tiles of the CTA's
+// each), warps 2-9 = epilogue (TMEM lane quarter = warp % 4 = 32 vertices, two warps
+// per quarter split the 128 replicas), warp 10 = signal.  With JRES the J tiles of the CTA's
 // single row tile stay in shared memory for the whole launch and only X_hat
 // streams; otherwise J and X_hat K-slices stream through the ring together.
 #include <algorithm>
@@ -47,9 +53,10 @@ constexpr int JRES_TILES = 4;              // resident J tiles (hi + lo entries)
 struct ItemInfo {
   int32_t row0, valid, tile_begin, nk;  // nk = K-slices (2 per J tile entry)
   int32_t block, k, last_t, steps_b;    // last_t < t0: nothing to do this launch
+  int32_t rt;                           // row tile index (= its column tile index)
   uint32_t rows_b;                      // row tiles of the block
   float dtc0, inv_dtc0;                 // dt * c0 and its reciprocal
-  int32_t pad_;
+  double inv_steps;                     // 1 / steps_b
 };
 
 template <bool JRES>
@@ -73,9 +80,12 @@ struct RunArgs {
   const float* c0;          // [n_blocks]
   const int32_t* active;    // [n_blocks] or nullptr
   const int32_t* steps_b;   // [n_blocks]
+  uint32_t* done;           // tile: [n_row_tiles][n_kt] steps finished; group:
+                            // [n_blocks][n_kt] items finished; zero at launch
   const int32_t* rows_b;    // [n_blocks] row tiles per block
-  uint32_t* done;           // [n_blocks][n_kt], zero at launch
+  int32_t group_sync;       // hand-off mode: 0 = tile, 1 = group
   const int2* work;         // [grid] {first item, item count}
+  int32_t item_stride;      // a CTA's items are first, first + stride, ...
   int32_t n_pad, n_kt, t0, t1, use_lo;
   float dt, dta0;
   double a0;
@@ -147,13 +157,16 @@ __device__ __forceinline__ bool rwait(uint32_t bar, uint32_t parity, int32_t* er
 
 // Bounded wait until a release counter reaches `target`; gives up on an abort of
 // this CTA or a timeout reported by any other CTA.
+// Polls back off for 64 ns, and the error word is read every 64th poll only, so a
+// waiting producer takes few issue slots and little L2 bandwidth.
 __device__ __forceinline__ bool wait_count(const uint32_t* p, uint32_t target, int32_t* err,
                                            volatile int32_t* abort) {
   if (ld_acquire_gpu(p) >= target) return true;
   const long long t0 = clock64();
-  while (ld_acquire_gpu(p) < target) {
+  for (uint32_t n = 1; ld_acquire_gpu(p) < target; ++n) {
+    __nanosleep(64);
     if (*abort) return false;
-    if (*reinterpret_cast<volatile int32_t*>(err) & ERR_TIMEOUT) {
+    if ((n & 63u) == 0 && (*reinterpret_cast<volatile int32_t*>(err) & ERR_TIMEOUT)) {
       *abort = 1;
       return false;
     }
@@ -204,7 +217,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (warp == 2 && lane < n_items) {
-    const int item = wk.x + lane;
+    const int item = wk.x + lane * a.item_stride;
     const RowTile rt = a.rt[item / a.n_kt];
     ItemInfo it;
     it.row0 = rt.row0;
@@ -216,10 +229,11 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
     it.steps_b = a.steps_b[rt.block];
     const bool on = a.active == nullptr || a.active[rt.block] != 0;
     it.last_t = on ? min(a.t1, it.steps_b) - 1 : a.t0 - 1;
+    it.rt = item / a.n_kt;
     it.rows_b = (uint32_t)a.rows_b[rt.block];
     it.dtc0 = a.dt * a.c0[rt.block];
     it.inv_dtc0 = 1.0f / it.dtc0;
-    it.pad_ = 0;
+    it.inv_steps = 1.0 / (double)it.steps_b;
     info[lane] = it;
   }
   if (threadIdx.x == 0) {
@@ -263,22 +277,33 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
         for (int i = 0; ok && i < n_items; ++i) {
           const ItemInfo& it = info[i];
           if (t > it.last_t) continue;
-          if (u > 0) {  // X_hat_t of the whole block, replica tile k, is written
-            ok = wait_count(a.done + (size_t)it.block * a.n_kt + it.k, (uint32_t)u * it.rows_b,
-                            a.err, abort_flag);
+          // tile mode: the item's own previous step has been released (this keeps the
+          // signal warp at most one edone phase behind even when the diagonal J tile is
+          // empty); group mode: every row tile of the block has finished step t-1
+          if (u > 0) {
+            ok = a.group_sync
+                     ? wait_count(a.done + (size_t)it.block * a.n_kt + it.k, (uint32_t)u * it.rows_b,
+                                  a.err, abort_flag)
+                     : wait_count(a.done + (size_t)it.rt * a.n_kt + it.k, (uint32_t)u, a.err,
+                                  abort_flag);
             if (!ok) break;
-            fence_proxy_async_global();
+            if (a.group_sync) fence_proxy_async_global();
           }
           for (int kb = 0; kb < it.nk; ++kb) {
+            const int e = kb >> 1, half = kb & 1;
+            const int32_t ct = a.tile_col[it.tile_begin + e];
+            if (u > 0 && half == 0 && !a.group_sync) {  // column tile ct of X_hat_t is written
+              ok = wait_count(a.done + (size_t)ct * a.n_kt + it.k, (uint32_t)u, a.err, abort_flag);
+              if (!ok) break;
+              fence_proxy_async_global();
+            }
             const int s = (int)(q % ST);
             const uint32_t ph = (q / ST) & 1u;
             if (!(ok = rwait(empty0 + 8 * s, ph ^ 1u, a.err, abort_flag))) break;
             uint8_t* slot = smem + L::RING_OFF + s * L::SLOT;
             mbar_expect_tx(full0 + 8 * s, L::SLOT);
-            const int e = kb >> 1, half = kb & 1;
             const uint32_t xdst = JRES ? smem_u32(slot) : smem_u32(slot + SLICE);
-            tma_load_2d(xdst, mx, full0 + 8 * s, a.tile_col[it.tile_begin + e] * TILE + half * 64,
-                        it.k * RB);
+            tma_load_2d(xdst, mx, full0 + 8 * s, ct * TILE + half * 64, it.k * RB);
             if (!JRES)
               tma_load_2d(smem_u32(slot), &tmJ, full0 + 8 * s, half * 64,
                           (it.tile_begin + e) * TILE);
@@ -314,11 +339,12 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
             if (!(ok = rwait(full0 + 8 * s, ph, a.err, abort_flag))) break;
             tc_fence_after();
             uint8_t* slot = smem + L::RING_OFF + s * L::SLOT;
-            const uint64_t ad = sdesc_sw128(JRES ? smem_u32(smem + kb * SLICE) : smem_u32(slot));
-            const uint64_t bd = sdesc_sw128(JRES ? smem_u32(slot) : smem_u32(slot + SLICE));
+            // D (vertices x replicas) += J slice (A) x X_hat slice (B)^T
+            const uint64_t jd = sdesc_sw128(JRES ? smem_u32(smem + kb * SLICE) : smem_u32(slot));
+            const uint64_t xd = sdesc_sw128(JRES ? smem_u32(slot) : smem_u32(slot + SLICE));
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-              mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, 1u);
+              mma_bf16(d, jd + (uint64_t)(2 * k), xd + (uint64_t)(2 * k), idesc, 1u);
             mma_commit(empty0 + 8 * s);
             ++q;
           }
@@ -330,22 +356,32 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
     }
   } else if (warp < SIGNAL_WARP) {
     // ------------------------------------------------------------ epilogue
+    // The accumulator is (vertex x replica): TMEM lane = vertex of the row tile,
+    // column = replica of the item.  A thread owns one vertex and 64 replicas (half hh
+    // of the item) in four chunks of 16; for each replica the 32 lanes of a warp touch
+    // 32 consecutive vertices, one coalesced 128-byte line of x ([R][n_pad]).
+    // Element indices fit 32 bits: R * n_pad <= MAX_ITEMS * 128 * 128 * CTAs.
     const int qd = warp & 3, hh = (warp - 2) >> 2;
     const int r = qd * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(hh * 64);
+    float* __restrict__ xs = a.x;
+    float* __restrict__ ys = a.y;
+    const uint32_t np = (uint32_t)a.n_pad;
+    // index of (replica k*128 + hh*64 + 16*chunk, vertex row0 + r)
+    auto elem0 = [&](const ItemInfo& it, int chunk) -> uint32_t {
+      return (uint32_t)(it.k * RB + hh * 64 + chunk * 16) * np + (uint32_t)(it.row0 + r);
+    };
     // y -> y / (dt c0) into the item's TMEM columns
     for (int i = 0; i < n_items; ++i) {
-      const ItemInfo& it = info[i];
+      const ItemInfo it = info[i];
       if (a.t0 > it.last_t) continue;
       const bool vr = r < it.valid;
-      const size_t base = (size_t)(it.k * RB + hh * 64) * a.n_pad + it.row0 + r;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
+        const float* yc = ys + elem0(it, c);
         uint32_t v[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          v[j] = vr ? __float_as_uint(a.y[base + (size_t)(c * 16 + j) * a.n_pad] * it.inv_dtc0)
-                    : 0u;
+        for (int j = 0; j < 16; ++j) v[j] = vr ? __float_as_uint(yc[j * np] * it.inv_dtc0) : 0u;
         __syncwarp();
         tmem_st16(lane_base + (uint32_t)(i * RB + c * 16), v);
       }
@@ -354,31 +390,40 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(edone0 + 8 * i);
     }
-    // x is prefetched three 16-column chunks ahead along the (step, item) sequence;
+    // x is prefetched three 16-replica chunks ahead along the (step, item) sequence;
     // chunk c of any item always lands in xb[c]
     float xb[4][16];
     Cursor cur{0, -1};
     cur = next_live(cur, info, n_items, a.t0, n_steps);
-    auto load_x = [&](float (&dst)[16], Cursor c, int chunk) {
-      if (c.u >= n_steps) return;
-      const ItemInfo& it = info[c.i];
-      if (r >= it.valid) return;
-      const size_t b0 = (size_t)(it.k * RB + hh * 64 + chunk * 16) * a.n_pad + it.row0 + r;
+    ItemInfo nit = info[cur.i < n_items ? cur.i : 0];
+    auto load_x = [&](float (&dst)[16], const ItemInfo& it, bool on, int chunk) {
+      if (!on || r >= it.valid) return;
+      // plain pointer based on xs: the prefetch may read what this thread stored one
+      // chunk earlier (a CTA with a single item) and must stay behind that store
+      const float* src = xs + elem0(it, chunk);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) dst[j] = a.x[b0 + (size_t)j * a.n_pad];
+      for (int j = 0; j < 16; ++j) dst[j] = src[j * np];
     };
-    load_x(xb[0], cur, 0);
-    load_x(xb[1], cur, 1);
-    load_x(xb[2], cur, 2);
+    {
+      const bool on = cur.u < n_steps;
+      load_x(xb[0], nit, on, 0);
+      load_x(xb[1], nit, on, 1);
+      load_x(xb[2], nit, on, 2);
+    }
     while (cur.u < n_steps) {
-      const ItemInfo& it = info[cur.i];
+      const ItemInfo it = nit;  // registers: the loop's stores cannot alias it
       const int t = a.t0 + cur.u;
       const Cursor nxt = next_live(cur, info, n_items, a.t0, n_steps);
+      const bool non = nxt.u < n_steps;
+      nit = info[non ? nxt.i : cur.i];
       const bool vr = r < it.valid, last = t == it.last_t;
-      const size_t base = (size_t)(it.k * RB + hh * 64) * a.n_pad + it.row0 + r;
-      __nv_bfloat16* xh_out = (t & 1) ? a.xh0 : a.xh1;  // X_hat_{t+1}
-      const double at = a.a0 * (double)t / (double)it.steps_b;
-      const float dtcx = a.dt * (float)(-(a.a0 - at));
+      __nv_bfloat16* __restrict__ xh_out = (t & 1) ? a.xh0 : a.xh1;  // X_hat_{t+1}
+      // -(a0 - a(t)) in FP64 as in the other step kernels (a(t) = a0 t / steps_b, with
+      // the reciprocal taken once per item), by one lane, shared with the warp
+      float coef = 0.f;
+      if (lane == 0) coef = (float)(-(a.a0 - a.a0 * (double)t * it.inv_steps));
+      const float dtcx = a.dt * __shfl_sync(0xffffffffu, coef, 0);
+      const float dtc0 = it.dtc0, inv = it.inv_dtc0, dta0 = a.dta0;
       const bool ok = __all_sync(0xffffffffu, rwait(accf0 + 8 * cur.i, (uint32_t)cur.u & 1u,
                                                     a.err, abort_flag));
       if (!ok) break;
@@ -398,25 +443,34 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
         }
         // chunk c + 3 of the sequence: chunk 3 of this item, else 0..2 of the next
         if (c == 0)
-          load_x(xb[3], cur, 3);
+          load_x(xb[3], it, true, 3);
         else
-          load_x(xb[c - 1], nxt, c - 1);
+          load_x(xb[c - 1], nit, non, c - 1);
+        const uint32_t e0 = elem0(it, c);
+        float* xc = xs + e0;
+        float* yc = ys + e0;
+        __nv_bfloat16* hc = xh_out + e0;
         uint32_t out[16];
+        float xo[16], yo[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          float x = xb[c][j];
-          float y = fmaf(it.dtc0, __uint_as_float(v[j]), dtcx * x);
-          x = x + a.dta0 * y;
-          if (fabsf(x) > 1.f) {
-            x = x > 0.f ? 1.f : -1.f;
-            y = 0.f;
+        for (int j = 0; j < 16; ++j) {  // branch-free update and wall
+          const float x0 = xb[c][j];
+          const float y1 = fmaf(dtc0, __uint_as_float(v[j]), dtcx * x0);
+          const float x1 = fmaf(dta0, y1, x0);
+          const bool wall = fabsf(x1) > 1.f;
+          xo[j] = wall ? copysignf(1.f, x1) : x1;
+          yo[j] = wall ? 0.f : y1;
+          out[j] = vr ? __float_as_uint(yo[j] * inv) : 0u;
+        }
+        if (vr) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            xc[j * np] = xo[j];
+            hc[j * np] = __float2bfloat16_rn(xo[j]);
           }
-          out[j] = vr ? __float_as_uint(y * it.inv_dtc0) : 0u;
-          if (vr) {
-            const size_t idx = base + (size_t)(c * 16 + j) * a.n_pad;
-            a.x[idx] = x;
-            xh_out[idx] = __float2bfloat16_rn(x);
-            if (last) a.y[idx] = y;
+          if (last) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) yc[j * np] = yo[j];
           }
         }
         if (!last) {
@@ -449,7 +503,8 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
           if (t == it.last_t) continue;  // nobody waits for X_hat beyond this launch
           fence_proxy_async_global();
           __threadfence();
-          red_release_gpu_add(a.done + (size_t)it.block * a.n_kt + it.k, 1u);
+          red_release_gpu_add(
+              a.done + (size_t)(a.group_sync ? it.block : it.rt) * a.n_kt + it.k, 1u);
         }
         if (!ok) break;
       }
@@ -468,13 +523,22 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
 // ---------------------------------------------------------------------------
 // Host side.
 
-bool run_variant(int v) { return v == RUN_VARIANT_JRES || v == RUN_VARIANT_STREAM; }
+bool run_variant(int v) { return v >= RUN_VARIANT_FIRST && v < RUN_VARIANT_FIRST + 4; }
+static bool run_jres(int v) { return v == RUN_VARIANT_FIRST || v == RUN_VARIANT_FIRST + 2; }
+static bool run_group(int v) { return v == RUN_VARIANT_FIRST || v == RUN_VARIANT_FIRST + 3; }
 
-// Work split: items are numbered row-tile-major (item = row_tile * n_kt + k).
-// JRES: every CTA takes up to MAX_ITEMS replica tiles of ONE row tile (its J tiles
-// stay resident).  Stream: the item list is cut into min(n_sm, items) near-equal
-// contiguous pieces.  False when the split does not fit one CTA per SM.
-bool run_plan(const Graph& g, int R, int n_sm, bool jres, bool use_lo, std::vector<int2>* work) {
+// Work split: items are numbered row-tile-major (item = row_tile * n_kt + k), and a
+// CTA processes its items in a fixed order every step.  The split puts the row-tile
+// neighbours of an item (item -+ n_kt, same k) at the same position in their CTAs, so
+// an item's inputs for step t+1 are finished a whole step period before it needs them.
+// JRES: every CTA takes up to MAX_ITEMS consecutive replica tiles of ONE row tile (its
+// J tiles stay resident), the same k ranges in every row.  Stream: CTA c of G =
+// min(n_sm, items) takes items c, c + G, c + 2G, ...  False when the split does not
+// fit one CTA per SM.
+bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, std::vector<int2>* work,
+              int* stride) {
+  if (!run_variant(variant)) return false;
+  const bool jres = run_jres(variant);
   if (R % RB != 0 || g.n_row_tiles == 0 || g.csr_mode) return false;
   const int n_kt = R / RB;
   const int64_t n_items = (int64_t)g.n_row_tiles * n_kt;
@@ -492,25 +556,27 @@ bool run_plan(const Graph& g, int R, int n_sm, bool jres, bool use_lo, std::vect
   } else {
     if (n_items > (int64_t)MAX_ITEMS * n_sm) return false;
     const int64_t grid = std::min<int64_t>(n_sm, n_items);
-    for (int64_t c = 0; c < grid; ++c) {
-      const int64_t b = n_items * c / grid, e = n_items * (c + 1) / grid;
-      w.push_back(make_int2((int)b, (int)(e - b)));
-    }
+    for (int64_t c = 0; c < grid; ++c)
+      w.push_back(make_int2((int)c, (int)((n_items - c + grid - 1) / grid)));
   }
+  if (stride) *stride = jres ? 1 : (int)w.size();
   if (work) *work = std::move(w);
   return true;
 }
 
-qh_status run_prepare(Ctx* ctx, const Graph& g, int R, bool jres, bool use_lo, RunBufs* rb) {
+qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo, RunBufs* rb) {
   std::vector<int2> work;
-  if (!run_plan(g, R, ctx->n_sm, jres, use_lo, &work))
+  if (!run_plan(g, R, ctx->n_sm, variant, use_lo, &work, &rb->item_stride))
     return set_err(ctx, QH_EINVAL, "multi-step kernel: split does not fit one CTA per SM");
+  const int n_kt = R / RB;
+  rb->jres = run_jres(variant);
+  rb->group_sync = run_group(variant);
   std::vector<int32_t> rows(std::max(g.n_blocks, 1), 0);
   for (const RowTile& rt : g.h_rt) rows[rt.block] += 1;
-  const int n_kt = R / RB;
+  rb->n_done = (int64_t)(rb->group_sync ? (int64_t)rows.size() : g.n_row_tiles) * n_kt;
   rb->work = (int2*)ctx->scratch(work.size() * sizeof(int2), S_RUN_WORK);
   rb->rows_b = (int32_t*)ctx->scratch(rows.size() * 4, S_RUN_ROWS);
-  rb->done = (uint32_t*)ctx->scratch((size_t)rows.size() * n_kt * 4, S_RUN_DONE);
+  rb->done = (uint32_t*)ctx->scratch((size_t)rb->n_done * 4, S_RUN_DONE);
   if (!rb->work || !rb->rows_b || !rb->done)
     return set_err(ctx, QH_ENOMEM, "allocation failed (multi-step kernel)");
   QH_CUDA_TRY(cudaMemcpyAsync(rb->work, work.data(), work.size() * sizeof(int2),
@@ -518,8 +584,6 @@ qh_status run_prepare(Ctx* ctx, const Graph& g, int R, bool jres, bool use_lo, R
   QH_CUDA_TRY(cudaMemcpyAsync(rb->rows_b, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice,
                               ctx->stream));
   rb->grid = (int)work.size();
-  rb->n_done = (int64_t)rows.size() * n_kt;
-  rb->jres = jres;
   return QH_OK;
 }
 
@@ -542,9 +606,11 @@ qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const Run
   a.c0 = s.c0;
   a.active = s.active;
   a.steps_b = s.steps_b;
-  a.rows_b = rb.rows_b;
   a.done = rb.done;
   a.work = rb.work;
+  a.item_stride = rb.item_stride;
+  a.rows_b = rb.rows_b;
+  a.group_sync = rb.group_sync ? 1 : 0;
   a.n_pad = s.n_pad;
   a.n_kt = s.R / RB;
   a.t0 = t0;

@@ -1097,21 +1097,22 @@ bool tc_plan_ok(int R, const TcPlan& plan) {
 }
 
 // Solver-step kernel variants the autotuner chooses from.
-int tc_n_variants() { return 8; }
+int tc_n_variants() { return 10; }
 const char* tc_variant_name(int v) {
   static const char* names[] = {"cta-bn128-s3",          "cta-bn128-s2-x3",
                                 "cta-bn64-s2-x4",        "cta-bn256-s2-x2",
                                 "persistent-bn128",      "persistent-bn64-tma-state",
-                                "multistep-y-tmem-jres", "multistep-y-tmem-stream"};
-  return (v >= 0 && v < 8) ? names[v] : "none";
+                                "multistep-jres-group",  "multistep-stream-tile",
+                                "multistep-jres-tile",   "multistep-stream-group"};
+  return (v >= 0 && v < 10) ? names[v] : "none";
 }
 bool tc_variant_ok(int v, const Graph& g, int R, int n_sm, bool use_lo) {
   switch (v) {
     case 0: case 1: case 4: return R % 128 == 0 && (v != 4 || g.max_tiles_per_row <= P2_MAX_TILES);
     case 2: case 5: return R % 64 == 0;
     case 3: return R % 256 == 0;
-    case RUN_VARIANT_JRES: case RUN_VARIANT_STREAM:
-      return run_plan(g, R, n_sm, v == RUN_VARIANT_JRES, use_lo, nullptr);
+    case 6: case 7: case 8: case 9:
+      return run_plan(g, R, n_sm, v, use_lo, nullptr);
     default: return false;
   }
 }
@@ -1127,7 +1128,7 @@ qh_status launch_step_tc(Ctx* ctx, const Graph& g, const StepArgs& a, const __nv
       case 3: return launch_variant<256, 2, 2>(ctx, g, a, xh_in);
       case 4: return launch_persistent2(ctx, g, a, xh_in);
       case 5: return launch_persistent<64, 3>(ctx, g, a, xh_in);
-      case RUN_VARIANT_JRES: case RUN_VARIANT_STREAM:
+      case 6: case 7: case 8: case 9:
         return set_err(ctx, QH_EUNSUPPORTED, "the multi-step kernel runs step ranges (launch_run)");
       default: break;
     }

@@ -255,21 +255,25 @@ bool tc_variant_ok(int v, const Graph& g, int R, int n_sm, bool use_lo);
 qh_status tc_prepare(Ctx* ctx);
 
 // Multi-step tensor-core kernel (bsb_run.cu): one launch runs a range of steps with
-// the momentum y held in TMEM.  Two of the autotuner's variants select it.
-constexpr int RUN_VARIANT_JRES = 6;    // J tiles of the CTA's row tile resident in smem
-constexpr int RUN_VARIANT_STREAM = 7;  // J and X_hat K-slices streamed
+// the momentum y held in TMEM.  Four of the autotuner's variants select it:
+//   6: J resident in smem, group hand-off   7: J streamed, tile hand-off
+//   8: J resident in smem, tile hand-off    9: J streamed, group hand-off
+constexpr int RUN_VARIANT_FIRST = 6;
 constexpr int S_RUN_WORK = 96, S_RUN_ROWS = 97, S_RUN_DONE = 98;  // scratch slots
 struct RunBufs {
   int2* work = nullptr;       // [grid] {first item, item count}
   int32_t* rows_b = nullptr;  // [n_blocks] row tiles per block
-  uint32_t* done = nullptr;   // [n_blocks][R/128] per-step release counters
+  uint32_t* done = nullptr;   // release counters (per item or per block x replica tile)
   int grid = 0;
+  int item_stride = 1;        // a CTA's items: first, first + stride, ...
   int64_t n_done = 0;
   bool jres = false;
+  bool group_sync = false;
 };
 bool run_variant(int v);
-bool run_plan(const Graph& g, int R, int n_sm, bool jres, bool use_lo, std::vector<int2>* work);
-qh_status run_prepare(Ctx* ctx, const Graph& g, int R, bool jres, bool use_lo, RunBufs* rb);
+bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, std::vector<int2>* work,
+              int* stride = nullptr);
+qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo, RunBufs* rb);
 // Steps t0 .. t1-1 in one launch.  X_hat_t is read from xh0 (t even) or xh1 (t odd);
 // x, y of `s` are updated in place.
 qh_status launch_run(Ctx* ctx, const Graph& g, const StepArgs& s, const RunBufs& rb,

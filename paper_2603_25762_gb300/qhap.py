@@ -52,7 +52,8 @@ class QhBsbOpts(C.Structure):
 
 STEP_KERNELS = ["cta-bn128-s3", "cta-bn128-s2-x3", "cta-bn64-s2-x4", "cta-bn256-s2-x2",
                 "persistent-bn128", "persistent-bn64-tma-state",
-                "multistep-y-tmem-jres", "multistep-y-tmem-stream"]
+                "multistep-jres-group", "multistep-stream-tile", "multistep-jres-tile",
+                "multistep-stream-group"]
 
 
 class QhError(RuntimeError):

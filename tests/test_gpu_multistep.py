@@ -13,7 +13,8 @@ from paper_2603_25762_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-MULTI = ["multistep-y-tmem-jres", "multistep-y-tmem-stream"]
+MULTI = ["multistep-jres-group", "multistep-stream-tile", "multistep-jres-tile",
+         "multistep-stream-group"]
 
 
 @pytest.fixture(scope="module")
@@ -89,7 +90,7 @@ def test_multistep_state_region_many_row_tiles(q, ctx, oracle, kernel):
 def test_multistep_state_snp_hilo(q, ctx, oracle):
     # real-valued SNP weights with the BF16 hi + lo split of J
     fr = synth.ont_region(1003, scale=0.04)
-    _state_case(q, ctx, oracle, fr, q.MODE_SNP, q.PREC_BF16X2, "multistep-y-tmem-stream", 128,
+    _state_case(q, ctx, oracle, fr, q.MODE_SNP, q.PREC_BF16X2, "multistep-stream-tile", 128,
                 20, 3)
 
 
