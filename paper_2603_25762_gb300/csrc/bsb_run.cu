@@ -73,8 +73,10 @@ struct RunSmem {
 struct RunArgs {
   const RowTile* rt;
   const int32_t* tile_col;
-  float* x;                 // [R][n_pad]
-  float* y;                 // [R][n_pad]
+  float* x;                 // [R][n_pad]: read before the first step, written after the last
+  float* y;                 // [R][n_pad]: likewise
+  float4* xq;               // [R/4][n_pad] working copy of x between the first and the last
+                            // step: xq[(rho/4) n_pad + v] holds replicas rho..rho+3 of v
   __nv_bfloat16* xh0;       // X_hat_t for even t
   __nv_bfloat16* xh1;       // X_hat_t for odd t
   const float* c0;          // [n_blocks]
@@ -157,14 +159,14 @@ __device__ __forceinline__ bool rwait(uint32_t bar, uint32_t parity, int32_t* er
 
 // Bounded wait until a release counter reaches `target`; gives up on an abort of
 // this CTA or a timeout reported by any other CTA.
-// Polls back off for 64 ns, and the error word is read every 64th poll only, so a
+// Polls back off for 32 ns, and the error word is read every 64th poll only, so a
 // waiting producer takes few issue slots and little L2 bandwidth.
 __device__ __forceinline__ bool wait_count(const uint32_t* p, uint32_t target, int32_t* err,
                                            volatile int32_t* abort) {
   if (ld_acquire_gpu(p) >= target) return true;
   const long long t0 = clock64();
   for (uint32_t n = 1; ld_acquire_gpu(p) < target; ++n) {
-    __nanosleep(64);
+    __nanosleep(32);
     if (*abort) return false;
     if ((n & 63u) == 0 && (*reinterpret_cast<volatile int32_t*>(err) & ERR_TIMEOUT)) {
       *abort = 1;
@@ -371,7 +373,11 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
     auto elem0 = [&](const ItemInfo& it, int chunk) -> uint32_t {
       return (uint32_t)(it.k * RB + hh * 64 + chunk * 16) * np + (uint32_t)(it.row0 + r);
     };
-    // y -> y / (dt c0) into the item's TMEM columns
+    // float4 index of replicas 4m .. 4m+3 of this chunk's 16 (m = 0..3), vertex row0 + r
+    auto quad0 = [&](const ItemInfo& it, int chunk) -> uint32_t {
+      return (uint32_t)(it.k * (RB / 4) + hh * 16 + chunk * 4) * np + (uint32_t)(it.row0 + r);
+    };
+    // y -> y / (dt c0) into the item's TMEM columns; x into the blocked working copy
     for (int i = 0; i < n_items; ++i) {
       const ItemInfo it = info[i];
       if (a.t0 > it.last_t) continue;
@@ -379,9 +385,18 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const float* yc = ys + elem0(it, c);
+        const float* xc = xs + elem0(it, c);
         uint32_t v[16];
+        float xv[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = vr ? __float_as_uint(yc[j * np] * it.inv_dtc0) : 0u;
+        for (int j = 0; j < 16; ++j) {
+          v[j] = vr ? __float_as_uint(yc[j * np] * it.inv_dtc0) : 0u;
+          xv[j] = vr ? xc[j * np] : 0.f;
+        }
+        float4* qc = a.xq + quad0(it, c);
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          qc[m * np] = make_float4(xv[4 * m], xv[4 * m + 1], xv[4 * m + 2], xv[4 * m + 3]);
         __syncwarp();
         tmem_st16(lane_base + (uint32_t)(i * RB + c * 16), v);
       }
@@ -397,12 +412,18 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
     cur = next_live(cur, info, n_items, a.t0, n_steps);
     ItemInfo nit = info[cur.i < n_items ? cur.i : 0];
     auto load_x = [&](float (&dst)[16], const ItemInfo& it, bool on, int chunk) {
-      if (!on || r >= it.valid) return;
-      // plain pointer based on xs: the prefetch may read what this thread stored one
-      // chunk earlier (a CTA with a single item) and must stay behind that store
-      const float* src = xs + elem0(it, chunk);
+      if (!on) return;
+      // the prefetch may read what this thread stored one chunk earlier (a CTA with a
+      // single item): both go through a.xq, so program order keeps it behind the store
+      const float4* src = a.xq + quad0(it, chunk);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) dst[j] = src[j * np];
+      for (int m = 0; m < 4; ++m) {
+        const float4 q = src[m * np];
+        dst[4 * m] = q.x;
+        dst[4 * m + 1] = q.y;
+        dst[4 * m + 2] = q.z;
+        dst[4 * m + 3] = q.w;
+      }
     };
     {
       const bool on = cur.u < n_steps;
@@ -450,6 +471,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
         float* xc = xs + e0;
         float* yc = ys + e0;
         __nv_bfloat16* hc = xh_out + e0;
+        float4* qc = a.xq + quad0(it, c);
         uint32_t out[16];
         float xo[16], yo[16];
 #pragma unroll
@@ -460,17 +482,22 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
           const bool wall = fabsf(x1) > 1.f;
           xo[j] = wall ? copysignf(1.f, x1) : x1;
           yo[j] = wall ? 0.f : y1;
-          out[j] = vr ? __float_as_uint(yo[j] * inv) : 0u;
+          // padding vertices hold x = y = 0 and J rows of zeros: their y stays 0
+          out[j] = __float_as_uint(yo[j] * inv);
         }
         if (vr) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            xc[j * np] = xo[j];
-            hc[j * np] = __float2bfloat16_rn(xo[j]);
-          }
-          if (last) {
+          for (int j = 0; j < 16; ++j) hc[j * np] = __float2bfloat16_rn(xo[j]);
+          if (!last) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) yc[j * np] = yo[j];
+            for (int m = 0; m < 4; ++m)
+              qc[m * np] = make_float4(xo[4 * m], xo[4 * m + 1], xo[4 * m + 2], xo[4 * m + 3]);
+          } else {  // the launch's last step: state back into the solver's layout
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              xc[j * np] = xo[j];
+              yc[j * np] = yo[j];
+            }
           }
         }
         if (!last) {
@@ -501,8 +528,9 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
           // phase 0 of edone is the initial y store; step u completes phase u + 1
           if (!(ok = rwait(edone0 + 8 * i, (uint32_t)(u + 1) & 1u, a.err, abort_flag))) break;
           if (t == it.last_t) continue;  // nobody waits for X_hat beyond this launch
+          // the epilogue's stores happen-before this thread's edone acquire (mbarrier,
+          // CTA scope); the gpu-scope release below is cumulative over them
           fence_proxy_async_global();
-          __threadfence();
           red_release_gpu_add(
               a.done + (size_t)(a.group_sync ? it.block : it.rt) * a.n_kt + it.k, 1u);
         }
@@ -577,7 +605,8 @@ qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo,
   rb->work = (int2*)ctx->scratch(work.size() * sizeof(int2), S_RUN_WORK);
   rb->rows_b = (int32_t*)ctx->scratch(rows.size() * 4, S_RUN_ROWS);
   rb->done = (uint32_t*)ctx->scratch((size_t)rb->n_done * 4, S_RUN_DONE);
-  if (!rb->work || !rb->rows_b || !rb->done)
+  rb->xq = (float4*)ctx->scratch((size_t)R * g.n_pad * 4, S_RUN_XQ);
+  if (!rb->work || !rb->rows_b || !rb->done || !rb->xq)
     return set_err(ctx, QH_ENOMEM, "allocation failed (multi-step kernel)");
   QH_CUDA_TRY(cudaMemcpyAsync(rb->work, work.data(), work.size() * sizeof(int2),
                               cudaMemcpyHostToDevice, ctx->stream));
@@ -601,6 +630,7 @@ qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const Run
   a.tile_col = s.tile_col;
   a.x = s.x;
   a.y = s.y;
+  a.xq = rb.xq;
   a.xh0 = xh0;
   a.xh1 = xh1;
   a.c0 = s.c0;

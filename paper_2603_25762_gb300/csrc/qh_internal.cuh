@@ -259,11 +259,12 @@ qh_status tc_prepare(Ctx* ctx);
 //   6: J resident in smem, group hand-off   7: J streamed, tile hand-off
 //   8: J resident in smem, tile hand-off    9: J streamed, group hand-off
 constexpr int RUN_VARIANT_FIRST = 6;
-constexpr int S_RUN_WORK = 96, S_RUN_ROWS = 97, S_RUN_DONE = 98;  // scratch slots
+constexpr int S_RUN_WORK = 96, S_RUN_ROWS = 97, S_RUN_DONE = 98, S_RUN_XQ = 99;  // scratch slots
 struct RunBufs {
   int2* work = nullptr;       // [grid] {first item, item count}
   int32_t* rows_b = nullptr;  // [n_blocks] row tiles per block
   uint32_t* done = nullptr;   // release counters (per item or per block x replica tile)
+  float4* xq = nullptr;       // [R/4][n_pad] blocked working copy of x
   int grid = 0;
   int item_stride = 1;        // a CTA's items: first, first + stride, ...
   int64_t n_done = 0;
