@@ -555,64 +555,103 @@ bool run_variant(int v) { return v >= RUN_VARIANT_FIRST && v < RUN_VARIANT_FIRST
 static bool run_jres(int v) { return v == RUN_VARIANT_FIRST || v == RUN_VARIANT_FIRST + 2; }
 static bool run_group(int v) { return v == RUN_VARIANT_FIRST || v == RUN_VARIANT_FIRST + 3; }
 
-// Work split: items are numbered row-tile-major (item = row_tile * n_kt + k), and a
-// CTA processes its items in a fixed order every step.  The split puts the row-tile
-// neighbours of an item (item -+ n_kt, same k) at the same position in their CTAs, so
-// an item's inputs for step t+1 are finished a whole step period before it needs them.
-// JRES: every CTA takes up to MAX_ITEMS consecutive replica tiles of ONE row tile (its
-// J tiles stay resident), the same k ranges in every row.  Stream: CTA c of G =
-// min(n_sm, items) takes items c, c + G, c + 2G, ...  False when the split does not
-// fit one CTA per SM.
-bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, std::vector<int2>* work,
-              int* stride) {
+// Work split.  Items are numbered row-tile-major (item = row_tile * n_kt + k), and
+// the blocks' row tiles are contiguous, so a set of whole blocks is a range of items.
+// Blocks are packed into waves whose items fit on chip (at most MAX_ITEMS per SM); a
+// wave is one launch over the step range, and the waves run one after the other.
+// Within a wave a CTA processes its items in a fixed order every step, and the split
+// puts the row-tile neighbours of an item (item -+ n_kt, same k) at the same position
+// in their CTAs, so an item's inputs for step t+1 are finished a whole step period
+// before it needs them.  JRES: every CTA takes up to MAX_ITEMS consecutive replica
+// tiles of ONE row tile (its J tiles stay resident), the same k ranges in every row.
+// Stream: CTA c of the wave's G CTAs takes the wave's items c, c + G, c + 2G, ...
+// False when some block does not fit one wave.
+bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, RunPlan* plan) {
   if (!run_variant(variant)) return false;
   const bool jres = run_jres(variant);
-  if (R % RB != 0 || g.n_row_tiles == 0 || g.csr_mode) return false;
+  if (R % RB != 0 || g.n_row_tiles == 0 || g.csr_mode || n_sm < 1) return false;
   const int n_kt = R / RB;
-  const int64_t n_items = (int64_t)g.n_row_tiles * n_kt;
-  std::vector<int2> w;
-  if (jres) {
+  const int cpr = (n_kt + MAX_ITEMS - 1) / MAX_ITEMS;  // JRES: CTAs per row tile
+  if (jres)
     for (const RowTile& rt : g.h_rt)
       if ((use_lo ? rt.n_all : rt.n_hi) > JRES_TILES) return false;
-    const int cpr = (n_kt + MAX_ITEMS - 1) / MAX_ITEMS;
-    if ((int64_t)g.n_row_tiles * cpr > n_sm) return false;
-    for (int32_t r = 0; r < g.n_row_tiles; ++r)
-      for (int c = 0; c < cpr; ++c) {
-        const int b = (int)((int64_t)n_kt * c / cpr), e = (int)((int64_t)n_kt * (c + 1) / cpr);
-        w.push_back(make_int2(r * n_kt + b, e - b));
-      }
-  } else {
-    if (n_items > (int64_t)MAX_ITEMS * n_sm) return false;
-    const int64_t grid = std::min<int64_t>(n_sm, n_items);
-    for (int64_t c = 0; c < grid; ++c)
-      w.push_back(make_int2((int)c, (int)((n_items - c + grid - 1) / grid)));
+  // row-tile range of every block (blocks appear in order in the row-tile list)
+  std::vector<int32_t> first(std::max(g.n_blocks, 1), -1), count(std::max(g.n_blocks, 1), 0);
+  for (int32_t r = 0; r < g.n_row_tiles; ++r) {
+    const int32_t b = g.h_rt[r].block;
+    if (first[b] < 0) first[b] = r;
+    count[b] += 1;
   }
-  if (stride) *stride = jres ? 1 : (int)w.size();
-  if (work) *work = std::move(w);
+  // a block's load on one wave: CTAs (JRES) or items (stream)
+  const int64_t cap = jres ? n_sm : (int64_t)MAX_ITEMS * n_sm;
+  auto load = [&](int32_t b) -> int64_t { return (int64_t)count[b] * (jres ? cpr : n_kt); };
+  int64_t total = 0;
+  for (int32_t b = 0; b < g.n_blocks; ++b) {
+    if (load(b) > cap) return false;
+    total += load(b);
+  }
+  const int64_t n_waves = (total + cap - 1) / cap;
+  const int64_t target = (total + n_waves - 1) / n_waves;
+  RunPlan p;
+  auto emit = [&](int32_t r0, int32_t r1) {
+    RunWave w;
+    w.work_off = (int)p.work.size();
+    if (jres) {
+      for (int32_t r = r0; r < r1; ++r)
+        for (int c = 0; c < cpr; ++c) {
+          const int b = (int)((int64_t)n_kt * c / cpr), e = (int)((int64_t)n_kt * (c + 1) / cpr);
+          p.work.push_back(make_int2(r * n_kt + b, e - b));
+        }
+      w.stride = 1;
+    } else {
+      const int64_t i0 = (int64_t)r0 * n_kt, n = (int64_t)(r1 - r0) * n_kt;
+      const int64_t grid = std::min<int64_t>(n_sm, n);
+      for (int64_t c = 0; c < grid; ++c)
+        p.work.push_back(make_int2((int)(i0 + c), (int)((n - c + grid - 1) / grid)));
+      w.stride = (int)grid;
+    }
+    w.grid = (int)p.work.size() - w.work_off;
+    p.waves.push_back(w);
+  };
+  int32_t r0 = -1, r1 = -1;
+  int64_t cur = 0;
+  for (int32_t b = 0; b < g.n_blocks; ++b) {
+    if (count[b] == 0) continue;
+    if (r0 >= 0 && cur + load(b) > target) {  // target <= cap
+      emit(r0, r1);
+      r0 = -1;
+      cur = 0;
+    }
+    if (r0 < 0) r0 = first[b];
+    r1 = first[b] + count[b];
+    cur += load(b);
+  }
+  if (r0 >= 0) emit(r0, r1);
+  if (plan) *plan = std::move(p);
   return true;
 }
 
 qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo, RunBufs* rb) {
-  std::vector<int2> work;
-  if (!run_plan(g, R, ctx->n_sm, variant, use_lo, &work, &rb->item_stride))
-    return set_err(ctx, QH_EINVAL, "multi-step kernel: split does not fit one CTA per SM");
+  RunPlan plan;
+  if (!run_plan(g, R, ctx->n_sm, variant, use_lo, &plan))
+    return set_err(ctx, QH_EINVAL, "multi-step kernel: a block does not fit one wave");
   const int n_kt = R / RB;
   rb->jres = run_jres(variant);
   rb->group_sync = run_group(variant);
+  rb->waves = plan.waves;
   std::vector<int32_t> rows(std::max(g.n_blocks, 1), 0);
   for (const RowTile& rt : g.h_rt) rows[rt.block] += 1;
   rb->n_done = (int64_t)(rb->group_sync ? (int64_t)rows.size() : g.n_row_tiles) * n_kt;
-  rb->work = (int2*)ctx->scratch(work.size() * sizeof(int2), S_RUN_WORK);
+  rb->work = (int2*)ctx->scratch(plan.work.size() * sizeof(int2), S_RUN_WORK);
   rb->rows_b = (int32_t*)ctx->scratch(rows.size() * 4, S_RUN_ROWS);
   rb->done = (uint32_t*)ctx->scratch((size_t)rb->n_done * 4, S_RUN_DONE);
   rb->xq = (float4*)ctx->scratch((size_t)R * g.n_pad * 4, S_RUN_XQ);
   if (!rb->work || !rb->rows_b || !rb->done || !rb->xq)
     return set_err(ctx, QH_ENOMEM, "allocation failed (multi-step kernel)");
-  QH_CUDA_TRY(cudaMemcpyAsync(rb->work, work.data(), work.size() * sizeof(int2),
+  QH_CUDA_TRY(cudaMemcpyAsync(rb->work, plan.work.data(), plan.work.size() * sizeof(int2),
                               cudaMemcpyHostToDevice, ctx->stream));
   QH_CUDA_TRY(cudaMemcpyAsync(rb->rows_b, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice,
                               ctx->stream));
-  rb->grid = (int)work.size();
   return QH_OK;
 }
 
@@ -638,7 +677,6 @@ qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const Run
   a.steps_b = s.steps_b;
   a.done = rb.done;
   a.work = rb.work;
-  a.item_stride = rb.item_stride;
   a.rows_b = rb.rows_b;
   a.group_sync = rb.group_sync ? 1 : 0;
   a.n_pad = s.n_pad;
@@ -650,20 +688,25 @@ qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const Run
   a.dta0 = s.dta0;
   a.a0 = s.a0;
   a.err = s.err;
+  // every wave's counters start from zero; waves use disjoint counters
   QH_CUDA_TRY(cudaMemsetAsync(rb.done, 0, (size_t)rb.n_done * 4, ctx->stream));
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)rb.grid);
-  cfg.blockDim = dim3(RUN_THREADS);
-  cfg.dynamicSmemBytes = L::BYTES;
-  cfg.stream = ctx->stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs resident: the waits always end
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  note_launch(1);
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_bsb_run<JRES>, mJ, mX0, mX1, a);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_bsb_run launch");
+  for (const RunWave& w : rb.waves) {
+    a.work = rb.work + w.work_off;
+    a.item_stride = w.stride;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)w.grid);
+    cfg.blockDim = dim3(RUN_THREADS);
+    cfg.dynamicSmemBytes = L::BYTES;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs resident: the waits always end
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    note_launch(1);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_bsb_run<JRES>, mJ, mX0, mX1, a);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_bsb_run launch");
+  }
   return QH_OK;
 }
 

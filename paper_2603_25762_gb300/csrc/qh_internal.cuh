@@ -260,20 +260,27 @@ qh_status tc_prepare(Ctx* ctx);
 //   8: J resident in smem, tile hand-off    9: J streamed, group hand-off
 constexpr int RUN_VARIANT_FIRST = 6;
 constexpr int S_RUN_WORK = 96, S_RUN_ROWS = 97, S_RUN_DONE = 98, S_RUN_XQ = 99;  // scratch slots
+struct RunWave {              // one launch: whole blocks whose items fit on chip
+  int work_off = 0;           // first entry of the wave in RunBufs::work
+  int grid = 0;               // CTAs
+  int stride = 1;             // a CTA's items: first, first + stride, ...
+};
+struct RunPlan {
+  std::vector<int2> work;     // per CTA of every wave: {first item, item count}
+  std::vector<RunWave> waves;
+};
 struct RunBufs {
-  int2* work = nullptr;       // [grid] {first item, item count}
+  int2* work = nullptr;       // device copy of RunPlan::work
   int32_t* rows_b = nullptr;  // [n_blocks] row tiles per block
   uint32_t* done = nullptr;   // release counters (per item or per block x replica tile)
   float4* xq = nullptr;       // [R/4][n_pad] blocked working copy of x
-  int grid = 0;
-  int item_stride = 1;        // a CTA's items: first, first + stride, ...
+  std::vector<RunWave> waves;
   int64_t n_done = 0;
   bool jres = false;
   bool group_sync = false;
 };
 bool run_variant(int v);
-bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, std::vector<int2>* work,
-              int* stride = nullptr);
+bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, RunPlan* plan);
 qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo, RunBufs* rb);
 // Steps t0 .. t1-1 in one launch.  X_hat_t is read from xh0 (t even) or xh1 (t odd);
 // x, y of `s` are updated in place.

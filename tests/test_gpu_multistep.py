@@ -167,3 +167,58 @@ def test_multistep_rejects_unfit_cases(q, ctx):
     with pytest.raises(RuntimeError):  # dt * c0 = 0 cannot hold y / (dt c0)
         ctx.debug_steps(g, q.PREC_BF16, 128, x, y, 0, 2, 10, c0=np.zeros_like(c0),
                         step_kernel=MULTI[1])
+
+
+def _wave_case(q, ctx, oracle, kernel, check_blocks):
+    import torch
+    # 40 blocks of 300-800 reads at R = 512: about 680 items, more than one wave holds
+    fr = synth.batched_blocks(1007, n_blocks=40, n_min=300, n_max=800)
+    g = ctx.build_graph(fr, mode=q.MODE_READ)
+    og = oracle.read_graph(fr, oracle.READ_SIGNED)
+    blocks = oracle.blocks_of(og)
+    n_pad, pidx, c0 = g.layout()
+    R, t0, nsteps, steps = 512, 30, 3, 200
+    rng = np.random.default_rng(9)
+    x = np.zeros((R, n_pad), np.float32)
+    y = np.zeros((R, n_pad), np.float32)
+    for nodes in blocks:
+        x[:, pidx[nodes]] = rng.uniform(-0.1, 0.1, (R, len(nodes)))
+        y[:, pidx[nodes]] = rng.uniform(-0.1, 0.1, (R, len(nodes)))
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    ctx.debug_steps(g, q.PREC_BF16, R, xd, yd, t0, nsteps, steps, c0=c0, step_kernel=kernel)
+    xg, yg = xd.cpu().numpy().astype(np.float64), yd.cpu().numpy().astype(np.float64)
+    for b in check_blocks:
+        nodes = blocks[b]
+        x1, y1 = oracle.bsb_run(og.subgraph(nodes), x[:, pidx[nodes]].astype(np.float64),
+                                y[:, pidx[nodes]].astype(np.float64), t0, t0 + nsteps, steps,
+                                c0=float(c0[b]))
+        xgb, ygb = xg[:, pidx[nodes]], yg[:, pidx[nodes]]
+        free = (np.abs(xgb) < 1.0) & (np.abs(x1) < 1.0)
+        assert (~free & (np.abs(xgb) != np.abs(x1))).mean() <= 0.01
+        x0 = x[:, pidx[nodes]]
+        assert _rel_frob((xgb - x0)[free], (x1 - x0)[free]) <= 1e-2
+        assert _rel_frob(ygb[free], y1[free]) <= 1e-2
+    return g, blocks
+
+
+@pytest.mark.parametrize("kernel", MULTI)
+def test_multistep_several_waves(q, ctx, oracle, kernel):
+    g, blocks = _wave_case(q, ctx, oracle, kernel, [0, 1, 19, 20, 38, 39])
+    assert sum(-(-len(b) // 128) for b in blocks) * 4 > 4 * 152  # more than one wave
+
+
+def test_multistep_several_waves_solve(q, ctx, oracle):
+    fr = synth.batched_blocks(1007, n_blocks=40, n_min=300, n_max=800)
+    g = ctx.build_graph(fr, mode=q.MODE_READ)
+    sol = ctx.solve(g, replicas=512, steps=400, precision=q.PREC_BF16, seed=4,
+                    step_kernel="multistep-stream-group")
+    og = oracle.read_graph(fr, oracle.READ_SIGNED)
+    blocks = oracle.blocks_of(og)
+    spins = sol.spins(g.n_nodes)
+    for b in [0, 13, 27, 39]:
+        nodes = blocks[b]
+        sub = og.subgraph(nodes)
+        info = sol.block(b, len(nodes))
+        assert info["best_cut"] == oracle.cut(sub, spins[nodes])
+        best, _, _, _ = oracle.bsb_solve(sub, list(range(8)), 400, 4, b)
+        assert info["best_cut"] >= 0.999 * best, (b, info["best_cut"], best)
