@@ -175,8 +175,11 @@ def _profiled_traffic(kernel):
     """DRAM bytes per launch from the committed ncu summary, or None once the kernel
     (its variant or its source file) differs from the one that was profiled."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "step_kernel_hifi_region.md")
-    src = os.path.join(ROOT, "paper_2603_25762_gb300", "csrc", "bsb_tc.cu")
+    multistep = kernel.startswith("multistep")
+    path = os.path.join(ROOT, "profiles", "multistep_kernel_hifi_region.md" if multistep
+                        else "step_kernel_hifi_region.md")
+    src = os.path.join(ROOT, "paper_2603_25762_gb300", "csrc",
+                       "bsb_run.cu" if multistep else "bsb_tc.cu")
     if not os.path.exists(path):
         return None
     fields = {}
@@ -281,6 +284,10 @@ def run_ours(args):
         stats["blocks"] = g.n_blocks
         stats["units"] = sol.timing()["spin_updates"]
         stats["nnz"] = g.nnz
+        bs = g.block_sizes()
+        its = [sol.block(b)["iterations"] for b in range(g.n_blocks)]
+        stats["spins"] = float(sum(bs)) * R  # spin states updated per step
+        stats["spin_solves"] = float(sum(n * i for n, i in zip(bs, its))) * R
         sol.free()
         g.free()
         return h, cut
@@ -334,18 +341,19 @@ def run_ours(args):
         return
     hbm, bf16_tf, src = _peaks()
     launch_us = statistics.mean(step_ms) * 1e3
-    # state traffic per spin update + each stored J nonzero read once per step (BF16: 2 B,
-    # FP32: 4 B)
+    # algorithmic bytes of the whole step loop: state traffic per spin update + each
+    # stored J nonzero read once per step (BF16: 2 B, FP32: 4 B); a multi-step launch
+    # also reads and writes y once (8 B per spin).  Divided by the step loop's time.
     n_launch = max(1, stats["timing"]["n_step_launches"])
     jb = stats["nnz"] * (4 if prec == qhap.PREC_FP32 else 2)
-    upd = units / n_launch  # spin updates per launch
+    steps_total = units / max(1, stats["spins"])  # steps run, summed over refinements
     if stats["timing"]["kernel"].startswith("multistep"):
-        steps_per_launch = T
-        per_launch_bytes = upd * SPIN_BYTES_MULTISTEP + 8 * upd / T + jb * steps_per_launch
+        loop_bytes = units * SPIN_BYTES_MULTISTEP + 8 * stats["spin_solves"] + jb * steps_total
     else:
-        steps_per_launch = 1
-        per_launch_bytes = upd * SPIN_BYTES + jb
-    achieved = per_launch_bytes / (launch_us * 1e-6) / 1e9
+        loop_bytes = units * SPIN_BYTES + jb * steps_total
+    loop_us = statistics.mean(step_ms) * 1e3 * n_launch
+    achieved = loop_bytes / (loop_us * 1e-6) / 1e9
+    per_launch_bytes = loop_bytes / n_launch
     traffic = _profiled_traffic(stats["timing"]["kernel"]) if args.workload == "hifi-region" else None
     h2d = sum(int(a.nbytes) for a in pinned_np[1:])
     d2h = fr.n_snps * (1 + 1 + 4) + 8
@@ -362,8 +370,8 @@ def run_ours(args):
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
                      "peak_source": src, "avg_launch_us": launch_us,
-                     "steps_per_launch": steps_per_launch,
-                     "avg_step_us": launch_us / steps_per_launch,
+                     "launches_per_step": n_launch,
+                     "avg_step_us": loop_us / steps_total,
                      "algorithmic_bytes_per_launch": per_launch_bytes},
         "gpu_launches": n_launched,
         "gpu_launches_trace_per_step": n_kern,

@@ -21,15 +21,30 @@ qh_status cuda_fail(Ctx* ctx, cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? QH_ENOMEM : QH_ECUDA;
 }
 
-void* dalloc(Graph& g, size_t bytes) {
+void* pool_alloc(const PoolRef& m, size_t bytes, std::vector<void*>* owner) {
   void* p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+  cudaError_t e = m.pool ? cudaMallocFromPoolAsync(&p, bytes, m.pool, m.stream)
+                         : cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
     (void)cudaGetLastError();
     return nullptr;
   }
-  g.allocs.push_back(p);
+  owner->push_back(p);
   return p;
 }
+
+void pool_free_all(const PoolRef& m, std::vector<void*>* owned) {
+  const bool ordered = m.pool && m.alive && *m.alive;
+  for (void* p : *owned) {
+    if (ordered)
+      cudaFreeAsync(p, m.stream);  // after the work already queued on the stream
+    else
+      cudaFree(p);  // the context is gone: release synchronously
+  }
+  owned->clear();
+}
+
+void* dalloc(Graph& g, size_t bytes) { return pool_alloc(g.mem, bytes, &g.allocs); }
 
 void* Ctx::scratch(size_t bytes, int slot) {
   if (slot >= (int)slots.size()) {
@@ -265,6 +280,21 @@ qh_status qh_create(qh_ctx** out, int device, void* stream) {
     }
     ctx->own_stream = true;
   }
+  {  // stream-ordered pool for graph and solution memory; keeps what it has reserved
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&ctx->mem.pool, &props) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(ctx->mem.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      (void)cudaGetLastError();
+      ctx->mem.pool = nullptr;  // plain cudaMalloc / cudaFree
+    }
+    ctx->mem.stream = ctx->stream;
+    ctx->mem.alive = std::make_shared<bool>(true);
+  }
   if (cudaMalloc(&ctx->d_err, sizeof(int32_t)) != cudaSuccess ||
       cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), ctx->stream) != cudaSuccess) {
     delete h;
@@ -291,15 +321,17 @@ void qh_destroy(qh_ctx* h) {
   if (ctx->d_err) cudaFree(ctx->d_err);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  if (ctx->mem.alive) *ctx->mem.alive = false;  // graphs and solutions left behind free synchronously
+  if (ctx->mem.pool) cudaMemPoolDestroy(ctx->mem.pool);  // released once they are freed
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete h;
 }
 
 void qh_graph_free(qh_graph* g) {
   if (!g) return;
-  // cudaFree waits for work in flight on the device; the owning context may already
-  // be gone, so nothing of it is touched here
-  for (void* p : g->g.allocs) cudaFree(p);
+  // the owning context may already be gone: only the graph's own pool reference
+  // (which knows whether it is) is used here
+  pool_free_all(g->g.mem, &g->g.allocs);
   delete g;
 }
 
@@ -324,6 +356,7 @@ qh_status qh_build_graph(qh_ctx* h, const qh_fragments* f, const qh_graph_opts* 
   qh_graph* gh = new (std::nothrow) qh_graph;
   if (!gh) return QH_ENOMEM;
   gh->owner = h;
+  gh->g.mem = ctx->mem;
   qh_status st = build_graph_device(ctx, f, o, &gh->g);
   if (st != QH_OK) {
     cudaStreamSynchronize(ctx->stream);
@@ -752,7 +785,9 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
     step_ms_total += ms;
-    launches += multistep ? (early ? (max_steps + o->check_every - 1) / o->check_every : 1) : max_steps;
+    launches += multistep ? (int64_t)rb.waves.size() *
+                                (early ? (max_steps + o->check_every - 1) / o->check_every : 1)
+                          : max_steps;
     for (int32_t b = 0; b < nb; ++b)
       if (h_active[b]) {
         spin_updates += (double)G.h_block_size[b] * R * h_steps_run[b];
@@ -822,20 +857,13 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   // device copies of the spins / counts for qh_phase
   sol.d_spins = (int8_t*)nullptr;
   {
-    void* p = nullptr;
-    if (cudaMalloc(&p, std::max(G.n_nodes, 1)) != cudaSuccess) {
-      delete sh;
+    sol.mem = ctx->mem;
+    sol.d_spins = (int8_t*)pool_alloc(sol.mem, std::max(G.n_nodes, 1), &sol.allocs);
+    sol.d_C = (int32_t*)pool_alloc(sol.mem, (size_t)std::max(G.n_nodes, 1) * 4, &sol.allocs);
+    if (!sol.d_spins || !sol.d_C) {
+      qh_solution_free(sh);
       return set_err(ctx, QH_ENOMEM, "allocation failed (solution)");
     }
-    sol.allocs.push_back(p);
-    sol.d_spins = (int8_t*)p;
-    if (cudaMalloc(&p, std::max(G.n_nodes, 1) * 4) != cudaSuccess) {
-      cudaFree(sol.d_spins);
-      delete sh;
-      return set_err(ctx, QH_ENOMEM, "allocation failed (solution)");
-    }
-    sol.allocs.push_back(p);
-    sol.d_C = (int32_t*)p;
     if (G.n_nodes) {
       QH_CUDA_TRY(cudaMemcpyAsync(sol.d_spins, sol.spins.data(), G.n_nodes, cudaMemcpyHostToDevice, s));
       QH_CUDA_TRY(cudaMemcpyAsync(sol.d_C, B.C, G.n_nodes * 4, cudaMemcpyDeviceToDevice, s));
@@ -907,7 +935,7 @@ const char* qh_tuning_report(const qh_ctx* h) { return h ? h->c.tune_report.c_st
 
 void qh_solution_free(qh_solution* sh) {
   if (!sh) return;
-  for (void* p : sh->s.allocs) cudaFree(p);
+  pool_free_all(sh->s.mem, &sh->s.allocs);
   delete sh;
 }
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -45,6 +46,17 @@ struct RowTile {           // one 128-row slab of a block in the padded layout
   int32_t f32_begin;       // first FP32 tile of this row tile
   int32_t pad_;
 };
+
+// Device memory of graphs and solutions comes from the owning context's stream-ordered
+// pool: allocation and release need no device synchronisation.  A handle may outlive
+// its context; `alive` tells whether the context (its stream and pool) still exists.
+struct PoolRef {
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t stream = nullptr;
+  std::shared_ptr<bool> alive;
+};
+void* pool_alloc(const PoolRef& m, size_t bytes, std::vector<void*>* owner);
+void pool_free_all(const PoolRef& m, std::vector<void*>* owned);
 
 struct Graph {
   int mode = 0, weight_mode = 1, linkage_k = 10;
@@ -108,6 +120,7 @@ struct Graph {
   std::vector<double> h_sum_w;
   // all device allocations of this graph, freed together
   std::vector<void*> allocs;
+  PoolRef mem;
 };
 
 struct Solution {
@@ -127,12 +140,14 @@ struct Solution {
   int8_t* d_spins = nullptr;             // device [n_nodes]
   int32_t* d_C = nullptr;                // device [n_nodes]
   std::vector<void*> allocs;
+  PoolRef mem;
 };
 
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  PoolRef mem;  // pool for graph and solution memory (on this context's stream)
   int n_sm = 148;
   std::string err;
   int32_t* d_err = nullptr;
