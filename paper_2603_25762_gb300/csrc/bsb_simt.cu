@@ -308,11 +308,10 @@ __global__ void k_signs_t(const float* __restrict__ x, int32_t n_pad, int32_t R,
   }
 }
 
-// Warp per vertex a: node_val[pad(a)][r] = s_a * sum_b w_ab s_b.  Lane l owns `per`
-// consecutive replicas (a multiple of 4, at most 32, sized so the warp spans R), so one
-// pass over the vertex's edges covers up to 1,024 replicas with 4-byte sign loads.
-// Integer weights accumulate in int32 (row sums stay far below 2^31), real in FP64.
-template <bool INT>
+// Warp per vertex a: node_val[pad(a)][r] = s_a * sum_b w_ab s_b, integer weights in
+// int32 (row sums stay far below 2^31).  Lane l owns `per` consecutive replicas (a
+// multiple of 4, at most 32, sized so the warp spans R), so one pass over the vertex's
+// edges covers up to 1,024 replicas with 4-byte sign loads.
 __global__ void k_cut_nodes(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                             const double* __restrict__ w, const int32_t* __restrict__ block_of,
                             const int32_t* __restrict__ pad_index, const int8_t* __restrict__ st,
@@ -326,40 +325,32 @@ __global__ void k_cut_nodes(int32_t n, const int64_t* __restrict__ rp, const int
   const int32_t pa = pad_index[a];
   const int64_t e0 = rp[a], e1 = rp[a + 1];
   const bool vec = (R & 3) == 0;
-  using Acc = typename std::conditional<INT, int32_t, double>::type;
   for (int32_t r0 = 0; r0 < R; r0 += 32 * per) {
     const int32_t r = r0 + per * lane;
     const int nr = max(0, min(per, R - r));
-    Acc acc[32];
+    int32_t acc[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) acc[k] = 0;
     if (nr > 0) {
       for (int64_t e = e0; e < e1; ++e) {
         const double we = w[e];
         if (we == 0.0) continue;  // zero edges may reach vertices outside every block
+        const int32_t wi = (int32_t)we;
         const int8_t* sb = st + (size_t)pad_index[col[e]] * R + r;
         if (vec && nr == per) {
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             if (4 * q >= per) break;
             char4 c = *reinterpret_cast<const char4*>(sb + 4 * q);
-            if (INT) {
-              const int32_t wi = (int32_t)we;
-              acc[4 * q + 0] += wi * c.x;
-              acc[4 * q + 1] += wi * c.y;
-              acc[4 * q + 2] += wi * c.z;
-              acc[4 * q + 3] += wi * c.w;
-            } else {
-              acc[4 * q + 0] += we * (double)c.x;
-              acc[4 * q + 1] += we * (double)c.y;
-              acc[4 * q + 2] += we * (double)c.z;
-              acc[4 * q + 3] += we * (double)c.w;
-            }
+            acc[4 * q + 0] += wi * c.x;
+            acc[4 * q + 1] += wi * c.y;
+            acc[4 * q + 2] += wi * c.z;
+            acc[4 * q + 3] += wi * c.w;
           }
         } else {
 #pragma unroll
           for (int k = 0; k < 32; ++k)
-            if (k < nr) acc[k] += (Acc)(INT ? (double)(int32_t)we * sb[k] : we * (double)sb[k]);
+            if (k < nr) acc[k] += wi * sb[k];
         }
       }
     }
@@ -367,6 +358,107 @@ __global__ void k_cut_nodes(int32_t n, const int64_t* __restrict__ rp, const int
 #pragma unroll
     for (int k = 0; k < 32; ++k)
       if (k < nr) node_val[(size_t)pa * R + r + k] = (double)sa[k] * (double)acc[k];
+  }
+}
+
+// Real weights, at most 4 replicas (the final parity cut): FP64, the lanes of the
+// vertex's warp stride over its edges and the partial sums are combined in a fixed
+// shuffle order, so the result does not depend on scheduling.
+__global__ void k_cut_nodes_few(int32_t n, const int64_t* __restrict__ rp,
+                                const int32_t* __restrict__ col, const double* __restrict__ w,
+                                const int32_t* __restrict__ block_of,
+                                const int32_t* __restrict__ pad_index,
+                                const int8_t* __restrict__ st, int32_t R, double* node_val,
+                                const int32_t* __restrict__ active) {
+  int32_t a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (a >= n) return;
+  int32_t b = block_of[a];
+  if (b < 0 || (active != nullptr && !active[b])) return;
+  const int32_t pa = pad_index[a];
+  const int64_t e0 = rp[a], e1 = rp[a + 1];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t e = e0 + lane; e < e1; e += 32) {
+    const double we = w[e];
+    if (we == 0.0) continue;  // zero edges may reach vertices outside every block
+    const int8_t* sb = st + (size_t)pad_index[col[e]] * R;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < R) acc[k] += sb[k] > 0 ? we : -we;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+  if (lane < R) {
+    double v = acc[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+      if (lane == k) v = acc[k];
+    node_val[(size_t)pa * R + lane] = (double)st[(size_t)pa * R + lane] * v;
+  }
+}
+
+// Real weights over many replicas: the same per-vertex sums, accumulated in FP32 with
+// compensation.  Each weight is split into FP32 hi + lo parts, and each running sum
+// is kept as an unevaluated pair (hi, lo) updated with the exact rounding error of the
+// hi addition (Knuth's TwoSum), which carries about 48 bits: within ~1e-11 of the FP64
+// sum even over thousands of edges, at FP32 speed (this part's FP64 rate is a small
+// fraction of its FP32 rate).  Signs are +-1, so the terms are exact negations.
+__global__ void k_cut_nodes_df(int32_t n, const int64_t* __restrict__ rp,
+                               const int32_t* __restrict__ col, const double* __restrict__ w,
+                               const int32_t* __restrict__ block_of,
+                               const int32_t* __restrict__ pad_index, const int8_t* __restrict__ st,
+                               int32_t R, int32_t per, double* node_val,
+                               const int32_t* __restrict__ active) {
+  int32_t a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (a >= n) return;
+  int32_t b = block_of[a];
+  if (b < 0 || (active != nullptr && !active[b])) return;
+  const int32_t pa = pad_index[a];
+  const int64_t e0 = rp[a], e1 = rp[a + 1];
+  const bool vec = (R & 3) == 0;
+  for (int32_t r0 = 0; r0 < R; r0 += 32 * per) {
+    const int32_t r = r0 + per * lane;
+    const int nr = max(0, min(per, R - r));
+    float hi[32], lo[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) hi[k] = lo[k] = 0.f;
+    auto add = [&](int k, int sg, float wh, float wl) {
+      const float th = sg > 0 ? wh : -wh, tl = sg > 0 ? wl : -wl;
+      const float s = __fadd_rn(hi[k], th);
+      const float bp = __fsub_rn(s, hi[k]);
+      const float err = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(s, bp)), __fsub_rn(th, bp));
+      hi[k] = s;
+      lo[k] = __fadd_rn(lo[k], __fadd_rn(err, tl));
+    };
+    if (nr > 0) {
+      for (int64_t e = e0; e < e1; ++e) {
+        const double we = w[e];
+        if (we == 0.0) continue;  // zero edges may reach vertices outside every block
+        const float wh = (float)we, wl = (float)(we - (double)wh);
+        const int8_t* sb = st + (size_t)pad_index[col[e]] * R + r;
+        if (vec && nr == per) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (4 * q >= per) break;
+            const char4 c = *reinterpret_cast<const char4*>(sb + 4 * q);
+            add(4 * q + 0, c.x, wh, wl);
+            add(4 * q + 1, c.y, wh, wl);
+            add(4 * q + 2, c.z, wh, wl);
+            add(4 * q + 3, c.w, wh, wl);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 32; ++k)
+            if (k < nr) add(k, sb[k], wh, wl);
+        }
+      }
+    }
+    const int8_t* sa = st + (size_t)pa * R + r;
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      if (k < nr) node_val[(size_t)pa * R + r + k] = (double)sa[k] * ((double)hi[k] + (double)lo[k]);
   }
 }
 
@@ -505,21 +597,34 @@ __global__ void k_block_sums(int32_t nb, const int64_t* __restrict__ block_ptr,
 // Per active block: stop if the best cut is <= 0 or all spins agree; otherwise
 // add 1 to C on the smaller subset (tie: the subset without the block's lowest
 // vertex).  Thread per block, vertices in ascending order.
-__global__ void k_refine_prepare(int32_t nb, const int64_t* __restrict__ block_ptr,
+__global__ void __launch_bounds__(256) k_refine_prepare(int32_t nb, const int64_t* __restrict__ block_ptr,
                                  const int32_t* __restrict__ perm, const int8_t* __restrict__ spins,
                                  const double* __restrict__ best_cut, int32_t* active, int32_t* C) {
-  int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb || !active[b]) return;
-  int64_t k0 = block_ptr[b], k1 = block_ptr[b + 1];
+  // CTA per block: count the +1 side, then flag the smaller side in parallel
+  __shared__ int64_t part[256];
+  __shared__ int32_t go;
+  const int32_t b = blockIdx.x;
+  if (b >= nb || !active[b]) return;  // CTA-uniform
+  const int64_t k0 = block_ptr[b], k1 = block_ptr[b + 1];
   int64_t npos = 0;
-  for (int64_t k = k0; k < k1; ++k) npos += spins[perm[k]] > 0;
-  int64_t sz = k1 - k0;
-  if (best_cut[b] <= 0.0 || npos == 0 || npos == sz) {
-    active[b] = 0;
-    return;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) npos += spins[perm[k]] > 0;
+  part[threadIdx.x] = npos;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) part[threadIdx.x] += part[threadIdx.x + off];
+    __syncthreads();
   }
-  int8_t small = (2 * npos < sz) ? 1 : (2 * npos > sz) ? -1 : (int8_t)(-spins[perm[k0]]);
-  for (int64_t k = k0; k < k1; ++k)
+  npos = part[0];
+  const int64_t sz = k1 - k0;
+  if (threadIdx.x == 0) {
+    go = !(best_cut[b] <= 0.0 || npos == 0 || npos == sz);
+    if (!go) active[b] = 0;
+  }
+  __syncthreads();
+  if (!go) return;
+  // the smaller subset; on a tie, the subset that does not hold the lowest vertex
+  const int8_t small = (2 * npos < sz) ? 1 : (2 * npos > sz) ? -1 : (int8_t)(-spins[perm[k0]]);
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x)
     if (spins[perm[k]] == small) C[perm[k]] += 1;
 }
 
@@ -659,11 +764,16 @@ void launch_cut(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t
   // replicas per lane: a multiple of 4 in [4, 32] so that one warp pass spans R
   int32_t per = (((R + 31) / 32) + 3) / 4 * 4;
   per = per < 4 ? 4 : (per > 32 ? 32 : per);
+  // integer weights: exact int32; real weights: FP64 for a few replicas (the final
+  // parity cut), compensated FP32 for the many-replica pick
   if (g.integer_weights)
-    k_cut_nodes<true><<<::qh::counted(nblk((int64_t)g.n_nodes * 32)), 256, 0, s>>>(
+    k_cut_nodes<<<::qh::counted(nblk((int64_t)g.n_nodes * 32)), 256, 0, s>>>(
         g.n_nodes, g.row_ptr, g.col, w, g.block_of, g.pad_index, signs_t, R, per, node_val, active);
+  else if (R <= 4)
+    k_cut_nodes_few<<<::qh::counted(nblk((int64_t)g.n_nodes * 32)), 256, 0, s>>>(
+        g.n_nodes, g.row_ptr, g.col, w, g.block_of, g.pad_index, signs_t, R, node_val, active);
   else
-    k_cut_nodes<false><<<::qh::counted(nblk((int64_t)g.n_nodes * 32)), 256, 0, s>>>(
+    k_cut_nodes_df<<<::qh::counted(nblk((int64_t)g.n_nodes * 32)), 256, 0, s>>>(
         g.n_nodes, g.row_ptr, g.col, w, g.block_of, g.pad_index, signs_t, R, per, node_val, active);
   dim3 grid((R + 31) / 32, g.n_blocks);
   k_cut_reduce<<<::qh::counted(grid), 1024, 0, s>>>(g.n_blocks, g.pad_off, g.block_ptr, R, node_val, sum_w, cuts,
@@ -702,8 +812,8 @@ void launch_block_sums(cudaStream_t s, const Graph& g, const double* w, double* 
 void launch_refine_prepare(cudaStream_t s, const Graph& g, const int8_t* spins,
                            const double* best_cut, int32_t* active, int32_t* C) {
   if (g.n_blocks > 0)
-    k_refine_prepare<<<::qh::counted(nblk(g.n_blocks, 64)), 64, 0, s>>>(g.n_blocks, g.block_ptr, g.perm, spins,
-                                                        best_cut, active, C);
+    k_refine_prepare<<<::qh::counted((unsigned)g.n_blocks), 256, 0, s>>>(g.n_blocks, g.block_ptr, g.perm,
+                                                                         spins, best_cut, active, C);
 }
 
 void launch_gauge(cudaStream_t s, const Graph& g, const int8_t* spins, double* w,

@@ -499,3 +499,24 @@ def test_full_size_hifi_region(q, ctx, oracle):
         sub = og.subgraph(nodes)
         info = sol.block(b)
         assert info["best_cut"] == oracle.cut(sub, spins[nodes])
+
+
+def test_real_weight_cuts_match_fp64(q, ctx, oracle):
+    # SNP weights are real: the many-replica pick sums them in compensated FP32, the
+    # reported cut is the FP64 cut of the partition.  With one refinement iteration the
+    # partition is the picked replica's spins, so the two must agree to ~1e-11.
+    fr = synth.ont_region(1003, scale=0.04)
+    g = ctx.build_graph(fr, mode=q.MODE_SNP)
+    sol = ctx.solve(g, replicas=128, steps=300, precision=q.PREC_BF16, seed=6, refine_max=1)
+    og = oracle.snp_graph(fr)
+    spins = sol.spins(g.n_nodes)
+    c = sol.cuts()
+    for b, nodes in enumerate(oracle.blocks_of(og)):
+        info = sol.block(b, len(nodes))
+        exact = oracle.cut(og.subgraph(nodes), spins[nodes])
+        assert info["best_cut"] == pytest.approx(exact, rel=1e-12, abs=1e-9)
+        picked = c[b][info["best_replica"]]
+        assert picked == c[b].max()
+        if picked <= 0:  # the refinement test stops before flipping: no partition
+            continue
+        assert picked == pytest.approx(exact, rel=1e-10, abs=1e-8)
