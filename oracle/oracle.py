@@ -77,6 +77,10 @@ def _setup(L):
     L.qo_ising_energy.argtypes = [I32, P, P, P, P]
     L.qo_bsb_solve.restype = D
     L.qo_bsb_solve.argtypes = [I32, P, P, P, I32, P, I32, D, D, D, U64, I64, I32, P, P, P]
+    L.qo_sb_run.restype = None
+    L.qo_sb_run.argtypes = [I32, P, P, P, I32, P, P, I32, I32, I32, D, D, D, I32]
+    L.qo_sb_solve.restype = D
+    L.qo_sb_solve.argtypes = [I32, P, P, P, I32, P, I32, D, D, D, U64, I64, I32, P, P, P, I32]
     L.qo_refine.restype = I32
     L.qo_refine.argtypes = [I32, P, P, P, I32, P, I32, D, D, D, U64, I64, I32, P, P]
     L.qo_vote.restype = None
@@ -219,15 +223,22 @@ def bsb_init(n, replica_ids, seed, block, it=0):
     return x, y
 
 
-def bsb_run(g: CSR, x, y, t0, t1, steps, dt=1.0, a0=1.0, c0=None):
-    """Advance x, y ([R][n] float64, in place copies returned) by steps t0..t1-1 with J = -w."""
+# simulated bifurcation variants compared in the paper (standard formulations it cites)
+SB_VARIANTS = {"ballistic": 0, "discrete": 1, "adiabatic": 2}
+
+
+def bsb_run(g: CSR, x, y, t0, t1, steps, dt=1.0, a0=1.0, c0=None, variant="ballistic"):
+    """Advance x, y ([R][n] float64, in place copies returned) by steps t0..t1-1 with J = -w.
+
+    variant: "ballistic" (bSB), "discrete" (dSB: J sgn(x)), "adiabatic" (aSB: cubic
+    detuning, no walls)."""
     x = np.array(x, dtype=np.float64, order="C")
     y = np.array(y, dtype=np.float64, order="C")
     J = _c(-g.w, np.float64)
     if c0 is None:
         c0 = default_c0(g)
-    lib().qo_bsb_run(g.n, _p(g.row_ptr), _p(g.col), _p(J), x.shape[0], _p(x), _p(y), t0, t1,
-                     steps, dt, a0, c0)
+    lib().qo_sb_run(g.n, _p(g.row_ptr), _p(g.col), _p(J), x.shape[0], _p(x), _p(y), t0, t1,
+                    steps, dt, a0, c0, SB_VARIANTS[variant])
     return x, y
 
 
@@ -242,15 +253,17 @@ def ising_energy(g: CSR, s):
     return lib().qo_ising_energy(g.n, _p(g.row_ptr), _p(g.col), _p(J), _p(s))
 
 
-def bsb_solve(g: CSR, replica_ids, steps, seed, block=0, it=0, dt=1.0, a0=1.0, c0=0.0):
-    """Multi-replica bSB (SB algorithm solution); returns (best_cut, spins, cuts, best_r)."""
+def bsb_solve(g: CSR, replica_ids, steps, seed, block=0, it=0, dt=1.0, a0=1.0, c0=0.0,
+              variant="ballistic"):
+    """Multi-replica SB (SB algorithm solution); returns (best_cut, spins, cuts, best_r)."""
     rid = _c(replica_ids, np.int32)
     R = rid.shape[0]
     s = np.zeros(g.n, np.int8)
     cuts = np.zeros(R)
     br = C.c_int32(-1)
-    best = lib().qo_bsb_solve(g.n, _p(g.row_ptr), _p(g.col), _p(g.w), R, _p(rid), steps, dt, a0,
-                              c0, seed, block, it, _p(s), _p(cuts), C.byref(br))
+    best = lib().qo_sb_solve(g.n, _p(g.row_ptr), _p(g.col), _p(g.w), R, _p(rid), steps, dt, a0,
+                             c0, seed, block, it, _p(s), _p(cuts), C.byref(br),
+                             SB_VARIANTS[variant])
     return best, s, cuts, br.value
 
 

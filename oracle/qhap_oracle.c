@@ -302,12 +302,20 @@ int32_t qo_components(int32_t n, const int64_t* rp, const int32_t* col, const do
 }
 
 /* ------------------------------------------------------------------------ */
-/* bSB on one component given as CSR of the coupling J (J = -A, SB algorithm
- * solution).  x, y: [R][n] row-major, updated in place from step t0 to t1-1 of
- * a schedule of `steps` steps.  Each replica evolves independently.          */
-void qo_bsb_run(int32_t n, const int64_t* rp, const int32_t* col, const double* J, int32_t R,
-                double* x, double* y, int32_t t0, int32_t t1, int32_t steps, double dt, double a0,
-                double c0) {
+/* Simulated bifurcation on one component given as CSR of the coupling J (J = -A,
+ * SB algorithm solution).  x, y: [R][n] row-major, updated in place from step t0
+ * to t1-1 of a schedule of `steps` steps; each replica evolves independently.
+ * Symplectic Euler as for bSB: y from x_t, then x from y_{t+1}; a(t) = a0 t / steps.
+ * The paper compares three SB variants and cites their standard formulations:
+ *   variant 0, ballistic (bSB):  y += dt (-(a0 - a(t)) x + c0 J x); x += dt a0 y;
+ *                                |x| > 1 => x = sgn(x), y = 0
+ *   variant 1, discrete (dSB):   as bSB with J sgn(x) in place of J x
+ *                                (sgn(0) = +1, as for the spins)
+ *   variant 2, adiabatic (aSB):  y += dt (-(x^2 + a0 - a(t)) x + c0 J x);
+ *                                x += dt a0 y; no walls                        */
+void qo_sb_run(int32_t n, const int64_t* rp, const int32_t* col, const double* J, int32_t R,
+               double* x, double* y, int32_t t0, int32_t t1, int32_t steps, double dt, double a0,
+               double c0, int32_t variant) {
 #pragma omp parallel for schedule(dynamic, 1)
   for (int32_t r = 0; r < R; ++r) {
     double* xr = x + (size_t)r * n;
@@ -317,20 +325,35 @@ void qo_bsb_run(int32_t n, const int64_t* rp, const int32_t* col, const double* 
       double at = a0 * (double)t / (double)steps;
       for (int32_t i = 0; i < n; ++i) {
         double acc = 0.0;
-        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) acc += J[e] * xr[col[e]];
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+          double xj = xr[col[e]];
+          if (variant == 1) xj = xj >= 0.0 ? 1.0 : -1.0;
+          acc += J[e] * xj;
+        }
         z[i] = acc;
       }
-      for (int32_t i = 0; i < n; ++i) yr[i] += dt * (-(a0 - at) * xr[i] + c0 * z[i]);
-      for (int32_t i = 0; i < n; ++i) xr[i] += dt * a0 * yr[i];
       for (int32_t i = 0; i < n; ++i) {
-        if (fabs(xr[i]) > 1.0) {
-          xr[i] = xr[i] > 0 ? 1.0 : -1.0;
-          yr[i] = 0.0;
-        }
+        double detune = a0 - at;
+        if (variant == 2) detune += xr[i] * xr[i];
+        yr[i] += dt * (-detune * xr[i] + c0 * z[i]);
       }
+      for (int32_t i = 0; i < n; ++i) xr[i] += dt * a0 * yr[i];
+      if (variant != 2)
+        for (int32_t i = 0; i < n; ++i) {
+          if (fabs(xr[i]) > 1.0) {
+            xr[i] = xr[i] > 0 ? 1.0 : -1.0;
+            yr[i] = 0.0;
+          }
+        }
     }
     free(z);
   }
+}
+
+void qo_bsb_run(int32_t n, const int64_t* rp, const int32_t* col, const double* J, int32_t R,
+                double* x, double* y, int32_t t0, int32_t t1, int32_t steps, double dt, double a0,
+                double c0) {
+  qo_sb_run(n, rp, col, J, R, x, y, t0, t1, steps, dt, a0, c0, 0);
 }
 
 /* Initial state for replicas replica_ids[0..R-1] of component `block`.       */
@@ -377,10 +400,10 @@ double qo_ising_energy(int32_t n, const int64_t* rp, const int32_t* col, const d
 /* Full multi-replica bSB on one component with weights w (J = -w): returns the
  * best replica's spins (s = sgn(x), sgn(0) = +1), its cut, and every replica's
  * cut.  Ties between replicas go to the lowest replica index.               */
-double qo_bsb_solve(int32_t n, const int64_t* rp, const int32_t* col, const double* w, int32_t R,
-                    const int32_t* replica_ids, int32_t steps, double dt, double a0, double c0,
-                    uint64_t seed, int64_t block, int32_t iter, int8_t* best_s, double* cuts,
-                    int32_t* best_r) {
+double qo_sb_solve(int32_t n, const int64_t* rp, const int32_t* col, const double* w, int32_t R,
+                   const int32_t* replica_ids, int32_t steps, double dt, double a0, double c0,
+                   uint64_t seed, int64_t block, int32_t iter, int8_t* best_s, double* cuts,
+                   int32_t* best_r, int32_t variant) {
   int64_t nnz = rp[n];
   double* J = (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
   for (int64_t e = 0; e < nnz; ++e) J[e] = -w[e];
@@ -389,7 +412,7 @@ double qo_bsb_solve(int32_t n, const int64_t* rp, const int32_t* col, const doub
   double* y = (double*)malloc(sizeof(double) * (size_t)R * (size_t)(n > 0 ? n : 1));
   int8_t* s = (int8_t*)malloc((size_t)(n > 0 ? n : 1));
   qo_bsb_init(n, R, replica_ids, seed, block, iter, x, y);
-  qo_bsb_run(n, rp, col, J, R, x, y, 0, steps, steps, dt, a0, c0);
+  qo_sb_run(n, rp, col, J, R, x, y, 0, steps, steps, dt, a0, c0, variant);
   double best = -INFINITY;
   *best_r = -1;
   for (int32_t r = 0; r < R; ++r) {
@@ -407,6 +430,14 @@ double qo_bsb_solve(int32_t n, const int64_t* rp, const int32_t* col, const doub
   free(y);
   free(s);
   return best;
+}
+
+double qo_bsb_solve(int32_t n, const int64_t* rp, const int32_t* col, const double* w, int32_t R,
+                    const int32_t* replica_ids, int32_t steps, double dt, double a0, double c0,
+                    uint64_t seed, int64_t block, int32_t iter, int8_t* best_s, double* cuts,
+                    int32_t* best_r) {
+  return qo_sb_solve(n, rp, col, w, R, replica_ids, steps, dt, a0, c0, seed, block, iter, best_s,
+                     cuts, best_r, 0);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -421,3 +421,115 @@ def test_n50_hand_case():
     assert metrics.n50([50_000, 30_000, 20_000]) == 50_000
     assert metrics.n50([10, 10, 10, 10]) == 10
     assert metrics.n50([]) == 0
+
+
+# ----------------------------------------------------------------------------- dSB and aSB
+def test_asb_matches_ode_integration(oracle):
+    """Adiabatic SB: symplectic Euler converges (first order) to its ODE, cubic detuning
+    included, and it has no walls."""
+    from scipy.integrate import solve_ivp
+    rng = np.random.default_rng(10)
+    n = 5
+    J = rng.normal(size=(n, n))  # asymmetric: catches a transposed product
+    np.fill_diagonal(J, 0)
+    g = oracle.CSR.from_dense(-J)
+    a0, c0, T = 1.0, 0.4, 8.0
+    x0 = rng.uniform(-0.3, 0.3, n)
+    y0 = rng.uniform(-0.3, 0.3, n)
+
+    def rhs(t, u):
+        x, y = u[:n], u[n:]
+        at = a0 * t / T
+        return np.concatenate([a0 * y, -(x * x + a0 - at) * x + c0 * (J @ x)])
+
+    ref = solve_ivp(rhs, (0, T), np.concatenate([x0, y0]), rtol=1e-11, atol=1e-13).y[:, -1]
+    assert np.abs(ref[:n]).max() > 0.3  # the cubic term matters at this amplitude
+    errs = []
+    for steps in (3000, 6000):
+        dt = T / steps
+        x, y = oracle.bsb_run(g, x0[None], y0[None], 0, steps, steps, dt=dt, a0=a0, c0=c0,
+                              variant="adiabatic")
+        errs.append(np.abs(np.concatenate([x[0], y[0]]) - ref).max() / np.abs(ref).max())
+    assert errs[1] < 2e-3
+    assert 1.6 < errs[0] / errs[1] < 2.4
+
+
+def test_asb_has_no_walls(oracle):
+    W = synth.random_graph(3, 8, p=0.6)
+    g = oracle.CSR.from_dense(W)
+    x0 = np.full((1, 8), 0.9)
+    y0 = np.full((1, 8), 2.0)
+    xa, ya = oracle.bsb_run(g, x0, y0, 0, 1, 10, dt=0.5, c0=0.0, variant="adiabatic")
+    xb, yb = oracle.bsb_run(g, x0, y0, 0, 1, 10, dt=0.5, c0=0.0, variant="ballistic")
+    assert (np.abs(xa) > 1.0).all() and (ya != 0).all()
+    assert (np.abs(xb) == 1.0).all() and (yb == 0).all()
+
+
+def test_dsb_from_binary_states_equals_bsb(oracle):
+    """On x in {-1, +1}^n, sgn(x) = x: one discrete step equals one ballistic step."""
+    W = synth.random_graph(5, 16, p=0.5, integer=False)
+    g = oracle.CSR.from_dense(W)
+    rng = np.random.default_rng(11)
+    x0 = np.where(rng.random((4, 16)) < 0.5, -1.0, 1.0)
+    y0 = rng.uniform(-0.1, 0.1, (4, 16))
+    c0 = oracle.default_c0(g)
+    xd, yd = oracle.bsb_run(g, x0, y0, 7, 8, 40, c0=c0, variant="discrete")
+    xb, yb = oracle.bsb_run(g, x0, y0, 7, 8, 40, c0=c0, variant="ballistic")
+    assert np.array_equal(xd, xb) and np.array_equal(yd, yb)
+
+
+def test_dsb_coupling_sees_only_signs(oracle):
+    """Two states with the same signs differ, after a discrete step, exactly as they do
+    without coupling (c0 = 0): the coupling term cancels.  The ballistic step does not."""
+    W = synth.random_graph(6, 12, p=0.6, integer=False)
+    g = oracle.CSR.from_dense(W)
+    rng = np.random.default_rng(12)
+    x1 = rng.uniform(0.05, 0.3, (2, 12)) * np.where(rng.random((2, 12)) < 0.5, -1, 1)
+    x2 = x1 * rng.uniform(0.2, 0.9, (2, 12))  # same signs, other magnitudes
+    y0 = rng.uniform(-0.05, 0.05, (2, 12))
+    c0 = oracle.default_c0(g)
+
+    def diff(variant, cc):
+        xa, ya = oracle.bsb_run(g, x1, y0, 3, 4, 20, c0=cc, variant=variant)
+        xb, yb = oracle.bsb_run(g, x2, y0, 3, 4, 20, c0=cc, variant=variant)
+        assert np.abs(xa).max() < 1.0 and np.abs(xb).max() < 1.0  # away from the walls
+        return np.concatenate([xa - xb, ya - yb])
+
+    np.testing.assert_allclose(diff("discrete", c0), diff("discrete", 0.0), rtol=0, atol=1e-15)
+    assert np.abs(diff("ballistic", c0) - diff("ballistic", 0.0)).max() > 1e-3
+
+
+@pytest.mark.parametrize("variant,dt", [("discrete", 1.0), ("adiabatic", 0.5)])
+def test_sb_variants_gauge_invariance_exact(oracle, variant, dt):
+    W = synth.random_graph(4, 14, p=0.4, integer=False)
+    g = oracle.CSR.from_dense(W)
+    rng = np.random.default_rng(13)
+    d = np.where(rng.random(14) < 0.5, -1.0, 1.0)
+    gd = oracle.CSR.from_dense(d[:, None] * W * d[None, :])
+    x0 = rng.uniform(-0.1, 0.1, (3, 14))
+    y0 = rng.uniform(-0.1, 0.1, (3, 14))
+    c0 = oracle.default_c0(g)
+    x1, y1 = oracle.bsb_run(g, x0, y0, 0, 300, 300, dt=dt, c0=c0, variant=variant)
+    x2, y2 = oracle.bsb_run(gd, x0 * d, y0 * d, 0, 300, 300, dt=dt, c0=c0, variant=variant)
+    assert np.array_equal(x2, x1 * d) and np.array_equal(y2, y1 * d)
+
+
+@pytest.mark.parametrize("variant,dt", [("discrete", 1.0), ("adiabatic", 0.5)])
+def test_sb_variants_brute_force(oracle, variant, dt):
+    """dSB and aSB reach the exhaustive-search optimum of small mixed-sign graphs."""
+    rng = np.random.default_rng(14)
+    hit, worst = 0, 1.0
+    for inst in range(12):
+        n = 11
+        A = np.triu(rng.integers(-3, 4, (n, n)), 1)
+        A = (A + A.T).astype(float)
+        g = oracle.CSR.from_dense(A)
+        best, s, _, _ = oracle.bsb_solve(g, list(range(32)), 2000, inst, dt=dt, variant=variant)
+        opt = -np.inf
+        for bits in range(1 << (n - 1)):
+            sp = np.array([1 if (bits >> i) & 1 else -1 for i in range(n)])
+            opt = max(opt, 0.25 * (A.sum() - sp @ A @ sp))
+        assert best == oracle.cut(g, s)
+        hit += best >= opt - 1e-9
+        worst = min(worst, best / opt)
+    assert hit >= 11 and worst >= 0.9, (hit, worst)
