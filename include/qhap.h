@@ -67,6 +67,13 @@ enum { QH_PREC_FP32 = 0, QH_PREC_BF16 = 1, QH_PREC_BF16X2 = 2, QH_PREC_FP8 = 3 }
  * AUTO = steps chosen from the block size as in the paper's SNP-based runs
  * (500 iterations for < 5,000 nodes, 1,000 otherwise). */
 enum { QH_SCHED_LINEAR = 0, QH_SCHED_AUTO = 1 };
+/* Simulated-bifurcation variants (the three the paper compares, in their standard
+ * formulations; a(t) as above, symplectic Euler: y from x_t, then x from y_{t+1}):
+ * BALLISTIC: y += dt(-(a0 - a(t)) x + c0 J x), x += dt a0 y, |x| > 1 => x = sgn x, y = 0
+ * DISCRETE:  as BALLISTIC with J sgn(x) (sgn(0) = +1) in place of J x
+ * ADIABATIC: y += dt(-(x^2 + a0 - a(t)) x + c0 J x), x += dt a0 y, no walls
+ * DISCRETE and ADIABATIC run on the FP32 and BF16 tile paths (not FP8, not CSR). */
+enum { QH_SB_BALLISTIC = 0, QH_SB_DISCRETE = 1, QH_SB_ADIABATIC = 2 };
 
 /* ---------------------------------------------------------------- context */
 
@@ -187,6 +194,8 @@ typedef struct {
                            qh_solution_kernel for names; 6..9 are the multi-step
                            kernels that keep y on chip and launch once per step
                            range); invalid choices -> QH_EINVAL */
+  int32_t sb_variant;   /* QH_SB_BALLISTIC (0, the paper's solver), QH_SB_DISCRETE,
+                           QH_SB_ADIABATIC */
 } qh_bsb_opts;
 
 /* Run multi-replica bSB on every block of the graph in one batched launch per
@@ -280,14 +289,16 @@ qh_status qh_debug_steps(qh_ctx* ctx, const qh_graph* g, int32_t precision, int3
                          float* x, float* y, int32_t t0, int32_t nsteps, int32_t steps, double dt,
                          double a0, const double* c0_per_block);
 
-/* qh_debug_steps with an explicit step kernel (BF16 / BF16X2 tile storage only):
+/* qh_debug_steps with an explicit step kernel (BF16 / BF16X2 tile storage only) and
+ * SB variant (QH_SB_*; not FP8, not CSR):
  * step_kernel = -1 is the default; otherwise an index into the solver's kernel
  * variants (qh_bsb_opts.step_kernel).  The multi-step variants run all `nsteps`
  * steps in ONE launch, the momentum y held on chip between steps.  QH_EINVAL when
  * the variant does not fit the graph, precision or R. */
 qh_status qh_debug_steps_v(qh_ctx* ctx, const qh_graph* g, int32_t precision, int32_t R,
                            float* x, float* y, int32_t t0, int32_t nsteps, int32_t steps,
-                           double dt, double a0, const double* c0_per_block, int32_t step_kernel);
+                           double dt, double a0, const double* c0_per_block, int32_t step_kernel,
+                           int32_t sb_variant);
 
 /* Padded layout: n_pad and padded_index int32[n_nodes] (-1 for vertices in no
  * block): vertex v of block b sits at padded column pad_off[b] + local[v]. */

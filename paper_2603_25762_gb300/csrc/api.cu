@@ -148,15 +148,18 @@ qh_status check_err_word(Ctx* ctx) {
 
 // Time every valid step-kernel variant on the live state for a few steps and keep
 // the fastest for this graph shape.  The state is re-initialised afterwards.
-std::string tune_key(const Graph& g, int R, int use_lo) {
+std::string tune_key(const Graph& g, int R, int use_lo, int sb) {
   char kb[160];
-  snprintf(kb, sizeof kb, "%d|%d|%lld|%d|%d|%d", R, g.n_row_tiles, (long long)g.n_tiles,
-           g.max_tiles_per_row, g.n_pad, use_lo);
+  snprintf(kb, sizeof kb, "%d|%d|%lld|%d|%d|%d|%d", R, g.n_row_tiles, (long long)g.n_tiles,
+           g.max_tiles_per_row, g.n_pad, use_lo, sb);
   return kb;
 }
 
-bool tuned_variant(Ctx* ctx, const Graph& g, int R, TcPlan* plan) {
-  const std::string kb = tune_key(g, R, 0);
+// The two persistent per-step kernels implement the ballistic update only.
+bool sb_kernel_ok(int v, int sb) { return sb == QH_SB_BALLISTIC || (v != 4 && v != 5); }
+
+bool tuned_variant(Ctx* ctx, const Graph& g, int R, int sb, TcPlan* plan) {
+  const std::string kb = tune_key(g, R, 0, sb);
   for (auto& kv : ctx->tuned)
     if (kv.first == kb) {
       plan->variant = kv.second;
@@ -177,7 +180,7 @@ bool run_c0_ok(const float* c0, int32_t nb, float dt) {
 
 qh_status autotune(Ctx* ctx, const Graph& g, StepArgs a, const SolveBufs& B, int R, TcPlan* plan,
                    bool allow_run) {
-  const std::string kb = tune_key(g, R, 0);
+  const std::string kb = tune_key(g, R, 0, a.sb);
   cudaStream_t s = ctx->stream;
   float best = 1e30f;
   int best_v = -1;
@@ -185,6 +188,7 @@ qh_status autotune(Ctx* ctx, const Graph& g, StepArgs a, const SolveBufs& B, int
   for (int v = 0; v < tc_n_variants(); ++v) {
     if (!tc_variant_ok(v, g, R, ctx->n_sm, a.use_lo != 0)) continue;
     if (run_variant(v) && !allow_run) continue;
+    if (!sb_kernel_ok(v, a.sb)) continue;
     TcPlan p = *plan;
     p.variant = v;
     RunBufs rb;
@@ -426,6 +430,12 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   if (o->schedule == QH_SCHED_LINEAR && o->steps < 1) return set_err(ctx, QH_EINVAL, "steps must be >= 1");
   if (o->precision != QH_PREC_FP32 && !is_tc_precision(o->precision) && o->precision != QH_PREC_FP8)
     return set_err(ctx, QH_EINVAL, "bad precision");
+  if (o->sb_variant < QH_SB_BALLISTIC || o->sb_variant > QH_SB_ADIABATIC)
+    return set_err(ctx, QH_EINVAL, "bad sb_variant");
+  if (o->sb_variant != QH_SB_BALLISTIC && (o->precision == QH_PREC_FP8 || G.csr_mode))
+    return set_err(ctx, QH_EUNSUPPORTED, "discrete / adiabatic SB need FP32 or BF16 tile storage");
+  if (o->sb_variant != QH_SB_BALLISTIC && o->step_kernel >= 0 && !sb_kernel_ok(o->step_kernel, o->sb_variant))
+    return set_err(ctx, QH_EINVAL, "this step_kernel implements the ballistic update only");
   if (o->precision == QH_PREC_FP8 && G.csr_mode)
     return set_err(ctx, QH_EUNSUPPORTED, "FP8 needs tile storage (the graph is stored as CSR)");
   if (o->precision == QH_PREC_FP8 && R % 64 != 0)
@@ -593,6 +603,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     auto add = [&skey](const void* p) { skey += std::to_string((uintptr_t)p) + "|"; };
     auto addi = [&skey](long long v) { skey += std::to_string(v) + "|"; };
     addi(o->precision); addi(R); addi(max_steps); addi(early ? o->check_every : 0);
+    addi(o->sb_variant);
     addi(o->patience);
     char d[64];
     snprintf(d, sizeof d, "%.17g|%.17g|", o->dt, o->a0);
@@ -632,6 +643,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   a.a0 = o->a0;
   a.dta0 = (float)(o->dt * o->a0);
   a.err = ctx->d_err;
+  a.sb = o->sb_variant;
   const float* x_final = B.x;
   if (o->precision == QH_PREC_FP32 && (max_steps % 2 == 1)) x_final = B.x1;
   TcPlan tplan = plan;
@@ -642,9 +654,10 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     if (o->step_kernel >= 0) {
       tplan.variant = o->step_kernel;
     } else if (!G.csr_mode) {
-      if (!tuned_variant(ctx, G, R, &tplan)) {  // first solve of this shape: time the variants
+      if (!tuned_variant(ctx, G, R, o->sb_variant, &tplan)) {  // first solve of this shape: time the variants
         QH_CUDA_TRY(cudaMemcpyAsync(B.running, B.active, nb * 4, cudaMemcpyDeviceToDevice, s));
-        launch_init_state(s, W, R, o->replica_base, o->seed, 0, B.x, B.y, B.xh0, B.active);
+        launch_init_state(s, W, R, o->replica_base, o->seed, 0, B.x, B.y, B.xh0, B.active,
+                          o->sb_variant);
         QH_STAGE_CHECK("solve: state init (tuning)");
         st = autotune(ctx, W, a, B, R, &tplan, run_c0_ok(h_c0.data(), nb, a.dt));
       }
@@ -734,7 +747,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     }
     QH_CUDA_TRY(cudaMemcpyAsync(B.running, B.active, nb * 4, cudaMemcpyDeviceToDevice, s));
     launch_init_state(s, W, R, o->replica_base, o->seed, it, B.x, B.y,
-                      is_tc_precision(o->precision) ? B.xh0 : nullptr, B.active);
+                      is_tc_precision(o->precision) ? B.xh0 : nullptr, B.active, o->sb_variant);
     if (fp8)
       launch_x_to_e4m3(s, B.x, (int64_t)NS, reinterpret_cast<uint8_t*>(B.xh0),
                        reinterpret_cast<uint8_t*>(B.xh0) + NS);
@@ -1110,13 +1123,16 @@ qh_status qh_debug_matvec(qh_ctx* h, const qh_graph* gh, int32_t precision, int3
 qh_status qh_debug_steps(qh_ctx* h, const qh_graph* gh, int32_t precision, int32_t R, float* x,
                          float* y, int32_t t0, int32_t nsteps, int32_t steps, double dt, double a0,
                          const double* c0_per_block) {
-  return qh_debug_steps_v(h, gh, precision, R, x, y, t0, nsteps, steps, dt, a0, c0_per_block, -1);
+  return qh_debug_steps_v(h, gh, precision, R, x, y, t0, nsteps, steps, dt, a0, c0_per_block, -1,
+                          QH_SB_BALLISTIC);
 }
 
 qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int32_t R, float* x,
                            float* y, int32_t t0, int32_t nsteps, int32_t steps, double dt,
-                           double a0, const double* c0_per_block, int32_t step_kernel) {
+                           double a0, const double* c0_per_block, int32_t step_kernel,
+                           int32_t sb_variant) {
   if (!h || !gh || !x || !y || nsteps < 0 || steps < 1 || t0 < 0) return QH_EINVAL;
+  if (sb_variant < QH_SB_BALLISTIC || sb_variant > QH_SB_ADIABATIC) return QH_EINVAL;
   Ctx* ctx = &h->c;
   const Graph& g = gh->g;
   cudaSetDevice(ctx->device);
@@ -1124,9 +1140,13 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
   std::vector<float> c0h;
   qh_status st = debug_common(ctx, g, precision, R, a, c0_per_block, steps, &c0h);
   if (st) return st;
+  a.sb = sb_variant;
+  if (sb_variant != QH_SB_BALLISTIC && (precision == QH_PREC_FP8 || g.csr_mode))
+    return set_err(ctx, QH_EUNSUPPORTED, "discrete / adiabatic SB need FP32 or BF16 tile storage");
   if (step_kernel >= 0) {
     if (!is_tc_precision(precision) || g.csr_mode || step_kernel >= tc_n_variants() ||
-        !tc_variant_ok(step_kernel, g, R, ctx->n_sm, a.use_lo != 0))
+        !tc_variant_ok(step_kernel, g, R, ctx->n_sm, a.use_lo != 0) ||
+        !sb_kernel_ok(step_kernel, sb_variant))
       return set_err(ctx, QH_EINVAL, "step_kernel variant not valid for this graph, precision and R");
     if (run_variant(step_kernel) && !run_c0_ok(c0h.data(), g.n_blocks, (float)dt))
       return set_err(ctx, QH_EINVAL, "multi-step kernel needs dt * c0 to be a normal float in every block");
@@ -1198,9 +1218,9 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
       if (st) return st;
       if (t0 % 2 == 1) {  // X_hat_t lives in xh0 for even t, xh1 for odd t
         QH_CUDA_TRY(cudaMemsetAsync(xh0, 0, NS * 2, s));
-        launch_f32_to_bf16(s, x, xh1, (int64_t)NS);
+        launch_x_operand(s, g, sb_variant, x, xh1, (int64_t)NS);
       } else {
-        launch_f32_to_bf16(s, x, xh0, (int64_t)NS);
+        launch_x_operand(s, g, sb_variant, x, xh0, (int64_t)NS);
       }
       st = launch_run(ctx, g, a, rb, xh0, xh1, t0, t0 + nsteps);
       if (st) return st;
@@ -1209,7 +1229,7 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
     }
     TcPlan plan = pick_plan(R);
     if (step_kernel >= 0) plan.variant = step_kernel;
-    launch_f32_to_bf16(s, x, xh0, (int64_t)NS);
+    launch_x_operand(s, g, sb_variant, x, xh0, (int64_t)NS);
     for (int32_t k = 0; k < nsteps; ++k) {
       a.t = t0 + k;
       a.xh_out = (k % 2 == 0) ? xh1 : xh0;

@@ -196,7 +196,7 @@ __device__ __forceinline__ Cursor next_live(Cursor c, const ItemInfo* info, int 
   }
 }
 
-template <bool JRES>
+template <bool JRES, int SB>
 __global__ void __launch_bounds__(RUN_THREADS, 1)
     k_bsb_run(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmX0,
               const __grid_constant__ CUtensorMap tmX1, RunArgs a) {
@@ -477,9 +477,11 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
 #pragma unroll
         for (int j = 0; j < 16; ++j) {  // branch-free update and wall
           const float x0 = xb[c][j];
-          const float y1 = fmaf(dtc0, __uint_as_float(v[j]), dtcx * x0);
+          // adiabatic SB: -(x^2 + a0 - a(t)); no walls
+          const float cx = SB == QH_SB_ADIABATIC ? dtcx - a.dt * x0 * x0 : dtcx;
+          const float y1 = fmaf(dtc0, __uint_as_float(v[j]), cx * x0);
           const float x1 = fmaf(dta0, y1, x0);
-          const bool wall = fabsf(x1) > 1.f;
+          const bool wall = SB != QH_SB_ADIABATIC && fabsf(x1) > 1.f;
           xo[j] = wall ? copysignf(1.f, x1) : x1;
           yo[j] = wall ? 0.f : y1;
           // padding vertices hold x = y = 0 and J rows of zeros: their y stays 0
@@ -487,7 +489,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
         }
         if (vr) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) hc[j * np] = __float2bfloat16_rn(xo[j]);
+          for (int j = 0; j < 16; ++j) hc[j * np] = __float2bfloat16_rn(sb_operand(SB, xo[j]));
           if (!last) {
 #pragma unroll
             for (int m = 0; m < 4; ++m)
@@ -655,7 +657,7 @@ qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo,
   return QH_OK;
 }
 
-template <bool JRES>
+template <bool JRES, int SB>
 qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const RunBufs& rb,
                           __nv_bfloat16* xh0, __nv_bfloat16* xh1, int t0, int t1) {
   using L = RunSmem<JRES>;
@@ -704,7 +706,7 @@ qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const Run
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     note_launch(1);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_bsb_run<JRES>, mJ, mX0, mX1, a);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_bsb_run<JRES, SB>, mJ, mX0, mX1, a);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_bsb_run launch");
   }
   return QH_OK;
@@ -713,16 +715,30 @@ qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const Run
 qh_status launch_run(Ctx* ctx, const Graph& g, const StepArgs& s, const RunBufs& rb,
                      __nv_bfloat16* xh0, __nv_bfloat16* xh1, int t0, int t1) {
   if (g.n_row_tiles == 0 || t1 <= t0) return QH_OK;
-  return rb.jres ? launch_run_impl<true>(ctx, g, s, rb, xh0, xh1, t0, t1)
-                 : launch_run_impl<false>(ctx, g, s, rb, xh0, xh1, t0, t1);
+  switch (s.sb * 2 + (rb.jres ? 1 : 0)) {
+    case 0: return launch_run_impl<false, QH_SB_BALLISTIC>(ctx, g, s, rb, xh0, xh1, t0, t1);
+    case 1: return launch_run_impl<true, QH_SB_BALLISTIC>(ctx, g, s, rb, xh0, xh1, t0, t1);
+    case 2: return launch_run_impl<false, QH_SB_DISCRETE>(ctx, g, s, rb, xh0, xh1, t0, t1);
+    case 3: return launch_run_impl<true, QH_SB_DISCRETE>(ctx, g, s, rb, xh0, xh1, t0, t1);
+    case 4: return launch_run_impl<false, QH_SB_ADIABATIC>(ctx, g, s, rb, xh0, xh1, t0, t1);
+    case 5: return launch_run_impl<true, QH_SB_ADIABATIC>(ctx, g, s, rb, xh0, xh1, t0, t1);
+    default: return set_err(ctx, QH_EINVAL, "bad SB variant");
+  }
+}
+
+template <bool JRES, int SB>
+static cudaError_t run_attr() {
+  return cudaFuncSetAttribute(k_bsb_run<JRES, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)RunSmem<JRES>::BYTES);
 }
 
 cudaError_t run_set_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(k_bsb_run<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)RunSmem<true>::BYTES);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_bsb_run<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)RunSmem<false>::BYTES);
+  cudaError_t e = run_attr<true, QH_SB_BALLISTIC>();
+  if (e == cudaSuccess) e = run_attr<false, QH_SB_BALLISTIC>();
+  if (e == cudaSuccess) e = run_attr<true, QH_SB_DISCRETE>();
+  if (e == cudaSuccess) e = run_attr<false, QH_SB_DISCRETE>();
+  if (e == cudaSuccess) e = run_attr<true, QH_SB_ADIABATIC>();
+  if (e == cudaSuccess) e = run_attr<false, QH_SB_ADIABATIC>();
   return e;
 }
 

@@ -18,7 +18,7 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t
 __global__ void k_init_state(const RowTile* __restrict__ rt, const int32_t* __restrict__ pad_node,
                              const int32_t* __restrict__ local, int32_t n_pad, int32_t R,
                              int32_t replica_base, uint64_t seed, int32_t iter, float* x, float* y,
-                             __nv_bfloat16* xh, const int32_t* __restrict__ active) {
+                             __nv_bfloat16* xh, const int32_t* __restrict__ active, int32_t sb) {
   int32_t col = blockIdx.x * blockDim.x + threadIdx.x;
   int32_t r = blockIdx.y;
   if (col >= n_pad || r >= R) return;
@@ -34,7 +34,7 @@ __global__ void k_init_state(const RowTile* __restrict__ rt, const int32_t* __re
   size_t idx = (size_t)r * n_pad + col;
   x[idx] = xv;
   y[idx] = yv;
-  if (xh != nullptr) xh[idx] = __float2bfloat16_rn(xv);
+  if (xh != nullptr) xh[idx] = __float2bfloat16_rn(v >= 0 ? sb_operand(sb, xv) : 0.f);
 }
 
 __global__ void k_f32_to_bf16(const float* __restrict__ x, __nv_bfloat16* xh, int64_t n) {
@@ -42,20 +42,16 @@ __global__ void k_f32_to_bf16(const float* __restrict__ x, __nv_bfloat16* xh, in
   if (i < n) xh[i] = __float2bfloat16_rn(x[i]);
 }
 
+// Product operand of a discrete-SB state: sgn(x) at real vertices, 0 at padding.
+__global__ void k_x_to_sign_bf16(const float* __restrict__ x, __nv_bfloat16* xh, int64_t n,
+                                 int32_t n_pad, const int32_t* __restrict__ pad_node) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) xh[i] = __float2bfloat16_rn(pad_node[i % n_pad] >= 0 ? sb_operand(QH_SB_DISCRETE, x[i]) : 0.f);
+}
+
 // ------------------------------------------------------------------ FP32 step
 constexpr int F_RT = 64;   // replicas per CTA
 constexpr int F_KC = 32;   // K chunk staged in shared memory
-
-// bSB update of one element (same operation order as the tensor-core path).
-__device__ __forceinline__ void bsb_update(float z, float& x, float& y, float dt, float coef_x,
-                                           float dta0, float c0) {
-  y = y + dt * (coef_x * x + c0 * z);
-  x = x + dta0 * y;
-  if (fabsf(x) > 1.f) {
-    x = x > 0.f ? 1.f : -1.f;
-    y = 0.f;
-  }
-}
 
 __global__ void __launch_bounds__(256) k_step_f32(StepArgs a) {
   const int32_t t = a.t;
@@ -103,6 +99,9 @@ __global__ void __launch_bounds__(256) k_step_f32(StepArgs a) {
         if (r0 + rep < a.R)
           v = *reinterpret_cast<const float4*>(a.xin + (size_t)(r0 + rep) * a.n_pad + cbase + kc +
                                                k4 * 4);
+        if (a.sb == QH_SB_DISCRETE)  // J sgn(x); padding columns meet zero columns of J
+          v = make_float4(sb_operand(a.sb, v.x), sb_operand(a.sb, v.y), sb_operand(a.sb, v.z),
+                          sb_operand(a.sb, v.w));
         Xs[k4 * 4 + 0][rep] = v.x;
         Xs[k4 * 4 + 1][rep] = v.y;
         Xs[k4 * 4 + 2][rep] = v.z;
@@ -140,7 +139,7 @@ __global__ void __launch_bounds__(256) k_step_f32(StepArgs a) {
         continue;
       }
       float x = a.xin[idx], y = a.y[idx];
-      bsb_update(acc[i][j], x, y, a.dt, coef_x, a.dta0, c0);
+      sb_update(a.sb, acc[i][j], x, y, a.dt, coef_x, a.dta0, c0);
       a.xout[idx] = x;
       a.y[idx] = y;
     }
@@ -261,7 +260,7 @@ __global__ void __launch_bounds__(256) k_step_csr(StepArgs a, const int64_t* __r
     float4 yv = *reinterpret_cast<const float4*>(a.y + idx);
     float xs[4] = {xv.x, xv.y, xv.z, xv.w}, ys[4] = {yv.x, yv.y, yv.z, yv.w};
 #pragma unroll
-    for (int j = 0; j < 4; ++j) bsb_update(acc[j], xs[j], ys[j], a.dt, coef_x, a.dta0, c0);
+    for (int j = 0; j < 4; ++j) sb_update(a.sb, acc[j], xs[j], ys[j], a.dt, coef_x, a.dta0, c0);
     float* xdst = BF16 ? a.x : a.xout;
     *reinterpret_cast<float4*>(xdst + idx) = make_float4(xs[0], xs[1], xs[2], xs[3]);
     *reinterpret_cast<float4*>(a.y + idx) = make_float4(ys[0], ys[1], ys[2], ys[3]);
@@ -707,7 +706,7 @@ __global__ void k_parity(int32_t n, const int32_t* __restrict__ block_of, const 
 
 void launch_init_state(cudaStream_t s, const Graph& g, int32_t R, int32_t replica_base,
                        uint64_t seed, int32_t iter, float* x, float* y, __nv_bfloat16* xh,
-                       const int32_t* active) {
+                       const int32_t* active, int32_t sb) {
   if (g.n_pad == 0 || R == 0) return;
   if (g.csr_mode) {
     const int64_t n = (int64_t)g.n_pad * R;
@@ -718,7 +717,16 @@ void launch_init_state(cudaStream_t s, const Graph& g, int32_t R, int32_t replic
   }
   dim3 grid(nblk(g.n_pad), R);
   k_init_state<<<::qh::counted(grid), 256, 0, s>>>(g.rt, g.pad_node, g.local, g.n_pad, R, replica_base, seed, iter,
-                                    x, y, xh, active);
+                                    x, y, xh, active, sb);
+}
+
+void launch_x_operand(cudaStream_t s, const Graph& g, int32_t sb, const float* x,
+                      __nv_bfloat16* xh, int64_t n) {
+  if (n <= 0) return;
+  if (sb == QH_SB_DISCRETE)
+    k_x_to_sign_bf16<<<::qh::counted(nblk(n)), 256, 0, s>>>(x, xh, n, g.n_pad, g.pad_node);
+  else
+    k_f32_to_bf16<<<::qh::counted(nblk(n)), 256, 0, s>>>(x, xh, n);
 }
 
 void launch_f32_to_bf16(cudaStream_t s, const float* x, __nv_bfloat16* xh, int64_t n) {

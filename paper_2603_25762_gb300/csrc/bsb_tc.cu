@@ -133,16 +133,11 @@ __global__ void __launch_bounds__(128) k_step_tc(const __grid_constant__ CUtenso
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       float x = xs[j], y = ys[j];
-      y = y + a.dt * (coef_x * x + c0 * __uint_as_float(v[j]));
-      x = x + a.dta0 * y;
-      if (fabsf(x) > 1.f) {
-        x = x > 0.f ? 1.f : -1.f;
-        y = 0.f;
-      }
+      sb_update(a.sb, __uint_as_float(v[j]), x, y, a.dt, coef_x, a.dta0, c0);
       const size_t idx = b0 + (size_t)j * a.n_pad;
       a.x[idx] = x;
       a.y[idx] = y;
-      a.xh_out[idx] = __float2bfloat16_rn(x);
+      a.xh_out[idx] = __float2bfloat16_rn(sb_operand(a.sb, x));
     }
   }
   tc_fence_before();
@@ -265,16 +260,11 @@ __global__ void __launch_bounds__(128, MINB) k_step_tc_v(const __grid_constant__
 #pragma unroll
       for (int j = 0; j < CH; ++j) {
         float x = xs[j], y = ys[j];
-        y = y + a.dt * (coef_x * x + c0 * __uint_as_float(v[j]));
-        x = x + a.dta0 * y;
-        if (fabsf(x) > 1.f) {
-          x = x > 0.f ? 1.f : -1.f;
-          y = 0.f;
-        }
+        sb_update(a.sb, __uint_as_float(v[j]), x, y, a.dt, coef_x, a.dta0, c0);
         const size_t idx = b0 + (size_t)j * a.n_pad;
         a.x[idx] = x;
         a.y[idx] = y;
-        a.xh_out[idx] = __float2bfloat16_rn(x);
+        a.xh_out[idx] = __float2bfloat16_rn(sb_operand(a.sb, x));
       }
     }
     if (more) {

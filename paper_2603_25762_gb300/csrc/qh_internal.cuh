@@ -187,7 +187,25 @@ struct StepArgs {
   float dt, dta0;         // dta0 = dt * a0
   double a0;
   int32_t* err;
+  int32_t sb;             // SB variant: QH_SB_BALLISTIC, QH_SB_DISCRETE, QH_SB_ADIABATIC
 };
+
+// One element of the SB update, after the coupling z (= J x_hat) is known.
+// coef_x = -(a0 - a(t)); the adiabatic variant adds -x^2 and has no walls.
+__device__ __forceinline__ void sb_update(int sb, float z, float& x, float& y, float dt,
+                                          float coef_x, float dta0, float c0) {
+  const float cx = sb == QH_SB_ADIABATIC ? coef_x - x * x : coef_x;
+  y = y + dt * (cx * x + c0 * z);
+  x = x + dta0 * y;
+  if (sb != QH_SB_ADIABATIC && fabsf(x) > 1.f) {
+    x = x > 0.f ? 1.f : -1.f;
+    y = 0.f;
+  }
+}
+// The product's operand for the next step: x, or sgn(x) (sgn(0) = +1) for discrete SB.
+__device__ __forceinline__ float sb_operand(int sb, float x) {
+  return sb == QH_SB_DISCRETE ? (x >= 0.f ? 1.f : -1.f) : x;
+}
 
 // Tensor-core precisions use the BF16 hi tiles; the lo (remainder) tiles join when
 // asked for (QH_PREC_BF16X2) or when integer weights above 256 need them to stay exact.
@@ -215,7 +233,10 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
 // ---- launchers (bsb_simt.cu)
 void launch_init_state(cudaStream_t s, const Graph& g, int32_t R, int32_t replica_base,
                        uint64_t seed, int32_t iter, float* x, float* y, __nv_bfloat16* xh,
-                       const int32_t* active);
+                       const int32_t* active, int32_t sb = QH_SB_BALLISTIC);
+// X_hat of a state for the given SB variant: bf16(x), or sgn(x) at real vertices.
+void launch_x_operand(cudaStream_t s, const Graph& g, int32_t sb, const float* x,
+                      __nv_bfloat16* xh, int64_t n);
 void launch_step_f32(cudaStream_t s, const Graph& g, const StepArgs& a);
 // CSR storage: warp per padded vertex, state [n_pad][R]; xh_in != nullptr selects the
 // BF16 X_hat operand, otherwise a.xin (FP32).

@@ -48,8 +48,10 @@ class QhBsbOpts(C.Structure):
                 ("precision", C.c_int32), ("dt", C.c_double), ("a0", C.c_double),
                 ("c0", C.c_double), ("seed", C.c_uint64), ("replica_base", C.c_int32),
                 ("check_every", C.c_int32), ("patience", C.c_int32), ("refine_max", C.c_int32),
-                ("step_kernel", C.c_int32)]
+                ("step_kernel", C.c_int32), ("sb_variant", C.c_int32)]
 
+# simulated-bifurcation variants (QH_SB_*)
+SB_VARIANTS = {"ballistic": 0, "discrete": 1, "adiabatic": 2}
 STEP_KERNELS = ["cta-bn128-s3", "cta-bn128-s2-x3", "cta-bn64-s2-x4", "cta-bn256-s2-x2",
                 "persistent-bn128", "persistent-bn64-tma-state",
                 "multistep-jres-group", "multistep-stream-tile", "multistep-jres-tile",
@@ -86,7 +88,7 @@ _SIGS = {
     "qh_phase": (C.c_int, [P, P, P, P, P, P, I32]),
     "qh_debug_matvec": (C.c_int, [P, P, I32, I32, P, P]),
     "qh_debug_steps": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P]),
-    "qh_debug_steps_v": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P, I32]),
+    "qh_debug_steps_v": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P, I32, I32]),
     "qh_debug_layout": (C.c_int, [P, P, P, P, P]),
     "qh_matvec_bf16_noalloc": (C.c_int, [P, P, I32, P, P]),
     "qh_solution_kernel": (C.c_char_p, [P]),
@@ -257,11 +259,12 @@ class Context:
 
     def solve(self, g, replicas=32, steps=1000, precision=PREC_FP32, seed=1, dt=1.0, a0=1.0,
               c0=0.0, schedule=SCHED_LINEAR, replica_base=0, check_every=0, patience=0,
-              refine_max=15, step_kernel=None):
-        """step_kernel: None = autotune, or a name from STEP_KERNELS (BF16 only)."""
+              refine_max=15, step_kernel=None, variant="ballistic"):
+        """step_kernel: None = autotune, or a name from STEP_KERNELS (BF16 only).
+        variant: "ballistic" (bSB), "discrete" (dSB) or "adiabatic" (aSB)."""
         sk = -1 if step_kernel is None else STEP_KERNELS.index(step_kernel)
         o = QhBsbOpts(replicas, steps, schedule, precision, dt, a0, c0, seed, replica_base,
-                      check_every, patience, refine_max, sk)
+                      check_every, patience, refine_max, sk, SB_VARIANTS[variant])
         s = C.c_void_p()
         self._check(lib().qh_bsb_solve(self.h, g.h, C.byref(o), C.byref(s)))
         return Solution(self, s, g.n_blocks, replicas)
@@ -283,13 +286,14 @@ class Context:
         self._check(lib().qh_debug_matvec(self.h, g.h, precision, R, _ptr(x), _ptr(z)))
 
     def debug_steps(self, g, precision, R, x, y, t0, nsteps, steps, dt=1.0, a0=1.0, c0=None,
-                    step_kernel=None):
+                    step_kernel=None, variant="ballistic"):
         """step_kernel: None = default kernel, or a name from STEP_KERNELS."""
         c0a = None if c0 is None else _np(c0, np.float64)
         sk = -1 if step_kernel is None else STEP_KERNELS.index(step_kernel)
         self._check(lib().qh_debug_steps_v(self.h, g.h, precision, R, _ptr(x), _ptr(y), t0,
                                            nsteps, steps, dt, a0,
-                                           _ptr(c0a) if c0a is not None else None, sk))
+                                           _ptr(c0a) if c0a is not None else None, sk,
+                                           SB_VARIANTS[variant]))
 
     def matvec_bf16_noalloc(self, g, R, x, z):
         """J x X in BF16 without any device allocation (fixed 8.5 MiB library array)."""

@@ -1,0 +1,110 @@
+"""Discrete (dSB) and adiabatic (aSB) simulated bifurcation on the GPU against the FP64
+oracle, through the C ABI: the state after a few steps and whole solves, on the FP32
+tile path, the BF16 per-step kernels and the multi-step kernel.
+
+Bars as for ballistic SB: state within 1e-5 (FP32) / 1e-2 (BF16) relative Frobenius
+of the oracle's after a few steps; best cut >= 0.999 x the oracle's on the same seed,
+steps and replica indices.  aSB runs at dt = 0.5 (at dt = 1 it diverges).
+"""
+import numpy as np
+import pytest
+
+from paper_2603_25762_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+DT = {"discrete": 1.0, "adiabatic": 0.5}
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_25762_gb300 import build, qhap
+    build.build()
+    return qhap
+
+
+@pytest.fixture(scope="module")
+def ctx(q):
+    return q.Context(0)
+
+
+def _rel_frob(a, b):
+    n = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / n if n > 0 else np.linalg.norm(a - b)
+
+
+@pytest.mark.parametrize("variant", ["discrete", "adiabatic"])
+@pytest.mark.parametrize("precision,kernel,tol", [(0, None, 1e-5), (1, None, 1e-2),
+                                                  (1, "cta-bn128-s2-x3", 1e-2),
+                                                  (1, "multistep-stream-tile", 1e-2),
+                                                  (1, "multistep-jres-group", 1e-2)])
+def test_variant_steps_match_oracle(q, ctx, oracle, variant, precision, kernel, tol):
+    import torch
+    fr = synth.batched_blocks(1004, n_blocks=5, n_min=80, n_max=400)
+    g = ctx.build_graph(fr, mode=q.MODE_READ)
+    og = oracle.read_graph(fr, oracle.READ_SIGNED)
+    blocks = oracle.blocks_of(og)
+    n_pad, pidx, c0 = g.layout()
+    R, t0, nsteps, steps, dt = 256, 40, 3, 200, DT[variant]
+    rng = np.random.default_rng(21)
+    x = np.zeros((R, n_pad), np.float32)
+    y = np.zeros((R, n_pad), np.float32)
+    amp = 0.1 if precision else 0.6
+    refs = []
+    for b, nodes in enumerate(blocks):
+        x[:, pidx[nodes]] = rng.uniform(-amp, amp, (R, len(nodes)))
+        y[:, pidx[nodes]] = rng.uniform(-amp, amp, (R, len(nodes)))
+        x1, y1 = oracle.bsb_run(og.subgraph(nodes), x[:, pidx[nodes]].astype(np.float64),
+                                y[:, pidx[nodes]].astype(np.float64), t0, t0 + nsteps, steps,
+                                dt=dt, c0=float(c0[b]), variant=variant)
+        refs.append((nodes, x1, y1))
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    ctx.debug_steps(g, precision, R, xd, yd, t0, nsteps, steps, dt=dt, c0=c0, step_kernel=kernel,
+                    variant=variant)
+    xg, yg = xd.cpu().numpy().astype(np.float64), yd.cpu().numpy().astype(np.float64)
+    for nodes, x1, y1 in refs:
+        xgb, ygb = xg[:, pidx[nodes]], yg[:, pidx[nodes]]
+        if variant == "discrete":  # walls: compare what neither side clamped
+            free = (np.abs(xgb) < 1.0) & (np.abs(x1) < 1.0)
+            assert (~free & (np.abs(xgb) != np.abs(x1))).mean() <= 0.01
+        else:
+            free = np.ones_like(xgb, bool)
+            assert np.abs(x1).max() < 5
+        x0 = x[:, pidx[nodes]]
+        assert _rel_frob((xgb - x0)[free], (x1 - x0)[free]) <= tol
+        assert _rel_frob(ygb[free], y1[free]) <= tol
+
+
+@pytest.mark.parametrize("variant", ["discrete", "adiabatic"])
+@pytest.mark.parametrize("precision,kernel", [(0, None), (1, None), (1, "multistep-stream-group")])
+def test_variant_solve_vs_oracle(q, ctx, oracle, variant, precision, kernel):
+    fr = synth.batched_blocks(1004, n_blocks=6, n_min=40, n_max=300)
+    g = ctx.build_graph(fr, mode=q.MODE_READ)
+    R = 128
+    sol = ctx.solve(g, replicas=R, steps=800, precision=precision, seed=7, dt=DT[variant],
+                    variant=variant, step_kernel=kernel)
+    og = oracle.read_graph(fr, oracle.READ_SIGNED)
+    spins = sol.spins(g.n_nodes)
+    for b, nodes in enumerate(oracle.blocks_of(og)):
+        sub = og.subgraph(nodes)
+        info = sol.block(b, len(nodes))
+        assert info["best_cut"] == oracle.cut(sub, spins[nodes])
+        best, _, _, _ = oracle.bsb_solve(sub, list(range(16)), 800, 7, b, dt=DT[variant],
+                                         variant=variant)
+        assert info["best_cut"] >= 0.999 * best, (b, info["best_cut"], best)
+
+
+def test_variant_unsupported_combinations(q, ctx):
+    fr = synth.tiny_reads(1001)
+    g = ctx.build_graph(fr)
+    with pytest.raises(RuntimeError):  # FP8 implements the ballistic update only
+        ctx.solve(g, replicas=64, steps=10, precision=q.PREC_FP8, variant="discrete")
+    with pytest.raises(RuntimeError):  # so do the two persistent per-step kernels
+        ctx.solve(g, replicas=128, steps=10, precision=q.PREC_BF16, variant="adiabatic",
+                  step_kernel="persistent-bn128")
+    gc = ctx.build_graph(fr, storage=q.STORAGE_CSR)
+    with pytest.raises(RuntimeError):  # and the CSR step
+        ctx.solve(gc, replicas=64, steps=10, precision=q.PREC_BF16, variant="discrete")
