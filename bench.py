@@ -133,6 +133,8 @@ def _workload(args):
     cfg = {"workload": desc, "mode": mode, "n_reads": fr.n_frags, "n_snps": fr.n_snps,
            "replicas": R, "bsb_steps": T, "precision": args.precision,
            "refine_max": REFINE_DEFAULT.get(args.workload, 15) if mode == "snp" else None,
+           "sb_variant": getattr(args, "variant", "ballistic"),
+           "linkage_k": getattr(args, "linkage_k", 10) if mode == "snp" else None,
            "l2": "flushed between timed steps (256 MiB write)"}
     return fr, cfg, mode, R, T
 
@@ -267,12 +269,13 @@ def run_ours(args):
     def one_step(host=False, pinned=None):
         t0 = time.perf_counter()
         if host:
-            g = ctx.build_graph(arrays=pinned, on_device=False, mode=gmode)
+            g = ctx.build_graph(arrays=pinned, on_device=False, mode=gmode, linkage_k=args.linkage_k)
         else:
-            g = ctx.build_graph(arrays=arrays_dev, on_device=True, mode=gmode)
+            g = ctx.build_graph(arrays=arrays_dev, on_device=True, mode=gmode, linkage_k=args.linkage_k)
         stats["build_ms"] = (time.perf_counter() - t0) * 1e3
         sol = ctx.solve(g, replicas=R, steps=T, precision=prec, seed=1, replica_base=base,
-                        step_kernel=args.step_kernel, refine_max=args.refine_max)
+                        step_kernel=args.step_kernel, refine_max=args.refine_max,
+                        variant=args.variant, dt=0.1 if args.variant == "adiabatic" else 1.0)
         if host:
             h = ctx.phase(g, sol, fr.n_snps)
             cut = sol.block(0)["best_cut"] if g.n_blocks else 0.0
@@ -399,6 +402,9 @@ def main():
     ap.add_argument("--refine-max", type=int, default=0, help="0 = the workload's (SNP graphs)")
     ap.add_argument("--ref-replicas", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", default="ballistic", choices=["ballistic", "discrete", "adiabatic"],
+                    help="simulated-bifurcation variant (the paper's solver is ballistic)")
+    ap.add_argument("--linkage-k", type=int, default=10, help="SNP graphs: linkage depth k/10")
     ap.add_argument("--step-kernel", default=None,
                     help="pin the BF16 step-kernel variant (default: autotune)")
     args = ap.parse_args()
