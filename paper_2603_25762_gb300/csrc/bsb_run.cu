@@ -474,18 +474,28 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
         float4* qc = a.xq + quad0(it, c);
         uint32_t out[16];
         float xo[16], yo[16];
+        const float2 dtc0_2 = make_float2(dtc0, dtc0), dta0_2 = make_float2(dta0, dta0);
+        const float2 inv_2 = make_float2(inv, inv), dtcx_2 = make_float2(dtcx, dtcx);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {  // branch-free update and wall
-          const float x0 = xb[c][j];
+        for (int j = 0; j < 16; j += 2) {  // element pairs on the packed FP32x2 pipe
+          const float2 x0 = make_float2(xb[c][j], xb[c][j + 1]);
+          const float2 acc = make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1]));
           // adiabatic SB: -(x^2 + a0 - a(t)); no walls
-          const float cx = SB == QH_SB_ADIABATIC ? dtcx - a.dt * x0 * x0 : dtcx;
-          const float y1 = fmaf(dtc0, __uint_as_float(v[j]), cx * x0);
-          const float x1 = fmaf(dta0, y1, x0);
-          const bool wall = SB != QH_SB_ADIABATIC && fabsf(x1) > 1.f;
-          xo[j] = wall ? copysignf(1.f, x1) : x1;
-          yo[j] = wall ? 0.f : y1;
+          float2 cx = dtcx_2;
+          if (SB == QH_SB_ADIABATIC)
+            cx = __ffma2_rn(make_float2(-a.dt * x0.x, -a.dt * x0.y), x0, dtcx_2);
+          const float2 y1 = __ffma2_rn(dtc0_2, acc, __fmul2_rn(cx, x0));
+          const float2 x1 = __ffma2_rn(dta0_2, y1, x0);
+          const bool w0 = SB != QH_SB_ADIABATIC && fabsf(x1.x) > 1.f;
+          const bool w1 = SB != QH_SB_ADIABATIC && fabsf(x1.y) > 1.f;
+          xo[j] = w0 ? copysignf(1.f, x1.x) : x1.x;
+          xo[j + 1] = w1 ? copysignf(1.f, x1.y) : x1.y;
+          yo[j] = w0 ? 0.f : y1.x;
+          yo[j + 1] = w1 ? 0.f : y1.y;
           // padding vertices hold x = y = 0 and J rows of zeros: their y stays 0
-          out[j] = __float_as_uint(yo[j] * inv);
+          const float2 ys = __fmul2_rn(make_float2(yo[j], yo[j + 1]), inv_2);
+          out[j] = __float_as_uint(ys.x);
+          out[j + 1] = __float_as_uint(ys.y);
         }
         if (vr) {
 #pragma unroll
