@@ -178,7 +178,7 @@ __global__ void k_signs_vm(const float* __restrict__ x, int64_t n, int8_t* st) {
 // a time and broadcast by shuffle; each neighbour costs one 8-byte (BF16) or 16-byte
 // (FP32) load per lane, i.e. a contiguous replica slice per warp.
 template <bool BF16>
-__global__ void __launch_bounds__(256) k_step_csr(StepArgs a, const int64_t* __restrict__ prow,
+__global__ void __launch_bounds__(256, 2) k_step_csr(StepArgs a, const int64_t* __restrict__ prow,
                                                   const int32_t* __restrict__ pcol,
                                                   const float* __restrict__ pval,
                                                   const __nv_bfloat16* __restrict__ xh_in) {
@@ -209,24 +209,29 @@ __global__ void __launch_bounds__(256) k_step_csr(StepArgs a, const int64_t* __r
       const int ne = (e1 - e) < 32 ? (int)(e1 - e) : 32;
       const int32_t cl = lane < ne ? pcol[e + lane] : 0;
       const float vl = lane < ne ? pval[e + lane] : 0.f;
-      // lanes >= ne hold column 0 and J = 0: a valid address contributing nothing
-      for (int k = 0; k < ne; k += 4) {
-        int32_t cc[4];
-        float jv[4];
+      // lanes >= ne hold column 0 and J = 0: a valid address contributing nothing.
+      // NB neighbours per batch, all loads issued before the first FMA: the step is
+      // bound by the latency of these gathers (16 per batch measured slower than 8).
+      constexpr int NB = 8;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          cc[q] = __shfl_sync(0xffffffffu, cl, (k + q) & 31);
-          jv[q] = __shfl_sync(0xffffffffu, vl, (k + q) & 31);
+      for (int k = 0; k < 32; k += NB) {
+        if (k >= ne) break;
+        int32_t cc[NB];
+        float jv[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          cc[q] = __shfl_sync(0xffffffffu, cl, k + q);
+          jv[q] = __shfl_sync(0xffffffffu, vl, k + q);
           if (k + q >= ne) jv[q] = 0.f;
         }
         if (!on) continue;
         if (BF16) {
-          uint2 u[4];
+          uint2 u[NB];
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
+          for (int q = 0; q < NB; ++q)
             u[q] = *reinterpret_cast<const uint2*>(xh_in + (size_t)cc[q] * a.R + r);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < NB; ++q) {
             const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&u[q].x);
             const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&u[q].y);
             acc[0] = fmaf(jv[q], __low2float(lo), acc[0]);
@@ -235,12 +240,12 @@ __global__ void __launch_bounds__(256) k_step_csr(StepArgs a, const int64_t* __r
             acc[3] = fmaf(jv[q], __high2float(hi), acc[3]);
           }
         } else {
-          float4 xv[4];
+          float4 xv[NB];
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
+          for (int q = 0; q < NB; ++q)
             xv[q] = *reinterpret_cast<const float4*>(a.xin + (size_t)cc[q] * a.R + r);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < NB; ++q) {
             acc[0] = fmaf(jv[q], xv[q].x, acc[0]);
             acc[1] = fmaf(jv[q], xv[q].y, acc[1]);
             acc[2] = fmaf(jv[q], xv[q].z, acc[2]);
