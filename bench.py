@@ -54,23 +54,30 @@ class ClockSampler:
     def __init__(self, device=0):
         self.device = device
         self.proc = None
-        self.lines = []
+        self.lines = []  # (arrival time, csv line)
+        self.t_start = 0.0
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi takes a moment to start: let its first sample arrive before the
+            # timed region, then keep only the samples taken inside it
+            t_end = time.monotonic() + 3.0
+            while not self.lines and time.monotonic() < t_end and self.proc.poll() is None:
+                time.sleep(0.01)
         except OSError:
             self.proc = None
+        self.t_start = time.monotonic()
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
 
     def __exit__(self, *a):
         if self.proc:
@@ -83,7 +90,8 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        inside = [ln for t, ln in self.lines if t >= self.t_start]
+        for ln in inside or [ln for _, ln in self.lines[-1:]]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -120,6 +128,8 @@ WORKLOADS = {
 SEEDS = {"hifi_region": 1002, "ont_region": 1003, "batched_blocks": 1004,
          "chromosome_porec": 1005}
 REFINE_DEFAULT = {"ont-snp": 15, "chromosome-porec": 2}
+# default timed steps: about a second of timed work (several clock samples) per workload
+STEPS_DEFAULT = {"hifi-region": 40, "ont-snp": 10, "batched-blocks": 4, "chromosome-porec": 3}
 
 
 def _workload(args):
@@ -139,13 +149,13 @@ def _workload(args):
     return fr, cfg, mode, R, T
 
 
-def cpu_baseline(args, fr, mode, steps, seed=1):
+def cpu_baseline(args, fr, mode, steps, seed=1, reps=None):
     """The FP64 oracle, as it stands, on the host cores: graph, blocks, bSB on a replica
     subset with the full step count, then voting or refinement + parity."""
     from oracle import oracle as o
     from paper_2603_25762_gb300 import synth
     o.build()
-    reps = args.ref_replicas
+    reps = min(reps or args.ref_replicas, args.ref_replicas)
     if args.workload == "hifi-region":
         sample_fr, what = fr, f"full graph ({fr.n_frags} reads)"
     elif args.workload == "chromosome-porec":
@@ -201,9 +211,16 @@ def run_reference(args):
     if rank != 0:
         return
     fr, cfg, mode, R, T = _workload(args)
+    # size each step's sample so that the whole warm-up + timed run stays near 150 s:
+    # one small calibration run, then replicas in proportion to the time left per step
+    t0 = time.perf_counter()
+    cpu_baseline(args, fr, mode, T, reps=8)
+    t_cal = time.perf_counter() - t0
+    per_step = max(1.0, (150.0 - t_cal) / (args.warmup + args.steps))
+    reps = max(8, int(8 * per_step / max(t_cal, 1e-3)) // 8 * 8)
     runs = []
     for i in range(args.warmup + args.steps):
-        cb, _ = cpu_baseline(args, fr, mode, T)
+        cb, _ = cpu_baseline(args, fr, mode, T, reps=reps)
         if i >= args.warmup:
             runs.append(cb)
     value = statistics.median([c["value"] for c in runs])
@@ -392,7 +409,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=0, help="0 = the workload's default")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16x2", "fp8", "fp32"])
@@ -408,6 +425,8 @@ def main():
     ap.add_argument("--step-kernel", default=None,
                     help="pin the BF16 step-kernel variant (default: autotune)")
     args = ap.parse_args()
+    if args.steps <= 0:
+        args.steps = STEPS_DEFAULT[args.workload]
     if args.impl == "reference":
         run_reference(args)
     else:
