@@ -135,7 +135,15 @@ STEPS_DEFAULT = {"hifi-region": 40, "ont-snp": 10, "batched-blocks": 4, "chromos
 def _workload(args):
     from paper_2603_25762_gb300 import synth
     gen, mode, R, T, desc = WORKLOADS[args.workload]
-    fr = getattr(synth, gen)(SEEDS[gen])
+    scale = getattr(args, "scale", 1.0)
+    if scale != 1.0:  # a reduced case of the same shape, for profiler captures
+        if gen == "batched_blocks":
+            fr = synth.batched_blocks(SEEDS[gen], n_blocks=max(1, int(round(512 * scale))))
+        else:
+            fr = getattr(synth, gen)(SEEDS[gen], scale=scale)
+        desc = f"{desc} [reduced: scale {scale}]"
+    else:
+        fr = getattr(synth, gen)(SEEDS[gen])
     R = args.replicas or R
     T = args.bsb_steps or T
     if args.refine_max <= 0:
@@ -146,6 +154,8 @@ def _workload(args):
            "sb_variant": getattr(args, "variant", "ballistic"),
            "linkage_k": getattr(args, "linkage_k", 10) if mode == "snp" else None,
            "l2": "flushed between timed steps (256 MiB write)"}
+    if scale != 1.0:
+        cfg["scale"] = scale
     return fr, cfg, mode, R, T
 
 
@@ -283,15 +293,20 @@ def run_ours(args):
     base, _ = multi.replica_range(rank, ws, R)
     stats = {}
 
-    def one_step(host=False, pinned=None):
+    def one_step(host=False, pinned=None, precision=None, collect=False):
+        """One pass of the whole path. collect=True also records the per-block figures
+        (block sizes, refinement iterations, best cuts): host loops kept out of the
+        timed steps."""
         t0 = time.perf_counter()
+        p = prec if precision is None else precision
         if host:
             g = ctx.build_graph(arrays=pinned, on_device=False, mode=gmode, linkage_k=args.linkage_k)
         else:
             g = ctx.build_graph(arrays=arrays_dev, on_device=True, mode=gmode, linkage_k=args.linkage_k)
         stats["build_ms"] = (time.perf_counter() - t0) * 1e3
-        sol = ctx.solve(g, replicas=R, steps=T, precision=prec, seed=1, replica_base=base,
-                        step_kernel=args.step_kernel, refine_max=args.refine_max,
+        sol = ctx.solve(g, replicas=R, steps=T, precision=p, seed=1, replica_base=base,
+                        step_kernel=args.step_kernel if p == prec else None,
+                        refine_max=args.refine_max,
                         variant=args.variant, dt=0.1 if args.variant == "adiabatic" else 1.0)
         if host:
             h = ctx.phase(g, sol, fr.n_snps)
@@ -304,17 +319,31 @@ def run_ours(args):
         stats["blocks"] = g.n_blocks
         stats["units"] = sol.timing()["spin_updates"]
         stats["nnz"] = g.nnz
-        bs = g.block_sizes()
-        its = [sol.block(b)["iterations"] for b in range(g.n_blocks)]
-        stats["spins"] = float(sum(bs)) * R  # spin states updated per step
-        stats["spin_solves"] = float(sum(n * i for n, i in zip(bs, its))) * R
+        if collect:
+            bs = g.block_sizes()
+            info = [sol.block(b) for b in range(g.n_blocks)]
+            stats["spins"] = float(sum(bs)) * R  # spin states updated per step
+            stats["spin_solves"] = float(sum(n * i["iterations"] for n, i in zip(bs, info))) * R
+            stats["best_cut_sum"] = float(sum(i["best_cut"] for i in info))
         sol.free()
         g.free()
         return h, cut
 
+    def quality(h):
+        """Phasing quality of one pass against the generator's truth (evaluation only)."""
+        from paper_2603_25762_gb300 import metrics
+        hap1, bid = h[0], h[2]
+        if isinstance(hap1, torch.Tensor):
+            hap1, bid = hap1.cpu().numpy(), bid.cpu().numpy()
+        se, he = metrics.switch_hamming(hap1, bid, fr.truth)
+        bid_ph = np.where(hap1 != 0, bid, -1)
+        return {"best_cut_sum": stats["best_cut_sum"], "switch_error": se, "hamming_error": he,
+                "n50_bp": metrics.n50(metrics.block_spans(bid_ph, fr.positions)),
+                "phased_fraction": metrics.completeness(hap1)}
+
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            one_step()
+        for i in range(args.warmup):
+            one_step(collect=i == args.warmup - 1)
         times, step_ms, launches = [], [], []
         parts = {"graph_build": [], "solve": [], "bsb_step_launches": [], "phase_and_host": []}
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -327,7 +356,7 @@ def run_ours(args):
                 flush.fill_(1)
                 stream.synchronize()
                 ev0.record(stream)
-                one_step()
+                h_last, _ = one_step()
                 ev1.record(stream)
                 ev1.synchronize()
                 times.append(ev0.elapsed_time(ev1))
@@ -352,13 +381,42 @@ def run_ours(args):
             one_step(host=True, pinned=pinned_np)
             e2e.append((time.perf_counter() - t0) * 1e3)
         n_kern = _count_kernels(lambda: one_step())  # cross-check from the CUDA activity trace
+        qual = quality(h_last)
+        # the same path with the plain FP32 SIMT step on the same GPU: the speedup of the
+        # low-precision path at equal best cut
+        vs_fp32 = None
+        if prec != qhap.PREC_FP32 and not args.no_fp32_leg:
+            saved = dict(stats)
+            one_step(precision=qhap.PREC_FP32, collect=True)
+            t32 = []
+            for _ in range(args.fp32_steps):
+                flush.fill_(1)
+                stream.synchronize()
+                ev0.record(stream)
+                h32, _ = one_step(precision=qhap.PREC_FP32)
+                ev1.record(stream)
+                ev1.synchronize()
+                t32.append(ev0.elapsed_time(ev1))
+            q32 = quality(h32)
+            ms32 = statistics.mean(t32)
+            vs_fp32 = {"fp32_ms_per_step": ms32, "fp32_kernel": stats["timing"]["kernel"],
+                       "fp32_value": stats["units"] * ws / (ms32 / 1e3),
+                       "fp32_steps": args.fp32_steps, "fp32_quality": q32}
+            stats.clear()
+            stats.update(saved)
     ms = statistics.mean(times)
     e2e_ms = statistics.mean(e2e)
     if ws > 1:  # the job's time is the slowest rank's
         ms = multi.max_over_ranks(ms)
         e2e_ms = multi.max_over_ranks(e2e_ms)
+        if vs_fp32 is not None:
+            vs_fp32["fp32_ms_per_step"] = multi.max_over_ranks(vs_fp32["fp32_ms_per_step"])
     if rank != 0:
         return
+    if vs_fp32 is not None:
+        vs_fp32["speedup"] = vs_fp32["fp32_ms_per_step"] / ms
+        c32 = vs_fp32["fp32_quality"]["best_cut_sum"]
+        vs_fp32["cut_ratio"] = qual["best_cut_sum"] / c32 if c32 else None
     hbm, bf16_tf, src = _peaks()
     launch_us = statistics.mean(step_ms) * 1e3
     # algorithmic bytes of the whole step loop: state traffic per spin update + each
@@ -393,6 +451,8 @@ def run_ours(args):
                      "launches_per_step": n_launch,
                      "avg_step_us": loop_us / steps_total,
                      "algorithmic_bytes_per_launch": per_launch_bytes},
+        "quality": qual,
+        "vs_fp32": vs_fp32,
         "gpu_launches": n_launched,
         "gpu_launches_trace_per_step": n_kern,
         "clocks": clk.summary(),
@@ -418,7 +478,12 @@ def main():
     ap.add_argument("--bsb-steps", type=int, default=0, help="0 = the workload's")
     ap.add_argument("--refine-max", type=int, default=0, help="0 = the workload's (SNP graphs)")
     ap.add_argument("--ref-replicas", type=int, default=1024)
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="reduced workload of the same shape (profiler captures only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-leg", action="store_true",
+                    help="skip timing the same path with the FP32 SIMT step")
+    ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--variant", default="ballistic", choices=["ballistic", "discrete", "adiabatic"],
                     help="simulated-bifurcation variant (the paper's solver is ballistic)")
     ap.add_argument("--linkage-k", type=int, default=10, help="SNP graphs: linkage depth k/10")
@@ -427,6 +492,7 @@ def main():
     args = ap.parse_args()
     if args.steps <= 0:
         args.steps = STEPS_DEFAULT[args.workload]
+    args.warmup = max(1, args.warmup)  # the last warm-up pass records the per-block figures
     if args.impl == "reference":
         run_reference(args)
     else:

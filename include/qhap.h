@@ -190,10 +190,14 @@ typedef struct {
   int32_t patience;     /* stop a block after this many checks without a better
                            best-replica energy (0 = never stop early) */
   int32_t refine_max;   /* SNP mode: maximum refinement iterations (>= 1) */
-  int32_t step_kernel;  /* BF16: -1 = autotune, else a variant index 0..9 (see
-                           qh_solution_kernel for names; 6..9 are the multi-step
-                           kernels that keep y on chip and launch once per step
-                           range); invalid choices -> QH_EINVAL */
+  int32_t step_kernel;  /* -1 = default.  Tile storage, BF16: autotuned by default,
+                           else a variant index 0..9 (see qh_solution_kernel for
+                           names; 6..9 are the multi-step kernels that keep y on
+                           chip and launch once per step range).  CSR storage
+                           (FP32 or BF16): 10 = 4 replicas per lane (R a multiple
+                           of 4), 11 = 8 replicas per lane, several neighbours per
+                           warp at once (R a multiple of 8); default 11 for BF16
+                           when R allows, else 10.  Invalid choices -> QH_EINVAL */
   int32_t sb_variant;   /* QH_SB_BALLISTIC (0, the paper's solver), QH_SB_DISCRETE,
                            QH_SB_ADIABATIC */
 } qh_bsb_opts;
@@ -289,8 +293,8 @@ qh_status qh_debug_steps(qh_ctx* ctx, const qh_graph* g, int32_t precision, int3
                          float* x, float* y, int32_t t0, int32_t nsteps, int32_t steps, double dt,
                          double a0, const double* c0_per_block);
 
-/* qh_debug_steps with an explicit step kernel (BF16 / BF16X2 tile storage only) and
- * SB variant (QH_SB_*; not FP8, not CSR):
+/* qh_debug_steps with an explicit step kernel (BF16 / BF16X2 tile storage: 0..9;
+ * CSR storage, FP32 or BF16: 10 or 11) and SB variant (QH_SB_*; not FP8, not CSR):
  * step_kernel = -1 is the default; otherwise an index into the solver's kernel
  * variants (qh_bsb_opts.step_kernel).  The multi-step variants run all `nsteps`
  * steps in ONE launch, the momentum y held on chip between steps.  QH_EINVAL when

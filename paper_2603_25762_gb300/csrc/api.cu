@@ -112,14 +112,14 @@ qh_status run_step(Ctx* ctx, const Graph& g, int precision, const TcPlan& plan, 
     a.xin = x_cur_f32;
     a.xout = x_next_f32;
     if (g.csr_mode)
-      launch_step_csr(ctx->stream, g, a, g.pval, nullptr);
+      launch_step_csr(ctx->stream, g, a, g.pval, nullptr, plan.variant);
     else
       launch_step_f32(ctx->stream, g, a);
     return QH_OK;
   }
   a.xh_out = xh_next;
   if (g.csr_mode) {
-    launch_step_csr(ctx->stream, g, a, g.pval, xh_cur);
+    launch_step_csr(ctx->stream, g, a, g.pval, xh_cur, plan.variant);
     return QH_OK;
   }
   return launch_step_tc(ctx, g, a, xh_cur, plan);
@@ -453,6 +453,9 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   const TcPlan plan = pick_plan(R);
   if (G.csr_mode && R % 4 != 0)
     return set_err(ctx, QH_EINVAL, "CSR storage needs replicas to be a multiple of 4");
+  if (o->step_kernel >= 0 && (G.csr_mode != (o->step_kernel >= CSR_LANE4) ||
+                              (G.csr_mode && !csr_variant_ok(o->step_kernel, R))))
+    return set_err(ctx, QH_EINVAL, "step_kernel variant not valid for this graph storage and R");
   if (is_tc_precision(o->precision) && !G.csr_mode && !tc_plan_ok(R, plan))
     return set_err(ctx, QH_EINVAL, "BF16 precision needs replicas to be a multiple of 64");
   cudaSetDevice(ctx->device);
@@ -651,7 +654,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   a.inv_scale = 1.f / f8_s;
   if (is_tc_precision(o->precision)) {
     qh_status st = QH_OK;
-    if (o->step_kernel >= 0) {
+    if (o->step_kernel >= 0 && !G.csr_mode) {
       tplan.variant = o->step_kernel;
     } else if (!G.csr_mode) {
       if (!tuned_variant(ctx, G, R, o->sb_variant, &tplan)) {  // first solve of this shape: time the variants
@@ -667,7 +670,9 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
       return st;
     }
   }
-  sol.kernel = G.csr_mode ? (is_tc_precision(o->precision) ? "csr-warp-bf16" : "csr-warp-fp32")
+  if (G.csr_mode)
+    tplan.variant = o->step_kernel >= 0 ? o->step_kernel : csr_default_variant(o->precision, R);
+  sol.kernel = G.csr_mode ? csr_variant_name(tplan.variant, is_tc_precision(o->precision))
               : fp8 ? (R % 128 == 0 ? "e4m3-bn128-s2-x3" : "e4m3-bn64-s2-x4")
               : is_tc_precision(o->precision) ? tc_variant_name(tplan.variant) : "k_step_f32";
   skey += "|v" + std::to_string(tplan.variant);
@@ -1080,12 +1085,13 @@ qh_status qh_debug_matvec(qh_ctx* h, const qh_graph* gh, int32_t precision, int3
     QH_CUDA_TRY(cudaMemsetAsync(zt, 0, NS * 4, ctx->stream));
     launch_transpose(ctx->stream, x, xt, R, g.n_pad);
     a.z_out = zt;
+    const int cv = csr_default_variant(precision, R);
     if (precision == QH_PREC_FP32) {
       a.xin = xt;
-      launch_step_csr(ctx->stream, g, a, g.pval, nullptr);
+      launch_step_csr(ctx->stream, g, a, g.pval, nullptr, cv);
     } else {
       launch_f32_to_bf16(ctx->stream, xt, xh, (int64_t)NS);
-      launch_step_csr(ctx->stream, g, a, g.pval, xh);
+      launch_step_csr(ctx->stream, g, a, g.pval, xh, cv);
     }
     launch_transpose(ctx->stream, zt, z, g.n_pad, R);
     QH_CUDA_TRY(cudaGetLastError());
@@ -1143,7 +1149,10 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
   a.sb = sb_variant;
   if (sb_variant != QH_SB_BALLISTIC && (precision == QH_PREC_FP8 || g.csr_mode))
     return set_err(ctx, QH_EUNSUPPORTED, "discrete / adiabatic SB need FP32 or BF16 tile storage");
-  if (step_kernel >= 0) {
+  if (step_kernel >= 0 && g.csr_mode) {
+    if (!csr_variant_ok(step_kernel, R))
+      return set_err(ctx, QH_EINVAL, "step_kernel variant not valid for this graph, precision and R");
+  } else if (step_kernel >= 0) {
     if (!is_tc_precision(precision) || g.csr_mode || step_kernel >= tc_n_variants() ||
         !tc_variant_ok(step_kernel, g, R, ctx->n_sm, a.use_lo != 0) ||
         !sb_kernel_ok(step_kernel, sb_variant))
@@ -1160,6 +1169,7 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
   cudaStream_t s = ctx->stream;
   float* xu = x;  // user buffers in [R][n_pad]
   float* yu = y;
+  const int csr_v = step_kernel >= 0 ? step_kernel : csr_default_variant(precision, R);
   if (g.csr_mode) {
     if (R % 4 != 0) return set_err(ctx, QH_EINVAL, "CSR storage needs R to be a multiple of 4");
     x = (float*)ctx->scratch(NS * 4, S_TR0);
@@ -1179,7 +1189,7 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
       a.xin = (k % 2 == 0) ? x : x1;
       a.xout = (k % 2 == 0) ? x1 : x;
       if (g.csr_mode)
-        launch_step_csr(s, g, a, g.pval, nullptr);
+        launch_step_csr(s, g, a, g.pval, nullptr, csr_v);
       else
         launch_step_f32(s, g, a);
     }
@@ -1234,7 +1244,7 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
       a.t = t0 + k;
       a.xh_out = (k % 2 == 0) ? xh1 : xh0;
       if (g.csr_mode) {
-        launch_step_csr(s, g, a, g.pval, (k % 2 == 0) ? xh0 : xh1);
+        launch_step_csr(s, g, a, g.pval, (k % 2 == 0) ? xh0 : xh1, csr_v);
         continue;
       }
       st = launch_step_tc(ctx, g, a, (k % 2 == 0) ? xh0 : xh1, plan);

@@ -178,7 +178,7 @@ __global__ void k_signs_vm(const float* __restrict__ x, int64_t n, int8_t* st) {
 // a time and broadcast by shuffle; each neighbour costs one 8-byte (BF16) or 16-byte
 // (FP32) load per lane, i.e. a contiguous replica slice per warp.
 template <bool BF16>
-__global__ void __launch_bounds__(256, 2) k_step_csr(StepArgs a, const int64_t* __restrict__ prow,
+__global__ void __launch_bounds__(256, 4) k_step_csr(StepArgs a, const int64_t* __restrict__ prow,
                                                   const int32_t* __restrict__ pcol,
                                                   const float* __restrict__ pval,
                                                   const __nv_bfloat16* __restrict__ xh_in) {
@@ -205,13 +205,19 @@ __global__ void __launch_bounds__(256, 2) k_step_csr(StepArgs a, const int64_t* 
     const int32_t r = r0 + 4 * lane;
     const bool on = r < a.R;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    // the next 32-edge group's columns and weights load while this group's gathers
+    // are in flight (they stream from DRAM); lanes past the row's end hold column 0 and
+    // J = 0: a valid address contributing nothing
+    int32_t cl_n = e0 + lane < e1 ? pcol[e0 + lane] : 0;
+    float vl_n = e0 + lane < e1 ? pval[e0 + lane] : 0.f;
     for (int64_t e = e0; e < e1; e += 32) {
       const int ne = (e1 - e) < 32 ? (int)(e1 - e) : 32;
-      const int32_t cl = lane < ne ? pcol[e + lane] : 0;
-      const float vl = lane < ne ? pval[e + lane] : 0.f;
-      // lanes >= ne hold column 0 and J = 0: a valid address contributing nothing.
+      const int32_t cl = cl_n;
+      const float vl = vl_n;
+      cl_n = e + 32 + lane < e1 ? pcol[e + 32 + lane] : 0;
+      vl_n = e + 32 + lane < e1 ? pval[e + 32 + lane] : 0.f;
       // NB neighbours per batch, all loads issued before the first FMA: the step is
-      // bound by the latency of these gathers (16 per batch measured slower than 8).
+      // bound by the latency of these gathers (16 per batch measured slower than 8)
       constexpr int NB = 8;
 #pragma unroll
       for (int k = 0; k < 32; k += NB) {
@@ -222,7 +228,6 @@ __global__ void __launch_bounds__(256, 2) k_step_csr(StepArgs a, const int64_t* 
         for (int q = 0; q < NB; ++q) {
           cc[q] = __shfl_sync(0xffffffffu, cl, k + q);
           jv[q] = __shfl_sync(0xffffffffu, vl, k + q);
-          if (k + q >= ne) jv[q] = 0.f;
         }
         if (!on) continue;
         if (BF16) {
@@ -276,6 +281,153 @@ __global__ void __launch_bounds__(256, 2) k_step_csr(StepArgs a, const int64_t* 
       u.x = *reinterpret_cast<uint32_t*>(&p0);
       u.y = *reinterpret_cast<uint32_t*>(&p1);
       *reinterpret_cast<uint2*>(a.xh_out + idx) = u;
+    }
+  }
+}
+
+// The CSR step for R a multiple of 8: each lane owns 8 consecutive replicas (one
+// 16-byte X_hat load per neighbour for BF16 operands, two for FP32), L = 32 / P lanes
+// cover one neighbour's replica row, and the warp walks P neighbours of its vertex at
+// once (P = 2 at R = 128).  The P partial sums meet in a shuffle butterfly; the lanes
+// of the first neighbour stream then apply the update.  Per neighbour this costs about
+// half the instructions of k_step_csr: two shuffles, one address, the loads and four
+// packed FP32x2 FMAs per lane.  Both CSR kernels are bound by the latency of the
+// gathers: they run at 64 registers, 4 CTAs (32 warps) per SM, a few bytes spilled in
+// some instantiations, which measured faster than 3 CTAs without spills.
+template <bool BF16, int P>
+__global__ void __launch_bounds__(256, 4) k_step_csr8(StepArgs a, const int64_t* __restrict__ prow,
+                                                   const int32_t* __restrict__ pcol,
+                                                   const float* __restrict__ pval,
+                                                   const __nv_bfloat16* __restrict__ xh_in) {
+  constexpr int L = 32 / P;                 // lanes per neighbour row
+  constexpr int NB0 = BF16 ? 8 : 4;
+  constexpr int NB = NB0 < 32 / P ? NB0 : 32 / P;  // neighbours per lane per batch
+  constexpr int STEP = P * NB;                       // edges per batch, at most 32
+  static_assert(STEP <= 32 && 32 % STEP == 0, "batches tile the 32-edge group");
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / L, li = lane % L;
+  if (row >= a.n_pad) return;
+  const RowTile rt = a.rt[row / TILE];
+  const int32_t sb = a.steps_b[rt.block];
+  const bool live = (a.active == nullptr || a.active[rt.block]) && a.t < sb;
+  if (row - rt.row0 >= rt.valid) return;  // padding vertex: state stays zero
+  const size_t rbase = (size_t)row * a.R;
+  if (!live) {
+    if (!BF16 && a.z_out == nullptr && a.xout != a.xin)  // carry a frozen block forward
+      for (int32_t r = 4 * lane; r < a.R; r += 128)
+        *reinterpret_cast<float4*>(a.xout + rbase + r) =
+            *reinterpret_cast<const float4*>(a.xin + rbase + r);
+    return;
+  }
+  const int64_t e0 = prow[row], e1 = prow[row + 1];
+  const double at = a.a0 * (double)a.t / (double)sb;
+  const float coef_x = (float)(-(a.a0 - at));
+  const float c0 = a.c0[rt.block];
+  for (int32_t r0 = 0; r0 < a.R; r0 += 8 * L) {
+    const int32_t r = r0 + 8 * li;
+    const bool on = r < a.R;
+    float2 acc[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] = make_float2(0.f, 0.f);
+    // next group's columns and weights prefetched as in k_step_csr
+    int32_t cl_n = e0 + lane < e1 ? pcol[e0 + lane] : 0;
+    float vl_n = e0 + lane < e1 ? pval[e0 + lane] : 0.f;
+    for (int64_t e = e0; e < e1; e += 32) {
+      const int ne = (e1 - e) < 32 ? (int)(e1 - e) : 32;
+      const int32_t cl = cl_n;
+      const float vl = vl_n;
+      cl_n = e + 32 + lane < e1 ? pcol[e + 32 + lane] : 0;
+      vl_n = e + 32 + lane < e1 ? pval[e + 32 + lane] : 0.f;
+#pragma unroll
+      for (int k = 0; k < 32; k += STEP) {
+        if (k >= ne) break;
+        int32_t cc[NB];
+        float jv[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          const int src = k + q * P + sub;  // < 32: STEP divides 32
+          cc[q] = __shfl_sync(0xffffffffu, cl, src);
+          jv[q] = __shfl_sync(0xffffffffu, vl, src);
+        }
+        if (!on) continue;
+        if (BF16) {
+          uint4 u[NB];
+#pragma unroll
+          for (int q = 0; q < NB; ++q)
+            u[q] = *reinterpret_cast<const uint4*>(xh_in + (size_t)cc[q] * a.R + r);
+#pragma unroll
+          for (int q = 0; q < NB; ++q) {
+            const float2 j2 = make_float2(jv[q], jv[q]);
+            const uint32_t w[4] = {u[q].x, u[q].y, u[q].z, u[q].w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)  // BF16 pair -> two FP32 values, exactly
+              acc[j] = __ffma2_rn(j2, make_float2(__uint_as_float(w[j] << 16),
+                                                  __uint_as_float(w[j] & 0xffff0000u)), acc[j]);
+          }
+        } else {
+          float4 xv[NB][2];
+#pragma unroll
+          for (int q = 0; q < NB; ++q) {
+            const float4* src4 = reinterpret_cast<const float4*>(a.xin + (size_t)cc[q] * a.R + r);
+            xv[q][0] = src4[0];
+            xv[q][1] = src4[1];
+          }
+#pragma unroll
+          for (int q = 0; q < NB; ++q) {
+            const float2 j2 = make_float2(jv[q], jv[q]);
+            acc[0] = __ffma2_rn(j2, make_float2(xv[q][0].x, xv[q][0].y), acc[0]);
+            acc[1] = __ffma2_rn(j2, make_float2(xv[q][0].z, xv[q][0].w), acc[1]);
+            acc[2] = __ffma2_rn(j2, make_float2(xv[q][1].x, xv[q][1].y), acc[2]);
+            acc[3] = __ffma2_rn(j2, make_float2(xv[q][1].z, xv[q][1].w), acc[3]);
+          }
+        }
+      }
+    }
+    // the P neighbour streams of the same replicas meet
+#pragma unroll
+    for (int off = 16; off >= L; off >>= 1)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, off);
+        acc[j].y += __shfl_xor_sync(0xffffffffu, acc[j].y, off);
+      }
+    if (!on || sub != 0) continue;
+    const size_t idx = rbase + r;
+    float zs[8] = {acc[0].x, acc[0].y, acc[1].x, acc[1].y, acc[2].x, acc[2].y, acc[3].x, acc[3].y};
+    if (a.z_out != nullptr) {
+      *reinterpret_cast<float4*>(a.z_out + idx) = make_float4(zs[0], zs[1], zs[2], zs[3]);
+      *reinterpret_cast<float4*>(a.z_out + idx + 4) = make_float4(zs[4], zs[5], zs[6], zs[7]);
+      continue;
+    }
+    const float* xsrc = BF16 ? a.x : a.xin;
+    float xs[8], ys[8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float4 xv = *reinterpret_cast<const float4*>(xsrc + idx + 4 * h);
+      const float4 yv = *reinterpret_cast<const float4*>(a.y + idx + 4 * h);
+      xs[4 * h] = xv.x; xs[4 * h + 1] = xv.y; xs[4 * h + 2] = xv.z; xs[4 * h + 3] = xv.w;
+      ys[4 * h] = yv.x; ys[4 * h + 1] = yv.y; ys[4 * h + 2] = yv.z; ys[4 * h + 3] = yv.w;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sb_update(a.sb, zs[j], xs[j], ys[j], a.dt, coef_x, a.dta0, c0);
+    float* xdst = BF16 ? a.x : a.xout;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      *reinterpret_cast<float4*>(xdst + idx + 4 * h) =
+          make_float4(xs[4 * h], xs[4 * h + 1], xs[4 * h + 2], xs[4 * h + 3]);
+      *reinterpret_cast<float4*>(a.y + idx + 4 * h) =
+          make_float4(ys[4 * h], ys[4 * h + 1], ys[4 * h + 2], ys[4 * h + 3]);
+    }
+    if (BF16) {
+      uint4 u;
+      uint32_t* uw = &u.x;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        __nv_bfloat162 p2 = __floats2bfloat162_rn(xs[2 * j], xs[2 * j + 1]);
+        uw[j] = *reinterpret_cast<uint32_t*>(&p2);
+      }
+      *reinterpret_cast<uint4*>(a.xh_out + idx) = u;
     }
   }
 }
@@ -744,10 +896,33 @@ void launch_step_f32(cudaStream_t s, const Graph& g, const StepArgs& a) {
   k_step_f32<<<::qh::counted(grid), 256, 0, s>>>(a);
 }
 
+const char* csr_variant_name(int v, bool bf16) {
+  if (v == CSR_LANE8) return bf16 ? "csr-lane8-bf16" : "csr-lane8-fp32";
+  return bf16 ? "csr-lane4-bf16" : "csr-lane4-fp32";
+}
+
 void launch_step_csr(cudaStream_t s, const Graph& g, const StepArgs& a, const float* pval,
-                     const __nv_bfloat16* xh_in) {
+                     const __nv_bfloat16* xh_in, int variant) {
   if (g.n_pad == 0) return;
   const unsigned grid = nblk((int64_t)g.n_pad * 32);
+  if (variant == CSR_LANE8 && a.R % 8 == 0) {
+    // lanes per neighbour row: 8 replicas each, at most a warp
+    const int lanes = a.R >= 256 ? 32 : a.R >= 128 ? 16 : a.R >= 64 ? 8 : 4;
+#define QH_CSR8(P)                                                                              \
+  (xh_in != nullptr                                                                             \
+       ? k_step_csr8<true, P><<<::qh::counted(grid), 256, 0, s>>>(a, g.prow_ptr, g.pcol, pval,  \
+                                                                   xh_in)                        \
+       : k_step_csr8<false, P><<<::qh::counted(grid), 256, 0, s>>>(a, g.prow_ptr, g.pcol, pval, \
+                                                                    nullptr))
+    switch (lanes) {
+      case 32: QH_CSR8(1); break;
+      case 16: QH_CSR8(2); break;
+      case 8: QH_CSR8(4); break;
+      default: QH_CSR8(8); break;
+    }
+#undef QH_CSR8
+    return;
+  }
   if (xh_in != nullptr)
     k_step_csr<true><<<::qh::counted(grid), 256, 0, s>>>(a, g.prow_ptr, g.pcol, pval, xh_in);
   else

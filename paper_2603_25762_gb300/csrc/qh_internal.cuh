@@ -239,9 +239,22 @@ void launch_x_operand(cudaStream_t s, const Graph& g, int32_t sb, const float* x
                       __nv_bfloat16* xh, int64_t n);
 void launch_step_f32(cudaStream_t s, const Graph& g, const StepArgs& a);
 // CSR storage: warp per padded vertex, state [n_pad][R]; xh_in != nullptr selects the
-// BF16 X_hat operand, otherwise a.xin (FP32).
+// BF16 X_hat operand, otherwise a.xin (FP32).  variant: CSR_LANE4 (4 replicas per lane,
+// any R that is a multiple of 4) or CSR_LANE8 (8 per lane, several neighbours per warp
+// at once; R a multiple of 8).
+constexpr int CSR_LANE4 = 10;
+constexpr int CSR_LANE8 = 11;
+inline bool csr_variant_ok(int v, int R) {
+  return v == CSR_LANE4 ? R % 4 == 0 : v == CSR_LANE8 ? R % 8 == 0 : false;
+}
+// Default: 8 replicas per lane for BF16 operands (fewer instructions per gathered
+// neighbour), 4 per lane for FP32 operands (fewer registers, more warps in flight).
+inline int csr_default_variant(int precision, int R) {
+  return (precision != QH_PREC_FP32 && R % 8 == 0) ? CSR_LANE8 : CSR_LANE4;
+}
+const char* csr_variant_name(int v, bool bf16);
 void launch_step_csr(cudaStream_t s, const Graph& g, const StepArgs& a, const float* pval,
-                     const __nv_bfloat16* xh_in);
+                     const __nv_bfloat16* xh_in, int variant);
 void launch_transpose(cudaStream_t s, const float* in, float* out, int64_t rows, int64_t cols);
 void launch_signs(cudaStream_t s, const Graph& g, int32_t R, const float* x, int8_t* signs_t);
 void launch_cut(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t, const double* w,

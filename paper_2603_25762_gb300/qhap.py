@@ -55,7 +55,9 @@ SB_VARIANTS = {"ballistic": 0, "discrete": 1, "adiabatic": 2}
 STEP_KERNELS = ["cta-bn128-s3", "cta-bn128-s2-x3", "cta-bn64-s2-x4", "cta-bn256-s2-x2",
                 "persistent-bn128", "persistent-bn64-tma-state",
                 "multistep-jres-group", "multistep-stream-tile", "multistep-jres-tile",
-                "multistep-stream-group"]
+                "multistep-stream-group",
+                # CSR storage (FP32 or BF16): 4 or 8 replicas per lane
+                "csr-lane4", "csr-lane8"]
 
 
 class QhError(RuntimeError):
@@ -260,7 +262,9 @@ class Context:
     def solve(self, g, replicas=32, steps=1000, precision=PREC_FP32, seed=1, dt=1.0, a0=1.0,
               c0=0.0, schedule=SCHED_LINEAR, replica_base=0, check_every=0, patience=0,
               refine_max=15, step_kernel=None, variant="ballistic"):
-        """step_kernel: None = autotune, or a name from STEP_KERNELS (BF16 only).
+        """step_kernel: None = the default (autotuned on BF16 tile storage), or a name
+        from STEP_KERNELS: the tile variants for BF16 tile storage, "csr-lane4" /
+        "csr-lane8" for CSR storage.
         variant: "ballistic" (bSB), "discrete" (dSB) or "adiabatic" (aSB)."""
         sk = -1 if step_kernel is None else STEP_KERNELS.index(step_kernel)
         o = QhBsbOpts(replicas, steps, schedule, precision, dt, a0, c0, seed, replica_base,

@@ -1,0 +1,67 @@
+"""Host-side logic of bench.py (no GPU): the clock sampler's parsing and its restriction
+to the timed region, the per-workload defaults, and the profiled-traffic lookup that a
+changed kernel source must invalidate."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _line(sm, mx, hw="Not Active", pc="Not Active"):
+    return f"0, {sm}, {mx}, 900.0, 0x0, {hw}, Not Active, Not Active, {pc}"
+
+
+def test_clock_summary_keeps_samples_inside_timed_region(bench):
+    c = bench.ClockSampler()
+    c.lines = [(0.5, _line(345, 2070)), (1.5, _line(2070, 2070)), (1.6, _line(2055, 2070)),
+               (1.7, _line(2070, 2070, pc="Active"))]
+    c.t_start = 1.0
+    s = c.summary()
+    assert s["samples"] == 3  # the idle sample before the region is dropped
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_summary_reports_slowdown_and_falls_back_to_last_sample(bench):
+    c = bench.ClockSampler()
+    c.lines = [(0.1, _line(1500, 2070, hw="Active"))]
+    c.t_start = 5.0  # nothing arrived inside: the last sample stands in
+    s = c.summary()
+    assert s["samples"] == 1 and s["reasons"] == ["hw_slowdown"] and s["sm_mhz"] == 1500.0
+    c.lines = [(6.0, "garbage"), (6.1, "0, [N/A], [N/A], 1, 2, 3, 4, 5, 6")]
+    assert c.summary()["samples"] == 0
+
+
+def test_workload_tables_agree(bench):
+    assert set(bench.STEPS_DEFAULT) == set(bench.WORKLOADS)
+    assert all(k >= 1 for k in bench.STEPS_DEFAULT.values())
+    for gen, *_ in bench.WORKLOADS.values():
+        assert gen in bench.SEEDS
+
+
+def test_profiled_traffic_tracks_kernel_source(bench, tmp_path, monkeypatch):
+    import hashlib
+    prof = tmp_path / "profiles"
+    src = tmp_path / "paper_2603_25762_gb300" / "csrc"
+    prof.mkdir()
+    src.mkdir(parents=True)
+    (src / "bsb_run.cu").write_text("// kernel v1\n")
+    sha = hashlib.sha256(b"// kernel v1\n").hexdigest()[:16]
+    (prof / "multistep_kernel_hifi_region.md").write_text(
+        f"kernel: multistep-stream-tile\nsource_sha256_16: {sha}\n"
+        "traffic_bytes_per_launch: 1234\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._profiled_traffic("multistep-stream-tile") == 1234
+    assert bench._profiled_traffic("multistep-jres-group") is None  # another variant
+    (src / "bsb_run.cu").write_text("// kernel v2\n")
+    assert bench._profiled_traffic("multistep-stream-tile") is None  # source changed

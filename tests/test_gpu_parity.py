@@ -249,6 +249,40 @@ def test_matvec_snp_graph_hilo(q, ctx, oracle):
 def test_steps_match_oracle(q, ctx, oracle, precision, tol, storage):
     if precision == 3 and storage == 2:
         pytest.skip("FP8 runs on tile storage only")
+    _steps_case(q, ctx, oracle, precision, tol, storage, 64 if precision != 3 else 128)
+
+
+@pytest.mark.parametrize("R,kernel", [(12, "csr-lane4"), (24, "csr-lane8"), (64, "csr-lane4"),
+                                      (192, "csr-lane8"), (384, "csr-lane8"), (384, "csr-lane4")])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-5), (1, 1e-2)])
+def test_csr_steps_replica_counts(q, ctx, oracle, precision, tol, R, kernel):
+    # the CSR step's lane layouts: 4 replicas per lane (R = 384: three passes), and
+    # 8 per lane with 8 (R = 24), 2 (R = 192, two passes) and 1 (R = 384, two passes)
+    # neighbours per warp at once
+    _steps_case(q, ctx, oracle, precision, tol, 2, R, kernel)
+
+
+def test_csr_variant_rejections(q, ctx):
+    import torch
+    fr = synth.tiny_reads(1001)
+    gc = ctx.build_graph(fr, storage=q.STORAGE_CSR)
+    gt = ctx.build_graph(fr)
+    with pytest.raises(RuntimeError):  # 8 replicas per lane needs R % 8 == 0
+        ctx.solve(gc, replicas=12, steps=10, precision=q.PREC_BF16, step_kernel="csr-lane8")
+    with pytest.raises(RuntimeError):  # a CSR variant on tile storage
+        ctx.solve(gt, replicas=64, steps=10, precision=q.PREC_BF16, step_kernel="csr-lane4")
+    with pytest.raises(RuntimeError):  # a tile variant on CSR storage
+        ctx.solve(gc, replicas=64, steps=10, precision=q.PREC_BF16, step_kernel="cta-bn128-s3")
+    n_pad, _, c0 = gc.layout()
+    x = torch.zeros((12, n_pad), dtype=torch.float32, device="cuda")
+    with pytest.raises(RuntimeError):
+        ctx.debug_steps(gc, q.PREC_FP32, 12, x, torch.zeros_like(x), 0, 1, 10, c0=c0,
+                        step_kernel="csr-lane8")
+    sol = ctx.solve(gc, replicas=12, steps=10, precision=q.PREC_FP32, step_kernel="csr-lane4")
+    assert sol.timing()["kernel"] == "csr-lane4-fp32"
+
+
+def _steps_case(q, ctx, oracle, precision, tol, storage, R, kernel=None):
     import torch
     fr = synth.hifi_region(1002, scale=0.06)
     g = ctx.build_graph(fr, mode=q.MODE_READ, storage=storage)
@@ -258,7 +292,6 @@ def test_steps_match_oracle(q, ctx, oracle, precision, tol, storage):
     # FP8's product error (~0.4% per step, within the 1e-2 per-step bar) compounds over
     # steps: its state is compared after one step, the others after three
     steps, nsteps, t0 = 200, (3 if precision != 3 else 1), 50
-    R = 64 if precision != 3 else 128
     x = np.zeros((R, n_pad), np.float32)
     y = np.zeros((R, n_pad), np.float32)
     refs = []
@@ -278,7 +311,7 @@ def test_steps_match_oracle(q, ctx, oracle, precision, tol, storage):
                                 c0=float(c0[b]))
         refs.append((nodes, x1, y1))
     xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
-    ctx.debug_steps(g, precision, R, xd, yd, t0, nsteps, steps, c0=c0)
+    ctx.debug_steps(g, precision, R, xd, yd, t0, nsteps, steps, c0=c0, step_kernel=kernel)
     xg, yg = xd.cpu().numpy(), yd.cpu().numpy()
     for nodes, x1, y1 in refs:
         xgb, ygb = xg[:, pidx[nodes]].astype(np.float64), yg[:, pidx[nodes]].astype(np.float64)
@@ -293,9 +326,11 @@ def test_steps_match_oracle(q, ctx, oracle, precision, tol, storage):
 
 
 # ----------------------------------------------------------------------------- full solve
-def _check_solve(q, ctx, oracle, fr, precision, R, steps, seed, n_oracle=None, storage=0):
+def _check_solve(q, ctx, oracle, fr, precision, R, steps, seed, n_oracle=None, storage=0,
+                 step_kernel=None):
     g = ctx.build_graph(fr, mode=q.MODE_READ, storage=storage)
-    sol = ctx.solve(g, replicas=R, steps=steps, precision=precision, seed=seed)
+    sol = ctx.solve(g, replicas=R, steps=steps, precision=precision, seed=seed,
+                    step_kernel=step_kernel)
     og = oracle.read_graph(fr, oracle.READ_SIGNED)
     blocks = oracle.blocks_of(og)
     spins = sol.spins(g.n_nodes)
@@ -369,13 +404,23 @@ def test_csr_storage_matvec(q, ctx, oracle, mode):
     assert e16 <= 1e-2, e16
 
 
+@pytest.mark.parametrize("R", [12, 24, 192, 384])
+def test_csr_matvec_replica_counts(q, ctx, oracle, R):
+    fr = synth.ont_region(1003, scale=0.06)
+    e32 = _matvec_case(q, ctx, oracle, fr, q.MODE_SNP, q.PREC_FP32, R, storage=q.STORAGE_CSR)
+    e16 = _matvec_case(q, ctx, oracle, fr, q.MODE_SNP, q.PREC_BF16, R, storage=q.STORAGE_CSR)
+    assert e32 <= 1e-5, e32
+    assert e16 <= 1e-2, e16
+
+
+@pytest.mark.parametrize("kernel", [None, "csr-lane4", "csr-lane8"])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_csr_storage_solve_vs_oracle(q, ctx, oracle, precision):
+def test_csr_storage_solve_vs_oracle(q, ctx, oracle, precision, kernel):
     _check_solve(q, ctx, oracle, synth.tiny_reads(1001), precision, 64, 2000, seed=11,
-                 storage=q.STORAGE_CSR)
+                 storage=q.STORAGE_CSR, step_kernel=kernel)
     g, sol = _check_solve(q, ctx, oracle, synth.hifi_region(1002, scale=0.1), precision, 128,
-                          1000, seed=3, n_oracle=16, storage=q.STORAGE_CSR)
-    assert g.n_tiles == 0 and sol.timing()["kernel"].startswith("csr-warp")
+                          1000, seed=3, n_oracle=16, storage=q.STORAGE_CSR, step_kernel=kernel)
+    assert g.n_tiles == 0 and sol.timing()["kernel"].startswith(kernel or "csr-lane")
 
 
 def test_csr_storage_early_stop(q, ctx):
@@ -433,7 +478,7 @@ def test_chromosome_porec_picks_csr(q, ctx):
     assert g.n_blocks >= 1 and g.block_sizes().max() > 0.9 * fr.n_snps
     sol = ctx.solve(g, replicas=64, steps=50, precision=q.PREC_BF16, seed=1, refine_max=1)
     h1, h2, bid = ctx.phase(g, sol, fr.n_snps)
-    assert sol.timing()["kernel"] == "csr-warp-bf16"
+    assert sol.timing()["kernel"] == "csr-lane8-bf16"
     assert (h1 != 0).mean() > 0.9
 
 
