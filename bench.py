@@ -186,7 +186,7 @@ def cpu_baseline(args, fr, mode, steps, seed=1, reps=None):
         units = sum(len(b) for b in res["blocks"]) * reps * steps
     else:
         res = o.phase_snp(sample_fr, range(reps), steps, seed=seed, refine_max=args.refine_max)
-        units = sum(len(b) * int(it) for b, it in zip(res["blocks"], res["iters"])) * reps * steps
+        units = sum(len(b) * int(k) for b, k in zip(res["blocks"], res["solves"])) * reps * steps
     dt = time.perf_counter() - t0
     return {"value": units / dt, "unit": "spin-updates/s", "cores": os.cpu_count(),
             "kind": "oracle",

@@ -83,6 +83,12 @@ def _setup(L):
     L.qo_sb_solve.argtypes = [I32, P, P, P, I32, P, I32, D, D, D, U64, I64, I32, P, P, P, I32]
     L.qo_refine.restype = I32
     L.qo_refine.argtypes = [I32, P, P, P, I32, P, I32, D, D, D, U64, I64, I32, P, P]
+    L.qo_sb_run_h.restype = None
+    L.qo_sb_run_h.argtypes = [I32, P, P, P, I32, P, P, I32, I32, I32, D, D, D, I32, D, P]
+    L.qo_sb_solve_h.restype = D
+    L.qo_sb_solve_h.argtypes = [I32, P, P, P, I32, P, I32, D, D, D, U64, I64, I32, P, P, P, I32, D]
+    L.qo_refine_h.restype = I32
+    L.qo_refine_h.argtypes = [I32, P, P, P, I32, P, I32, D, D, D, U64, I64, I32, P, P, D, I32, P]
     L.qo_vote.restype = None
     L.qo_vote.argtypes = [I32, I32, P, P, P, P, P, I32, P, P]
     L.qo_parity.restype = None
@@ -227,18 +233,22 @@ def bsb_init(n, replica_ids, seed, block, it=0):
 SB_VARIANTS = {"ballistic": 0, "discrete": 1, "adiabatic": 2}
 
 
-def bsb_run(g: CSR, x, y, t0, t1, steps, dt=1.0, a0=1.0, c0=None, variant="ballistic"):
+def bsb_run(g: CSR, x, y, t0, t1, steps, dt=1.0, a0=1.0, c0=None, variant="ballistic",
+            h=0.0, hdir=None):
     """Advance x, y ([R][n] float64, in place copies returned) by steps t0..t1-1 with J = -w.
 
     variant: "ballistic" (bSB), "discrete" (dSB: J sgn(x)), "adiabatic" (aSB: cubic
-    detuning, no walls)."""
+    detuning, no walls).  h, hdir: the deformation field h (1 - t / steps) hdir_i added
+    to the force on y (hdir in {-1, +1}^n, None = all +1)."""
     x = np.array(x, dtype=np.float64, order="C")
     y = np.array(y, dtype=np.float64, order="C")
     J = _c(-g.w, np.float64)
     if c0 is None:
         c0 = default_c0(g)
-    lib().qo_sb_run(g.n, _p(g.row_ptr), _p(g.col), _p(J), x.shape[0], _p(x), _p(y), t0, t1,
-                    steps, dt, a0, c0, SB_VARIANTS[variant])
+    hd = None if hdir is None else _c(hdir, np.float64)
+    lib().qo_sb_run_h(g.n, _p(g.row_ptr), _p(g.col), _p(J), x.shape[0], _p(x), _p(y), t0, t1,
+                      steps, dt, a0, c0, SB_VARIANTS[variant], h,
+                      _p(hd) if hd is not None else None)
     return x, y
 
 
@@ -254,27 +264,36 @@ def ising_energy(g: CSR, s):
 
 
 def bsb_solve(g: CSR, replica_ids, steps, seed, block=0, it=0, dt=1.0, a0=1.0, c0=0.0,
-              variant="ballistic"):
-    """Multi-replica SB (SB algorithm solution); returns (best_cut, spins, cuts, best_r)."""
+              variant="ballistic", h=0.0):
+    """Multi-replica SB (SB algorithm solution); returns (best_cut, spins, cuts, best_r).
+    h > 0: the deformation field along +1 on every vertex."""
     rid = _c(replica_ids, np.int32)
     R = rid.shape[0]
     s = np.zeros(g.n, np.int8)
     cuts = np.zeros(R)
     br = C.c_int32(-1)
-    best = lib().qo_sb_solve(g.n, _p(g.row_ptr), _p(g.col), _p(g.w), R, _p(rid), steps, dt, a0,
-                             c0, seed, block, it, _p(s), _p(cuts), C.byref(br),
-                             SB_VARIANTS[variant])
+    best = lib().qo_sb_solve_h(g.n, _p(g.row_ptr), _p(g.col), _p(g.w), R, _p(rid), steps, dt,
+                               a0, c0, seed, block, it, _p(s), _p(cuts), C.byref(br),
+                               SB_VARIANTS[variant], h)
     return best, s, cuts, br.value
 
 
-def refine(g: CSR, replica_ids, steps, seed, block=0, refine_max=15, dt=1.0, a0=1.0, c0=0.0):
-    """SNP-based iterative refinement: returns (C counts, iterations, first cut, gauged w)."""
+def refine(g: CSR, replica_ids, steps, seed, block=0, refine_max=15, dt=1.0, a0=1.0, c0=0.0,
+           deform_h=0.0, deform_tries=0, stats=None):
+    """SNP-based iterative refinement: returns (C counts, accepted partitions, first cut,
+    gauged w).  deform_h > 0: re-solve with the deformation field (up to deform_tries
+    times, strength deform_h 2^(k-1)) when a solve's cut is <= 0.  stats (a dict, if
+    given) receives "solves", the number of bSB solves made."""
     rid = _c(replica_ids, np.int32)
     w = g.w.copy()
     Cc = np.zeros(g.n, np.int32)
     first = C.c_double(0.0)
-    it = lib().qo_refine(g.n, _p(g.row_ptr), _p(g.col), _p(w), rid.shape[0], _p(rid), steps, dt,
-                         a0, c0, seed, block, refine_max, _p(Cc), C.byref(first))
+    solves = C.c_int32(0)
+    it = lib().qo_refine_h(g.n, _p(g.row_ptr), _p(g.col), _p(w), rid.shape[0], _p(rid), steps,
+                           dt, a0, c0, seed, block, refine_max, _p(Cc), C.byref(first),
+                           deform_h, deform_tries, C.byref(solves))
+    if stats is not None:
+        stats["solves"] = solves.value
     return Cc, it, first.value, w
 
 
@@ -316,22 +335,27 @@ def phase_read(fr, mode=READ_SIGNED, replica_ids=range(8), steps=1000, seed=1, d
 
 
 def phase_snp(fr, replica_ids=range(8), steps=1000, seed=1, refine_max=15, porec_alpha=0.1,
-              linkage_k=10, dt=1.0, a0=1.0, c0=0.0):
-    """Whole SNP-based path: graph -> blocks -> refinement (bSB per iteration) -> parity."""
+              linkage_k=10, dt=1.0, a0=1.0, c0=0.0, deform_h=0.0, deform_tries=0):
+    """Whole SNP-based path: graph -> blocks -> refinement (bSB per iteration) -> parity.
+    "iters": accepted partitions per block; "solves": bSB solves per block."""
     g = snp_graph(fr, porec_alpha, linkage_k)
     blocks = blocks_of(g)
     Ctot = np.zeros(fr.n_snps, np.int32)
     in_block = np.zeros(fr.n_snps, np.uint8)
     snp_block = -np.ones(fr.n_snps, np.int32)
-    iters, first_cuts = [], []
+    iters, first_cuts, solves = [], [], []
     for b, nodes in enumerate(blocks):
         sub = g.subgraph(nodes)
-        Cc, it, first, _ = refine(sub, list(replica_ids), steps, seed, b, refine_max, dt, a0, c0)
+        st = {}
+        Cc, it, first, _ = refine(sub, list(replica_ids), steps, seed, b, refine_max, dt, a0, c0,
+                                  deform_h, deform_tries, st)
         Ctot[nodes] = Cc
         in_block[nodes] = 1
         snp_block[nodes] = b
         iters.append(it)
+        solves.append(st["solves"])
         first_cuts.append(first)
     hap1 = parity(Ctot, in_block)
     return {"graph": g, "blocks": blocks, "C": Ctot, "hap1": hap1, "snp_block": snp_block,
-            "iters": np.array(iters), "first_cuts": np.array(first_cuts)}
+            "iters": np.array(iters), "solves": np.array(solves),
+            "first_cuts": np.array(first_cuts)}

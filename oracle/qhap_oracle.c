@@ -313,9 +313,26 @@ int32_t qo_components(int32_t n, const int64_t* rp, const int32_t* col, const do
  *                                (sgn(0) = +1, as for the spins)
  *   variant 2, adiabatic (aSB):  y += dt (-(x^2 + a0 - a(t)) x + c0 J x);
  *                                x += dt a0 y; no walls                        */
+void qo_sb_run_h(int32_t n, const int64_t* rp, const int32_t* col, const double* J, int32_t R,
+                 double* x, double* y, int32_t t0, int32_t t1, int32_t steps, double dt, double a0,
+                 double c0, int32_t variant, double h, const double* hdir);
+
 void qo_sb_run(int32_t n, const int64_t* rp, const int32_t* col, const double* J, int32_t R,
                double* x, double* y, int32_t t0, int32_t t1, int32_t steps, double dt, double a0,
                double c0, int32_t variant) {
+  qo_sb_run_h(n, rp, col, J, R, x, y, t0, t1, steps, dt, a0, c0, variant, 0.0, NULL);
+}
+
+/* The same with the deformation term of the SNP refinement's adaptive strategy (SB
+ * algorithm solution, SNP-based method: a term h added to escape local minima when
+ * the cut stays negative; the paper gives no formula).  Reading used here: a field
+ * along a direction d (d_i in {-1, +1}; NULL = all +1) whose strength falls linearly
+ * to zero over the schedule, added to the force on y:
+ *     y_i += dt (... + h (1 - t / steps) d_i)
+ * so the landscape is tilted toward d early and is the undeformed one at the end. */
+void qo_sb_run_h(int32_t n, const int64_t* rp, const int32_t* col, const double* J, int32_t R,
+                 double* x, double* y, int32_t t0, int32_t t1, int32_t steps, double dt, double a0,
+                 double c0, int32_t variant, double h, const double* hdir) {
 #pragma omp parallel for schedule(dynamic, 1)
   for (int32_t r = 0; r < R; ++r) {
     double* xr = x + (size_t)r * n;
@@ -332,10 +349,12 @@ void qo_sb_run(int32_t n, const int64_t* rp, const int32_t* col, const double* J
         }
         z[i] = acc;
       }
+      double ht = h * (1.0 - (double)t / (double)steps);
       for (int32_t i = 0; i < n; ++i) {
         double detune = a0 - at;
         if (variant == 2) detune += xr[i] * xr[i];
-        yr[i] += dt * (-detune * xr[i] + c0 * z[i]);
+        double field = ht * (hdir ? hdir[i] : 1.0);
+        yr[i] += dt * (-detune * xr[i] + c0 * z[i] + field);
       }
       for (int32_t i = 0; i < n; ++i) xr[i] += dt * a0 * yr[i];
       if (variant != 2)
@@ -400,10 +419,25 @@ double qo_ising_energy(int32_t n, const int64_t* rp, const int32_t* col, const d
 /* Full multi-replica bSB on one component with weights w (J = -w): returns the
  * best replica's spins (s = sgn(x), sgn(0) = +1), its cut, and every replica's
  * cut.  Ties between replicas go to the lowest replica index.               */
+double qo_sb_solve_h(int32_t n, const int64_t* rp, const int32_t* col, const double* w, int32_t R,
+                     const int32_t* replica_ids, int32_t steps, double dt, double a0, double c0,
+                     uint64_t seed, int64_t block, int32_t iter, int8_t* best_s, double* cuts,
+                     int32_t* best_r, int32_t variant, double h);
+
 double qo_sb_solve(int32_t n, const int64_t* rp, const int32_t* col, const double* w, int32_t R,
                    const int32_t* replica_ids, int32_t steps, double dt, double a0, double c0,
                    uint64_t seed, int64_t block, int32_t iter, int8_t* best_s, double* cuts,
                    int32_t* best_r, int32_t variant) {
+  return qo_sb_solve_h(n, rp, col, w, R, replica_ids, steps, dt, a0, c0, seed, block, iter,
+                       best_s, cuts, best_r, variant, 0.0);
+}
+
+/* qo_sb_solve with the deformation field of strength h along +1 on every vertex (the
+ * incumbent partition in the refinement's gauged frame). */
+double qo_sb_solve_h(int32_t n, const int64_t* rp, const int32_t* col, const double* w, int32_t R,
+                     const int32_t* replica_ids, int32_t steps, double dt, double a0, double c0,
+                     uint64_t seed, int64_t block, int32_t iter, int8_t* best_s, double* cuts,
+                     int32_t* best_r, int32_t variant, double h) {
   int64_t nnz = rp[n];
   double* J = (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
   for (int64_t e = 0; e < nnz; ++e) J[e] = -w[e];
@@ -412,7 +446,7 @@ double qo_sb_solve(int32_t n, const int64_t* rp, const int32_t* col, const doubl
   double* y = (double*)malloc(sizeof(double) * (size_t)R * (size_t)(n > 0 ? n : 1));
   int8_t* s = (int8_t*)malloc((size_t)(n > 0 ? n : 1));
   qo_bsb_init(n, R, replica_ids, seed, block, iter, x, y);
-  qo_sb_run(n, rp, col, J, R, x, y, 0, steps, steps, dt, a0, c0, variant);
+  qo_sb_run_h(n, rp, col, J, R, x, y, 0, steps, steps, dt, a0, c0, variant, h, NULL);
   double best = -INFINITY;
   *best_r = -1;
   for (int32_t r = 0; r < R; ++r) {
@@ -447,22 +481,54 @@ double qo_bsb_solve(int32_t n, const int64_t* rp, const int32_t* col, const doub
  * subset (tie: the subset without the lowest-index vertex) and invert the
  * sign of every edge crossing the partition (w' = -w if s_u != s_v).
  * w is modified in place (the final gauged weights).  Returns iterations done. */
+int32_t qo_refine_h(int32_t n, const int64_t* rp, const int32_t* col, double* w, int32_t R,
+                    const int32_t* replica_ids, int32_t steps, double dt, double a0, double c0,
+                    uint64_t seed, int64_t block, int32_t refine_max, int32_t* C,
+                    double* first_cut, double deform_h, int32_t deform_tries, int32_t* solves);
+
 int32_t qo_refine(int32_t n, const int64_t* rp, const int32_t* col, double* w, int32_t R,
                   const int32_t* replica_ids, int32_t steps, double dt, double a0, double c0,
                   uint64_t seed, int64_t block, int32_t refine_max, int32_t* C,
                   double* first_cut) {
+  return qo_refine_h(n, rp, col, w, R, replica_ids, steps, dt, a0, c0, seed, block, refine_max,
+                     C, first_cut, 0.0, 0, NULL);
+}
+
+/* The refinement with the adaptive deformation (reading of the SNP-based method's
+ * adaptive parameter strategy): when a solve ends with a cut <= 0 or with every
+ * vertex in one subset, and fewer than deform_tries re-solves have been made since the
+ * last accepted partition, the component is solved again with the deformation field
+ * along the incumbent (all +1 in the gauged frame), of strength deform_h 2^(k-1) on
+ * the k-th re-solve; a positive cut is then accepted as usual.  Every solve, plain or
+ * deformed, counts toward refine_max and draws its initial state with its own
+ * iteration index.  Returns the number of accepted partitions; *solves (if not NULL)
+ * receives the number of solves.                                                  */
+int32_t qo_refine_h(int32_t n, const int64_t* rp, const int32_t* col, double* w, int32_t R,
+                    const int32_t* replica_ids, int32_t steps, double dt, double a0, double c0,
+                    uint64_t seed, int64_t block, int32_t refine_max, int32_t* C,
+                    double* first_cut, double deform_h, int32_t deform_tries, int32_t* solves) {
   int8_t* s = (int8_t*)malloc((size_t)(n > 0 ? n : 1));
   double* cuts = (double*)malloc(sizeof(double) * (size_t)(R > 0 ? R : 1));
-  int32_t it = 0;
+  int32_t it = 0, accepted = 0, tries = 0;
   for (int32_t v = 0; v < n; ++v) C[v] = 0;
   for (it = 0; it < refine_max; ++it) {
     int32_t br;
-    double cut = qo_bsb_solve(n, rp, col, w, R, replica_ids, steps, dt, a0, c0, seed, block, it,
-                              s, cuts, &br);
+    double h = tries == 0 ? 0.0 : deform_h * ldexp(1.0, tries - 1);
+    double cut = qo_sb_solve_h(n, rp, col, w, R, replica_ids, steps, dt, a0, c0, seed, block, it,
+                               s, cuts, &br, 0, h);
     if (it == 0 && first_cut) *first_cut = cut;
     int32_t n_pos = 0;
     for (int32_t v = 0; v < n; ++v) n_pos += (s[v] > 0);
-    if (cut <= 0.0 || n_pos == 0 || n_pos == n) break;
+    if (cut <= 0.0 || n_pos == 0 || n_pos == n) {
+      if (deform_h > 0.0 && tries < deform_tries) {
+        ++tries;
+        continue;
+      }
+      ++it;
+      break;
+    }
+    tries = 0;
+    ++accepted;
     int8_t small;
     if (n_pos * 2 < n)
       small = 1;
@@ -476,9 +542,10 @@ int32_t qo_refine(int32_t n, const int64_t* rp, const int32_t* col, double* w, i
       for (int64_t e = rp[a]; e < rp[a + 1]; ++e)
         if (s[a] != s[col[e]]) w[e] = -w[e];
   }
+  if (solves) *solves = it;
   free(s);
   free(cuts);
-  return it;
+  return accepted;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -533,3 +533,102 @@ def test_sb_variants_brute_force(oracle, variant, dt):
         hit += best >= opt - 1e-9
         worst = min(worst, best / opt)
     assert hit >= 11 and worst >= 0.9, (hit, worst)
+
+
+# ----------------------------------------------------------------------------- deformation
+def test_deformed_bsb_matches_ode_integration(oracle):
+    """bSB with the deformation field h (1 - t/T) d_i converges (first order) to its ODE."""
+    from scipy.integrate import solve_ivp
+    rng = np.random.default_rng(20)
+    n = 5
+    J = rng.normal(size=(n, n))  # asymmetric: catches a transposed product
+    np.fill_diagonal(J, 0)
+    g = oracle.CSR.from_dense(-J)
+    a0, c0, T, h = 1.0, 0.15, 6.0, 0.02
+    d = np.array([1.0, -1.0, -1.0, 1.0, 1.0])
+    x0 = rng.uniform(-0.05, 0.05, n)
+    y0 = rng.uniform(-0.05, 0.05, n)
+
+    def rhs(t, u):
+        x, y = u[:n], u[n:]
+        return np.concatenate([a0 * y, -(a0 - a0 * t / T) * x + c0 * (J @ x)
+                               + h * (1 - t / T) * d])
+
+    ref = solve_ivp(rhs, (0, T), np.concatenate([x0, y0]), rtol=1e-11, atol=1e-13).y[:, -1]
+    assert np.abs(ref[:n]).max() < 1.0
+    x_plain, _ = oracle.bsb_run(g, x0[None], y0[None], 0, 6000, 6000, dt=T / 6000, a0=a0, c0=c0)
+    assert np.abs(x_plain[0] - ref[:n]).max() > 0.01  # the field changes the trajectory
+    errs = []
+    for steps in (3000, 6000):
+        x, y = oracle.bsb_run(g, x0[None], y0[None], 0, steps, steps, dt=T / steps, a0=a0,
+                              c0=c0, h=h, hdir=d)
+        errs.append(np.abs(np.concatenate([x[0], y[0]]) - ref).max() / np.abs(ref).max())
+    assert errs[1] < 2e-3
+    assert 1.6 < errs[0] / errs[1] < 2.4
+
+
+def test_deformation_uniform_field_is_field_along_the_gauge(oracle):
+    """A field along d on J equals, spin for spin, the uniform field on D J D from D x0:
+    the refinement's uniform field in the gauged frame is a field along the incumbent."""
+    W = synth.random_graph(4, 14, p=0.4, integer=False)
+    g = oracle.CSR.from_dense(W)
+    rng = np.random.default_rng(21)
+    d = np.where(rng.random(14) < 0.5, -1.0, 1.0)
+    gd = oracle.CSR.from_dense(d[:, None] * W * d[None, :])
+    x0 = rng.uniform(-0.1, 0.1, (3, 14))
+    y0 = rng.uniform(-0.1, 0.1, (3, 14))
+    c0 = oracle.default_c0(g)
+    x1, y1 = oracle.bsb_run(g, x0, y0, 0, 400, 400, c0=c0, h=0.05, hdir=d)
+    x2, y2 = oracle.bsb_run(gd, x0 * d, y0 * d, 0, 400, 400, c0=c0, h=0.05)
+    assert np.array_equal(x2, x1 * d) and np.array_equal(y2, y1 * d)
+    x3, y3 = oracle.bsb_run(g, x0, y0, 0, 400, 400, c0=c0, h=0.0, hdir=d)
+    x4, y4 = oracle.bsb_run(g, x0, y0, 0, 400, 400, c0=c0)
+    assert np.array_equal(x3, x4) and np.array_equal(y3, y4)
+
+
+def test_deformation_field_direction_and_decay(oracle):
+    """Without couplings the field alone moves every spin toward d; its strength falls
+    to zero at the end of the schedule (the last step adds nothing to y)."""
+    n = 6
+    g = oracle.CSR.from_dense(np.zeros((n, n)))
+    d = np.array([1.0, -1.0, 1.0, -1.0, -1.0, 1.0])
+    x0 = np.zeros((1, n))
+    y0 = np.zeros((1, n))
+    x, _ = oracle.bsb_run(g, x0, y0, 0, 100, 100, dt=0.5, c0=0.0, h=0.2, hdir=d)
+    assert np.array_equal(np.sign(x[0]), d)
+    # last step of the schedule, from rest at x = 0: the field term is h (1 - (T-1)/T)
+    T = 50
+    x1, y1 = oracle.bsb_run(g, x0, y0, T - 1, T, T, dt=1.0, c0=0.0, h=0.5, hdir=d)
+    np.testing.assert_allclose(y1[0], 0.5 / T * d, rtol=0, atol=1e-15)
+    x2, y2 = oracle.bsb_run(g, x0, y0, 0, 1, T, dt=1.0, c0=0.0, h=0.5, hdir=d)
+    np.testing.assert_allclose(y2[0], 0.5 * d, rtol=0, atol=1e-15)
+
+
+def test_refine_deformation_retries_count_toward_refine_max(oracle):
+    """Every weight negative: no cut is positive, so each solve fails.  The plain
+    refinement stops after one solve; with deformation it re-solves deform_tries times
+    (never beyond refine_max) and accepts nothing."""
+    rng = np.random.default_rng(22)
+    n = 10
+    A = -np.triu(rng.uniform(0.5, 2.0, (n, n)), 1)
+    A = A + A.T
+    g = oracle.CSR.from_dense(A)
+    for h, tries, rmax, solves in [(0.0, 3, 15, 1), (0.05, 3, 15, 4), (0.05, 3, 2, 2),
+                                   (0.05, 0, 15, 1)]:
+        st = {}
+        Cc, acc, first, _ = oracle.refine(g, range(8), 200, 3, 0, rmax, deform_h=h,
+                                          deform_tries=tries, stats=st)
+        assert acc == 0 and st["solves"] == solves and not Cc.any(), (h, tries, rmax, st)
+        assert first <= 0.0
+
+
+def test_refine_with_deformation_matches_plain_when_cuts_stay_positive(oracle):
+    """The deformation only acts after a failed solve: on an error-free read set (each
+    refinement ends in one accepted partition, then a failed solve) the accepted
+    partitions, and so the phase, are those of the plain refinement."""
+    fr = synth.region_reads(40, n_snps=60, region=30_000, n_reads=30, len_mean=6000,
+                            len_sd=1500, flip_p=0.0, miss_p=0.0, qual=(20, 30))
+    a = oracle.phase_snp(fr, range(8), 300, seed=2, refine_max=15)
+    b = oracle.phase_snp(fr, range(8), 300, seed=2, refine_max=15, deform_h=0.02, deform_tries=2)
+    assert np.array_equal(a["hap1"], b["hap1"])
+    assert (b["solves"] >= a["solves"]).all()
