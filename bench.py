@@ -153,6 +153,8 @@ def _workload(args):
            "refine_max": REFINE_DEFAULT.get(args.workload, 15) if mode == "snp" else None,
            "sb_variant": getattr(args, "variant", "ballistic"),
            "linkage_k": getattr(args, "linkage_k", 10) if mode == "snp" else None,
+           "deform": ({"h": args.deform_h, "tries": args.deform_tries}
+                      if mode == "snp" and getattr(args, "deform_h", 0.0) > 0 else None),
            "l2": "flushed between timed steps (256 MiB write)"}
     if scale != 1.0:
         cfg["scale"] = scale
@@ -185,7 +187,8 @@ def cpu_baseline(args, fr, mode, steps, seed=1, reps=None):
         res = o.phase_read(sample_fr, o.READ_SIGNED, range(reps), steps, seed=seed)
         units = sum(len(b) for b in res["blocks"]) * reps * steps
     else:
-        res = o.phase_snp(sample_fr, range(reps), steps, seed=seed, refine_max=args.refine_max)
+        res = o.phase_snp(sample_fr, range(reps), steps, seed=seed, refine_max=args.refine_max,
+                          deform_h=args.deform_h, deform_tries=args.deform_tries)
         units = sum(len(b) * int(k) for b, k in zip(res["blocks"], res["solves"])) * reps * steps
     dt = time.perf_counter() - t0
     return {"value": units / dt, "unit": "spin-updates/s", "cores": os.cpu_count(),
@@ -307,7 +310,8 @@ def run_ours(args):
         sol = ctx.solve(g, replicas=R, steps=T, precision=p, seed=1, replica_base=base,
                         step_kernel=args.step_kernel if p == prec else None,
                         refine_max=args.refine_max,
-                        variant=args.variant, dt=0.1 if args.variant == "adiabatic" else 1.0)
+                        variant=args.variant, dt=0.1 if args.variant == "adiabatic" else 1.0,
+                        deform_h=args.deform_h, deform_tries=args.deform_tries)
         if host:
             h = ctx.phase(g, sol, fr.n_snps)
             cut = sol.block(0)["best_cut"] if g.n_blocks else 0.0
@@ -487,6 +491,10 @@ def main():
     ap.add_argument("--variant", default="ballistic", choices=["ballistic", "discrete", "adiabatic"],
                     help="simulated-bifurcation variant (the paper's solver is ballistic)")
     ap.add_argument("--linkage-k", type=int, default=10, help="SNP graphs: linkage depth k/10")
+    ap.add_argument("--deform-h", type=float, default=0.0,
+                    help="SNP graphs: deformation field strength of the refinement's re-solves")
+    ap.add_argument("--deform-tries", type=int, default=0,
+                    help="SNP graphs: deformed re-solves after a failed solve")
     ap.add_argument("--step-kernel", default=None,
                     help="pin the BF16 step-kernel variant (default: autotune)")
     args = ap.parse_args()

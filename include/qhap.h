@@ -200,6 +200,19 @@ typedef struct {
                            when R allows, else 10.  Invalid choices -> QH_EINVAL */
   int32_t sb_variant;   /* QH_SB_BALLISTIC (0, the paper's solver), QH_SB_DISCRETE,
                            QH_SB_ADIABATIC */
+  double deform_h;      /* SNP mode: the adaptive deformation of the refinement
+                           (0 = off, the plain refinement).  When a solve of a block
+                           ends with a cut <= 0 or with all vertices in one subset,
+                           the block is solved again, up to deform_tries times, with
+                           the force dt h_k (1 - t / steps) added to y along the
+                           incumbent partition (h_k = deform_h 2^(k-1) on the k-th
+                           re-solve); a positive cut is accepted as usual.  Every
+                           solve counts toward refine_max.  The paper introduces a
+                           deformation term h for components whose cut stays
+                           negative without a formula: this is the library's
+                           reading of it.  Must be finite and >= 0. */
+  int32_t deform_tries; /* re-solves with deformation after a failed solve (>= 0) */
+  int32_t reserved;     /* must be 0 */
 } qh_bsb_opts;
 
 /* Run multi-replica bSB on every block of the graph in one batched launch per
@@ -298,11 +311,13 @@ qh_status qh_debug_steps(qh_ctx* ctx, const qh_graph* g, int32_t precision, int3
  * step_kernel = -1 is the default; otherwise an index into the solver's kernel
  * variants (qh_bsb_opts.step_kernel).  The multi-step variants run all `nsteps`
  * steps in ONE launch, the momentum y held on chip between steps.  QH_EINVAL when
- * the variant does not fit the graph, precision or R. */
+ * the variant does not fit the graph, precision or R.  field_per_block (host,
+ * n_blocks values, or NULL): the refinement's deformation field strength h_b of each
+ * block; every step then adds dt h_b (1 - t / steps) to y on every vertex. */
 qh_status qh_debug_steps_v(qh_ctx* ctx, const qh_graph* g, int32_t precision, int32_t R,
                            float* x, float* y, int32_t t0, int32_t nsteps, int32_t steps,
                            double dt, double a0, const double* c0_per_block, int32_t step_kernel,
-                           int32_t sb_variant);
+                           int32_t sb_variant, const double* field_per_block);
 
 /* Padded layout: n_pad and padded_index int32[n_nodes] (-1 for vertices in no
  * block): vertex v of block b sits at padded column pad_off[b] + local[v]. */

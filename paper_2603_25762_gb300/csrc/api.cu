@@ -83,7 +83,7 @@ enum {
   S_X = 32, S_Y, S_X1, S_XH0, S_XH1, S_SIGNS, S_NODEVAL, S_CUTS, S_BESTR, S_BESTCUT, S_ACTIVE,
   S_STEPSB, S_C0, S_SEEN, S_STALL, S_STEPSRUN, S_SPINS, S_C, S_WWORK, S_TBWORK, S_TFWORK,
   S_SUMW, S_SUMJ2, S_NODETMP, S_SIGNS1, S_NODEVAL1, S_CUT1, S_DBG0, S_DBG1, S_DBG2, S_RUNNING,
-  S_PVWORK, S_TR0, S_TR1, S_F8H, S_F8L, S_F8FLAG, S_X8
+  S_PVWORK, S_TR0, S_TR1, S_F8H, S_F8L, S_F8FLAG, S_X8, S_DEFORM, S_TRIES, S_DBGDEF
 };
 
 struct SolveBufs {
@@ -95,6 +95,8 @@ struct SolveBufs {
   float* c0;
   int8_t* spins;
   int32_t* C;
+  float* deform;    // nullptr without the refinement's deformation
+  int32_t* tries;
 };
 
 qh_status run_step(Ctx* ctx, const Graph& g, int precision, const TcPlan& plan, StepArgs a,
@@ -441,6 +443,9 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   if (o->precision == QH_PREC_FP8 && R % 64 != 0)
     return set_err(ctx, QH_EINVAL, "FP8 precision needs replicas to be a multiple of 64");
   if (!(o->dt > 0.0) || !(o->a0 > 0.0)) return set_err(ctx, QH_EINVAL, "dt and a0 must be > 0");
+  if (!(o->deform_h >= 0.0) || !std::isfinite(o->deform_h) || o->deform_tries < 0 ||
+      o->reserved != 0)
+    return set_err(ctx, QH_EINVAL, "deform_h must be finite and >= 0, deform_tries >= 0, reserved 0");
   if (o->check_every < 0 || o->patience < 0 || o->replica_base < 0) return set_err(ctx, QH_EINVAL, "negative option");
   if ((int64_t)o->replica_base + R > (1 << 16)) return set_err(ctx, QH_EINVAL, "replica indices must stay below 65536");
   if (is_tc_precision(o->precision) && o->step_kernel >= 0 && !G.csr_mode &&
@@ -516,8 +521,13 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   B.steps_run = (int32_t*)sc(nb * 4, S_STEPSRUN);
   B.spins = (int8_t*)sc(G.n_nodes + 16, S_SPINS);
   B.C = (int32_t*)sc((G.n_nodes + 1) * 4, S_C);
+  // the refinement's adaptive deformation: per-block field strength and re-solve count
+  const bool deform_on = snp && o->deform_h > 0.0 && o->deform_tries > 0;
+  B.deform = deform_on ? (float*)sc(nb * 4, S_DEFORM) : nullptr;
+  B.tries = deform_on ? (int32_t*)sc(nb * 4, S_TRIES) : nullptr;
   bool okb = B.x && B.y && B.signs && B.node_val && B.cuts && B.best_r && B.best_cut && B.active && B.running &&
              B.steps_b && B.c0 && B.seen && B.stall && B.steps_run && B.spins && B.C &&
+             (!deform_on || (B.deform && B.tries)) &&
              (o->precision == QH_PREC_FP32 ? B.x1 != nullptr : (B.xh0 && B.xh1));
   // working copy of the graph for the SNP refinement (weights, tiles, sums are gauged)
   Graph W = G;
@@ -586,6 +596,10 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   QH_CUDA_TRY(cudaMemcpyAsync(B.steps_b, h_steps.data(), nb * 4, cudaMemcpyHostToDevice, s));
   QH_CUDA_TRY(cudaMemcpyAsync(B.c0, h_c0.data(), nb * 4, cudaMemcpyHostToDevice, s));
   QH_CUDA_TRY(cudaMemsetAsync(B.C, 0, (G.n_nodes + 1) * 4, s));
+  if (B.deform) {
+    QH_CUDA_TRY(cudaMemsetAsync(B.deform, 0, nb * 4, s));
+    QH_CUDA_TRY(cudaMemsetAsync(B.tries, 0, nb * 4, s));
+  }
   // the second operand buffer is written at real vertices only: its padding columns
   // must hold zeros (they meet the zero columns of J, and 0 * NaN would not vanish)
   if (o->precision == QH_PREC_FP32)
@@ -628,7 +642,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
                           (const void*)B.cuts, (const void*)B.best_r, (const void*)B.best_cut,
                           (const void*)B.running, (const void*)B.steps_b, (const void*)B.c0,
                           (const void*)B.seen, (const void*)B.stall, (const void*)B.steps_run,
-                          (const void*)ctx->d_err})
+                          (const void*)ctx->d_err, (const void*)B.deform})
       add(p);
   }
   StepArgs a{};
@@ -638,6 +652,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   a.x = B.x;
   a.y = B.y;
   a.c0 = B.c0;
+  a.deform = B.deform;
   a.active = B.running;
   a.steps_b = B.steps_b;
   a.n_pad = G.n_pad;
@@ -813,14 +828,15 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
       }
     if (!snp) break;
     // ---- SNP refinement: termination test, flip counter, sign inversion
-    launch_refine_prepare(s, W, B.spins, B.best_cut, B.active, B.C);
+    launch_refine_prepare(s, W, B.spins, B.best_cut, B.active, B.C, B.deform, B.tries,
+                          (float)o->deform_h, o->deform_tries);
     QH_STAGE_CHECK("solve: refinement test");
     QH_CUDA_TRY(cudaMemcpyAsync(h_active.data(), B.active, nb * 4, cudaMemcpyDeviceToHost, s));
     QH_CUDA_TRY(cudaStreamSynchronize(s));
     int32_t n_active = 0;
     for (int32_t b = 0; b < nb; ++b) n_active += h_active[b] != 0;
     if (n_active == 0 || it + 1 == refine_max) break;
-    launch_gauge(s, W, B.spins, W.w, B.active);
+    launch_gauge(s, W, B.spins, W.w, B.active, B.deform);
     {
       qh_status st = retile(ctx, &W, W.w, W.tile_bf16, W.tile_f32, W.csr_mode ? W.pval : nullptr);
       if (st == QH_OK && fp8) st = convert_fp8_tiles();
@@ -1130,13 +1146,13 @@ qh_status qh_debug_steps(qh_ctx* h, const qh_graph* gh, int32_t precision, int32
                          float* y, int32_t t0, int32_t nsteps, int32_t steps, double dt, double a0,
                          const double* c0_per_block) {
   return qh_debug_steps_v(h, gh, precision, R, x, y, t0, nsteps, steps, dt, a0, c0_per_block, -1,
-                          QH_SB_BALLISTIC);
+                          QH_SB_BALLISTIC, nullptr);
 }
 
 qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int32_t R, float* x,
                            float* y, int32_t t0, int32_t nsteps, int32_t steps, double dt,
                            double a0, const double* c0_per_block, int32_t step_kernel,
-                           int32_t sb_variant) {
+                           int32_t sb_variant, const double* field_per_block) {
   if (!h || !gh || !x || !y || nsteps < 0 || steps < 1 || t0 < 0) return QH_EINVAL;
   if (sb_variant < QH_SB_BALLISTIC || sb_variant > QH_SB_ADIABATIC) return QH_EINVAL;
   Ctx* ctx = &h->c;
@@ -1149,6 +1165,19 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
   a.sb = sb_variant;
   if (sb_variant != QH_SB_BALLISTIC && (precision == QH_PREC_FP8 || g.csr_mode))
     return set_err(ctx, QH_EUNSUPPORTED, "discrete / adiabatic SB need FP32 or BF16 tile storage");
+  a.deform = nullptr;
+  if (field_per_block != nullptr && g.n_blocks > 0) {
+    std::vector<float> hf(g.n_blocks);
+    for (int32_t b = 0; b < g.n_blocks; ++b) {
+      if (!std::isfinite(field_per_block[b]))
+        return set_err(ctx, QH_EINVAL, "deformation field strengths must be finite");
+      hf[b] = (float)field_per_block[b];
+    }
+    float* d = (float*)ctx->scratch((size_t)g.n_blocks * 4, S_DBGDEF);
+    if (!d) return set_err(ctx, QH_ENOMEM, "allocation failed (debug)");
+    QH_CUDA_TRY(cudaMemcpy(d, hf.data(), (size_t)g.n_blocks * 4, cudaMemcpyHostToDevice));
+    a.deform = d;
+  }
   if (step_kernel >= 0 && g.csr_mode) {
     if (!csr_variant_ok(step_kernel, R))
       return set_err(ctx, QH_EINVAL, "step_kernel variant not valid for this graph, precision and R");

@@ -56,6 +56,7 @@ struct ItemInfo {
   int32_t rt;                           // row tile index (= its column tile index)
   uint32_t rows_b;                      // row tiles of the block
   float dtc0, inv_dtc0;                 // dt * c0 and its reciprocal
+  float dth;                            // dt * deformation field strength (0: none)
   double inv_steps;                     // 1 / steps_b
 };
 
@@ -92,6 +93,7 @@ struct RunArgs {
   float dt, dta0;
   double a0;
   int32_t* err;
+  const float* deform;      // [n_blocks] deformation field strength, or nullptr
 };
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
@@ -236,6 +238,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
     it.dtc0 = a.dt * a.c0[rt.block];
     it.inv_dtc0 = 1.0f / it.dtc0;
     it.inv_steps = 1.0 / (double)it.steps_b;
+    it.dth = a.deform ? a.dt * a.deform[rt.block] : 0.f;
     info[lane] = it;
   }
   if (threadIdx.x == 0) {
@@ -441,9 +444,14 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
       __nv_bfloat16* __restrict__ xh_out = (t & 1) ? a.xh0 : a.xh1;  // X_hat_{t+1}
       // -(a0 - a(t)) in FP64 as in the other step kernels (a(t) = a0 t / steps_b, with
       // the reciprocal taken once per item), by one lane, shared with the warp
-      float coef = 0.f;
-      if (lane == 0) coef = (float)(-(a.a0 - a.a0 * (double)t * it.inv_steps));
+      // and the deformation force dt h (1 - t / steps_b) (0 without deformation)
+      float coef = 0.f, dtfe = 0.f;
+      if (lane == 0) {
+        coef = (float)(-(a.a0 - a.a0 * (double)t * it.inv_steps));
+        dtfe = it.dth * (float)(1.0 - (double)t * it.inv_steps);
+      }
       const float dtcx = a.dt * __shfl_sync(0xffffffffu, coef, 0);
+      const float dtfe_s = __shfl_sync(0xffffffffu, dtfe, 0);
       const float dtc0 = it.dtc0, inv = it.inv_dtc0, dta0 = a.dta0;
       const bool ok = __all_sync(0xffffffffu, rwait(accf0 + 8 * cur.i, (uint32_t)cur.u & 1u,
                                                     a.err, abort_flag));
@@ -476,6 +484,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
         float xo[16], yo[16];
         const float2 dtc0_2 = make_float2(dtc0, dtc0), dta0_2 = make_float2(dta0, dta0);
         const float2 inv_2 = make_float2(inv, inv), dtcx_2 = make_float2(dtcx, dtcx);
+        const float2 dtfe_2 = make_float2(dtfe_s, dtfe_s);
 #pragma unroll
         for (int j = 0; j < 16; j += 2) {  // element pairs on the packed FP32x2 pipe
           const float2 x0 = make_float2(xb[c][j], xb[c][j + 1]);
@@ -484,7 +493,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
           float2 cx = dtcx_2;
           if (SB == QH_SB_ADIABATIC)
             cx = __ffma2_rn(make_float2(-a.dt * x0.x, -a.dt * x0.y), x0, dtcx_2);
-          const float2 y1 = __ffma2_rn(dtc0_2, acc, __fmul2_rn(cx, x0));
+          const float2 y1 = __ffma2_rn(dtc0_2, acc, __ffma2_rn(cx, x0, dtfe_2));
           const float2 x1 = __ffma2_rn(dta0_2, y1, x0);
           const bool w0 = SB != QH_SB_ADIABATIC && fabsf(x1.x) > 1.f;
           const bool w1 = SB != QH_SB_ADIABATIC && fabsf(x1.y) > 1.f;
@@ -492,7 +501,8 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
           xo[j + 1] = w1 ? copysignf(1.f, x1.y) : x1.y;
           yo[j] = w0 ? 0.f : y1.x;
           yo[j + 1] = w1 ? 0.f : y1.y;
-          // padding vertices hold x = y = 0 and J rows of zeros: their y stays 0
+          // padding vertices (J rows of zeros) may drift under the deformation field,
+          // in TMEM only: their x, y and X_hat are never stored (vr)
           const float2 ys = __fmul2_rn(make_float2(yo[j], yo[j + 1]), inv_2);
           out[j] = __float_as_uint(ys.x);
           out[j + 1] = __float_as_uint(ys.y);
@@ -700,6 +710,7 @@ qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const Run
   a.dta0 = s.dta0;
   a.a0 = s.a0;
   a.err = s.err;
+  a.deform = s.deform;
   // every wave's counters start from zero; waves use disjoint counters
   QH_CUDA_TRY(cudaMemsetAsync(rb.done, 0, (size_t)rb.n_done * 4, ctx->stream));
   for (const RunWave& w : rb.waves) {

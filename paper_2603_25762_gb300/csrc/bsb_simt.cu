@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(256) k_step_f32(StepArgs a) {
   const double at = a0d * (double)t / (double)sb;
   const float coef_x = (float)(-(a0d - at));
   const float c0 = a.c0[rt.block];
+  const float fe = deform_force(a.deform, rt.block, a.t, a.steps_b[rt.block]);
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(256) k_step_f32(StepArgs a) {
         continue;
       }
       float x = a.xin[idx], y = a.y[idx];
-      sb_update(a.sb, acc[i][j], x, y, a.dt, coef_x, a.dta0, c0);
+      sb_update(a.sb, acc[i][j], x, y, a.dt, coef_x, a.dta0, c0, fe);
       a.xout[idx] = x;
       a.y[idx] = y;
     }
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(256, 4) k_step_csr(StepArgs a, const int64_t* 
   const double at = a.a0 * (double)a.t / (double)sb;
   const float coef_x = (float)(-(a.a0 - at));
   const float c0 = a.c0[rt.block];
+  const float fe = deform_force(a.deform, rt.block, a.t, a.steps_b[rt.block]);
   for (int32_t r0 = 0; r0 < a.R; r0 += 128) {
     const int32_t r = r0 + 4 * lane;
     const bool on = r < a.R;
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(256, 4) k_step_csr(StepArgs a, const int64_t* 
     float4 yv = *reinterpret_cast<const float4*>(a.y + idx);
     float xs[4] = {xv.x, xv.y, xv.z, xv.w}, ys[4] = {yv.x, yv.y, yv.z, yv.w};
 #pragma unroll
-    for (int j = 0; j < 4; ++j) sb_update(a.sb, acc[j], xs[j], ys[j], a.dt, coef_x, a.dta0, c0);
+    for (int j = 0; j < 4; ++j) sb_update(a.sb, acc[j], xs[j], ys[j], a.dt, coef_x, a.dta0, c0, fe);
     float* xdst = BF16 ? a.x : a.xout;
     *reinterpret_cast<float4*>(xdst + idx) = make_float4(xs[0], xs[1], xs[2], xs[3]);
     *reinterpret_cast<float4*>(a.y + idx) = make_float4(ys[0], ys[1], ys[2], ys[3]);
@@ -324,6 +326,7 @@ __global__ void __launch_bounds__(256, 4) k_step_csr8(StepArgs a, const int64_t*
   const double at = a.a0 * (double)a.t / (double)sb;
   const float coef_x = (float)(-(a.a0 - at));
   const float c0 = a.c0[rt.block];
+  const float fe = deform_force(a.deform, rt.block, a.t, a.steps_b[rt.block]);
   for (int32_t r0 = 0; r0 < a.R; r0 += 8 * L) {
     const int32_t r = r0 + 8 * li;
     const bool on = r < a.R;
@@ -410,7 +413,7 @@ __global__ void __launch_bounds__(256, 4) k_step_csr8(StepArgs a, const int64_t*
       ys[4 * h] = yv.x; ys[4 * h + 1] = yv.y; ys[4 * h + 2] = yv.z; ys[4 * h + 3] = yv.w;
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) sb_update(a.sb, zs[j], xs[j], ys[j], a.dt, coef_x, a.dta0, c0);
+    for (int j = 0; j < 8; ++j) sb_update(a.sb, zs[j], xs[j], ys[j], a.dt, coef_x, a.dta0, c0, fe);
     float* xdst = BF16 ? a.x : a.xout;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -753,9 +756,15 @@ __global__ void k_block_sums(int32_t nb, const int64_t* __restrict__ block_ptr,
 // Per active block: stop if the best cut is <= 0 or all spins agree; otherwise
 // add 1 to C on the smaller subset (tie: the subset without the block's lowest
 // vertex).  Thread per block, vertices in ascending order.
+// With deformation (deform != nullptr): a failed solve (cut <= 0, or one subset empty)
+// of a block with tries left keeps the block active for a re-solve with field strength
+// deform_h 2^(k-1) on its k-th try, and accepts nothing (k_gauge skips blocks whose
+// deform entry is nonzero); an accepted partition clears the field and the try count.
 __global__ void __launch_bounds__(256) k_refine_prepare(int32_t nb, const int64_t* __restrict__ block_ptr,
                                  const int32_t* __restrict__ perm, const int8_t* __restrict__ spins,
-                                 const double* __restrict__ best_cut, int32_t* active, int32_t* C) {
+                                 const double* __restrict__ best_cut, int32_t* active, int32_t* C,
+                                 float* deform, int32_t* tries, float deform_h,
+                                 int32_t deform_tries) {
   // CTA per block: count the +1 side, then flag the smaller side in parallel
   __shared__ int64_t part[256];
   __shared__ int32_t go;
@@ -774,7 +783,20 @@ __global__ void __launch_bounds__(256) k_refine_prepare(int32_t nb, const int64_
   const int64_t sz = k1 - k0;
   if (threadIdx.x == 0) {
     go = !(best_cut[b] <= 0.0 || npos == 0 || npos == sz);
-    if (!go) active[b] = 0;
+    if (deform != nullptr) {
+      if (go) {
+        deform[b] = 0.f;
+        tries[b] = 0;
+      } else if (tries[b] < deform_tries) {
+        tries[b] += 1;
+        deform[b] = ldexpf(deform_h, tries[b] - 1);
+      } else {
+        deform[b] = 0.f;
+        active[b] = 0;
+      }
+    } else if (!go) {
+      active[b] = 0;
+    }
   }
   __syncthreads();
   if (!go) return;
@@ -785,13 +807,15 @@ __global__ void __launch_bounds__(256) k_refine_prepare(int32_t nb, const int64_
 }
 
 // w'_ab = -w_ab for edges crossing the partition (s_a != s_b) of active blocks.
+// Blocks waiting for a deformed re-solve (deform[b] != 0) keep their weights.
 __global__ void k_gauge(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                         const int32_t* __restrict__ block_of, const int8_t* __restrict__ spins,
-                        double* w, const int32_t* __restrict__ active) {
+                        double* w, const int32_t* __restrict__ active,
+                        const float* __restrict__ deform) {
   int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= n) return;
   int32_t b = block_of[a];
-  if (b < 0 || !active[b]) return;
+  if (b < 0 || !active[b] || (deform != nullptr && deform[b] != 0.f)) return;
   int8_t sa = spins[a];
   for (int64_t e = rp[a]; e < rp[a + 1]; ++e)
     if (spins[col[e]] != sa) w[e] = -w[e];
@@ -998,17 +1022,19 @@ void launch_block_sums(cudaStream_t s, const Graph& g, const double* w, double* 
 }
 
 void launch_refine_prepare(cudaStream_t s, const Graph& g, const int8_t* spins,
-                           const double* best_cut, int32_t* active, int32_t* C) {
+                           const double* best_cut, int32_t* active, int32_t* C, float* deform,
+                           int32_t* tries, float deform_h, int32_t deform_tries) {
   if (g.n_blocks > 0)
-    k_refine_prepare<<<::qh::counted((unsigned)g.n_blocks), 256, 0, s>>>(g.n_blocks, g.block_ptr, g.perm,
-                                                                         spins, best_cut, active, C);
+    k_refine_prepare<<<::qh::counted((unsigned)g.n_blocks), 256, 0, s>>>(
+        g.n_blocks, g.block_ptr, g.perm, spins, best_cut, active, C, deform, tries, deform_h,
+        deform_tries);
 }
 
 void launch_gauge(cudaStream_t s, const Graph& g, const int8_t* spins, double* w,
-                  const int32_t* active) {
+                  const int32_t* active, const float* deform) {
   if (g.n_nodes > 0)
     k_gauge<<<::qh::counted(nblk(g.n_nodes)), 256, 0, s>>>(g.n_nodes, g.row_ptr, g.col, g.block_of, spins, w,
-                                            active);
+                                            active, deform);
 }
 
 void launch_vote(cudaStream_t s, const Graph& g, const int8_t* spins, int8_t* hap1, int8_t* hap2,

@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(128) k_step_tc(const __grid_constant__ CUtenso
   const double at = (double)a.a0 * (double)a.t / (double)sb;
   const float coef_x = (float)(-((double)a.a0 - at));
   const float c0 = a.c0[rt.block];
+  const float fe = deform_force(a.deform, rt.block, a.t, a.steps_b[rt.block]);
   const size_t base = (size_t)blockIdx.y * BN * a.n_pad + rt.row0 + row;
 #pragma unroll
   for (int c = 0; c < BN / 32; ++c) {
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(128) k_step_tc(const __grid_constant__ CUtenso
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       float x = xs[j], y = ys[j];
-      sb_update(a.sb, __uint_as_float(v[j]), x, y, a.dt, coef_x, a.dta0, c0);
+      sb_update(a.sb, __uint_as_float(v[j]), x, y, a.dt, coef_x, a.dta0, c0, fe);
       const size_t idx = b0 + (size_t)j * a.n_pad;
       a.x[idx] = x;
       a.y[idx] = y;
@@ -236,6 +237,7 @@ __global__ void __launch_bounds__(128, MINB) k_step_tc_v(const __grid_constant__
   const double at = a.a0 * (double)a.t / (double)sb;
   const float coef_x = (float)(-(a.a0 - at));
   const float c0 = a.c0[rt.block];
+  const float fe = deform_force(a.deform, rt.block, a.t, a.steps_b[rt.block]);
 #pragma unroll
   for (int c = 0; c < BN / CH; ++c) {
     uint32_t v[CH];
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(128, MINB) k_step_tc_v(const __grid_constant__
 #pragma unroll
       for (int j = 0; j < CH; ++j) {
         float x = xs[j], y = ys[j];
-        sb_update(a.sb, __uint_as_float(v[j]), x, y, a.dt, coef_x, a.dta0, c0);
+        sb_update(a.sb, __uint_as_float(v[j]), x, y, a.dt, coef_x, a.dta0, c0, fe);
         const size_t idx = b0 + (size_t)j * a.n_pad;
         a.x[idx] = x;
         a.y[idx] = y;
@@ -398,6 +400,7 @@ __global__ void __launch_bounds__(128, MINB)
   const double at = a.a0 * (double)a.t / (double)sb;
   const float coef_x = (float)(-(a.a0 - at));
   const float c0 = a.c0[rt.block];
+  const float fe = deform_force(a.deform, rt.block, a.t, a.steps_b[rt.block]);
   const float inv_s = a.inv_scale;
 #pragma unroll
   for (int c = 0; c < BN / CH; ++c) {
@@ -430,7 +433,7 @@ __global__ void __launch_bounds__(128, MINB)
 #pragma unroll
       for (int j = 0; j < CH; ++j) {
         float x = xs[j], y = ys[j];
-        y = y + a.dt * (coef_x * x + c0 * (__uint_as_float(v[j]) * inv_s));
+        y = y + a.dt * (coef_x * x + c0 * (__uint_as_float(v[j]) * inv_s) + fe);
         x = x + a.dta0 * y;
         if (fabsf(x) > 1.f) {
           x = x > 0.f ? 1.f : -1.f;
@@ -635,6 +638,7 @@ __global__ void __launch_bounds__(192, 1)
       const double at = a.a0 * (double)a.t / (double)a.steps_b[rt.block];
       const float coef_x = (float)(-(a.a0 - at));
       const float c0 = a.c0[rt.block];
+      const float fe = deform_force(a.deform, rt.block, a.t, a.steps_b[rt.block]);
       const bool vrow = ok && row < rt.valid;
       __nv_bfloat16* xh = a.xh_out + (size_t)rn * BN * a.n_pad + rt.row0 + row;
 #pragma unroll
@@ -647,7 +651,7 @@ __global__ void __launch_bounds__(192, 1)
           for (int j = 0; j < 32; ++j) {
             const int r = c * 32 + j;
             float x = sx[r * TILE + row], y = sy[r * TILE + row];
-            y = y + a.dt * (coef_x * x + c0 * __uint_as_float(v[j]));
+            y = y + a.dt * (coef_x * x + c0 * __uint_as_float(v[j]) + fe);
             x = x + a.dta0 * y;
             if (fabsf(x) > 1.f) {
               x = x > 0.f ? 1.f : -1.f;
@@ -840,6 +844,7 @@ __global__ void __launch_bounds__(384, 1)
       const double at = a.a0 * (double)a.t / (double)a.steps_b[rt.block];
       const float coef_x = (float)(-(a.a0 - at));
       const float c0 = a.c0[rt.block];
+      const float fe = deform_force(a.deform, rt.block, a.t, a.steps_b[rt.block]);
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         uint32_t v[32];
@@ -858,7 +863,7 @@ __global__ void __launch_bounds__(384, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             float x = xs[j], y = ys[j];
-            y = y + a.dt * (coef_x * x + c0 * __uint_as_float(v[j]));
+            y = y + a.dt * (coef_x * x + c0 * __uint_as_float(v[j]) + fe);
             x = x + a.dta0 * y;
             if (fabsf(x) > 1.f) {
               x = x > 0.f ? 1.f : -1.f;

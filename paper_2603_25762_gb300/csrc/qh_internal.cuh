@@ -188,14 +188,24 @@ struct StepArgs {
   double a0;
   int32_t* err;
   int32_t sb;             // SB variant: QH_SB_BALLISTIC, QH_SB_DISCRETE, QH_SB_ADIABATIC
+  const float* deform;    // [n_blocks] deformation field strength h_b of this solve, or
+                          // nullptr: y gains dt h_b (1 - t / steps_b) (uniform field
+                          // along the incumbent, all +1 in the refinement's gauged frame)
 };
+
+// The deformation field's force at step t of a block with schedule length sb.
+__device__ __forceinline__ float deform_force(const float* deform, int32_t block, int32_t t,
+                                              int32_t sb) {
+  return deform ? deform[block] * (1.f - (float)t / (float)sb) : 0.f;
+}
 
 // One element of the SB update, after the coupling z (= J x_hat) is known.
 // coef_x = -(a0 - a(t)); the adiabatic variant adds -x^2 and has no walls.
+// fe: the deformation field's force (0 without deformation).
 __device__ __forceinline__ void sb_update(int sb, float z, float& x, float& y, float dt,
-                                          float coef_x, float dta0, float c0) {
+                                          float coef_x, float dta0, float c0, float fe = 0.f) {
   const float cx = sb == QH_SB_ADIABATIC ? coef_x - x * x : coef_x;
-  y = y + dt * (cx * x + c0 * z);
+  y = y + dt * (cx * x + c0 * z + fe);
   x = x + dta0 * y;
   if (sb != QH_SB_ADIABATIC && fabsf(x) > 1.f) {
     x = x > 0.f ? 1.f : -1.f;
@@ -269,9 +279,10 @@ void launch_extract_spins(cudaStream_t s, const Graph& g, int32_t R, const int8_
 void launch_block_sums(cudaStream_t s, const Graph& g, const double* w, double* sum_w,
                        double* sum_j2, double* node_tmp /* 2 * n_nodes */);
 void launch_refine_prepare(cudaStream_t s, const Graph& g, const int8_t* spins,
-                           const double* best_cut, int32_t* active, int32_t* C);
+                           const double* best_cut, int32_t* active, int32_t* C, float* deform,
+                           int32_t* tries, float deform_h, int32_t deform_tries);
 void launch_gauge(cudaStream_t s, const Graph& g, const int8_t* spins, double* w,
-                  const int32_t* active);
+                  const int32_t* active, const float* deform);
 void launch_vote(cudaStream_t s, const Graph& g, const int8_t* spins, int8_t* hap1, int8_t* hap2,
                  int32_t* block_id);
 void launch_parity(cudaStream_t s, const Graph& g, const int32_t* C, int8_t* hap1, int8_t* hap2,

@@ -48,7 +48,8 @@ class QhBsbOpts(C.Structure):
                 ("precision", C.c_int32), ("dt", C.c_double), ("a0", C.c_double),
                 ("c0", C.c_double), ("seed", C.c_uint64), ("replica_base", C.c_int32),
                 ("check_every", C.c_int32), ("patience", C.c_int32), ("refine_max", C.c_int32),
-                ("step_kernel", C.c_int32), ("sb_variant", C.c_int32)]
+                ("step_kernel", C.c_int32), ("sb_variant", C.c_int32),
+                ("deform_h", C.c_double), ("deform_tries", C.c_int32), ("reserved", C.c_int32)]
 
 # simulated-bifurcation variants (QH_SB_*)
 SB_VARIANTS = {"ballistic": 0, "discrete": 1, "adiabatic": 2}
@@ -90,7 +91,7 @@ _SIGS = {
     "qh_phase": (C.c_int, [P, P, P, P, P, P, I32]),
     "qh_debug_matvec": (C.c_int, [P, P, I32, I32, P, P]),
     "qh_debug_steps": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P]),
-    "qh_debug_steps_v": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P, I32, I32]),
+    "qh_debug_steps_v": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P, I32, I32, P]),
     "qh_debug_layout": (C.c_int, [P, P, P, P, P]),
     "qh_matvec_bf16_noalloc": (C.c_int, [P, P, I32, P, P]),
     "qh_solution_kernel": (C.c_char_p, [P]),
@@ -261,14 +262,19 @@ class Context:
 
     def solve(self, g, replicas=32, steps=1000, precision=PREC_FP32, seed=1, dt=1.0, a0=1.0,
               c0=0.0, schedule=SCHED_LINEAR, replica_base=0, check_every=0, patience=0,
-              refine_max=15, step_kernel=None, variant="ballistic"):
+              refine_max=15, step_kernel=None, variant="ballistic", deform_h=0.0,
+              deform_tries=0):
         """step_kernel: None = the default (autotuned on BF16 tile storage), or a name
         from STEP_KERNELS: the tile variants for BF16 tile storage, "csr-lane4" /
         "csr-lane8" for CSR storage.
-        variant: "ballistic" (bSB), "discrete" (dSB) or "adiabatic" (aSB)."""
+        variant: "ballistic" (bSB), "discrete" (dSB) or "adiabatic" (aSB).
+        deform_h, deform_tries: the SNP refinement's adaptive deformation (0 = off): up
+        to deform_tries re-solves of a block whose cut is <= 0, with a field along the
+        incumbent of strength deform_h 2^(k-1)."""
         sk = -1 if step_kernel is None else STEP_KERNELS.index(step_kernel)
         o = QhBsbOpts(replicas, steps, schedule, precision, dt, a0, c0, seed, replica_base,
-                      check_every, patience, refine_max, sk, SB_VARIANTS[variant])
+                      check_every, patience, refine_max, sk, SB_VARIANTS[variant], deform_h,
+                      deform_tries, 0)
         s = C.c_void_p()
         self._check(lib().qh_bsb_solve(self.h, g.h, C.byref(o), C.byref(s)))
         return Solution(self, s, g.n_blocks, replicas)
@@ -290,14 +296,17 @@ class Context:
         self._check(lib().qh_debug_matvec(self.h, g.h, precision, R, _ptr(x), _ptr(z)))
 
     def debug_steps(self, g, precision, R, x, y, t0, nsteps, steps, dt=1.0, a0=1.0, c0=None,
-                    step_kernel=None, variant="ballistic"):
-        """step_kernel: None = default kernel, or a name from STEP_KERNELS."""
+                    step_kernel=None, variant="ballistic", field=None):
+        """step_kernel: None = default kernel, or a name from STEP_KERNELS.
+        field: per-block deformation field strengths (None = no field)."""
         c0a = None if c0 is None else _np(c0, np.float64)
+        fa = None if field is None else _np(field, np.float64)
         sk = -1 if step_kernel is None else STEP_KERNELS.index(step_kernel)
         self._check(lib().qh_debug_steps_v(self.h, g.h, precision, R, _ptr(x), _ptr(y), t0,
                                            nsteps, steps, dt, a0,
                                            _ptr(c0a) if c0a is not None else None, sk,
-                                           SB_VARIANTS[variant]))
+                                           SB_VARIANTS[variant],
+                                           _ptr(fa) if fa is not None else None))
 
     def matvec_bf16_noalloc(self, g, R, x, z):
         """J x X in BF16 without any device allocation (fixed 8.5 MiB library array)."""

@@ -52,4 +52,4 @@ def test_struct_layouts_match_header():
     from paper_2603_25762_gb300 import qhap
     assert ctypes.sizeof(qhap.QhFragments) == 4 + 4 + 5 * 8 + 8
     assert ctypes.sizeof(qhap.QhGraphOpts) == 5 * 4 + 4 + 8
-    assert ctypes.sizeof(qhap.QhBsbOpts) == 4 * 4 + 3 * 8 + 8 + 4 * 4 + 8
+    assert ctypes.sizeof(qhap.QhBsbOpts) == 4 * 4 + 3 * 8 + 8 + 4 * 4 + 8 + 8 + 8
