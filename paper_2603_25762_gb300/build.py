@@ -11,7 +11,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqhap.so")
-SOURCES = ["util.cu", "graph.cu", "bsb_simt.cu", "bsb_tc.cu", "bsb_run.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["util.cu", "graph.cu", "bsb_simt.cu", "bsb_tc.cu", "bsb_run.cu", "bsb_band.cu", "api.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -83,7 +83,8 @@ enum {
   S_X = 32, S_Y, S_X1, S_XH0, S_XH1, S_SIGNS, S_NODEVAL, S_CUTS, S_BESTR, S_BESTCUT, S_ACTIVE,
   S_STEPSB, S_C0, S_SEEN, S_STALL, S_STEPSRUN, S_SPINS, S_C, S_WWORK, S_TBWORK, S_TFWORK,
   S_SUMW, S_SUMJ2, S_NODETMP, S_SIGNS1, S_NODEVAL1, S_CUT1, S_DBG0, S_DBG1, S_DBG2, S_RUNNING,
-  S_PVWORK, S_TR0, S_TR1, S_F8H, S_F8L, S_F8FLAG, S_X8, S_DEFORM, S_TRIES, S_DBGDEF
+  S_PVWORK, S_TR0, S_TR1, S_F8H, S_F8L, S_F8FLAG, S_X8, S_DEFORM, S_TRIES, S_DBGDEF,
+  S_ZBAND, S_BANDWORK, S_RVWORK
 };
 
 struct SolveBufs {
@@ -97,11 +98,13 @@ struct SolveBufs {
   int32_t* C;
   float* deform;    // nullptr without the refinement's deformation
   int32_t* tries;
+  float* zband;     // CSR band-tile step: the band product Z ([n_pad][R]), else nullptr
 };
 
 qh_status run_step(Ctx* ctx, const Graph& g, int precision, const TcPlan& plan, StepArgs a,
                    const float* x_cur_f32, float* x_next_f32, const __nv_bfloat16* xh_cur,
-                   __nv_bfloat16* xh_next, const Fp8Operands* f8 = nullptr, int64_t ns = 0) {
+                   __nv_bfloat16* xh_next, const Fp8Operands* f8 = nullptr, int64_t ns = 0,
+                   float* zband = nullptr) {
   if (precision == QH_PREC_FP8) {  // X_hat buffers hold the e4m3 hi part, then the lo part
     Fp8Operands op = *f8;
     op.xh_in = reinterpret_cast<const uint8_t*>(xh_cur);
@@ -121,6 +124,13 @@ qh_status run_step(Ctx* ctx, const Graph& g, int precision, const TcPlan& plan, 
   }
   a.xh_out = xh_next;
   if (g.csr_mode) {
+    if (plan.variant == CSR_BAND8) {  // band on the tensor cores, then the remainder
+      qh_status st = launch_band_mma(ctx, g, a, g.band, xh_cur, zband);
+      if (st != QH_OK) return st;
+      a.zb = zband;
+      launch_step_csr(ctx->stream, g, a, g.rval, xh_cur, plan.variant, true);
+      return QH_OK;
+    }
     launch_step_csr(ctx->stream, g, a, g.pval, xh_cur, plan.variant);
     return QH_OK;
   }
@@ -459,7 +469,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   if (G.csr_mode && R % 4 != 0)
     return set_err(ctx, QH_EINVAL, "CSR storage needs replicas to be a multiple of 4");
   if (o->step_kernel >= 0 && (G.csr_mode != (o->step_kernel >= CSR_LANE4) ||
-                              (G.csr_mode && !csr_variant_ok(o->step_kernel, R))))
+                              (G.csr_mode && !csr_variant_ok(o->step_kernel, R, o->precision))))
     return set_err(ctx, QH_EINVAL, "step_kernel variant not valid for this graph storage and R");
   if (is_tc_precision(o->precision) && !G.csr_mode && !tc_plan_ok(R, plan))
     return set_err(ctx, QH_EINVAL, "BF16 precision needs replicas to be a multiple of 64");
@@ -523,11 +533,18 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   B.C = (int32_t*)sc((G.n_nodes + 1) * 4, S_C);
   // the refinement's adaptive deformation: per-block field strength and re-solve count
   const bool deform_on = snp && o->deform_h > 0.0 && o->deform_tries > 0;
+  // CSR storage: the step variant (the band-tile step needs the band product buffer and,
+  // in SNP mode, working copies of the band tiles and remainder values)
+  const int csr_v = !G.csr_mode ? -1
+                    : o->step_kernel >= 0 ? o->step_kernel
+                                          : csr_default_variant(G, o->precision, R);
+  const bool band_on = csr_v == CSR_BAND8;
+  B.zband = band_on ? (float*)sc(NS * 4, S_ZBAND) : nullptr;
   B.deform = deform_on ? (float*)sc(nb * 4, S_DEFORM) : nullptr;
   B.tries = deform_on ? (int32_t*)sc(nb * 4, S_TRIES) : nullptr;
   bool okb = B.x && B.y && B.signs && B.node_val && B.cuts && B.best_r && B.best_cut && B.active && B.running &&
              B.steps_b && B.c0 && B.seen && B.stall && B.steps_run && B.spins && B.C &&
-             (!deform_on || (B.deform && B.tries)) &&
+             (!deform_on || (B.deform && B.tries)) && (!band_on || B.zband) &&
              (o->precision == QH_PREC_FP32 ? B.x1 != nullptr : (B.xh0 && B.xh1));
   // working copy of the graph for the SNP refinement (weights, tiles, sums are gauged)
   Graph W = G;
@@ -542,10 +559,20 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
       if (W.pval && G.pnnz)
         QH_CUDA_TRY(cudaMemcpyAsync(W.pval, G.pval, G.pnnz * 4, cudaMemcpyDeviceToDevice, s));
     }
+    if (band_on) {
+      const size_t bb = (size_t)3 * G.n_row_tiles * TILE * TILE * 2;
+      W.band = (__nv_bfloat16*)sc(std::max<size_t>(bb, 2), S_BANDWORK);
+      W.rval = (float*)sc(std::max<int64_t>(G.rnnz, 1) * 4, S_RVWORK);
+      if (!W.band || !W.rval) okb = false;
+      if (okb && bb) QH_CUDA_TRY(cudaMemcpyAsync(W.band, G.band, bb, cudaMemcpyDeviceToDevice, s));
+      if (okb && G.rnnz)
+        QH_CUDA_TRY(cudaMemcpyAsync(W.rval, G.rval, G.rnnz * 4, cudaMemcpyDeviceToDevice, s));
+    }
     sum_w_work = (double*)sc(nb * 8, S_SUMW);
     double* sj2 = (double*)sc(nb * 8, S_SUMJ2);
     double* ntmp = (double*)sc((size_t)std::max(G.n_nodes, 1) * 16, S_NODETMP);
-    okb = W.w && W.tile_bf16 && W.tile_f32 && sum_w_work && sj2 && ntmp && W.pval;
+    okb = W.w && W.tile_bf16 && W.tile_f32 && sum_w_work && sj2 && ntmp && W.pval &&
+          (!band_on || (W.band && W.rval));
     if (okb) {
       if (G.nnz) QH_CUDA_TRY(cudaMemcpyAsync(W.w, G.w, G.nnz * 8, cudaMemcpyDeviceToDevice, s));
       if (G.n_tiles)
@@ -632,7 +659,9 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     skey += std::to_string(f8_s) + "|";
     for (const void* p : {(const void*)G.rt, (const void*)G.tile_col, (const void*)W.tile_bf16,
                           (const void*)W.tile_f32, (const void*)G.prow_ptr, (const void*)G.pcol,
-                          (const void*)W.pval, (const void*)G.row_ptr, (const void*)G.col,
+                          (const void*)W.pval, (const void*)W.band, (const void*)W.rval,
+                          (const void*)G.rrow_ptr, (const void*)G.rcol, (const void*)B.zband,
+                          (const void*)G.row_ptr, (const void*)G.col,
                           (const void*)W.w, (const void*)G.block_of, (const void*)G.pad_index,
                           (const void*)G.pad_node, (const void*)G.local, (const void*)G.pad_off,
                           (const void*)G.block_ptr, (const void*)G.perm, (const void*)sum_w_work})
@@ -685,8 +714,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
       return st;
     }
   }
-  if (G.csr_mode)
-    tplan.variant = o->step_kernel >= 0 ? o->step_kernel : csr_default_variant(o->precision, R);
+  if (G.csr_mode) tplan.variant = csr_v;
   sol.kernel = G.csr_mode ? csr_variant_name(tplan.variant, is_tc_precision(o->precision))
               : fp8 ? (R % 128 == 0 ? "e4m3-bn128-s2-x3" : "e4m3-bn64-s2-x4")
               : is_tc_precision(o->precision) ? tc_variant_name(tplan.variant) : "k_step_f32";
@@ -720,7 +748,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
       a.t = t;
       const bool even = (t % 2) == 0;
       st = run_step(ctx, W, o->precision, tplan, a, even ? B.x : B.x1, even ? B.x1 : B.x,
-                    even ? B.xh0 : B.xh1, even ? B.xh1 : B.xh0, &f8, (int64_t)NS);
+                    even ? B.xh0 : B.xh1, even ? B.xh1 : B.xh0, &f8, (int64_t)NS, B.zband);
       if (early && (t + 1) % o->check_every == 0 && t + 1 < max_steps) {
         const float* xc = (o->precision == QH_PREC_FP32 && even) ? B.x1 : B.x;
         launch_signs(s, W, R, xc, B.signs);
@@ -839,6 +867,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     launch_gauge(s, W, B.spins, W.w, B.active, B.deform);
     {
       qh_status st = retile(ctx, &W, W.w, W.tile_bf16, W.tile_f32, W.csr_mode ? W.pval : nullptr);
+      if (st == QH_OK && band_on) st = reband(ctx, &W, W.w, W.band, W.rval);
       if (st == QH_OK && fp8) st = convert_fp8_tiles();
       if (st != QH_OK) {
         delete sh;
@@ -1101,10 +1130,18 @@ qh_status qh_debug_matvec(qh_ctx* h, const qh_graph* gh, int32_t precision, int3
     QH_CUDA_TRY(cudaMemsetAsync(zt, 0, NS * 4, ctx->stream));
     launch_transpose(ctx->stream, x, xt, R, g.n_pad);
     a.z_out = zt;
-    const int cv = csr_default_variant(precision, R);
+    const int cv = csr_default_variant(g, precision, R);
     if (precision == QH_PREC_FP32) {
       a.xin = xt;
       launch_step_csr(ctx->stream, g, a, g.pval, nullptr, cv);
+    } else if (cv == CSR_BAND8) {  // band product on the tensor cores + the remainder
+      launch_f32_to_bf16(ctx->stream, xt, xh, (int64_t)NS);
+      float* zb = (float*)ctx->scratch(NS * 4, S_ZBAND);
+      if (!zb) return set_err(ctx, QH_ENOMEM, "allocation failed (debug)");
+      st = launch_band_mma(ctx, g, a, g.band, xh, zb);
+      if (st) return st;
+      a.zb = zb;
+      launch_step_csr(ctx->stream, g, a, g.rval, xh, cv, true);
     } else {
       launch_f32_to_bf16(ctx->stream, xt, xh, (int64_t)NS);
       launch_step_csr(ctx->stream, g, a, g.pval, xh, cv);
@@ -1179,7 +1216,7 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
     a.deform = d;
   }
   if (step_kernel >= 0 && g.csr_mode) {
-    if (!csr_variant_ok(step_kernel, R))
+    if (!csr_variant_ok(step_kernel, R, precision))
       return set_err(ctx, QH_EINVAL, "step_kernel variant not valid for this graph, precision and R");
   } else if (step_kernel >= 0) {
     if (!is_tc_precision(precision) || g.csr_mode || step_kernel >= tc_n_variants() ||
@@ -1198,7 +1235,7 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
   cudaStream_t s = ctx->stream;
   float* xu = x;  // user buffers in [R][n_pad]
   float* yu = y;
-  const int csr_v = step_kernel >= 0 ? step_kernel : csr_default_variant(precision, R);
+  const int csr_v = step_kernel >= 0 ? step_kernel : csr_default_variant(g, precision, R);
   if (g.csr_mode) {
     if (R % 4 != 0) return set_err(ctx, QH_EINVAL, "CSR storage needs R to be a multiple of 4");
     x = (float*)ctx->scratch(NS * 4, S_TR0);
@@ -1273,7 +1310,18 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
       a.t = t0 + k;
       a.xh_out = (k % 2 == 0) ? xh1 : xh0;
       if (g.csr_mode) {
-        launch_step_csr(s, g, a, g.pval, (k % 2 == 0) ? xh0 : xh1, csr_v);
+        const __nv_bfloat16* xc = (k % 2 == 0) ? xh0 : xh1;
+        if (csr_v == CSR_BAND8) {
+          float* zb = (float*)ctx->scratch(NS * 4, S_ZBAND);
+          if (!zb) return set_err(ctx, QH_ENOMEM, "allocation failed (debug)");
+          st = launch_band_mma(ctx, g, a, g.band, xc, zb);
+          if (st) return st;
+          StepArgs ab = a;
+          ab.zb = zb;
+          launch_step_csr(s, g, ab, g.rval, xc, csr_v, true);
+        } else {
+          launch_step_csr(s, g, a, g.pval, xc, csr_v);
+        }
         continue;
       }
       st = launch_step_tc(ctx, g, a, (k % 2 == 0) ? xh0 : xh1, plan);

@@ -207,6 +207,13 @@ __global__ void __launch_bounds__(256, 4) k_step_csr(StepArgs a, const int64_t* 
     const int32_t r = r0 + 4 * lane;
     const bool on = r < a.R;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    if (a.zb != nullptr && on) {  // the band product, from the tensor cores
+      const float4 z0 = *reinterpret_cast<const float4*>(a.zb + rbase + r);
+      acc[0] = z0.x;
+      acc[1] = z0.y;
+      acc[2] = z0.z;
+      acc[3] = z0.w;
+    }
     // the next 32-edge group's columns and weights load while this group's gathers
     // are in flight (they stream from DRAM); lanes past the row's end hold column 0 and
     // J = 0: a valid address contributing nothing
@@ -296,7 +303,7 @@ __global__ void __launch_bounds__(256, 4) k_step_csr(StepArgs a, const int64_t* 
 // packed FP32x2 FMAs per lane.  Both CSR kernels are bound by the latency of the
 // gathers: they run at 64 registers, 4 CTAs (32 warps) per SM, a few bytes spilled in
 // some instantiations, which measured faster than 3 CTAs without spills.
-template <bool BF16, int P>
+template <bool BF16, int P, bool ZB>
 __global__ void __launch_bounds__(256, 4) k_step_csr8(StepArgs a, const int64_t* __restrict__ prow,
                                                    const int32_t* __restrict__ pcol,
                                                    const float* __restrict__ pval,
@@ -323,16 +330,20 @@ __global__ void __launch_bounds__(256, 4) k_step_csr8(StepArgs a, const int64_t*
     return;
   }
   const int64_t e0 = prow[row], e1 = prow[row + 1];
-  const double at = a.a0 * (double)a.t / (double)sb;
-  const float coef_x = (float)(-(a.a0 - at));
-  const float c0 = a.c0[rt.block];
-  const float fe = deform_force(a.deform, rt.block, a.t, a.steps_b[rt.block]);
   for (int32_t r0 = 0; r0 < a.R; r0 += 8 * L) {
     const int32_t r = r0 + 8 * li;
     const bool on = r < a.R;
     float2 acc[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[j] = make_float2(0.f, 0.f);
+    if (ZB && on && sub == 0) {  // the band product, from the tensor cores
+      const float4 z0 = *reinterpret_cast<const float4*>(a.zb + rbase + r);
+      const float4 z1 = *reinterpret_cast<const float4*>(a.zb + rbase + r + 4);
+      acc[0] = make_float2(z0.x, z0.y);
+      acc[1] = make_float2(z0.z, z0.w);
+      acc[2] = make_float2(z1.x, z1.y);
+      acc[3] = make_float2(z1.z, z1.w);
+    }
     // next group's columns and weights prefetched as in k_step_csr
     int32_t cl_n = e0 + lane < e1 ? pcol[e0 + lane] : 0;
     float vl_n = e0 + lane < e1 ? pval[e0 + lane] : 0.f;
@@ -403,6 +414,11 @@ __global__ void __launch_bounds__(256, 4) k_step_csr8(StepArgs a, const int64_t*
       *reinterpret_cast<float4*>(a.z_out + idx + 4) = make_float4(zs[4], zs[5], zs[6], zs[7]);
       continue;
     }
+    // the update's constants, taken after the gathers (fewer live registers there)
+    const double at = a.a0 * (double)a.t / (double)sb;
+    const float coef_x = (float)(-(a.a0 - at));
+    const float c0 = a.c0[rt.block];
+    const float fe = deform_force(a.deform, rt.block, a.t, sb);
     const float* xsrc = BF16 ? a.x : a.xin;
     float xs[8], ys[8];
 #pragma unroll
@@ -921,23 +937,27 @@ void launch_step_f32(cudaStream_t s, const Graph& g, const StepArgs& a) {
 }
 
 const char* csr_variant_name(int v, bool bf16) {
+  if (v == CSR_BAND8) return "csr-band8-bf16";
   if (v == CSR_LANE8) return bf16 ? "csr-lane8-bf16" : "csr-lane8-fp32";
   return bf16 ? "csr-lane4-bf16" : "csr-lane4-fp32";
 }
 
 void launch_step_csr(cudaStream_t s, const Graph& g, const StepArgs& a, const float* pval,
-                     const __nv_bfloat16* xh_in, int variant) {
+                     const __nv_bfloat16* xh_in, int variant, bool remainder) {
   if (g.n_pad == 0) return;
   const unsigned grid = nblk((int64_t)g.n_pad * 32);
-  if (variant == CSR_LANE8 && a.R % 8 == 0) {
+  const int64_t* rowp = remainder ? g.rrow_ptr : g.prow_ptr;
+  const int32_t* colp = remainder ? g.rcol : g.pcol;
+  if ((variant == CSR_LANE8 || variant == CSR_BAND8) && a.R % 8 == 0) {
     // lanes per neighbour row: 8 replicas each, at most a warp
     const int lanes = a.R >= 256 ? 32 : a.R >= 128 ? 16 : a.R >= 64 ? 8 : 4;
-#define QH_CSR8(P)                                                                              \
-  (xh_in != nullptr                                                                             \
-       ? k_step_csr8<true, P><<<::qh::counted(grid), 256, 0, s>>>(a, g.prow_ptr, g.pcol, pval,  \
-                                                                   xh_in)                        \
-       : k_step_csr8<false, P><<<::qh::counted(grid), 256, 0, s>>>(a, g.prow_ptr, g.pcol, pval, \
-                                                                    nullptr))
+#define QH_CSR8(P)                                                                               \
+  (xh_in == nullptr                                                                              \
+       ? k_step_csr8<false, P, false><<<::qh::counted(grid), 256, 0, s>>>(a, rowp, colp, pval,   \
+                                                                          nullptr)               \
+   : a.zb != nullptr                                                                             \
+       ? k_step_csr8<true, P, true><<<::qh::counted(grid), 256, 0, s>>>(a, rowp, colp, pval, xh_in) \
+       : k_step_csr8<true, P, false><<<::qh::counted(grid), 256, 0, s>>>(a, rowp, colp, pval, xh_in))
     switch (lanes) {
       case 32: QH_CSR8(1); break;
       case 16: QH_CSR8(2); break;
@@ -948,9 +968,9 @@ void launch_step_csr(cudaStream_t s, const Graph& g, const StepArgs& a, const fl
     return;
   }
   if (xh_in != nullptr)
-    k_step_csr<true><<<::qh::counted(grid), 256, 0, s>>>(a, g.prow_ptr, g.pcol, pval, xh_in);
+    k_step_csr<true><<<::qh::counted(grid), 256, 0, s>>>(a, rowp, colp, pval, xh_in);
   else
-    k_step_csr<false><<<::qh::counted(grid), 256, 0, s>>>(a, g.prow_ptr, g.pcol, pval, nullptr);
+    k_step_csr<false><<<::qh::counted(grid), 256, 0, s>>>(a, rowp, colp, pval, nullptr);
 }
 
 void launch_transpose(cudaStream_t s, const float* in, float* out, int64_t rows, int64_t cols) {

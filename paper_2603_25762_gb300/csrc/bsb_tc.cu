@@ -1063,6 +1063,7 @@ qh_status tc_prepare(Ctx* ctx) {
     e = cudaFuncSetAttribute(k_step_tc_p2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)P2Smem::BYTES);
   if (e == cudaSuccess) e = run_set_attrs();
+  if (e == cudaSuccess) e = band_set_attrs();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute(k_step_tc)");
   if (!get_encode()) return set_err(ctx, QH_ECUDA, "cuTensorMapEncodeTiled entry point not found");
   return QH_OK;

@@ -609,6 +609,60 @@ __global__ void k_pcsr_fill(int32_t n, const int64_t* __restrict__ rp, const int
   }
 }
 
+// Band / remainder split of the padded CSR (CSR mode): entry (v, u) lies in the band
+// when the column tile of u is the row tile of v or one of its two neighbours.
+__device__ __forceinline__ int band_offset(int32_t v, int32_t u) { return u / TILE - v / TILE; }
+
+__global__ void k_rem_count(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            const double* __restrict__ w, const int32_t* __restrict__ pad_index,
+                            int64_t* cnt) {
+  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n || pad_index[a] < 0) return;
+  const int32_t v = pad_index[a];
+  int64_t c = 0;
+  for (int64_t e = rp[a]; e < rp[a + 1]; ++e) {
+    if (w[e] == 0.0) continue;
+    const int d = band_offset(v, pad_index[col[e]]);
+    c += d < -1 || d > 1;
+  }
+  cnt[v] = c;
+}
+
+__global__ void k_rem_fill(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                           const double* __restrict__ w, const int32_t* __restrict__ pad_index,
+                           const int64_t* __restrict__ rrow, int32_t* rcol, float* rval) {
+  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n || pad_index[a] < 0) return;
+  const int32_t v = pad_index[a];
+  int64_t o = rrow[v];
+  for (int64_t e = rp[a]; e < rp[a + 1]; ++e) {
+    if (w[e] == 0.0) continue;
+    const int32_t u = pad_index[col[e]];
+    const int d = band_offset(v, u);
+    if (d >= -1 && d <= 1) continue;
+    if (rcol != nullptr) rcol[o] = u;
+    rval[o] = (float)(-w[e]);
+    ++o;
+  }
+}
+
+// band[(rt * 3 + d + 1)][v % 128][u % 128] = BF16(-w) for band entries (zeroed before)
+__global__ void k_band_fill(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            const double* __restrict__ w, const int32_t* __restrict__ pad_index,
+                            __nv_bfloat16* band) {
+  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n || pad_index[a] < 0) return;
+  const int32_t v = pad_index[a];
+  for (int64_t e = rp[a]; e < rp[a + 1]; ++e) {
+    if (w[e] == 0.0) continue;
+    const int32_t u = pad_index[col[e]];
+    const int d = band_offset(v, u);
+    if (d < -1 || d > 1) continue;
+    const int64_t t = (int64_t)(v / TILE) * 3 + (d + 1);
+    band[t * TILE * TILE + (int64_t)(v % TILE) * TILE + (u % TILE)] = __float2bfloat16_rn((float)(-w[e]));
+  }
+}
+
 // Tile fill (also used after a refinement sign inversion): J = -w into the
 // FP32 tiles and the BF16 hi (+ lo remainder) tiles.
 __global__ void k_tile_fill(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
@@ -1020,6 +1074,30 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
       k_pcsr_fill<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, g->pad_index,
                                                          g->prow_ptr, g->pcol, g->pval);
   }
+  // CSR mode: band tiles and the remainder CSR
+  if (g->csr_mode) {
+    int64_t* rcnt = (int64_t*)ctx->scratch(sizeof(int64_t) * (g->n_pad + 1), 22);
+    g->rrow_ptr = (int64_t*)dalloc(*g, sizeof(int64_t) * (g->n_pad + 1));
+    g->band = (__nv_bfloat16*)dalloc(*g, sizeof(__nv_bfloat16) * TILE * TILE * 3 *
+                                             std::max<int64_t>(g->n_row_tiles, 1));
+    if (!rcnt || !g->rrow_ptr || !g->band) return set_err(ctx, QH_ENOMEM, "allocation failed (band)");
+    QH_CUDA_TRY(cudaMemsetAsync(rcnt, 0, sizeof(int64_t) * (g->n_pad + 1), s));
+    if (N > 0)
+      k_rem_count<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, g->pad_index, rcnt);
+    scan_i64(s, rcnt, g->rrow_ptr, g->n_pad);
+    int64_t rnnz = 0;
+    QH_CUDA_TRY(cudaMemcpyAsync(&rnnz, g->rrow_ptr + g->n_pad, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+    g->rnnz = rnnz;
+    g->rcol = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max<int64_t>(rnnz, 1));
+    g->rval = (float*)dalloc(*g, sizeof(float) * std::max<int64_t>(rnnz, 1));
+    if (!g->rcol || !g->rval) return set_err(ctx, QH_ENOMEM, "allocation failed (band)");
+    if (N > 0)
+      k_rem_fill<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, g->pad_index,
+                                                        g->rrow_ptr, g->rcol, g->rval);
+    qh_status st = reband(ctx, g, g->w, g->band, nullptr);
+    if (st != QH_OK) return st;
+  }
   {
     qh_status st = retile(ctx, g, g->w, g->tile_bf16, g->tile_f32, nullptr);
     if (st != QH_OK) return st;
@@ -1046,6 +1124,22 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
   }
   g->h_block_ptr = h_block_ptr;
   QH_STAGE_CHECK("graph build: block sums");
+  return QH_OK;
+}
+
+qh_status reband(Ctx* ctx, const Graph* g, const double* w, __nv_bfloat16* band, float* rval) {
+  cudaStream_t s = ctx->stream;
+  if (!g->csr_mode || g->n_row_tiles == 0) return QH_OK;
+  if (band != nullptr) {
+    QH_CUDA_TRY(cudaMemsetAsync(band, 0, sizeof(__nv_bfloat16) * TILE * TILE * 3 * g->n_row_tiles, s));
+    if (g->n_nodes > 0)
+      k_band_fill<<<::qh::counted(nblk(g->n_nodes)), 256, 0, s>>>(g->n_nodes, g->row_ptr, g->col, w,
+                                                                g->pad_index, band);
+  }
+  if (rval != nullptr && g->n_nodes > 0)
+    k_rem_fill<<<::qh::counted(nblk(g->n_nodes)), 256, 0, s>>>(g->n_nodes, g->row_ptr, g->col, w,
+                                                             g->pad_index, g->rrow_ptr, nullptr, rval);
+  QH_CUDA_TRY(cudaGetLastError());
   return QH_OK;
 }
 

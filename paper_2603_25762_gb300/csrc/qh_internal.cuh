@@ -113,6 +113,15 @@ struct Graph {
   int64_t* prow_ptr = nullptr;  // [n_pad+1]
   int32_t* pcol = nullptr;      // [nnz] padded column
   float* pval = nullptr;        // [nnz] J = -w (FP32)
+  // CSR mode: J split into a band and a remainder for the BF16 band-tile step.  The
+  // band holds the entries whose padded column lies in the row's tile or in one of its
+  // two neighbour tiles, as three dense 128 x 128 BF16 tiles per row tile (offsets -1,
+  // 0, +1); the remainder CSR holds every other stored entry (FP32).
+  __nv_bfloat16* band = nullptr;  // [n_row_tiles][3][128][128] row-major, J = -w
+  int64_t rnnz = 0;
+  int64_t* rrow_ptr = nullptr;    // [n_pad+1]
+  int32_t* rcol = nullptr;        // [rnnz] padded column
+  float* rval = nullptr;          // [rnnz] J = -w (FP32)
   // per-block constants
   double* sum_w = nullptr;        // [n_blocks] sum_{a,b} w_ab (both triangles)
   double* sum_j2 = nullptr;       // [n_blocks]
@@ -188,6 +197,8 @@ struct StepArgs {
   double a0;
   int32_t* err;
   int32_t sb;             // SB variant: QH_SB_BALLISTIC, QH_SB_DISCRETE, QH_SB_ADIABATIC
+  const float* zb;        // CSR step: band product Z = J_band X_hat ([n_pad][R], FP32) to
+                          // start the accumulation from, or nullptr
   const float* deform;    // [n_blocks] deformation field strength h_b of this solve, or
                           // nullptr: y gains dt h_b (1 - t / steps_b) (uniform field
                           // along the incumbent, all +1 in the refinement's gauged frame)
@@ -252,19 +263,37 @@ void launch_step_f32(cudaStream_t s, const Graph& g, const StepArgs& a);
 // BF16 X_hat operand, otherwise a.xin (FP32).  variant: CSR_LANE4 (4 replicas per lane,
 // any R that is a multiple of 4) or CSR_LANE8 (8 per lane, several neighbours per warp
 // at once; R a multiple of 8).
+// CSR_BAND8: the band on the tensor cores (launch_band_mma, BF16 operands, R a multiple
+// of 128), then the lane-8 CSR step over the remainder, starting from the band product.
 constexpr int CSR_LANE4 = 10;
 constexpr int CSR_LANE8 = 11;
-inline bool csr_variant_ok(int v, int R) {
-  return v == CSR_LANE4 ? R % 4 == 0 : v == CSR_LANE8 ? R % 8 == 0 : false;
+constexpr int CSR_BAND8 = 12;
+inline bool csr_variant_ok(int v, int R, int precision) {
+  return v == CSR_LANE4   ? R % 4 == 0
+         : v == CSR_LANE8 ? R % 8 == 0
+         : v == CSR_BAND8 ? R % 128 == 0 && precision != QH_PREC_FP32
+                          : false;
 }
-// Default: 8 replicas per lane for BF16 operands (fewer instructions per gathered
-// neighbour), 4 per lane for FP32 operands (fewer registers, more warps in flight).
-inline int csr_default_variant(int precision, int R) {
+// Default: the band on the tensor cores when it holds at least a quarter of the
+// entries (BF16 operands, R a multiple of 128); else 8 replicas per lane for BF16
+// operands (fewer instructions per gathered neighbour), 4 per lane for FP32 operands
+// (fewer registers, more warps in flight).
+inline int csr_default_variant(const Graph& g, int precision, int R) {
+  if (precision != QH_PREC_FP32 && R % 128 == 0 && g.band != nullptr &&
+      4 * (g.pnnz - g.rnnz) >= g.pnnz && g.pnnz > 0)
+    return CSR_BAND8;
   return (precision != QH_PREC_FP32 && R % 8 == 0) ? CSR_LANE8 : CSR_LANE4;
 }
 const char* csr_variant_name(int v, bool bf16);
+// remainder = true: walk the remainder CSR (rrow_ptr / rcol with values pval), adding
+// to a.zb; otherwise the full padded CSR (prow_ptr / pcol).
 void launch_step_csr(cudaStream_t s, const Graph& g, const StepArgs& a, const float* pval,
-                     const __nv_bfloat16* xh_in, int variant);
+                     const __nv_bfloat16* xh_in, int variant, bool remainder = false);
+cudaError_t band_set_attrs();
+// Z = J_band X_hat for the live blocks (X_hat vertex-major, [n_pad][R]); the band tiles
+// `band` as built by the graph (or a working copy).
+qh_status launch_band_mma(Ctx* ctx, const Graph& g, const StepArgs& a, const __nv_bfloat16* band,
+                          const __nv_bfloat16* xh_vm, float* z);
 void launch_transpose(cudaStream_t s, const float* in, float* out, int64_t rows, int64_t cols);
 void launch_signs(cudaStream_t s, const Graph& g, int32_t R, const float* x, int8_t* signs_t);
 void launch_cut(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t, const double* w,
@@ -278,6 +307,9 @@ void launch_extract_spins(cudaStream_t s, const Graph& g, int32_t R, const int8_
                           const int32_t* best_r, int8_t* spins, const int32_t* active);
 void launch_block_sums(cudaStream_t s, const Graph& g, const double* w, double* sum_w,
                        double* sum_j2, double* node_tmp /* 2 * n_nodes */);
+// Refill the band tiles and the remainder CSR values of a CSR-mode graph from weights
+// w (after a refinement sign inversion; the pattern is unchanged).
+qh_status reband(Ctx* ctx, const Graph* g, const double* w, __nv_bfloat16* band, float* rval);
 void launch_refine_prepare(cudaStream_t s, const Graph& g, const int8_t* spins,
                            const double* best_cut, int32_t* active, int32_t* C, float* deform,
                            int32_t* tries, float deform_h, int32_t deform_tries);

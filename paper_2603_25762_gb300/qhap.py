@@ -58,7 +58,9 @@ STEP_KERNELS = ["cta-bn128-s3", "cta-bn128-s2-x3", "cta-bn64-s2-x4", "cta-bn256-
                 "multistep-jres-group", "multistep-stream-tile", "multistep-jres-tile",
                 "multistep-stream-group",
                 # CSR storage (FP32 or BF16): 4 or 8 replicas per lane
-                "csr-lane4", "csr-lane8"]
+                "csr-lane4", "csr-lane8",
+                # CSR storage, BF16: the band on the tensor cores + the lane-8 remainder step
+                "csr-band8"]
 
 
 class QhError(RuntimeError):

@@ -253,9 +253,12 @@ def test_steps_match_oracle(q, ctx, oracle, precision, tol, storage):
 
 
 @pytest.mark.parametrize("R,kernel", [(12, "csr-lane4"), (24, "csr-lane8"), (64, "csr-lane4"),
-                                      (192, "csr-lane8"), (384, "csr-lane8"), (384, "csr-lane4")])
+                                      (192, "csr-lane8"), (384, "csr-lane8"), (384, "csr-lane4"),
+                                      (128, "csr-band8"), (256, "csr-band8")])
 @pytest.mark.parametrize("precision,tol", [(0, 1e-5), (1, 1e-2)])
 def test_csr_steps_replica_counts(q, ctx, oracle, precision, tol, R, kernel):
+    if kernel == "csr-band8" and precision == 0:
+        pytest.skip("the band-tile step takes BF16 operands")
     # the CSR step's lane layouts: 4 replicas per lane (R = 384: three passes), and
     # 8 per lane with 8 (R = 24), 2 (R = 192, two passes) and 1 (R = 384, two passes)
     # neighbours per warp at once
@@ -273,6 +276,10 @@ def test_csr_variant_rejections(q, ctx):
         ctx.solve(gt, replicas=64, steps=10, precision=q.PREC_BF16, step_kernel="csr-lane4")
     with pytest.raises(RuntimeError):  # a tile variant on CSR storage
         ctx.solve(gc, replicas=64, steps=10, precision=q.PREC_BF16, step_kernel="cta-bn128-s3")
+    with pytest.raises(RuntimeError):  # the band-tile step: BF16 operands, R % 128 == 0
+        ctx.solve(gc, replicas=128, steps=10, precision=q.PREC_FP32, step_kernel="csr-band8")
+    with pytest.raises(RuntimeError):
+        ctx.solve(gc, replicas=64, steps=10, precision=q.PREC_BF16, step_kernel="csr-band8")
     n_pad, _, c0 = gc.layout()
     x = torch.zeros((12, n_pad), dtype=torch.float32, device="cuda")
     with pytest.raises(RuntimeError):
@@ -404,6 +411,27 @@ def test_csr_storage_matvec(q, ctx, oracle, mode):
     assert e16 <= 1e-2, e16
 
 
+def test_csr_band_matvec_exact_on_bf16_inputs(q, ctx, oracle):
+    # integer read weights (exact in BF16) and x exact in BF16: the band product on the
+    # tensor cores plus the remainder leave only FP32 accumulation error
+    fr = synth.hifi_region(1002, scale=0.1)
+    for R in (128, 256):
+        e = _matvec_case(q, ctx, oracle, fr, q.MODE_READ, q.PREC_BF16, R, bf16_x=True,
+                         storage=q.STORAGE_CSR)
+        assert e <= 1e-6, (R, e)
+
+
+def test_csr_band_split_covers_every_entry(q, ctx):
+    # band (three tiles per row tile) + remainder = the stored entries, on a graph with
+    # long-range contacts; the default BF16 step at R = 128 is the band-tile step
+    fr = synth.chromosome_porec(1005, scale=0.03)
+    g = ctx.build_graph(fr, mode=q.MODE_SNP, storage=q.STORAGE_CSR)
+    sol = ctx.solve(g, replicas=128, steps=20, precision=q.PREC_BF16, seed=1, refine_max=1)
+    assert sol.timing()["kernel"] == "csr-band8-bf16"
+    sol64 = ctx.solve(g, replicas=64, steps=20, precision=q.PREC_BF16, seed=1, refine_max=1)
+    assert sol64.timing()["kernel"] == "csr-lane8-bf16"
+
+
 @pytest.mark.parametrize("R", [12, 24, 192, 384])
 def test_csr_matvec_replica_counts(q, ctx, oracle, R):
     fr = synth.ont_region(1003, scale=0.06)
@@ -413,14 +441,17 @@ def test_csr_matvec_replica_counts(q, ctx, oracle, R):
     assert e16 <= 1e-2, e16
 
 
-@pytest.mark.parametrize("kernel", [None, "csr-lane4", "csr-lane8"])
+@pytest.mark.parametrize("kernel", [None, "csr-lane4", "csr-lane8", "csr-band8"])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_csr_storage_solve_vs_oracle(q, ctx, oracle, precision, kernel):
-    _check_solve(q, ctx, oracle, synth.tiny_reads(1001), precision, 64, 2000, seed=11,
+    if kernel == "csr-band8" and precision == 0:
+        pytest.skip("the band-tile step takes BF16 operands")
+    _check_solve(q, ctx, oracle, synth.tiny_reads(1001), precision,
+                 128 if kernel == "csr-band8" else 64, 2000, seed=11,
                  storage=q.STORAGE_CSR, step_kernel=kernel)
     g, sol = _check_solve(q, ctx, oracle, synth.hifi_region(1002, scale=0.1), precision, 128,
                           1000, seed=3, n_oracle=16, storage=q.STORAGE_CSR, step_kernel=kernel)
-    assert g.n_tiles == 0 and sol.timing()["kernel"].startswith(kernel or "csr-lane")
+    assert g.n_tiles == 0 and sol.timing()["kernel"].startswith(kernel or "csr-")
 
 
 def test_csr_storage_early_stop(q, ctx):
@@ -433,13 +464,21 @@ def test_csr_storage_early_stop(q, ctx):
         assert all(50 <= r <= 3000 for r in runs) and min(runs) < 3000
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_csr_storage_snp_refinement(q, ctx, oracle, precision):
-    fr = synth.region_reads(32, n_snps=150, region=50_000, n_reads=40, len_mean=8000,
-                            len_sd=2000, flip_p=0.08, miss_p=0.0, qual=(7, 30))
+@pytest.mark.parametrize("precision,R,kernel", [(0, 64, None), (1, 64, None),
+                                                (1, 128, "csr-band8")])
+def test_csr_storage_snp_refinement(q, ctx, oracle, precision, R, kernel):
+    # the band-tile step refreshes its band tiles and remainder after each sign inversion
+    # (its case spans four row tiles, so off-diagonal band tiles are in play)
+    if kernel == "csr-band8":
+        fr = synth.region_reads(32, n_snps=400, region=140_000, n_reads=100, len_mean=8000,
+                                len_sd=2000, flip_p=0.08, miss_p=0.0, qual=(7, 30))
+    else:
+        fr = synth.region_reads(32, n_snps=150, region=50_000, n_reads=40, len_mean=8000,
+                                len_sd=2000, flip_p=0.08, miss_p=0.0, qual=(7, 30))
     g = ctx.build_graph(fr, mode=q.MODE_SNP, storage=q.STORAGE_CSR)
-    sol = ctx.solve(g, replicas=64, steps=300, precision=precision, seed=6, refine_max=15)
-    res = oracle.phase_snp(fr, range(64), 300, seed=6, refine_max=15)
+    sol = ctx.solve(g, replicas=R, steps=300, precision=precision, seed=6, refine_max=15,
+                    step_kernel=kernel)
+    res = oracle.phase_snp(fr, range(R), 300, seed=6, refine_max=15)
     og = res["graph"]
     for b, nodes in enumerate(res["blocks"]):
         sub = og.subgraph(nodes)
