@@ -246,22 +246,32 @@ struct SnpRowSmem {
   double val[SNP_ROW_CAP];
 };
 
+// SNP rows whose window of covered SNPs fits this many entries go to the small kernel.
+constexpr int SNP_SMALL_CAP = 2048;
+
 // CTA per SNP row u.  PASS 0: count distinct partners; PASS 1: write (v, w_uv).
-template <int PASS>
-__global__ void __launch_bounds__(512) k_snp_rows(
+// SMALL: a dense window of at most SNP_SMALL_CAP SNPs in a small shared-memory
+// footprint (many CTAs per SM); a row with a wider window is appended to `defer` in
+// PASS 0 and left to the large kernel (dense window up to SNP_DENSE_CAP, else the
+// sorted-terms path), which walks the deferred rows (`rows`, `n_list` of them).  Both
+// sum a partner's terms fragment by fragment in fragment order: the same weights.
+template <int PASS, bool SMALL>
+__global__ void __launch_bounds__(SMALL ? 128 : 512) k_snp_rows(
     int32_t n, const int64_t* __restrict__ fp, const int32_t* __restrict__ snp,
     const int8_t* __restrict__ allele, const uint8_t* __restrict__ qual,
     const uint8_t* __restrict__ is_porec, const int64_t* __restrict__ cov_ptr,
     const int32_t* __restrict__ cov_frag, const double* __restrict__ L, double alpha,
     int linkage_k, int64_t* cnt, const int64_t* __restrict__ row_ptr, int32_t* col, double* w,
-    int32_t* err) {
+    int32_t* err, const int32_t* __restrict__ rows, const int32_t* __restrict__ n_list,
+    int32_t* defer, int32_t* n_defer) {
+  constexpr int DCAP = SMALL ? SNP_SMALL_CAP : SNP_DENSE_CAP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SnpRowSmem& sm = *reinterpret_cast<SnpRowSmem*>(smem_raw);
-  __shared__ int32_t s_off[1025];
   __shared__ int32_t s_total;
-  __shared__ int32_t s_runs[512];
+  __shared__ int32_t s_runs[32];
   __shared__ int32_t s_w0, s_w1;
-  for (int32_t u = blockIdx.x; u < n; u += gridDim.x) {
+  const int32_t count = rows != nullptr ? *n_list : n;
+  for (int32_t ri = blockIdx.x; ri < count; ri += gridDim.x) {
+    const int32_t u = rows != nullptr ? rows[ri] : ri;
     int64_t cb = cov_ptr[u], ce = cov_ptr[u + 1];
     int32_t ncov = (int32_t)(ce - cb);
     // SNP window spanned by the covering fragments
@@ -285,11 +295,17 @@ __global__ void __launch_bounds__(512) k_snp_rows(
     }
     __syncthreads();
     const int32_t w0 = s_w0, W = s_w1 - s_w0 + 1;
-    if (ncov > 0 && W <= SNP_DENSE_CAP) {
+    if (SMALL && ncov > 0 && W > DCAP) {  // wide window: the large kernel's row
+      if (PASS == 0 && threadIdx.x == 0) defer[atomicAdd(n_defer, 1)] = u;
+      __syncthreads();
+      continue;
+    }
+    if (ncov > 0 && W <= DCAP) {
       // Dense window: acc[v - w0] summed fragment by fragment in fragment order (the
-      // partners of one fragment are distinct, so its terms go in parallel).
+      // partners of one fragment are distinct, so its terms go in parallel).  The
+      // counting pass needs only which partners occur.
       double* acc = reinterpret_cast<double*>(smem_raw);
-      uint8_t* touched = reinterpret_cast<uint8_t*>(acc + SNP_DENSE_CAP);
+      uint8_t* touched = reinterpret_cast<uint8_t*>(acc + DCAP);
       for (int32_t t = threadIdx.x; t < W; t += blockDim.x) {
         acc[t] = 0.0;
         touched[t] = 0;
@@ -312,12 +328,13 @@ __global__ void __launch_bounds__(512) k_snp_rows(
         for (int32_t pp = lo + threadIdx.x; pp <= hi; pp += blockDim.x) {
           if (pp == p) continue;
           const int64_t ev = fb + pp;
+          const int32_t k = snp[ev] - w0;
+          touched[k] = 1;
+          if (PASS == 0) continue;
           const double lv = L[(int)qual[eu] * 94 + (int)qual[ev]];
           const double sg = ((int)allele[eu] * (int)allele[ev] > 0) ? 1.0 : -1.0;
           const double term = -(a * (sg * lv)) / (double)(S - 1);
-          const int32_t k = snp[ev] - w0;
           acc[k] += term;
-          touched[k] = 1;
         }
         __syncthreads();
       }
@@ -353,6 +370,9 @@ __global__ void __launch_bounds__(512) k_snp_rows(
       __syncthreads();
       continue;
     }
+    if constexpr (!SMALL) {
+    __shared__ int32_t s_off[1025];
+    SnpRowSmem& sm = *reinterpret_cast<SnpRowSmem*>(smem_raw);
     // per covering fragment: number of partners inside the linkage window
     int32_t base = 0;
     for (int32_t c0 = 0; c0 < ncov; c0 += 1024) {
@@ -478,6 +498,9 @@ __global__ void __launch_bounds__(512) k_snp_rows(
     }
     if (PASS == 0 && threadIdx.x == 0) cnt[u] = done;
     __syncthreads();
+    } else if (PASS == 0 && threadIdx.x == 0) {  // no covering fragment: no partners
+      cnt[u] = 0;
+    }
   }
 }
 
@@ -844,17 +867,29 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     if (!L || !cnt) return set_err(ctx, QH_ENOMEM, "allocation failed (SNP graph scratch)");
     k_llr_table<<<::qh::counted(94), 94, 0, s>>>(L);
     QH_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), s));
-    size_t smem = sizeof(SnpRowSmem);
-    QH_CUDA_TRY(cudaFuncSetAttribute(k_snp_rows<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    QH_CUDA_TRY(cudaFuncSetAttribute(k_snp_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    unsigned grid = (unsigned)std::max(1, std::min(n, ctx->n_sm * 4));
+    // rows whose covered window is narrow go to the small-footprint kernel (many CTAs
+    // per SM); the others are deferred to the large kernel
+    const size_t smem = sizeof(SnpRowSmem);
+    const size_t smem_s = (size_t)SNP_SMALL_CAP * (sizeof(double) + 1);
+    QH_CUDA_TRY(cudaFuncSetAttribute(k_snp_rows<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    QH_CUDA_TRY(cudaFuncSetAttribute(k_snp_rows<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned grid = (unsigned)std::max(1, std::min(n, ctx->n_sm * 4));
+    const unsigned grid_s = (unsigned)std::max(1, std::min(n, ctx->n_sm * 16));
+    int32_t* defer = (int32_t*)ctx->scratch(sizeof(int32_t) * (n + 1), 23);
     g->row_ptr = (int64_t*)dalloc(*g, sizeof(int64_t) * (n + 1));
-    if (!g->row_ptr) return set_err(ctx, QH_ENOMEM, "allocation failed (edges)");
-    if (n > 0)
-      k_snp_rows<0><<<::qh::counted(grid), 512, smem, s>>>(n, g->frag_ptr, g->snp, g->allele, g->qual,
-                                           g->is_porec, g->cov_ptr, g->cov_frag, L,
-                                           o->porec_alpha, o->linkage_k, cnt, nullptr, nullptr,
-                                           nullptr, ctx->d_err);
+    if (!g->row_ptr || !defer) return set_err(ctx, QH_ENOMEM, "allocation failed (edges)");
+    int32_t* n_defer = defer + n;
+    QH_CUDA_TRY(cudaMemsetAsync(n_defer, 0, sizeof(int32_t), s));
+    if (n > 0) {
+      k_snp_rows<0, true><<<::qh::counted(grid_s), 128, smem_s, s>>>(
+          n, g->frag_ptr, g->snp, g->allele, g->qual, g->is_porec, g->cov_ptr, g->cov_frag, L,
+          o->porec_alpha, o->linkage_k, cnt, nullptr, nullptr, nullptr, ctx->d_err, nullptr,
+          nullptr, defer, n_defer);
+      k_snp_rows<0, false><<<::qh::counted(grid), 512, smem, s>>>(
+          n, g->frag_ptr, g->snp, g->allele, g->qual, g->is_porec, g->cov_ptr, g->cov_frag, L,
+          o->porec_alpha, o->linkage_k, cnt, nullptr, nullptr, nullptr, ctx->d_err, defer,
+          n_defer, nullptr, nullptr);
+    }
     scan_i64(s, cnt, g->row_ptr, n);
     QH_CUDA_TRY(cudaMemcpyAsync(&g->nnz, g->row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     QH_CUDA_TRY(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -864,11 +899,16 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     g->col = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max<int64_t>(g->nnz, 1));
     g->w = (double*)dalloc(*g, sizeof(double) * std::max<int64_t>(g->nnz, 1));
     if (!g->col || !g->w) return set_err(ctx, QH_ENOMEM, "allocation failed (edges)");
-    if (n > 0 && g->nnz > 0)
-      k_snp_rows<1><<<::qh::counted(grid), 512, smem, s>>>(n, g->frag_ptr, g->snp, g->allele, g->qual,
-                                           g->is_porec, g->cov_ptr, g->cov_frag, L,
-                                           o->porec_alpha, o->linkage_k, nullptr, g->row_ptr,
-                                           g->col, g->w, ctx->d_err);
+    if (n > 0 && g->nnz > 0) {
+      k_snp_rows<1, true><<<::qh::counted(grid_s), 128, smem_s, s>>>(
+          n, g->frag_ptr, g->snp, g->allele, g->qual, g->is_porec, g->cov_ptr, g->cov_frag, L,
+          o->porec_alpha, o->linkage_k, nullptr, g->row_ptr, g->col, g->w, ctx->d_err, nullptr,
+          nullptr, nullptr, nullptr);
+      k_snp_rows<1, false><<<::qh::counted(grid), 512, smem, s>>>(
+          n, g->frag_ptr, g->snp, g->allele, g->qual, g->is_porec, g->cov_ptr, g->cov_frag, L,
+          o->porec_alpha, o->linkage_k, nullptr, g->row_ptr, g->col, g->w, ctx->d_err, defer,
+          n_defer, nullptr, nullptr);
+    }
   }
   const int32_t N = g->n_nodes;
   QH_STAGE_CHECK("graph build: edges");
