@@ -246,17 +246,21 @@ struct SnpRowSmem {
   double val[SNP_ROW_CAP];
 };
 
-// SNP rows whose window of covered SNPs fits this many entries go to the small kernel.
+// The small kernel's capacities: a dense window of this many SNPs, else this many
+// fragment terms on the sorted path (both fit its 32 KB of shared memory).
 constexpr int SNP_SMALL_CAP = 2048;
+constexpr int SNP_SMALL_TERMS = 2048;
+constexpr size_t SNP_SMALL_SMEM = (size_t)SNP_SMALL_TERMS * 16;
 
 // CTA per SNP row u.  PASS 0: count distinct partners; PASS 1: write (v, w_uv).
-// SMALL: a dense window of at most SNP_SMALL_CAP SNPs in a small shared-memory
-// footprint (many CTAs per SM); a row with a wider window is appended to `defer` in
-// PASS 0 and left to the large kernel (dense window up to SNP_DENSE_CAP, else the
-// sorted-terms path), which walks the deferred rows (`rows`, `n_list` of them).  Both
-// sum a partner's terms fragment by fragment in fragment order: the same weights.
+// A row with a narrow window of covered SNPs sums into a dense window; otherwise its
+// fragment terms are gathered and sorted by (partner, fragment).  SMALL: capacities
+// SNP_SMALL_CAP / SNP_SMALL_TERMS in a small shared-memory footprint (many CTAs per
+// SM); a row over them is appended to `defer` in PASS 0 and left to the large kernel
+// (SNP_DENSE_CAP / SNP_ROW_CAP), which walks the deferred rows (`rows`, `n_list` of
+// them).  Every path sums a partner's terms in fragment order: the same weights.
 template <int PASS, bool SMALL>
-__global__ void __launch_bounds__(SMALL ? 128 : 512) k_snp_rows(
+__global__ void __launch_bounds__(SMALL ? 256 : 512) k_snp_rows(
     int32_t n, const int64_t* __restrict__ fp, const int32_t* __restrict__ snp,
     const int8_t* __restrict__ allele, const uint8_t* __restrict__ qual,
     const uint8_t* __restrict__ is_porec, const int64_t* __restrict__ cov_ptr,
@@ -265,10 +269,14 @@ __global__ void __launch_bounds__(SMALL ? 128 : 512) k_snp_rows(
     int32_t* err, const int32_t* __restrict__ rows, const int32_t* __restrict__ n_list,
     int32_t* defer, int32_t* n_defer) {
   constexpr int DCAP = SMALL ? SNP_SMALL_CAP : SNP_DENSE_CAP;
+  constexpr int TCAP = SMALL ? SNP_SMALL_TERMS : SNP_ROW_CAP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int32_t s_total;
   __shared__ int32_t s_runs[32];
   __shared__ int32_t s_w0, s_w1;
+  __shared__ int32_t s_off[1025];
+  uint64_t* skey = reinterpret_cast<uint64_t*>(smem_raw);       // sorted path: TCAP keys
+  double* sval = reinterpret_cast<double*>(smem_raw) + TCAP;    // and their terms
   const int32_t count = rows != nullptr ? *n_list : n;
   for (int32_t ri = blockIdx.x; ri < count; ri += gridDim.x) {
     const int32_t u = rows != nullptr ? rows[ri] : ri;
@@ -295,11 +303,6 @@ __global__ void __launch_bounds__(SMALL ? 128 : 512) k_snp_rows(
     }
     __syncthreads();
     const int32_t w0 = s_w0, W = s_w1 - s_w0 + 1;
-    if (SMALL && ncov > 0 && W > DCAP) {  // wide window: the large kernel's row
-      if (PASS == 0 && threadIdx.x == 0) defer[atomicAdd(n_defer, 1)] = u;
-      __syncthreads();
-      continue;
-    }
     if (ncov > 0 && W <= DCAP) {
       // Dense window: acc[v - w0] summed fragment by fragment in fragment order (the
       // partners of one fragment are distinct, so its terms go in parallel).  The
@@ -370,9 +373,6 @@ __global__ void __launch_bounds__(SMALL ? 128 : 512) k_snp_rows(
       __syncthreads();
       continue;
     }
-    if constexpr (!SMALL) {
-    __shared__ int32_t s_off[1025];
-    SnpRowSmem& sm = *reinterpret_cast<SnpRowSmem*>(smem_raw);
     // per covering fragment: number of partners inside the linkage window
     int32_t base = 0;
     for (int32_t c0 = 0; c0 < ncov; c0 += 1024) {
@@ -399,9 +399,9 @@ __global__ void __launch_bounds__(SMALL ? 128 : 512) k_snp_rows(
       }
       __syncthreads();
       int32_t tot = s_off[cn];
-      if (base + tot > SNP_ROW_CAP) {
-        if (threadIdx.x == 0) atomicOr(err, ERR_ROWCAP);
-        base = SNP_ROW_CAP + 1;
+      if (base + tot > TCAP) {  // small kernel: the large kernel's row; large: error
+        if (threadIdx.x == 0 && !SMALL) atomicOr(err, ERR_ROWCAP);
+        base = TCAP + 1;
         __syncthreads();
         break;
       }
@@ -432,14 +432,18 @@ __global__ void __launch_bounds__(SMALL ? 128 : 512) k_snp_rows(
         double sg = ((int)allele[eu] * (int)allele[ev] > 0) ? 1.0 : -1.0;
         double a = (is_porec != nullptr && is_porec[i]) ? alpha : 1.0;
         double term = -(a * (sg * lv)) / (double)(S - 1);
-        sm.key[base + t] = ((uint64_t)(uint32_t)v << 32) | (uint32_t)i;
-        sm.val[base + t] = term;
+        skey[base + t] = ((uint64_t)(uint32_t)v << 32) | (uint32_t)i;
+        sval[base + t] = term;
       }
       base += tot;
       __syncthreads();
     }
-    if (base > SNP_ROW_CAP) {
-      if (PASS == 0 && threadIdx.x == 0) cnt[u] = 0;
+    if (base > TCAP) {
+      if (SMALL) {
+        if (PASS == 0 && threadIdx.x == 0) defer[atomicAdd(n_defer, 1)] = u;
+      } else if (PASS == 0 && threadIdx.x == 0) {
+        cnt[u] = 0;
+      }
       __syncthreads();
       continue;
     }
@@ -447,8 +451,8 @@ __global__ void __launch_bounds__(SMALL ? 128 : 512) k_snp_rows(
     int32_t N = 1;
     while (N < total) N <<= 1;
     for (int32_t t = total + threadIdx.x; t < N; t += blockDim.x) {
-      sm.key[t] = ~0ull;
-      sm.val[t] = 0.0;
+      skey[t] = ~0ull;
+      sval[t] = 0.0;
     }
     __syncthreads();
     // bitonic sort of (key, val) by key
@@ -457,14 +461,14 @@ __global__ void __launch_bounds__(SMALL ? 128 : 512) k_snp_rows(
         for (int32_t t = threadIdx.x; t < N; t += blockDim.x) {
           int32_t l = t ^ j;
           if (l > t) {
-            uint64_t ka = sm.key[t], kb = sm.key[l];
+            uint64_t ka = skey[t], kb = skey[l];
             bool up = (t & k) == 0;
             if ((ka > kb) == up) {
-              sm.key[t] = kb;
-              sm.key[l] = ka;
-              double va = sm.val[t];
-              sm.val[t] = sm.val[l];
-              sm.val[l] = va;
+              skey[t] = kb;
+              skey[l] = ka;
+              double va = sval[t];
+              sval[t] = sval[l];
+              sval[l] = va;
             }
           }
         }
@@ -476,7 +480,7 @@ __global__ void __launch_bounds__(SMALL ? 128 : 512) k_snp_rows(
     int32_t done = 0;
     for (int32_t t0 = 0; t0 < total; t0 += blockDim.x) {
       int32_t t = t0 + threadIdx.x;
-      bool start = t < total && (t == 0 || (sm.key[t] >> 32) != (sm.key[t - 1] >> 32));
+      bool start = t < total && (t == 0 || (skey[t] >> 32) != (skey[t - 1] >> 32));
       unsigned bal = __ballot_sync(0xffffffffu, start);
       if ((threadIdx.x & 31) == 0) s_runs[threadIdx.x >> 5] = __popc(bal);
       __syncthreads();
@@ -488,8 +492,8 @@ __global__ void __launch_bounds__(SMALL ? 128 : 512) k_snp_rows(
       before += __popc(bal & ((1u << (threadIdx.x & 31)) - 1));
       if (PASS == 1 && start) {
         double acc = 0.0;
-        uint32_t v = (uint32_t)(sm.key[t] >> 32);
-        for (int32_t q = t; q < total && (uint32_t)(sm.key[q] >> 32) == v; ++q) acc += sm.val[q];
+        uint32_t v = (uint32_t)(skey[t] >> 32);
+        for (int32_t q = t; q < total && (uint32_t)(skey[q] >> 32) == v; ++q) acc += sval[q];
         col[out + done + before] = (int32_t)v;
         w[out + done + before] = acc;
       }
@@ -498,9 +502,6 @@ __global__ void __launch_bounds__(SMALL ? 128 : 512) k_snp_rows(
     }
     if (PASS == 0 && threadIdx.x == 0) cnt[u] = done;
     __syncthreads();
-    } else if (PASS == 0 && threadIdx.x == 0) {  // no covering fragment: no partners
-      cnt[u] = 0;
-    }
   }
 }
 
@@ -870,7 +871,9 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     // rows whose covered window is narrow go to the small-footprint kernel (many CTAs
     // per SM); the others are deferred to the large kernel
     const size_t smem = sizeof(SnpRowSmem);
-    const size_t smem_s = (size_t)SNP_SMALL_CAP * (sizeof(double) + 1);
+    const size_t smem_s = SNP_SMALL_SMEM;
+    QH_CUDA_TRY(cudaFuncSetAttribute(k_snp_rows<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s));
+    QH_CUDA_TRY(cudaFuncSetAttribute(k_snp_rows<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s));
     QH_CUDA_TRY(cudaFuncSetAttribute(k_snp_rows<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     QH_CUDA_TRY(cudaFuncSetAttribute(k_snp_rows<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const unsigned grid = (unsigned)std::max(1, std::min(n, ctx->n_sm * 4));
@@ -881,7 +884,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     int32_t* n_defer = defer + n;
     QH_CUDA_TRY(cudaMemsetAsync(n_defer, 0, sizeof(int32_t), s));
     if (n > 0) {
-      k_snp_rows<0, true><<<::qh::counted(grid_s), 128, smem_s, s>>>(
+      k_snp_rows<0, true><<<::qh::counted(grid_s), 256, smem_s, s>>>(
           n, g->frag_ptr, g->snp, g->allele, g->qual, g->is_porec, g->cov_ptr, g->cov_frag, L,
           o->porec_alpha, o->linkage_k, cnt, nullptr, nullptr, nullptr, ctx->d_err, nullptr,
           nullptr, defer, n_defer);
@@ -900,7 +903,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     g->w = (double*)dalloc(*g, sizeof(double) * std::max<int64_t>(g->nnz, 1));
     if (!g->col || !g->w) return set_err(ctx, QH_ENOMEM, "allocation failed (edges)");
     if (n > 0 && g->nnz > 0) {
-      k_snp_rows<1, true><<<::qh::counted(grid_s), 128, smem_s, s>>>(
+      k_snp_rows<1, true><<<::qh::counted(grid_s), 256, smem_s, s>>>(
           n, g->frag_ptr, g->snp, g->allele, g->qual, g->is_porec, g->cov_ptr, g->cov_frag, L,
           o->porec_alpha, o->linkage_k, nullptr, g->row_ptr, g->col, g->w, ctx->d_err, nullptr,
           nullptr, nullptr, nullptr);
