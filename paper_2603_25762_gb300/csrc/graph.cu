@@ -819,7 +819,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     g->cov_frag = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max<int64_t>(nnz_f, 1));
     g->cov_allele = (int8_t*)dalloc(*g, std::max<int64_t>(nnz_f, 1));
     if (!g->cov_ptr || !g->cov_frag || !g->cov_allele) return set_err(ctx, QH_ENOMEM, "allocation failed (coverage)");
-    scan_i32_to_i64(s, cnt, g->cov_ptr, n);
+    if (!scan_i32_to_i64(ctx, s, cnt, g->cov_ptr, n)) return set_err(ctx, QH_ENOMEM, "allocation failed (scan)");
     QH_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), s));
     if (m > 0)
       k_cov_fill<<<::qh::counted(nblk(m)), 256, 0, s>>>(m, g->frag_ptr, g->snp, g->allele, g->cov_ptr, cnt,
@@ -846,12 +846,12 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
       k_first_last<<<::qh::counted(nblk(m)), 256, 0, s>>>(m, g->frag_ptr, g->snp, first, last, keys);
       sort_u64(s, keys, m, cap);
       k_unpack_order<<<::qh::counted(nblk(m)), 256, 0, s>>>(m, keys, last, order, sfirst, slast);
-      scan_max_i32(s, slast, pmax, m);
+      if (!scan_max_i32(ctx, s, slast, pmax, m)) return set_err(ctx, QH_ENOMEM, "allocation failed (scan)");
       k_read_edges<0><<<::qh::counted(nblk((int64_t)m * 32)), 256, 0, s>>>(
           m, g->frag_ptr, g->snp, g->allele, first, last, order, sfirst, slast, pmax,
           o->weight_mode, cnt, nullptr, nullptr, nullptr);
     }
-    scan_i64(s, cnt, g->row_ptr, m);
+    if (!scan_i64(ctx, s, cnt, g->row_ptr, m)) return set_err(ctx, QH_ENOMEM, "allocation failed (scan)");
     QH_CUDA_TRY(cudaMemcpyAsync(&g->nnz, g->row_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     QH_CUDA_TRY(cudaStreamSynchronize(s));
     g->col = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max<int64_t>(g->nnz, 1));
@@ -893,7 +893,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
           o->porec_alpha, o->linkage_k, cnt, nullptr, nullptr, nullptr, ctx->d_err, defer,
           n_defer, nullptr, nullptr);
     }
-    scan_i64(s, cnt, g->row_ptr, n);
+    if (!scan_i64(ctx, s, cnt, g->row_ptr, n)) return set_err(ctx, QH_ENOMEM, "allocation failed (scan)");
     QH_CUDA_TRY(cudaMemcpyAsync(&g->nnz, g->row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     QH_CUDA_TRY(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     QH_CUDA_TRY(cudaStreamSynchronize(s));
@@ -955,7 +955,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     k_uf_compress<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, parent, label, csize);
     k_block_roots<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, label, csize, isroot);
   }
-  scan_i32_to_i64(s, isroot, rrank, N);
+  if (!scan_i32_to_i64(ctx, s, isroot, rrank, N)) return set_err(ctx, QH_ENOMEM, "allocation failed (scan)");
   int64_t nb64 = 0;
   QH_CUDA_TRY(cudaMemcpyAsync(&nb64, rrank + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   QH_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1026,7 +1026,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
       k_tile_flags<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, g->block_of, g->local,
                                           d_slot_off, d_T, flags);
   }
-  scan_i32_to_i64(s, flags, slot_tile, n_slots);
+  if (!scan_i32_to_i64(ctx, s, flags, slot_tile, n_slots)) return set_err(ctx, QH_ENOMEM, "allocation failed (scan)");
   std::vector<int64_t> h_slot_tile(n_slots + 1);
   QH_CUDA_TRY(cudaMemcpyAsync(h_slot_tile.data(), slot_tile, sizeof(int64_t) * (n_slots + 1),
                               cudaMemcpyDeviceToHost, s));
@@ -1105,7 +1105,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     QH_CUDA_TRY(cudaMemsetAsync(pcnt, 0, sizeof(int64_t) * (g->n_pad + 1), s));
     if (N > 0)
       k_pcsr_count<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->w, g->pad_index, pcnt);
-    scan_i64(s, pcnt, g->prow_ptr, g->n_pad);
+    if (!scan_i64(ctx, s, pcnt, g->prow_ptr, g->n_pad)) return set_err(ctx, QH_ENOMEM, "allocation failed (scan)");
     int64_t pnnz = 0;
     QH_CUDA_TRY(cudaMemcpyAsync(&pnnz, g->prow_ptr + g->n_pad, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     QH_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1127,7 +1127,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     QH_CUDA_TRY(cudaMemsetAsync(rcnt, 0, sizeof(int64_t) * (g->n_pad + 1), s));
     if (N > 0)
       k_rem_count<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, g->pad_index, rcnt);
-    scan_i64(s, rcnt, g->rrow_ptr, g->n_pad);
+    if (!scan_i64(ctx, s, rcnt, g->rrow_ptr, g->n_pad)) return set_err(ctx, QH_ENOMEM, "allocation failed (scan)");
     int64_t rnnz = 0;
     QH_CUDA_TRY(cudaMemcpyAsync(&rnnz, g->rrow_ptr + g->n_pad, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     QH_CUDA_TRY(cudaStreamSynchronize(s));

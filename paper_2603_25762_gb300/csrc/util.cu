@@ -12,52 +12,111 @@ int64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
-constexpr int SCAN_THREADS = 1024;
+// Scans in three passes over tiles of 2,048 elements (coalesced loads): the total (or
+// maximum) of each tile, an exclusive scan of those in one CTA, then each tile's own
+// scan from its offset.
+constexpr int SCAN_THREADS = 256, SCAN_ITEMS = 8, SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
-// One CTA, each thread owns a contiguous chunk: local sums, block scan, write-back.
-template <typename TIn>
-__global__ void k_scan_excl(const TIn* __restrict__ in, int64_t* __restrict__ out, int64_t n) {
-  __shared__ int64_t part[SCAN_THREADS];
-  int64_t chunk = (n + SCAN_THREADS - 1) / SCAN_THREADS;
-  int64_t b = (int64_t)threadIdx.x * chunk, e = b + chunk < n ? b + chunk : n;
-  int64_t s = 0;
-  for (int64_t i = b; i < e; ++i) s += (int64_t)in[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int off = 1; off < SCAN_THREADS; off <<= 1) {
-    int64_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
-  }
-  int64_t run = part[threadIdx.x] - s;
-  for (int64_t i = b; i < e; ++i) {
-    int64_t v = (int64_t)in[i];
-    out[i] = run;
-    run += v;
-  }
-  if (threadIdx.x == SCAN_THREADS - 1) out[n] = part[SCAN_THREADS - 1];
+template <bool MAX>
+__device__ __forceinline__ int64_t scan_op(int64_t a, int64_t b) {
+  return MAX ? (a > b ? a : b) : a + b;
 }
 
-__global__ void k_scan_max(const int32_t* __restrict__ in, int32_t* __restrict__ out, int64_t n) {
-  __shared__ int32_t part[SCAN_THREADS];
-  int64_t chunk = (n + SCAN_THREADS - 1) / SCAN_THREADS;
-  int64_t b = (int64_t)threadIdx.x * chunk, e = b + chunk < n ? b + chunk : n;
-  int32_t m = INT32_MIN;
-  for (int64_t i = b; i < e; ++i) m = max(m, in[i]);
-  part[threadIdx.x] = m;
+// Block-wide exclusive scan of one value per thread (and the block total).
+template <bool MAX>
+__device__ __forceinline__ int64_t block_excl(int64_t v, int64_t ident, int64_t* total) {
+  __shared__ int64_t warp_tot[SCAN_THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t incl = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int64_t u = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl = scan_op<MAX>(incl, u);
+  }
+  if (lane == 31) warp_tot[warp] = incl;
   __syncthreads();
-  for (int off = 1; off < SCAN_THREADS; off <<= 1) {
-    int32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : INT32_MIN;
-    __syncthreads();
-    part[threadIdx.x] = max(part[threadIdx.x], v);
-    __syncthreads();
+  int64_t before = ident, all = ident;
+  for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+    if (w < warp) before = scan_op<MAX>(before, warp_tot[w]);
+    all = scan_op<MAX>(all, warp_tot[w]);
   }
-  int32_t run = threadIdx.x > 0 ? part[threadIdx.x - 1] : INT32_MIN;
-  for (int64_t i = b; i < e; ++i) {
-    run = max(run, in[i]);
-    out[i] = run;
+  __syncthreads();
+  const int64_t excl_in_warp = __shfl_up_sync(0xffffffffu, incl, 1);
+  *total = all;
+  return lane == 0 ? before : scan_op<MAX>(before, excl_in_warp);
+}
+
+template <typename TIn, bool MAX>
+__global__ void __launch_bounds__(SCAN_THREADS) k_tile_total(const TIn* __restrict__ in,
+                                                             int64_t* __restrict__ part, int64_t n,
+                                                             int64_t ident) {
+  const int64_t b = (int64_t)blockIdx.x * SCAN_TILE;
+  int64_t acc = ident;
+  for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS)
+    if (b + i < n) acc = scan_op<MAX>(acc, (int64_t)in[b + i]);
+  int64_t total;
+  block_excl<MAX>(acc, ident, &total);
+  if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+// One CTA: part[0..nt) <- exclusive scan; part[nt] <- the grand total.
+template <bool MAX>
+__global__ void __launch_bounds__(SCAN_THREADS) k_part_scan(int64_t* part, int64_t nt,
+                                                            int64_t ident) {
+  int64_t carry = ident;
+  for (int64_t b = 0; b < nt; b += SCAN_THREADS) {
+    const int64_t i = b + threadIdx.x;
+    const int64_t v = i < nt ? part[i] : ident;
+    int64_t total;
+    const int64_t ex = block_excl<MAX>(v, ident, &total);
+    if (i < nt) part[i] = scan_op<MAX>(carry, ex);
+    carry = scan_op<MAX>(carry, total);
   }
+  if (threadIdx.x == 0) part[nt] = carry;
+}
+
+// Each tile from its offset: exclusive (sum, int64 out, out[n] = total) or inclusive
+// (max, int32 out).
+template <typename TIn, typename TOut, bool MAX>
+__global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(const TIn* __restrict__ in,
+                                                            const int64_t* __restrict__ part,
+                                                            TOut* __restrict__ out, int64_t n,
+                                                            int64_t nt, int64_t ident) {
+  __shared__ int64_t s[SCAN_TILE];
+  const int64_t b = (int64_t)blockIdx.x * SCAN_TILE;
+  for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS)
+    s[i] = b + i < n ? (int64_t)in[b + i] : ident;
+  __syncthreads();
+  int64_t loc = ident;
+#pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j) loc = scan_op<MAX>(loc, s[threadIdx.x * SCAN_ITEMS + j]);
+  int64_t total;
+  int64_t run = scan_op<MAX>(part[blockIdx.x], block_excl<MAX>(loc, ident, &total));
+#pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j) {
+    const int i = threadIdx.x * SCAN_ITEMS + j;
+    const int64_t v = s[i];
+    if (MAX) run = scan_op<MAX>(run, v);  // inclusive
+    if (b + i < n) out[b + i] = (TOut)run;
+    if (!MAX) run += v;  // exclusive
+  }
+  if (!MAX && blockIdx.x == 0 && threadIdx.x == 0) out[n] = (TOut)part[nt];
+}
+
+template <typename TIn, typename TOut, bool MAX>
+bool scan3(Ctx* ctx, cudaStream_t s, const TIn* in, TOut* out, int64_t n, int64_t ident) {
+  if (n <= 0) {
+    if (!MAX) return cudaMemsetAsync(out, 0, sizeof(TOut), s) == cudaSuccess;
+    return true;
+  }
+  const int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+  int64_t* part = (int64_t*)ctx->scratch(sizeof(int64_t) * (nt + 1), 24);
+  if (part == nullptr) return false;
+  k_tile_total<TIn, MAX><<<::qh::counted((unsigned)nt), SCAN_THREADS, 0, s>>>(in, part, n, ident);
+  k_part_scan<MAX><<<::qh::counted(1), SCAN_THREADS, 0, s>>>(part, nt, ident);
+  k_tile_scan<TIn, TOut, MAX><<<::qh::counted((unsigned)nt), SCAN_THREADS, 0, s>>>(in, part, out, n,
+                                                                                  nt, ident);
+  return true;
 }
 
 // Bitonic sort: global compare-exchange for strides >= 1024, shared-memory
@@ -115,14 +174,14 @@ int64_t next_pow2(int64_t n) {
   return p;
 }
 
-void scan_i64(cudaStream_t s, const int64_t* in, int64_t* out, int64_t n) {
-  k_scan_excl<int64_t><<<::qh::counted(1), SCAN_THREADS, 0, s>>>(in, out, n);
+bool scan_i64(Ctx* ctx, cudaStream_t s, const int64_t* in, int64_t* out, int64_t n) {
+  return scan3<int64_t, int64_t, false>(ctx, s, in, out, n, 0);
 }
-void scan_i32_to_i64(cudaStream_t s, const int32_t* in, int64_t* out, int64_t n) {
-  k_scan_excl<int32_t><<<::qh::counted(1), SCAN_THREADS, 0, s>>>(in, out, n);
+bool scan_i32_to_i64(Ctx* ctx, cudaStream_t s, const int32_t* in, int64_t* out, int64_t n) {
+  return scan3<int32_t, int64_t, false>(ctx, s, in, out, n, 0);
 }
-void scan_max_i32(cudaStream_t s, const int32_t* in, int32_t* out, int64_t n) {
-  if (n > 0) k_scan_max<<<::qh::counted(1), SCAN_THREADS, 0, s>>>(in, out, n);
+bool scan_max_i32(Ctx* ctx, cudaStream_t s, const int32_t* in, int32_t* out, int64_t n) {
+  return scan3<int32_t, int32_t, true>(ctx, s, in, out, n, (int64_t)INT32_MIN);
 }
 
 void sort_u64(cudaStream_t s, uint64_t* keys, int64_t n, int64_t cap) {
