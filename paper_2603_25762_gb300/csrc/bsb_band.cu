@@ -156,6 +156,8 @@ qh_status launch_band_mma(Ctx* ctx, const Graph& g, const StepArgs& a, const __n
                           const __nv_bfloat16* xh_vm, float* z) {
   if (g.n_row_tiles == 0) return QH_OK;
   if (a.R % 128 != 0) return set_err(ctx, QH_EINVAL, "band product needs R to be a multiple of 128");
+  if (a.R / 128 > 65535)  // replica tiles index the grid's y dimension
+    return set_err(ctx, QH_EUNSUPPORTED, "band product: more than 65,535 replica tiles");
   CUtensorMap mA, mB;
   if (!make_map(&mA, band, TILE, (uint64_t)3 * g.n_row_tiles * TILE, TILE) ||
       !make_map(&mB, xh_vm, (uint64_t)a.R, (uint64_t)g.n_pad, 64))
