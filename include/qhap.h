@@ -319,6 +319,13 @@ qh_status qh_debug_steps_v(qh_ctx* ctx, const qh_graph* g, int32_t precision, in
                            double dt, double a0, const double* c0_per_block, int32_t step_kernel,
                            int32_t sb_variant, const double* field_per_block);
 
+/* Test hook of the failure detection (not part of the paper's method): runs one of the
+ * step kernels' bounded device waits on something that nothing completes (which = 0:
+ * an mbarrier phase; 1: a release counter of the multi-step kernel).  The wait gives
+ * up after about one second and the call returns QH_ETIMEOUT; the context stays
+ * usable for the next call.  QH_EINVAL for another `which`. */
+qh_status qh_debug_wait_timeout(qh_ctx* ctx, int32_t which);
+
 /* Padded layout: n_pad and padded_index int32[n_nodes] (-1 for vertices in no
  * block): vertex v of block b sits at padded column pad_off[b] + local[v]. */
 qh_status qh_debug_layout(qh_ctx* ctx, const qh_graph* g, int32_t* n_pad, int32_t* padded_index,

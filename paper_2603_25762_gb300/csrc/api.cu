@@ -1039,6 +1039,16 @@ qh_status qh_phase(qh_ctx* h, const qh_graph* gh, const qh_solution* sh, int8_t*
 }
 
 // ------------------------------------------------------------------ test hooks
+qh_status qh_debug_wait_timeout(qh_ctx* h, int32_t which) {
+  if (!h || which < 0 || which > 1) return QH_EINVAL;
+  Ctx* ctx = &h->c;
+  cudaSetDevice(ctx->device);
+  clear_foreign_error(ctx);
+  qh_status st = launch_wait_probe(ctx, which);
+  if (st != QH_OK) return st;
+  return check_err_word(ctx);
+}
+
 qh_status qh_debug_layout(qh_ctx* h, const qh_graph* gh, int32_t* n_pad, int32_t* padded_index,
                           double* c0_default) {
   if (!h || !gh) return QH_EINVAL;

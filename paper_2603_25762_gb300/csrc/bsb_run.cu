@@ -183,6 +183,26 @@ __device__ __forceinline__ bool wait_count(const uint32_t* p, uint32_t target, i
   return true;
 }
 
+// Failure-detection probe: one of the step kernels' bounded waits on something that
+// nothing will complete (which = 0: an mbarrier phase; 1: a release counter).  The wait
+// expires after about a second, sets ERR_TIMEOUT and the kernel returns.
+__global__ void k_wait_probe(int which, const uint32_t* counter, int32_t* err) {
+  __shared__ uint64_t bar;
+  __shared__ int32_t abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (which == 0)
+      rwait(smem_u32(&bar), 0, err, &abort_flag);
+    else
+      wait_count(counter, 1u, err, &abort_flag);
+  }
+}
+
 // Position in the CTA's sequence of (step, item) pairs that have work.
 struct Cursor {
   int u, i;
@@ -751,6 +771,16 @@ template <bool JRES, int SB>
 static cudaError_t run_attr() {
   return cudaFuncSetAttribute(k_bsb_run<JRES, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)RunSmem<JRES>::BYTES);
+}
+
+qh_status launch_wait_probe(Ctx* ctx, int which) {
+  uint32_t* counter = (uint32_t*)ctx->scratch(16, S_WAIT_PROBE);
+  if (!counter) return set_err(ctx, QH_ENOMEM, "allocation failed (wait probe)");
+  QH_CUDA_TRY(cudaMemsetAsync(counter, 0, 16, ctx->stream));
+  k_wait_probe<<<::qh::counted(1), 32, 0, ctx->stream>>>(which, counter, ctx->d_err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_wait_probe launch");
+  return QH_OK;
 }
 
 cudaError_t run_set_attrs() {

@@ -290,6 +290,8 @@ const char* csr_variant_name(int v, bool bf16);
 void launch_step_csr(cudaStream_t s, const Graph& g, const StepArgs& a, const float* pval,
                      const __nv_bfloat16* xh_in, int variant, bool remainder = false);
 cudaError_t band_set_attrs();
+// Failure-detection probe (bsb_run.cu): a bounded device wait that expires.
+qh_status launch_wait_probe(Ctx* ctx, int which);
 // Z = J_band X_hat for the live blocks (X_hat vertex-major, [n_pad][R]); the band tiles
 // `band` as built by the graph (or a working copy).
 qh_status launch_band_mma(Ctx* ctx, const Graph& g, const StepArgs& a, const __nv_bfloat16* band,
@@ -352,6 +354,7 @@ qh_status tc_prepare(Ctx* ctx);
 //   8: J resident in smem, tile hand-off    9: J streamed, group hand-off
 constexpr int RUN_VARIANT_FIRST = 6;
 constexpr int S_RUN_WORK = 96, S_RUN_ROWS = 97, S_RUN_DONE = 98, S_RUN_XQ = 99;  // scratch slots
+constexpr int S_WAIT_PROBE = 100;
 struct RunWave {              // one launch: whole blocks whose items fit on chip
   int work_off = 0;           // first entry of the wave in RunBufs::work
   int grid = 0;               // CTAs

@@ -93,6 +93,7 @@ _SIGS = {
     "qh_phase": (C.c_int, [P, P, P, P, P, P, I32]),
     "qh_debug_matvec": (C.c_int, [P, P, I32, I32, P, P]),
     "qh_debug_steps": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P]),
+    "qh_debug_wait_timeout": (C.c_int, [P, I32]),
     "qh_debug_steps_v": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P, I32, I32, P]),
     "qh_debug_layout": (C.c_int, [P, P, P, P, P]),
     "qh_matvec_bf16_noalloc": (C.c_int, [P, P, I32, P, P]),
@@ -309,6 +310,11 @@ class Context:
                                            _ptr(c0a) if c0a is not None else None, sk,
                                            SB_VARIANTS[variant],
                                            _ptr(fa) if fa is not None else None))
+
+    def debug_wait_timeout(self, which=0):
+        """Failure-detection hook: a bounded device wait that expires (raises QhError
+        with status QH_ETIMEOUT after about a second)."""
+        self._check(lib().qh_debug_wait_timeout(self.h, which))
 
     def matvec_bf16_noalloc(self, g, R, x, z):
         """J x X in BF16 without any device allocation (fixed 8.5 MiB library array)."""

@@ -604,3 +604,17 @@ def test_real_weight_cuts_match_fp64(q, ctx, oracle):
         if picked <= 0:  # the refinement test stops before flipping: no partition
             continue
         assert picked == pytest.approx(exact, rel=1e-10, abs=1e-8)
+
+
+# ----------------------------------------------------------------------------- failure detection
+@pytest.mark.parametrize("which", [0, 1])
+def test_bounded_wait_expires_and_context_survives(q, ctx, oracle, which):
+    # a wait that nothing completes (an mbarrier phase, a release counter) gives up
+    # after about a second with QH_ETIMEOUT; the next call on the context works
+    import time
+    t0 = time.perf_counter()
+    with pytest.raises(q.QhError) as e:
+        ctx.debug_wait_timeout(which)
+    assert e.value.status == 4  # QH_ETIMEOUT
+    assert 0.2 < time.perf_counter() - t0 < 30
+    _check_solve(q, ctx, oracle, synth.tiny_reads(1001), q.PREC_BF16, 64, 500, seed=11)
