@@ -1,0 +1,92 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the bench times:
+the step kernel the bench picks runs a few steps on every replica of the full graph,
+and the FP64 oracle recomputes a sample of replicas one by one.
+
+Workloads: hifi-region (7,200 reads, R = 1,024, multi-step kernel), ont-snp (12,000
+SNPs, R = 512, multi-step kernel) and chromosome + Pore-C (200,000 SNPs, R = 128, band
+tiles on the tensor cores + CSR remainder).  Bar: 1e-2 relative Frobenius (BF16
+operands) on the sampled replicas, as for the small cases.
+"""
+import numpy as np
+import pytest
+
+from paper_2603_25762_gb300 import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_25762_gb300 import build, qhap
+    build.build()
+    return qhap
+
+
+@pytest.fixture(scope="module")
+def ctx(q):
+    return q.Context(0)
+
+
+def _rel_frob(a, b):
+    n = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / n if n > 0 else np.linalg.norm(a - b)
+
+
+def _full_state_case(q, ctx, oracle, fr, mode, kernel, R, sample, t0, nsteps, steps,
+                     storage=0):
+    import torch
+    g = ctx.build_graph(fr, mode=mode, storage=storage)
+    og = oracle.read_graph(fr, oracle.READ_SIGNED) if mode == q.MODE_READ else oracle.snp_graph(fr)
+    blocks = oracle.blocks_of(og)
+    n_pad, pidx, c0 = g.layout()
+    rng = np.random.default_rng(77)
+    x = np.zeros((R, n_pad), np.float32)
+    y = np.zeros((R, n_pad), np.float32)
+    inb = pidx >= 0
+    x[:, pidx[inb]] = rng.uniform(-0.1, 0.1, (R, int(inb.sum())))
+    y[:, pidx[inb]] = rng.uniform(-0.1, 0.1, (R, int(inb.sum())))
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    ctx.debug_steps(g, q.PREC_BF16, R, xd, yd, t0, nsteps, steps, c0=c0, step_kernel=kernel)
+    xg, yg = xd.cpu().numpy().astype(np.float64), yd.cpu().numpy().astype(np.float64)
+    checked = 0
+    for b, nodes in enumerate(blocks):
+        if len(nodes) < 128:  # the large blocks carry the workload
+            continue
+        sub = og.subgraph(nodes)
+        cols = pidx[nodes]
+        x0 = x[sample][:, cols].astype(np.float64)
+        y0 = y[sample][:, cols].astype(np.float64)
+        x1, y1 = oracle.bsb_run(sub, x0, y0, t0, t0 + nsteps, steps, c0=float(c0[b]))
+        xgb, ygb = xg[sample][:, cols], yg[sample][:, cols]
+        free = (np.abs(xgb) < 1.0) & (np.abs(x1) < 1.0)
+        assert (~free & (np.abs(xgb) != np.abs(x1))).mean() <= 0.01
+        assert _rel_frob((xgb - x0)[free], (x1 - x0)[free]) <= 1e-2
+        assert _rel_frob(ygb[free], y1[free]) <= 1e-2
+        checked += len(nodes)
+    assert checked > 0.9 * og.n
+    return g
+
+
+def test_full_size_hifi_region_multistep_sampled(q, ctx, oracle):
+    fr = synth.hifi_region(1002)
+    sample = [0, 1, 127, 128, 511, 640, 1000, 1023]
+    _full_state_case(q, ctx, oracle, fr, q.MODE_READ, "multistep-stream-tile", 1024, sample,
+                     500, 3, 1000)
+
+
+def test_full_size_ont_snp_multistep_sampled(q, ctx, oracle):
+    fr = synth.ont_region(1003)
+    sample = [0, 63, 64, 255, 256, 511]
+    _full_state_case(q, ctx, oracle, fr, q.MODE_SNP, "multistep-stream-group", 512, sample,
+                     1000, 3, 2000)
+
+
+def test_full_size_chromosome_band_sampled(q, ctx, oracle):
+    fr = synth.chromosome_porec(1005)
+    sample = [0, 77, 127]
+    g = _full_state_case(q, ctx, oracle, fr, q.MODE_SNP, "csr-band8", 128, sample, 1000, 2,
+                         2000, storage=q.STORAGE_CSR)
+    assert g.n_tiles == 0
