@@ -256,10 +256,17 @@ def _count_kernels(fn):
         with profile(activities=[ProfilerActivity.CUDA]) as prof:
             fn()
             torch.cuda.synchronize()
-        n = 0
+        # this library's kernels live in namespace qh: demangled "qh::", mangled "_ZN2qh"
+        n, names = 0, set()
         for ev in prof.events():
-            if ev.device_type.name == "CUDA" and "qh::" in ev.name:
+            if ev.device_type.name != "CUDA":
+                continue
+            names.add(ev.name[:60])
+            if "qh::" in ev.name or "_ZN2qh" in ev.name:
                 n += 1
+        if n == 0:
+            print(f"kernel count: no kernel of this library in the trace ({len(names)} names, "
+                  f"e.g. {sorted(names)[:3]})", file=sys.stderr)
         return n if n > 0 else None
     except Exception as e:  # the activity trace is optional: report why it is missing
         print(f"kernel count unavailable: {e!r}", file=sys.stderr)
