@@ -47,6 +47,7 @@ CASES = [  # (precision, step kernel, storage, R, steps compared, tolerance)
     (0, "csr-lane8", 2, 64, 3, 1e-5),
     (1, "csr-lane4", 2, 128, 3, 1e-2),
     (1, "csr-lane8", 2, 128, 3, 1e-2),
+    (1, "csr-band8", 2, 128, 3, 1e-2),
 ]
 
 
