@@ -149,23 +149,28 @@ def test_invalid_inputs_rejected(q, ctx):
     assert g.n_nodes == fr.n_frags
 
 
-def test_empty_and_edgeless_inputs(q, ctx):
+@pytest.mark.parametrize("storage", [1, 2])
+def test_empty_and_edgeless_inputs(q, ctx, storage):
     empty = synth.Fragments(10, np.zeros(1, np.int64), np.zeros(0, np.int32),
                             np.zeros(0, np.int8), np.zeros(0, np.uint8), np.zeros(0, np.uint8),
                             np.arange(10), np.ones(10, np.int8))
-    g = ctx.build_graph(empty)
-    assert g.n_nodes == 0 and g.n_blocks == 0
-    sol = ctx.solve(g, replicas=64, steps=10, precision=q.PREC_BF16)
-    h1, h2, bid = ctx.phase(g, sol, 10)
-    assert (h1 == 0).all() and (bid == -1).all()
     lone = synth.Fragments(10, np.array([0, 1, 2, 2], np.int64), np.array([1, 5], np.int32),
                            np.array([1, -1], np.int8), np.array([30, 30], np.uint8),
                            np.zeros(3, np.uint8), np.arange(10), np.ones(10, np.int8))
-    g = ctx.build_graph(lone)
-    assert g.n_blocks == 0
-    sol = ctx.solve(g, replicas=32, steps=10)
-    h1, _, bid = ctx.phase(g, sol, 10)
-    assert (h1 == 0).all()
+    # every step path on graphs without blocks: CSR storage adds the band-tile step and
+    # an SNP-mode solve with deformed re-solves
+    runs = [dict(replicas=64, precision=q.PREC_BF16), dict(replicas=32, precision=q.PREC_FP32)]
+    if storage == 2:
+        runs.append(dict(replicas=128, precision=q.PREC_BF16, step_kernel="csr-band8"))
+    for fr in (empty, lone):
+        for mode in (q.MODE_READ, q.MODE_SNP):
+            g = ctx.build_graph(fr, mode=mode, storage=storage)
+            assert g.n_blocks == 0
+            for kw in runs:
+                extra = dict(deform_h=0.05, deform_tries=2) if mode == q.MODE_SNP else {}
+                sol = ctx.solve(g, steps=10, **kw, **extra)
+                h1, h2, bid = ctx.phase(g, sol, 10)
+                assert (h1 == 0).all() and (bid == -1).all()
 
 
 # ----------------------------------------------------------------------------- J x X precision
