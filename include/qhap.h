@@ -179,7 +179,7 @@ typedef struct {
   int32_t replicas;     /* R >= 1 (multiple of 16 for QH_PREC_BF16) */
   int32_t steps;        /* >= 1 (LINEAR schedule) */
   int32_t schedule;     /* QH_SCHED_LINEAR | QH_SCHED_AUTO */
-  int32_t precision;    /* QH_PREC_FP32 | QH_PREC_BF16 */
+  int32_t precision;    /* QH_PREC_FP32 | QH_PREC_BF16 | QH_PREC_BF16X2 | QH_PREC_FP8 */
   double dt;            /* time step (1.0) */
   double a0;            /* bifurcation parameter target (1.0) */
   double c0;            /* coupling scale; <= 0 selects 0.5 / (sigma sqrt(N)) per
@@ -196,8 +196,13 @@ typedef struct {
                            chip and launch once per step range).  CSR storage
                            (FP32 or BF16): 10 = 4 replicas per lane (R a multiple
                            of 4), 11 = 8 replicas per lane, several neighbours per
-                           warp at once (R a multiple of 8); default 11 for BF16
-                           when R allows, else 10.  Invalid choices -> QH_EINVAL */
+                           warp at once (R a multiple of 8); BF16 only: 12 = the
+                           band (entries within a row tile's neighbourhood) on the
+                           tensor cores, then 11 over the remaining entries (R a
+                           multiple of 128).  Default for CSR: 12 when R allows and
+                           the band holds at least a quarter of the entries, else
+                           11 for BF16 when R allows, else 10.  Invalid choices ->
+                           QH_EINVAL */
   int32_t sb_variant;   /* QH_SB_BALLISTIC (0, the paper's solver), QH_SB_DISCRETE,
                            QH_SB_ADIABATIC */
   double deform_h;      /* SNP mode: the adaptive deformation of the refinement
