@@ -312,7 +312,8 @@ qh_status qh_debug_steps(qh_ctx* ctx, const qh_graph* g, int32_t precision, int3
                          double a0, const double* c0_per_block);
 
 /* qh_debug_steps with an explicit step kernel (BF16 / BF16X2 tile storage: 0..9;
- * CSR storage, FP32 or BF16: 10 or 11) and SB variant (QH_SB_*; not FP8, not CSR):
+ * CSR storage, FP32 or BF16: 10 or 11; CSR storage, BF16: 12) and SB variant (QH_SB_*;
+ * not FP8, not CSR):
  * step_kernel = -1 is the default; otherwise an index into the solver's kernel
  * variants (qh_bsb_opts.step_kernel).  The multi-step variants run all `nsteps`
  * steps in ONE launch, the momentum y held on chip between steps.  QH_EINVAL when
