@@ -147,6 +147,12 @@ __global__ void __launch_bounds__(256) k_step_f32(StepArgs a) {
 }
 
 // ------------------------------------------------------------------ CSR storage
+// CSR step CTAs: 2 vertices (warps) each, 32 warps per SM at 64 registers.  Vertices
+// of one CTA differ in degree and the CTA's slot frees with its slowest warp, so small
+// CTAs keep more warps resident (measured faster than 4- and 8-warp CTAs).
+#ifndef CSR_CTA
+#define CSR_CTA 64
+#endif
 // Vertex-major state ([n_pad][R]): initial draws, thread per (vertex, replica).
 __global__ void k_init_state_vm(const RowTile* __restrict__ rt, const int32_t* __restrict__ pad_node,
                                 const int32_t* __restrict__ local, int32_t n_pad, int32_t R,
@@ -179,7 +185,7 @@ __global__ void k_signs_vm(const float* __restrict__ x, int64_t n, int8_t* st) {
 // a time and broadcast by shuffle; each neighbour costs one 8-byte (BF16) or 16-byte
 // (FP32) load per lane, i.e. a contiguous replica slice per warp.
 template <bool BF16>
-__global__ void __launch_bounds__(256, 4) k_step_csr(StepArgs a, const int64_t* __restrict__ prow,
+__global__ void __launch_bounds__(CSR_CTA, 1024 / CSR_CTA) k_step_csr(StepArgs a, const int64_t* __restrict__ prow,
                                                   const int32_t* __restrict__ pcol,
                                                   const float* __restrict__ pval,
                                                   const __nv_bfloat16* __restrict__ xh_in) {
@@ -301,10 +307,10 @@ __global__ void __launch_bounds__(256, 4) k_step_csr(StepArgs a, const int64_t* 
 // of the first neighbour stream then apply the update.  Per neighbour this costs about
 // half the instructions of k_step_csr: two shuffles, one address, the loads and four
 // packed FP32x2 FMAs per lane.  Both CSR kernels are bound by the latency of the
-// gathers: they run at 64 registers, 4 CTAs (32 warps) per SM, a few bytes spilled in
-// some instantiations, which measured faster than 3 CTAs without spills.
+// gathers: they run at 64 registers, 32 warps per SM, a few bytes spilled in some
+// instantiations, which measured faster than 24 warps without spills.
 template <bool BF16, int P, bool ZB>
-__global__ void __launch_bounds__(256, 4) k_step_csr8(StepArgs a, const int64_t* __restrict__ prow,
+__global__ void __launch_bounds__(CSR_CTA, 1024 / CSR_CTA) k_step_csr8(StepArgs a, const int64_t* __restrict__ prow,
                                                    const int32_t* __restrict__ pcol,
                                                    const float* __restrict__ pval,
                                                    const __nv_bfloat16* __restrict__ xh_in) {
@@ -945,7 +951,8 @@ const char* csr_variant_name(int v, bool bf16) {
 void launch_step_csr(cudaStream_t s, const Graph& g, const StepArgs& a, const float* pval,
                      const __nv_bfloat16* xh_in, int variant, bool remainder) {
   if (g.n_pad == 0) return;
-  const unsigned grid = nblk((int64_t)g.n_pad * 32);
+  // a warp per vertex, CSR_CTA threads per CTA
+  const unsigned grid = (unsigned)(((int64_t)g.n_pad * 32 + CSR_CTA - 1) / CSR_CTA);
   const int64_t* rowp = remainder ? g.rrow_ptr : g.prow_ptr;
   const int32_t* colp = remainder ? g.rcol : g.pcol;
   if ((variant == CSR_LANE8 || variant == CSR_BAND8) && a.R % 8 == 0) {
@@ -953,11 +960,11 @@ void launch_step_csr(cudaStream_t s, const Graph& g, const StepArgs& a, const fl
     const int lanes = a.R >= 256 ? 32 : a.R >= 128 ? 16 : a.R >= 64 ? 8 : 4;
 #define QH_CSR8(P)                                                                               \
   (xh_in == nullptr                                                                              \
-       ? k_step_csr8<false, P, false><<<::qh::counted(grid), 256, 0, s>>>(a, rowp, colp, pval,   \
+       ? k_step_csr8<false, P, false><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, pval,   \
                                                                           nullptr)               \
    : a.zb != nullptr                                                                             \
-       ? k_step_csr8<true, P, true><<<::qh::counted(grid), 256, 0, s>>>(a, rowp, colp, pval, xh_in) \
-       : k_step_csr8<true, P, false><<<::qh::counted(grid), 256, 0, s>>>(a, rowp, colp, pval, xh_in))
+       ? k_step_csr8<true, P, true><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, pval, xh_in) \
+       : k_step_csr8<true, P, false><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, pval, xh_in))
     switch (lanes) {
       case 32: QH_CSR8(1); break;
       case 16: QH_CSR8(2); break;
@@ -968,9 +975,9 @@ void launch_step_csr(cudaStream_t s, const Graph& g, const StepArgs& a, const fl
     return;
   }
   if (xh_in != nullptr)
-    k_step_csr<true><<<::qh::counted(grid), 256, 0, s>>>(a, rowp, colp, pval, xh_in);
+    k_step_csr<true><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, pval, xh_in);
   else
-    k_step_csr<false><<<::qh::counted(grid), 256, 0, s>>>(a, rowp, colp, pval, nullptr);
+    k_step_csr<false><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, pval, nullptr);
 }
 
 void launch_transpose(cudaStream_t s, const float* in, float* out, int64_t rows, int64_t cols) {
