@@ -1047,7 +1047,7 @@ cudaError_t set_attr() {
 }  // namespace
 
 // Once per process and device, outside any stream capture: shared-memory opt-in of
-// every kernel variant and the driver entry point for tensor-map encoding.
+// every kernel variant and the CUDA driver entry point for tensor-map encoding.
 qh_status tc_prepare(Ctx* ctx) {
   cudaError_t e = set_attr<64, 4>();
   if (e == cudaSuccess) e = set_attr<128, 3>();

@@ -165,8 +165,9 @@ def test_snp_edge_two_snp_closed_form(oracle, qa, qb):
         assert W[1, 0] == W[0, 1]
 
 
-def test_snp_edge_survey_reference_values(oracle):
-    # Q=10 equal alleles, and the three-SNP fragment normalised by |S_i| - 1 = 2
+def test_snp_edge_hand_computed_values(oracle):
+    # Q = 10, equal alleles: q = 0.9, P_cis = 0.82, P_trans = 0.18, w = -log10(0.82 / 0.18);
+    # and the three-SNP fragment normalised by |S_i| - 1 = 2 (Eq. edge_weight_SNP)
     fr = _frags_from_M([[1, 1]], qual=[[10, 10]])
     assert oracle.snp_graph(fr).dense()[0, 1] == pytest.approx(-0.6585413472804108, rel=1e-14)
     fr3 = _frags_from_M([[1, 1, -1]], qual=[[10, 20, 30]])
