@@ -512,12 +512,23 @@ __global__ void k_cut_nodes(int32_t n, const int64_t* __restrict__ rp, const int
     int32_t acc[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) acc[k] = 0;
-    if (nr > 0) {
-      for (int64_t e = e0; e < e1; ++e) {
-        const double we = w[e];
-        if (we == 0.0) continue;  // zero edges may reach vertices outside every block
-        const int32_t wi = (int32_t)we;
-        const int8_t* sb = st + (size_t)pad_index[col[e]] * R + r;
+    // edges in groups of 32: each lane loads one edge's weight and padded column (the
+    // next group's while this group is summed), the warp takes them in order by shuffle
+    int32_t wv_n = e0 + lane < e1 ? (int32_t)w[e0 + lane] : 0;
+    int32_t pv_n = wv_n != 0 ? pad_index[col[e0 + lane]] : 0;
+    for (int64_t eg = e0; eg < e1; eg += 32) {
+      const int ne = e1 - eg < 32 ? (int)(e1 - eg) : 32;
+      const int32_t wv = wv_n, pv = pv_n;
+      const int64_t en = eg + 32 + lane;
+      wv_n = en < e1 ? (int32_t)w[en] : 0;
+      pv_n = wv_n != 0 ? pad_index[col[en]] : 0;
+#pragma unroll 4
+      for (int k = 0; k < ne; ++k) {
+        const int32_t wi = __shfl_sync(0xffffffffu, wv, k);
+        const int32_t p = __shfl_sync(0xffffffffu, pv, k);
+        // zero edges may reach vertices outside every block: skipped before any load
+        if (wi == 0 || nr <= 0) continue;
+        const int8_t* sb = st + (size_t)p * R + r;
         if (vec && nr == per) {
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
@@ -530,8 +541,8 @@ __global__ void k_cut_nodes(int32_t n, const int64_t* __restrict__ rp, const int
           }
         } else {
 #pragma unroll
-          for (int k = 0; k < 32; ++k)
-            if (k < nr) acc[k] += wi * sb[k];
+          for (int k2 = 0; k2 < 32; ++k2)
+            if (k2 < nr) acc[k2] += wi * sb[k2];
         }
       }
     }
@@ -613,12 +624,26 @@ __global__ void k_cut_nodes_df(int32_t n, const int64_t* __restrict__ rp,
       hi[k] = s;
       lo[k] = __fadd_rn(lo[k], __fadd_rn(err, tl));
     };
-    if (nr > 0) {
-      for (int64_t e = e0; e < e1; ++e) {
-        const double we = w[e];
-        if (we == 0.0) continue;  // zero edges may reach vertices outside every block
-        const float wh = (float)we, wl = (float)(we - (double)wh);
-        const int8_t* sb = st + (size_t)pad_index[col[e]] * R + r;
+    // edges in groups of 32, as in k_cut_nodes; the terms still go in edge order
+    double wv_n = e0 + lane < e1 ? w[e0 + lane] : 0.0;
+    int32_t pv_n = wv_n != 0.0 ? pad_index[col[e0 + lane]] : 0;
+    for (int64_t eg = e0; eg < e1; eg += 32) {
+      const int ne = e1 - eg < 32 ? (int)(e1 - eg) : 32;
+      const float whv = (float)wv_n, wlv = (float)(wv_n - (double)(float)wv_n);
+      const bool nzv = wv_n != 0.0;
+      const int32_t pv = pv_n;
+      const int64_t en = eg + 32 + lane;
+      wv_n = en < e1 ? w[en] : 0.0;
+      pv_n = wv_n != 0.0 ? pad_index[col[en]] : 0;
+#pragma unroll 4
+      for (int k = 0; k < ne; ++k) {
+        const float wh = __shfl_sync(0xffffffffu, whv, k);
+        const float wl = __shfl_sync(0xffffffffu, wlv, k);
+        const int32_t p = __shfl_sync(0xffffffffu, pv, k);
+        const bool nz = __shfl_sync(0xffffffffu, (int)nzv, k) != 0;
+        // zero edges may reach vertices outside every block: skipped before any load
+        if (!nz || nr <= 0) continue;
+        const int8_t* sb = st + (size_t)p * R + r;
         if (vec && nr == per) {
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
@@ -631,8 +656,8 @@ __global__ void k_cut_nodes_df(int32_t n, const int64_t* __restrict__ rp,
           }
         } else {
 #pragma unroll
-          for (int k = 0; k < 32; ++k)
-            if (k < nr) add(k, sb[k], wh, wl);
+          for (int k2 = 0; k2 < 32; ++k2)
+            if (k2 < nr) add(k2, sb[k2], wh, wl);
         }
       }
     }
