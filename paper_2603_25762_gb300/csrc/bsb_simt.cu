@@ -596,6 +596,7 @@ __global__ void k_cut_nodes_few(int32_t n, const int64_t* __restrict__ rp,
 // hi addition (Knuth's TwoSum), which carries about 48 bits: within ~1e-11 of the FP64
 // sum even over thousands of edges, at FP32 speed (this part's FP64 rate is a small
 // fraction of its FP32 rate).  Signs are +-1, so the terms are exact negations.
+template <int PER>
 __global__ void k_cut_nodes_df(int32_t n, const int64_t* __restrict__ rp,
                                const int32_t* __restrict__ col, const double* __restrict__ w,
                                const int32_t* __restrict__ block_of,
@@ -613,9 +614,9 @@ __global__ void k_cut_nodes_df(int32_t n, const int64_t* __restrict__ rp,
   for (int32_t r0 = 0; r0 < R; r0 += 32 * per) {
     const int32_t r = r0 + per * lane;
     const int nr = max(0, min(per, R - r));
-    float hi[32], lo[32];
+    float hi[PER], lo[PER];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) hi[k] = lo[k] = 0.f;
+    for (int k = 0; k < PER; ++k) hi[k] = lo[k] = 0.f;
     auto add = [&](int k, int sg, float wh, float wl) {
       const float th = sg > 0 ? wh : -wh, tl = sg > 0 ? wl : -wl;
       const float s = __fadd_rn(hi[k], th);
@@ -646,7 +647,7 @@ __global__ void k_cut_nodes_df(int32_t n, const int64_t* __restrict__ rp,
         const int8_t* sb = st + (size_t)p * R + r;
         if (vec && nr == per) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
+          for (int q = 0; q < PER / 4; ++q) {
             if (4 * q >= per) break;
             const char4 c = *reinterpret_cast<const char4*>(sb + 4 * q);
             add(4 * q + 0, c.x, wh, wl);
@@ -656,14 +657,14 @@ __global__ void k_cut_nodes_df(int32_t n, const int64_t* __restrict__ rp,
           }
         } else {
 #pragma unroll
-          for (int k2 = 0; k2 < 32; ++k2)
+          for (int k2 = 0; k2 < PER; ++k2)
             if (k2 < nr) add(k2, sb[k2], wh, wl);
         }
       }
     }
     const int8_t* sa = st + (size_t)pa * R + r;
 #pragma unroll
-    for (int k = 0; k < 32; ++k)
+    for (int k = 0; k < PER; ++k)
       if (k < nr) node_val[(size_t)pa * R + r + k] = (double)sa[k] * ((double)hi[k] + (double)lo[k]);
   }
 }
@@ -1036,9 +1037,10 @@ void launch_cut(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t
   else if (R <= 4)
     k_cut_nodes_few<<<::qh::counted(nblk((int64_t)g.n_nodes * 32)), 256, 0, s>>>(
         g.n_nodes, g.row_ptr, g.col, w, g.block_of, g.pad_index, signs_t, R, node_val, active);
-  else
-    k_cut_nodes_df<<<::qh::counted(nblk((int64_t)g.n_nodes * 32)), 256, 0, s>>>(
-        g.n_nodes, g.row_ptr, g.col, w, g.block_of, g.pad_index, signs_t, R, per, node_val, active);
+  else  // at most 8 replicas per lane: 16 accumulators, more warps in flight
+    k_cut_nodes_df<8><<<::qh::counted(nblk((int64_t)g.n_nodes * 32)), 256, 0, s>>>(
+        g.n_nodes, g.row_ptr, g.col, w, g.block_of, g.pad_index, signs_t, R, per < 8 ? per : 8,
+        node_val, active);
   dim3 grid((R + 31) / 32, g.n_blocks);
   k_cut_reduce<<<::qh::counted(grid), 1024, 0, s>>>(g.n_blocks, g.pad_off, g.block_ptr, R, node_val, sum_w, cuts,
                                      active);
