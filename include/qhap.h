@@ -204,7 +204,10 @@ typedef struct {
                            11 for BF16 when R allows, else 10.  Invalid choices ->
                            QH_EINVAL */
   int32_t sb_variant;   /* QH_SB_BALLISTIC (0, the paper's solver), QH_SB_DISCRETE,
-                           QH_SB_ADIABATIC */
+                           QH_SB_ADIABATIC.  The latter two run on every storage
+                           and step kernel of the FP32, BF16 and BF16X2 precisions
+                           except the persistent per-step kernels 4 and 5
+                           (QH_EINVAL); FP8 -> QH_EUNSUPPORTED */
   double deform_h;      /* SNP mode: the adaptive deformation of the refinement
                            (0 = off, the plain refinement).  When a solve of a block
                            ends with a cut <= 0 or with all vertices in one subset,
@@ -313,7 +316,7 @@ qh_status qh_debug_steps(qh_ctx* ctx, const qh_graph* g, int32_t precision, int3
 
 /* qh_debug_steps with an explicit step kernel (BF16 / BF16X2 tile storage: 0..9;
  * CSR storage, FP32 or BF16: 10 or 11; CSR storage, BF16: 12) and SB variant (QH_SB_*;
- * not FP8, not CSR):
+ * not FP8):
  * step_kernel = -1 is the default; otherwise an index into the solver's kernel
  * variants (qh_bsb_opts.step_kernel).  The multi-step variants run all `nsteps`
  * steps in ONE launch, the momentum y held on chip between steps.  QH_EINVAL when

@@ -89,6 +89,9 @@ def _setup(L):
     L.qo_sb_solve_h.argtypes = [I32, P, P, P, I32, P, I32, D, D, D, U64, I64, I32, P, P, P, I32, D]
     L.qo_refine_h.restype = I32
     L.qo_refine_h.argtypes = [I32, P, P, P, I32, P, I32, D, D, D, U64, I64, I32, P, P, D, I32, P]
+    L.qo_refine_v.restype = I32
+    L.qo_refine_v.argtypes = [I32, P, P, P, I32, P, I32, D, D, D, U64, I64, I32, P, P, D, I32, P,
+                              I32]
     L.qo_vote.restype = None
     L.qo_vote.argtypes = [I32, I32, P, P, P, P, P, I32, P, P]
     L.qo_parity.restype = None
@@ -279,19 +282,20 @@ def bsb_solve(g: CSR, replica_ids, steps, seed, block=0, it=0, dt=1.0, a0=1.0, c
 
 
 def refine(g: CSR, replica_ids, steps, seed, block=0, refine_max=15, dt=1.0, a0=1.0, c0=0.0,
-           deform_h=0.0, deform_tries=0, stats=None):
+           deform_h=0.0, deform_tries=0, stats=None, variant="ballistic"):
     """SNP-based iterative refinement: returns (C counts, accepted partitions, first cut,
     gauged w).  deform_h > 0: re-solve with the deformation field (up to deform_tries
     times, strength deform_h 2^(k-1)) when a solve's cut is <= 0.  stats (a dict, if
-    given) receives "solves", the number of bSB solves made."""
+    given) receives "solves", the number of bSB solves made.  variant: the SB variant
+    of every solve (as in bsb_run)."""
     rid = _c(replica_ids, np.int32)
     w = g.w.copy()
     Cc = np.zeros(g.n, np.int32)
     first = C.c_double(0.0)
     solves = C.c_int32(0)
-    it = lib().qo_refine_h(g.n, _p(g.row_ptr), _p(g.col), _p(w), rid.shape[0], _p(rid), steps,
+    it = lib().qo_refine_v(g.n, _p(g.row_ptr), _p(g.col), _p(w), rid.shape[0], _p(rid), steps,
                            dt, a0, c0, seed, block, refine_max, _p(Cc), C.byref(first),
-                           deform_h, deform_tries, C.byref(solves))
+                           deform_h, deform_tries, C.byref(solves), SB_VARIANTS[variant])
     if stats is not None:
         stats["solves"] = solves.value
     return Cc, it, first.value, w
@@ -335,9 +339,11 @@ def phase_read(fr, mode=READ_SIGNED, replica_ids=range(8), steps=1000, seed=1, d
 
 
 def phase_snp(fr, replica_ids=range(8), steps=1000, seed=1, refine_max=15, porec_alpha=0.1,
-              linkage_k=10, dt=1.0, a0=1.0, c0=0.0, deform_h=0.0, deform_tries=0):
+              linkage_k=10, dt=1.0, a0=1.0, c0=0.0, deform_h=0.0, deform_tries=0,
+              variant="ballistic"):
     """Whole SNP-based path: graph -> blocks -> refinement (bSB per iteration) -> parity.
-    "iters": accepted partitions per block; "solves": bSB solves per block."""
+    "iters": accepted partitions per block; "solves": bSB solves per block.  variant:
+    the SB variant of the solves (bSB is the paper's)."""
     g = snp_graph(fr, porec_alpha, linkage_k)
     blocks = blocks_of(g)
     Ctot = np.zeros(fr.n_snps, np.int32)
@@ -348,7 +354,7 @@ def phase_snp(fr, replica_ids=range(8), steps=1000, seed=1, refine_max=15, porec
         sub = g.subgraph(nodes)
         st = {}
         Cc, it, first, _ = refine(sub, list(replica_ids), steps, seed, b, refine_max, dt, a0, c0,
-                                  deform_h, deform_tries, st)
+                                  deform_h, deform_tries, st, variant)
         Ctot[nodes] = Cc
         in_block[nodes] = 1
         snp_block[nodes] = b

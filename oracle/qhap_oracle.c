@@ -481,10 +481,19 @@ double qo_bsb_solve(int32_t n, const int64_t* rp, const int32_t* col, const doub
  * subset (tie: the subset without the lowest-index vertex) and invert the
  * sign of every edge crossing the partition (w' = -w if s_u != s_v).
  * w is modified in place (the final gauged weights).  Returns iterations done. */
+int32_t qo_refine_v(int32_t n, const int64_t* rp, const int32_t* col, double* w, int32_t R,
+                    const int32_t* replica_ids, int32_t steps, double dt, double a0, double c0,
+                    uint64_t seed, int64_t block, int32_t refine_max, int32_t* C,
+                    double* first_cut, double deform_h, int32_t deform_tries, int32_t* solves,
+                    int32_t variant);
+
 int32_t qo_refine_h(int32_t n, const int64_t* rp, const int32_t* col, double* w, int32_t R,
                     const int32_t* replica_ids, int32_t steps, double dt, double a0, double c0,
                     uint64_t seed, int64_t block, int32_t refine_max, int32_t* C,
-                    double* first_cut, double deform_h, int32_t deform_tries, int32_t* solves);
+                    double* first_cut, double deform_h, int32_t deform_tries, int32_t* solves) {
+  return qo_refine_v(n, rp, col, w, R, replica_ids, steps, dt, a0, c0, seed, block, refine_max,
+                     C, first_cut, deform_h, deform_tries, solves, 0);
+}
 
 int32_t qo_refine(int32_t n, const int64_t* rp, const int32_t* col, double* w, int32_t R,
                   const int32_t* replica_ids, int32_t steps, double dt, double a0, double c0,
@@ -502,11 +511,13 @@ int32_t qo_refine(int32_t n, const int64_t* rp, const int32_t* col, double* w, i
  * the k-th re-solve; a positive cut is then accepted as usual.  Every solve, plain or
  * deformed, counts toward refine_max and draws its initial state with its own
  * iteration index.  Returns the number of accepted partitions; *solves (if not NULL)
- * receives the number of solves.                                                  */
-int32_t qo_refine_h(int32_t n, const int64_t* rp, const int32_t* col, double* w, int32_t R,
+ * receives the number of solves.  variant: the SB variant of every solve (0 = bSB,
+ * the paper's solver; 1 = dSB, 2 = aSB as in qo_sb_run).                           */
+int32_t qo_refine_v(int32_t n, const int64_t* rp, const int32_t* col, double* w, int32_t R,
                     const int32_t* replica_ids, int32_t steps, double dt, double a0, double c0,
                     uint64_t seed, int64_t block, int32_t refine_max, int32_t* C,
-                    double* first_cut, double deform_h, int32_t deform_tries, int32_t* solves) {
+                    double* first_cut, double deform_h, int32_t deform_tries, int32_t* solves,
+                    int32_t variant) {
   int8_t* s = (int8_t*)malloc((size_t)(n > 0 ? n : 1));
   double* cuts = (double*)malloc(sizeof(double) * (size_t)(R > 0 ? R : 1));
   int32_t it = 0, accepted = 0, tries = 0;
@@ -515,7 +526,7 @@ int32_t qo_refine_h(int32_t n, const int64_t* rp, const int32_t* col, double* w,
     int32_t br;
     double h = tries == 0 ? 0.0 : deform_h * ldexp(1.0, tries - 1);
     double cut = qo_sb_solve_h(n, rp, col, w, R, replica_ids, steps, dt, a0, c0, seed, block, it,
-                               s, cuts, &br, 0, h);
+                               s, cuts, &br, variant, h);
     if (it == 0 && first_cut) *first_cut = cut;
     int32_t n_pos = 0;
     for (int32_t v = 0; v < n; ++v) n_pos += (s[v] > 0);

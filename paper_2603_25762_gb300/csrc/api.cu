@@ -444,8 +444,8 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     return set_err(ctx, QH_EINVAL, "bad precision");
   if (o->sb_variant < QH_SB_BALLISTIC || o->sb_variant > QH_SB_ADIABATIC)
     return set_err(ctx, QH_EINVAL, "bad sb_variant");
-  if (o->sb_variant != QH_SB_BALLISTIC && (o->precision == QH_PREC_FP8 || G.csr_mode))
-    return set_err(ctx, QH_EUNSUPPORTED, "discrete / adiabatic SB need FP32 or BF16 tile storage");
+  if (o->sb_variant != QH_SB_BALLISTIC && o->precision == QH_PREC_FP8)
+    return set_err(ctx, QH_EUNSUPPORTED, "discrete / adiabatic SB need FP32, BF16 or BF16X2 precision");
   if (o->sb_variant != QH_SB_BALLISTIC && o->step_kernel >= 0 && !sb_kernel_ok(o->step_kernel, o->sb_variant))
     return set_err(ctx, QH_EINVAL, "this step_kernel implements the ballistic update only");
   if (o->precision == QH_PREC_FP8 && G.csr_mode)
@@ -1210,8 +1210,8 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
   qh_status st = debug_common(ctx, g, precision, R, a, c0_per_block, steps, &c0h);
   if (st) return st;
   a.sb = sb_variant;
-  if (sb_variant != QH_SB_BALLISTIC && (precision == QH_PREC_FP8 || g.csr_mode))
-    return set_err(ctx, QH_EUNSUPPORTED, "discrete / adiabatic SB need FP32 or BF16 tile storage");
+  if (sb_variant != QH_SB_BALLISTIC && precision == QH_PREC_FP8)
+    return set_err(ctx, QH_EUNSUPPORTED, "discrete / adiabatic SB need FP32, BF16 or BF16X2 precision");
   a.deform = nullptr;
   if (field_per_block != nullptr && g.n_blocks > 0) {
     std::vector<float> hf(g.n_blocks);

@@ -43,10 +43,13 @@ __global__ void k_f32_to_bf16(const float* __restrict__ x, __nv_bfloat16* xh, in
 }
 
 // Product operand of a discrete-SB state: sgn(x) at real vertices, 0 at padding.
+// State layout [R][n_pad] (r_vm = 0) or vertex-major [n_pad][r_vm].
 __global__ void k_x_to_sign_bf16(const float* __restrict__ x, __nv_bfloat16* xh, int64_t n,
-                                 int32_t n_pad, const int32_t* __restrict__ pad_node) {
+                                 int32_t n_pad, int32_t r_vm, const int32_t* __restrict__ pad_node) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) xh[i] = __float2bfloat16_rn(pad_node[i % n_pad] >= 0 ? sb_operand(QH_SB_DISCRETE, x[i]) : 0.f);
+  if (i >= n) return;
+  const int64_t col = r_vm > 0 ? i / r_vm : i % n_pad;
+  xh[i] = __float2bfloat16_rn(pad_node[col] >= 0 ? sb_operand(QH_SB_DISCRETE, x[i]) : 0.f);
 }
 
 // ------------------------------------------------------------------ FP32 step
@@ -153,11 +156,18 @@ __global__ void __launch_bounds__(256) k_step_f32(StepArgs a) {
 #ifndef CSR_CTA
 #define CSR_CTA 64
 #endif
+// The discrete-SB operand of four gathered values.
+__device__ __forceinline__ float4 sgn4(float4 v) {
+  return make_float4(sb_operand(QH_SB_DISCRETE, v.x), sb_operand(QH_SB_DISCRETE, v.y),
+                     sb_operand(QH_SB_DISCRETE, v.z), sb_operand(QH_SB_DISCRETE, v.w));
+}
+
 // Vertex-major state ([n_pad][R]): initial draws, thread per (vertex, replica).
 __global__ void k_init_state_vm(const RowTile* __restrict__ rt, const int32_t* __restrict__ pad_node,
                                 const int32_t* __restrict__ local, int32_t n_pad, int32_t R,
                                 int32_t replica_base, uint64_t seed, int32_t iter, float* x,
-                                float* y, __nv_bfloat16* xh, const int32_t* __restrict__ active) {
+                                float* y, __nv_bfloat16* xh, const int32_t* __restrict__ active,
+                                int32_t sb) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= (int64_t)n_pad * R) return;
   const int32_t col = (int32_t)(i / R), r = (int32_t)(i % R);
@@ -172,7 +182,7 @@ __global__ void k_init_state_vm(const RowTile* __restrict__ rt, const int32_t* _
   }
   x[i] = xv;
   y[i] = yv;
-  if (xh != nullptr) xh[i] = __float2bfloat16_rn(xv);
+  if (xh != nullptr) xh[i] = __float2bfloat16_rn(v >= 0 ? sb_operand(sb, xv) : 0.f);
 }
 
 __global__ void k_signs_vm(const float* __restrict__ x, int64_t n, int8_t* st) {
@@ -184,7 +194,9 @@ __global__ void k_signs_vm(const float* __restrict__ x, int64_t n, int8_t* st) {
 // 4l .. 4l+3 of every 128-replica chunk.  The row's (column, J) pairs are read 32 at
 // a time and broadcast by shuffle; each neighbour costs one 8-byte (BF16) or 16-byte
 // (FP32) load per lane, i.e. a contiguous replica slice per warp.
-template <bool BF16>
+// DISC (FP32 operands only): discrete SB, the product takes sgn of each gathered x.
+// BF16 operands already hold the variant's operand (sgn(x) for discrete SB).
+template <bool BF16, bool DISC>
 __global__ void __launch_bounds__(CSR_CTA, 1024 / CSR_CTA) k_step_csr(StepArgs a, const int64_t* __restrict__ prow,
                                                   const int32_t* __restrict__ pcol,
                                                   const float* __restrict__ pval,
@@ -264,6 +276,9 @@ __global__ void __launch_bounds__(CSR_CTA, 1024 / CSR_CTA) k_step_csr(StepArgs a
 #pragma unroll
           for (int q = 0; q < NB; ++q)
             xv[q] = *reinterpret_cast<const float4*>(a.xin + (size_t)cc[q] * a.R + r);
+          if (DISC)
+#pragma unroll
+            for (int q = 0; q < NB; ++q) xv[q] = sgn4(xv[q]);
 #pragma unroll
           for (int q = 0; q < NB; ++q) {
             acc[0] = fmaf(jv[q], xv[q].x, acc[0]);
@@ -290,8 +305,8 @@ __global__ void __launch_bounds__(CSR_CTA, 1024 / CSR_CTA) k_step_csr(StepArgs a
     *reinterpret_cast<float4*>(xdst + idx) = make_float4(xs[0], xs[1], xs[2], xs[3]);
     *reinterpret_cast<float4*>(a.y + idx) = make_float4(ys[0], ys[1], ys[2], ys[3]);
     if (BF16) {
-      __nv_bfloat162 p0 = __floats2bfloat162_rn(xs[0], xs[1]);
-      __nv_bfloat162 p1 = __floats2bfloat162_rn(xs[2], xs[3]);
+      __nv_bfloat162 p0 = __floats2bfloat162_rn(sb_operand(a.sb, xs[0]), sb_operand(a.sb, xs[1]));
+      __nv_bfloat162 p1 = __floats2bfloat162_rn(sb_operand(a.sb, xs[2]), sb_operand(a.sb, xs[3]));
       uint2 u;
       u.x = *reinterpret_cast<uint32_t*>(&p0);
       u.y = *reinterpret_cast<uint32_t*>(&p1);
@@ -309,7 +324,7 @@ __global__ void __launch_bounds__(CSR_CTA, 1024 / CSR_CTA) k_step_csr(StepArgs a
 // packed FP32x2 FMAs per lane.  Both CSR kernels are bound by the latency of the
 // gathers: they run at 64 registers, 32 warps per SM, a few bytes spilled in some
 // instantiations, which measured faster than 24 warps without spills.
-template <bool BF16, int P, bool ZB>
+template <bool BF16, int P, bool ZB, bool DISC>
 __global__ void __launch_bounds__(CSR_CTA, 1024 / CSR_CTA) k_step_csr8(StepArgs a, const int64_t* __restrict__ prow,
                                                    const int32_t* __restrict__ pcol,
                                                    const float* __restrict__ pval,
@@ -390,8 +405,8 @@ __global__ void __launch_bounds__(CSR_CTA, 1024 / CSR_CTA) k_step_csr8(StepArgs 
 #pragma unroll
           for (int q = 0; q < NB; ++q) {
             const float4* src4 = reinterpret_cast<const float4*>(a.xin + (size_t)cc[q] * a.R + r);
-            xv[q][0] = src4[0];
-            xv[q][1] = src4[1];
+            xv[q][0] = DISC ? sgn4(src4[0]) : src4[0];
+            xv[q][1] = DISC ? sgn4(src4[1]) : src4[1];
           }
 #pragma unroll
           for (int q = 0; q < NB; ++q) {
@@ -449,7 +464,8 @@ __global__ void __launch_bounds__(CSR_CTA, 1024 / CSR_CTA) k_step_csr8(StepArgs 
       uint32_t* uw = &u.x;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        __nv_bfloat162 p2 = __floats2bfloat162_rn(xs[2 * j], xs[2 * j + 1]);
+        __nv_bfloat162 p2 =
+            __floats2bfloat162_rn(sb_operand(a.sb, xs[2 * j]), sb_operand(a.sb, xs[2 * j + 1]));
         uw[j] = *reinterpret_cast<uint32_t*>(&p2);
       }
       *reinterpret_cast<uint4*>(a.xh_out + idx) = u;
@@ -941,7 +957,7 @@ void launch_init_state(cudaStream_t s, const Graph& g, int32_t R, int32_t replic
     const int64_t n = (int64_t)g.n_pad * R;
     k_init_state_vm<<<::qh::counted(nblk(n)), 256, 0, s>>>(g.rt, g.pad_node, g.local, g.n_pad, R,
                                                           replica_base, seed, iter, x, y, xh,
-                                                          active);
+                                                          active, sb);
     return;
   }
   dim3 grid(nblk(g.n_pad), R);
@@ -952,8 +968,9 @@ void launch_init_state(cudaStream_t s, const Graph& g, int32_t R, int32_t replic
 void launch_x_operand(cudaStream_t s, const Graph& g, int32_t sb, const float* x,
                       __nv_bfloat16* xh, int64_t n) {
   if (n <= 0) return;
-  if (sb == QH_SB_DISCRETE)
-    k_x_to_sign_bf16<<<::qh::counted(nblk(n)), 256, 0, s>>>(x, xh, n, g.n_pad, g.pad_node);
+  if (sb == QH_SB_DISCRETE)  // CSR storage keeps the state vertex-major
+    k_x_to_sign_bf16<<<::qh::counted(nblk(n)), 256, 0, s>>>(
+        x, xh, n, g.n_pad, g.csr_mode ? (int32_t)(n / g.n_pad) : 0, g.pad_node);
   else
     k_f32_to_bf16<<<::qh::counted(nblk(n)), 256, 0, s>>>(x, xh, n);
 }
@@ -981,16 +998,22 @@ void launch_step_csr(cudaStream_t s, const Graph& g, const StepArgs& a, const fl
   const unsigned grid = (unsigned)(((int64_t)g.n_pad * 32 + CSR_CTA - 1) / CSR_CTA);
   const int64_t* rowp = remainder ? g.rrow_ptr : g.prow_ptr;
   const int32_t* colp = remainder ? g.rcol : g.pcol;
+  const bool disc = a.sb == QH_SB_DISCRETE;  // FP32 operands: sgn of the gathered x
   if ((variant == CSR_LANE8 || variant == CSR_BAND8) && a.R % 8 == 0) {
     // lanes per neighbour row: 8 replicas each, at most a warp
     const int lanes = a.R >= 256 ? 32 : a.R >= 128 ? 16 : a.R >= 64 ? 8 : 4;
 #define QH_CSR8(P)                                                                               \
-  (xh_in == nullptr                                                                              \
-       ? k_step_csr8<false, P, false><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, pval,   \
-                                                                          nullptr)               \
+  (xh_in == nullptr && disc                                                                      \
+       ? k_step_csr8<false, P, false, true><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, \
+                                                                          pval, nullptr)         \
+   : xh_in == nullptr                                                                            \
+       ? k_step_csr8<false, P, false, false><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, \
+                                                                          pval, nullptr)         \
    : a.zb != nullptr                                                                             \
-       ? k_step_csr8<true, P, true><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, pval, xh_in) \
-       : k_step_csr8<true, P, false><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, pval, xh_in))
+       ? k_step_csr8<true, P, true, false><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, \
+                                                                          pval, xh_in)           \
+       : k_step_csr8<true, P, false, false><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, \
+                                                                          pval, xh_in))
     switch (lanes) {
       case 32: QH_CSR8(1); break;
       case 16: QH_CSR8(2); break;
@@ -1001,9 +1024,11 @@ void launch_step_csr(cudaStream_t s, const Graph& g, const StepArgs& a, const fl
     return;
   }
   if (xh_in != nullptr)
-    k_step_csr<true><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, pval, xh_in);
+    k_step_csr<true, false><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, pval, xh_in);
+  else if (disc)
+    k_step_csr<false, true><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, pval, nullptr);
   else
-    k_step_csr<false><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, pval, nullptr);
+    k_step_csr<false, false><<<::qh::counted(grid), CSR_CTA, 0, s>>>(a, rowp, colp, pval, nullptr);
 }
 
 void launch_transpose(cudaStream_t s, const float* in, float* out, int64_t rows, int64_t cols) {

@@ -1,6 +1,7 @@
 """Discrete (dSB) and adiabatic (aSB) simulated bifurcation on the GPU against the FP64
 oracle, through the C ABI: the state after a few steps and whole solves, on the FP32
-tile path, the BF16 per-step kernels and the multi-step kernel.
+tile path, the BF16 per-step kernels, the multi-step kernel and the CSR steps (FP32 and
+BF16 gathers, and the band on the tensor cores plus the remainder).
 
 Bars as for ballistic SB: state within 1e-5 (FP32) / 1e-2 (BF16) relative Frobenius
 of the oracle's after a few steps; best cut >= 0.999 x the oracle's on the same seed,
@@ -37,14 +38,15 @@ def _rel_frob(a, b):
 
 
 @pytest.mark.parametrize("variant", ["discrete", "adiabatic"])
-@pytest.mark.parametrize("precision,kernel,tol", [(0, None, 1e-5), (1, None, 1e-2),
-                                                  (1, "cta-bn128-s2-x3", 1e-2),
-                                                  (1, "multistep-stream-tile", 1e-2),
-                                                  (1, "multistep-jres-group", 1e-2)])
-def test_variant_steps_match_oracle(q, ctx, oracle, variant, precision, kernel, tol):
+@pytest.mark.parametrize("precision,kernel,storage,tol", [
+    (0, None, 1, 1e-5), (1, None, 1, 1e-2), (1, "cta-bn128-s2-x3", 1, 1e-2),
+    (1, "multistep-stream-tile", 1, 1e-2), (1, "multistep-jres-group", 1, 1e-2),
+    (0, "csr-lane4", 2, 1e-5), (0, "csr-lane8", 2, 1e-5), (1, "csr-lane4", 2, 1e-2),
+    (1, "csr-lane8", 2, 1e-2), (1, "csr-band8", 2, 1e-2)])
+def test_variant_steps_match_oracle(q, ctx, oracle, variant, precision, kernel, storage, tol):
     import torch
     fr = synth.batched_blocks(1004, n_blocks=5, n_min=80, n_max=400)
-    g = ctx.build_graph(fr, mode=q.MODE_READ)
+    g = ctx.build_graph(fr, mode=q.MODE_READ, storage=storage)
     og = oracle.read_graph(fr, oracle.READ_SIGNED)
     blocks = oracle.blocks_of(og)
     n_pad, pidx, c0 = g.layout()
@@ -79,10 +81,12 @@ def test_variant_steps_match_oracle(q, ctx, oracle, variant, precision, kernel, 
 
 
 @pytest.mark.parametrize("variant", ["discrete", "adiabatic"])
-@pytest.mark.parametrize("precision,kernel", [(0, None), (1, None), (1, "multistep-stream-group")])
-def test_variant_solve_vs_oracle(q, ctx, oracle, variant, precision, kernel):
+@pytest.mark.parametrize("precision,kernel,storage", [
+    (0, None, 1), (1, None, 1), (1, "multistep-stream-group", 1), (0, None, 2), (1, None, 2),
+    (1, "csr-lane8", 2)])
+def test_variant_solve_vs_oracle(q, ctx, oracle, variant, precision, kernel, storage):
     fr = synth.batched_blocks(1004, n_blocks=6, n_min=40, n_max=300)
-    g = ctx.build_graph(fr, mode=q.MODE_READ)
+    g = ctx.build_graph(fr, mode=q.MODE_READ, storage=storage)
     R = 128
     sol = ctx.solve(g, replicas=R, steps=800, precision=precision, seed=7, dt=DT[variant],
                     variant=variant, step_kernel=kernel)
@@ -106,5 +110,34 @@ def test_variant_unsupported_combinations(q, ctx):
         ctx.solve(g, replicas=128, steps=10, precision=q.PREC_BF16, variant="adiabatic",
                   step_kernel="persistent-bn128")
     gc = ctx.build_graph(fr, storage=q.STORAGE_CSR)
-    with pytest.raises(RuntimeError):  # and the CSR step
-        ctx.solve(gc, replicas=64, steps=10, precision=q.PREC_BF16, variant="discrete")
+    with pytest.raises(RuntimeError):  # FP8 needs tile storage in any case
+        ctx.solve(gc, replicas=64, steps=10, precision=q.PREC_FP8, variant="discrete")
+
+
+@pytest.mark.parametrize("variant", ["discrete", "adiabatic"])
+def test_variant_snp_refinement_csr_vs_tiles(q, ctx, oracle, variant):
+    """The SNP refinement (gauge, re-solves) with dSB / aSB on both storages at FP32,
+    against the oracle's refinement with the same variant, seed and replica indices:
+    the first solve's best cut >= 0.999 x the oracle's; the final partition's cut
+    >= 0.999 x the oracle's for dSB.  aSB runs at dt 0.25 (at 0.5 it collapses on SNP
+    graphs) and its refined cut varies by a few per cent between replica sets (oracle,
+    four sets of 64: 491 .. 507), so its bar there is 0.97."""
+    fr = synth.region_reads(33, n_snps=400, region=150_000, n_reads=90, len_mean=9000,
+                            len_sd=3000, flip_p=0.08, miss_p=0.0, qual=(7, 30))
+    dt = {"discrete": 1.0, "adiabatic": 0.25}[variant]
+    kw = dict(replicas=64, steps=400, precision=q.PREC_FP32, seed=6, refine_max=15, dt=dt,
+              variant=variant)
+    sols = [ctx.solve(ctx.build_graph(fr, mode=q.MODE_SNP, storage=s), **kw)
+            for s in (q.STORAGE_TILES, q.STORAGE_CSR)]
+    res = oracle.phase_snp(fr, range(64), 400, seed=6, refine_max=15, dt=dt, variant=variant)
+    og = res["graph"]
+    bar = 0.999 if variant == "discrete" else 0.97
+    for b, nodes in enumerate(res["blocks"]):
+        sub = og.subgraph(nodes)
+        p_or = np.where(res["C"][nodes] % 2 == 0, 1, -1).astype(np.int8)
+        for sol in sols:
+            info = sol.block(b, len(nodes))
+            assert info["best_cut"] == pytest.approx(oracle.cut(sub, info["spins"]), rel=1e-12,
+                                                     abs=1e-9)
+            assert sol.cuts()[b].max() >= 0.999 * res["first_cuts"][b] - 1e-9
+            assert info["best_cut"] >= bar * oracle.cut(sub, p_or) - 1e-9

@@ -633,3 +633,34 @@ def test_refine_with_deformation_matches_plain_when_cuts_stay_positive(oracle):
     b = oracle.phase_snp(fr, range(8), 300, seed=2, refine_max=15, deform_h=0.02, deform_tries=2)
     assert np.array_equal(a["hap1"], b["hap1"])
     assert (b["solves"] >= a["solves"]).all()
+
+
+@pytest.mark.parametrize("variant,dt", [("discrete", 1.0), ("adiabatic", 0.25)])
+def test_refinement_with_sb_variants(oracle, variant, dt):
+    """The refinement runs every solve with the chosen SB variant: its first solve is
+    that variant's solve of the ungauged block (a different solve from bSB's), and the
+    final parity partition never cuts less than that first solve.  dSB phases error-free
+    reads exactly.  aSB (dt 0.25: at 0.5 its explicit cubic term collapses every
+    replica on these SNP graphs) is weaker and leaves a few errors."""
+    fr = synth.region_reads(31, n_snps=150, region=50_000, n_reads=50, len_mean=8000,
+                            len_sd=2000, flip_p=0.0, miss_p=0.0, qual=(10, 30))
+    res = oracle.phase_snp(fr, range(8), 300, seed=5, refine_max=15, dt=dt, variant=variant)
+    se, he = metrics.switch_hamming(res["hap1"], res["snp_block"], fr.truth)
+    if variant == "discrete":
+        assert se == 0.0 and he == 0.0
+    else:
+        assert se < 0.2 and he < 0.2
+    fr2 = synth.region_reads(32, n_snps=150, region=50_000, n_reads=40, len_mean=8000,
+                             len_sd=2000, flip_p=0.08, miss_p=0.0, qual=(7, 30))
+    res2 = oracle.phase_snp(fr2, range(4), 150, seed=6, refine_max=15, dt=dt, variant=variant)
+    g = res2["graph"]
+    differs = 0
+    for b, nodes in enumerate(res2["blocks"]):
+        sub = g.subgraph(nodes)
+        best, _, _, _ = oracle.bsb_solve(sub, range(4), 150, 6, b, 0, dt=dt, variant=variant)
+        plain, _, _, _ = oracle.bsb_solve(sub, range(4), 150, 6, b, 0, dt=dt)
+        assert res2["first_cuts"][b] == best
+        differs += best != plain
+        p = np.where(res2["C"][nodes] % 2 == 0, 1, -1).astype(np.int8)
+        assert oracle.cut(sub, p) >= res2["first_cuts"][b] - 1e-9
+    assert differs > 0
