@@ -72,7 +72,7 @@ enum { QH_SCHED_LINEAR = 0, QH_SCHED_AUTO = 1 };
  * BALLISTIC: y += dt(-(a0 - a(t)) x + c0 J x), x += dt a0 y, |x| > 1 => x = sgn x, y = 0
  * DISCRETE:  as BALLISTIC with J sgn(x) (sgn(0) = +1) in place of J x
  * ADIABATIC: y += dt(-(x^2 + a0 - a(t)) x + c0 J x), x += dt a0 y, no walls
- * DISCRETE and ADIABATIC run on the FP32 and BF16 tile paths (not FP8, not CSR). */
+ * All three run on every precision, storage and step kernel. */
 enum { QH_SB_BALLISTIC = 0, QH_SB_DISCRETE = 1, QH_SB_ADIABATIC = 2 };
 
 /* ---------------------------------------------------------------- context */
@@ -204,10 +204,9 @@ typedef struct {
                            11 for BF16 when R allows, else 10.  Invalid choices ->
                            QH_EINVAL */
   int32_t sb_variant;   /* QH_SB_BALLISTIC (0, the paper's solver), QH_SB_DISCRETE,
-                           QH_SB_ADIABATIC.  The latter two run on every storage
-                           and step kernel of the FP32, BF16 and BF16X2 precisions
-                           except the persistent per-step kernels 4 and 5
-                           (QH_EINVAL); FP8 -> QH_EUNSUPPORTED */
+                           QH_SB_ADIABATIC; every precision, storage and step
+                           kernel.  Discrete SB multiplies J by sgn(x), which FP8
+                           and BF16 hold exactly.  Other values -> QH_EINVAL */
   double deform_h;      /* SNP mode: the adaptive deformation of the refinement
                            (0 = off, the plain refinement).  When a solve of a block
                            ends with a cut <= 0 or with all vertices in one subset,
@@ -315,8 +314,7 @@ qh_status qh_debug_steps(qh_ctx* ctx, const qh_graph* g, int32_t precision, int3
                          double a0, const double* c0_per_block);
 
 /* qh_debug_steps with an explicit step kernel (BF16 / BF16X2 tile storage: 0..9;
- * CSR storage, FP32 or BF16: 10 or 11; CSR storage, BF16: 12) and SB variant (QH_SB_*;
- * not FP8):
+ * CSR storage, FP32 or BF16: 10 or 11; CSR storage, BF16: 12) and SB variant (QH_SB_*):
  * step_kernel = -1 is the default; otherwise an index into the solver's kernel
  * variants (qh_bsb_opts.step_kernel).  The multi-step variants run all `nsteps`
  * steps in ONE launch, the momentum y held on chip between steps.  QH_EINVAL when

@@ -167,8 +167,6 @@ std::string tune_key(const Graph& g, int R, int use_lo, int sb) {
   return kb;
 }
 
-// The two persistent per-step kernels implement the ballistic update only.
-bool sb_kernel_ok(int v, int sb) { return sb == QH_SB_BALLISTIC || (v != 4 && v != 5); }
 
 bool tuned_variant(Ctx* ctx, const Graph& g, int R, int sb, TcPlan* plan) {
   const std::string kb = tune_key(g, R, 0, sb);
@@ -200,7 +198,6 @@ qh_status autotune(Ctx* ctx, const Graph& g, StepArgs a, const SolveBufs& B, int
   for (int v = 0; v < tc_n_variants(); ++v) {
     if (!tc_variant_ok(v, g, R, ctx->n_sm, a.use_lo != 0)) continue;
     if (run_variant(v) && !allow_run) continue;
-    if (!sb_kernel_ok(v, a.sb)) continue;
     TcPlan p = *plan;
     p.variant = v;
     RunBufs rb;
@@ -444,10 +441,6 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     return set_err(ctx, QH_EINVAL, "bad precision");
   if (o->sb_variant < QH_SB_BALLISTIC || o->sb_variant > QH_SB_ADIABATIC)
     return set_err(ctx, QH_EINVAL, "bad sb_variant");
-  if (o->sb_variant != QH_SB_BALLISTIC && o->precision == QH_PREC_FP8)
-    return set_err(ctx, QH_EUNSUPPORTED, "discrete / adiabatic SB need FP32, BF16 or BF16X2 precision");
-  if (o->sb_variant != QH_SB_BALLISTIC && o->step_kernel >= 0 && !sb_kernel_ok(o->step_kernel, o->sb_variant))
-    return set_err(ctx, QH_EINVAL, "this step_kernel implements the ballistic update only");
   if (o->precision == QH_PREC_FP8 && G.csr_mode)
     return set_err(ctx, QH_EUNSUPPORTED, "FP8 needs tile storage (the graph is stored as CSR)");
   if (o->precision == QH_PREC_FP8 && R % 64 != 0)
@@ -797,8 +790,8 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     launch_init_state(s, W, R, o->replica_base, o->seed, it, B.x, B.y,
                       is_tc_precision(o->precision) ? B.xh0 : nullptr, B.active, o->sb_variant);
     if (fp8)
-      launch_x_to_e4m3(s, B.x, (int64_t)NS, reinterpret_cast<uint8_t*>(B.xh0),
-                       reinterpret_cast<uint8_t*>(B.xh0) + NS);
+      launch_x_operand_e4m3(s, W, o->sb_variant, B.x, (int64_t)NS,
+                            reinterpret_cast<uint8_t*>(B.xh0), reinterpret_cast<uint8_t*>(B.xh0) + NS);
     QH_STAGE_CHECK("solve: state init");
     QH_CUDA_TRY(cudaEventRecord(ctx->ev[2], s));
     if (multistep) {
@@ -1210,8 +1203,6 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
   qh_status st = debug_common(ctx, g, precision, R, a, c0_per_block, steps, &c0h);
   if (st) return st;
   a.sb = sb_variant;
-  if (sb_variant != QH_SB_BALLISTIC && precision == QH_PREC_FP8)
-    return set_err(ctx, QH_EUNSUPPORTED, "discrete / adiabatic SB need FP32, BF16 or BF16X2 precision");
   a.deform = nullptr;
   if (field_per_block != nullptr && g.n_blocks > 0) {
     std::vector<float> hf(g.n_blocks);
@@ -1230,8 +1221,7 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
       return set_err(ctx, QH_EINVAL, "step_kernel variant not valid for this graph, precision and R");
   } else if (step_kernel >= 0) {
     if (!is_tc_precision(precision) || g.csr_mode || step_kernel >= tc_n_variants() ||
-        !tc_variant_ok(step_kernel, g, R, ctx->n_sm, a.use_lo != 0) ||
-        !sb_kernel_ok(step_kernel, sb_variant))
+        !tc_variant_ok(step_kernel, g, R, ctx->n_sm, a.use_lo != 0))
       return set_err(ctx, QH_EINVAL, "step_kernel variant not valid for this graph, precision and R");
     if (run_variant(step_kernel) && !run_c0_ok(c0h.data(), g.n_blocks, (float)dt))
       return set_err(ctx, QH_EINVAL, "multi-step kernel needs dt * c0 to be a normal float in every block");
@@ -1283,7 +1273,7 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
       a.inv_scale = 1.f / sc8;
       uint8_t* b0 = reinterpret_cast<uint8_t*>(xh0);
       uint8_t* b1 = reinterpret_cast<uint8_t*>(xh1);
-      launch_x_to_e4m3(s, x, (int64_t)NS, b0, b0 + NS);
+      launch_x_operand_e4m3(s, g, sb_variant, x, (int64_t)NS, b0, b0 + NS);
       for (int32_t k = 0; k < nsteps; ++k) {
         a.t = t0 + k;
         uint8_t* cur = (k % 2 == 0) ? b0 : b1;

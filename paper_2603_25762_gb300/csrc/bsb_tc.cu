@@ -433,17 +433,12 @@ __global__ void __launch_bounds__(128, MINB)
 #pragma unroll
       for (int j = 0; j < CH; ++j) {
         float x = xs[j], y = ys[j];
-        y = y + a.dt * (coef_x * x + c0 * (__uint_as_float(v[j]) * inv_s) + fe);
-        x = x + a.dta0 * y;
-        if (fabsf(x) > 1.f) {
-          x = x > 0.f ? 1.f : -1.f;
-          y = 0.f;
-        }
+        sb_update(a.sb, __uint_as_float(v[j]) * inv_s, x, y, a.dt, coef_x, a.dta0, c0, fe);
         const size_t idx = b0 + (size_t)j * a.n_pad;
         a.x[idx] = x;
         a.y[idx] = y;
-        uint8_t h8, l8;
-        split_e4m3(x, h8, l8);
+        uint8_t h8, l8;  // the variant's operand: for discrete SB sgn(x), lo = 0
+        split_e4m3(sb_operand(a.sb, x), h8, l8);
         a.x8h_out[idx] = h8;
         a.x8l_out[idx] = l8;
       }
@@ -476,9 +471,16 @@ __global__ void k_tiles_to_e4m3(const float* __restrict__ tf, int64_t n, float s
   if (l != 0 && (l & 0x7f) != 0) atomicOr(has_lo, 1);
 }
 
-__global__ void k_x_to_e4m3(const float* __restrict__ x, int64_t n, uint8_t* h, uint8_t* l) {
+// x -> e4m3 hi / lo.  pad_node != nullptr: the operand of SB variant sb at real
+// vertices (state [R][n_pad]), 0 at padding.
+__global__ void k_x_to_e4m3(const float* __restrict__ x, int64_t n, uint8_t* h, uint8_t* l,
+                            int32_t sb, int32_t n_pad, const int32_t* __restrict__ pad_node) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) split_e4m3(x[i], h[i], l[i]);
+  if (i >= n) return;
+  const float v = pad_node == nullptr      ? x[i]
+                  : pad_node[i % n_pad] >= 0 ? sb_operand(sb, x[i])
+                                             : 0.f;
+  split_e4m3(v, h[i], l[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -651,15 +653,10 @@ __global__ void __launch_bounds__(192, 1)
           for (int j = 0; j < 32; ++j) {
             const int r = c * 32 + j;
             float x = sx[r * TILE + row], y = sy[r * TILE + row];
-            y = y + a.dt * (coef_x * x + c0 * __uint_as_float(v[j]) + fe);
-            x = x + a.dta0 * y;
-            if (fabsf(x) > 1.f) {
-              x = x > 0.f ? 1.f : -1.f;
-              y = 0.f;
-            }
+            sb_update(a.sb, __uint_as_float(v[j]), x, y, a.dt, coef_x, a.dta0, c0, fe);
             sx[r * TILE + row] = x;
             sy[r * TILE + row] = y;
-            xh[(size_t)r * a.n_pad] = __float2bfloat16_rn(x);
+            xh[(size_t)r * a.n_pad] = __float2bfloat16_rn(sb_operand(a.sb, x));
           }
         }
       }
@@ -863,16 +860,11 @@ __global__ void __launch_bounds__(384, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             float x = xs[j], y = ys[j];
-            y = y + a.dt * (coef_x * x + c0 * __uint_as_float(v[j]) + fe);
-            x = x + a.dta0 * y;
-            if (fabsf(x) > 1.f) {
-              x = x > 0.f ? 1.f : -1.f;
-              y = 0.f;
-            }
+            sb_update(a.sb, __uint_as_float(v[j]), x, y, a.dt, coef_x, a.dta0, c0, fe);
             const size_t idx = b0 + (size_t)j * a.n_pad;
             a.x[idx] = x;
             a.y[idx] = y;
-            a.xh_out[idx] = __float2bfloat16_rn(x);
+            a.xh_out[idx] = __float2bfloat16_rn(sb_operand(a.sb, x));
           }
         }
         if (c == 0) {
@@ -1084,7 +1076,15 @@ void launch_tiles_to_e4m3(cudaStream_t s, const float* tf, int64_t n, float scal
 
 void launch_x_to_e4m3(cudaStream_t s, const float* x, int64_t n, uint8_t* h, uint8_t* l) {
   if (n > 0)
-    k_x_to_e4m3<<<::qh::counted((unsigned)((n + 255) / 256)), 256, 0, s>>>(x, n, h, l);
+    k_x_to_e4m3<<<::qh::counted((unsigned)((n + 255) / 256)), 256, 0, s>>>(x, n, h, l, 0, 1,
+                                                                          nullptr);
+}
+
+void launch_x_operand_e4m3(cudaStream_t s, const Graph& g, int32_t sb, const float* x, int64_t n,
+                           uint8_t* h, uint8_t* l) {
+  if (n > 0 && g.n_pad > 0)
+    k_x_to_e4m3<<<::qh::counted((unsigned)((n + 255) / 256)), 256, 0, s>>>(x, n, h, l, sb, g.n_pad,
+                                                                          g.pad_node);
 }
 
 bool tc_plan_ok(int R, const TcPlan& plan) {

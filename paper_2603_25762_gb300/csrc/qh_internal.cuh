@@ -343,6 +343,10 @@ qh_status launch_step_f8(Ctx* ctx, const Graph& g, const StepArgs& a, const Fp8O
 void launch_tiles_to_e4m3(cudaStream_t s, const float* tf, int64_t n, float scale, uint8_t* th,
                           uint8_t* tl, int32_t* has_lo);
 void launch_x_to_e4m3(cudaStream_t s, const float* x, int64_t n, uint8_t* h, uint8_t* l);
+// The FP8 product operand of a state [R][n_pad] for SB variant sb (sgn(x) for discrete
+// SB, x otherwise) at real vertices, 0 at padding, as e4m3 hi / lo.
+void launch_x_operand_e4m3(cudaStream_t s, const Graph& g, int32_t sb, const float* x, int64_t n,
+                           uint8_t* h, uint8_t* l);
 int tc_n_variants();
 const char* tc_variant_name(int v);
 bool tc_variant_ok(int v, const Graph& g, int R, int n_sm, bool use_lo);

@@ -53,6 +53,10 @@ class QhBsbOpts(C.Structure):
 
 # simulated-bifurcation variants (QH_SB_*)
 SB_VARIANTS = {"ballistic": 0, "discrete": 1, "adiabatic": 2}
+
+
+def _sb(variant):
+    return SB_VARIANTS[variant] if isinstance(variant, str) else int(variant)
 STEP_KERNELS = ["cta-bn128-s3", "cta-bn128-s2-x3", "cta-bn64-s2-x4", "cta-bn256-s2-x2",
                 "persistent-bn128", "persistent-bn64-tma-state",
                 "multistep-jres-group", "multistep-stream-tile", "multistep-jres-tile",
@@ -270,13 +274,14 @@ class Context:
         """step_kernel: None = the default (autotuned on BF16 tile storage), or a name
         from STEP_KERNELS: the tile variants for BF16 tile storage, "csr-lane4" /
         "csr-lane8" for CSR storage.
-        variant: "ballistic" (bSB), "discrete" (dSB) or "adiabatic" (aSB).
+        variant: "ballistic" (bSB), "discrete" (dSB) or "adiabatic" (aSB), or the
+        QH_SB_* value itself.
         deform_h, deform_tries: the SNP refinement's adaptive deformation (0 = off): up
         to deform_tries re-solves of a block whose cut is <= 0, with a field along the
         incumbent of strength deform_h 2^(k-1)."""
         sk = -1 if step_kernel is None else STEP_KERNELS.index(step_kernel)
         o = QhBsbOpts(replicas, steps, schedule, precision, dt, a0, c0, seed, replica_base,
-                      check_every, patience, refine_max, sk, SB_VARIANTS[variant], deform_h,
+                      check_every, patience, refine_max, sk, _sb(variant), deform_h,
                       deform_tries, 0)
         s = C.c_void_p()
         self._check(lib().qh_bsb_solve(self.h, g.h, C.byref(o), C.byref(s)))
@@ -308,7 +313,7 @@ class Context:
         self._check(lib().qh_debug_steps_v(self.h, g.h, precision, R, _ptr(x), _ptr(y), t0,
                                            nsteps, steps, dt, a0,
                                            _ptr(c0a) if c0a is not None else None, sk,
-                                           SB_VARIANTS[variant],
+                                           _sb(variant),
                                            _ptr(fa) if fa is not None else None))
 
     def debug_wait_timeout(self, which=0):

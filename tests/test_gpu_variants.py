@@ -1,11 +1,13 @@
 """Discrete (dSB) and adiabatic (aSB) simulated bifurcation on the GPU against the FP64
 oracle, through the C ABI: the state after a few steps and whole solves, on the FP32
-tile path, the BF16 per-step kernels, the multi-step kernel and the CSR steps (FP32 and
-BF16 gathers, and the band on the tensor cores plus the remainder).
+tile path, the BF16 per-step kernels (persistent ones included), the multi-step kernel,
+the FP8 step and the CSR steps (FP32 and BF16 gathers, and the band on the tensor cores
+plus the remainder).
 
-Bars as for ballistic SB: state within 1e-5 (FP32) / 1e-2 (BF16) relative Frobenius
-of the oracle's after a few steps; best cut >= 0.999 x the oracle's on the same seed,
-steps and replica indices.  aSB runs at dt = 0.5 (at dt = 1 it diverges).
+Bars as for ballistic SB: state within 1e-5 (FP32) / 1e-2 (BF16, FP8) relative
+Frobenius of the oracle's after a few steps (FP8 aSB after one step, as for bSB);
+best cut >= 0.999 x the oracle's on the same seed, steps and replica indices.  aSB runs
+at dt = 0.5 on read graphs (at dt = 1 it diverges).
 """
 import numpy as np
 import pytest
@@ -40,7 +42,9 @@ def _rel_frob(a, b):
 @pytest.mark.parametrize("variant", ["discrete", "adiabatic"])
 @pytest.mark.parametrize("precision,kernel,storage,tol", [
     (0, None, 1, 1e-5), (1, None, 1, 1e-2), (1, "cta-bn128-s2-x3", 1, 1e-2),
+    (1, "persistent-bn128", 1, 1e-2), (1, "persistent-bn64-tma-state", 1, 1e-2),
     (1, "multistep-stream-tile", 1, 1e-2), (1, "multistep-jres-group", 1, 1e-2),
+    (3, None, 1, 1e-2),
     (0, "csr-lane4", 2, 1e-5), (0, "csr-lane8", 2, 1e-5), (1, "csr-lane4", 2, 1e-2),
     (1, "csr-lane8", 2, 1e-2), (1, "csr-band8", 2, 1e-2)])
 def test_variant_steps_match_oracle(q, ctx, oracle, variant, precision, kernel, storage, tol):
@@ -50,7 +54,8 @@ def test_variant_steps_match_oracle(q, ctx, oracle, variant, precision, kernel, 
     og = oracle.read_graph(fr, oracle.READ_SIGNED)
     blocks = oracle.blocks_of(og)
     n_pad, pidx, c0 = g.layout()
-    R, t0, nsteps, steps, dt = 256, 40, 3, 200, DT[variant]
+    R, t0, steps, dt = 256, 40, 200, DT[variant]
+    nsteps = 1 if precision == 3 and variant == "adiabatic" else 3
     rng = np.random.default_rng(21)
     x = np.zeros((R, n_pad), np.float32)
     y = np.zeros((R, n_pad), np.float32)
@@ -82,8 +87,8 @@ def test_variant_steps_match_oracle(q, ctx, oracle, variant, precision, kernel, 
 
 @pytest.mark.parametrize("variant", ["discrete", "adiabatic"])
 @pytest.mark.parametrize("precision,kernel,storage", [
-    (0, None, 1), (1, None, 1), (1, "multistep-stream-group", 1), (0, None, 2), (1, None, 2),
-    (1, "csr-lane8", 2)])
+    (0, None, 1), (1, None, 1), (1, "multistep-stream-group", 1), (1, "persistent-bn128", 1),
+    (3, None, 1), (0, None, 2), (1, None, 2), (1, "csr-lane8", 2)])
 def test_variant_solve_vs_oracle(q, ctx, oracle, variant, precision, kernel, storage):
     fr = synth.batched_blocks(1004, n_blocks=6, n_min=40, n_max=300)
     g = ctx.build_graph(fr, mode=q.MODE_READ, storage=storage)
@@ -101,17 +106,47 @@ def test_variant_solve_vs_oracle(q, ctx, oracle, variant, precision, kernel, sto
         assert info["best_cut"] >= 0.999 * best, (b, info["best_cut"], best)
 
 
-def test_variant_unsupported_combinations(q, ctx):
+def test_variant_value_validated(q, ctx):
+    import torch
     fr = synth.tiny_reads(1001)
     g = ctx.build_graph(fr)
-    with pytest.raises(RuntimeError):  # FP8 implements the ballistic update only
-        ctx.solve(g, replicas=64, steps=10, precision=q.PREC_FP8, variant="discrete")
-    with pytest.raises(RuntimeError):  # so do the two persistent per-step kernels
-        ctx.solve(g, replicas=128, steps=10, precision=q.PREC_BF16, variant="adiabatic",
-                  step_kernel="persistent-bn128")
+    for bad in (-1, 3):
+        with pytest.raises(RuntimeError):
+            ctx.solve(g, replicas=64, steps=10, precision=q.PREC_BF16, variant=bad)
+    n_pad, _, c0 = g.layout()
+    x = torch.zeros((64, n_pad), device="cuda")
+    y = torch.zeros((64, n_pad), device="cuda")
+    with pytest.raises(RuntimeError):
+        ctx.debug_steps(g, q.PREC_FP32, 64, x, y, 0, 1, 10, c0=c0, variant=3)
     gc = ctx.build_graph(fr, storage=q.STORAGE_CSR)
-    with pytest.raises(RuntimeError):  # FP8 needs tile storage in any case
+    with pytest.raises(RuntimeError):  # FP8 needs tile storage, whatever the variant
         ctx.solve(gc, replicas=64, steps=10, precision=q.PREC_FP8, variant="discrete")
+
+
+def test_discrete_fp8_product_is_exact_on_integer_weights(q, ctx, oracle):
+    """dSB on FP8: the operand sgn(x) is +-1 in e4m3 (lo part zero) and integer weights
+    below 256 split exactly into e4m3 hi + lo, so one step's y equals FP64
+    y + dt c0 J sgn(x) up to FP32 rounding of the update (no product error)."""
+    import torch
+    fr = synth.batched_blocks(1004, n_blocks=3, n_min=80, n_max=300)
+    g = ctx.build_graph(fr, mode=q.MODE_READ)
+    og = oracle.read_graph(fr, oracle.READ_SIGNED)
+    n_pad, pidx, c0 = g.layout()
+    R, t0, steps = 128, 100, 200
+    rng = np.random.default_rng(5)
+    x = np.zeros((R, n_pad), np.float32)
+    y = np.zeros((R, n_pad), np.float32)
+    for nodes in oracle.blocks_of(og):
+        x[:, pidx[nodes]] = rng.uniform(-0.5, 0.5, (R, len(nodes)))
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    ctx.debug_steps(g, q.PREC_FP8, R, xd, yd, t0, 1, steps, c0=c0, variant="discrete")
+    yg = yd.cpu().numpy().astype(np.float64)
+    for b, nodes in enumerate(oracle.blocks_of(og)):
+        _, y1 = oracle.bsb_run(og.subgraph(nodes), x[:, pidx[nodes]].astype(np.float64),
+                               y[:, pidx[nodes]].astype(np.float64), t0, t0 + 1, steps,
+                               c0=float(c0[b]), variant="discrete")
+        free = np.abs(x[:, pidx[nodes]] + y1) < 0.999  # clear of the wall on both sides
+        assert _rel_frob(yg[:, pidx[nodes]][free], y1[free]) <= 1e-6
 
 
 @pytest.mark.parametrize("variant", ["discrete", "adiabatic"])
