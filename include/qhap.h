@@ -333,6 +333,15 @@ qh_status qh_debug_steps_v(qh_ctx* ctx, const qh_graph* g, int32_t precision, in
  * usable for the next call.  QH_EINVAL for another `which`. */
 qh_status qh_debug_wait_timeout(qh_ctx* ctx, int32_t which);
 
+/* Test hook of the error paths (not part of the paper's method): allocation-failure
+ * injection on the host.  after >= 0: the context's next `after` device allocations
+ * (graph and solution memory, grown scratch buffers) succeed and every later one
+ * fails as if the device were out of memory, so the call that meets it returns
+ * QH_ENOMEM (graphs and solutions it had begun are freed); after = -1 turns the
+ * injection off.  Allocations that an earlier call left in place are reused and not
+ * counted.  QH_EINVAL for after < -1.  No device work. */
+qh_status qh_debug_fail_alloc(qh_ctx* ctx, int64_t after);
+
 /* Padded layout: n_pad and padded_index int32[n_nodes] (-1 for vertices in no
  * block): vertex v of block b sits at padded column pad_off[b] + local[v]. */
 qh_status qh_debug_layout(qh_ctx* ctx, const qh_graph* g, int32_t* n_pad, int32_t* padded_index,

@@ -21,7 +21,15 @@ qh_status cuda_fail(Ctx* ctx, cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? QH_ENOMEM : QH_ECUDA;
 }
 
+bool alloc_permitted(const PoolRef& m) {
+  if (!m.fail_after || *m.fail_after < 0) return true;
+  if (*m.fail_after == 0) return false;
+  --*m.fail_after;
+  return true;
+}
+
 void* pool_alloc(const PoolRef& m, size_t bytes, std::vector<void*>* owner) {
+  if (!alloc_permitted(m)) return nullptr;
   void* p = nullptr;
   cudaError_t e = m.pool ? cudaMallocFromPoolAsync(&p, bytes, m.pool, m.stream)
                          : cudaMalloc(&p, bytes);
@@ -66,6 +74,7 @@ void* Ctx::scratch(size_t bytes, int slot) {
     }
     void* p = nullptr;
     size_t want = bytes + bytes / 8;
+    if (!alloc_permitted(mem)) return nullptr;
     if (cudaMalloc(&p, want) != cudaSuccess) {
       (void)cudaGetLastError();
       return nullptr;
@@ -307,6 +316,7 @@ qh_status qh_create(qh_ctx** out, int device, void* stream) {
     }
     ctx->mem.stream = ctx->stream;
     ctx->mem.alive = std::make_shared<bool>(true);
+    ctx->mem.fail_after = std::make_shared<int64_t>(-1);
   }
   if (cudaMalloc(&ctx->d_err, sizeof(int32_t)) != cudaSuccess ||
       cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), ctx->stream) != cudaSuccess) {
@@ -349,6 +359,7 @@ void qh_graph_free(qh_graph* g) {
 }
 
 qh_status qh_build_graph(qh_ctx* h, const qh_fragments* f, const qh_graph_opts* o, qh_graph** out) {
+  NvtxRange nvtx_range("qh_build_graph");
   if (!h) return QH_EINVAL;
   Ctx* ctx = &h->c;
   ctx->err.clear();
@@ -426,6 +437,7 @@ qh_status qh_graph_blocks(qh_ctx* h, const qh_graph* gh, int32_t* block_of, int3
 }
 
 qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_solution** out) {
+  NvtxRange nvtx_range("qh_bsb_solve");
   if (!h) return QH_EINVAL;
   Ctx* ctx = &h->c;
   ctx->err.clear();
@@ -777,6 +789,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   int64_t launches = 0;
   std::vector<int32_t> h_active(nb, 1), h_steps_run(nb);
   for (int32_t it = 0; it < refine_max; ++it) {
+    NvtxRange nvtx_iter("qh_bsb_solve: solve of every active block");
     for (int32_t b = 0; b < nb; ++b)
       if (h_active[b]) sol.iters[b] += 1;
     // steps_run defaults to the block's schedule length; early stop lowers it
@@ -999,6 +1012,7 @@ qh_status qh_phase(qh_ctx* h, const qh_graph* gh, const qh_solution* sh, int8_t*
                    int32_t* block_id, int32_t on_device) {
   if (!h) return QH_EINVAL;
   Ctx* ctx = &h->c;
+  NvtxRange nvtx_range("qh_phase");
   ctx->err.clear();
   clear_foreign_error(ctx);
   if (!gh || !sh || !hap1 || !hap2 || !block_id) return set_err(ctx, QH_EINVAL, "NULL argument");
@@ -1040,6 +1054,12 @@ qh_status qh_debug_wait_timeout(qh_ctx* h, int32_t which) {
   qh_status st = launch_wait_probe(ctx, which);
   if (st != QH_OK) return st;
   return check_err_word(ctx);
+}
+
+qh_status qh_debug_fail_alloc(qh_ctx* h, int64_t after) {
+  if (!h || after < -1 || !h->c.mem.fail_after) return QH_EINVAL;
+  *h->c.mem.fail_after = after;
+  return QH_OK;
 }
 
 qh_status qh_debug_layout(qh_ctx* h, const qh_graph* gh, int32_t* n_pad, int32_t* padded_index,

@@ -813,6 +813,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
   // ---- SNP -> fragment coverage lists (used by SNP rows and by voting)
   {
     int32_t* cnt = (int32_t*)ctx->scratch(sizeof(int32_t) * (n + 1), 0);
+    if (!cnt) return set_err(ctx, QH_ENOMEM, "allocation failed (coverage)");
     QH_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), s));
     if (nnz_f > 0) k_cov_count<<<::qh::counted(nblk(nnz_f)), 256, 0, s>>>(nnz_f, g->snp, cnt);
     g->cov_ptr = (int64_t*)dalloc(*g, sizeof(int64_t) * (n + 1));
@@ -842,6 +843,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     if (!first || !last || !keys || !order || !sfirst || !slast || !pmax || !cnt)
       return set_err(ctx, QH_ENOMEM, "allocation failed (read graph scratch)");
     g->row_ptr = (int64_t*)dalloc(*g, sizeof(int64_t) * (m + 1));
+    if (!g->row_ptr) return set_err(ctx, QH_ENOMEM, "allocation failed (edges)");
     if (m > 0) {
       k_first_last<<<::qh::counted(nblk(m)), 256, 0, s>>>(m, g->frag_ptr, g->snp, first, last, keys);
       sort_u64(s, keys, m, cap);
@@ -856,7 +858,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     QH_CUDA_TRY(cudaStreamSynchronize(s));
     g->col = (int32_t*)dalloc(*g, sizeof(int32_t) * std::max<int64_t>(g->nnz, 1));
     g->w = (double*)dalloc(*g, sizeof(double) * std::max<int64_t>(g->nnz, 1));
-    if (!g->row_ptr || !g->col || !g->w) return set_err(ctx, QH_ENOMEM, "allocation failed (edges)");
+    if (!g->col || !g->w) return set_err(ctx, QH_ENOMEM, "allocation failed (edges)");
     if (m > 0 && g->nnz > 0)
       k_read_edges<1><<<::qh::counted(nblk((int64_t)m * 32)), 256, 0, s>>>(
           m, g->frag_ptr, g->snp, g->allele, first, last, order, sfirst, slast, pmax,
@@ -918,6 +920,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
   // ---- weight range: integer weights up to 256 are exact in one BF16 operand
   {
     unsigned long long* amax = (unsigned long long*)ctx->scratch(16, 9);
+    if (!amax) return set_err(ctx, QH_ENOMEM, "allocation failed (weight range)");
     int32_t* nonint = (int32_t*)(amax + 1);
     QH_CUDA_TRY(cudaMemsetAsync(amax, 0, 16, s));
     if (g->nnz > 0)

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -54,7 +55,12 @@ struct PoolRef {
   cudaMemPool_t pool = nullptr;
   cudaStream_t stream = nullptr;
   std::shared_ptr<bool> alive;
+  // Allocation-failure injection (test hook): device allocations left before every
+  // further one fails; -1 = off.  Shared by the context's scratch and its graphs.
+  std::shared_ptr<int64_t> fail_after;
 };
+// false when the injected failure point is reached (counts the allocation otherwise)
+bool alloc_permitted(const PoolRef& m);
 void* pool_alloc(const PoolRef& m, size_t bytes, std::vector<void*>* owner);
 void pool_free_all(const PoolRef& m, std::vector<void*>* owned);
 
@@ -399,6 +405,15 @@ struct qh_graph {
 };
 struct qh_solution {
   qh::Solution s;
+};
+
+// NVTX range over a scope (host timeline for nsys / ncu range filters; a no-op
+// unless a profiler is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // Launch-error check at a stage boundary (kernel launches are not checked one by one).

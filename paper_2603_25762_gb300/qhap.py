@@ -98,6 +98,7 @@ _SIGS = {
     "qh_debug_matvec": (C.c_int, [P, P, I32, I32, P, P]),
     "qh_debug_steps": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P]),
     "qh_debug_wait_timeout": (C.c_int, [P, I32]),
+    "qh_debug_fail_alloc": (C.c_int, [P, I64]),
     "qh_debug_steps_v": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P, I32, I32, P]),
     "qh_debug_layout": (C.c_int, [P, P, P, P, P]),
     "qh_matvec_bf16_noalloc": (C.c_int, [P, P, I32, P, P]),
@@ -320,6 +321,11 @@ class Context:
         """Failure-detection hook: a bounded device wait that expires (raises QhError
         with status QH_ETIMEOUT after about a second)."""
         self._check(lib().qh_debug_wait_timeout(self.h, which))
+
+    def debug_fail_alloc(self, after):
+        """Error-path hook: the next `after` device allocations succeed, later ones fail
+        with QH_ENOMEM; after = -1 turns it off."""
+        self._check(lib().qh_debug_fail_alloc(self.h, after))
 
     def matvec_bf16_noalloc(self, g, R, x, z):
         """J x X in BF16 without any device allocation (fixed 8.5 MiB library array)."""
