@@ -482,6 +482,13 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   cudaStream_t s = ctx->stream;
   qh_solution* sh = new (std::nothrow) qh_solution;
   if (!sh) return QH_ENOMEM;
+  // every return that does not hand the solution out frees it (with any device memory)
+  struct SolutionGuard {
+    qh_solution*& p;
+    ~SolutionGuard() {
+      if (p) qh_solution_free(p);
+    }
+  } sol_guard{sh};
   Solution& sol = sh->s;
   sol.mode = G.mode;
   sol.n_blocks = nb;
@@ -499,6 +506,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   sol.C.assign(G.n_nodes, 0);
   if (nb == 0) {
     *out = sh;
+    sh = nullptr;
     return QH_OK;
   }
   // ---- per-block schedule and coupling scale
@@ -589,10 +597,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
       QH_CUDA_TRY(cudaMemcpyAsync(sum_w_work, G.sum_w, nb * 8, cudaMemcpyDeviceToDevice, s));
     }
   }
-  if (!okb) {
-    delete sh;
-    return set_err(ctx, QH_ENOMEM, "device allocation failed (solver state)");
-  }
+  if (!okb) return set_err(ctx, QH_ENOMEM, "device allocation failed (solver state)");
   // FP8: e4m3 hi / lo tiles of s*J from the (working) FP32 tiles
   const bool fp8 = o->precision == QH_PREC_FP8;
   Fp8Operands f8{};
@@ -614,14 +619,10 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     f8_jl = (uint8_t*)sc(std::max<int64_t>(f8_n, 1), S_F8L);
     f8_flag = (int32_t*)sc(16, S_F8FLAG);
     if (!f8_jh || !f8_jl || !f8_flag) {
-      delete sh;
       return set_err(ctx, QH_ENOMEM, "device allocation failed (FP8 tiles)");
     }
     qh_status st = convert_fp8_tiles();
-    if (st != QH_OK) {
-      delete sh;
-      return st;
-    }
+    if (st != QH_OK) return st;
     f8.jh = f8_jh;
     f8.jl = f8_jl;
   }
@@ -714,10 +715,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
         st = autotune(ctx, W, a, B, R, &tplan, run_c0_ok(h_c0.data(), nb, a.dt));
       }
     }
-    if (st != QH_OK) {
-      delete sh;
-      return st;
-    }
+    if (st != QH_OK) return st;
   }
   if (G.csr_mode) tplan.variant = csr_v;
   sol.kernel = G.csr_mode ? csr_variant_name(tplan.variant, is_tc_precision(o->precision))
@@ -728,15 +726,11 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   const bool multistep = is_tc_precision(o->precision) && !G.csr_mode && run_variant(tplan.variant);
   RunBufs rb;
   if (multistep && !run_c0_ok(h_c0.data(), nb, a.dt)) {
-    delete sh;
     return set_err(ctx, QH_EINVAL, "multi-step kernel needs dt * c0 to be a normal float in every block");
   }
   if (multistep) {
     qh_status st = run_prepare(ctx, W, R, tplan.variant, a.use_lo != 0, &rb);
-    if (st != QH_OK) {
-      delete sh;
-      return st;
-    }
+    if (st != QH_OK) return st;
   }
   if (!multistep && (ctx->loop_key != skey || !ctx->loop_exec)) {
     if (ctx->loop_exec) {
@@ -766,18 +760,13 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
     if (st != QH_OK) {
       if (ce == cudaSuccess) cudaGraphDestroy(graph);
-      delete sh;
       return st;
     }
-    if (ce != cudaSuccess) {
-      delete sh;
-      return cuda_fail(ctx, ce, "cudaStreamEndCapture");
-    }
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
     ce = cudaGraphInstantiate(&ctx->loop_exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) {
       ctx->loop_exec = nullptr;
-      delete sh;
       return cuda_fail(ctx, ce, "cudaGraphInstantiate");
     }
     ctx->loop_key = skey;
@@ -812,10 +801,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
       for (int32_t t0 = 0; t0 < max_steps; t0 += chunk) {
         const int32_t t1 = std::min(max_steps, t0 + chunk);
         qh_status st = launch_run(ctx, W, a, rb, B.xh0, B.xh1, t0, t1);
-        if (st != QH_OK) {
-          delete sh;
-          return st;
-        }
+        if (st != QH_OK) return st;
         if (early && t1 < max_steps) {
           launch_signs(s, W, R, B.x, B.signs);
           launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.running);
@@ -844,10 +830,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     QH_CUDA_TRY(cudaStreamSynchronize(s));
     {
       qh_status st = check_err_word(ctx);
-      if (st != QH_OK) {
-        delete sh;
-        return st;
-      }
+      if (st != QH_OK) return st;
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
@@ -875,10 +858,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
       qh_status st = retile(ctx, &W, W.w, W.tile_bf16, W.tile_f32, W.csr_mode ? W.pval : nullptr);
       if (st == QH_OK && band_on) st = reband(ctx, &W, W.w, W.band, W.rval);
       if (st == QH_OK && fp8) st = convert_fp8_tiles();
-      if (st != QH_OK) {
-        delete sh;
-        return st;
-      }
+      if (st != QH_OK) return st;
     }
     launch_block_sums(s, W, W.w, sum_w_work, (double*)ctx->scratch(nb * 8, S_SUMJ2),
                       (double*)ctx->scratch((size_t)std::max(G.n_nodes, 1) * 16, S_NODETMP));
@@ -903,7 +883,6 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     double* cut1 = (double*)ctx->scratch((size_t)nb * 8, S_CUT1);
     int32_t* pidx = (int32_t*)ctx->scratch((size_t)std::max(G.n_nodes, 1) * 4, S_DBG0);
     if (!st1 || !nv1 || !cut1 || !pidx) {
-      delete sh;
       return set_err(ctx, QH_ENOMEM, "allocation failed (final cut)");
     }
     std::vector<int32_t> hp(G.n_nodes);
@@ -930,7 +909,6 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     sol.d_spins = (int8_t*)pool_alloc(sol.mem, std::max(G.n_nodes, 1), &sol.allocs);
     sol.d_C = (int32_t*)pool_alloc(sol.mem, (size_t)std::max(G.n_nodes, 1) * 4, &sol.allocs);
     if (!sol.d_spins || !sol.d_C) {
-      qh_solution_free(sh);
       return set_err(ctx, QH_ENOMEM, "allocation failed (solution)");
     }
     if (G.n_nodes) {
@@ -951,6 +929,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   sol.n_step_launches = launches;
   sol.spin_updates = spin_updates;
   *out = sh;
+  sh = nullptr;
   return QH_OK;
 }
 
