@@ -664,3 +664,25 @@ def test_refinement_with_sb_variants(oracle, variant, dt):
         p = np.where(res2["C"][nodes] % 2 == 0, 1, -1).astype(np.int8)
         assert oracle.cut(sub, p) >= res2["first_cuts"][b] - 1e-9
     assert differs > 0
+
+
+@pytest.mark.parametrize("variant,dt", [("ballistic", 1.0), ("discrete", 1.0), ("adiabatic", 0.5)])
+def test_sb_spin_flip_symmetry_exact(oracle, variant, dt):
+    """Every SB variant is odd in (x, y): the flipped start gives the flipped run, bit for
+    bit (negation commutes with IEEE rounding; the wall, sgn and the cubic term are
+    odd; no initial value is exactly zero).  The deformation field is not odd, and
+    breaks it."""
+    W = synth.random_graph(5, 16, p=0.4, integer=False)
+    g = oracle.CSR.from_dense(W)
+    rng = np.random.default_rng(17)
+    x0 = rng.uniform(-0.1, 0.1, (4, 16))
+    y0 = rng.uniform(-0.1, 0.1, (4, 16))
+    c0 = oracle.default_c0(g)
+    x1, y1 = oracle.bsb_run(g, x0, y0, 0, 200, 200, dt=dt, c0=c0, variant=variant)
+    x2, y2 = oracle.bsb_run(g, -x0, -y0, 0, 200, 200, dt=dt, c0=c0, variant=variant)
+    assert np.array_equal(x2, -x1) and np.array_equal(y2, -y1)
+    assert np.abs(x1).max() > 0.5  # the run got somewhere
+    # mid-schedule, before the walls take every vertex (the field decays to 0 at the end)
+    xm, ym = oracle.bsb_run(g, x0, y0, 0, 60, 200, dt=dt, c0=c0, variant=variant, h=0.05)
+    xf, yf = oracle.bsb_run(g, -x0, -y0, 0, 60, 200, dt=dt, c0=c0, variant=variant, h=0.05)
+    assert not (np.array_equal(xf, -xm) and np.array_equal(yf, -ym))
