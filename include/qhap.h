@@ -91,8 +91,8 @@ const char* qh_last_error(const qh_ctx* ctx);
 
 /* ---------------------------------------------------------------- inputs */
 
-/* Fragments: the paper's "sparse vector of phased allele observations with
- * associated quality scores" per read (Methods, input preprocessing), as CSR.
+/* Fragments: per read, the heterozygous sites it covers, the allele seen at each
+ * and its base quality (Methods, input preprocessing), stored as CSR.
  *  n_frags, n_snps : m fragments over n heterozygous SNPs
  *  frag_ptr  int64[m+1]  fragment i owns entries frag_ptr[i] .. frag_ptr[i+1]-1;
  *                        frag_ptr[0] = 0, non-decreasing

@@ -1,4 +1,4 @@
-// Graph construction for the read-based and SNP-based methods, connected
+// Graph construction (read graph and SNP graph), connected
 // components (phase blocks) and the padded 128 x 128 J tile layout.
 //
 // Read graph (read-based Max-Cut graph construction, Eqs. delta / w_ab): for

@@ -1,7 +1,7 @@
 """Host logic for running the solver on several GPUs of one node (one process per GPU).
 
-Replicas of bSB are independent (SB algorithm solution: "multiple initial
-configurations are sampled in parallel"), so the path shards by replica range and
+Replicas of bSB are independent (SB algorithm solution: the solver runs many random
+starts side by side and keeps the best), so the path shards by replica range and
 needs no exchange while it runs:
   * rank r solves replicas base_r .. base_r + R - 1 with base_r = r * R (weak scaling);
   * afterwards one small all-gather picks, per block, the best cut over all ranks

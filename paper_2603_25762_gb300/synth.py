@@ -4,8 +4,9 @@ This module only draws inputs: truth haplotypes, read placements, allele observa
 Phred qualities and Pore-C contacts.  It holds none of the phasing arithmetic (no encoding
 rule beyond emitting +1/-1 relative to the initial H1, no graph weights, no solver).
 
-A fragment set is the paper's "sparse vector of phased allele observations with
-associated quality scores" (Methods, input preprocessing), stored as CSR:
+A fragment holds, for one read, the heterozygous sites it covers, the allele seen at
+each and its base quality (Methods, input preprocessing). A fragment set is stored as
+CSR:
 
   frag_ptr  int64[m+1]   fragment i owns entries frag_ptr[i] .. frag_ptr[i+1]-1
   snp       int32[nnz]   SNP index, strictly increasing inside a fragment
