@@ -214,10 +214,10 @@ typedef struct {
                            the force dt h_k (1 - t / steps) added to y along the
                            incumbent partition (h_k = deform_h 2^(k-1) on the k-th
                            re-solve); a positive cut is accepted as usual.  Every
-                           solve counts toward refine_max.  The paper introduces a
-                           deformation term h for components whose cut stays
-                           negative without a formula: this is the library's
-                           reading of it.  Must be finite and >= 0. */
+                           solve counts toward refine_max.  The paper names a
+                           deformation h for components whose cut keeps coming
+                           out negative but gives no formula: this is the
+                           library's reading of it.  Must be finite and >= 0. */
   int32_t deform_tries; /* re-solves with deformation after a failed solve (>= 0) */
   int32_t reserved;     /* must be 0 */
 } qh_bsb_opts;

@@ -270,7 +270,7 @@ void qo_free(void* p) { free(p); }
 
 /* ------------------------------------------------------------------------ */
 /* Connected components by breadth-first search over edges with w != 0
- * (read-based and SNP-based graph construction: components are independent
+ * (both graph constructions, read graph and SNP graph: components are independent
  * subproblems; single-node components are excluded).
  * label[v] = component index, components numbered in order of their smallest
  * vertex.  Returns the number of components (singletons included).          */

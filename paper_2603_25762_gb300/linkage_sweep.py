@@ -1,7 +1,7 @@
 """Linkage-depth trade-off of the SNP-based graph (the paper's SNP linkage depth
 analysis, its Fig. 4) on the synthetic ONT-like region.
 
-A linkage depth of k/10 links each SNP of a read only to its floor(k (N-1) / 10)
+Depth k/10 links each SNP of a read only to its floor(k (N-1) / 10)
 nearest downstream SNPs in that read (N SNPs in the read); k = 10 links every pair.
 For k = 1..10 this builds the SNP graph on the GPU, solves it with multi-replica bSB
 and the iterative refinement, phases it, and reports the edge count, the core

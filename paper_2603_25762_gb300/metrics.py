@@ -1,4 +1,4 @@
-"""Phasing quality metrics (Methods, evaluation metrics of haplotype phasing).
+"""Phasing quality metrics: switch error, Hamming error, N50 (their definitions in Methods).
 
 Evaluation only: these compare phased output with the generator's truth; they are
 not part of the GPU path.
