@@ -53,3 +53,52 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(qhap.QhFragments) == 4 + 4 + 5 * 8 + 8
     assert ctypes.sizeof(qhap.QhGraphOpts) == 5 * 4 + 4 + 8
     assert ctypes.sizeof(qhap.QhBsbOpts) == 4 * 4 + 3 * 8 + 8 + 4 * 4 + 8 + 8 + 8
+
+
+def _header_enums():
+    src = open(os.path.join(ROOT, "include", "qhap.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return {k: int(v) for k, v in re.findall(r"\b(QH_[A-Z0-9_]+)\s*=\s*(\d+)", src)}
+
+
+def test_binding_constants_match_header_enums():
+    from paper_2603_25762_gb300 import qhap
+    enums = _header_enums()
+    assert len(enums) >= 20
+    checked = 0
+    for name, value in enums.items():
+        short = name[len("QH_"):]
+        if name.startswith("QH_SB_"):
+            assert qhap.SB_VARIANTS[short[len("SB_"):].lower()] == value, name
+            checked += 1
+            continue
+        for cand in (name, short):
+            if hasattr(qhap, cand):
+                assert getattr(qhap, cand) == value, name
+                checked += 1
+                break
+        else:
+            pytest.fail(f"{name} has no binding constant")
+    assert checked == len(enums)
+
+
+def test_every_status_has_its_string(libpath):
+    from paper_2603_25762_gb300 import qhap
+    lib = ctypes.CDLL(libpath)
+    lib.qh_status_str.restype = ctypes.c_char_p
+    for value, name in qhap._STATUS.items():
+        assert lib.qh_status_str(value).decode() == name
+
+
+def test_step_kernel_names_match_the_library_sources():
+    """The binding's step-kernel list is the library's variant numbering: the tile
+    variants in the order of their name table, then the CSR variants 10, 11, 12."""
+    from paper_2603_25762_gb300 import qhap
+    tc = open(os.path.join(ROOT, "paper_2603_25762_gb300", "csrc", "bsb_tc.cu")).read()
+    table = re.search(r"static const char\* names\[\] = \{(.*?)\};", tc, flags=re.S).group(1)
+    tile = re.findall(r'"([a-z0-9-]+)"', table)
+    hdr = open(os.path.join(ROOT, "paper_2603_25762_gb300", "csrc", "qh_internal.cuh")).read()
+    csr = {int(v): k for k, v in re.findall(r"constexpr int (CSR_[A-Z0-9]+) = (\d+);", hdr)}
+    assert sorted(csr) == [len(tile), len(tile) + 1, len(tile) + 2]
+    names = {"CSR_LANE4": "csr-lane4", "CSR_LANE8": "csr-lane8", "CSR_BAND8": "csr-band8"}
+    assert qhap.STEP_KERNELS == tile + [names[csr[i]] for i in sorted(csr)]
