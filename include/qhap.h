@@ -308,7 +308,10 @@ qh_status qh_debug_matvec(qh_ctx* ctx, const qh_graph* g, int32_t precision, int
 
 /* Run `nsteps` solver steps t0 .. t0+nsteps-1 of a `steps`-step schedule from a
  * given state, in place: x, y float32[R][n_pad] (device), same layout.
- * c0_per_block float64[n_blocks] (host) or NULL for the default c0. */
+ * c0_per_block float64[n_blocks] (host) or NULL for the default c0.
+ * Resume: the state (x, y, t) is all a step range needs.  The product operand is
+ * rebuilt from x exactly as the kernels write it, so running t0 .. t0+n and then
+ * t0+n .. t0+2n gives the same bits as one call over t0 .. t0+2n. */
 qh_status qh_debug_steps(qh_ctx* ctx, const qh_graph* g, int32_t precision, int32_t R,
                          float* x, float* y, int32_t t0, int32_t nsteps, int32_t steps, double dt,
                          double a0, const double* c0_per_block);
