@@ -214,6 +214,26 @@ def test_snp_graph_truth_signs_without_errors(oracle):
     assert np.all(np.sign(W[nz]) == -np.outer(t, t)[nz])
 
 
+def test_snp_graph_gauge_under_allele_flips(oracle):
+    """Flipping the alleles at a set T of SNPs in every fragment gives exactly D W D
+    (d = -1 on T): each edge term carries the allele product M_iu M_iv, the quality
+    terms do not depend on the allele, and the summation order is unchanged.  With
+    Pore-C fragments and a linkage depth below 10."""
+    import dataclasses
+    fr = synth.region_reads(12, n_snps=150, region=50_000, n_reads=50, len_mean=8000,
+                            len_sd=2000, flip_p=0.05, miss_p=0.0, qual=(7, 30))
+    rng = np.random.default_rng(3)
+    fr = dataclasses.replace(fr, is_porec=(rng.random(fr.n_frags) < 0.3).astype(np.uint8))
+    T = rng.random(fr.n_snps) < 0.4
+    frt = dataclasses.replace(fr, allele=np.where(T[fr.snp], -fr.allele, fr.allele).astype(fr.allele.dtype))
+    d = np.where(T, -1.0, 1.0)
+    for k in (10, 6):
+        W = oracle.snp_graph(fr, linkage_k=k).dense()
+        Wt = oracle.snp_graph(frt, linkage_k=k).dense()
+        assert np.count_nonzero(W) > 0
+        assert np.array_equal(Wt, d[:, None] * W * d[None, :])
+
+
 # ----------------------------------------------------------------------------- components
 def test_components_match_scipy(oracle):
     from scipy.sparse import csr_matrix
