@@ -474,6 +474,77 @@ double qo_bsb_solve(int32_t n, const int64_t* rp, const int32_t* col, const doub
                      cuts, best_r, 0);
 }
 
+/* Multi-replica SB with early stop on energy stagnation.  The paper caps its runs by
+ * a "maximum convergence count"; the reading used here is a patience on the best
+ * energy over replicas:
+ *   every check_every steps, while the schedule still has steps left (t < steps),
+ *   each replica's spins s = sgn(x) are cut-evaluated and the best cut over the
+ *   replicas is compared with the best of all earlier checks of this solve;
+ *   a strictly larger value resets the stall count, any other adds one;
+ *   when the stall count reaches `patience` the solve stops after t steps.
+ * The replicas' state is then the state after t steps of the `steps`-step schedule
+ * (a(t) keeps its full-schedule definition), and the result is evaluated from it as in
+ * qo_sb_solve.  check_every = 0 or patience = 0: no early stop.  *steps_run receives
+ * the number of steps made.                                                          */
+double qo_sb_solve_es(int32_t n, const int64_t* rp, const int32_t* col, const double* w,
+                      int32_t R, const int32_t* replica_ids, int32_t steps, double dt, double a0,
+                      double c0, uint64_t seed, int64_t block, int32_t iter, int32_t check_every,
+                      int32_t patience, int8_t* best_s, double* cuts, int32_t* best_r,
+                      int32_t* steps_run, int32_t variant) {
+  int64_t nnz = rp[n];
+  double* J = (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+  for (int64_t e = 0; e < nnz; ++e) J[e] = -w[e];
+  if (c0 <= 0.0) c0 = qo_default_c0(n, rp, J);
+  double* x = (double*)malloc(sizeof(double) * (size_t)R * (size_t)(n > 0 ? n : 1));
+  double* y = (double*)malloc(sizeof(double) * (size_t)R * (size_t)(n > 0 ? n : 1));
+  int8_t* s = (int8_t*)malloc((size_t)(n > 0 ? n : 1));
+  qo_bsb_init(n, R, replica_ids, seed, block, iter, x, y);
+  int32_t t = 0;
+  if (check_every > 0 && patience > 0) {
+    double seen = -INFINITY;
+    int32_t stall = 0;
+    while (t < steps) {
+      int32_t t1 = t + check_every < steps ? t + check_every : steps;
+      qo_sb_run(n, rp, col, J, R, x, y, t, t1, steps, dt, a0, c0, variant);
+      t = t1;
+      if (t >= steps) break; /* no check once the schedule is complete */
+      double best_now = -INFINITY;
+      for (int32_t r = 0; r < R; ++r) {
+        for (int32_t i = 0; i < n; ++i) s[i] = (x[(size_t)r * n + i] >= 0.0) ? 1 : -1;
+        double c = qo_cut(n, rp, col, w, s);
+        if (c > best_now) best_now = c;
+      }
+      if (best_now > seen) {
+        seen = best_now;
+        stall = 0;
+      } else if (++stall >= patience) {
+        break;
+      }
+    }
+  } else {
+    qo_sb_run(n, rp, col, J, R, x, y, 0, steps, steps, dt, a0, c0, variant);
+    t = steps;
+  }
+  *steps_run = t;
+  double best = -INFINITY;
+  *best_r = -1;
+  for (int32_t r = 0; r < R; ++r) {
+    for (int32_t i = 0; i < n; ++i) s[i] = (x[(size_t)r * n + i] >= 0.0) ? 1 : -1;
+    double c = qo_cut(n, rp, col, w, s);
+    cuts[r] = c;
+    if (c > best) {
+      best = c;
+      *best_r = r;
+      memcpy(best_s, s, (size_t)n);
+    }
+  }
+  free(J);
+  free(x);
+  free(y);
+  free(s);
+  return best;
+}
+
 /* ------------------------------------------------------------------------ */
 /* SNP-based iterative refinement (SB algorithm solution, SNP-based method).
  * Repeat up to refine_max times: solve with bSB; stop if the cut is <= 0 or

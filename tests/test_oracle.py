@@ -312,6 +312,9 @@ def test_bsb_gauge_invariance_exact(oracle):
 
 
 def test_default_c0_definition(oracle):
+    """Definition check, not a pin: the paper prints no c0, and the oracle's c0 is the
+    normalisation of the bSB literature it cites.  This only guards the sums (both
+    triangles, N (N - 1) pairs) against an indexing slip."""
     W = synth.random_graph(9, 10, p=0.6, integer=False)
     g = oracle.CSR.from_dense(W)
     n = 10
@@ -706,3 +709,80 @@ def test_sb_spin_flip_symmetry_exact(oracle, variant, dt):
     xm, ym = oracle.bsb_run(g, x0, y0, 0, 60, 200, dt=dt, c0=c0, variant=variant, h=0.05)
     xf, yf = oracle.bsb_run(g, -x0, -y0, 0, 60, 200, dt=dt, c0=c0, variant=variant, h=0.05)
     assert not (np.array_equal(xf, -xm) and np.array_equal(yf, -ym))
+
+
+# ----------------------------------------------------------------------------- hand-worked steps
+def test_bsb_two_steps_hand_values(oracle):
+    """Two bSB steps worked by hand in exact fractions (tests/golden): pins the order of
+    the half-steps (y from x_t, then x from y_{t+1}), a(t) indexed at t, the row-wise
+    product z_i = sum_j J_ij x_j on an asymmetric J, and the wall."""
+    gold = json.load(open(os.path.join(GOLD, "bsb_two_steps_hand.json")))
+    for case in gold["cases"]:
+        J = np.array(case["J"], np.float64)
+        g = oracle.CSR.from_dense(-J)  # the oracle takes w = -J
+        x = np.array([case["x0"]])
+        y = np.array([case["y0"]])
+        for t, key in enumerate(["after_step_0", "after_step_1"]):
+            x, y = oracle.bsb_run(g, x, y, t, t + 1, case["steps"], dt=case["dt"],
+                                  a0=case["a0"], c0=case["c0"])
+            assert np.array_equal(x[0], np.array(case[key]["x"])), (case["name"], key)
+            assert np.array_equal(y[0], np.array(case[key]["y"])), (case["name"], key)
+
+
+# ----------------------------------------------------------------------------- early stop
+def test_early_stop_off_equals_plain_solve(oracle):
+    fr = synth.tiny_reads(1001)
+    g = oracle.read_graph(fr, oracle.READ_SIGNED)
+    sub = g.subgraph(oracle.blocks_of(g)[0])
+    ref = oracle.bsb_solve(sub, list(range(8)), 400, 5)
+    for ce, pat in [(0, 3), (50, 0), (50, 100)]:  # off, off, never reached
+        best, s, cuts, br, sr = oracle.bsb_solve_early_stop(sub, list(range(8)), 400, 5, ce, pat)
+        assert sr == 400
+        assert best == ref[0] and br == ref[3]
+        assert np.array_equal(s, ref[1]) and np.array_equal(cuts, ref[2])
+
+
+@pytest.mark.parametrize("check_every,patience", [(10, 1), (25, 3), (40, 4)])
+def test_early_stop_two_node_closed_form(oracle, check_every, patience):
+    """One edge of weight 3: every check can at best see the cut 3, and some replica
+    already splits the two vertices at the first check, so the best never improves
+    after it: the stall count reaches `patience` at check 1 + patience exactly."""
+    g = oracle.CSR.from_dense(np.array([[0.0, 3.0], [3.0, 0.0]]))
+    steps = 2000
+    best, s, cuts, br, sr = oracle.bsb_solve_early_stop(g, list(range(32)), steps, 9,
+                                                         check_every, patience)
+    assert sr == check_every * (1 + patience)
+    assert best == 3.0 and s[0] != s[1]
+
+
+def test_early_stop_result_is_the_truncated_run(oracle):
+    """A block that stops keeps the state it reached: the result equals a plain run of
+    the same schedule cut off after steps_run steps, evaluated with numpy."""
+    fr = synth.tiny_reads(1001)
+    g = oracle.read_graph(fr, oracle.READ_SIGNED)
+    sub = g.subgraph(oracle.blocks_of(g)[0])
+    reps, steps, seed = list(range(16)), 3000, 2
+    best, s, cuts, br, sr = oracle.bsb_solve_early_stop(sub, reps, steps, seed, 50, 3)
+    assert 0 < sr < steps and sr % 50 == 0
+    x, y = oracle.bsb_init(sub.n, reps, seed, 0)
+    x, _ = oracle.bsb_run(sub, x, y, 0, sr, steps)
+    W = sub.dense()
+    S = np.where(x >= 0, 1.0, -1.0)
+    ref = 0.25 * (W.sum() - np.einsum("ri,ij,rj->r", S, W, S))
+    assert np.array_equal(cuts, ref)
+    assert best == ref.max() and br == int(np.argmax(ref))
+    # the stopping check is the patience-th check in a row without a better best cut
+    xs, ys = oracle.bsb_init(sub.n, reps, seed, 0)
+    seen, stall, t = -np.inf, 0, 0
+    while True:
+        xs, ys = oracle.bsb_run(sub, xs, ys, t, t + 50, steps)
+        t += 50
+        Sx = np.where(xs >= 0, 1.0, -1.0)
+        c = (0.25 * (W.sum() - np.einsum("ri,ij,rj->r", Sx, W, Sx))).max()
+        if c > seen:
+            seen, stall = c, 0
+        else:
+            stall += 1
+            if stall == 3:
+                break
+    assert t == sr
