@@ -234,10 +234,34 @@ typedef struct {
 qh_status qh_bsb_solve(qh_ctx* ctx, const qh_graph* g, const qh_bsb_opts* opts,
                        qh_solution** out);
 
+/* qh_bsb_solve on the listed blocks only (block indices as numbered by the graph,
+ * each at most once): the unit of block sharding, where the blocks of one graph are
+ * split across processes or GPUs (connected components are independent subproblems,
+ * SB algorithm solution).  The listed blocks get exactly the result qh_bsb_solve gives
+ * them (same draws, keyed by block and replica); the others stay unsolved: best cut 0,
+ * best replica -1, steps_run 0, iterations 0, spins 0, zero rows in qh_solution_cuts,
+ * and qh_phase leaves their SNPs unphased.  n_blocks = 0 solves nothing.
+ * Errors: as qh_bsb_solve, and QH_EINVAL for an index out of range or listed twice. */
+qh_status qh_bsb_solve_blocks(qh_ctx* ctx, const qh_graph* g, const qh_bsb_opts* opts,
+                              const int32_t* blocks, int32_t n_blocks, qh_solution** out);
+
+/* Import one block's result into a solution, e.g. a block solved by another process
+ * of a sharded run (host values as qh_solution_block returns them there).
+ *  spins        : int8[block size], +1 / -1 in local vertex order (SNP mode: the
+ *                 parity partition, +1 where the flip count is even)
+ *  best_cut, best_replica (>= 0, a global replica index), steps_run (>= 0),
+ *  iterations (>= 1) : reported back by qh_solution_block
+ * The block's row of qh_solution_cuts becomes zeros.  qh_phase uses the imported
+ * spins (read voting, or the SNP parity).  Errors: QH_EINVAL. */
+qh_status qh_solution_set_block(qh_ctx* ctx, qh_solution* sol, int32_t block, const int8_t* spins,
+                                double best_cut, int32_t best_replica, int32_t steps_run,
+                                int32_t iterations);
+
 /* Per-block result.  Any output pointer may be NULL.
  *  spins        : int8[block size], best replica's spins in local vertex order
  *  best_cut     : cut of those spins on the block's original (ungauged) graph
- *  best_replica : replica index (replica_base + r) of the winner
+ *  best_replica : replica index (replica_base + r) of the winner; -1 for a block
+ *                 that a partial solve (qh_bsb_solve_blocks) left unsolved
  *  steps_run    : bSB steps actually run (early stop may shorten it)
  *  iterations   : refinement iterations (1 in READ mode)
  * Errors: QH_EINVAL (block out of range). */
@@ -345,6 +369,16 @@ qh_status qh_debug_wait_timeout(qh_ctx* ctx, int32_t which);
  * counted.  QH_EINVAL for after < -1.  No device work. */
 qh_status qh_debug_fail_alloc(qh_ctx* ctx, int64_t after);
 
+/* The solver's initial state (SB algorithm solution: random starts of the replicas),
+ * for checks of the random draws.  Writes x, y float32[R][n_pad] (device, padded
+ * layout, zero at padding columns) exactly as qh_bsb_solve draws them for replicas
+ * replica_base .. replica_base + R - 1 of refinement iteration `iter`: SplitMix64 keyed
+ * by (seed, block << 16 | iter), draw ((replica << 24) | local vertex) * 2 + {0: x, 1: y},
+ * value ((v >> 40) 2^-24) 0.2 - 0.1 computed in FP64 and rounded once to FP32.
+ * Errors: QH_EINVAL (R < 1, iter < 0, replica index >= 65536), QH_ENOMEM, QH_ECUDA. */
+qh_status qh_debug_init_state(qh_ctx* ctx, const qh_graph* g, int32_t R, int32_t replica_base,
+                              uint64_t seed, int32_t iter, float* x, float* y);
+
 /* Padded layout: n_pad and padded_index int32[n_nodes] (-1 for vertices in no
  * block): vertex v of block b sits at padded column pad_off[b] + local[v]. */
 qh_status qh_debug_layout(qh_ctx* ctx, const qh_graph* g, int32_t* n_pad, int32_t* padded_index,
@@ -354,11 +388,12 @@ qh_status qh_debug_layout(qh_ctx* ctx, const qh_graph* g, int32_t* n_pad, int32_
 
 /* J_hat x X_hat with the BF16 tensor cores, exactly as qh_debug_matvec(...,
  * QH_PREC_BF16, ...) computes it, but without allocating any device memory.
- * The paper has no counterpart; this exists for callers that cannot allocate:
- * code running while a CUDA graph is being captured (an allocation there is an
- * error or becomes part of the graph), host callbacks and real-time loops where
- * cudaMalloc would synchronise the device, and hosts whose memory budget is
- * handed out by their own allocator.
+ * The paper has no counterpart.  It serves callers that are not free to allocate
+ * GPU memory: a host whose allocator already owns the device memory (a framework
+ * or serving process that reserves the GPU's memory up front and hands it out
+ * itself, where an extra cudaMalloc fails or escapes its accounting), and a
+ * process held to a fixed device-memory budget.  Such callers pass their own
+ * input and output buffers; the library adds nothing to the device's allocations.
  * x  float32[R][n_pad] (device, caller-owned): state in the padded layout
  * z  float32[R][n_pad] (device, caller-owned): output; set to zero, then every
  *    vertex of every block receives sum_b J_hat_ab X_hat_b in FP32
@@ -367,10 +402,13 @@ qh_status qh_debug_layout(qh_ctx* ctx, const qh_graph* g, int32_t* n_pad, int32_
  * loads the library keeps until the process exits.  Limits: R a multiple of 64,
  * R * n_pad <= 4,194,304 and at most 65,536 blocks, otherwise QH_EINVAL with a
  * message.  The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.  All
- * calls share the one array and each call overwrites it in full, so two calls
- * whose work overlaps on the GPU (different streams or contexts) race on it.
- * Synchronises the context stream.  Errors: QH_EINVAL, QH_ECUDA, QH_ETIMEOUT. */
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not use the library across a
+ * cudaDeviceReset of the device.  All calls share the one array and each call
+ * overwrites it in full, so two calls whose work overlaps on the GPU (different
+ * streams or contexts) race on it.  The call synchronises the context stream and
+ * reads back the context's error word before it returns.
+ * Errors: QH_EINVAL, QH_ECUDA, QH_ETIMEOUT. */
 qh_status qh_matvec_bf16_noalloc(qh_ctx* ctx, const qh_graph* g, int32_t R, const float* x,
                                  float* z);
 

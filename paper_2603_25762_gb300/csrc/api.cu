@@ -436,7 +436,9 @@ qh_status qh_graph_blocks(qh_ctx* h, const qh_graph* gh, int32_t* block_of, int3
   return QH_OK;
 }
 
-qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_solution** out) {
+// The solve of every block (sel == nullptr) or of the listed blocks only.
+static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
+                            const int32_t* sel, int32_t n_sel, qh_solution** out) {
   NvtxRange nvtx_range("qh_bsb_solve");
   if (!h) return QH_EINVAL;
   Ctx* ctx = &h->c;
@@ -446,6 +448,16 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   *out = nullptr;
   const Graph& G = gh->g;
   const int32_t R = o->replicas, nb = G.n_blocks;
+  // blocks to solve: all, or the listed ones (each at most once)
+  std::vector<int32_t> sel_mask(std::max(nb, 1), sel ? 0 : 1);
+  if (sel) {
+    if (n_sel < 0) return set_err(ctx, QH_EINVAL, "negative block count");
+    for (int32_t k = 0; k < n_sel; ++k) {
+      if (sel[k] < 0 || sel[k] >= nb) return set_err(ctx, QH_EINVAL, "block index out of range");
+      if (sel_mask[sel[k]]) return set_err(ctx, QH_EINVAL, "block listed twice");
+      sel_mask[sel[k]] = 1;
+    }
+  }
   if (R < 1) return set_err(ctx, QH_EINVAL, "replicas must be >= 1");
   if (o->schedule != QH_SCHED_LINEAR && o->schedule != QH_SCHED_AUTO) return set_err(ctx, QH_EINVAL, "bad schedule");
   if (o->schedule == QH_SCHED_LINEAR && o->steps < 1) return set_err(ctx, QH_EINVAL, "steps must be >= 1");
@@ -504,7 +516,19 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   sol.cuts_first.assign((size_t)nb * R, 0.0);
   sol.spins.assign(G.n_nodes, 0);
   sol.C.assign(G.n_nodes, 0);
-  if (nb == 0) {
+  sol.solved.assign(std::max(nb, 1), 0);
+  int32_t n_solve = 0;
+  for (int32_t b = 0; b < nb; ++b) {
+    sol.solved[b] = (uint8_t)sel_mask[b];
+    n_solve += sel_mask[b];
+  }
+  if (n_solve == 0) {  // no block, or an empty selection: nothing to solve
+    for (int32_t v = 0; v < G.n_nodes; ++v) sol.C[v] = -1;
+    sol.mem = ctx->mem;
+    sol.d_spins = (int8_t*)pool_alloc(sol.mem, std::max(G.n_nodes, 1), &sol.allocs);
+    sol.d_C = (int32_t*)pool_alloc(sol.mem, (size_t)std::max(G.n_nodes, 1) * 4, &sol.allocs);
+    if (!sol.d_spins || !sol.d_C) return set_err(ctx, QH_ENOMEM, "allocation failed (solution)");
+    sol.device_stale = true;
     *out = sh;
     sh = nullptr;
     return QH_OK;
@@ -640,8 +664,12 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   else
     QH_CUDA_TRY(cudaMemsetAsync(B.xh1, 0, NS * 2, s));
   QH_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, 4, s));
-  std::vector<int32_t> ones(nb, 1);
-  QH_CUDA_TRY(cudaMemcpyAsync(B.active, ones.data(), nb * 4, cudaMemcpyHostToDevice, s));
+  // blocks left out of a partial solve keep zero cuts, picks and spins
+  QH_CUDA_TRY(cudaMemsetAsync(B.cuts, 0, (size_t)nb * R * 8, s));
+  QH_CUDA_TRY(cudaMemsetAsync(B.best_r, 0, nb * 4, s));
+  QH_CUDA_TRY(cudaMemsetAsync(B.best_cut, 0, nb * 8, s));
+  QH_CUDA_TRY(cudaMemsetAsync(B.spins, 0, G.n_nodes + 16, s));
+  QH_CUDA_TRY(cudaMemcpyAsync(B.active, sel_mask.data(), nb * 4, cudaMemcpyHostToDevice, s));
   QH_CUDA_TRY(cudaEventRecord(ctx->ev[0], s));
 
   const bool early = o->check_every > 0 && o->patience > 0;
@@ -729,7 +757,8 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     return set_err(ctx, QH_EINVAL, "multi-step kernel needs dt * c0 to be a normal float in every block");
   }
   if (multistep) {
-    qh_status st = run_prepare(ctx, W, R, tplan.variant, a.use_lo != 0, &rb);
+    qh_status st = run_prepare(ctx, W, R, tplan.variant, a.use_lo != 0, &rb,
+                               sel ? &sel_mask : nullptr);
     if (st != QH_OK) return st;
   }
   if (!multistep && (ctx->loop_key != skey || !ctx->loop_exec)) {
@@ -754,7 +783,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
         launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.running);
         launch_pick_best(s, nb, R, B.cuts, B.best_r, B.best_cut, B.running);
         launch_early_stop(s, nb, B.best_cut, B.seen, B.stall, B.running, B.steps_run, o->patience,
-                          t + 1);
+                          t + 1, B.steps_b);
       }
     }
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
@@ -776,7 +805,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   }
   double step_ms_total = 0.0, spin_updates = 0.0;
   int64_t launches = 0;
-  std::vector<int32_t> h_active(nb, 1), h_steps_run(nb);
+  std::vector<int32_t> h_active(sel_mask.begin(), sel_mask.begin() + nb), h_steps_run(nb);
   for (int32_t it = 0; it < refine_max; ++it) {
     NvtxRange nvtx_iter("qh_bsb_solve: solve of every active block");
     for (int32_t b = 0; b < nb; ++b)
@@ -807,7 +836,7 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
           launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.running);
           launch_pick_best(s, nb, R, B.cuts, B.best_r, B.best_cut, B.running);
           launch_early_stop(s, nb, B.best_cut, B.seen, B.stall, B.running, B.steps_run,
-                            o->patience, t1);
+                            o->patience, t1, B.steps_b);
         }
       }
     } else {
@@ -873,9 +902,11 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
       QH_CUDA_TRY(cudaMemcpyAsync(blk.data(), G.block_of, G.n_nodes * 4, cudaMemcpyDeviceToHost, s));
     }
     QH_CUDA_TRY(cudaStreamSynchronize(s));
+    // vertices of blocks left out of a partial solve: spin 0, flip count -1 (unphased)
     for (int32_t v = 0; v < G.n_nodes; ++v) {
-      sol.C[v] = hC[v];
-      sol.spins[v] = blk[v] >= 0 ? ((hC[v] % 2 == 0) ? 1 : -1) : 0;
+      const bool on = blk[v] >= 0 && sel_mask[blk[v]];
+      sol.C[v] = on ? hC[v] : -1;
+      sol.spins[v] = on ? ((hC[v] % 2 == 0) ? 1 : -1) : 0;
     }
     // cut of the parity partition on the ungauged weights (one pseudo-replica)
     int8_t* st1 = (int8_t*)ctx->scratch((size_t)std::max(G.n_pad, 1) + 16, S_SIGNS1);
@@ -891,11 +922,14 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     QH_CUDA_TRY(cudaStreamSynchronize(s));
     std::vector<int8_t> hs(std::max(G.n_pad, 1), 1);
     for (int32_t v = 0; v < G.n_nodes; ++v)
-      if (hp[v] >= 0) hs[hp[v]] = sol.spins[v];
+      if (hp[v] >= 0 && sol.spins[v] != 0) hs[hp[v]] = sol.spins[v];
     QH_CUDA_TRY(cudaMemcpyAsync(st1, hs.data(), G.n_pad, cudaMemcpyHostToDevice, s));
     launch_cut(s, G, 1, st1, G.w, G.sum_w, nv1, cut1, nullptr);
     QH_STAGE_CHECK("solve: final parity cut");
     QH_CUDA_TRY(cudaMemcpyAsync(sol.best_cut.data(), cut1, nb * 8, cudaMemcpyDeviceToHost, s));
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int32_t b = 0; b < nb; ++b)
+      if (!sel_mask[b]) sol.best_cut[b] = 0.0;
   } else {
     if (G.n_nodes)
       QH_CUDA_TRY(cudaMemcpyAsync(sol.spins.data(), B.spins, G.n_nodes, cudaMemcpyDeviceToHost, s));
@@ -913,7 +947,10 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
     }
     if (G.n_nodes) {
       QH_CUDA_TRY(cudaMemcpyAsync(sol.d_spins, sol.spins.data(), G.n_nodes, cudaMemcpyHostToDevice, s));
-      QH_CUDA_TRY(cudaMemcpyAsync(sol.d_C, B.C, G.n_nodes * 4, cudaMemcpyDeviceToDevice, s));
+      if (snp)
+        QH_CUDA_TRY(cudaMemcpyAsync(sol.d_C, sol.C.data(), G.n_nodes * 4, cudaMemcpyHostToDevice, s));
+      else
+        QH_CUDA_TRY(cudaMemcpyAsync(sol.d_C, B.C, G.n_nodes * 4, cudaMemcpyDeviceToDevice, s));
     }
     QH_CUDA_TRY(cudaStreamSynchronize(s));
   }
@@ -933,6 +970,47 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   return QH_OK;
 }
 
+qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_solution** out) {
+  return solve_impl(h, gh, o, nullptr, -1, out);
+}
+
+qh_status qh_bsb_solve_blocks(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
+                              const int32_t* blocks, int32_t n_blocks, qh_solution** out) {
+  if (h && !blocks && n_blocks > 0) return set_err(&h->c, QH_EINVAL, "NULL block list");
+  static const int32_t none = 0;
+  return solve_impl(h, gh, o, blocks ? blocks : &none, blocks ? n_blocks : 0, out);
+}
+
+qh_status qh_solution_set_block(qh_ctx* h, qh_solution* sh, int32_t b, const int8_t* spins,
+                                double best_cut, int32_t best_replica, int32_t steps_run,
+                                int32_t iterations) {
+  if (!h) return QH_EINVAL;
+  Ctx* ctx = &h->c;
+  ctx->err.clear();
+  if (!sh || !spins) return set_err(ctx, QH_EINVAL, "NULL argument");
+  Solution& s = sh->s;
+  if (b < 0 || b >= s.n_blocks) return set_err(ctx, QH_EINVAL, "block out of range");
+  if (best_replica < 0 || steps_run < 0 || iterations < 1 || !std::isfinite(best_cut))
+    return set_err(ctx, QH_EINVAL, "best_replica, steps_run >= 0, iterations >= 1, finite cut");
+  const int64_t k0 = s.block_ptr[b], k1 = s.block_ptr[b + 1];
+  for (int64_t k = k0; k < k1; ++k)
+    if (spins[k - k0] != 1 && spins[k - k0] != -1) return set_err(ctx, QH_EINVAL, "spins must be +1 or -1");
+  for (int64_t k = k0; k < k1; ++k) {
+    const int32_t v = s.perm[k];
+    s.spins[v] = spins[k - k0];
+    // SNP mode: the parity partition, +1 where the flip count is even
+    s.C[v] = spins[k - k0] > 0 ? 0 : 1;
+  }
+  s.best_cut[b] = best_cut;
+  s.best_r[b] = best_replica - s.replica_base;
+  s.steps_run[b] = steps_run;
+  s.iters[b] = iterations;
+  for (int32_t r = 0; r < s.R; ++r) s.cuts_first[(size_t)b * s.R + r] = 0.0;
+  s.solved[b] = 1;
+  s.device_stale = true;
+  return QH_OK;
+}
+
 qh_status qh_solution_block(qh_ctx* h, const qh_solution* sh, int32_t b, int8_t* spins,
                             double* best_cut, int32_t* best_replica, int32_t* steps_run,
                             int32_t* iterations) {
@@ -944,7 +1022,7 @@ qh_status qh_solution_block(qh_ctx* h, const qh_solution* sh, int32_t b, int8_t*
     for (int64_t k = s.block_ptr[b]; k < s.block_ptr[b + 1]; ++k)
       spins[k - s.block_ptr[b]] = s.spins[s.perm[k]];
   if (best_cut) *best_cut = s.best_cut[b];
-  if (best_replica) *best_replica = s.replica_base + s.best_r[b];
+  if (best_replica) *best_replica = s.solved[b] ? s.replica_base + s.best_r[b] : -1;
   if (steps_run) *steps_run = s.steps_run[b];
   if (iterations) *iterations = s.iters[b];
   return QH_OK;
@@ -1001,6 +1079,12 @@ qh_status qh_phase(qh_ctx* h, const qh_graph* gh, const qh_solution* sh, int8_t*
     return set_err(ctx, QH_EINVAL, "solution does not belong to this graph");
   cudaSetDevice(ctx->device);
   cudaStream_t s = ctx->stream;
+  if (sol.device_stale && g.n_nodes) {  // blocks imported by qh_solution_set_block
+    QH_CUDA_TRY(cudaMemcpyAsync(sol.d_spins, sol.spins.data(), g.n_nodes, cudaMemcpyHostToDevice, s));
+    QH_CUDA_TRY(cudaMemcpyAsync(sol.d_C, sol.C.data(), (size_t)g.n_nodes * 4, cudaMemcpyHostToDevice, s));
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+    sol.device_stale = false;
+  }
   const int32_t n = g.n_snps;
   int8_t *d1 = hap1, *d2 = hap2;
   int32_t* db = block_id;
@@ -1038,6 +1122,35 @@ qh_status qh_debug_wait_timeout(qh_ctx* h, int32_t which) {
 qh_status qh_debug_fail_alloc(qh_ctx* h, int64_t after) {
   if (!h || after < -1 || !h->c.mem.fail_after) return QH_EINVAL;
   *h->c.mem.fail_after = after;
+  return QH_OK;
+}
+
+qh_status qh_debug_init_state(qh_ctx* h, const qh_graph* gh, int32_t R, int32_t replica_base,
+                              uint64_t seed, int32_t iter, float* x, float* y) {
+  if (!h) return QH_EINVAL;
+  Ctx* ctx = &h->c;
+  ctx->err.clear();
+  clear_foreign_error(ctx);
+  if (!gh || !x || !y) return set_err(ctx, QH_EINVAL, "NULL argument");
+  if (R < 1 || replica_base < 0 || (int64_t)replica_base + R > (1 << 16) || iter < 0)
+    return set_err(ctx, QH_EINVAL, "R >= 1, iter >= 0 and replica indices below 65536 required");
+  const Graph& g = gh->g;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = ctx->stream;
+  const size_t NS = (size_t)R * g.n_pad;
+  if (NS == 0) return QH_OK;
+  if (g.csr_mode) {  // the solver's vertex-major layout, transposed to [R][n_pad]
+    float* xt = (float*)ctx->scratch(NS * 4, S_TR0);
+    float* yt = (float*)ctx->scratch(NS * 4, S_TR1);
+    if (!xt || !yt) return set_err(ctx, QH_ENOMEM, "allocation failed (debug)");
+    launch_init_state(s, g, R, replica_base, seed, iter, xt, yt, nullptr, nullptr);
+    launch_transpose(s, xt, x, g.n_pad, R);
+    launch_transpose(s, yt, y, g.n_pad, R);
+  } else {
+    launch_init_state(s, g, R, replica_base, seed, iter, x, y, nullptr, nullptr);
+  }
+  QH_STAGE_CHECK("debug: state init");
+  QH_CUDA_TRY(cudaStreamSynchronize(s));
   return QH_OK;
 }
 

@@ -87,8 +87,9 @@ struct RunArgs {
                             // [n_blocks][n_kt] items finished; zero at launch
   const int32_t* rows_b;    // [n_blocks] row tiles per block
   int32_t group_sync;       // hand-off mode: 0 = tile, 1 = group
-  const int2* work;         // [grid] {first item, item count}
-  int32_t item_stride;      // a CTA's items are first, first + stride, ...
+  const int2* work;         // [grid] {first position, item count} in the wave's item list
+  const int32_t* items;     // the wave's items (row tile * n_kt + replica tile)
+  int32_t item_stride;      // a CTA's items sit at positions first, first + stride, ...
   int32_t n_pad, n_kt, t0, t1, use_lo;
   float dt, dta0;
   double a0;
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (warp == 2 && lane < n_items) {
-    const int item = wk.x + lane * a.item_stride;
+    const int item = a.items[wk.x + lane * a.item_stride];
     const RowTile rt = a.rt[item / a.n_kt];
     ItemInfo it;
     it.row0 = rt.row0;
@@ -598,9 +599,10 @@ static bool run_jres(int v) { return v == RUN_VARIANT_FIRST || v == RUN_VARIANT_
 static bool run_group(int v) { return v == RUN_VARIANT_FIRST || v == RUN_VARIANT_FIRST + 3; }
 
 // Work split.  Items are numbered row-tile-major (item = row_tile * n_kt + k), and
-// the blocks' row tiles are contiguous, so a set of whole blocks is a range of items.
-// Blocks are packed into waves whose items fit on chip (at most MAX_ITEMS per SM); a
-// wave is one launch over the step range, and the waves run one after the other.
+// the blocks' row tiles are contiguous.  Blocks (all, or those of a partial solve)
+// are packed into waves whose items fit on chip (at most MAX_ITEMS per SM); a wave
+// lists its items row-tile-major and is one launch over the step range, and the
+// waves run one after the other.
 // Within a wave a CTA processes its items in a fixed order every step, and the split
 // puts the row-tile neighbours of an item (item -+ n_kt, same k) at the same position
 // in their CTAs, so an item's inputs for step t+1 are finished a whole step period
@@ -608,7 +610,8 @@ static bool run_group(int v) { return v == RUN_VARIANT_FIRST || v == RUN_VARIANT
 // tiles of ONE row tile (its J tiles stay resident), the same k ranges in every row.
 // Stream: CTA c of the wave's G CTAs takes the wave's items c, c + G, c + 2G, ...
 // False when some block does not fit one wave.
-bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, RunPlan* plan) {
+bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, RunPlan* plan,
+              const std::vector<int32_t>* mask) {
   if (!run_variant(variant)) return false;
   const bool jres = run_jres(variant);
   if (R % RB != 0 || g.n_row_tiles == 0 || g.csr_mode || n_sm < 1) return false;
@@ -621,6 +624,7 @@ bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, RunPlan
   std::vector<int32_t> first(std::max(g.n_blocks, 1), -1), count(std::max(g.n_blocks, 1), 0);
   for (int32_t r = 0; r < g.n_row_tiles; ++r) {
     const int32_t b = g.h_rt[r].block;
+    if (mask && !(*mask)[b]) continue;
     if (first[b] < 0) first[b] = r;
     count[b] += 1;
   }
@@ -635,47 +639,51 @@ bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, RunPlan
   const int64_t n_waves = (total + cap - 1) / cap;
   const int64_t target = (total + n_waves - 1) / n_waves;
   RunPlan p;
-  auto emit = [&](int32_t r0, int32_t r1) {
+  // a wave's items: those of its row tiles, row-tile-major; work entries index this list
+  auto emit = [&](const std::vector<int32_t>& rows) {
     RunWave w;
     w.work_off = (int)p.work.size();
+    w.item_off = (int)p.items.size();
+    for (int32_t r : rows)
+      for (int k = 0; k < n_kt; ++k) p.items.push_back(r * n_kt + k);
     if (jres) {
-      for (int32_t r = r0; r < r1; ++r)
+      for (size_t j = 0; j < rows.size(); ++j)
         for (int c = 0; c < cpr; ++c) {
           const int b = (int)((int64_t)n_kt * c / cpr), e = (int)((int64_t)n_kt * (c + 1) / cpr);
-          p.work.push_back(make_int2(r * n_kt + b, e - b));
+          p.work.push_back(make_int2((int)j * n_kt + b, e - b));
         }
       w.stride = 1;
     } else {
-      const int64_t i0 = (int64_t)r0 * n_kt, n = (int64_t)(r1 - r0) * n_kt;
+      const int64_t n = (int64_t)rows.size() * n_kt;
       const int64_t grid = std::min<int64_t>(n_sm, n);
       for (int64_t c = 0; c < grid; ++c)
-        p.work.push_back(make_int2((int)(i0 + c), (int)((n - c + grid - 1) / grid)));
+        p.work.push_back(make_int2((int)c, (int)((n - c + grid - 1) / grid)));
       w.stride = (int)grid;
     }
     w.grid = (int)p.work.size() - w.work_off;
     p.waves.push_back(w);
   };
-  int32_t r0 = -1, r1 = -1;
+  std::vector<int32_t> rows;
   int64_t cur = 0;
   for (int32_t b = 0; b < g.n_blocks; ++b) {
     if (count[b] == 0) continue;
-    if (r0 >= 0 && cur + load(b) > target) {  // target <= cap
-      emit(r0, r1);
-      r0 = -1;
+    if (!rows.empty() && cur + load(b) > target) {  // target <= cap
+      emit(rows);
+      rows.clear();
       cur = 0;
     }
-    if (r0 < 0) r0 = first[b];
-    r1 = first[b] + count[b];
+    for (int32_t r = first[b]; r < first[b] + count[b]; ++r) rows.push_back(r);
     cur += load(b);
   }
-  if (r0 >= 0) emit(r0, r1);
+  if (!rows.empty()) emit(rows);
   if (plan) *plan = std::move(p);
   return true;
 }
 
-qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo, RunBufs* rb) {
+qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo, RunBufs* rb,
+                      const std::vector<int32_t>* mask) {
   RunPlan plan;
-  if (!run_plan(g, R, ctx->n_sm, variant, use_lo, &plan))
+  if (!run_plan(g, R, ctx->n_sm, variant, use_lo, &plan, mask))
     return set_err(ctx, QH_EINVAL, "multi-step kernel: a block does not fit one wave");
   const int n_kt = R / RB;
   rb->jres = run_jres(variant);
@@ -684,13 +692,16 @@ qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo,
   std::vector<int32_t> rows(std::max(g.n_blocks, 1), 0);
   for (const RowTile& rt : g.h_rt) rows[rt.block] += 1;
   rb->n_done = (int64_t)(rb->group_sync ? (int64_t)rows.size() : g.n_row_tiles) * n_kt;
-  rb->work = (int2*)ctx->scratch(plan.work.size() * sizeof(int2), S_RUN_WORK);
+  rb->work = (int2*)ctx->scratch(std::max<size_t>(plan.work.size(), 1) * sizeof(int2), S_RUN_WORK);
+  rb->items = (int32_t*)ctx->scratch(std::max<size_t>(plan.items.size(), 1) * 4, S_RUN_ITEMS);
   rb->rows_b = (int32_t*)ctx->scratch(rows.size() * 4, S_RUN_ROWS);
   rb->done = (uint32_t*)ctx->scratch((size_t)rb->n_done * 4, S_RUN_DONE);
   rb->xq = (float4*)ctx->scratch((size_t)R * g.n_pad * 4, S_RUN_XQ);
-  if (!rb->work || !rb->rows_b || !rb->done || !rb->xq)
+  if (!rb->work || !rb->items || !rb->rows_b || !rb->done || !rb->xq)
     return set_err(ctx, QH_ENOMEM, "allocation failed (multi-step kernel)");
   QH_CUDA_TRY(cudaMemcpyAsync(rb->work, plan.work.data(), plan.work.size() * sizeof(int2),
+                              cudaMemcpyHostToDevice, ctx->stream));
+  QH_CUDA_TRY(cudaMemcpyAsync(rb->items, plan.items.data(), plan.items.size() * 4,
                               cudaMemcpyHostToDevice, ctx->stream));
   QH_CUDA_TRY(cudaMemcpyAsync(rb->rows_b, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice,
                               ctx->stream));
@@ -735,6 +746,7 @@ qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const Run
   QH_CUDA_TRY(cudaMemsetAsync(rb.done, 0, (size_t)rb.n_done * 4, ctx->stream));
   for (const RunWave& w : rb.waves) {
     a.work = rb.work + w.work_off;
+    a.items = rb.items + w.item_off;
     a.item_stride = w.stride;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)w.grid);

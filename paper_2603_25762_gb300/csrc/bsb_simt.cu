@@ -746,11 +746,15 @@ __global__ void k_pick_best(int32_t nb, int32_t R, const double* __restrict__ cu
   }
 }
 
+// Early stop on a stalled best energy: a check after t_done steps compares the block's
+// best cut over replicas with the best of its earlier checks.  Checks happen only while
+// the block's own schedule has steps left (t_done < steps_b): a block whose schedule is
+// shorter than the longest one is not checked after it has finished.
 __global__ void k_early_stop(int32_t nb, const double* __restrict__ best_cut, double* best_seen,
                              int32_t* stall, int32_t* active, int32_t* steps_run, int32_t patience,
-                             int32_t t_done) {
+                             int32_t t_done, const int32_t* __restrict__ steps_b) {
   int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb || !active[b]) return;
+  if (b >= nb || !active[b] || t_done >= steps_b[b]) return;
   if (best_cut[b] > best_seen[b]) {
     best_seen[b] = best_cut[b];
     stall[b] = 0;
@@ -941,6 +945,7 @@ __global__ void k_parity(int32_t n, const int32_t* __restrict__ block_of, const 
   int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= n) return;
   int32_t b = block_of[u];
+  if (b >= 0 && C[u] < 0) b = -1;  // block not solved (partial solution): unphased
   int8_t h = b >= 0 ? ((C[u] % 2 == 0) ? 1 : -1) : 0;
   hap1[u] = h;
   hap2[u] = (int8_t)(-h);
@@ -1078,10 +1083,10 @@ void launch_pick_best(cudaStream_t s, int32_t n_blocks, int32_t R, const double*
 
 void launch_early_stop(cudaStream_t s, int32_t n_blocks, const double* best_cut, double* best_seen,
                        int32_t* stall, int32_t* active, int32_t* steps_run, int32_t patience,
-                       int32_t t_done) {
+                       int32_t t_done, const int32_t* steps_b) {
   if (n_blocks > 0)
     k_early_stop<<<::qh::counted(nblk(n_blocks)), 256, 0, s>>>(n_blocks, best_cut, best_seen, stall, active,
-                                               steps_run, patience, t_done);
+                                               steps_run, patience, t_done, steps_b);
 }
 
 void launch_extract_spins(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t,

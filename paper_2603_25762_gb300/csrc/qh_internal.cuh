@@ -145,7 +145,9 @@ struct Solution {
   std::vector<double> best_cut;
   std::vector<double> cuts_first;        // [n_blocks * R]
   std::vector<int8_t> spins;             // [n_nodes] best spins by vertex (0 = dropped)
-  std::vector<int32_t> C;                // SNP mode flip counts [n_nodes]
+  std::vector<int32_t> C;                // SNP mode flip counts [n_nodes] (-1: block not solved)
+  std::vector<uint8_t> solved;           // [n_blocks] 1 = solved here or imported
+  mutable bool device_stale = false;     // host spins / C changed after the device copies
   double solve_ms = 0, step_ms = 0, spin_updates = 0;
   int64_t n_step_launches = 0;
   std::string kernel;                    // step kernel that ran
@@ -310,7 +312,7 @@ void launch_pick_best(cudaStream_t s, int32_t n_blocks, int32_t R, const double*
                       int32_t* best_r, double* best_cut, const int32_t* active);
 void launch_early_stop(cudaStream_t s, int32_t n_blocks, const double* best_cut, double* best_seen,
                        int32_t* stall, int32_t* active, int32_t* steps_run, int32_t patience,
-                       int32_t t_done);
+                       int32_t t_done, const int32_t* steps_b);
 void launch_extract_spins(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t,
                           const int32_t* best_r, int8_t* spins, const int32_t* active);
 void launch_block_sums(cudaStream_t s, const Graph& g, const double* w, double* sum_w,
@@ -364,18 +366,21 @@ qh_status tc_prepare(Ctx* ctx);
 //   8: J resident in smem, tile hand-off    9: J streamed, group hand-off
 constexpr int RUN_VARIANT_FIRST = 6;
 constexpr int S_RUN_WORK = 96, S_RUN_ROWS = 97, S_RUN_DONE = 98, S_RUN_XQ = 99;  // scratch slots
-constexpr int S_WAIT_PROBE = 100;
+constexpr int S_WAIT_PROBE = 100, S_RUN_ITEMS = 101;
 struct RunWave {              // one launch: whole blocks whose items fit on chip
   int work_off = 0;           // first entry of the wave in RunBufs::work
+  int item_off = 0;           // first entry of the wave in RunBufs::items
   int grid = 0;               // CTAs
   int stride = 1;             // a CTA's items: first, first + stride, ...
 };
 struct RunPlan {
-  std::vector<int2> work;     // per CTA of every wave: {first item, item count}
+  std::vector<int2> work;     // per CTA of every wave: {first position, item count}
+  std::vector<int32_t> items; // per wave: its items, row-tile-major
   std::vector<RunWave> waves;
 };
 struct RunBufs {
   int2* work = nullptr;       // device copy of RunPlan::work
+  int32_t* items = nullptr;   // device copy of RunPlan::items
   int32_t* rows_b = nullptr;  // [n_blocks] row tiles per block
   uint32_t* done = nullptr;   // release counters (per item or per block x replica tile)
   float4* xq = nullptr;       // [R/4][n_pad] blocked working copy of x
@@ -385,8 +390,11 @@ struct RunBufs {
   bool group_sync = false;
 };
 bool run_variant(int v);
-bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, RunPlan* plan);
-qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo, RunBufs* rb);
+// mask (n_blocks flags, or nullptr = every block): blocks left out take no items
+bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, RunPlan* plan,
+              const std::vector<int32_t>* mask = nullptr);
+qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo, RunBufs* rb,
+                      const std::vector<int32_t>* mask = nullptr);
 // Steps t0 .. t1-1 in one launch.  X_hat_t is read from xh0 (t even) or xh1 (t odd);
 // x, y of `s` are updated in place.
 qh_status launch_run(Ctx* ctx, const Graph& g, const StepArgs& s, const RunBufs& rb,

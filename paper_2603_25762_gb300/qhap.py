@@ -89,6 +89,8 @@ _SIGS = {
     "qh_graph_blocks": (C.c_int, [P, P, P, P]),
     "qh_graph_free": (None, [P]),
     "qh_bsb_solve": (C.c_int, [P, P, C.POINTER(QhBsbOpts), PP]),
+    "qh_bsb_solve_blocks": (C.c_int, [P, P, C.POINTER(QhBsbOpts), P, I32, PP]),
+    "qh_solution_set_block": (C.c_int, [P, P, I32, P, D, I32, I32, I32]),
     "qh_solution_block": (C.c_int, [P, P, I32, P, P, P, P, P]),
     "qh_solution_spins": (C.c_int, [P, P, P]),
     "qh_solution_cuts": (C.c_int, [P, P, P]),
@@ -101,6 +103,7 @@ _SIGS = {
     "qh_debug_fail_alloc": (C.c_int, [P, I64]),
     "qh_debug_steps_v": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P, I32, I32, P]),
     "qh_debug_layout": (C.c_int, [P, P, P, P, P]),
+    "qh_debug_init_state": (C.c_int, [P, P, I32, I32, C.c_uint64, I32, P, P]),
     "qh_matvec_bf16_noalloc": (C.c_int, [P, P, I32, P, P]),
     "qh_solution_kernel": (C.c_char_p, [P]),
     "qh_tuning_report": (C.c_char_p, [P]),
@@ -209,6 +212,13 @@ class Solution:
         return {"best_cut": cut.value, "best_replica": br.value, "steps_run": sr.value,
                 "iterations": it.value, "spins": sp[:size] if size else None}
 
+    def set_block(self, b, spins, best_cut, best_replica, steps_run, iterations):
+        """Import block b's result (as block() returns it in another process)."""
+        sp = _np(spins, np.int8)
+        self.ctx._check(lib().qh_solution_set_block(self.ctx.h, self.h, b, _ptr(sp),
+                                                    float(best_cut), int(best_replica),
+                                                    int(steps_run), int(iterations)))
+
     def spins(self, n_nodes):
         s = np.zeros(max(n_nodes, 1), np.int8)
         self.ctx._check(lib().qh_solution_spins(self.ctx.h, self.h, _ptr(s)))
@@ -271,7 +281,7 @@ class Context:
     def solve(self, g, replicas=32, steps=1000, precision=PREC_FP32, seed=1, dt=1.0, a0=1.0,
               c0=0.0, schedule=SCHED_LINEAR, replica_base=0, check_every=0, patience=0,
               refine_max=15, step_kernel=None, variant="ballistic", deform_h=0.0,
-              deform_tries=0):
+              deform_tries=0, blocks=None):
         """step_kernel: None = the default (autotuned on BF16 tile storage), or a name
         from STEP_KERNELS: the tile variants for BF16 tile storage, "csr-lane4" /
         "csr-lane8" for CSR storage.
@@ -279,13 +289,21 @@ class Context:
         QH_SB_* value itself.
         deform_h, deform_tries: the SNP refinement's adaptive deformation (0 = off): up
         to deform_tries re-solves of a block whose cut is <= 0, with a field along the
-        incumbent of strength deform_h 2^(k-1)."""
+        incumbent of strength deform_h 2^(k-1).
+        blocks: None = every block; else the block indices to solve (the others stay
+        unsolved, see qh_bsb_solve_blocks)."""
         sk = -1 if step_kernel is None else STEP_KERNELS.index(step_kernel)
         o = QhBsbOpts(replicas, steps, schedule, precision, dt, a0, c0, seed, replica_base,
                       check_every, patience, refine_max, sk, _sb(variant), deform_h,
                       deform_tries, 0)
         s = C.c_void_p()
-        self._check(lib().qh_bsb_solve(self.h, g.h, C.byref(o), C.byref(s)))
+        if blocks is None:
+            self._check(lib().qh_bsb_solve(self.h, g.h, C.byref(o), C.byref(s)))
+        else:
+            sel = _np(blocks, np.int32)
+            self._check(lib().qh_bsb_solve_blocks(self.h, g.h, C.byref(o),
+                                                  _ptr(sel) if sel.size else None,
+                                                  int(sel.size), C.byref(s)))
         return Solution(self, s, g.n_blocks, replicas)
 
     def phase(self, g, sol, n_snps, out=None):
@@ -316,6 +334,12 @@ class Context:
                                            _ptr(c0a) if c0a is not None else None, sk,
                                            _sb(variant),
                                            _ptr(fa) if fa is not None else None))
+
+    def debug_init_state(self, g, R, x, y, replica_base=0, seed=1, it=0):
+        """The solver's initial x, y (torch CUDA float32 tensors [R][n_pad]) for replicas
+        replica_base .. replica_base + R - 1 of refinement iteration `it`."""
+        self._check(lib().qh_debug_init_state(self.h, g.h, R, replica_base, seed, it, _ptr(x),
+                                              _ptr(y)))
 
     def debug_wait_timeout(self, which=0):
         """Failure-detection hook: a bounded device wait that expires (raises QhError

@@ -100,12 +100,15 @@ def _solve_case(q, ctx, oracle, fr, R, steps, seed, kernel, n_oracle=16, **kw):
                     step_kernel=kernel, **kw)
     og = oracle.read_graph(fr, oracle.READ_SIGNED)
     spins = sol.spins(g.n_nodes)
+    cuts = sol.cuts()
     for b, nodes in enumerate(oracle.blocks_of(og)):
         sub = og.subgraph(nodes)
         info = sol.block(b, len(nodes))
         assert info["best_cut"] == oracle.cut(sub, spins[nodes])
+        # the GPU's best over the oracle's replica indices (same initial draws)
         best, _, _, _ = oracle.bsb_solve(sub, list(range(n_oracle)), steps, seed, b)
-        assert info["best_cut"] >= 0.999 * best, (b, info["best_cut"], best)
+        same = cuts[b][:n_oracle].max()
+        assert same >= 0.999 * best, (b, same, best)
     assert sol.timing()["kernel"] == kernel
     return g, sol
 
@@ -215,10 +218,11 @@ def test_multistep_several_waves_solve(q, ctx, oracle):
     og = oracle.read_graph(fr, oracle.READ_SIGNED)
     blocks = oracle.blocks_of(og)
     spins = sol.spins(g.n_nodes)
+    cuts = sol.cuts()
     for b in [0, 13, 27, 39]:
         nodes = blocks[b]
         sub = og.subgraph(nodes)
         info = sol.block(b, len(nodes))
         assert info["best_cut"] == oracle.cut(sub, spins[nodes])
         best, _, _, _ = oracle.bsb_solve(sub, list(range(8)), 400, 4, b)
-        assert info["best_cut"] >= 0.999 * best, (b, info["best_cut"], best)
+        assert cuts[b][:8].max() >= 0.999 * best, (b, cuts[b][:8].max(), best)

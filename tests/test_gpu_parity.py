@@ -346,15 +346,21 @@ def _check_solve(q, ctx, oracle, fr, precision, R, steps, seed, n_oracle=None, s
     og = oracle.read_graph(fr, oracle.READ_SIGNED)
     blocks = oracle.blocks_of(og)
     spins = sol.spins(g.n_nodes)
-    ridx = list(range(n_oracle or R))
+    n_or = n_oracle or R
+    ridx = list(range(n_or))
+    cuts = sol.cuts()
     for b, nodes in enumerate(blocks):
         sub = og.subgraph(nodes)
         info = sol.block(b, len(nodes))
         # exact cut evaluation of the GPU's chosen spins
         assert info["best_cut"] == oracle.cut(sub, spins[nodes])
         assert np.array_equal(info["spins"], spins[nodes])
+        assert info["best_cut"] == cuts[b].max()
+        # same seed, steps and replica indices on both sides: the GPU's best over the
+        # oracle's replicas (identical initial draws), not over its larger R
         best, _, _, _ = oracle.bsb_solve(sub, ridx, steps, seed, b)
-        assert info["best_cut"] >= 0.999 * best, (b, info["best_cut"], best)
+        same = cuts[b][:n_or].max()
+        assert same >= 0.999 * best, (b, same, best)
     return g, sol
 
 
@@ -391,14 +397,124 @@ def test_solution_cuts_are_exact_and_deterministic(q, ctx, oracle):
         assert info["best_replica"] == int(np.argmax(c[b]))
 
 
-def test_early_stop_and_auto_schedule(q, ctx):
+# ----------------------------------------------------------------------------- bSB setup
+def _init_state_case(q, ctx, oracle, g, og, R, base, seed, it):
+    import torch
+    n_pad, pidx, _ = g.layout()
+    x = torch.full((R, n_pad), float("nan"), dtype=torch.float32, device="cuda")
+    y = torch.full_like(x, float("nan"))
+    ctx.debug_init_state(g, R, x, y, replica_base=base, seed=seed, it=it)
+    xg, yg = x.cpu().numpy(), y.cpu().numpy()
+    pad = np.ones(n_pad, bool)
+    pad[pidx[pidx >= 0]] = False
+    assert np.all(xg[:, pad] == 0) and np.all(yg[:, pad] == 0)
+    for b, nodes in enumerate(oracle.blocks_of(og)):
+        xo, yo = oracle.bsb_init(len(nodes), list(range(base, base + R)), seed, b, it)
+        # drawn in FP64, rounded once to FP32 on the GPU: bit-identical after that rounding
+        assert np.array_equal(xg[:, pidx[nodes]], xo.astype(np.float32)), b
+        assert np.array_equal(yg[:, pidx[nodes]], yo.astype(np.float32)), b
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+@pytest.mark.parametrize("base,it", [(0, 0), (64, 0), (3, 5)])
+def test_init_state_matches_oracle_draws(q, ctx, oracle, storage, base, it):
+    """The initial x, y of every replica equal the oracle's SplitMix64 draws bit for bit
+    (after the one FP32 rounding), keyed by block, refinement iteration and the global
+    replica index, so a replica range starting at replica_base is the oracle's range."""
+    fr = synth.batched_blocks(1004, n_blocks=5, n_min=30, n_max=300)
+    g = ctx.build_graph(fr, storage=storage)
+    og = oracle.read_graph(fr, oracle.READ_SIGNED)
+    _init_state_case(q, ctx, oracle, g, og, 64, base, seed=1234567, it=it)
+
+
+def test_init_state_snp_graph(q, ctx, oracle):
+    fr = synth.ont_region(1003, scale=0.05)
+    g = ctx.build_graph(fr, mode=q.MODE_SNP)
+    _init_state_case(q, ctx, oracle, g, oracle.snp_graph(fr), 32, 0, seed=9, it=2)
+
+
+@pytest.mark.parametrize("mode", ["read", "snp"])
+def test_default_c0_matches_oracle(q, ctx, oracle, mode):
+    """The default coupling scale c0 = 0.5 / (sigma sqrt(N)) of every block, from the
+    GPU's block sums (FP64), against the oracle's per-block sums."""
+    if mode == "read":
+        fr = synth.batched_blocks(1004, n_blocks=6, n_min=40, n_max=500)
+        g, og = ctx.build_graph(fr), oracle.read_graph(fr, oracle.READ_SIGNED)
+    else:
+        fr = synth.ont_region(1003, scale=0.06)
+        g, og = ctx.build_graph(fr, mode=q.MODE_SNP), oracle.snp_graph(fr)
+    _, _, c0 = g.layout()
+    blocks = oracle.blocks_of(og)
+    assert len(blocks) == g.n_blocks
+    for b, nodes in enumerate(blocks):
+        ref = oracle.default_c0(og.subgraph(nodes))
+        assert c0[b] == pytest.approx(ref, rel=1e-12), b
+
+
+# ----------------------------------------------------------------------------- early stop
+@pytest.mark.parametrize("precision,R", [(0, 32), (1, 64)])
+def test_early_stop_steps_run_matches_oracle(q, ctx, oracle, precision, R):
+    """Early stop on a stalled best energy (check every 50 steps, patience 3): each
+    block stops after exactly the oracle's number of steps on the same replicas, and
+    its best cut is the oracle's to 0.999."""
     fr = synth.tiny_reads(1001)
     g = ctx.build_graph(fr)
-    sol = ctx.solve(g, replicas=64, steps=3000, precision=q.PREC_BF16, seed=2, check_every=50,
-                    patience=3)
-    runs = [sol.block(b)["steps_run"] for b in range(g.n_blocks)]
-    assert all(50 <= r <= 3000 for r in runs)
-    assert min(runs) < 3000
+    steps, seed, ce, pat = 3000, 2, 50, 3
+    sol = ctx.solve(g, replicas=R, steps=steps, precision=precision, seed=seed, check_every=ce,
+                    patience=pat)
+    og = oracle.read_graph(fr, oracle.READ_SIGNED)
+    spins = sol.spins(g.n_nodes)
+    for b, nodes in enumerate(oracle.blocks_of(og)):
+        sub = og.subgraph(nodes)
+        best, _, _, _, sr = oracle.bsb_solve_early_stop(sub, list(range(R)), steps, seed, ce,
+                                                        pat, block=b)
+        info = sol.block(b)
+        assert sr < steps
+        assert info["steps_run"] == sr, (b, info["steps_run"], sr)
+        assert info["best_cut"] == oracle.cut(sub, spins[nodes])
+        assert info["best_cut"] >= 0.999 * best
+
+
+def _two_schedule_fragments():
+    """One block of more than 5,000 reads (AUTO schedule: 1,000 steps) and one small
+    block (500 steps) on disjoint SNPs."""
+    big = synth.region_reads(77, n_snps=9000, region=3_000_000, n_reads=5200)
+    small = synth.tiny_reads(1001)
+    ptr = np.concatenate([big.frag_ptr, small.frag_ptr[1:] + big.frag_ptr[-1]])
+    return synth.Fragments(big.n_snps + small.n_snps, ptr.astype(np.int64),
+                           np.concatenate([big.snp, small.snp + big.n_snps]).astype(np.int32),
+                           np.concatenate([big.allele, small.allele]),
+                           np.concatenate([big.qual, small.qual]),
+                           np.zeros(ptr.shape[0] - 1, np.uint8),
+                           np.concatenate([big.positions, small.positions + 4_000_000]),
+                           np.concatenate([big.truth, small.truth]))
+
+
+def test_early_stop_respects_each_block_schedule(q, ctx, oracle):
+    """AUTO schedule with blocks of 500 and 1,000 steps: the short block is checked only
+    while its own schedule runs, as in the oracle (patience 12 cannot be reached in its
+    nine checks, so it runs all 500 steps)."""
+    fr = _two_schedule_fragments()
+    g = ctx.build_graph(fr)
+    sizes = g.block_sizes()
+    assert sorted(sizes)[-1] >= 5000 and sorted(sizes)[0] < 5000
+    sol = ctx.solve(g, replicas=64, precision=q.PREC_BF16, seed=4, schedule=q.SCHED_AUTO,
+                    check_every=50, patience=12)
+    og = oracle.read_graph(fr, oracle.READ_SIGNED)
+    for b, nodes in enumerate(oracle.blocks_of(og)):
+        info = sol.block(b)
+        if len(nodes) >= 5000:
+            assert info["steps_run"] <= 1000
+            continue
+        _, _, _, _, sr = oracle.bsb_solve_early_stop(og.subgraph(nodes), list(range(64)), 500,
+                                                     4, 50, 12, block=b)
+        assert sr == 500
+        assert info["steps_run"] == sr, (b, info["steps_run"])
+
+
+def test_auto_schedule_steps(q, ctx):
+    fr = synth.tiny_reads(1001)
+    g = ctx.build_graph(fr)
     sol2 = ctx.solve(g, replicas=64, precision=q.PREC_FP32, seed=2, schedule=q.SCHED_AUTO)
     assert all(sol2.block(b)["steps_run"] == 500 for b in range(g.n_blocks))
 
@@ -623,3 +739,88 @@ def test_bounded_wait_expires_and_context_survives(q, ctx, oracle, which):
     assert e.value.status == 4  # QH_ETIMEOUT
     assert 0.2 < time.perf_counter() - t0 < 30
     _check_solve(q, ctx, oracle, synth.tiny_reads(1001), q.PREC_BF16, 64, 500, seed=11)
+
+
+# ----------------------------------------------------------------------------- sharding
+@pytest.mark.parametrize("precision,kernel,R", [(0, None, 32), (1, "cta-bn64-s2-x4", 64),
+                                                (1, "multistep-stream-tile", 128)])
+def test_replica_ranges_combine_to_one_solve(q, ctx, precision, kernel, R):
+    """Replica sharding: replicas base .. base + R - 1 of a solve at replica_base are
+    exactly those replicas of one solve over 2R (same draws, same per-replica
+    arithmetic), and the cross-rank pick over the two halves is that solve's pick."""
+    from paper_2603_25762_gb300 import multi
+    fr = synth.batched_blocks(1004, n_blocks=4, n_min=60, n_max=400)
+    g = ctx.build_graph(fr)
+    kw = dict(steps=400, precision=precision, seed=8, step_kernel=kernel)
+    full = ctx.solve(g, replicas=2 * R, **kw)
+    halves = [ctx.solve(g, replicas=R, replica_base=base, **kw) for base in (0, R)]
+    cf = full.cuts()
+    assert np.array_equal(halves[0].cuts(), cf[:, :R])
+    assert np.array_equal(halves[1].cuts(), cf[:, R:])
+    C = np.array([[h.block(b)["best_cut"] for b in range(g.n_blocks)] for h in halves])
+    P = np.array([[h.block(b)["best_replica"] for b in range(g.n_blocks)] for h in halves])
+    owner = multi.pick_best(C, P)
+    for b in range(g.n_blocks):
+        ref = full.block(b)
+        assert C[owner[b], b] == ref["best_cut"] and P[owner[b], b] == ref["best_replica"]
+
+
+def _block_subset_case(q, ctx, fr, mode, **kw):
+    from paper_2603_25762_gb300 import multi
+    g = ctx.build_graph(fr, mode=mode)
+    sizes = g.block_sizes()
+    full = ctx.solve(g, **kw)
+    shards = multi.block_shards(sizes, 2, kw["replicas"])
+    assert shards[0] and shards[1]
+    part = [ctx.solve(g, blocks=s, **kw) for s in shards]
+    # before the exchange: each part has its own blocks only
+    h1p, _, bidp = ctx.phase(g, part[0], fr.n_snps)
+    for b in shards[1]:
+        info = part[0].block(b, int(sizes[b]))
+        assert info["best_replica"] == -1 and info["steps_run"] == 0
+        assert not np.any(info["spins"])
+        assert not np.any(bidp == b)
+    # import the other part's blocks, as the all-gather of a sharded run does
+    for b in shards[1]:
+        r = part[1].block(b, int(sizes[b]))
+        part[0].set_block(b, r["spins"], r["best_cut"], r["best_replica"], r["steps_run"],
+                          r["iterations"])
+    for b in range(g.n_blocks):
+        a, ref = part[0].block(b, int(sizes[b])), full.block(b, int(sizes[b]))
+        for key in ("best_cut", "best_replica", "steps_run", "iterations"):
+            assert a[key] == ref[key], (b, key)
+        assert np.array_equal(a["spins"], ref["spins"]), b
+    h1, h2, bid = ctx.phase(g, part[0], fr.n_snps)
+    r1, r2, rbid = ctx.phase(g, full, fr.n_snps)
+    assert np.array_equal(h1, r1) and np.array_equal(h2, r2) and np.array_equal(bid, rbid)
+    return g
+
+
+@pytest.mark.parametrize("kernel", ["cta-bn128-s3", "multistep-stream-group",
+                                    "multistep-jres-tile"])
+def test_block_subsets_combine_to_the_full_solve_read(q, ctx, kernel):
+    """Block sharding: two disjoint block subsets (split by cost), solved separately and
+    merged with qh_solution_set_block, give exactly the full solve and its phasing."""
+    fr = synth.batched_blocks(1004, n_blocks=7, n_min=40, n_max=420)
+    _block_subset_case(q, ctx, fr, q.MODE_READ, replicas=128, steps=300, precision=q.PREC_BF16,
+                       seed=5, step_kernel=kernel)
+
+
+def test_block_subsets_combine_to_the_full_solve_snp(q, ctx):
+    fr = synth.batched_blocks(1004, n_blocks=5, n_min=30, n_max=200)
+    _block_subset_case(q, ctx, fr, q.MODE_SNP, replicas=32, steps=300, precision=q.PREC_FP32,
+                       seed=5, refine_max=4)
+
+
+def test_block_subset_arguments_checked(q, ctx):
+    fr = synth.batched_blocks(1004, n_blocks=3, n_min=40, n_max=100)
+    g = ctx.build_graph(fr)
+    for bad in ([0, 0], [g.n_blocks], [-1]):
+        with pytest.raises(q.QhError) as e:
+            ctx.solve(g, replicas=64, steps=10, precision=q.PREC_BF16, blocks=bad)
+        assert e.value.status == q.QH_EINVAL
+    empty = ctx.solve(g, replicas=64, steps=10, precision=q.PREC_BF16, blocks=[])
+    _, _, bid = ctx.phase(g, empty, fr.n_snps)
+    assert np.all(bid == -1)
+    with pytest.raises(q.QhError):
+        empty.set_block(0, np.zeros(g.block_sizes()[0], np.int8), 1.0, 0, 10, 1)  # spins 0

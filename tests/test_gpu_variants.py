@@ -97,13 +97,15 @@ def test_variant_solve_vs_oracle(q, ctx, oracle, variant, precision, kernel, sto
                     variant=variant, step_kernel=kernel)
     og = oracle.read_graph(fr, oracle.READ_SIGNED)
     spins = sol.spins(g.n_nodes)
+    cuts = sol.cuts()
     for b, nodes in enumerate(oracle.blocks_of(og)):
         sub = og.subgraph(nodes)
         info = sol.block(b, len(nodes))
         assert info["best_cut"] == oracle.cut(sub, spins[nodes])
         best, _, _, _ = oracle.bsb_solve(sub, list(range(16)), 800, 7, b, dt=DT[variant],
                                          variant=variant)
-        assert info["best_cut"] >= 0.999 * best, (b, info["best_cut"], best)
+        same = cuts[b][:16].max()  # the GPU's best over the oracle's 16 replicas
+        assert same >= 0.999 * best, (b, same, best)
 
 
 def test_variant_value_validated(q, ctx):
@@ -155,8 +157,11 @@ def test_variant_snp_refinement_csr_vs_tiles(q, ctx, oracle, variant):
     against the oracle's refinement with the same variant, seed and replica indices:
     the first solve's best cut >= 0.999 x the oracle's; the final partition's cut
     >= 0.999 x the oracle's for dSB.  aSB runs at dt 0.25 (at 0.5 it collapses on SNP
-    graphs) and its refined cut varies by a few per cent between replica sets (oracle,
-    four sets of 64: 491 .. 507), so its bar there is 0.97."""
+    graphs).  Its refined cut is held to 0.97: every later solve runs on the graph gauged
+    by the previous partition, so one replica whose FP32 trajectory ends on another
+    partition than its FP64 twin changes every later solve's input, and aSB's refined
+    cut spreads by a few per cent over such changes (oracle, four replica sets of 64:
+    491 .. 507).  The first solve, on the ungauged graph, keeps the 0.999 bar."""
     fr = synth.region_reads(33, n_snps=400, region=150_000, n_reads=90, len_mean=9000,
                             len_sd=3000, flip_p=0.08, miss_p=0.0, qual=(7, 30))
     dt = {"discrete": 1.0, "adiabatic": 0.25}[variant]
