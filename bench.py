@@ -12,7 +12,9 @@ host memory and haplotypes + cut copied back inside the timed region.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
                        [--impl ours|reference]
-Under torchrun each rank runs its own replica range (replica_base = rank * R): weak scaling.
+Under torchrun each rank runs its own replica range (replica_base = rank * R, weak scaling)
+and the per-block best is combined across ranks; --shard blocks splits the phase blocks
+by cost instead (strong scaling).
 """
 from __future__ import annotations
 
@@ -30,10 +32,25 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-SPIN_BYTES = 16 + 2  # FP32 x, y read + write, BF16 X_hat write, per spin update
-# multi-step kernels hold y on chip for a whole launch: x read + write, X_hat write per
-# spin update, and y read + written once per launch
-SPIN_BYTES_MULTISTEP = 8 + 2
+
+
+def spin_update_work(deg, R, j_bytes):
+    """Algorithmic work of one spin update (one vertex, one replica, one step), the
+    measurement plan's model whatever a kernel keeps on chip:
+      bytes = 16 (x, y FP32 read + write) + 2 (X_hat BF16 write) + deg * j_bytes / R
+              (J streamed once per step, amortised over the R replicas)
+      flops = 2 deg
+    deg = stored J entries per vertex, j_bytes = bytes per stored entry."""
+    return 16.0 + 2.0 + deg * j_bytes / R, 2.0 * deg
+
+
+def kernel_bound(kernel):
+    """What binds a step kernel, from its ncu captures: the multi-step and band-tile
+    kernels keep the state in L2 / TMEM and wait on latency (hand-offs, gathers), the
+    FP32 SIMT step is bound by FP32 arithmetic on the tiles."""
+    if kernel == "k_step_f32":
+        return "alu"
+    return "latency"
 
 
 def _peaks():
@@ -196,9 +213,10 @@ def cpu_baseline(args, fr, mode, steps, seed=1, reps=None):
             "sample": f"{what}, {reps} replicas x {steps} steps, whole path, {dt:.1f} s"}, res
 
 
-def _profiled_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, or None once the kernel
-    (its variant or its source file) differs from the one that was profiled."""
+def _profiled(kernel):
+    """DRAM bytes per launch and the utilisation counters from the committed ncu summary
+    of the kernel, or None once the kernel (its variant or its source file) differs from
+    the one that was profiled."""
     import hashlib
     multistep = kernel.startswith("multistep")
     path = os.path.join(ROOT, "profiles", "multistep_kernel_hifi_region.md" if multistep
@@ -208,15 +226,21 @@ def _profiled_traffic(kernel):
     if not os.path.exists(path):
         return None
     fields = {}
+    keys = ("traffic_bytes_per_launch", "kernel", "source_sha256_16", "tensor_pipe_pct",
+            "l2_throughput_pct", "dram_throughput_pct", "issue_active_pct")
     for line in open(path):
-        if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch", "kernel",
-                                                   "source_sha256_16"):
+        if ":" in line and line.split(":")[0] in keys:
             k, v = line.split(":", 1)
             fields[k.strip()] = v.strip()
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if fields.get("kernel") != kernel or fields.get("source_sha256_16") != sha:
         return None
-    return int(fields["traffic_bytes_per_launch"])
+    out = {"traffic": int(fields["traffic_bytes_per_launch"]),
+           "profile": os.path.relpath(path, ROOT)}
+    for k in keys[3:]:
+        if k in fields:
+            out[k] = float(fields[k])
+    return out
 
 
 def run_reference(args):
@@ -246,31 +270,6 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
-def _count_kernels(fn):
-    """Kernel launches of one call, from the CUDA activity trace (torch.profiler)."""
-    try:
-        import torch
-        from torch.profiler import ProfilerActivity, profile
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
-            fn()
-            torch.cuda.synchronize()
-        # this library's kernels live in namespace qh: demangled "qh::", mangled "_ZN2qh"
-        n, names = 0, set()
-        for ev in prof.events():
-            if ev.device_type.name != "CUDA":
-                continue
-            names.add(ev.name[:60])
-            if "qh::" in ev.name or "_ZN2qh" in ev.name:
-                n += 1
-        if n == 0:
-            print(f"kernel count: no kernel of this library in the trace ({len(names)} names, "
-                  f"e.g. {sorted(names)[:3]})", file=sys.stderr)
-        return n if n > 0 else None
-    except Exception as e:  # the activity trace is optional: report why it is missing
-        print(f"kernel count unavailable: {e!r}", file=sys.stderr)
-        return None
 
 
 def run_ours(args):
@@ -314,11 +313,18 @@ def run_ours(args):
         else:
             g = ctx.build_graph(arrays=arrays_dev, on_device=True, mode=gmode, linkage_k=args.linkage_k)
         stats["build_ms"] = (time.perf_counter() - t0) * 1e3
-        sol = ctx.solve(g, replicas=R, steps=T, precision=p, seed=1, replica_base=base,
-                        step_kernel=args.step_kernel if p == prec else None,
-                        refine_max=args.refine_max,
-                        variant=args.variant, dt=0.1 if args.variant == "adiabatic" else 1.0,
-                        deform_h=args.deform_h, deform_tries=args.deform_tries)
+        kw = dict(replicas=R, steps=T, precision=p, seed=1,
+                  step_kernel=args.step_kernel if p == prec else None,
+                  refine_max=args.refine_max,
+                  variant=args.variant, dt=0.1 if args.variant == "adiabatic" else 1.0,
+                  deform_h=args.deform_h, deform_tries=args.deform_tries)
+        if ws > 1 and args.shard == "blocks":
+            # this rank's share of the blocks by cost, then the per-block exchange
+            sol = multi.solve_blocks_sharded(ctx, g, rank, ws, **kw)
+        else:
+            sol = ctx.solve(g, replica_base=base, **kw)
+            if ws > 1:  # replica shards: every block takes the best rank's result
+                multi.combine_replica_shards(sol, g)
         if host:
             h = ctx.phase(g, sol, fr.n_snps)
             cut = sol.block(0)["best_cut"] if g.n_blocks else 0.0
@@ -331,11 +337,18 @@ def run_ours(args):
         stats["units"] = sol.timing()["spin_updates"]
         stats["nnz"] = g.nnz
         if collect:
+            from paper_2603_25762_gb300 import metrics
             bs = g.block_sizes()
             info = [sol.block(b) for b in range(g.n_blocks)]
             stats["spins"] = float(sum(bs)) * R  # spin states updated per step
-            stats["spin_solves"] = float(sum(n * i["iterations"] for n, i in zip(bs, info))) * R
+            stats["in_blocks"] = float(sum(bs))
             stats["best_cut_sum"] = float(sum(i["best_cut"] for i in info))
+            # the cut of the generator's true partition on the same graph (reads: each
+            # read's haplotype; SNPs: the true haplotype), for the solver's gap to it
+            truth = fr.meta.get("read_hap") if mode == "read" else fr.truth
+            if truth is not None and not host:
+                rp, col, w = g.edges()
+                stats["truth_cut"] = metrics.partition_cut(rp, col, w, truth)
         sol.free()
         g.free()
         return h, cut
@@ -348,7 +361,10 @@ def run_ours(args):
             hap1, bid = hap1.cpu().numpy(), bid.cpu().numpy()
         se, he = metrics.switch_hamming(hap1, bid, fr.truth)
         bid_ph = np.where(hap1 != 0, bid, -1)
-        return {"best_cut_sum": stats["best_cut_sum"], "switch_error": se, "hamming_error": he,
+        tc = stats.get("truth_cut")
+        return {"best_cut_sum": stats["best_cut_sum"], "truth_cut": tc,
+                "best_over_truth": stats["best_cut_sum"] / tc if tc else None,
+                "switch_error": se, "hamming_error": he,
                 "n50_bp": metrics.n50(metrics.block_spans(bid_ph, fr.positions)),
                 "phased_fraction": metrics.completeness(hap1)}
 
@@ -391,7 +407,6 @@ def run_ours(args):
             t0 = time.perf_counter()
             one_step(host=True, pinned=pinned_np)
             e2e.append((time.perf_counter() - t0) * 1e3)
-        n_kern = _count_kernels(lambda: one_step())  # cross-check from the CUDA activity trace
         qual = quality(h_last)
         # the same path with the plain FP32 SIMT step on the same GPU: the speedup of the
         # low-precision path at equal best cut
@@ -417,9 +432,12 @@ def run_ours(args):
             stats.update(saved)
     ms = statistics.mean(times)
     e2e_ms = statistics.mean(e2e)
+    units_all = units * ws
     if ws > 1:  # the job's time is the slowest rank's
         ms = multi.max_over_ranks(ms)
         e2e_ms = multi.max_over_ranks(e2e_ms)
+        if args.shard == "blocks":  # each rank ran its own blocks
+            units_all = multi.sum_over_ranks(units)
         if vs_fp32 is not None:
             vs_fp32["fp32_ms_per_step"] = multi.max_over_ranks(vs_fp32["fp32_ms_per_step"])
     if rank != 0:
@@ -429,43 +447,46 @@ def run_ours(args):
         c32 = vs_fp32["fp32_quality"]["best_cut_sum"]
         vs_fp32["cut_ratio"] = qual["best_cut_sum"] / c32 if c32 else None
     hbm, bf16_tf, src = _peaks()
-    launch_us = statistics.mean(step_ms) * 1e3
-    # algorithmic bytes of the whole step loop: state traffic per spin update + each
-    # stored J nonzero read once per step (BF16: 2 B, FP32: 4 B); a multi-step launch
-    # also reads and writes y once (8 B per spin).  Divided by the step loop's time.
+    # Roofline of the dominant kernel, the step kernel: the measurement plan's work per
+    # spin update (spin_update_work) times the spin updates of one launch, over that
+    # launch's average duration from the library's CUDA events on the bench's stream.
+    kname = stats["timing"]["kernel"]
     n_launch = max(1, stats["timing"]["n_step_launches"])
-    jb = stats["nnz"] * (4 if prec == qhap.PREC_FP32 else 2)
-    steps_total = units / max(1, stats["spins"])  # steps run, summed over refinements
-    if stats["timing"]["kernel"].startswith("multistep"):
-        loop_bytes = units * SPIN_BYTES_MULTISTEP + 8 * stats["spin_solves"] + jb * steps_total
-    else:
-        loop_bytes = units * SPIN_BYTES + jb * steps_total
-    loop_us = statistics.mean(step_ms) * 1e3 * n_launch
-    achieved = loop_bytes / (loop_us * 1e-6) / 1e9
-    per_launch_bytes = loop_bytes / n_launch
-    traffic = _profiled_traffic(stats["timing"]["kernel"]) if args.workload == "hifi-region" else None
+    launch_us = statistics.mean(step_ms) * 1e3
+    deg = stats["nnz"] / max(1.0, stats["in_blocks"])  # stored J entries per vertex
+    b_unit, f_unit = spin_update_work(deg, R, 4 if prec == qhap.PREC_FP32 else 2)
+    per_launch = units / n_launch  # spin updates of one launch
+    achieved = per_launch * b_unit / (launch_us * 1e-6) / 1e9
+    achieved_tf = per_launch * f_unit / (launch_us * 1e-6) / 1e12
+    prof = _profiled(kname) if args.workload == "hifi-region" else None
     h2d = sum(int(a.nbytes) for a in pinned_np[1:])
     d2h = fr.n_snps * (1 + 1 + 4) + 8
     line = {
-        "metric": "bSB spin-updates/s", "value": units * ws / (ms / 1e3),
+        "metric": "bSB spin-updates/s", "value": units_all / (ms / 1e3),
         "unit": "spin-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if ws > 1 and args.shard == "blocks" else "weak",
+        "vs_baseline": None,
         "dtype": args.precision, "data": "synthetic", "config": cfg,
         "phasing_wall_ms": ms,
         "breakdown_ms": {k: round(statistics.mean(v), 3) for k, v in parts.items()},
-        "e2e": {"value": units * ws / (e2e_ms / 1e3), "unit": "spin-updates/s",
+        "e2e": {"value": units_all / (e2e_ms / 1e3), "unit": "spin-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-        "roofline": {"bound": "hbm", "kernel": stats["timing"]["kernel"],
+        "roofline": {"bound": kernel_bound(kname), "kernel": kname,
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": traffic,
-                     "peak_source": src, "avg_launch_us": launch_us,
-                     "launches_per_step": n_launch,
-                     "avg_step_us": loop_us / steps_total,
-                     "algorithmic_bytes_per_launch": per_launch_bytes},
+                     "frac": achieved / hbm, "peak_source": f"{src} HBM copy",
+                     "traffic": prof["traffic"] if prof else None,
+                     "model": "16 + 2 + deg * b_J / R bytes and 2 deg flops per spin update",
+                     "deg": deg, "bytes_per_spin_update": b_unit,
+                     "algorithmic_bytes_per_launch": per_launch * b_unit,
+                     "avg_launch_us": launch_us, "launches_per_step": n_launch,
+                     "tensor": {"achieved": achieved_tf, "peak": bf16_tf, "unit": "TFLOP/s",
+                                "frac": achieved_tf / bf16_tf,
+                                "peak_source": f"{src} BF16 dense burst"},
+                     "ncu": prof},
         "quality": qual,
         "vs_fp32": vs_fp32,
         "gpu_launches": n_launched,
-        "gpu_launches_trace_per_step": n_kern,
         "clocks": clk.summary(),
         "step_kernel_tuning": ctx.tuning_report(),
     }
@@ -494,7 +515,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-leg", action="store_true",
                     help="skip timing the same path with the FP32 SIMT step")
-    ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--fp32-steps", type=int, default=3)
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "blocks"],
+                    help="under torchrun: each rank a replica range (weak scaling) or a "
+                         "cost-balanced share of the phase blocks (strong scaling)")
     ap.add_argument("--variant", default="ballistic", choices=["ballistic", "discrete", "adiabatic"],
                     help="simulated-bifurcation variant (the paper's solver is ballistic)")
     ap.add_argument("--linkage-k", type=int, default=10, help="SNP graphs: linkage depth k/10")

@@ -1,10 +1,13 @@
 // J x X product on the BF16 tensor cores for callers that must not allocate device
-// memory (see qh_matvec_bf16_noalloc in qhap.h).
+// memory: hosts whose own allocator already owns the GPU's memory, or processes held
+// to a fixed device-memory budget (see qh_matvec_bf16_noalloc in qhap.h).
 //
 // The only working memory beyond the caller's input and output is the BF16 copy of
 // X and two small per-block parameter arrays.  Instead of coming from cudaMalloc or
 // the context's grow-on-demand buffers, they live in the file-scope array below,
-// which every GPU that loads this library holds until the process exits.
+// which every GPU that loads this library holds until the process exits.  Its device
+// address is looked up once per device and kept for the life of the process, so the
+// library must not be used across a cudaDeviceReset of that device.
 #include <mutex>
 
 #include "qh_internal.cuh"

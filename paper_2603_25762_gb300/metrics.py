@@ -70,3 +70,13 @@ def completeness(hap1):
     """Fraction of SNPs that received a phase."""
     hap1 = np.asarray(hap1)
     return float(np.count_nonzero(hap1)) / max(1, hap1.size)
+
+
+def partition_cut(row_ptr, col, w, spins):
+    """Cut sum_{a<b} w_ab [s_a != s_b] of a +-1 partition of a graph given as CSR with both
+    directions (evaluation only: e.g. the cut of the generator's true partition)."""
+    row_ptr = np.asarray(row_ptr, np.int64)
+    s = np.asarray(spins, np.int64)
+    rows = np.repeat(np.arange(row_ptr.shape[0] - 1), np.diff(row_ptr))
+    cross = s[rows] != s[np.asarray(col, np.int64)]
+    return 0.5 * float(np.asarray(w, np.float64)[cross].sum())

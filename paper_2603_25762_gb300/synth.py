@@ -72,8 +72,10 @@ def _emit(rng, n_snps, lo, hi, hap_sign, truth, flip_p, miss_p, qual_lo, qual_hi
 
 
 def reads_on_positions(rng, positions, truth, n_reads, region, len_mean, len_sd,
-                       len_max=None, flip_p=0.01, miss_p=0.0, qual=(20, 40)):
-    """Long reads with lognormal lengths placed uniformly on [0, region - len]."""
+                       len_max=None, flip_p=0.01, miss_p=0.0, qual=(20, 40), info=None):
+    """Long reads with lognormal lengths placed uniformly on [0, region - len].
+    info (a dict, if given) receives "hap": each read's haplotype (+1 = truth, -1 = its
+    complement), in the returned read order."""
     mu, sig = _lognormal_params(len_mean, len_sd)
     lens = rng.lognormal(mu, sig, size=n_reads)
     if len_max is not None:
@@ -88,6 +90,8 @@ def reads_on_positions(rng, positions, truth, n_reads, region, len_mean, len_sd,
     hap = np.where(rng.random(n_reads) < 0.5, 1, -1).astype(np.int8)
     ptr, snp, allele, q = _emit(rng, positions.shape[0], lo, hi, hap, truth,
                                 flip_p, miss_p, qual[0], qual[1])
+    if info is not None:
+        info["hap"] = hap
     return ptr, snp, allele, q
 
 
@@ -120,7 +124,8 @@ def tiny_reads(seed=1001, n_snps=300, n_reads=80, len_lo=10, len_hi=30, flip_p=0
     ptr, snp, allele, q = _emit(rng, n_snps, lo, hi, hap, truth, flip_p, miss_p, qual[0], qual[1])
     return Fragments(n_snps, ptr, snp, allele, q, np.zeros(n_reads, np.uint8),
                      np.arange(n_snps, dtype=np.int64), truth,
-                     {"workload": "tiny-reads", "seed": seed, "n_reads": n_reads})
+                     {"workload": "tiny-reads", "seed": seed, "n_reads": n_reads,
+                      "read_hap": hap})
 
 
 def region_reads(seed, n_snps=12000, region=4_000_000, n_reads=7200, len_mean=15_000,
@@ -130,11 +135,12 @@ def region_reads(seed, n_snps=12000, region=4_000_000, n_reads=7200, len_mean=15
     rng = np.random.Generator(np.random.PCG64(seed))
     positions = np.sort(rng.choice(region, size=n_snps, replace=False)).astype(np.int64)
     truth = np.where(rng.random(n_snps) < 0.5, 1, -1).astype(np.int8)
+    info = {}
     ptr, snp, allele, q = reads_on_positions(rng, positions, truth, n_reads, region, len_mean,
-                                             len_sd, len_max, flip_p, miss_p, qual)
+                                             len_sd, len_max, flip_p, miss_p, qual, info)
     return Fragments(n_snps, ptr, snp, allele, q, np.zeros(n_reads, np.uint8), positions,
                      truth, {"workload": name, "seed": seed, "n_reads": n_reads,
-                             "region_bp": region})
+                             "region_bp": region, "read_hap": info["hap"]})
 
 
 def hifi_region(seed=1002, scale=1.0):
@@ -161,7 +167,7 @@ def batched_blocks(seed=1004, n_blocks=512, n_min=50, n_max=6000, gap=1_000_000,
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     sizes = np.rint(np.exp(rng.uniform(np.log(n_min), np.log(n_max), size=n_blocks))).astype(int)
-    parts, positions, truths = [], [], []
+    parts, positions, truths, haps = [], [], [], []
     snp_base, bp_base = 0, 0
     for b, nb in enumerate(sizes):
         brng = np.random.Generator(np.random.PCG64(40000 + b))
@@ -169,8 +175,10 @@ def batched_blocks(seed=1004, n_blocks=512, n_min=50, n_max=6000, gap=1_000_000,
         ns = max(2, int(round(region * snp_per_kb / 1000)))
         pos = np.sort(brng.choice(region, size=ns, replace=False)).astype(np.int64)
         tr = np.where(brng.random(ns) < 0.5, 1, -1).astype(np.int8)
+        info = {}
         ptr, snp, allele, q = reads_on_positions(brng, pos, tr, int(nb), region, 15_000, 5_000,
-                                                 None, 0.01, 0.02, (20, 40))
+                                                 None, 0.01, 0.02, (20, 40), info)
+        haps.append(info["hap"])
         parts.append((ptr, snp + snp_base, allele, q, 0))
         positions.append(pos + bp_base)
         truths.append(tr)
@@ -179,7 +187,8 @@ def batched_blocks(seed=1004, n_blocks=512, n_min=50, n_max=6000, gap=1_000_000,
     ptr, snp, allele, q, pc = _concat(parts, snp_base)
     return Fragments(snp_base, ptr, snp, allele, q, pc, np.concatenate(positions),
                      np.concatenate(truths), {"workload": "batched-blocks", "seed": seed,
-                                              "block_reads": sizes.tolist()})
+                                              "block_reads": sizes.tolist(),
+                                              "read_hap": np.concatenate(haps)})
 
 
 def porec_contacts(rng, positions, truth, n_contacts, k_lo=2, k_hi=6, d_lo=100_000,

@@ -59,9 +59,20 @@ def test_profiled_traffic_tracks_kernel_source(bench, tmp_path, monkeypatch):
     sha = hashlib.sha256(b"// kernel v1\n").hexdigest()[:16]
     (prof / "multistep_kernel_hifi_region.md").write_text(
         f"kernel: multistep-stream-tile\nsource_sha256_16: {sha}\n"
-        "traffic_bytes_per_launch: 1234\n")
+        "traffic_bytes_per_launch: 1234\ntensor_pipe_pct: 17.5\nl2_throughput_pct: 40.25\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench._profiled_traffic("multistep-stream-tile") == 1234
-    assert bench._profiled_traffic("multistep-jres-group") is None  # another variant
+    got = bench._profiled("multistep-stream-tile")
+    assert got["traffic"] == 1234
+    assert got["tensor_pipe_pct"] == 17.5 and got["l2_throughput_pct"] == 40.25
+    assert "dram_throughput_pct" not in got
+    assert bench._profiled("multistep-jres-group") is None  # another variant
     (src / "bsb_run.cu").write_text("// kernel v2\n")
-    assert bench._profiled_traffic("multistep-stream-tile") is None  # source changed
+    assert bench._profiled("multistep-stream-tile") is None  # source changed
+
+
+def test_spin_update_work_follows_the_measurement_model(bench):
+    # 16 B of x, y, 2 B of X_hat, J once per step over R replicas; 2 flops per entry
+    b, f = bench.spin_update_work(52.8, 1024, 2)
+    assert b == pytest.approx(18.0 + 52.8 * 2 / 1024) and f == pytest.approx(105.6)
+    assert bench.kernel_bound("k_step_f32") == "alu"
+    assert bench.kernel_bound("multistep-stream-tile") == "latency"
