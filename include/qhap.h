@@ -379,6 +379,24 @@ qh_status qh_debug_fail_alloc(qh_ctx* ctx, int64_t after);
 qh_status qh_debug_init_state(qh_ctx* ctx, const qh_graph* g, int32_t R, int32_t replica_base,
                               uint64_t seed, int32_t iter, float* x, float* y);
 
+/* Step timeline of the multi-step kernel (tracing hook, not part of the paper's
+ * method).  Runs steps 0 .. steps-1 of bSB (BF16, seed 1, default c0, dt = a0 = 1) as
+ * ONE launch of multi-step variant `step_kernel` (6..9) with R replicas, and records
+ * for the steps u0 .. u0+nu-1 of every CTA and item slot the hand-off points of its
+ * pipeline: [0] inputs released, [1] last operand load issued, [2] accumulator free,
+ * [3] first operand landed, [4] MMAs committed, [5] epilogue start, [6] epilogue end,
+ * [7] X_hat released, [8] producer reaches the item, [9] its own previous step is
+ * released, [10] its first ring slot is free.  stamps (host) uint64[n_ctas][nu][4][24]:
+ * columns 0..11 the events as global-timer nanoseconds, 12..23 the same events as SM
+ * clock cycles (0 = event not reached or not recorded).
+ * items (host, may be NULL) int32[n_ctas][4]: the item (row tile * R/128 + replica
+ * tile) of each slot, -1 for none.  stamps = NULL only returns n_ctas.
+ * Errors: QH_EINVAL (not a multi-step variant for this graph, or more than one wave),
+ * QH_ENOMEM, QH_ECUDA, QH_ETIMEOUT. */
+qh_status qh_debug_run_trace(qh_ctx* ctx, const qh_graph* g, int32_t R, int32_t step_kernel,
+                             int32_t steps, int32_t u0, int32_t nu, uint64_t* stamps,
+                             int32_t* items, int32_t* n_ctas);
+
 /* Padded layout: n_pad and padded_index int32[n_nodes] (-1 for vertices in no
  * block): vertex v of block b sits at padded column pad_off[b] + local[v]. */
 qh_status qh_debug_layout(qh_ctx* ctx, const qh_graph* g, int32_t* n_pad, int32_t* padded_index,

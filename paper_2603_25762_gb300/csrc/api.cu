@@ -93,7 +93,7 @@ enum {
   S_STEPSB, S_C0, S_SEEN, S_STALL, S_STEPSRUN, S_SPINS, S_C, S_WWORK, S_TBWORK, S_TFWORK,
   S_SUMW, S_SUMJ2, S_NODETMP, S_SIGNS1, S_NODEVAL1, S_CUT1, S_DBG0, S_DBG1, S_DBG2, S_RUNNING,
   S_PVWORK, S_TR0, S_TR1, S_F8H, S_F8L, S_F8FLAG, S_X8, S_DEFORM, S_TRIES, S_DBGDEF,
-  S_ZBAND, S_BANDWORK, S_RVWORK
+  S_ZBAND, S_BANDWORK, S_RVWORK, S_TRACE
 };
 
 struct SolveBufs {
@@ -185,16 +185,6 @@ bool tuned_variant(Ctx* ctx, const Graph& g, int R, int sb, TcPlan* plan) {
       return true;
     }
   return false;
-}
-
-// The multi-step kernel keeps y / (dt c0) on chip: every block's dt * c0 must be a
-// normal float with a finite reciprocal.
-bool run_c0_ok(const float* c0, int32_t nb, float dt) {
-  for (int32_t b = 0; b < nb; ++b) {
-    const float d = dt * c0[b];
-    if (!std::isnormal(d) || !std::isfinite(1.0f / d)) return false;
-  }
-  return true;
 }
 
 qh_status autotune(Ctx* ctx, const Graph& g, StepArgs a, const SolveBufs& B, int R, TcPlan* plan,
@@ -740,7 +730,7 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
         launch_init_state(s, W, R, o->replica_base, o->seed, 0, B.x, B.y, B.xh0, B.active,
                           o->sb_variant);
         QH_STAGE_CHECK("solve: state init (tuning)");
-        st = autotune(ctx, W, a, B, R, &tplan, run_c0_ok(h_c0.data(), nb, a.dt));
+        st = autotune(ctx, W, a, B, R, &tplan, true);
       }
     }
     if (st != QH_OK) return st;
@@ -753,9 +743,6 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
   // the multi-step kernel runs whole step ranges: a few direct launches, no capture
   const bool multistep = is_tc_precision(o->precision) && !G.csr_mode && run_variant(tplan.variant);
   RunBufs rb;
-  if (multistep && !run_c0_ok(h_c0.data(), nb, a.dt)) {
-    return set_err(ctx, QH_EINVAL, "multi-step kernel needs dt * c0 to be a normal float in every block");
-  }
   if (multistep) {
     qh_status st = run_prepare(ctx, W, R, tplan.variant, a.use_lo != 0, &rb,
                                sel ? &sel_mask : nullptr);
@@ -1222,6 +1209,79 @@ static qh_status debug_common(Ctx* ctx, const Graph& g, int precision, int32_t R
   return QH_OK;
 }
 
+qh_status qh_debug_run_trace(qh_ctx* h, const qh_graph* gh, int32_t R, int32_t step_kernel,
+                             int32_t steps, int32_t u0, int32_t nu, uint64_t* stamps,
+                             int32_t* items, int32_t* n_ctas) {
+  if (!h) return QH_EINVAL;
+  Ctx* ctx = &h->c;
+  ctx->err.clear();
+  clear_foreign_error(ctx);
+  if (!gh || !n_ctas) return set_err(ctx, QH_EINVAL, "NULL argument");
+  const Graph& g = gh->g;
+  if (steps < 1 || u0 < 0 || nu < 1 || u0 + nu > steps)
+    return set_err(ctx, QH_EINVAL, "steps >= 1 and 0 <= u0 < u0 + nu <= steps required");
+  const bool use_lo = use_lo_for(g, QH_PREC_BF16) != 0;
+  if (!run_variant(step_kernel) || !tc_variant_ok(step_kernel, g, R, ctx->n_sm, use_lo))
+    return set_err(ctx, QH_EINVAL, "step_kernel must be a multi-step variant valid for this graph");
+  RunPlan plan;
+  if (!run_plan(g, R, ctx->n_sm, step_kernel, use_lo, &plan) || plan.waves.size() != 1)
+    return set_err(ctx, QH_EINVAL, "the traced launch must be a single wave");
+  const RunWave& w = plan.waves[0];
+  *n_ctas = w.grid;
+  if (!stamps) return QH_OK;
+  const int EV = run_trace_events(), MI = run_max_items();
+  constexpr int SLOTS = 4, COLS = 24;  // item slots per CTA, stamps per slot in the caller's arrays
+  if (2 * EV > COLS) return set_err(ctx, QH_EUNSUPPORTED, "more trace events than the layout holds");
+  if (MI > SLOTS) return set_err(ctx, QH_EUNSUPPORTED, "more item slots than the trace layout holds");
+  if (items)
+    for (int c = 0; c < w.grid; ++c) {
+      const int2 wk = plan.work[w.work_off + c];
+      for (int j = 0; j < SLOTS; ++j)
+        items[c * SLOTS + j] =
+            j < std::min(wk.y, MI) ? plan.items[w.item_off + wk.x + j * w.stride] : -1;
+    }
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = ctx->stream;
+  StepArgs a;
+  qh_status st = debug_common(ctx, g, QH_PREC_BF16, R, a, nullptr, steps);
+  if (st) return st;
+  const size_t NS = (size_t)R * g.n_pad;
+  const size_t n_stamps = (size_t)w.grid * nu * MI * 2 * EV;
+  float* x = (float*)ctx->scratch(NS * 4, S_X);
+  float* y = (float*)ctx->scratch(NS * 4, S_Y);
+  __nv_bfloat16* xh0 = (__nv_bfloat16*)ctx->scratch(NS * 2, S_XH0);
+  __nv_bfloat16* xh1 = (__nv_bfloat16*)ctx->scratch(NS * 2, S_XH1);
+  unsigned long long* tr = (unsigned long long*)ctx->scratch(n_stamps * 8, S_TRACE);
+  if (!x || !y || !xh0 || !xh1 || !tr) return set_err(ctx, QH_ENOMEM, "allocation failed (trace)");
+  a.x = x;
+  a.y = y;
+  a.dt = 1.f;
+  a.a0 = 1.0;
+  a.dta0 = 1.f;
+  a.sb = QH_SB_BALLISTIC;
+  QH_CUDA_TRY(cudaMemsetAsync(xh1, 0, NS * 2, s));
+  QH_CUDA_TRY(cudaMemsetAsync(tr, 0, n_stamps * 8, s));
+  launch_init_state(s, g, R, 0, 1, 0, x, y, xh0, nullptr);
+  RunBufs rb;
+  st = run_prepare(ctx, g, R, step_kernel, use_lo, &rb);
+  if (st) return st;
+  st = launch_run(ctx, g, a, rb, xh0, xh1, 0, steps, tr, u0, nu);
+  if (st) return st;
+  QH_STAGE_CHECK("debug: traced multi-step launch");
+  std::vector<unsigned long long> hs(n_stamps);
+  QH_CUDA_TRY(cudaMemcpyAsync(hs.data(), tr, n_stamps * 8, cudaMemcpyDeviceToHost, s));
+  QH_CUDA_TRY(cudaStreamSynchronize(s));
+  // [cta][step][MI][EV global, EV clock] -> [cta][step][SLOTS][12 global, 12 clock]
+  memset(stamps, 0, (size_t)w.grid * nu * SLOTS * COLS * 8);
+  for (size_t cs = 0; cs < (size_t)w.grid * nu; ++cs)
+    for (int j = 0; j < MI; ++j)
+      for (int e = 0; e < EV; ++e) {
+        stamps[(cs * SLOTS + j) * COLS + e] = hs[(cs * MI + j) * 2 * EV + e];
+        stamps[(cs * SLOTS + j) * COLS + COLS / 2 + e] = hs[(cs * MI + j) * 2 * EV + EV + e];
+      }
+  return check_err_word(ctx);
+}
+
 qh_status qh_debug_matvec(qh_ctx* h, const qh_graph* gh, int32_t precision, int32_t R, const float* x,
                           float* z) {
   if (!h || !gh || !x || !z) return QH_EINVAL;
@@ -1335,8 +1395,6 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
     if (!is_tc_precision(precision) || g.csr_mode || step_kernel >= tc_n_variants() ||
         !tc_variant_ok(step_kernel, g, R, ctx->n_sm, a.use_lo != 0))
       return set_err(ctx, QH_EINVAL, "step_kernel variant not valid for this graph, precision and R");
-    if (run_variant(step_kernel) && !run_c0_ok(c0h.data(), g.n_blocks, (float)dt))
-      return set_err(ctx, QH_EINVAL, "multi-step kernel needs dt * c0 to be a normal float in every block");
   }
   a.x = x;
   a.y = y;

@@ -397,8 +397,14 @@ qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo,
                       const std::vector<int32_t>* mask = nullptr);
 // Steps t0 .. t1-1 in one launch.  X_hat_t is read from xh0 (t even) or xh1 (t odd);
 // x, y of `s` are updated in place.
+// trace (test hook, else nullptr): step-timeline stamps of steps trace_u0 ..
+// trace_u0 + trace_nu - 1 (relative to t0), run_trace_events() global-timer and as many
+// SM-clock stamps per (CTA, step, item slot of run_max_items()).
 qh_status launch_run(Ctx* ctx, const Graph& g, const StepArgs& s, const RunBufs& rb,
-                     __nv_bfloat16* xh0, __nv_bfloat16* xh1, int t0, int t1);
+                     __nv_bfloat16* xh0, __nv_bfloat16* xh1, int t0, int t1,
+                     unsigned long long* trace = nullptr, int trace_u0 = 0, int trace_nu = 0);
+int run_trace_events();
+int run_max_items();
 cudaError_t run_set_attrs();
 
 }  // namespace qh

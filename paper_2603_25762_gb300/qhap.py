@@ -104,6 +104,7 @@ _SIGS = {
     "qh_debug_steps_v": (C.c_int, [P, P, I32, I32, P, P, I32, I32, I32, D, D, P, I32, I32, P]),
     "qh_debug_layout": (C.c_int, [P, P, P, P, P]),
     "qh_debug_init_state": (C.c_int, [P, P, I32, I32, C.c_uint64, I32, P, P]),
+    "qh_debug_run_trace": (C.c_int, [P, P, I32, I32, I32, I32, I32, P, P, P]),
     "qh_matvec_bf16_noalloc": (C.c_int, [P, P, I32, P, P]),
     "qh_solution_kernel": (C.c_char_p, [P]),
     "qh_tuning_report": (C.c_char_p, [P]),
@@ -340,6 +341,19 @@ class Context:
         replica_base .. replica_base + R - 1 of refinement iteration `it`."""
         self._check(lib().qh_debug_init_state(self.h, g.h, R, replica_base, seed, it, _ptr(x),
                                               _ptr(y)))
+
+    def debug_run_trace(self, g, R, step_kernel, steps, u0, nu):
+        """Step timeline of one multi-step launch: (stamps uint64[n_ctas, nu, 4, 24],
+        items int32[n_ctas, 4]); see qh_debug_run_trace for the events."""
+        sk = STEP_KERNELS.index(step_kernel) if isinstance(step_kernel, str) else step_kernel
+        n = I32()
+        self._check(lib().qh_debug_run_trace(self.h, g.h, R, sk, steps, u0, nu, None, None,
+                                             C.byref(n)))
+        stamps = np.zeros((n.value, nu, 4, 24), np.uint64)
+        items = np.zeros((n.value, 4), np.int32)
+        self._check(lib().qh_debug_run_trace(self.h, g.h, R, sk, steps, u0, nu, _ptr(stamps),
+                                             _ptr(items), C.byref(n)))
+        return stamps, items
 
     def debug_wait_timeout(self, which=0):
         """Failure-detection hook: a bounded device wait that expires (raises QhError
