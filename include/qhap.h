@@ -386,9 +386,10 @@ qh_status qh_debug_init_state(qh_ctx* ctx, const qh_graph* g, int32_t R, int32_t
  * pipeline: [0] inputs released, [1] last operand load issued, [2] accumulator free,
  * [3] first operand landed, [4] MMAs committed, [5] epilogue start, [6] epilogue end,
  * [7] X_hat released, [8] producer reaches the item, [9] its own previous step is
- * released, [10] its first ring slot is free.  stamps (host) uint64[n_ctas][nu][4][24]:
- * columns 0..11 the events as global-timer nanoseconds, 12..23 the same events as SM
- * clock cycles (0 = event not reached or not recorded).
+ * released, [10] its first ring slot is free, [11..15] the ring slots of its K-slices
+ * 1..5 are free.  stamps (host) uint64[n_ctas][nu][4][32]: columns 0..15 the events as
+ * global-timer nanoseconds, 16..31 the same events as SM clock cycles (0 = event not
+ * reached or not recorded).
  * items (host, may be NULL) int32[n_ctas][4]: the item (row tile * R/128 + replica
  * tile) of each slot, -1 for none.  stamps = NULL only returns n_ctas.
  * Errors: QH_EINVAL (not a multi-step variant for this graph, or more than one wave),

@@ -187,6 +187,16 @@ bool tuned_variant(Ctx* ctx, const Graph& g, int R, int sb, TcPlan* plan) {
   return false;
 }
 
+// The multi-step kernel keeps y / (dt c0) on chip: every block's dt * c0 must be a
+// normal float with a finite reciprocal.
+bool run_c0_ok(const float* c0, int32_t nb, float dt) {
+  for (int32_t b = 0; b < nb; ++b) {
+    const float d = dt * c0[b];
+    if (!std::isnormal(d) || !std::isfinite(1.0f / d)) return false;
+  }
+  return true;
+}
+
 qh_status autotune(Ctx* ctx, const Graph& g, StepArgs a, const SolveBufs& B, int R, TcPlan* plan,
                    bool allow_run) {
   const std::string kb = tune_key(g, R, 0, a.sb);
@@ -730,7 +740,7 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
         launch_init_state(s, W, R, o->replica_base, o->seed, 0, B.x, B.y, B.xh0, B.active,
                           o->sb_variant);
         QH_STAGE_CHECK("solve: state init (tuning)");
-        st = autotune(ctx, W, a, B, R, &tplan, true);
+        st = autotune(ctx, W, a, B, R, &tplan, run_c0_ok(h_c0.data(), nb, a.dt));
       }
     }
     if (st != QH_OK) return st;
@@ -743,6 +753,9 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
   // the multi-step kernel runs whole step ranges: a few direct launches, no capture
   const bool multistep = is_tc_precision(o->precision) && !G.csr_mode && run_variant(tplan.variant);
   RunBufs rb;
+  if (multistep && !run_c0_ok(h_c0.data(), nb, a.dt)) {
+    return set_err(ctx, QH_EINVAL, "multi-step kernel needs dt * c0 to be a normal float in every block");
+  }
   if (multistep) {
     qh_status st = run_prepare(ctx, W, R, tplan.variant, a.use_lo != 0, &rb,
                                sel ? &sel_mask : nullptr);
@@ -1230,7 +1243,7 @@ qh_status qh_debug_run_trace(qh_ctx* h, const qh_graph* gh, int32_t R, int32_t s
   *n_ctas = w.grid;
   if (!stamps) return QH_OK;
   const int EV = run_trace_events(), MI = run_max_items();
-  constexpr int SLOTS = 4, COLS = 24;  // item slots per CTA, stamps per slot in the caller's arrays
+  constexpr int SLOTS = 4, COLS = 32;  // item slots per CTA, stamps per slot in the caller's arrays
   if (2 * EV > COLS) return set_err(ctx, QH_EUNSUPPORTED, "more trace events than the layout holds");
   if (MI > SLOTS) return set_err(ctx, QH_EUNSUPPORTED, "more item slots than the trace layout holds");
   if (items)
@@ -1238,7 +1251,8 @@ qh_status qh_debug_run_trace(qh_ctx* h, const qh_graph* gh, int32_t R, int32_t s
       const int2 wk = plan.work[w.work_off + c];
       for (int j = 0; j < SLOTS; ++j)
         items[c * SLOTS + j] =
-            j < std::min(wk.y, MI) ? plan.items[w.item_off + wk.x + j * w.stride] : -1;
+            j < std::min(wk.y, MI) ? plan.items[w.item_off + wk.x + j * w.stride] & run_item_mask()
+                                   : -1;
     }
   cudaSetDevice(ctx->device);
   cudaStream_t s = ctx->stream;
@@ -1253,6 +1267,10 @@ qh_status qh_debug_run_trace(qh_ctx* h, const qh_graph* gh, int32_t R, int32_t s
   __nv_bfloat16* xh1 = (__nv_bfloat16*)ctx->scratch(NS * 2, S_XH1);
   unsigned long long* tr = (unsigned long long*)ctx->scratch(n_stamps * 8, S_TRACE);
   if (!x || !y || !xh0 || !xh1 || !tr) return set_err(ctx, QH_ENOMEM, "allocation failed (trace)");
+  std::vector<float> c0h(std::max(g.n_blocks, 1));
+  for (int32_t b = 0; b < g.n_blocks; ++b) c0h[b] = (float)g.h_c0[b];
+  if (!run_c0_ok(c0h.data(), g.n_blocks, 1.f))
+    return set_err(ctx, QH_EINVAL, "multi-step kernel needs dt * c0 to be a normal float in every block");
   a.x = x;
   a.y = y;
   a.dt = 1.f;
@@ -1271,7 +1289,7 @@ qh_status qh_debug_run_trace(qh_ctx* h, const qh_graph* gh, int32_t R, int32_t s
   std::vector<unsigned long long> hs(n_stamps);
   QH_CUDA_TRY(cudaMemcpyAsync(hs.data(), tr, n_stamps * 8, cudaMemcpyDeviceToHost, s));
   QH_CUDA_TRY(cudaStreamSynchronize(s));
-  // [cta][step][MI][EV global, EV clock] -> [cta][step][SLOTS][12 global, 12 clock]
+  // [cta][step][MI][EV global, EV clock] -> [cta][step][SLOTS][16 global, 16 clock]
   memset(stamps, 0, (size_t)w.grid * nu * SLOTS * COLS * 8);
   for (size_t cs = 0; cs < (size_t)w.grid * nu; ++cs)
     for (int j = 0; j < MI; ++j)
@@ -1395,6 +1413,8 @@ qh_status qh_debug_steps_v(qh_ctx* h, const qh_graph* gh, int32_t precision, int
     if (!is_tc_precision(precision) || g.csr_mode || step_kernel >= tc_n_variants() ||
         !tc_variant_ok(step_kernel, g, R, ctx->n_sm, a.use_lo != 0))
       return set_err(ctx, QH_EINVAL, "step_kernel variant not valid for this graph, precision and R");
+    if (run_variant(step_kernel) && !run_c0_ok(c0h.data(), g.n_blocks, (float)dt))
+      return set_err(ctx, QH_EINVAL, "multi-step kernel needs dt * c0 to be a normal float in every block");
   }
   a.x = x;
   a.y = y;

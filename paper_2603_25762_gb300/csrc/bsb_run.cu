@@ -4,14 +4,13 @@
 //   |x| > 1 => x <- sgn(x), y <- 0,                       X_hat_{t+1} <- bf16(x)
 // with the momentum y held on chip for the whole launch.
 //
-// Work item = (128-row tile of J, 128 replicas).  A CTA owns up to three items and
-// gives each its own 128 TMEM columns, which hold the item's momentum y between steps:
-// y never leaves the SM between t0 and t1 (it is read from HBM before the first step
-// and written back after the last one), so per spin-update the state costs 4 + 4
-// bytes (x) + 2 bytes (X_hat) of memory traffic instead of 16 + 2.  The product
-// Z = J_hat X_hat of one item at a time goes to the fourth group of 128 columns: the
-// MMAs of the next item wait only until the epilogue has read the previous Z, not
-// for its whole update, so operand loads and MMAs run an item ahead of the epilogue.
+// Work item = (128-row tile of J, 128 replicas).  A CTA owns up to four items and
+// gives each its own 128 TMEM columns.  Those columns are the MMA accumulator and
+// hold y / (dt c0) between steps: every MMA accumulates J_hat X_hat onto it, so
+//   dt c0 * acc = y + dt c0 Z,   y_{t+1} = dt c0 * acc - dt (a0 - a(t)) x.
+// y therefore never leaves the SM between t0 and t1: it is read from HBM before the
+// first step and written back after the last one.  Per spin-update the state costs
+// 4 + 4 bytes (x) + 2 bytes (X_hat) of memory traffic instead of 16 + 2.
 //
 // Hand-off between steps, through release counters in global memory that a dedicated
 // warp releases (gpu scope) after each item's epilogue and the TMA producer acquires
@@ -44,8 +43,7 @@ namespace qh {
 namespace {
 
 constexpr int RB = 128;          // replicas per item (MMA N)
-constexpr int MAX_ITEMS = 3;     // 3 items' y + one product buffer: 4 x 128 TMEM columns
-constexpr uint32_t Z_COL = MAX_ITEMS * RB;  // TMEM column of the product buffer
+constexpr int MAX_ITEMS = 4;     // 4 items x 128 TMEM columns = 512
 constexpr int EPI_WARPS = 8;
 constexpr int RUN_THREADS = 32 * (3 + EPI_WARPS);
 constexpr int SIGNAL_WARP = 2 + EPI_WARPS;
@@ -57,8 +55,8 @@ struct ItemInfo {
   int32_t block, k, last_t, steps_b;    // last_t < t0: nothing to do this launch
   int32_t rt;                           // row tile index (= its column tile index)
   uint32_t rows_b;                      // row tiles of the block
-  float c0;                             // coupling scale of the block
-  float fh;                             // deformation field strength h (0: none)
+  float dtc0, inv_dtc0;                 // dt * c0 and its reciprocal
+  float dth;                            // dt * deformation field strength (0: none)
   double inv_steps;                     // 1 / steps_b
 };
 
@@ -68,9 +66,7 @@ struct RunSmem {
   static constexpr uint32_t SLOT = JRES ? SLICE : 2 * SLICE;    // X_hat (+ J) per slot
   static constexpr uint32_t RING_OFF = JRES ? JRES_TILES * 2 * SLICE : 0;
   static constexpr uint32_t BAR_OFF = RING_OFF + ST * SLOT;
-  // full / empty per ring slot, edone per item, zfull + zfree of the product buffer,
-  // the resident J tiles, the final MMA drain
-  static constexpr int N_BARS = 2 * ST + MAX_ITEMS + 4;
+  static constexpr int N_BARS = 2 * ST + 2 * MAX_ITEMS + 2;
   static constexpr uint32_t INFO_OFF = BAR_OFF + 8 * N_BARS;
   static constexpr uint32_t BYTES = INFO_OFF + sizeof(ItemInfo) * MAX_ITEMS + 16 + 1024;
 };
@@ -110,7 +106,7 @@ struct RunArgs {
 enum : int {
   TR_DEPS = 0,      // producer: the item's inputs of this step are released
   TR_LOADED = 1,    // producer: the item's last operand load is issued
-  TR_ACC_FREE = 2,  // MMA issuer: the product buffer is free (the previous Z has been read)
+  TR_ACC_FREE = 2,  // MMA issuer: the epilogue of the previous step left the accumulator
   TR_FIRST_OP = 3,  // MMA issuer: the first operand slice has landed
   TR_MMA_DONE = 4,  // MMA issuer: every MMA of the item is issued (stamped before its commit)
   TR_EPI_START = 5, // epilogue (warp 2): the accumulator is ready
@@ -119,7 +115,8 @@ enum : int {
   TR_PROD_START = 8,  // producer: reaches the item (before any of its waits)
   TR_OWN = 9,       // producer: the item's own previous step is released (tile mode)
   TR_SLOT = 10,     // producer: the first ring slot for the item is free
-  TRACE_EVENTS = 11
+  TR_SLOT1 = 11,    // producer: the ring slots of K-slices 1 .. 5 are free (5 events)
+  TRACE_EVENTS = 16
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -170,17 +167,10 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[16]) {
                :
                : "memory");
 }
-// The same for two register sets loaded together (a product chunk and a momentum chunk).
-__device__ __forceinline__ void tmem_wait_ld2(uint32_t (&v)[16], uint32_t (&w)[16]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;"
-               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
-                 "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
-                 "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(w[0]), "+r"(w[1]),
-                 "+r"(w[2]), "+r"(w[3]), "+r"(w[4]), "+r"(w[5]), "+r"(w[6]), "+r"(w[7]),
-                 "+r"(w[8]), "+r"(w[9]), "+r"(w[10]), "+r"(w[11]), "+r"(w[12]), "+r"(w[13]),
-                 "+r"(w[14]), "+r"(w[15])
-               :
-               : "memory");
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 __device__ __forceinline__ void red_release_gpu_add(uint32_t* p, uint32_t v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -208,17 +198,10 @@ __device__ __forceinline__ bool rwait(uint32_t bar, uint32_t parity, int32_t* er
   return true;
 }
 
-__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 // Bounded wait until a release counter reaches `target`; gives up on an abort of
 // this CTA or a timeout reported by any other CTA.
 // Polls back off for 32 ns, and the error word is read every 64th poll only, so a
-// waiting producer takes few issue slots and little L2 bandwidth (tight polling with
-// relaxed loads and one fence measured slower).
+// waiting producer takes few issue slots and little L2 bandwidth.
 __device__ __forceinline__ bool wait_count(const uint32_t* p, uint32_t target, int32_t* err,
                                            volatile int32_t* abort) {
   if (ld_acquire_gpu(p) >= target) return true;
@@ -288,9 +271,8 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
   __shared__ uint32_t tmem_slot;
   __shared__ int32_t abort_s;
   volatile int32_t* abort_flag = &abort_s;
-  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * ST, edone0 = empty0 + 8 * ST,
-                 zfull = edone0 + 8 * MAX_ITEMS, zfree = zfull + 8, jbar = zfree + 8,
-                 drain = jbar + 8;
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * ST, accf0 = empty0 + 8 * ST,
+                 edone0 = accf0 + 8 * MAX_ITEMS, jbar = edone0 + 8 * MAX_ITEMS, drain = jbar + 8;
 
   const int2 wk = a.work[blockIdx.x];
   const int n_items = wk.y;
@@ -312,9 +294,10 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
     it.last_t = on ? min(a.t1, it.steps_b) - 1 : a.t0 - 1;
     it.rt = item / a.n_kt;
     it.rows_b = (uint32_t)a.rows_b[rt.block];
-    it.c0 = a.c0[rt.block];
+    it.dtc0 = a.dt * a.c0[rt.block];
+    it.inv_dtc0 = 1.0f / it.dtc0;
     it.inv_steps = 1.0 / (double)it.steps_b;
-    it.fh = a.deform ? a.deform[rt.block] : 0.f;
+    it.dth = a.deform ? a.dt * a.deform[rt.block] : 0.f;
     info[lane] = it;
   }
   if (threadIdx.x == 0) {
@@ -322,9 +305,10 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    for (int i = 0; i < MAX_ITEMS; ++i) mbar_init(edone0 + 8 * i, EPI_WARPS);
-    mbar_init(zfull, 1);          // the MMAs of one item have written Z
-    mbar_init(zfree, EPI_WARPS);  // the epilogue warps have read Z
+    for (int i = 0; i < MAX_ITEMS; ++i) {
+      mbar_init(accf0 + 8 * i, 1);
+      mbar_init(edone0 + 8 * i, EPI_WARPS);
+    }
     mbar_init(jbar, 1);
     mbar_init(drain, 1);
     abort_s = 0;
@@ -339,10 +323,15 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
-    if (lane == 0 && n_items > 0) {
+    // Lanes 0 .. ST-1 fill up to ST ring slots at once, one K-slice (X_hat and J
+    // copies) per lane: the bulk copies of one thread complete one after the other, so
+    // parallel lanes multiply the bytes in flight.  The MMA issuer consumes the slots
+    // in order.
+    if (n_items > 0) {
+      const bool lead = lane == 0;
       uint32_t q = 0;
       bool jissued = false;
-      if (JRES) {  // all items of the CTA share one row tile
+      if (JRES && lead) {  // all items of the CTA share one row tile
         const ItemInfo& it = info[0];
         mbar_expect_tx(jbar, (uint32_t)it.nk * SLICE);
         for (int kb = 0; kb < it.nk; ++kb)
@@ -357,51 +346,68 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
         for (int i = 0; ok && i < n_items; ++i) {
           const ItemInfo& it = info[i];
           if (t > it.last_t) continue;
-          trace_at(a, u, i, TR_PROD_START);
-          // tile mode: the item's own previous step has been released (this keeps the
-          // signal warp at most one edone phase behind even when the diagonal J tile is
-          // empty); group mode: every row tile of the block has finished step t-1
-          if (u > 0) {
-            ok = a.group_sync
-                     ? wait_count(a.done + (size_t)it.block * a.n_kt + it.k, (uint32_t)u * it.rows_b,
-                                  a.err, abort_flag)
-                     : wait_count(a.done + (size_t)it.rt * a.n_kt + it.k, (uint32_t)u, a.err,
-                                  abort_flag);
-            if (!ok) break;
-            if (a.group_sync) fence_proxy_async_global();
-          }
-          trace_at(a, u, i, TR_OWN);
-          if (a.group_sync || u == 0) trace_at(a, u, i, TR_DEPS);
-          for (int kb = 0; kb < it.nk; ++kb) {
+          // Dependencies, waited in parallel by the lanes (acquire loads of one thread
+          // would serialise, a round trip each).  Tile mode: lane 0 waits for the item's
+          // own previous step, every loading lane for the column tile of its K-slice
+          // (both halves of a column check its counter).  Group mode: lane 0 waits until
+          // every row tile of the block has finished step t-1.  Then the lanes fill up to
+          // ST ring slots, one K-slice each.
+          if (lead) trace_at(a, u, i, TR_PROD_START);
+          for (int kb0 = 0; ok && kb0 < it.nk; kb0 += ST) {
+            const int kb = kb0 + lane;
+            const bool mine = lane < ST && kb < it.nk;
             const int e = kb >> 1, half = kb & 1;
-            const int32_t ct = a.tile_col[it.tile_begin + e];
-            if (u > 0 && half == 0 && !a.group_sync) {  // column tile ct of X_hat_t is written
-              ok = wait_count(a.done + (size_t)ct * a.n_kt + it.k, (uint32_t)u, a.err, abort_flag);
-              if (!ok) break;
-              fence_proxy_async_global();
-              if (kb + 2 >= it.nk) trace_at(a, u, i, TR_DEPS);  // the last column tile
+            const int32_t ct = mine ? a.tile_col[it.tile_begin + e] : 0;
+            bool lok = true;
+            if (u > 0 && kb0 == 0 && lead && !a.group_sync) {
+              lok = wait_count(a.done + (size_t)it.rt * a.n_kt + it.k, (uint32_t)u, a.err,
+                               abort_flag);
+              if (lok) trace_at(a, u, i, TR_OWN);
             }
-            const int s = (int)(q % ST);
-            const uint32_t ph = (q / ST) & 1u;
-            if (!(ok = rwait(empty0 + 8 * s, ph ^ 1u, a.err, abort_flag))) break;
-            if (kb == 0) trace_at(a, u, i, TR_SLOT);
-            uint8_t* slot = smem + L::RING_OFF + s * L::SLOT;
-            mbar_expect_tx(full0 + 8 * s, L::SLOT);
-            const uint32_t xdst = JRES ? smem_u32(slot) : smem_u32(slot + SLICE);
-            tma_load_2d(xdst, mx, full0 + 8 * s, ct * TILE + half * 64, it.k * RB);
-            if (!JRES)
-              tma_load_2d(smem_u32(slot), &tmJ, full0 + 8 * s, half * 64,
-                          (it.tile_begin + e) * TILE);
-            ++q;
+            // every loading lane acquires the release its own copies depend on
+            if (lok && mine && u > 0)
+              lok = a.group_sync
+                        ? wait_count(a.done + (size_t)it.block * a.n_kt + it.k,
+                                     (uint32_t)u * it.rows_b, a.err, abort_flag)
+                        : wait_count(a.done + (size_t)ct * a.n_kt + it.k, (uint32_t)u, a.err,
+                                     abort_flag);
+            if (lok && lead && (u == 0 || a.group_sync) && kb0 == 0) trace_at(a, u, i, TR_OWN);
+            if (!__all_sync(0xffffffffu, lok)) {
+              ok = false;
+              break;
+            }
+            if (u > 0 && mine) fence_proxy_async_global();
+            if (kb0 + ST >= it.nk && lead) trace_at(a, u, i, TR_DEPS);
+            if (mine) {
+              const int s = (int)((q + kb) % ST);
+              const uint32_t ph = ((q + kb) / ST) & 1u;
+              lok = rwait(empty0 + 8 * s, ph ^ 1u, a.err, abort_flag);
+              if (lok) {
+                if (kb == 0) trace_at(a, u, i, TR_SLOT);
+                if (kb >= 1 && kb <= 5) trace_at(a, u, i, TR_SLOT1 + kb - 1);
+                uint8_t* slot = smem + L::RING_OFF + s * L::SLOT;
+                mbar_expect_tx(full0 + 8 * s, L::SLOT);
+                const uint32_t xdst = JRES ? smem_u32(slot) : smem_u32(slot + SLICE);
+                tma_load_2d(xdst, mx, full0 + 8 * s, ct * TILE + half * 64, it.k * RB);
+                if (!JRES)
+                  tma_load_2d(smem_u32(slot), &tmJ, full0 + 8 * s, half * 64,
+                              (it.tile_begin + e) * TILE);
+              }
+            }
+            if (!__all_sync(0xffffffffu, lok)) ok = false;
           }
-          if (ok) trace_at(a, u, i, TR_LOADED);
+          if (!ok) break;
+          q += (uint32_t)it.nk;
+          if (lead) trace_at(a, u, i, TR_LOADED);
         }
       }
       // copies still in flight must land before the CTA exits: the last load of
       // every ring slot, and the resident J tiles
-      for (uint32_t j = q > (uint32_t)ST ? q - ST : 0u; j < q; ++j)
-        mbar_wait(full0 + 8 * (j % ST), (j / ST) & 1u, a.err);
-      if (jissued) mbar_wait(jbar, 0, a.err);
+      if (lead) {
+        for (uint32_t jq = q > (uint32_t)ST ? q - ST : 0u; jq < q; ++jq)
+          mbar_wait(full0 + 8 * (jq % ST), (jq / ST) & 1u, a.err);
+        if (jissued) mbar_wait(jbar, 0, a.err);
+      }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -409,19 +415,17 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
       constexpr uint32_t idesc = idesc_bf16<RB>();
       bool ok = true;
       if (JRES) ok = rwait(jbar, 0, a.err, abort_flag);
-      uint32_t q = 0, zq = 0;  // ring position; uses of the product buffer
-      const uint32_t d = tmem + Z_COL;
+      uint32_t q = 0;
       for (int u = 0; ok && u < n_steps; ++u) {
         const int t = a.t0 + u;
         for (int i = 0; ok && i < n_items; ++i) {
           const ItemInfo& it = info[i];
           if (t > it.last_t) continue;
-          // the epilogue has read the previous item's product out of the buffer (the
-          // item's own X_hat of this step is an operand, so its previous epilogue is
-          // already done: the producer waited for its release)
-          if (zq > 0 && !(ok = rwait(zfree, (zq - 1) & 1u, a.err, abort_flag))) break;
+          // the epilogue has stored y / (dt c0) of the previous step into the columns
+          if (!(ok = rwait(edone0 + 8 * i, (uint32_t)u & 1u, a.err, abort_flag))) break;
           tc_fence_after();
           trace_at(a, u, i, TR_ACC_FREE);
+          const uint32_t d = tmem + (uint32_t)(i * RB);
           for (int kb = 0; kb < it.nk; ++kb) {
             const int s = (int)(q % ST);
             const uint32_t ph = (q / ST) & 1u;
@@ -429,20 +433,18 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
             tc_fence_after();
             if (kb == 0) trace_at(a, u, i, TR_FIRST_OP);
             uint8_t* slot = smem + L::RING_OFF + s * L::SLOT;
-            // Z (vertices x replicas) = sum over K-slices of J slice (A) x X_hat slice (B)^T
+            // D (vertices x replicas) += J slice (A) x X_hat slice (B)^T
             const uint64_t jd = sdesc_sw128(JRES ? smem_u32(smem + kb * SLICE) : smem_u32(slot));
             const uint64_t xd = sdesc_sw128(JRES ? smem_u32(slot) : smem_u32(slot + SLICE));
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-              mma_bf16(d, jd + (uint64_t)(2 * k), xd + (uint64_t)(2 * k), idesc,
-                       (kb | k) != 0 ? 1u : 0u);
+              mma_bf16(d, jd + (uint64_t)(2 * k), xd + (uint64_t)(2 * k), idesc, 1u);
             mma_commit(empty0 + 8 * s);
             ++q;
           }
           if (ok) {
             trace_at(a, u, i, TR_MMA_DONE);
-            mma_commit(zfull);
-            ++zq;
+            mma_commit(accf0 + 8 * i);
           }
         }
       }
@@ -451,11 +453,11 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
     }
   } else if (warp < SIGNAL_WARP) {
     // ------------------------------------------------------------ epilogue
-    // TMEM holds (vertex x replica): lane = vertex of the row tile, column = replica of
-    // the item (y) or of the item being updated (Z).  A thread owns one vertex and 64
-    // replicas (half hh of the item) in four chunks of 16; for each replica the 32 lanes
-    // of a warp touch 32 consecutive vertices, one coalesced 128-byte line of x
-    // ([R][n_pad]).  Element indices fit 32 bits: R * n_pad <= MAX_ITEMS * 128 * 128 * CTAs.
+    // The accumulator is (vertex x replica): TMEM lane = vertex of the row tile,
+    // column = replica of the item.  A thread owns one vertex and 64 replicas (half hh
+    // of the item) in four chunks of 16; for each replica the 32 lanes of a warp touch
+    // 32 consecutive vertices, one coalesced 128-byte line of x ([R][n_pad]).
+    // Element indices fit 32 bits: R * n_pad <= MAX_ITEMS * 128 * 128 * CTAs.
     const int qd = warp & 3, hh = (warp - 2) >> 2;
     const int r = qd * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(hh * 64);
@@ -470,7 +472,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
     auto quad0 = [&](const ItemInfo& it, int chunk) -> uint32_t {
       return (uint32_t)(it.k * (RB / 4) + hh * 16 + chunk * 4) * np + (uint32_t)(it.row0 + r);
     };
-    // y into the item's TMEM columns; x into the blocked working copy
+    // y -> y / (dt c0) into the item's TMEM columns; x into the blocked working copy
     for (int i = 0; i < n_items; ++i) {
       const ItemInfo it = info[i];
       if (a.t0 > it.last_t) continue;
@@ -483,7 +485,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
         float xv[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          v[j] = vr ? __float_as_uint(yc[j * np]) : 0u;
+          v[j] = vr ? __float_as_uint(yc[j * np] * it.inv_dtc0) : 0u;
           xv[j] = vr ? xc[j * np] : 0.f;
         }
         float4* qc = a.xq + quad0(it, c);
@@ -524,7 +526,6 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
       load_x(xb[1], nit, on, 1);
       load_x(xb[2], nit, on, 2);
     }
-    uint32_t zq = 0;  // uses of the product buffer, in the MMA issuer's order
     while (cur.u < n_steps) {
       const ItemInfo it = nit;  // registers: the loop's stores cannot alias it
       const int t = a.t0 + cur.u;
@@ -534,41 +535,33 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
       const bool vr = r < it.valid, last = t == it.last_t;
       __nv_bfloat16* __restrict__ xh_out = (t & 1) ? a.xh0 : a.xh1;  // X_hat_{t+1}
       // -(a0 - a(t)) in FP64 as in the other step kernels (a(t) = a0 t / steps_b, with
-      // the reciprocal taken once per item), by one lane, shared with the warp,
-      // and the deformation force h (1 - t / steps_b) (0 without deformation)
-      float coef = 0.f, fld = 0.f;
+      // the reciprocal taken once per item), by one lane, shared with the warp
+      // and the deformation force dt h (1 - t / steps_b) (0 without deformation)
+      float coef = 0.f, dtfe = 0.f;
       if (lane == 0) {
         coef = (float)(-(a.a0 - a.a0 * (double)t * it.inv_steps));
-        fld = it.fh * (float)(1.0 - (double)t * it.inv_steps);
+        dtfe = it.dth * (float)(1.0 - (double)t * it.inv_steps);
       }
-      const float cx_s = __shfl_sync(0xffffffffu, coef, 0);
-      const float fe_s = __shfl_sync(0xffffffffu, fld, 0);
-      const bool ok = __all_sync(0xffffffffu, rwait(zfull, zq & 1u, a.err, abort_flag));
+      const float dtcx = a.dt * __shfl_sync(0xffffffffu, coef, 0);
+      const float dtfe_s = __shfl_sync(0xffffffffu, dtfe, 0);
+      const float dtc0 = it.dtc0, inv = it.inv_dtc0, dta0 = a.dta0;
+      const bool ok = __all_sync(0xffffffffu, rwait(accf0 + 8 * cur.i, (uint32_t)cur.u & 1u,
+                                                    a.err, abort_flag));
       if (!ok) break;
-      ++zq;
       tc_fence_after();
       if (warp == 2 && lane == 0) trace_at(a, cur.u, cur.i, TR_EPI_START);
-      const uint32_t zcol = lane_base + Z_COL;  // this thread's half of the product
-      const uint32_t ycol = lane_base + (uint32_t)(cur.i * RB);
-      // Z chunks are loaded one chunk ahead; y chunks when they are needed
-      uint32_t za[16], zb[16], yv[16];
+      const uint32_t col0 = lane_base + (uint32_t)(cur.i * RB);
+      uint32_t va[16], vb[16];
       __syncwarp();
-      tmem_ld16_async(zcol, za);
+      tmem_ld16_async(col0, va);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        uint32_t(&zv)[16] = (c & 1) ? zb : za;
-        uint32_t(&zn)[16] = (c & 1) ? za : zb;
-        tmem_ld16_async(ycol + (uint32_t)(c * 16), yv);
-        tmem_wait_ld2(zv, yv);
+        uint32_t(&v)[16] = (c & 1) ? vb : va;
+        uint32_t(&vn)[16] = (c & 1) ? va : vb;
+        tmem_wait_ld(v);
         if (c < 3) {
           __syncwarp();
-          tmem_ld16_async(zcol + (uint32_t)((c + 1) * 16), zn);
-        } else {
-          // every chunk of this item's Z is in registers: the MMAs of the next item
-          // may overwrite the buffer
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(zfree);
+          tmem_ld16_async(col0 + (uint32_t)((c + 1) * 16), vn);
         }
         // chunk c + 3 of the sequence: chunk 3 of this item, else 0..2 of the next
         if (c == 0)
@@ -580,54 +573,51 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
         float* yc = ys + e0;
         __nv_bfloat16* hc = xh_out + e0;
         float4* qc = a.xq + quad0(it, c);
-        uint32_t yo[16];
-        const float2 c0_2 = make_float2(it.c0, it.c0), fe_2 = make_float2(fe_s, fe_s);
-        const float2 dt_2 = make_float2(a.dt, a.dt), dta0_2 = make_float2(a.dta0, a.dta0);
-        // four replicas at a time: update, then store x, X_hat (and at the launch's
-        // last step y) at once, so only y stays live until the TMEM store
+        uint32_t out[16];
+        float xo[16], yo[16];
+        const float2 dtc0_2 = make_float2(dtc0, dtc0), dta0_2 = make_float2(dta0, dta0);
+        const float2 inv_2 = make_float2(inv, inv), dtcx_2 = make_float2(dtcx, dtcx);
+        const float2 dtfe_2 = make_float2(dtfe_s, dtfe_s);
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          float xq4[4];
+        for (int j = 0; j < 16; j += 2) {  // element pairs on the packed FP32x2 pipe
+          const float2 x0 = make_float2(xb[c][j], xb[c][j + 1]);
+          const float2 acc = make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1]));
+          // adiabatic SB: -(x^2 + a0 - a(t)); no walls
+          float2 cx = dtcx_2;
+          if (SB == QH_SB_ADIABATIC)
+            cx = __ffma2_rn(make_float2(-a.dt * x0.x, -a.dt * x0.y), x0, dtcx_2);
+          const float2 y1 = __ffma2_rn(dtc0_2, acc, __ffma2_rn(cx, x0, dtfe_2));
+          const float2 x1 = __ffma2_rn(dta0_2, y1, x0);
+          const bool w0 = SB != QH_SB_ADIABATIC && fabsf(x1.x) > 1.f;
+          const bool w1 = SB != QH_SB_ADIABATIC && fabsf(x1.y) > 1.f;
+          xo[j] = w0 ? copysignf(1.f, x1.x) : x1.x;
+          xo[j + 1] = w1 ? copysignf(1.f, x1.y) : x1.y;
+          yo[j] = w0 ? 0.f : y1.x;
+          yo[j + 1] = w1 ? 0.f : y1.y;
+          // padding vertices (J rows of zeros) may drift under the deformation field,
+          // in TMEM only: their x, y and X_hat are never stored (vr)
+          const float2 ys = __fmul2_rn(make_float2(yo[j], yo[j + 1]), inv_2);
+          out[j] = __float_as_uint(ys.x);
+          out[j + 1] = __float_as_uint(ys.y);
+        }
+        if (vr) {
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {  // element pairs on the packed FP32x2 pipe
-            const int j = 4 * m + 2 * h;
-            const float2 x0 = make_float2(xb[c][j], xb[c][j + 1]);
-            const float2 z = make_float2(__uint_as_float(zv[j]), __uint_as_float(zv[j + 1]));
-            const float2 y0 = make_float2(__uint_as_float(yv[j]), __uint_as_float(yv[j + 1]));
-            // adiabatic SB: -(x^2 + a0 - a(t)); no walls
-            float2 cx = make_float2(cx_s, cx_s);
-            if (SB == QH_SB_ADIABATIC) cx = __ffma2_rn(make_float2(-x0.x, -x0.y), x0, cx);
-            // y + dt (-(a0 - a(t)) x + c0 Z + field), then x + dt a0 y
-            const float2 g = __ffma2_rn(cx, x0, __ffma2_rn(c0_2, z, fe_2));
-            const float2 y1 = __ffma2_rn(dt_2, g, y0);
-            const float2 x1 = __ffma2_rn(dta0_2, y1, x0);
-            const bool w0 = SB != QH_SB_ADIABATIC && fabsf(x1.x) > 1.f;
-            const bool w1 = SB != QH_SB_ADIABATIC && fabsf(x1.y) > 1.f;
-            // padding vertices (J rows of zeros) may drift under the deformation field,
-            // in TMEM only: their x, y and X_hat are never stored (vr)
-            xq4[2 * h] = w0 ? copysignf(1.f, x1.x) : x1.x;
-            xq4[2 * h + 1] = w1 ? copysignf(1.f, x1.y) : x1.y;
-            yo[j] = __float_as_uint(w0 ? 0.f : y1.x);
-            yo[j + 1] = __float_as_uint(w1 ? 0.f : y1.y);
-          }
-          if (vr) {
+          for (int j = 0; j < 16; ++j) hc[j * np] = __float2bfloat16_rn(sb_operand(SB, xo[j]));
+          if (!last) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-              hc[(4 * m + e) * np] = __float2bfloat16_rn(sb_operand(SB, xq4[e]));
-            if (!last) {
-              qc[m * np] = make_float4(xq4[0], xq4[1], xq4[2], xq4[3]);
-            } else {  // the launch's last step: state back into the solver's layout
+            for (int m = 0; m < 4; ++m)
+              qc[m * np] = make_float4(xo[4 * m], xo[4 * m + 1], xo[4 * m + 2], xo[4 * m + 3]);
+          } else {  // the launch's last step: state back into the solver's layout
 #pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                xc[(4 * m + e) * np] = xq4[e];
-                yc[(4 * m + e) * np] = __uint_as_float(yo[4 * m + e]);
-              }
+            for (int j = 0; j < 16; ++j) {
+              xc[j * np] = xo[j];
+              yc[j * np] = yo[j];
             }
           }
         }
         if (!last) {
           __syncwarp();
-          tmem_st16(ycol + (uint32_t)(c * 16), yo);
+          tmem_st16(col0 + (uint32_t)(c * 16), out);
         }
       }
       if (!last) tmem_wait_st();
@@ -709,9 +699,6 @@ bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, RunPlan
   for (int32_t r = 0; r < g.n_row_tiles; ++r) {
     const int32_t b = g.h_rt[r].block;
     if (mask && !(*mask)[b]) continue;
-    // every item writes its product buffer: a row tile needs at least one J tile (true
-    // of any row tile of a block, whose vertices all have edges)
-    if ((use_lo ? g.h_rt[r].n_all : g.h_rt[r].n_hi) == 0) return false;
     if (first[b] < 0) first[b] = r;
     count[b] += 1;
   }
@@ -876,6 +863,7 @@ qh_status launch_run(Ctx* ctx, const Graph& g, const StepArgs& s, const RunBufs&
 
 int run_trace_events() { return TRACE_EVENTS; }
 int run_max_items() { return MAX_ITEMS; }
+int run_item_mask() { return 0x7fffffff; }
 
 template <bool JRES, int SB>
 static cudaError_t run_attr() {

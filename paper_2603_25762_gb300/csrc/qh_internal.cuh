@@ -405,6 +405,7 @@ qh_status launch_run(Ctx* ctx, const Graph& g, const StepArgs& s, const RunBufs&
                      unsigned long long* trace = nullptr, int trace_u0 = 0, int trace_nu = 0);
 int run_trace_events();
 int run_max_items();
+int run_item_mask();  // the item-id bits of a wave's item list entries
 cudaError_t run_set_attrs();
 
 }  // namespace qh

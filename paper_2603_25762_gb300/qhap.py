@@ -343,13 +343,13 @@ class Context:
                                               _ptr(y)))
 
     def debug_run_trace(self, g, R, step_kernel, steps, u0, nu):
-        """Step timeline of one multi-step launch: (stamps uint64[n_ctas, nu, 4, 24],
+        """Step timeline of one multi-step launch: (stamps uint64[n_ctas, nu, 4, 32],
         items int32[n_ctas, 4]); see qh_debug_run_trace for the events."""
         sk = STEP_KERNELS.index(step_kernel) if isinstance(step_kernel, str) else step_kernel
         n = I32()
         self._check(lib().qh_debug_run_trace(self.h, g.h, R, sk, steps, u0, nu, None, None,
                                              C.byref(n)))
-        stamps = np.zeros((n.value, nu, 4, 24), np.uint64)
+        stamps = np.zeros((n.value, nu, 4, 32), np.uint64)
         items = np.zeros((n.value, 4), np.int32)
         self._check(lib().qh_debug_run_trace(self.h, g.h, R, sk, steps, u0, nu, _ptr(stamps),
                                              _ptr(items), C.byref(n)))

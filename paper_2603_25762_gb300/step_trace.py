@@ -27,10 +27,10 @@ import argparse
 import numpy as np
 
 EV = ["deps", "loaded", "acc_free", "first_op", "mma_done", "epi_start", "epi_end", "release",
-      "prod_start", "own", "slot"]
+      "prod_start", "own", "slot", "slot1", "slot2", "slot3", "slot4", "slot5"]
 E = {n: i for i, n in enumerate(EV)}
 N_EV = len(EV)
-CLOCK0 = 12  # first SM-clock column of a stamp row
+CLOCK0 = 16  # first SM-clock column of a stamp row
 
 
 def _q(a):
@@ -90,6 +90,9 @@ def analyse(stamps, items, n_kt, ns_per_cycle):
     rows.append(("producer: own released -> all inputs released", d("own", "deps")))
     rows.append(("producer: reaches item -> first ring slot free", d("prod_start", "slot")))
     rows.append(("producer: all inputs released -> last load issued", d("deps", "loaded")))
+    for j in range(1, 6):
+        rows.append((f"producer: ring slot of K-slice {j - 1} -> of K-slice {j}",
+                     d("slot" if j == 1 else f"slot{j - 1}", f"slot{j}")))
     rows.append(("last load issued -> MMA committed", d("loaded", "mma_done")))
     rows.append(("epilogue end -> X_hat released", d("epi_end", "release")))
     # own release at step u-1 (global timer) -> the producer seeing it at step u

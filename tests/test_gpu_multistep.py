@@ -145,9 +145,8 @@ def test_multistep_early_stop_chunks(q, ctx, kernel):
 
 
 def test_multistep_agrees_with_per_step_kernel(q, ctx):
-    # same seed, steps and replicas: the two kernels contract the update into FMAs in
-    # different orders, so the trajectories separate, but the best cuts are of equal
-    # quality
+    # same seed, steps and replicas: the two kernels round differently (y / (dt c0)
+    # on chip), so the trajectories separate, but the best cuts are of equal quality
     fr = synth.hifi_region(1002, scale=0.1)
     g = ctx.build_graph(fr)
     a = ctx.solve(g, replicas=256, steps=1000, precision=q.PREC_BF16, seed=3,
@@ -165,34 +164,12 @@ def test_multistep_rejects_unfit_cases(q, ctx):
     g = ctx.build_graph(fr)
     with pytest.raises(RuntimeError):  # replicas not a multiple of 128
         ctx.solve(g, replicas=64, steps=10, precision=q.PREC_BF16, step_kernel=MULTI[0])
-
-
-@pytest.mark.parametrize("kernel", MULTI)
-def test_multistep_zero_coupling_is_the_free_oscillator(q, ctx, oracle, kernel):
-    """c0 = 0: the product no longer enters y (the multi-step kernel keeps y and the
-    product apart, so no c0 is excluded); x, y follow the uncoupled oscillator of the
-    oracle to FP32 rounding."""
-    import torch
-    fr = synth.batched_blocks(1004, n_blocks=4, n_min=60, n_max=300)
-    g = ctx.build_graph(fr)
-    og = oracle.read_graph(fr, oracle.READ_SIGNED)
-    n_pad, pidx, c0 = g.layout()
-    R = 128
-    rng = np.random.default_rng(4)
-    x = np.zeros((R, n_pad), np.float32)
-    y = np.zeros((R, n_pad), np.float32)
-    blocks = oracle.blocks_of(og)
-    for nodes in blocks:
-        x[:, pidx[nodes]] = rng.uniform(-0.5, 0.5, (R, len(nodes)))
-        y[:, pidx[nodes]] = rng.uniform(-0.5, 0.5, (R, len(nodes)))
-    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
-    ctx.debug_steps(g, q.PREC_BF16, R, xd, yd, 10, 4, 40, c0=np.zeros_like(c0), step_kernel=kernel)
-    xg, yg = xd.cpu().numpy().astype(np.float64), yd.cpu().numpy().astype(np.float64)
-    for nodes in blocks:
-        x1, y1 = oracle.bsb_run(og.subgraph(nodes), x[:, pidx[nodes]].astype(np.float64),
-                                y[:, pidx[nodes]].astype(np.float64), 10, 14, 40, c0=0.0)
-        assert np.allclose(xg[:, pidx[nodes]], x1, rtol=0, atol=1e-5)
-        assert np.allclose(yg[:, pidx[nodes]], y1, rtol=0, atol=1e-5)
+    n_pad, _, c0 = g.layout()
+    x = torch.zeros((128, n_pad), dtype=torch.float32, device="cuda")
+    y = torch.zeros_like(x)
+    with pytest.raises(RuntimeError):  # dt * c0 = 0 cannot hold y / (dt c0)
+        ctx.debug_steps(g, q.PREC_BF16, 128, x, y, 0, 2, 10, c0=np.zeros_like(c0),
+                        step_kernel=MULTI[1])
 
 
 def _wave_case(q, ctx, oracle, kernel, check_blocks):
@@ -261,7 +238,7 @@ def test_step_trace_events_are_ordered(q, ctx, kernel):
     stamps, items = ctx.debug_run_trace(g, 256, kernel, 40, 10, 8)
     live = items >= 0
     assert live.any(axis=1).all()
-    c = stamps[..., 12:23].astype(np.int64)
+    c = stamps[..., 16:27].astype(np.int64)
     for cta in range(stamps.shape[0]):
         for sl in np.nonzero(live[cta])[0]:
             ev = c[cta, :, sl]  # [nu, 11]
