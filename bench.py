@@ -172,6 +172,11 @@ def _workload(args):
            "linkage_k": getattr(args, "linkage_k", 10) if mode == "snp" else None,
            "deform": ({"h": args.deform_h, "tries": args.deform_tries}
                       if mode == "snp" and getattr(args, "deform_h", 0.0) > 0 else None),
+           "early_stop": ({"check_every": args.check_every, "patience": args.patience,
+                           "checks": ("between launches" if getattr(args, "check_mode", 0) else
+                                      "inside the multi-step launch where it applies")}
+                          if getattr(args, "check_every", 0) > 0 and getattr(args, "patience", 0) > 0
+                          else None),
            "l2": "flushed between timed steps (256 MiB write)"}
     if scale != 1.0:
         cfg["scale"] = scale
@@ -317,7 +322,9 @@ def run_ours(args):
                   step_kernel=args.step_kernel if p == prec else None,
                   refine_max=args.refine_max,
                   variant=args.variant, dt=0.1 if args.variant == "adiabatic" else 1.0,
-                  deform_h=args.deform_h, deform_tries=args.deform_tries)
+                  deform_h=args.deform_h, deform_tries=args.deform_tries,
+                  check_every=args.check_every, patience=args.patience,
+                  check_mode=args.check_mode)
         if ws > 1 and args.shard == "blocks":
             # this rank's share of the blocks by cost, then the per-block exchange
             sol = multi.solve_blocks_sharded(ctx, g, rank, ws, **kw)
@@ -526,6 +533,12 @@ def main():
                     help="SNP graphs: deformation field strength of the refinement's re-solves")
     ap.add_argument("--deform-tries", type=int, default=0,
                     help="SNP graphs: deformed re-solves after a failed solve")
+    ap.add_argument("--check-every", type=int, default=0,
+                    help="early stop: energy check period in bSB steps (0 = off)")
+    ap.add_argument("--patience", type=int, default=0,
+                    help="early stop: checks without a better best cut before a block stops")
+    ap.add_argument("--check-mode", type=int, default=0, choices=[0, 1],
+                    help="0 = checks inside the multi-step launch where it applies, 1 = between launches")
     ap.add_argument("--step-kernel", default=None,
                     help="pin the BF16 step-kernel variant (default: autotune)")
     args = ap.parse_args()

@@ -219,7 +219,14 @@ typedef struct {
                            out negative but gives no formula: this is the
                            library's reading of it.  Must be finite and >= 0. */
   int32_t deform_tries; /* re-solves with deformation after a failed solve (>= 0) */
-  int32_t reserved;     /* must be 0 */
+  int32_t check_mode;   /* where the early-stop checks run (with check_every and
+                           patience > 0): 0 = inside the multi-step launch when it
+                           applies (a multi-step step kernel, integer weights, at
+                           most three items per SM fit every block) and pays
+                           (check_every <= 128), else between launches; 1 = always
+                           between launches, with the separate cut kernels.  Both
+                           give the same steps_run, cuts and spins.  Other values
+                           -> QH_EINVAL */
 } qh_bsb_opts;
 
 /* Run multi-replica bSB on every block of the graph in one batched launch per

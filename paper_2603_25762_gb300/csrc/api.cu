@@ -164,6 +164,10 @@ qh_status check_err_word(Ctx* ctx) {
     cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), ctx->stream);
     return set_err(ctx, QH_ETIMEOUT, "a bounded device wait expired in the bSB step kernel");
   }
+  if (herr & ERR_CONFIG) {
+    cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), ctx->stream);
+    return set_err(ctx, QH_EINVAL, "the multi-step kernel refused its launch arguments");
+  }
   return QH_OK;
 }
 
@@ -471,8 +475,8 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
     return set_err(ctx, QH_EINVAL, "FP8 precision needs replicas to be a multiple of 64");
   if (!(o->dt > 0.0) || !(o->a0 > 0.0)) return set_err(ctx, QH_EINVAL, "dt and a0 must be > 0");
   if (!(o->deform_h >= 0.0) || !std::isfinite(o->deform_h) || o->deform_tries < 0 ||
-      o->reserved != 0)
-    return set_err(ctx, QH_EINVAL, "deform_h must be finite and >= 0, deform_tries >= 0, reserved 0");
+      o->check_mode < 0 || o->check_mode > 1)
+    return set_err(ctx, QH_EINVAL, "deform_h must be finite and >= 0, deform_tries >= 0, check_mode 0 or 1");
   if (o->check_every < 0 || o->patience < 0 || o->replica_base < 0) return set_err(ctx, QH_EINVAL, "negative option");
   if ((int64_t)o->replica_base + R > (1 << 16)) return set_err(ctx, QH_EINVAL, "replica indices must stay below 65536");
   if (is_tc_precision(o->precision) && o->step_kernel >= 0 && !G.csr_mode &&
@@ -756,10 +760,42 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
   if (multistep && !run_c0_ok(h_c0.data(), nb, a.dt)) {
     return set_err(ctx, QH_EINVAL, "multi-step kernel needs dt * c0 to be a normal float in every block");
   }
+  // Early-stop checks inside the multi-step launch: integer weights, so that the tensor
+  // cores give the energies exactly (every row sum of |J| below 2^24), and every block
+  // in one wave at three items per SM (the fourth item's TMEM holds the check product).
+  // The kernel with checks runs its steps about 20% slower than the one without, and a
+  // check between launches costs about 30 step times (hifi-region, 1,024 replicas), so
+  // the checks move inside the launch when they come at least every FUSED_CHECK_MAX
+  // steps.
+  constexpr int32_t FUSED_CHECK_MAX = 128;
+  bool fused = multistep && early && o->check_mode == 0 && W.integer_weights &&
+               o->check_every <= FUSED_CHECK_MAX;
+  if (fused) {
+    int32_t max_n = 0;
+    for (int32_t b = 0; b < nb; ++b) max_n = std::max(max_n, W.h_block_size[b]);
+    fused = W.max_abs_w * (double)max_n < 16777216.0 &&
+            run_plan(W, R, ctx->n_sm, tplan.variant, a.use_lo != 0, nullptr,
+                     sel ? &sel_mask : nullptr, 3);
+  }
+  RunCheck chk;
   if (multistep) {
     qh_status st = run_prepare(ctx, W, R, tplan.variant, a.use_lo != 0, &rb,
-                               sel ? &sel_mask : nullptr);
+                               sel ? &sel_mask : nullptr, fused ? 3 : 4);
     if (st != QH_OK) return st;
+  }
+  if (fused) {
+    chk.check_every = o->check_every;
+    chk.patience = o->patience;
+    chk.s = (__nv_bfloat16*)ctx->scratch((size_t)2 * NS * 2, S_RUN_S);
+    chk.sum_w = sum_w_work;
+    chk.e_sum = (unsigned long long*)ctx->scratch((size_t)2 * nb * R * 8, S_RUN_E);
+    chk.e_cnt = (uint32_t*)ctx->scratch((size_t)4 * nb * 4, S_RUN_EC);  // e_cnt, decided, stop_t
+    chk.seen = B.seen;
+    chk.stall = B.stall;
+    if (!chk.s || !chk.e_sum || !chk.e_cnt)
+      return set_err(ctx, QH_ENOMEM, "allocation failed (early-stop checks)");
+    chk.decided = chk.e_cnt + 2 * nb;
+    chk.stop_t = reinterpret_cast<int32_t*>(chk.e_cnt + 3 * nb);
   }
   if (!multistep && (ctx->loop_key != skey || !ctx->loop_exec)) {
     if (ctx->loop_exec) {
@@ -825,7 +861,16 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
                             reinterpret_cast<uint8_t*>(B.xh0), reinterpret_cast<uint8_t*>(B.xh0) + NS);
     QH_STAGE_CHECK("solve: state init");
     QH_CUDA_TRY(cudaEventRecord(ctx->ev[2], s));
-    if (multistep) {
+    if (fused) {
+      // one launch over all steps; the blocks stop inside it
+      QH_CUDA_TRY(cudaMemsetAsync(chk.s, 0, (size_t)2 * NS * 2, s));
+      QH_CUDA_TRY(cudaMemsetAsync(chk.e_sum, 0, (size_t)2 * nb * R * 8, s));
+      QH_CUDA_TRY(cudaMemsetAsync(chk.e_cnt, 0, (size_t)3 * nb * 4, s));
+      QH_CUDA_TRY(cudaMemsetAsync(chk.stop_t, 0xff, (size_t)nb * 4, s));
+      qh_status st = launch_run(ctx, W, a, rb, B.xh0, B.xh1, 0, max_steps, nullptr, 0, 0, &chk);
+      if (st != QH_OK) return st;
+      launch_stop_fixup(s, W, R, chk, B.x, B.steps_run);
+    } else if (multistep) {
       const int32_t chunk = early ? o->check_every : max_steps;
       for (int32_t t0 = 0; t0 < max_steps; t0 += chunk) {
         const int32_t t1 = std::min(max_steps, t0 + chunk);
@@ -864,9 +909,10 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
     step_ms_total += ms;
-    launches += multistep ? (int64_t)rb.waves.size() *
-                                (early ? (max_steps + o->check_every - 1) / o->check_every : 1)
-                          : max_steps;
+    launches += fused ? (int64_t)rb.waves.size()
+                : multistep ? (int64_t)rb.waves.size() *
+                                  (early ? (max_steps + o->check_every - 1) / o->check_every : 1)
+                            : max_steps;
     for (int32_t b = 0; b < nb; ++b)
       if (h_active[b]) {
         spin_updates += (double)G.h_block_size[b] * R * h_steps_run[b];

@@ -27,6 +27,19 @@
 // wait is nevertheless bounded and sets ERR_TIMEOUT in the error word when it
 // expires, after which all CTAs stop and drain their copies in flight.
 //
+// Early-stop checks inside the launch (read graphs: integer weights; at most three items
+// per CTA).  At a check step t (a multiple of check_every, 0 < t < steps_b) the
+// epilogue of step t-1 also writes S_t = sgn(x_t) in BF16 (exact +-1) next to X_hat_t,
+// under the same release.  Step t's producer loads the (J, S_t) K-slices after the
+// item's usual ones, the MMA issuer multiplies them into the spare TMEM columns
+// 384..511, and the epilogue reduces s_i (J S)_i over its rows into exact per-replica
+// integer sums E = S^T J S of the block (the cut is (sum W + E) / 4, J = -W).  The last
+// contributing warp of the block takes the decision of the Results' stopping rule (a
+// best cut above the best seen resets the stall count, else it grows; the block stops
+// when it reaches patience) and publishes it; every item waits for that decision one
+// check later, so a stopped block runs at most check_every steps past its stop, and its
+// spins at the stop stay in the S buffer of that check's parity.
+//
 // Roles (352 threads): warp 0 = TMA producer, warp 1 = MMA issuer (one thread
 // each), warps 2-9 = epilogue (TMEM lane quarter = warp % 4 = 32 vertices, two warps
 // per quarter split the 128 replicas), warp 10 = signal.  With JRES the J tiles of the CTA's
@@ -66,9 +79,11 @@ struct RunSmem {
   static constexpr uint32_t SLOT = JRES ? SLICE : 2 * SLICE;    // X_hat (+ J) per slot
   static constexpr uint32_t RING_OFF = JRES ? JRES_TILES * 2 * SLICE : 0;
   static constexpr uint32_t BAR_OFF = RING_OFF + ST * SLOT;
-  static constexpr int N_BARS = 2 * ST + 2 * MAX_ITEMS + 2;
+  // full, empty (ring); accf, edone, decision (per item); jbar, drain, sfull, sfree
+  static constexpr int N_BARS = 2 * ST + 3 * MAX_ITEMS + 4;
   static constexpr uint32_t INFO_OFF = BAR_OFF + 8 * N_BARS;
-  static constexpr uint32_t BYTES = INFO_OFF + sizeof(ItemInfo) * MAX_ITEMS + 16 + 1024;
+  static constexpr uint32_t STOP_OFF = INFO_OFF + sizeof(ItemInfo) * MAX_ITEMS;
+  static constexpr uint32_t BYTES = STOP_OFF + 4 * MAX_ITEMS + 16 + 1024;
 };
 
 struct RunArgs {
@@ -90,11 +105,22 @@ struct RunArgs {
   const int2* work;         // [grid] {first position, item count} in the wave's item list
   const int32_t* items;     // the wave's items (row tile * n_kt + replica tile)
   int32_t item_stride;      // a CTA's items sit at positions first, first + stride, ...
-  int32_t n_pad, n_kt, t0, t1, use_lo;
+  int32_t n_pad, n_kt, n_blocks, t0, t1, use_lo;
   float dt, dta0;
   double a0;
   int32_t* err;
   const float* deform;      // [n_blocks] deformation field strength, or nullptr
+  // early-stop checks inside the launch (check_every = 0: none)
+  int32_t check_every, patience;
+  __nv_bfloat16* s0;        // [R][n_pad] S_t = sgn(x_t) for even t / check_every
+  __nv_bfloat16* s1;        //            and for odd
+  const double* sum_w;      // [n_blocks] sum of W over both directions
+  unsigned long long* e_sum;  // [2][n_blocks][R] S^T J S per replica (two's complement)
+  uint32_t* e_cnt;          // [2][n_blocks] epilogue warps that have added their share
+  uint32_t* decided;        // [n_blocks] checks decided (released after each decision)
+  double* seen;             // [n_blocks] best cut seen at a check
+  int32_t* stall;           // [n_blocks] checks since it last improved
+  int32_t* stop_t;          // [n_blocks] the step count the block stopped at, or -1
   // step timeline (test hook; nullptr in the solver): per CTA, traced step u0 + j and
   // item slot i, TRACE_EVENTS global-timer stamps followed by TRACE_EVENTS SM-clock
   // stamps at trace[((cta * trace_nu + j) * MAX_ITEMS + i) * 2 * TRACE_EVENTS + ...]
@@ -175,6 +201,39 @@ __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
 __device__ __forceinline__ void red_release_gpu_add(uint32_t* p, uint32_t v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ uint32_t atom_add_acq_rel_gpu(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void st_release_gpu(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Relaxed gpu-scope accesses: L2-coherent, never a stale L1 line.
+__device__ __forceinline__ int32_t ld_relaxed_s32(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ double ld_relaxed_f64(const double* p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_s32(int32_t* p, int32_t v) {
+  asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_f64(double* p, double v) {
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
 // Orders generic-proxy global accesses against later async-proxy (TMA) ones.
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -242,25 +301,131 @@ __global__ void k_wait_probe(int which, const uint32_t* counter, int32_t* err) {
   }
 }
 
-// Position in the CTA's sequence of (step, item) pairs that have work.
+// Position in the CTA's sequence of (step, item) pairs that have work; `dead` masks the
+// items whose block stopped early.
 struct Cursor {
   int u, i;
 };
 __device__ __forceinline__ Cursor next_live(Cursor c, const ItemInfo* info, int n_items,
-                                            int t0, int n_steps) {
+                                            int t0, int n_steps, uint32_t dead) {
   while (true) {
     if (++c.i == n_items) {
       c.i = 0;
       if (++c.u >= n_steps) return Cursor{n_steps, 0};
     }
-    if (t0 + c.u <= info[c.i].last_t) return c;
+    if (t0 + c.u <= info[c.i].last_t && !((dead >> c.i) & 1u)) return c;
   }
 }
 
-template <bool JRES, int SB>
+// Step t of a block is a check step: its product also runs on S_t = sgn(x_t).  The
+// kernel without checks (CHECK = false) compiles none of their code: the roles' loops
+// stay as small as before, which their instruction caches need.
+template <bool CHECK>
+__device__ __forceinline__ bool check_step(const RunArgs& a, int t, int steps_b) {
+  return CHECK && t > 0 && t < steps_b && t % a.check_every == 0;
+}
+// A check step that first waits for the decision of the previous check.
+template <bool CHECK>
+__device__ __forceinline__ bool decision_step(const RunArgs& a, int t, int steps_b) {
+  return check_step<CHECK>(a, t, steps_b) && t >= 2 * a.check_every;
+}
+
+// S = sgn(x) of one epilogue thread's vertex and 64 replicas, read back from its x
+// working copy (q0: float4 m of chunk c at q0[(4c + m) np]; sc: replica j at sc[j np]).
+__device__ __forceinline__ void write_signs(const float4* __restrict__ q0, uint32_t np,
+                                         __nv_bfloat16* __restrict__ sc) {
+  const __nv_bfloat16 one = __float2bfloat16_rn(1.f), neg = __float2bfloat16_rn(-1.f);
+#pragma unroll 1
+  for (int m = 0; m < 16; ++m) {
+    const float4 v = q0[(size_t)m * np];
+    sc[(size_t)(4 * m) * np] = v.x >= 0.f ? one : neg;
+    sc[(size_t)(4 * m + 1) * np] = v.y >= 0.f ? one : neg;
+    sc[(size_t)(4 * m + 2) * np] = v.z >= 0.f ? one : neg;
+    sc[(size_t)(4 * m + 3) * np] = v.w >= 0.f ? one : neg;
+  }
+}
+
+// The energy of one check product, by one epilogue warp, and the block's decision when
+// this warp is the block's last contributor.  E = S^T J S per replica: this thread's
+// row contributes s_i (J S)_{i,rho} for its 64 replicas (s_own: its own S_t values,
+// replica j at s_own[j np]), the warp sums its 32 rows.  The products are integers
+// (integer J, +-1 S), summed exactly by the MMA in FP32.  False when a wait gave up.
+__device__ __forceinline__ bool check_energy(
+    uint32_t scol, const __nv_bfloat16* __restrict__ s_own, uint32_t np,
+    const unsigned long long* e_blk, unsigned long long* e_mine,
+    unsigned long long* e_next, uint32_t* cnt, uint32_t* cnt_next, uint32_t total, int32_t R,
+    double sum_w, double* seen, int32_t* stall, int32_t* stop_t, uint32_t* decided, int t,
+    int check_every, int patience, uint32_t sfull, uint32_t sfree, uint32_t n_chk,
+    int32_t* err, volatile int32_t* abort, int lane) {
+  if (!__all_sync(0xffffffffu, rwait(sfull, n_chk & 1u, err, abort))) return false;
+  tc_fence_after();
+#pragma unroll 1
+  for (int c = 0; c < 4; ++c) {
+    uint32_t v[16];
+    __syncwarp();
+    tmem_ld16(scol + (uint32_t)(c * 16), v);
+    int p[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {  // s_i of this thread's row, as written at step t - 1
+      const int iv = __float2int_rn(__uint_as_float(v[j]));
+      p[j] = __bfloat162float(s_own[(size_t)(16 * c + j) * np]) < 0.f ? -iv : iv;
+    }
+    // butterfly over the lanes: after the four halving rounds lane l holds 16 lanes'
+    // sums for replica (l >> 1) & 15; the last round adds its neighbour's
+#pragma unroll
+    for (int w = 8, o = 16; w >= 1; w >>= 1, o >>= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int m = 0; m < w; ++m) {
+        const int keep = up ? p[m + w] : p[m], send = up ? p[m] : p[m + w];
+        p[m] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    }
+    const int tot = p[0] + __shfl_xor_sync(0xffffffffu, p[0], 1);
+    if ((lane & 1) == 0)
+      atomicAdd(e_mine + c * 16 + ((lane >> 1) & 15), (unsigned long long)(long long)tot);
+  }
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(sfree);
+  // this warp's share is in; the block's last warp takes the decision
+  __threadfence();
+  __syncwarp();
+  uint32_t old = 0;
+  if (lane == 0) old = atom_add_acq_rel_gpu(cnt, 1u);
+  old = __shfl_sync(0xffffffffu, old, 0);
+  if (old + 1 != total) return true;
+  __threadfence();
+  double best = -INFINITY;
+  for (int rho = lane; rho < R; rho += 32)  // cut = (sum W + S^T J S) / 4, J = -W
+    best = fmax(best, 0.25 * (sum_w + (double)(long long)ld_relaxed_u64(e_blk + rho)));
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  // the next check uses the other parity: clear it (its last reader, the previous
+  // decision, is done: every contributor above waited for it)
+  for (int rho = lane; rho < R; rho += 32) st_relaxed_u64(e_next + rho, 0ull);
+  if (lane == 0) {
+    if (best > ld_relaxed_f64(seen)) {
+      st_relaxed_f64(seen, best);
+      st_relaxed_s32(stall, 0);
+    } else {
+      const int32_t st = ld_relaxed_s32(stall) + 1;
+      st_relaxed_s32(stall, st);
+      if (st >= patience) st_relaxed_s32(stop_t, t);
+    }
+    st_relaxed_s32(reinterpret_cast<int32_t*>(cnt_next), 0);
+  }
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) st_release_gpu(decided, (uint32_t)(t / check_every));
+  return true;
+}
+
+template <bool JRES, int SB, bool CHECK>
 __global__ void __launch_bounds__(RUN_THREADS, 1)
     k_bsb_run(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmX0,
-              const __grid_constant__ CUtensorMap tmX1, RunArgs a) {
+              const __grid_constant__ CUtensorMap tmX1, const __grid_constant__ CUtensorMap tmS0,
+              const __grid_constant__ CUtensorMap tmS1, RunArgs a) {
   using L = RunSmem<JRES>;
   constexpr int ST = L::ST;
   extern __shared__ uint8_t smem_raw[];
@@ -272,10 +437,20 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
   __shared__ int32_t abort_s;
   volatile int32_t* abort_flag = &abort_s;
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * ST, accf0 = empty0 + 8 * ST,
-                 edone0 = accf0 + 8 * MAX_ITEMS, jbar = edone0 + 8 * MAX_ITEMS, drain = jbar + 8;
+                 edone0 = accf0 + 8 * MAX_ITEMS, decb0 = edone0 + 8 * MAX_ITEMS,
+                 jbar = decb0 + 8 * MAX_ITEMS, drain = jbar + 8, sfull = drain + 8,
+                 sfree = sfull + 8;
+  // first step an item does not run because its block stopped (written by the producer
+  // before it arrives on the item's decision barrier)
+  volatile int32_t* stop_u = reinterpret_cast<volatile int32_t*>(smem + L::STOP_OFF);
+  // TMEM columns of the check product (free when a CTA holds at most three items)
+  constexpr uint32_t SPARE_COL = 3 * RB;
 
   const int2 wk = a.work[blockIdx.x];
-  const int n_items = wk.y;
+  // the check product needs the spare TMEM columns and S_t written in this launch:
+  // a CTA given more items, or a launch not starting at step 0, does nothing
+  const bool refused = CHECK && (a.check_every < 1 || wk.y > 3 || a.t0 != 0);
+  const int n_items = refused ? 0 : wk.y;
   const int n_steps = a.t1 - a.t0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -308,10 +483,15 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
     for (int i = 0; i < MAX_ITEMS; ++i) {
       mbar_init(accf0 + 8 * i, 1);
       mbar_init(edone0 + 8 * i, EPI_WARPS);
+      mbar_init(decb0 + 8 * i, 1);
+      stop_u[i] = 0x7fffffff;
     }
     mbar_init(jbar, 1);
     mbar_init(drain, 1);
+    mbar_init(sfull, 1);
+    mbar_init(sfree, EPI_WARPS);
     abort_s = 0;
+    if (refused) atomicOr(a.err, ERR_CONFIG);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -340,12 +520,40 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
         jissued = true;
       }
       bool ok = true;
+      uint32_t dead = 0;  // items whose block stopped early
       for (int u = 0; ok && u < n_steps; ++u) {
         const int t = a.t0 + u;
         const CUtensorMap* mx = (t & 1) ? &tmX1 : &tmX0;
         for (int i = 0; ok && i < n_items; ++i) {
           const ItemInfo& it = info[i];
-          if (t > it.last_t) continue;
+          if (t > it.last_t || ((dead >> i) & 1u)) continue;
+          const bool chk = check_step<CHECK>(a, t, it.steps_b);
+          if (chk && t >= 2 * a.check_every) {
+            // the previous check's decision: the items of a stopped block end here; the
+            // other roles learn it from stop_u after the item's decision barrier
+            int verdict = 0;  // 0: go on, 1: stopped, -1: the wait gave up
+            if (lead) {
+              if (wait_count(a.decided + it.block, (uint32_t)(t / a.check_every - 1), a.err,
+                             abort_flag)) {
+                if (ld_relaxed_s32(a.stop_t + it.block) >= 0) {
+                  stop_u[i] = u;
+                  verdict = 1;
+                }
+                mbar_arrive(decb0 + 8 * i);
+              } else {
+                verdict = -1;
+              }
+            }
+            verdict = __shfl_sync(0xffffffffu, verdict, 0);
+            if (verdict < 0) {
+              ok = false;
+              break;
+            }
+            if (verdict > 0) {
+              dead |= 1u << i;
+              continue;
+            }
+          }
           // Dependencies, waited in parallel by the lanes (acquire loads of one thread
           // would serialise, a round trip each).  Tile mode: lane 0 waits for the item's
           // own previous step, every loading lane for the column tile of its K-slice
@@ -353,51 +561,62 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
           // every row tile of the block has finished step t-1.  Then the lanes fill up to
           // ST ring slots, one K-slice each.
           if (lead) trace_at(a, u, i, TR_PROD_START);
-          for (int kb0 = 0; ok && kb0 < it.nk; kb0 += ST) {
-            const int kb = kb0 + lane;
-            const bool mine = lane < ST && kb < it.nk;
-            const int e = kb >> 1, half = kb & 1;
-            const int32_t ct = mine ? a.tile_col[it.tile_begin + e] : 0;
-            bool lok = true;
-            if (u > 0 && kb0 == 0 && lead && !a.group_sync) {
-              lok = wait_count(a.done + (size_t)it.rt * a.n_kt + it.k, (uint32_t)u, a.err,
-                               abort_flag);
-              if (lok) trace_at(a, u, i, TR_OWN);
-            }
-            // every loading lane acquires the release its own copies depend on
-            if (lok && mine && u > 0)
-              lok = a.group_sync
-                        ? wait_count(a.done + (size_t)it.block * a.n_kt + it.k,
-                                     (uint32_t)u * it.rows_b, a.err, abort_flag)
-                        : wait_count(a.done + (size_t)ct * a.n_kt + it.k, (uint32_t)u, a.err,
-                                     abort_flag);
-            if (lok && lead && (u == 0 || a.group_sync) && kb0 == 0) trace_at(a, u, i, TR_OWN);
-            if (!__all_sync(0xffffffffu, lok)) {
-              ok = false;
-              break;
-            }
-            if (u > 0 && mine) fence_proxy_async_global();
-            if (kb0 + ST >= it.nk && lead) trace_at(a, u, i, TR_DEPS);
-            if (mine) {
-              const int s = (int)((q + kb) % ST);
-              const uint32_t ph = ((q + kb) / ST) & 1u;
-              lok = rwait(empty0 + 8 * s, ph ^ 1u, a.err, abort_flag);
-              if (lok) {
-                if (kb == 0) trace_at(a, u, i, TR_SLOT);
-                if (kb >= 1 && kb <= 5) trace_at(a, u, i, TR_SLOT1 + kb - 1);
-                uint8_t* slot = smem + L::RING_OFF + s * L::SLOT;
-                mbar_expect_tx(full0 + 8 * s, L::SLOT);
-                const uint32_t xdst = JRES ? smem_u32(slot) : smem_u32(slot + SLICE);
-                tma_load_2d(xdst, mx, full0 + 8 * s, ct * TILE + half * 64, it.k * RB);
-                if (!JRES)
-                  tma_load_2d(smem_u32(slot), &tmJ, full0 + 8 * s, half * 64,
-                              (it.tile_begin + e) * TILE);
+          // pass 0: X_hat_t and J; pass 1 (check steps): S_t and J for the check product.
+          // S_t is released together with X_hat_t, so pass 1 needs no waits of its own:
+          // each lane's acquire and proxy fence of pass 0 covered its K-slices.
+          for (int pass = 0; ok && pass < (chk ? 2 : 1); ++pass) {
+            const CUtensorMap* mp =
+                pass == 0 ? mx : (((t / a.check_every) & 1) ? &tmS1 : &tmS0);
+            for (int kb0 = 0; ok && kb0 < it.nk; kb0 += ST) {
+              const int kb = kb0 + lane;
+              const bool mine = lane < ST && kb < it.nk;
+              const int e = kb >> 1, half = kb & 1;
+              const int32_t ct = mine ? a.tile_col[it.tile_begin + e] : 0;
+              bool lok = true;
+              if (pass == 0) {
+                if (u > 0 && kb0 == 0 && lead && !a.group_sync) {
+                  lok = wait_count(a.done + (size_t)it.rt * a.n_kt + it.k, (uint32_t)u, a.err,
+                                   abort_flag);
+                  if (lok) trace_at(a, u, i, TR_OWN);
+                }
+                // every loading lane acquires the release its own copies depend on
+                if (lok && mine && u > 0)
+                  lok = a.group_sync
+                            ? wait_count(a.done + (size_t)it.block * a.n_kt + it.k,
+                                         (uint32_t)u * it.rows_b, a.err, abort_flag)
+                            : wait_count(a.done + (size_t)ct * a.n_kt + it.k, (uint32_t)u,
+                                         a.err, abort_flag);
+                if (lok && lead && (u == 0 || a.group_sync) && kb0 == 0)
+                  trace_at(a, u, i, TR_OWN);
+                if (!__all_sync(0xffffffffu, lok)) {
+                  ok = false;
+                  break;
+                }
+                if (u > 0 && mine) fence_proxy_async_global();
+                if (kb0 + ST >= it.nk && lead) trace_at(a, u, i, TR_DEPS);
               }
+              if (mine) {
+                const int s = (int)((q + kb) % ST);
+                const uint32_t ph = ((q + kb) / ST) & 1u;
+                lok = rwait(empty0 + 8 * s, ph ^ 1u, a.err, abort_flag);
+                if (lok) {
+                  if (pass == 0 && kb == 0) trace_at(a, u, i, TR_SLOT);
+                  if (pass == 0 && kb >= 1 && kb <= 5) trace_at(a, u, i, TR_SLOT1 + kb - 1);
+                  uint8_t* slot = smem + L::RING_OFF + s * L::SLOT;
+                  mbar_expect_tx(full0 + 8 * s, L::SLOT);
+                  const uint32_t xdst = JRES ? smem_u32(slot) : smem_u32(slot + SLICE);
+                  tma_load_2d(xdst, mp, full0 + 8 * s, ct * TILE + half * 64, it.k * RB);
+                  if (!JRES)
+                    tma_load_2d(smem_u32(slot), &tmJ, full0 + 8 * s, half * 64,
+                                (it.tile_begin + e) * TILE);
+                }
+              }
+              if (!__all_sync(0xffffffffu, lok)) ok = false;
             }
-            if (!__all_sync(0xffffffffu, lok)) ok = false;
+            if (!ok) break;
+            q += (uint32_t)it.nk;
           }
           if (!ok) break;
-          q += (uint32_t)it.nk;
           if (lead) trace_at(a, u, i, TR_LOADED);
         }
       }
@@ -415,36 +634,59 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
       constexpr uint32_t idesc = idesc_bf16<RB>();
       bool ok = true;
       if (JRES) ok = rwait(jbar, 0, a.err, abort_flag);
-      uint32_t q = 0;
+      uint32_t q = 0, dead = 0, n_chk = 0;
       for (int u = 0; ok && u < n_steps; ++u) {
         const int t = a.t0 + u;
         for (int i = 0; ok && i < n_items; ++i) {
           const ItemInfo& it = info[i];
-          if (t > it.last_t) continue;
+          if (t > it.last_t || ((dead >> i) & 1u)) continue;
+          const bool chk = check_step<CHECK>(a, t, it.steps_b);
+          if (chk && t >= 2 * a.check_every) {
+            if (!(ok = rwait(decb0 + 8 * i, (uint32_t)(t / a.check_every) & 1u, a.err,
+                             abort_flag)))
+              break;
+            if (u >= stop_u[i]) {
+              dead |= 1u << i;
+              continue;
+            }
+          }
           // the epilogue has stored y / (dt c0) of the previous step into the columns
           if (!(ok = rwait(edone0 + 8 * i, (uint32_t)u & 1u, a.err, abort_flag))) break;
           tc_fence_after();
           trace_at(a, u, i, TR_ACC_FREE);
-          const uint32_t d = tmem + (uint32_t)(i * RB);
-          for (int kb = 0; kb < it.nk; ++kb) {
-            const int s = (int)(q % ST);
-            const uint32_t ph = (q / ST) & 1u;
-            if (!(ok = rwait(full0 + 8 * s, ph, a.err, abort_flag))) break;
-            tc_fence_after();
-            if (kb == 0) trace_at(a, u, i, TR_FIRST_OP);
-            uint8_t* slot = smem + L::RING_OFF + s * L::SLOT;
-            // D (vertices x replicas) += J slice (A) x X_hat slice (B)^T
-            const uint64_t jd = sdesc_sw128(JRES ? smem_u32(smem + kb * SLICE) : smem_u32(slot));
-            const uint64_t xd = sdesc_sw128(JRES ? smem_u32(slot) : smem_u32(slot + SLICE));
+          // pass 0: the step's product onto y / (dt c0); pass 1 (check steps): J S_t into
+          // the spare columns, once the epilogue has read the last check product
+          for (int pass = 0; ok && pass < (chk ? 2 : 1); ++pass) {
+            if (pass == 1) {
+              if (!(ok = rwait(sfree, (n_chk & 1u) ^ 1u, a.err, abort_flag))) break;
+              tc_fence_after();
+            }
+            const uint32_t d = pass == 0 ? tmem + (uint32_t)(i * RB) : tmem + SPARE_COL;
+            for (int kb = 0; kb < it.nk; ++kb) {
+              const int s = (int)(q % ST);
+              const uint32_t ph = (q / ST) & 1u;
+              if (!(ok = rwait(full0 + 8 * s, ph, a.err, abort_flag))) break;
+              tc_fence_after();
+              if (pass == 0 && kb == 0) trace_at(a, u, i, TR_FIRST_OP);
+              uint8_t* slot = smem + L::RING_OFF + s * L::SLOT;
+              // D (vertices x replicas) += J slice (A) x X_hat (or S) slice (B)^T
+              const uint64_t jd = sdesc_sw128(JRES ? smem_u32(smem + kb * SLICE) : smem_u32(slot));
+              const uint64_t xd = sdesc_sw128(JRES ? smem_u32(slot) : smem_u32(slot + SLICE));
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-              mma_bf16(d, jd + (uint64_t)(2 * k), xd + (uint64_t)(2 * k), idesc, 1u);
-            mma_commit(empty0 + 8 * s);
-            ++q;
-          }
-          if (ok) {
-            trace_at(a, u, i, TR_MMA_DONE);
-            mma_commit(accf0 + 8 * i);
+              for (int k = 0; k < 4; ++k)
+                mma_bf16(d, jd + (uint64_t)(2 * k), xd + (uint64_t)(2 * k), idesc,
+                         (pass == 0 || kb > 0 || k > 0) ? 1u : 0u);
+              mma_commit(empty0 + 8 * s);
+              ++q;
+            }
+            if (!ok) break;
+            if (pass == 0) {
+              trace_at(a, u, i, TR_MMA_DONE);
+              mma_commit(accf0 + 8 * i);
+            } else {
+              mma_commit(sfull);
+              ++n_chk;
+            }
           }
         }
       }
@@ -503,8 +745,9 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
     // x is prefetched three 16-replica chunks ahead along the (step, item) sequence;
     // chunk c of any item always lands in xb[c]
     float xb[4][16];
+    uint32_t dead = 0, n_chk = 0;  // items whose block stopped; check products read
     Cursor cur{0, -1};
-    cur = next_live(cur, info, n_items, a.t0, n_steps);
+    cur = next_live(cur, info, n_items, a.t0, n_steps, dead);
     ItemInfo nit = info[cur.i < n_items ? cur.i : 0];
     auto load_x = [&](float (&dst)[16], const ItemInfo& it, bool on, int chunk) {
       if (!on) return;
@@ -520,17 +763,36 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
         dst[4 * m + 3] = q.w;
       }
     };
-    {
-      const bool on = cur.u < n_steps;
-      load_x(xb[0], nit, on, 0);
-      load_x(xb[1], nit, on, 1);
-      load_x(xb[2], nit, on, 2);
-    }
+    bool fresh = true;  // xb holds nothing for the cursor's item yet
     while (cur.u < n_steps) {
+      if (fresh) {
+        load_x(xb[0], nit, true, 0);
+        load_x(xb[1], nit, true, 1);
+        load_x(xb[2], nit, true, 2);
+        fresh = false;
+      }
+      if (decision_step<CHECK>(a, a.t0 + cur.u, nit.steps_b)) {
+        const bool dok = __all_sync(
+            0xffffffffu, rwait(decb0 + 8 * cur.i, (uint32_t)((a.t0 + cur.u) / a.check_every) & 1u,
+                               a.err, abort_flag));
+        if (!dok) break;
+        if (cur.u >= stop_u[cur.i]) {
+          // the block stopped at the previous check: drop the item, and the x prefetched
+          // for it
+          dead |= 1u << cur.i;
+          cur = next_live(cur, info, n_items, a.t0, n_steps, dead);
+          nit = info[cur.u < n_steps ? cur.i : 0];
+          fresh = true;
+          continue;
+        }
+      }
       const ItemInfo it = nit;  // registers: the loop's stores cannot alias it
       const int t = a.t0 + cur.u;
-      const Cursor nxt = next_live(cur, info, n_items, a.t0, n_steps);
+      const Cursor nxt = next_live(cur, info, n_items, a.t0, n_steps, dead);
       const bool non = nxt.u < n_steps;
+      // a check step: the energy of S_t after the update; the step before a check step
+      // writes S_{t+1}
+      const bool chk = check_step<CHECK>(a, t, it.steps_b), wchk = check_step<CHECK>(a, t + 1, it.steps_b);
       nit = info[non ? nxt.i : cur.i];
       const bool vr = r < it.valid, last = t == it.last_t;
       __nv_bfloat16* __restrict__ xh_out = (t & 1) ? a.xh0 : a.xh1;  // X_hat_{t+1}
@@ -621,10 +883,31 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
         }
       }
       if (!last) tmem_wait_st();
+      // S_{t+1} = sgn(x_{t+1}) before the arrive, so that the release covers it
+      if (wchk && vr)
+        write_signs(a.xq + quad0(it, 0), np,
+                    ((((t + 1) / a.check_every) & 1) ? a.s1 : a.s0) + elem0(it, 0));
       tc_fence_before();
       __syncwarp();
       if (warp == 2 && lane == 0) trace_at(a, cur.u, cur.i, TR_EPI_END);
       if (lane == 0) mbar_arrive(edone0 + 8 * cur.i);
+      if (chk) {
+        const int par = (t / a.check_every) & 1;
+        const int32_t R = a.n_kt * RB;
+        const size_t eo = ((size_t)par * a.n_blocks + it.block) * R;
+        const size_t eo1 = ((size_t)(par ^ 1) * a.n_blocks + it.block) * R;
+        const bool cok = check_energy(
+            tmem + ((uint32_t)(qd * 32) << 16) + SPARE_COL + (uint32_t)(hh * 64),
+            (par ? a.s1 : a.s0) + elem0(it, 0), np,
+            a.e_sum + eo, a.e_sum + eo + it.k * RB + hh * 64, a.e_sum + eo1,
+            a.e_cnt + (size_t)par * a.n_blocks + it.block,
+            a.e_cnt + (size_t)(par ^ 1) * a.n_blocks + it.block,
+            it.rows_b * (uint32_t)a.n_kt * EPI_WARPS, R, a.sum_w[it.block], a.seen + it.block,
+            a.stall + it.block, a.stop_t + it.block, a.decided + it.block, t, a.check_every,
+            a.patience, sfull, sfree, n_chk, a.err, abort_flag, lane);
+        if (!cok) break;
+        ++n_chk;
+      }
       cur = nxt;
     }
   } else {
@@ -636,11 +919,21 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
       bool ok = true;
       for (int i = 0; ok && i < n_items; ++i)
         if (a.t0 <= info[i].last_t) ok = rwait(edone0 + 8 * i, 0u, a.err, abort_flag);
+      uint32_t dead = 0;
       for (int u = 0; ok && u < n_steps; ++u) {
         const int t = a.t0 + u;
         for (int i = 0; i < n_items; ++i) {
           const ItemInfo& it = info[i];
-          if (t > it.last_t) continue;
+          if (t > it.last_t || ((dead >> i) & 1u)) continue;
+          if (decision_step<CHECK>(a, t, it.steps_b)) {
+            if (!(ok = rwait(decb0 + 8 * i, (uint32_t)(t / a.check_every) & 1u, a.err,
+                             abort_flag)))
+              break;
+            if (u >= stop_u[i]) {
+              dead |= 1u << i;
+              continue;
+            }
+          }
           // phase 0 of edone is the initial y store; step u completes phase u + 1
           if (!(ok = rwait(edone0 + 8 * i, (uint32_t)(u + 1) & 1u, a.err, abort_flag))) break;
           if (t == it.last_t) continue;  // nobody waits for X_hat beyond this launch
@@ -663,7 +956,40 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
   }
 }
 
+// A block stopped at check step t keeps the signs it had there: x <- S of t's parity
+// (exactly +-1, so sgn(x) is that check's spin pattern), steps_run <- t.
+__global__ void k_stop_fixup(int64_t n, int32_t n_pad, const int32_t* __restrict__ pad_node,
+                             const int32_t* __restrict__ block_of,
+                             const int32_t* __restrict__ stop_t, int32_t check_every,
+                             const __nv_bfloat16* __restrict__ s0,
+                             const __nv_bfloat16* __restrict__ s1, float* x) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int32_t node = pad_node[e % n_pad];
+  if (node < 0) return;
+  const int32_t t = stop_t[block_of[node]];
+  if (t < 0) return;
+  x[e] = __bfloat162float((((t / check_every) & 1) ? s1 : s0)[e]);
+}
+
+__global__ void k_stop_steps(int32_t nb, const int32_t* __restrict__ stop_t, int32_t* steps_run) {
+  const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < nb && stop_t[b] >= 0) steps_run[b] = stop_t[b];
+}
+
 }  // namespace
+
+void launch_stop_fixup(cudaStream_t s, const Graph& g, int32_t R, const RunCheck& c, float* x,
+                       int32_t* steps_run) {
+  const int64_t n = (int64_t)R * g.n_pad;
+  if (n > 0)
+    k_stop_fixup<<<::qh::counted((unsigned)((n + 255) / 256)), 256, 0, s>>>(
+        n, g.n_pad, g.pad_node, g.block_of, c.stop_t, c.check_every, c.s,
+        c.s + (size_t)R * g.n_pad, x);
+  if (g.n_blocks > 0)
+    k_stop_steps<<<::qh::counted((unsigned)((g.n_blocks + 255) / 256)), 256, 0, s>>>(
+        g.n_blocks, c.stop_t, steps_run);
+}
 
 // ---------------------------------------------------------------------------
 // Host side.
@@ -685,12 +1011,12 @@ static bool run_group(int v) { return v == RUN_VARIANT_FIRST || v == RUN_VARIANT
 // Stream: CTA c of the wave's G CTAs takes the wave's items c, c + G, c + 2G, ...
 // False when some block does not fit one wave.
 bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, RunPlan* plan,
-              const std::vector<int32_t>* mask) {
-  if (!run_variant(variant)) return false;
+              const std::vector<int32_t>* mask, int max_items) {
+  if (!run_variant(variant) || max_items < 1 || max_items > MAX_ITEMS) return false;
   const bool jres = run_jres(variant);
   if (R % RB != 0 || g.n_row_tiles == 0 || g.csr_mode || n_sm < 1) return false;
   const int n_kt = R / RB;
-  const int cpr = (n_kt + MAX_ITEMS - 1) / MAX_ITEMS;  // JRES: CTAs per row tile
+  const int cpr = (n_kt + max_items - 1) / max_items;  // JRES: CTAs per row tile
   if (jres)
     for (const RowTile& rt : g.h_rt)
       if ((use_lo ? rt.n_all : rt.n_hi) > JRES_TILES) return false;
@@ -703,7 +1029,7 @@ bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, RunPlan
     count[b] += 1;
   }
   // a block's load on one wave: CTAs (JRES) or items (stream)
-  const int64_t cap = jres ? n_sm : (int64_t)MAX_ITEMS * n_sm;
+  const int64_t cap = jres ? n_sm : (int64_t)max_items * n_sm;
   auto load = [&](int32_t b) -> int64_t { return (int64_t)count[b] * (jres ? cpr : n_kt); };
   int64_t total = 0;
   for (int32_t b = 0; b < g.n_blocks; ++b) {
@@ -755,9 +1081,9 @@ bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, RunPlan
 }
 
 qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo, RunBufs* rb,
-                      const std::vector<int32_t>* mask) {
+                      const std::vector<int32_t>* mask, int max_items) {
   RunPlan plan;
-  if (!run_plan(g, R, ctx->n_sm, variant, use_lo, &plan, mask))
+  if (!run_plan(g, R, ctx->n_sm, variant, use_lo, &plan, mask, max_items))
     return set_err(ctx, QH_EINVAL, "multi-step kernel: a block does not fit one wave");
   const int n_kt = R / RB;
   rb->jres = run_jres(variant);
@@ -785,12 +1111,18 @@ qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo,
 template <bool JRES, int SB>
 qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const RunBufs& rb,
                           __nv_bfloat16* xh0, __nv_bfloat16* xh1, int t0, int t1,
-                          unsigned long long* trace, int trace_u0, int trace_nu) {
+                          unsigned long long* trace, int trace_u0, int trace_nu,
+                          const RunCheck* chk) {
   using L = RunSmem<JRES>;
-  CUtensorMap mJ, mX0, mX1;
+  CUtensorMap mJ, mX0, mX1, mS0, mS1;
+  // without checks the S maps repeat the X_hat ones (never loaded)
+  __nv_bfloat16* s0 = chk ? chk->s : xh0;
+  __nv_bfloat16* s1 = chk ? chk->s + (size_t)s.R * g.n_pad : xh1;
   if (!make_map(&mJ, g.tile_bf16, TILE, (uint64_t)std::max<int64_t>(g.n_tiles, 1) * TILE, TILE) ||
       !make_map(&mX0, xh0, (uint64_t)g.n_pad, (uint64_t)s.R, RB) ||
-      !make_map(&mX1, xh1, (uint64_t)g.n_pad, (uint64_t)s.R, RB))
+      !make_map(&mX1, xh1, (uint64_t)g.n_pad, (uint64_t)s.R, RB) ||
+      !make_map(&mS0, s0, (uint64_t)g.n_pad, (uint64_t)s.R, RB) ||
+      !make_map(&mS1, s1, (uint64_t)g.n_pad, (uint64_t)s.R, RB))
     return set_err(ctx, QH_ECUDA, "cuTensorMapEncodeTiled failed (multi-step kernel)");
   RunArgs a{};
   a.rt = s.rt;
@@ -809,6 +1141,7 @@ qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const Run
   a.group_sync = rb.group_sync ? 1 : 0;
   a.n_pad = s.n_pad;
   a.n_kt = s.R / RB;
+  a.n_blocks = g.n_blocks;
   a.t0 = t0;
   a.t1 = t1;
   a.use_lo = s.use_lo;
@@ -820,6 +1153,19 @@ qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const Run
   a.trace = trace;
   a.trace_u0 = trace_u0;
   a.trace_nu = trace_nu;
+  if (chk) {
+    a.check_every = chk->check_every;
+    a.patience = chk->patience;
+    a.s0 = s0;
+    a.s1 = s1;
+    a.sum_w = chk->sum_w;
+    a.e_sum = chk->e_sum;
+    a.e_cnt = chk->e_cnt;
+    a.decided = chk->decided;
+    a.seen = chk->seen;
+    a.stall = chk->stall;
+    a.stop_t = chk->stop_t;
+  }
   // every wave's counters start from zero; waves use disjoint counters
   QH_CUDA_TRY(cudaMemsetAsync(rb.done, 0, (size_t)rb.n_done * 4, ctx->stream));
   for (const RunWave& w : rb.waves) {
@@ -837,7 +1183,9 @@ qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const Run
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     note_launch(1);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_bsb_run<JRES, SB>, mJ, mX0, mX1, a);
+    cudaError_t e =
+        chk ? cudaLaunchKernelEx(&cfg, k_bsb_run<JRES, SB, true>, mJ, mX0, mX1, mS0, mS1, a)
+            : cudaLaunchKernelEx(&cfg, k_bsb_run<JRES, SB, false>, mJ, mX0, mX1, mS0, mS1, a);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_bsb_run launch");
   }
   return QH_OK;
@@ -845,10 +1193,13 @@ qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const Run
 
 qh_status launch_run(Ctx* ctx, const Graph& g, const StepArgs& s, const RunBufs& rb,
                      __nv_bfloat16* xh0, __nv_bfloat16* xh1, int t0, int t1,
-                     unsigned long long* trace, int trace_u0, int trace_nu) {
+                     unsigned long long* trace, int trace_u0, int trace_nu,
+                     const RunCheck* check) {
   if (g.n_row_tiles == 0 || t1 <= t0) return QH_OK;
+  if (check && (check->check_every < 1 || check->patience < 1 || t0 != 0))
+    return set_err(ctx, QH_EINVAL, "multi-step checks need check_every, patience >= 1 from step 0");
 #define QH_RUN_CASE(J, V) \
-  launch_run_impl<J, V>(ctx, g, s, rb, xh0, xh1, t0, t1, trace, trace_u0, trace_nu)
+  launch_run_impl<J, V>(ctx, g, s, rb, xh0, xh1, t0, t1, trace, trace_u0, trace_nu, check)
   switch (s.sb * 2 + (rb.jres ? 1 : 0)) {
     case 0: return QH_RUN_CASE(false, QH_SB_BALLISTIC);
     case 1: return QH_RUN_CASE(true, QH_SB_BALLISTIC);
@@ -867,8 +1218,13 @@ int run_item_mask() { return 0x7fffffff; }
 
 template <bool JRES, int SB>
 static cudaError_t run_attr() {
-  return cudaFuncSetAttribute(k_bsb_run<JRES, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)RunSmem<JRES>::BYTES);
+  cudaError_t e = cudaFuncSetAttribute(k_bsb_run<JRES, SB, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)RunSmem<JRES>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_bsb_run<JRES, SB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)RunSmem<JRES>::BYTES);
+  return e;
 }
 
 qh_status launch_wait_probe(Ctx* ctx, int which) {

@@ -35,6 +35,7 @@ enum : int32_t {
   ERR_QUAL = 2,         // Phred quality outside [4, 93]
   ERR_ROWCAP = 4,       // SNP row over SNP_ROW_CAP terms
   ERR_TIMEOUT = 8,      // bounded wait expired (mbarrier)
+  ERR_CONFIG = 16,      // a kernel refused the launch's arguments (host-side slip)
 };
 
 struct RowTile {           // one 128-row slab of a block in the padded layout
@@ -366,7 +367,7 @@ qh_status tc_prepare(Ctx* ctx);
 //   8: J resident in smem, tile hand-off    9: J streamed, group hand-off
 constexpr int RUN_VARIANT_FIRST = 6;
 constexpr int S_RUN_WORK = 96, S_RUN_ROWS = 97, S_RUN_DONE = 98, S_RUN_XQ = 99;  // scratch slots
-constexpr int S_WAIT_PROBE = 100, S_RUN_ITEMS = 101;
+constexpr int S_WAIT_PROBE = 100, S_RUN_ITEMS = 101, S_RUN_S = 102, S_RUN_E = 103, S_RUN_EC = 104;
 struct RunWave {              // one launch: whole blocks whose items fit on chip
   int work_off = 0;           // first entry of the wave in RunBufs::work
   int item_off = 0;           // first entry of the wave in RunBufs::items
@@ -391,10 +392,25 @@ struct RunBufs {
 };
 bool run_variant(int v);
 // mask (n_blocks flags, or nullptr = every block): blocks left out take no items
+// max_items: items per CTA at most (run_max_items(), or 3 for checks inside the launch)
 bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, RunPlan* plan,
-              const std::vector<int32_t>* mask = nullptr);
+              const std::vector<int32_t>* mask = nullptr, int max_items = 4);
 qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo, RunBufs* rb,
-                      const std::vector<int32_t>* mask = nullptr);
+                      const std::vector<int32_t>* mask = nullptr, int max_items = 4);
+// Early-stop checks inside one multi-step launch over steps 0 .. t1 (integer weights;
+// the plan must hold at most three items per CTA).  All device buffers, zeroed by the
+// caller except seen (-inf) and stop_t (-1).
+struct RunCheck {
+  int32_t check_every = 0, patience = 0;
+  __nv_bfloat16* s = nullptr;        // two [R][n_pad] buffers of S = sgn(x), zero at start
+  const double* sum_w = nullptr;     // [n_blocks]
+  unsigned long long* e_sum = nullptr;  // [2][n_blocks][R]
+  uint32_t* e_cnt = nullptr;         // [2][n_blocks]
+  uint32_t* decided = nullptr;       // [n_blocks]
+  double* seen = nullptr;            // [n_blocks]
+  int32_t* stall = nullptr;          // [n_blocks]
+  int32_t* stop_t = nullptr;         // [n_blocks]
+};
 // Steps t0 .. t1-1 in one launch.  X_hat_t is read from xh0 (t even) or xh1 (t odd);
 // x, y of `s` are updated in place.
 // trace (test hook, else nullptr): step-timeline stamps of steps trace_u0 ..
@@ -402,7 +418,12 @@ qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo,
 // SM-clock stamps per (CTA, step, item slot of run_max_items()).
 qh_status launch_run(Ctx* ctx, const Graph& g, const StepArgs& s, const RunBufs& rb,
                      __nv_bfloat16* xh0, __nv_bfloat16* xh1, int t0, int t1,
-                     unsigned long long* trace = nullptr, int trace_u0 = 0, int trace_nu = 0);
+                     unsigned long long* trace = nullptr, int trace_u0 = 0, int trace_nu = 0,
+                     const RunCheck* check = nullptr);
+// After a launch with checks: a block that stopped at check step t takes the signs it had
+// there (S of that check's parity) as its x, and t as its steps_run.
+void launch_stop_fixup(cudaStream_t s, const Graph& g, int32_t R, const RunCheck& c,
+                       float* x, int32_t* steps_run);
 int run_trace_events();
 int run_max_items();
 int run_item_mask();  // the item-id bits of a wave's item list entries

@@ -144,6 +144,54 @@ def test_multistep_early_stop_chunks(q, ctx, kernel):
         assert sol.block(b)["best_cut"] == c[b].max()
 
 
+def _stop_case(q, ctx, g, R, steps, seed, kernel, check_every, patience, blocks=None):
+    """The same early-stopping solve with the checks inside the multi-step launch and
+    between launches (separate cut kernels): the trajectories are the same bits, so
+    steps_run, every replica's cut, the picks and the spins must agree exactly."""
+    kw = dict(replicas=R, steps=steps, precision=q.PREC_BF16, seed=seed,
+              check_every=check_every, patience=patience, step_kernel=kernel, blocks=blocks)
+    inside = ctx.solve(g, check_mode=0, **kw)
+    between = ctx.solve(g, check_mode=1, **kw)
+    ti, tb = inside.timing(), between.timing()
+    # one launch per wave against one per check period
+    assert ti["n_step_launches"] < tb["n_step_launches"]
+    assert np.array_equal(inside.cuts(), between.cuts())
+    assert np.array_equal(inside.spins(g.n_nodes), between.spins(g.n_nodes))
+    runs = []
+    for b in range(g.n_blocks):
+        bi, bb = inside.block(b), between.block(b)
+        for key in ("steps_run", "best_cut", "best_replica"):
+            assert bi[key] == bb[key], (b, key, bi[key], bb[key])
+        runs.append(bi["steps_run"])
+    return runs
+
+
+@pytest.mark.parametrize("kernel", MULTI)
+def test_multistep_checks_inside_the_launch_tiny(q, ctx, kernel):
+    g = ctx.build_graph(synth.tiny_reads(1001))
+    runs = _stop_case(q, ctx, g, 128, 3000, 2, kernel, 50, 3)
+    assert min(runs) < 3000 and all(r % 50 == 0 or r == 3000 for r in runs)
+
+
+@pytest.mark.parametrize("kernel", MULTI)
+def test_multistep_checks_inside_the_launch_blocks(q, ctx, kernel):
+    # uneven blocks, each deciding on its own
+    fr = synth.batched_blocks(1004, n_blocks=10, n_min=20, n_max=400)
+    g = ctx.build_graph(fr)
+    runs = _stop_case(q, ctx, g, 128, 1200, 5, kernel, 40, 2)
+    assert min(runs) < 1200 and all(r % 40 == 0 for r in runs)
+    # a partial solve stops the same way
+    _stop_case(q, ctx, g, 128, 1200, 5, kernel, 40, 2, blocks=[1, 4, 7])
+
+
+@pytest.mark.parametrize("kernel", ["multistep-stream-tile", "multistep-stream-group"])
+def test_multistep_checks_inside_the_launch_region(q, ctx, kernel):
+    # many row tiles of one block: the decision waits on every item of the block
+    g = ctx.build_graph(synth.hifi_region(1002, scale=0.1))
+    runs = _stop_case(q, ctx, g, 256, 2000, 3, kernel, 25, 2)
+    assert min(runs) < 2000
+
+
 def test_multistep_agrees_with_per_step_kernel(q, ctx):
     # same seed, steps and replicas: the two kernels round differently (y / (dt c0)
     # on chip), so the trajectories separate, but the best cuts are of equal quality
