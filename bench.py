@@ -147,6 +147,8 @@ SEEDS = {"hifi_region": 1002, "ont_region": 1003, "batched_blocks": 1004,
 REFINE_DEFAULT = {"ont-snp": 15, "chromosome-porec": 2}
 # default timed steps: about a second of timed work (several clock samples) per workload
 STEPS_DEFAULT = {"hifi-region": 40, "ont-snp": 10, "batched-blocks": 4, "chromosome-porec": 3}
+# timed passes of each workload summarised beside the headline line
+OTHER_STEPS = {"hifi-region": 10, "ont-snp": 5, "batched-blocks": 2, "chromosome-porec": 2}
 
 
 def _workload(args):
@@ -275,6 +277,43 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def other_workloads(args):
+    """The ONT-like, batched and chromosome + Pore-C workloads, each measured by this
+    script in a process of its own (a few timed passes, no CPU baseline), summarised
+    beside the headline line."""
+    import subprocess
+    import sys
+    out = {}
+    for wl in sorted(WORKLOADS):
+        if wl == args.workload:
+            continue
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", wl, "--steps",
+               str(OTHER_STEPS.get(wl, 2)), "--warmup", "3", "--no-cpu-baseline",
+               "--no-other-workloads", "--fp32-steps", "1", "--precision", args.precision]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+        if r.returncode != 0 or not lines:
+            out[wl] = {"error": (r.stderr.strip().splitlines() or ["no output"])[-1][:300]}
+            continue
+        d = json.loads(lines[-1])
+        rf = d["roofline"]
+        q = d["quality"]
+        v = d.get("vs_fp32") or {}
+        out[wl] = {
+            "config": d["config"], "steps": d["steps"], "warmup": d["warmup"],
+            "ms_per_step": d["ms_per_step"], "value": d["value"], "unit": d["unit"],
+            "e2e": d["e2e"], "breakdown_ms": d["breakdown_ms"],
+            "roofline": {k: rf[k] for k in ("bound", "kernel", "achieved", "peak", "unit",
+                                            "frac", "avg_launch_us", "launches_per_step",
+                                            "bytes_per_spin_update", "tensor")},
+            "quality": {k: q[k] for k in ("best_cut_sum", "truth_cut", "best_over_truth",
+                                          "switch_error", "hamming_error", "n50_bp")},
+            "vs_fp32": {k: v.get(k) for k in ("fp32_ms_per_step", "fp32_kernel", "speedup",
+                                              "cut_ratio", "fp32_steps")},
+            "clocks": d["clocks"], "gpu_launches": d["gpu_launches"]}
+    return out
 
 
 def run_ours(args):
@@ -500,6 +539,8 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         cb, _ = cpu_baseline(args, fr, mode, T)
         line["cpu_baseline"] = cb
+    if ws == 1 and not args.no_other_workloads:
+        line["workloads"] = other_workloads(args)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -533,6 +574,9 @@ def main():
                     help="SNP graphs: deformation field strength of the refinement's re-solves")
     ap.add_argument("--deform-tries", type=int, default=0,
                     help="SNP graphs: deformed re-solves after a failed solve")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="measure the chosen workload only (by default a 1-GPU run also "
+                         "summarises the other workloads under 'workloads')")
     ap.add_argument("--check-every", type=int, default=0,
                     help="early stop: energy check period in bSB steps (0 = off)")
     ap.add_argument("--patience", type=int, default=0,

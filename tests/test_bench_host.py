@@ -44,6 +44,7 @@ def test_clock_summary_reports_slowdown_and_falls_back_to_last_sample(bench):
 
 def test_workload_tables_agree(bench):
     assert set(bench.STEPS_DEFAULT) == set(bench.WORKLOADS)
+    assert set(bench.OTHER_STEPS) == set(bench.WORKLOADS)
     assert all(k >= 1 for k in bench.STEPS_DEFAULT.values())
     for gen, *_ in bench.WORKLOADS.values():
         assert gen in bench.SEEDS
