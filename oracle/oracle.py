@@ -82,7 +82,7 @@ def _setup(L):
     L.qo_sb_solve.restype = D
     L.qo_sb_solve_es.restype = D
     L.qo_sb_solve_es.argtypes = [I32, P, P, P, I32, P, I32, D, D, D, U64, I64, I32, I32, I32, P, P,
-                                 P, P, I32]
+                                 P, P, I32, I32]
     L.qo_sb_solve.argtypes = [I32, P, P, P, I32, P, I32, D, D, D, U64, I64, I32, P, P, P, I32]
     L.qo_refine.restype = I32
     L.qo_refine.argtypes = [I32, P, P, P, I32, P, I32, D, D, D, U64, I64, I32, P, P]
@@ -285,10 +285,12 @@ def bsb_solve(g: CSR, replica_ids, steps, seed, block=0, it=0, dt=1.0, a0=1.0, c
 
 
 def bsb_solve_early_stop(g: CSR, replica_ids, steps, seed, check_every, patience, block=0,
-                         it=0, dt=1.0, a0=1.0, c0=0.0, variant="ballistic"):
+                         it=0, dt=1.0, a0=1.0, c0=0.0, variant="ballistic", track_best=False):
     """Multi-replica SB with early stop on a stalled best energy (the paper's maximum
-    convergence count, read as a patience over periodic energy checks).  Returns
-    (best_cut, spins, cuts, best_r, steps_run)."""
+    convergence count, read as a patience over periodic energy checks).  track_best:
+    the result is the best cut reached at any check or at the end (the best value
+    during the run), ties to the earliest check and lowest replica.  Returns
+    (best_cut, spins, cuts, best_r, steps_run); cuts are the final state's."""
     rid = _c(replica_ids, np.int32)
     R = rid.shape[0]
     s = np.zeros(g.n, np.int8)
@@ -297,7 +299,8 @@ def bsb_solve_early_stop(g: CSR, replica_ids, steps, seed, check_every, patience
     sr = C.c_int32(0)
     best = lib().qo_sb_solve_es(g.n, _p(g.row_ptr), _p(g.col), _p(g.w), R, _p(rid), steps, dt,
                                 a0, c0, seed, block, it, check_every, patience, _p(s), _p(cuts),
-                                C.byref(br), C.byref(sr), SB_VARIANTS[variant])
+                                C.byref(br), C.byref(sr), SB_VARIANTS[variant],
+                                1 if track_best else 0)
     return best, s, cuts, br.value, sr.value
 
 

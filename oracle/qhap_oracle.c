@@ -485,12 +485,17 @@ double qo_bsb_solve(int32_t n, const int64_t* rp, const int32_t* col, const doub
  * The replicas' state is then the state after t steps of the `steps`-step schedule
  * (a(t) keeps its full-schedule definition), and the result is evaluated from it as in
  * qo_sb_solve.  check_every = 0 or patience = 0: no early stop.  *steps_run receives
- * the number of steps made.                                                          */
+ * the number of steps made.
+ * track_best != 0 (the best value reached during the run, Results): the result is the
+ * best cut over the replicas at any check or at the end, with its replica and spins;
+ * ties keep the earliest check (the end counts as the last) and the lowest replica.
+ * cuts[] stays the final state's.  Checks then run every check_every steps even when
+ * patience = 0 (no early stop).                                                      */
 double qo_sb_solve_es(int32_t n, const int64_t* rp, const int32_t* col, const double* w,
                       int32_t R, const int32_t* replica_ids, int32_t steps, double dt, double a0,
                       double c0, uint64_t seed, int64_t block, int32_t iter, int32_t check_every,
                       int32_t patience, int8_t* best_s, double* cuts, int32_t* best_r,
-                      int32_t* steps_run, int32_t variant) {
+                      int32_t* steps_run, int32_t variant, int32_t track_best) {
   int64_t nnz = rp[n];
   double* J = (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
   for (int64_t e = 0; e < nnz; ++e) J[e] = -w[e];
@@ -498,9 +503,13 @@ double qo_sb_solve_es(int32_t n, const int64_t* rp, const int32_t* col, const do
   double* x = (double*)malloc(sizeof(double) * (size_t)R * (size_t)(n > 0 ? n : 1));
   double* y = (double*)malloc(sizeof(double) * (size_t)R * (size_t)(n > 0 ? n : 1));
   int8_t* s = (int8_t*)malloc((size_t)(n > 0 ? n : 1));
+  /* best during the run (track_best): its cut, replica and spins, over the checks */
+  int8_t* kept_s = (int8_t*)malloc((size_t)(n > 0 ? n : 1));
+  double kept = -INFINITY;
+  int32_t kept_r = -1;
   qo_bsb_init(n, R, replica_ids, seed, block, iter, x, y);
   int32_t t = 0;
-  if (check_every > 0 && patience > 0) {
+  if (check_every > 0 && (patience > 0 || track_best)) {
     double seen = -INFINITY;
     int32_t stall = 0;
     while (t < steps) {
@@ -513,7 +522,13 @@ double qo_sb_solve_es(int32_t n, const int64_t* rp, const int32_t* col, const do
         for (int32_t i = 0; i < n; ++i) s[i] = (x[(size_t)r * n + i] >= 0.0) ? 1 : -1;
         double c = qo_cut(n, rp, col, w, s);
         if (c > best_now) best_now = c;
+        if (track_best && c > kept) { /* strictly better: ties keep the earlier */
+          kept = c;
+          kept_r = r;
+          memcpy(kept_s, s, (size_t)n);
+        }
       }
+      if (patience <= 0) continue; /* checks for track_best only */
       if (best_now > seen) {
         seen = best_now;
         stall = 0;
@@ -538,10 +553,18 @@ double qo_sb_solve_es(int32_t n, const int64_t* rp, const int32_t* col, const do
       memcpy(best_s, s, (size_t)n);
     }
   }
+  /* the final state is the last check: an earlier check keeps the result unless the
+     final best is strictly better */
+  if (track_best && kept_r >= 0 && kept >= best) {
+    best = kept;
+    *best_r = kept_r;
+    memcpy(best_s, kept_s, (size_t)n);
+  }
   free(J);
   free(x);
   free(y);
   free(s);
+  free(kept_s);
   return best;
 }
 

@@ -786,3 +786,56 @@ def test_early_stop_result_is_the_truncated_run(oracle):
             if stall == 3:
                 break
     assert t == sr
+
+
+# ----------------------------------------------------------------------------- best during the run
+def test_track_best_is_the_best_over_the_checks(oracle):
+    """track_best: the best cut reached at any check or at the end, recomputed here from
+    plain runs cut off at every check (numpy cuts), with the earliest check and the
+    lowest replica winning ties; the final state's cuts are still reported."""
+    fr = synth.tiny_reads(1001)
+    g = oracle.read_graph(fr, oracle.READ_SIGNED)
+    sub = g.subgraph(oracle.blocks_of(g)[0])
+    reps, steps, seed, ce = list(range(12)), 600, 4, 20
+    W = sub.dense()
+    x, y = oracle.bsb_init(sub.n, reps, seed, 0)
+    kept, kept_r, kept_s = -np.inf, -1, None
+    for t in range(ce, steps + 1, ce):
+        x, y = oracle.bsb_run(sub, x, y, t - ce, t, steps)
+        S = np.where(x >= 0, 1.0, -1.0)
+        c = 0.25 * (W.sum() - np.einsum("ri,ij,rj->r", S, W, S))
+        if t == steps:
+            final = c
+            r = int(np.argmax(c))
+            if c[r] > kept:  # the end counts as the last check
+                kept, kept_r, kept_s = c[r], r, S[r]
+        else:
+            r = int(np.argmax(c))
+            if c[r] > kept:
+                kept, kept_r, kept_s = c[r], r, S[r]
+    best, s, cuts, br, sr = oracle.bsb_solve_early_stop(sub, reps, steps, seed, ce, 0,
+                                                         track_best=True)
+    assert sr == steps
+    assert np.array_equal(cuts, final)
+    assert best == kept and br == kept_r and np.array_equal(s, kept_s.astype(np.int8))
+    assert best >= final.max()
+    # without checks, or without track_best, the final state decides
+    plain = oracle.bsb_solve(sub, reps, steps, seed)
+    for ce2, tb in [(0, True), (ce, False)]:
+        b2, s2, _, br2, _ = oracle.bsb_solve_early_stop(sub, reps, steps, seed, ce2, 0,
+                                                         track_best=tb)
+        assert b2 == plain[0] and br2 == plain[3] and np.array_equal(s2, plain[1])
+
+
+def test_track_best_with_early_stop(oracle):
+    """With early stop too: the stop comes at the same step as without track_best, and
+    the kept result is at least the stopped state's best."""
+    fr = synth.tiny_reads(1001)
+    g = oracle.read_graph(fr, oracle.READ_SIGNED)
+    sub = g.subgraph(oracle.blocks_of(g)[0])
+    reps, steps, seed = list(range(16)), 3000, 2
+    b0, _, c0_, _, sr0 = oracle.bsb_solve_early_stop(sub, reps, steps, seed, 50, 3)
+    b1, s1, c1, br1, sr1 = oracle.bsb_solve_early_stop(sub, reps, steps, seed, 50, 3,
+                                                        track_best=True)
+    assert sr1 == sr0 and np.array_equal(c1, c0_)
+    assert b1 >= b0 and b1 == oracle.cut(sub, s1)
