@@ -227,6 +227,13 @@ typedef struct {
                            between launches, with the separate cut kernels.  Both
                            give the same steps_run, cuts and spins.  Other values
                            -> QH_EINVAL */
+  int32_t track_best;   /* 1 = report the best value reached during the run (Results):
+                           with check_every > 0, the best cut over the replicas at
+                           any check or at the end, with its replica and spins (ties:
+                           the earliest check, the end last; the lowest replica).
+                           qh_solution_cuts still gives the final state's cuts.  The
+                           checks then run between launches, and also without early
+                           stop (patience 0).  0 = the final state (default) */
 } qh_bsb_opts;
 
 /* Run multi-replica bSB on every block of the graph in one batched launch per

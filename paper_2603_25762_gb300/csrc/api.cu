@@ -93,7 +93,7 @@ enum {
   S_STEPSB, S_C0, S_SEEN, S_STALL, S_STEPSRUN, S_SPINS, S_C, S_WWORK, S_TBWORK, S_TFWORK,
   S_SUMW, S_SUMJ2, S_NODETMP, S_SIGNS1, S_NODEVAL1, S_CUT1, S_DBG0, S_DBG1, S_DBG2, S_RUNNING,
   S_PVWORK, S_TR0, S_TR1, S_F8H, S_F8L, S_F8FLAG, S_X8, S_DEFORM, S_TRIES, S_DBGDEF,
-  S_ZBAND, S_BANDWORK, S_RVWORK, S_TRACE
+  S_ZBAND, S_BANDWORK, S_RVWORK, S_TRACE, S_KCUT, S_KR, S_KFLAG, S_KSPINS
 };
 
 struct SolveBufs {
@@ -108,6 +108,10 @@ struct SolveBufs {
   float* deform;    // nullptr without the refinement's deformation
   int32_t* tries;
   float* zband;     // CSR band-tile step: the band product Z ([n_pad][R]), else nullptr
+  // track_best: the best result kept over the checks (cut, replica, copy flag, spins)
+  double* kept_cut;
+  int32_t *kept_r, *kept_flag;
+  int8_t* kept_spins;
 };
 
 qh_status run_step(Ctx* ctx, const Graph& g, int precision, const TcPlan& plan, StepArgs a,
@@ -475,8 +479,9 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
     return set_err(ctx, QH_EINVAL, "FP8 precision needs replicas to be a multiple of 64");
   if (!(o->dt > 0.0) || !(o->a0 > 0.0)) return set_err(ctx, QH_EINVAL, "dt and a0 must be > 0");
   if (!(o->deform_h >= 0.0) || !std::isfinite(o->deform_h) || o->deform_tries < 0 ||
-      o->check_mode < 0 || o->check_mode > 1)
-    return set_err(ctx, QH_EINVAL, "deform_h must be finite and >= 0, deform_tries >= 0, check_mode 0 or 1");
+      o->check_mode < 0 || o->check_mode > 1 || o->track_best < 0 || o->track_best > 1)
+    return set_err(ctx, QH_EINVAL,
+                   "deform_h must be finite and >= 0, deform_tries >= 0, check_mode and track_best 0 or 1");
   if (o->check_every < 0 || o->patience < 0 || o->replica_base < 0) return set_err(ctx, QH_EINVAL, "negative option");
   if ((int64_t)o->replica_base + R > (1 << 16)) return set_err(ctx, QH_EINVAL, "replica indices must stay below 65536");
   if (is_tc_precision(o->precision) && o->step_kernel >= 0 && !G.csr_mode &&
@@ -583,9 +588,15 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
   B.zband = band_on ? (float*)sc(NS * 4, S_ZBAND) : nullptr;
   B.deform = deform_on ? (float*)sc(nb * 4, S_DEFORM) : nullptr;
   B.tries = deform_on ? (int32_t*)sc(nb * 4, S_TRIES) : nullptr;
+  const bool track = o->track_best != 0 && o->check_every > 0;
+  B.kept_cut = track ? (double*)sc(nb * 8, S_KCUT) : nullptr;
+  B.kept_r = track ? (int32_t*)sc(nb * 4, S_KR) : nullptr;
+  B.kept_flag = track ? (int32_t*)sc(nb * 4, S_KFLAG) : nullptr;
+  B.kept_spins = track ? (int8_t*)sc(G.n_nodes + 16, S_KSPINS) : nullptr;
   bool okb = B.x && B.y && B.signs && B.node_val && B.cuts && B.best_r && B.best_cut && B.active && B.running &&
              B.steps_b && B.c0 && B.seen && B.stall && B.steps_run && B.spins && B.C &&
              (!deform_on || (B.deform && B.tries)) && (!band_on || B.zband) &&
+             (!track || (B.kept_cut && B.kept_r && B.kept_flag && B.kept_spins)) &&
              (o->precision == QH_PREC_FP32 ? B.x1 != nullptr : (B.xh0 && B.xh1));
   // working copy of the graph for the SNP refinement (weights, tiles, sums are gauged)
   Graph W = G;
@@ -676,7 +687,10 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
   QH_CUDA_TRY(cudaMemcpyAsync(B.active, sel_mask.data(), nb * 4, cudaMemcpyHostToDevice, s));
   QH_CUDA_TRY(cudaEventRecord(ctx->ev[0], s));
 
+  // energy checks every check_every steps: for the early stop (patience > 0) and for
+  // the best result during the run (track_best)
   const bool early = o->check_every > 0 && o->patience > 0;
+  const bool checking = early || track;
   // ---- the step loop, captured once per shape and replayed
   // The captured step loop bakes in pointers and sizes; it is replayed only when every
   // one of them is unchanged (a rebuilt graph at other addresses is captured anew).
@@ -684,9 +698,10 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
   {
     auto add = [&skey](const void* p) { skey += std::to_string((uintptr_t)p) + "|"; };
     auto addi = [&skey](long long v) { skey += std::to_string(v) + "|"; };
-    addi(o->precision); addi(R); addi(max_steps); addi(early ? o->check_every : 0);
+    addi(o->precision); addi(R); addi(max_steps); addi(checking ? o->check_every : 0);
     addi(o->sb_variant);
     addi(o->patience);
+    addi(track ? 1 : 0);
     char d[64];
     snprintf(d, sizeof d, "%.17g|%.17g|", o->dt, o->a0);
     skey += d;
@@ -768,7 +783,7 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
   // the checks move inside the launch when they come at least every FUSED_CHECK_MAX
   // steps.
   constexpr int32_t FUSED_CHECK_MAX = 128;
-  bool fused = multistep && early && o->check_mode == 0 && W.integer_weights &&
+  bool fused = multistep && early && !track && o->check_mode == 0 && W.integer_weights &&
                o->check_every <= FUSED_CHECK_MAX;
   if (fused) {
     int32_t max_n = 0;
@@ -813,13 +828,17 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
       const bool even = (t % 2) == 0;
       st = run_step(ctx, W, o->precision, tplan, a, even ? B.x : B.x1, even ? B.x1 : B.x,
                     even ? B.xh0 : B.xh1, even ? B.xh1 : B.xh0, &f8, (int64_t)NS, B.zband);
-      if (early && (t + 1) % o->check_every == 0 && t + 1 < max_steps) {
+      if (checking && (t + 1) % o->check_every == 0 && t + 1 < max_steps) {
         const float* xc = (o->precision == QH_PREC_FP32 && even) ? B.x1 : B.x;
         launch_signs(s, W, R, xc, B.signs);
         launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.running);
         launch_pick_best(s, nb, R, B.cuts, B.best_r, B.best_cut, B.running);
-        launch_early_stop(s, nb, B.best_cut, B.seen, B.stall, B.running, B.steps_run, o->patience,
-                          t + 1, B.steps_b);
+        if (track)
+          launch_track_check(s, W, R, B.signs, B.best_cut, B.best_r, B.running, t + 1, B.steps_b,
+                             B.kept_cut, B.kept_r, B.kept_flag, B.kept_spins);
+        if (early)
+          launch_early_stop(s, nb, B.best_cut, B.seen, B.stall, B.running, B.steps_run,
+                            o->patience, t + 1, B.steps_b);
       }
     }
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
@@ -853,6 +872,11 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
       QH_CUDA_TRY(cudaMemcpyAsync(B.seen, neg.data(), nb * 8, cudaMemcpyHostToDevice, s));
       QH_CUDA_TRY(cudaMemsetAsync(B.stall, 0, nb * 4, s));
     }
+    if (track) {  // nothing kept yet
+      std::vector<double> neg(nb, -INFINITY);
+      QH_CUDA_TRY(cudaMemcpyAsync(B.kept_cut, neg.data(), nb * 8, cudaMemcpyHostToDevice, s));
+      QH_CUDA_TRY(cudaMemsetAsync(B.kept_r, 0xff, nb * 4, s));
+    }
     QH_CUDA_TRY(cudaMemcpyAsync(B.running, B.active, nb * 4, cudaMemcpyDeviceToDevice, s));
     launch_init_state(s, W, R, o->replica_base, o->seed, it, B.x, B.y,
                       is_tc_precision(o->precision) ? B.xh0 : nullptr, B.active, o->sb_variant);
@@ -871,17 +895,21 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
       if (st != QH_OK) return st;
       launch_stop_fixup(s, W, R, chk, B.x, B.steps_run);
     } else if (multistep) {
-      const int32_t chunk = early ? o->check_every : max_steps;
+      const int32_t chunk = checking ? o->check_every : max_steps;
       for (int32_t t0 = 0; t0 < max_steps; t0 += chunk) {
         const int32_t t1 = std::min(max_steps, t0 + chunk);
         qh_status st = launch_run(ctx, W, a, rb, B.xh0, B.xh1, t0, t1);
         if (st != QH_OK) return st;
-        if (early && t1 < max_steps) {
+        if (checking && t1 < max_steps) {
           launch_signs(s, W, R, B.x, B.signs);
           launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.running);
           launch_pick_best(s, nb, R, B.cuts, B.best_r, B.best_cut, B.running);
-          launch_early_stop(s, nb, B.best_cut, B.seen, B.stall, B.running, B.steps_run,
-                            o->patience, t1, B.steps_b);
+          if (track)
+            launch_track_check(s, W, R, B.signs, B.best_cut, B.best_r, B.running, t1, B.steps_b,
+                               B.kept_cut, B.kept_r, B.kept_flag, B.kept_spins);
+          if (early)
+            launch_early_stop(s, nb, B.best_cut, B.seen, B.stall, B.running, B.steps_run,
+                              o->patience, t1, B.steps_b);
         }
       }
     } else {
@@ -893,6 +921,9 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
     launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.active);
     launch_pick_best(s, nb, R, B.cuts, B.best_r, B.best_cut, B.active);
     launch_extract_spins(s, W, R, B.signs, B.best_r, B.spins, B.active);
+    if (track)  // the best result during the run, unless the final one is strictly better
+      launch_track_final(s, W, B.best_cut, B.best_r, B.active, B.kept_cut, B.kept_r, B.kept_flag,
+                         B.kept_spins, B.spins);
     QH_STAGE_CHECK("solve: signs, cut, replica pick");
     if (it == 0)
       QH_CUDA_TRY(cudaMemcpyAsync(sol.cuts_first.data(), B.cuts, (size_t)nb * R * 8, cudaMemcpyDeviceToHost, s));
@@ -911,7 +942,7 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
     step_ms_total += ms;
     launches += fused ? (int64_t)rb.waves.size()
                 : multistep ? (int64_t)rb.waves.size() *
-                                  (early ? (max_steps + o->check_every - 1) / o->check_every : 1)
+                                  (checking ? (max_steps + o->check_every - 1) / o->check_every : 1)
                             : max_steps;
     for (int32_t b = 0; b < nb; ++b)
       if (h_active[b]) {

@@ -764,6 +764,47 @@ __global__ void k_early_stop(int32_t nb, const double* __restrict__ best_cut, do
   }
 }
 
+// Best during the run (track_best): after a check's pick, a running block whose best cut
+// beats the kept one keeps it (cut, replica; flag = 1 to copy its spins); at the end the
+// kept result replaces the final one unless the final is strictly better.
+__global__ void k_track_check(int32_t nb, const double* __restrict__ best_cut,
+                              const int32_t* __restrict__ best_r,
+                              const int32_t* __restrict__ active, int32_t t_done,
+                              const int32_t* __restrict__ steps_b, double* kept_cut,
+                              int32_t* kept_r, int32_t* flag) {
+  const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  flag[b] = 0;
+  if (!active[b] || t_done >= steps_b[b]) return;
+  if (best_cut[b] > kept_cut[b]) {  // strictly better: ties keep the earlier check
+    kept_cut[b] = best_cut[b];
+    kept_r[b] = best_r[b];
+    flag[b] = 1;
+  }
+}
+
+__global__ void k_track_final(int32_t nb, double* best_cut, int32_t* best_r,
+                              const int32_t* __restrict__ active,
+                              const double* __restrict__ kept_cut,
+                              const int32_t* __restrict__ kept_r, int32_t* flag) {
+  const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  flag[b] = 0;
+  if (!active[b] || kept_r[b] < 0 || kept_cut[b] < best_cut[b]) return;
+  best_cut[b] = kept_cut[b];
+  best_r[b] = kept_r[b];
+  flag[b] = 1;
+}
+
+__global__ void k_copy_spins(int32_t n, const int32_t* __restrict__ block_of,
+                             const int32_t* __restrict__ flag, const int8_t* __restrict__ src,
+                             int8_t* dst) {
+  const int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  const int32_t b = block_of[a];
+  if (b >= 0 && flag[b]) dst[a] = src[a];
+}
+
 __global__ void k_extract_spins(int32_t n, const int32_t* __restrict__ block_of,
                                 const int32_t* __restrict__ pad_index, const int8_t* __restrict__ st,
                                 int32_t R, const int32_t* __restrict__ best_r, int8_t* spins,
@@ -1087,6 +1128,27 @@ void launch_early_stop(cudaStream_t s, int32_t n_blocks, const double* best_cut,
   if (n_blocks > 0)
     k_early_stop<<<::qh::counted(nblk(n_blocks)), 256, 0, s>>>(n_blocks, best_cut, best_seen, stall, active,
                                                steps_run, patience, t_done, steps_b);
+}
+
+void launch_track_check(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t,
+                        const double* best_cut, const int32_t* best_r, const int32_t* active,
+                        int32_t t_done, const int32_t* steps_b, double* kept_cut, int32_t* kept_r,
+                        int32_t* flag, int8_t* kept_spins) {
+  if (g.n_blocks == 0) return;
+  k_track_check<<<::qh::counted(nblk(g.n_blocks)), 256, 0, s>>>(g.n_blocks, best_cut, best_r, active,
+                                                   t_done, steps_b, kept_cut, kept_r, flag);
+  launch_extract_spins(s, g, R, signs_t, best_r, kept_spins, flag);
+}
+
+void launch_track_final(cudaStream_t s, const Graph& g, double* best_cut, int32_t* best_r,
+                        const int32_t* active, const double* kept_cut, const int32_t* kept_r,
+                        int32_t* flag, const int8_t* kept_spins, int8_t* spins) {
+  if (g.n_blocks == 0) return;
+  k_track_final<<<::qh::counted(nblk(g.n_blocks)), 256, 0, s>>>(g.n_blocks, best_cut, best_r, active,
+                                                   kept_cut, kept_r, flag);
+  if (g.n_nodes > 0)
+    k_copy_spins<<<::qh::counted(nblk(g.n_nodes)), 256, 0, s>>>(g.n_nodes, g.block_of, flag,
+                                                   kept_spins, spins);
 }
 
 void launch_extract_spins(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t,

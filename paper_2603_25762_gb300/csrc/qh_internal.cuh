@@ -314,6 +314,16 @@ void launch_pick_best(cudaStream_t s, int32_t n_blocks, int32_t R, const double*
 void launch_early_stop(cudaStream_t s, int32_t n_blocks, const double* best_cut, double* best_seen,
                        int32_t* stall, int32_t* active, int32_t* steps_run, int32_t patience,
                        int32_t t_done, const int32_t* steps_b);
+// Best during the run (track_best): after a check (signs, cut and pick of that state)
+// keep each running block's better result; at the end let the kept result replace the
+// final one unless the final is strictly better.
+void launch_track_check(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t,
+                        const double* best_cut, const int32_t* best_r, const int32_t* active,
+                        int32_t t_done, const int32_t* steps_b, double* kept_cut, int32_t* kept_r,
+                        int32_t* flag, int8_t* kept_spins);
+void launch_track_final(cudaStream_t s, const Graph& g, double* best_cut, int32_t* best_r,
+                        const int32_t* active, const double* kept_cut, const int32_t* kept_r,
+                        int32_t* flag, const int8_t* kept_spins, int8_t* spins);
 void launch_extract_spins(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t,
                           const int32_t* best_r, int8_t* spins, const int32_t* active);
 void launch_block_sums(cudaStream_t s, const Graph& g, const double* w, double* sum_w,

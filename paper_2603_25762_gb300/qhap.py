@@ -49,7 +49,8 @@ class QhBsbOpts(C.Structure):
                 ("c0", C.c_double), ("seed", C.c_uint64), ("replica_base", C.c_int32),
                 ("check_every", C.c_int32), ("patience", C.c_int32), ("refine_max", C.c_int32),
                 ("step_kernel", C.c_int32), ("sb_variant", C.c_int32),
-                ("deform_h", C.c_double), ("deform_tries", C.c_int32), ("check_mode", C.c_int32)]
+                ("deform_h", C.c_double), ("deform_tries", C.c_int32), ("check_mode", C.c_int32),
+                ("track_best", C.c_int32)]
 
 # simulated-bifurcation variants (QH_SB_*)
 SB_VARIANTS = {"ballistic": 0, "discrete": 1, "adiabatic": 2}
@@ -282,7 +283,7 @@ class Context:
     def solve(self, g, replicas=32, steps=1000, precision=PREC_FP32, seed=1, dt=1.0, a0=1.0,
               c0=0.0, schedule=SCHED_LINEAR, replica_base=0, check_every=0, patience=0,
               refine_max=15, step_kernel=None, variant="ballistic", deform_h=0.0,
-              deform_tries=0, blocks=None, check_mode=0):
+              deform_tries=0, blocks=None, check_mode=0, track_best=False):
         """step_kernel: None = the default (autotuned on BF16 tile storage), or a name
         from STEP_KERNELS: the tile variants for BF16 tile storage, "csr-lane4" /
         "csr-lane8" for CSR storage.
@@ -294,11 +295,13 @@ class Context:
         blocks: None = every block; else the block indices to solve (the others stay
         unsolved, see qh_bsb_solve_blocks).
         check_mode: where early-stop checks run, 0 = inside the multi-step launch when it
-        applies, 1 = between launches (qh_bsb_opts.check_mode)."""
+        applies, 1 = between launches (qh_bsb_opts.check_mode).
+        track_best: report the best result reached at any check (every check_every
+        steps) or at the end, instead of the final state's."""
         sk = -1 if step_kernel is None else STEP_KERNELS.index(step_kernel)
         o = QhBsbOpts(replicas, steps, schedule, precision, dt, a0, c0, seed, replica_base,
                       check_every, patience, refine_max, sk, _sb(variant), deform_h,
-                      deform_tries, check_mode)
+                      deform_tries, check_mode, 1 if track_best else 0)
         s = C.c_void_p()
         if blocks is None:
             self._check(lib().qh_bsb_solve(self.h, g.h, C.byref(o), C.byref(s)))

@@ -52,7 +52,38 @@ def test_struct_layouts_match_header():
     from paper_2603_25762_gb300 import qhap
     assert ctypes.sizeof(qhap.QhFragments) == 4 + 4 + 5 * 8 + 8
     assert ctypes.sizeof(qhap.QhGraphOpts) == 5 * 4 + 4 + 8
-    assert ctypes.sizeof(qhap.QhBsbOpts) == 4 * 4 + 3 * 8 + 8 + 4 * 4 + 8 + 8 + 8
+    # replicas .. precision, dt a0 c0, seed, replica_base .. refine_max, step_kernel and
+    # sb_variant, deform_h, deform_tries and check_mode, track_best (+ padding)
+    assert ctypes.sizeof(qhap.QhBsbOpts) == 4 * 4 + 3 * 8 + 8 + 4 * 4 + 8 + 8 + 8 + 8
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Every field offset of the binding's structs equals the C compiler's for the
+    header (gcc is the host compiler the library's host code is built with)."""
+    import shutil
+    import subprocess
+    from paper_2603_25762_gb300 import qhap
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    lines = []
+    for py, c in ((qhap.QhFragments, "qh_fragments"), (qhap.QhGraphOpts, "qh_graph_opts"),
+                  (qhap.QhBsbOpts, "qh_bsb_opts")):
+        lines.append(f'printf("{c} %zu\\n", sizeof({c}));')
+        for name, _ in py._fields_:
+            lines.append(f'printf("{c}.{name} %zu\\n", offsetof({c}, {name}));')
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "qhap.h"\n'
+                   "int main(void) {\n" + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for py, c in ((qhap.QhFragments, "qh_fragments"), (qhap.QhGraphOpts, "qh_graph_opts"),
+                  (qhap.QhBsbOpts, "qh_bsb_opts")):
+        assert int(got[c]) == ctypes.sizeof(py), c
+        for name, _ in py._fields_:
+            assert int(got[f"{c}.{name}"]) == getattr(py, name).offset, (c, name)
 
 
 def _header_enums():

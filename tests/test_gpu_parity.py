@@ -475,6 +475,38 @@ def test_early_stop_steps_run_matches_oracle(q, ctx, oracle, precision, R):
         assert info["best_cut"] >= 0.999 * best
 
 
+@pytest.mark.parametrize("precision,R,pat,kernel", [(0, 32, 0, None), (0, 32, 3, None),
+                                                     (1, 64, 0, None),
+                                                     (1, 128, 3, "multistep-stream-tile")])
+def test_track_best_matches_oracle(q, ctx, oracle, precision, R, pat, kernel):
+    """The best result during the run (checks every 25 steps, with and without early
+    stop): the GPU keeps a best cut of at least 0.999 x the oracle's kept one on the
+    same replicas, its spins give exactly that cut, it is never below the final
+    state's, the final state's per-replica cuts are still reported, and early stop
+    comes at the oracle's step."""
+    fr = synth.tiny_reads(1001)
+    g = ctx.build_graph(fr)
+    steps, seed, ce = 1500, 2, 25
+    kw = dict(replicas=R, steps=steps, precision=precision, seed=seed, check_every=ce,
+              patience=pat, step_kernel=kernel)
+    sol = ctx.solve(g, track_best=True, **kw)
+    fin = ctx.solve(g, **kw)
+    og = oracle.read_graph(fr, oracle.READ_SIGNED)
+    spins = sol.spins(g.n_nodes)
+    assert np.array_equal(sol.cuts(), fin.cuts())
+    for b, nodes in enumerate(oracle.blocks_of(og)):
+        sub = og.subgraph(nodes)
+        best, _, _, _, sr = oracle.bsb_solve_early_stop(sub, list(range(R)), steps, seed, ce,
+                                                        pat, block=b, track_best=True)
+        info, ref = sol.block(b), fin.block(b)
+        assert info["steps_run"] == ref["steps_run"]
+        if precision == 0 or kernel is None:
+            assert info["steps_run"] == sr, (b, info["steps_run"], sr)
+        assert info["best_cut"] == oracle.cut(sub, spins[nodes])
+        assert info["best_cut"] >= ref["best_cut"]
+        assert info["best_cut"] >= 0.999 * best, (b, info["best_cut"], best)
+
+
 def _two_schedule_fragments():
     """One block of more than 5,000 reads (AUTO schedule: 1,000 steps) and one small
     block (500 steps) on disjoint SNPs."""
