@@ -185,6 +185,23 @@ def _workload(args):
     return fr, cfg, mode, R, T
 
 
+def _cpu_model():
+    """The host CPU as /proc/cpuinfo names it (model name, else implementer and part)."""
+    import platform
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.machine()
+    for line in info:
+        if line.lower().startswith("model name"):
+            return line.split(":", 1)[1].strip()
+    impl = [l.split(":", 1)[1].strip() for l in info if l.startswith("CPU implementer")]
+    part = [l.split(":", 1)[1].strip() for l in info if l.startswith("CPU part")]
+    if impl and part:
+        return f"{platform.machine()} (implementer {impl[0]}, part {part[0]})"
+    return platform.machine()
+
+
 def cpu_baseline(args, fr, mode, steps, seed=1, reps=None):
     """The FP64 oracle, as it stands, on the host cores: graph, blocks, bSB on a replica
     subset with the full step count, then voting or refinement + parity."""
@@ -216,7 +233,7 @@ def cpu_baseline(args, fr, mode, steps, seed=1, reps=None):
         units = sum(len(b) * int(k) for b, k in zip(res["blocks"], res["solves"])) * reps * steps
     dt = time.perf_counter() - t0
     return {"value": units / dt, "unit": "spin-updates/s", "cores": os.cpu_count(),
-            "kind": "oracle",
+            "cpu_model": _cpu_model(), "kind": "oracle", "replicas": reps,
             "sample": f"{what}, {reps} replicas x {steps} steps, whole path, {dt:.1f} s"}, res
 
 
@@ -273,7 +290,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": os.cpu_count(),
-                             "kind": "oracle", "sample": runs[-1]["sample"]},
+                             "cpu_model": _cpu_model(), "kind": "oracle",
+                             "sample": runs[-1]["sample"]},
             "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -389,6 +407,7 @@ def run_ours(args):
             stats["spins"] = float(sum(bs)) * R  # spin states updated per step
             stats["in_blocks"] = float(sum(bs))
             stats["best_cut_sum"] = float(sum(i["best_cut"] for i in info))
+            stats["cuts"] = sol.cuts()  # every replica's cut, per block
             # the cut of the generator's true partition on the same graph (reads: each
             # read's haplotype; SNPs: the true haplotype), for the solver's gap to it
             truth = fr.meta.get("read_hap") if mode == "read" else fr.truth
@@ -537,8 +556,17 @@ def run_ours(args):
         "step_kernel_tuning": ctx.tuning_report(),
     }
     if not args.no_cpu_baseline:
-        cb, _ = cpu_baseline(args, fr, mode, T)
+        cb, res = cpu_baseline(args, fr, mode, T)
         line["cpu_baseline"] = cb
+        if mode == "read" and args.workload == "hifi-region" and "cuts" in stats:
+            # cut parity on the oracle's sample: its best over replicas 0 .. r-1 of the
+            # full graph against the GPU's best over the same replica indices
+            r = cb["replicas"]
+            gpu = float(sum(c[:r].max() for c in stats["cuts"]))
+            ora = float(sum(res["cuts"]))
+            cb["parity"] = {"replicas": r, "oracle_best_cut_sum": ora,
+                            "gpu_best_cut_sum_same_replicas": gpu,
+                            "gpu_over_oracle": gpu / ora if ora else None}
     if ws == 1 and not args.no_other_workloads:
         line["workloads"] = other_workloads(args)
     print(json.dumps(line), flush=True)
