@@ -38,10 +38,12 @@
 // best cut above the best seen resets the stall count, else it grows; the block stops
 // when it reaches patience) and publishes it; every item waits for that decision one
 // check later, so a stopped block runs at most check_every steps past its stop, and its
-// spins at the stop stay in the S buffer of that check's parity.
+// spins at the stop stay in the S buffer of that check's parity.  The checks are a
+// separate instantiation (CHECK = true): the kernel without them carries none of their
+// code.
 //
-// Roles (352 threads): warp 0 = TMA producer, warp 1 = MMA issuer (one thread
-// each), warps 2-9 = epilogue (TMEM lane quarter = warp % 4 = 32 vertices, two warps
+// Roles (352 threads): warp 0 = TMA producer (six lanes), warp 1 = MMA issuer (one
+// thread), warps 2-9 = epilogue (TMEM lane quarter = warp % 4 = 32 vertices, two warps
 // per quarter split the 128 replicas), warp 10 = signal.  With JRES the J tiles of the CTA's
 // single row tile stay in shared memory for the whole launch and only X_hat
 // streams; otherwise J and X_hat K-slices stream through the ring together.
