@@ -215,6 +215,51 @@ def test_matvec_read_graph(q, ctx, oracle, dense):
     assert e16 <= 1e-2, e16
 
 
+def _states_along_schedule(q, ctx, g, R, steps):
+    """The solver's own states at t = 0, steps / 2 and steps - 1: the initial draws, then
+    FP32 steps (x of the early schedule is small, of the late one mostly at the walls)."""
+    import torch
+    n_pad = g.layout()[0]
+    x = torch.zeros((R, n_pad), dtype=torch.float32, device="cuda")
+    y = torch.zeros_like(x)
+    ctx.debug_init_state(g, R, x, y, seed=3)
+    out, t = [x.cpu().numpy().copy()], 0
+    for t1 in (steps // 2, steps - 1):
+        ctx.debug_steps(g, q.PREC_FP32, R, x, y, t, t1 - t, steps)
+        t = t1
+        out.append(x.cpu().numpy().copy())
+    return out
+
+
+@pytest.mark.parametrize("storage", [0, 2])
+def test_matvec_along_the_schedule(q, ctx, oracle, storage):
+    """J x X at the schedule points the measurement plan samples (t = 0, steps / 2,
+    steps - 1), on the solver's own states: relative Frobenius error against FP64
+    <= 1e-5 for FP32 and <= 1e-2 for BF16 (and FP8 on tile storage)."""
+    import torch
+    from scipy.sparse import csr_matrix
+    fr = synth.hifi_region(1002, scale=0.1)
+    g = ctx.build_graph(fr, storage=storage)
+    og = oracle.read_graph(fr, oracle.READ_SIGNED)
+    n_pad, pidx, _ = g.layout()
+    inb = pidx >= 0
+    J = -csr_matrix((og.w, og.col, og.row_ptr), shape=(og.n, og.n))
+    R, steps = 128, 1000
+    precs = [(q.PREC_FP32, 1e-5), (q.PREC_BF16, 1e-2)]
+    if storage == 0:
+        precs.append((q.PREC_FP8, 1e-2))
+    for k, x in enumerate(_states_along_schedule(q, ctx, g, R, steps)):
+        xv = x[:, pidx[inb]].astype(np.float64)
+        zref = (J @ xv.T).T[:, inb]
+        for prec, bar in precs:
+            zd = torch.zeros((R, n_pad), dtype=torch.float32, device="cuda")
+            ctx.debug_matvec(g, prec, R, torch.from_numpy(x).cuda(), zd)
+            err = _rel_frob(zd.cpu().numpy()[:, pidx[inb]].astype(np.float64), zref)
+            assert err <= bar, (k, prec, err)
+        if k == 2:
+            assert (np.abs(xv) == 1.0).mean() > 0.5  # the late state sits at the walls
+
+
 @pytest.mark.parametrize("mode", ["read", "snp"])
 def test_matvec_fp8(q, ctx, oracle, mode):
     # e4m3 with J and x each split into hi + lo parts: within the 1e-2 bar
