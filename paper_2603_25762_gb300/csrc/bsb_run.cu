@@ -42,11 +42,13 @@
 // separate instantiation (CHECK = true): the kernel without them carries none of their
 // code.
 //
-// Roles (352 threads): warp 0 = TMA producer (six lanes), warp 1 = MMA issuer (one
+// Roles (384 threads): warp 0 = TMA producer (six lanes), warp 1 = MMA issuer (one
 // thread), warps 2-9 = epilogue (TMEM lane quarter = warp % 4 = 32 vertices, two warps
-// per quarter split the 128 replicas), warp 10 = signal.  With JRES the J tiles of the CTA's
-// single row tile stay in shared memory for the whole launch and only X_hat
-// streams; otherwise J and X_hat K-slices stream through the ring together.
+// per quarter split the 128 replicas), warp 10 = signal, warp 11 = J producer.  With JRES
+// the J tiles of the CTA's single row tile stay in shared memory for the whole launch and
+// only X_hat streams.  Otherwise J and X_hat K-slices stream through the ring: copied
+// together by warp 0, or (jsplit: the kernel without checks, rows wider than the ring)
+// J by warp 11 as soon as a slot frees, X_hat by warp 0 once its release is seen.
 #include <algorithm>
 #include <vector>
 
@@ -60,8 +62,9 @@ namespace {
 constexpr int RB = 128;          // replicas per item (MMA N)
 constexpr int MAX_ITEMS = 4;     // 4 items x 128 TMEM columns = 512
 constexpr int EPI_WARPS = 8;
-constexpr int RUN_THREADS = 32 * (3 + EPI_WARPS);
+constexpr int RUN_THREADS = 32 * (4 + EPI_WARPS);
 constexpr int SIGNAL_WARP = 2 + EPI_WARPS;
+constexpr int JPROD_WARP = SIGNAL_WARP + 1;  // J K-slices into their own ring (stream mode)
 constexpr uint32_t SLICE = TILE * 64 * 2;  // a 128 x 64 BF16 K-slice (16 KB)
 constexpr int JRES_TILES = 4;              // resident J tiles (hi + lo entries) per CTA
 
@@ -81,8 +84,9 @@ struct RunSmem {
   static constexpr uint32_t SLOT = JRES ? SLICE : 2 * SLICE;    // X_hat (+ J) per slot
   static constexpr uint32_t RING_OFF = JRES ? JRES_TILES * 2 * SLICE : 0;
   static constexpr uint32_t BAR_OFF = RING_OFF + ST * SLOT;
-  // full, empty (ring); accf, edone, decision (per item); jbar, drain, sfull, sfree
-  static constexpr int N_BARS = 2 * ST + 3 * MAX_ITEMS + 4;
+  // full (X_hat), empty, full (J) (ring); accf, edone, decision (per item); jbar, drain,
+  // sfull, sfree
+  static constexpr int N_BARS = 3 * ST + 3 * MAX_ITEMS + 4;
   static constexpr uint32_t INFO_OFF = BAR_OFF + 8 * N_BARS;
   static constexpr uint32_t STOP_OFF = INFO_OFF + sizeof(ItemInfo) * MAX_ITEMS;
   static constexpr uint32_t BYTES = STOP_OFF + 4 * MAX_ITEMS + 16 + 1024;
@@ -104,6 +108,7 @@ struct RunArgs {
                             // [n_blocks][n_kt] items finished; zero at launch
   const int32_t* rows_b;    // [n_blocks] row tiles per block
   int32_t group_sync;       // hand-off mode: 0 = tile, 1 = group
+  int32_t jsplit;           // stream mode without checks: J K-slices copied by their own warp
   const int2* work;         // [grid] {first position, item count} in the wave's item list
   const int32_t* items;     // the wave's items (row tile * n_kt + replica tile)
   int32_t item_stride;      // a CTA's items sit at positions first, first + stride, ...
@@ -430,6 +435,10 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
               const __grid_constant__ CUtensorMap tmS1, RunArgs a) {
   using L = RunSmem<JRES>;
   constexpr int ST = L::ST;
+  // J K-slices in a ring of their own, filled by the J producer warp (stream mode without
+  // checks, chosen by the host when row tiles span more K-slices than the ring holds);
+  // otherwise the TMA producer copies J and X_hat of a K-slice together
+  const bool jsplit = !JRES && !CHECK && a.jsplit != 0;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -438,7 +447,8 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
   __shared__ uint32_t tmem_slot;
   __shared__ int32_t abort_s;
   volatile int32_t* abort_flag = &abort_s;
-  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * ST, accf0 = empty0 + 8 * ST,
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * ST, fullj0 = empty0 + 8 * ST,
+                 accf0 = fullj0 + 8 * ST,
                  edone0 = accf0 + 8 * MAX_ITEMS, decb0 = edone0 + 8 * MAX_ITEMS,
                  jbar = decb0 + 8 * MAX_ITEMS, drain = jbar + 8, sfull = drain + 8,
                  sfree = sfull + 8;
@@ -481,6 +491,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
     for (int s = 0; s < ST; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
+      mbar_init(fullj0 + 8 * s, 1);
     }
     for (int i = 0; i < MAX_ITEMS; ++i) {
       mbar_init(accf0 + 8 * i, 1);
@@ -605,10 +616,10 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
                   if (pass == 0 && kb == 0) trace_at(a, u, i, TR_SLOT);
                   if (pass == 0 && kb >= 1 && kb <= 5) trace_at(a, u, i, TR_SLOT1 + kb - 1);
                   uint8_t* slot = smem + L::RING_OFF + s * L::SLOT;
-                  mbar_expect_tx(full0 + 8 * s, L::SLOT);
+                  mbar_expect_tx(full0 + 8 * s, jsplit ? SLICE : L::SLOT);
                   const uint32_t xdst = JRES ? smem_u32(slot) : smem_u32(slot + SLICE);
                   tma_load_2d(xdst, mp, full0 + 8 * s, ct * TILE + half * 64, it.k * RB);
-                  if (!JRES)
+                  if (!JRES && !jsplit)
                     tma_load_2d(smem_u32(slot), &tmJ, full0 + 8 * s, half * 64,
                                 (it.tile_begin + e) * TILE);
                 }
@@ -668,6 +679,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
               const int s = (int)(q % ST);
               const uint32_t ph = (q / ST) & 1u;
               if (!(ok = rwait(full0 + 8 * s, ph, a.err, abort_flag))) break;
+              if (jsplit && !(ok = rwait(fullj0 + 8 * s, ph, a.err, abort_flag))) break;
               tc_fence_after();
               if (pass == 0 && kb == 0) trace_at(a, u, i, TR_FIRST_OP);
               uint8_t* slot = smem + L::RING_OFF + s * L::SLOT;
@@ -912,6 +924,48 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
       }
       cur = nxt;
     }
+  } else if (warp == JPROD_WARP) {
+    // ------------------------------------------------------------ J producer
+    // Stream mode without checks, when the host asks for it: the J K-slices depend on no
+    // other CTA, so they go into a ring of their own as soon as the MMAs free a slot,
+    // ahead of the X_hat copies that wait for the neighbours' releases.  The warp walks the MMA issuer's sequence of
+    // (step, item, K-slice), lanes 0 .. ST-1 one K-slice each.  Lane s < ST keeps the
+    // latest use of ring slot s, so that the copies still in flight land before the exit.
+    if (jsplit && n_items > 0) {
+      uint32_t q = 0;
+      int32_t last_use = -1;
+      bool ok = true;
+      for (int u = 0; ok && u < n_steps; ++u) {
+        const int t = a.t0 + u;
+        for (int i = 0; ok && i < n_items; ++i) {
+          const ItemInfo& it = info[i];
+          if (t > it.last_t) continue;
+          for (int kb0 = 0; ok && kb0 < it.nk; kb0 += ST) {
+            const int kb = kb0 + lane;
+            const bool mine = lane < ST && kb < it.nk;
+            bool lok = true;
+            if (mine) {
+              const int s = (int)((q + kb) % ST);
+              const uint32_t ph = ((q + kb) / ST) & 1u;
+              lok = rwait(empty0 + 8 * s, ph ^ 1u, a.err, abort_flag);
+              if (lok) {
+                mbar_expect_tx(fullj0 + 8 * s, SLICE);
+                tma_load_2d(smem_u32(smem + L::RING_OFF + s * L::SLOT), &tmJ, fullj0 + 8 * s,
+                            (kb & 1) * 64, (it.tile_begin + (kb >> 1)) * TILE);
+              }
+            }
+            const uint32_t issued = __ballot_sync(0xffffffffu, mine && lok);
+            if (lane < ST) {  // this round's use of slot `lane`, if it was issued
+              const int kbs = kb0 + (int)(((uint32_t)lane + 2u * ST - (q + kb0) % ST) % ST);
+              if ((issued >> (kbs - kb0)) & 1u) last_use = (int32_t)(q + kbs);
+            }
+            if (!__all_sync(0xffffffffu, !mine || lok)) ok = false;
+          }
+          q += (uint32_t)it.nk;
+        }
+      }
+      if (last_use >= 0) mbar_wait(fullj0 + 8 * lane, ((uint32_t)last_use / ST) & 1u, a.err);
+    }
   } else {
     // ------------------------------------------------------------ signal
     // After the epilogue of an item, release its X_hat_{t+1} to the other CTAs.
@@ -1090,6 +1144,14 @@ qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo,
   const int n_kt = R / RB;
   rb->jres = run_jres(variant);
   rb->group_sync = run_group(variant);
+  // J copies run ahead in their own ring when most row tiles span more K-slices (2 per
+  // stored tile entry) than the operand ring holds: the copies of their later K-slices
+  // wait for ring slots, and without the split the J copies wait with them.  Rows that
+  // fit the ring measured slower with the split (one more wait per K-slice).
+  int64_t wide = 0;
+  for (const RowTile& rt : g.h_rt)
+    if (2 * (use_lo ? rt.n_all : rt.n_hi) > RunSmem<false>::ST) ++wide;
+  rb->jsplit = 2 * wide > (int64_t)g.h_rt.size();
   rb->waves = plan.waves;
   std::vector<int32_t> rows(std::max(g.n_blocks, 1), 0);
   for (const RowTile& rt : g.h_rt) rows[rt.block] += 1;
@@ -1141,6 +1203,7 @@ qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const Run
   a.work = rb.work;
   a.rows_b = rb.rows_b;
   a.group_sync = rb.group_sync ? 1 : 0;
+  a.jsplit = (!JRES && chk == nullptr && rb.jsplit) ? 1 : 0;
   a.n_pad = s.n_pad;
   a.n_kt = s.R / RB;
   a.n_blocks = g.n_blocks;

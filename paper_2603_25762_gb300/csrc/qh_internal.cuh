@@ -399,6 +399,7 @@ struct RunBufs {
   int64_t n_done = 0;
   bool jres = false;
   bool group_sync = false;
+  bool jsplit = false;  // stream mode: J K-slices in a ring of their own (rows of > 6 slices)
 };
 bool run_variant(int v);
 // mask (n_blocks flags, or nullptr = every block): blocks left out take no items
