@@ -200,6 +200,35 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[16]) {
                :
                : "memory");
 }
+// The same for FP32 values (x of an item kept in TMEM): .b32 TMEM accesses take any
+// 32-bit register.  The loads are ordered with the other TMEM accesses (volatile).
+__device__ __forceinline__ void tmem_ld16f(uint32_t taddr, float (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
+        "=f"(v[7]), "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]),
+        "=f"(v[14]), "=f"(v[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld_f(float (&v)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]),
+                 "+f"(v[6]), "+f"(v[7]), "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]),
+                 "+f"(v[12]), "+f"(v[13]), "+f"(v[14]), "+f"(v[15])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st16f(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]),
+      "f"(v[8]), "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]),
+      "f"(v[15])
+      : "memory");
+}
 __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -428,7 +457,7 @@ __device__ __forceinline__ bool check_energy(
   return true;
 }
 
-template <bool JRES, int SB, bool CHECK>
+template <bool JRES, int SB, bool CHECK, bool XT>
 __global__ void __launch_bounds__(RUN_THREADS, 1)
     k_bsb_run(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmX0,
               const __grid_constant__ CUtensorMap tmX1, const __grid_constant__ CUtensorMap tmS0,
@@ -728,7 +757,14 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
     auto quad0 = [&](const ItemInfo& it, int chunk) -> uint32_t {
       return (uint32_t)(it.k * (RB / 4) + hh * 16 + chunk * 4) * np + (uint32_t)(it.row0 + r);
     };
-    // y -> y / (dt c0) into the item's TMEM columns; x into the blocked working copy
+    // XT (kernel without checks, waves of at most three items per CTA): the TMEM columns
+    // that no accumulator uses hold x of the first items, item i when i + n_items <= 3, at
+    // columns (n_items + i) * 128 (one item of three, two of two, one of one).  The others
+    // keep x in the blocked working copy.  A separate instantiation: the branches cost
+    // waves of four-item CTAs about 3% of their step time.
+    auto xt = [&](int i) { return XT && i + n_items <= 3; };
+    auto xt_col = [&](int i) { return lane_base + (uint32_t)((n_items + i) * RB); };
+    // y -> y / (dt c0) into the item's TMEM columns; x into TMEM or the working copy
     for (int i = 0; i < n_items; ++i) {
       const ItemInfo it = info[i];
       if (a.t0 > it.last_t) continue;
@@ -744,11 +780,14 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
           v[j] = vr ? __float_as_uint(yc[j * np] * it.inv_dtc0) : 0u;
           xv[j] = vr ? xc[j * np] : 0.f;
         }
-        float4* qc = a.xq + quad0(it, c);
+        if (!xt(i)) {
+          float4* qc = a.xq + quad0(it, c);
 #pragma unroll
-        for (int m = 0; m < 4; ++m)
-          qc[m * np] = make_float4(xv[4 * m], xv[4 * m + 1], xv[4 * m + 2], xv[4 * m + 3]);
+          for (int m = 0; m < 4; ++m)
+            qc[m * np] = make_float4(xv[4 * m], xv[4 * m + 1], xv[4 * m + 2], xv[4 * m + 3]);
+        }
         __syncwarp();
+        if (xt(i)) tmem_st16f(xt_col(i) + (uint32_t)(c * 16), xv);
         tmem_st16(lane_base + (uint32_t)(i * RB + c * 16), v);
       }
       tmem_wait_st();
@@ -780,9 +819,10 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
     bool fresh = true;  // xb holds nothing for the cursor's item yet
     while (cur.u < n_steps) {
       if (fresh) {
-        load_x(xb[0], nit, true, 0);
-        load_x(xb[1], nit, true, 1);
-        load_x(xb[2], nit, true, 2);
+        const bool gx = !xt(cur.i);
+        load_x(xb[0], nit, gx, 0);
+        load_x(xb[1], nit, gx, 1);
+        load_x(xb[2], nit, gx, 2);
         fresh = false;
       }
       if (decision_step<CHECK>(a, a.t0 + cur.u, nit.steps_b)) {
@@ -803,7 +843,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
       const ItemInfo it = nit;  // registers: the loop's stores cannot alias it
       const int t = a.t0 + cur.u;
       const Cursor nxt = next_live(cur, info, n_items, a.t0, n_steps, dead);
-      const bool non = nxt.u < n_steps;
+      const bool non = nxt.u < n_steps, gxn = non && !xt(nxt.i);
       // a check step: the energy of S_t after the update; the step before a check step
       // writes S_{t+1}
       const bool chk = check_step<CHECK>(a, t, it.steps_b), wchk = check_step<CHECK>(a, t + 1, it.steps_b);
@@ -827,23 +867,35 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
       tc_fence_after();
       if (warp == 2 && lane == 0) trace_at(a, cur.u, cur.i, TR_EPI_START);
       const uint32_t col0 = lane_base + (uint32_t)(cur.i * RB);
+      const bool xti = xt(cur.i);
+      const uint32_t xcol = xt_col(cur.i);
       uint32_t va[16], vb[16];
       __syncwarp();
+      if (xti) {  // x of all four chunks from TMEM, awaited with the first product chunk
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tmem_ld16f(xcol + (uint32_t)(c * 16), xb[c]);
+      }
       tmem_ld16_async(col0, va);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         uint32_t(&v)[16] = (c & 1) ? vb : va;
         uint32_t(&vn)[16] = (c & 1) ? va : vb;
         tmem_wait_ld(v);
+        if (c == 0 && xti) {  // nothing is in flight now: these waits return at once
+          tmem_wait_ld_f(xb[0]);
+          tmem_wait_ld_f(xb[1]);
+          tmem_wait_ld_f(xb[2]);
+          tmem_wait_ld_f(xb[3]);
+        }
         if (c < 3) {
           __syncwarp();
           tmem_ld16_async(col0 + (uint32_t)((c + 1) * 16), vn);
         }
         // chunk c + 3 of the sequence: chunk 3 of this item, else 0..2 of the next
         if (c == 0)
-          load_x(xb[3], it, true, 3);
+          load_x(xb[3], it, !xti, 3);
         else
-          load_x(xb[c - 1], nit, non, c - 1);
+          load_x(xb[c - 1], nit, gxn, c - 1);
         const uint32_t e0 = elem0(it, c);
         float* xc = xs + e0;
         float* yc = ys + e0;
@@ -880,9 +932,11 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
 #pragma unroll
           for (int j = 0; j < 16; ++j) hc[j * np] = __float2bfloat16_rn(sb_operand(SB, xo[j]));
           if (!last) {
+            if (!xti) {
 #pragma unroll
-            for (int m = 0; m < 4; ++m)
-              qc[m * np] = make_float4(xo[4 * m], xo[4 * m + 1], xo[4 * m + 2], xo[4 * m + 3]);
+              for (int m = 0; m < 4; ++m)
+                qc[m * np] = make_float4(xo[4 * m], xo[4 * m + 1], xo[4 * m + 2], xo[4 * m + 3]);
+            }
           } else {  // the launch's last step: state back into the solver's layout
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -893,6 +947,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
         }
         if (!last) {
           __syncwarp();
+          if (xti) tmem_st16f(xcol + (uint32_t)(c * 16), xo);
           tmem_st16(col0 + (uint32_t)(c * 16), out);
         }
       }
@@ -1117,6 +1172,7 @@ bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, RunPlan
       w.stride = (int)grid;
     }
     w.grid = (int)p.work.size() - w.work_off;
+    for (int c = w.work_off; c < (int)p.work.size(); ++c) w.max_items = std::max(w.max_items, p.work[c].y);
     p.waves.push_back(w);
   };
   std::vector<int32_t> rows;
@@ -1249,8 +1305,12 @@ qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const Run
     cfg.numAttrs = 1;
     note_launch(1);
     cudaError_t e =
-        chk ? cudaLaunchKernelEx(&cfg, k_bsb_run<JRES, SB, true>, mJ, mX0, mX1, mS0, mS1, a)
-            : cudaLaunchKernelEx(&cfg, k_bsb_run<JRES, SB, false>, mJ, mX0, mX1, mS0, mS1, a);
+        chk         ? cudaLaunchKernelEx(&cfg, k_bsb_run<JRES, SB, true, false>, mJ, mX0, mX1, mS0,
+                                         mS1, a)
+        : w.max_items <= 3
+            ? cudaLaunchKernelEx(&cfg, k_bsb_run<JRES, SB, false, true>, mJ, mX0, mX1, mS0, mS1, a)
+            : cudaLaunchKernelEx(&cfg, k_bsb_run<JRES, SB, false, false>, mJ, mX0, mX1, mS0, mS1,
+                                 a);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_bsb_run launch");
   }
   return QH_OK;
@@ -1283,12 +1343,15 @@ int run_item_mask() { return 0x7fffffff; }
 
 template <bool JRES, int SB>
 static cudaError_t run_attr() {
-  cudaError_t e = cudaFuncSetAttribute(k_bsb_run<JRES, SB, false>,
+  cudaError_t e = cudaFuncSetAttribute(k_bsb_run<JRES, SB, false, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)RunSmem<JRES>::BYTES);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_bsb_run<JRES, SB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)RunSmem<JRES>::BYTES);
+    e = cudaFuncSetAttribute(k_bsb_run<JRES, SB, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RunSmem<JRES>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_bsb_run<JRES, SB, true, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RunSmem<JRES>::BYTES);
   return e;
 }
 

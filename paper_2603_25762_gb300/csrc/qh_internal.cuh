@@ -383,6 +383,7 @@ struct RunWave {              // one launch: whole blocks whose items fit on chi
   int item_off = 0;           // first entry of the wave in RunBufs::items
   int grid = 0;               // CTAs
   int stride = 1;             // a CTA's items: first, first + stride, ...
+  int max_items = 0;          // most items of one CTA
 };
 struct RunPlan {
   std::vector<int2> work;     // per CTA of every wave: {first position, item count}
