@@ -219,7 +219,8 @@ qh_status autotune(Ctx* ctx, const Graph& g, StepArgs a, const SolveBufs& B, int
     p.variant = v;
     RunBufs rb;
     if (run_variant(v)) {
-      qh_status st = run_prepare(ctx, g, R, v, a.use_lo != 0, &rb);
+      qh_status st = run_prepare(ctx, g, R, v, a.use_lo != 0, &rb, nullptr,
+                                 run_items(g, R, ctx->n_sm, v, a.use_lo != 0));
       if (st != QH_OK) return st;
     }
     float ms = 0.f;
@@ -795,7 +796,10 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
   RunCheck chk;
   if (multistep) {
     qh_status st = run_prepare(ctx, W, R, tplan.variant, a.use_lo != 0, &rb,
-                               sel ? &sel_mask : nullptr, fused ? 3 : 4);
+                               sel ? &sel_mask : nullptr,
+                               fused ? 3
+                                     : run_items(W, R, ctx->n_sm, tplan.variant, a.use_lo != 0,
+                                                 sel ? &sel_mask : nullptr));
     if (st != QH_OK) return st;
   }
   if (fused) {

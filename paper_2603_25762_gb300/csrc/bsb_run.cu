@@ -1192,6 +1192,20 @@ bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, RunPlan
   return true;
 }
 
+// Items per CTA for a solve: three or four, whichever gives the fewer step-periods of
+// waves.  A CTA runs its items' epilogues one after another, so four items make the step
+// period epilogue-bound: measured on batched-blocks (R = 256, 11,048 items), 13.5 µs per
+// step at four items per CTA (20 waves) against 9.44 µs at three (27 waves, x of one item
+// in TMEM), a ratio of 0.70.  Three items win unless they need more than 1/0.70 times
+// the waves (a graph that fits one wave at four but not at three keeps four).
+int run_items(const Graph& g, int R, int n_sm, int variant, bool use_lo,
+              const std::vector<int32_t>* mask) {
+  RunPlan p3, p4;
+  if (!run_plan(g, R, n_sm, variant, use_lo, &p3, mask, 3)) return MAX_ITEMS;
+  if (!run_plan(g, R, n_sm, variant, use_lo, &p4, mask, MAX_ITEMS)) return 3;
+  return 100 * (int64_t)p3.waves.size() <= 143 * (int64_t)p4.waves.size() ? 3 : MAX_ITEMS;
+}
+
 qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo, RunBufs* rb,
                       const std::vector<int32_t>* mask, int max_items) {
   RunPlan plan;

@@ -407,6 +407,9 @@ bool run_variant(int v);
 // max_items: items per CTA at most (run_max_items(), or 3 for checks inside the launch)
 bool run_plan(const Graph& g, int R, int n_sm, int variant, bool use_lo, RunPlan* plan,
               const std::vector<int32_t>* mask = nullptr, int max_items = 4);
+// items per CTA (3 or 4) that minimise the waves' step periods (see bsb_run.cu)
+int run_items(const Graph& g, int R, int n_sm, int variant, bool use_lo,
+              const std::vector<int32_t>* mask = nullptr);
 qh_status run_prepare(Ctx* ctx, const Graph& g, int R, int variant, bool use_lo, RunBufs* rb,
                       const std::vector<int32_t>* mask = nullptr, int max_items = 4);
 // Early-stop checks inside one multi-step launch over steps 0 .. t1 (integer weights;
