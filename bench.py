@@ -237,14 +237,15 @@ def cpu_baseline(args, fr, mode, steps, seed=1, reps=None):
             "sample": f"{what}, {reps} replicas x {steps} steps, whole path, {dt:.1f} s"}, res
 
 
-def _profiled(kernel):
+def _profiled(kernel, workload="hifi-region"):
     """DRAM bytes per launch and the utilisation counters from the committed ncu summary
-    of the kernel, or None once the kernel (its variant or its source file) differs from
-    the one that was profiled."""
+    of the kernel on this workload, or None when there is none or the kernel (its variant
+    or its source file) differs from the one that was profiled."""
     import hashlib
     multistep = kernel.startswith("multistep")
-    path = os.path.join(ROOT, "profiles", "multistep_kernel_hifi_region.md" if multistep
-                        else "step_kernel_hifi_region.md")
+    wl = workload.replace("-", "_")
+    path = os.path.join(ROOT, "profiles", f"multistep_kernel_{wl}.md" if multistep
+                        else f"step_kernel_{wl}.md")
     src = os.path.join(ROOT, "paper_2603_25762_gb300", "csrc",
                        "bsb_run.cu" if multistep else "bsb_tc.cu")
     if not os.path.exists(path):
@@ -324,8 +325,9 @@ def other_workloads(args):
             "ms_per_step": d["ms_per_step"], "value": d["value"], "unit": d["unit"],
             "e2e": d["e2e"], "breakdown_ms": d["breakdown_ms"],
             "roofline": {k: rf[k] for k in ("bound", "kernel", "achieved", "peak", "unit",
-                                            "frac", "avg_launch_us", "launches_per_step",
-                                            "bytes_per_spin_update", "tensor")},
+                                            "frac", "traffic", "avg_launch_us",
+                                            "launches_per_step", "bytes_per_spin_update",
+                                            "tensor", "ncu")},
             "quality": {k: q[k] for k in ("best_cut_sum", "truth_cut", "best_over_truth",
                                           "switch_error", "hamming_error", "n50_bp")},
             "vs_fp32": {k: v.get(k) for k in ("fp32_ms_per_step", "fp32_kernel", "speedup",
@@ -523,7 +525,7 @@ def run_ours(args):
     per_launch = units / n_launch  # spin updates of one launch
     achieved = per_launch * b_unit / (launch_us * 1e-6) / 1e9
     achieved_tf = per_launch * f_unit / (launch_us * 1e-6) / 1e12
-    prof = _profiled(kname) if args.workload == "hifi-region" else None
+    prof = _profiled(kname, args.workload)
     h2d = sum(int(a.nbytes) for a in pinned_np[1:])
     d2h = fr.n_snps * (1 + 1 + 4) + 8
     line = {

@@ -69,6 +69,13 @@ def test_profiled_traffic_tracks_kernel_source(bench, tmp_path, monkeypatch):
     assert bench._profiled("multistep-jres-group") is None  # another variant
     (src / "bsb_run.cu").write_text("// kernel v2\n")
     assert bench._profiled("multistep-stream-tile") is None  # source changed
+    assert bench._profiled("multistep-stream-tile", "ont-snp") is None  # no summary
+    (src / "bsb_run.cu").write_text("// kernel v1\n")
+    (prof / "multistep_kernel_ont_snp.md").write_text(
+        f"kernel: multistep-stream-tile\nsource_sha256_16: {sha}\n"
+        "traffic_bytes_per_launch: 99\n")
+    assert bench._profiled("multistep-stream-tile", "ont-snp")["traffic"] == 99
+    assert bench._profiled("multistep-stream-tile")["traffic"] == 1234
 
 
 def test_spin_update_work_follows_the_measurement_model(bench):
