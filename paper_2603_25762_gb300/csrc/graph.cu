@@ -612,24 +612,36 @@ __global__ void k_tile_flags(int32_t n, const int64_t* __restrict__ rp, const in
 // Padded CSR of J = -w: rows in padded order, columns as padded indices.
 __global__ void k_pcsr_count(int32_t n, const int64_t* __restrict__ rp, const double* __restrict__ w,
                              const int32_t* __restrict__ pad_index, int64_t* cnt) {
-  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= n || pad_index[a] < 0) return;
+  const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;  // warp per vertex
+  const int lane = threadIdx.x & 31;
+  if (a >= n || pad_index[a] < 0) return;  // warp-uniform
   int64_t c = 0;
-  for (int64_t e = rp[a]; e < rp[a + 1]; ++e) c += w[e] != 0.0;
-  cnt[pad_index[a]] = c;
+  const int64_t e1 = rp[a + 1];
+  for (int64_t e0 = rp[a]; e0 < e1; e0 += 32)
+    c += __popc(__ballot_sync(0xffffffffu, e0 + lane < e1 && w[e0 + lane] != 0.0));
+  if (lane == 0) cnt[pad_index[a]] = c;
 }
 
+// Warp per vertex: the lanes take 32 entries of the row at a time and write its nonzeros
+// in row order (a ballot gives each lane its place among them), so the stores coalesce.
 __global__ void k_pcsr_fill(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                             const double* __restrict__ w, const int32_t* __restrict__ pad_index,
                             const int64_t* __restrict__ prow, int32_t* pcol, float* pval) {
-  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= n || pad_index[a] < 0) return;
+  const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (a >= n || pad_index[a] < 0) return;  // warp-uniform
   int64_t o = prow[pad_index[a]];
-  for (int64_t e = rp[a]; e < rp[a + 1]; ++e) {
-    if (w[e] == 0.0) continue;
-    if (pcol != nullptr) pcol[o] = pad_index[col[e]];
-    pval[o] = (float)(-w[e]);
-    ++o;
+  const int64_t e1 = rp[a + 1];
+  for (int64_t e0 = rp[a]; e0 < e1; e0 += 32) {
+    const int64_t e = e0 + lane;
+    const double wv = e < e1 ? w[e] : 0.0;
+    const uint32_t nz = __ballot_sync(0xffffffffu, wv != 0.0);
+    if (wv != 0.0) {
+      const int64_t q = o + __popc(nz & ((1u << lane) - 1u));
+      if (pcol != nullptr) pcol[q] = pad_index[col[e]];
+      pval[q] = (float)(-wv);
+    }
+    o += __popc(nz);
   }
 }
 
@@ -637,36 +649,58 @@ __global__ void k_pcsr_fill(int32_t n, const int64_t* __restrict__ rp, const int
 // when the column tile of u is the row tile of v or one of its two neighbours.
 __device__ __forceinline__ int band_offset(int32_t v, int32_t u) { return u / TILE - v / TILE; }
 
+// The band / remainder kernels below run a warp per vertex, the lanes taking 32 entries
+// of the row at a time; the remainder keeps the row order through a ballot.
 __global__ void k_rem_count(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                             const double* __restrict__ w, const int32_t* __restrict__ pad_index,
                             int64_t* cnt) {
-  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= n || pad_index[a] < 0) return;
+  const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (a >= n || pad_index[a] < 0) return;  // warp-uniform
   const int32_t v = pad_index[a];
   int64_t c = 0;
-  for (int64_t e = rp[a]; e < rp[a + 1]; ++e) {
-    if (w[e] == 0.0) continue;
-    const int d = band_offset(v, pad_index[col[e]]);
-    c += d < -1 || d > 1;
+  const int64_t e1 = rp[a + 1];
+  for (int64_t e0 = rp[a]; e0 < e1; e0 += 32) {
+    const int64_t e = e0 + lane;
+    bool rem = false;
+    if (e < e1 && w[e] != 0.0) {
+      const int d = band_offset(v, pad_index[col[e]]);
+      rem = d < -1 || d > 1;
+    }
+    c += __popc(__ballot_sync(0xffffffffu, rem));
   }
-  cnt[v] = c;
+  if (lane == 0) cnt[v] = c;
 }
 
 __global__ void k_rem_fill(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                            const double* __restrict__ w, const int32_t* __restrict__ pad_index,
                            const int64_t* __restrict__ rrow, int32_t* rcol, float* rval) {
-  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= n || pad_index[a] < 0) return;
+  const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (a >= n || pad_index[a] < 0) return;  // warp-uniform
   const int32_t v = pad_index[a];
   int64_t o = rrow[v];
-  for (int64_t e = rp[a]; e < rp[a + 1]; ++e) {
-    if (w[e] == 0.0) continue;
-    const int32_t u = pad_index[col[e]];
-    const int d = band_offset(v, u);
-    if (d >= -1 && d <= 1) continue;
-    if (rcol != nullptr) rcol[o] = u;
-    rval[o] = (float)(-w[e]);
-    ++o;
+  const int64_t e1 = rp[a + 1];
+  for (int64_t e0 = rp[a]; e0 < e1; e0 += 32) {
+    const int64_t e = e0 + lane;
+    bool rem = false;
+    int32_t u = 0;
+    double wv = 0.0;
+    if (e < e1) {
+      wv = w[e];
+      if (wv != 0.0) {
+        u = pad_index[col[e]];
+        const int d = band_offset(v, u);
+        rem = d < -1 || d > 1;
+      }
+    }
+    const uint32_t m = __ballot_sync(0xffffffffu, rem);
+    if (rem) {
+      const int64_t q = o + __popc(m & ((1u << lane) - 1u));
+      if (rcol != nullptr) rcol[q] = u;
+      rval[q] = (float)(-wv);
+    }
+    o += __popc(m);
   }
 }
 
@@ -674,10 +708,11 @@ __global__ void k_rem_fill(int32_t n, const int64_t* __restrict__ rp, const int3
 __global__ void k_band_fill(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                             const double* __restrict__ w, const int32_t* __restrict__ pad_index,
                             __nv_bfloat16* band) {
-  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (a >= n || pad_index[a] < 0) return;
   const int32_t v = pad_index[a];
-  for (int64_t e = rp[a]; e < rp[a + 1]; ++e) {
+  for (int64_t e = rp[a] + lane; e < rp[a + 1]; e += 32) {
     if (w[e] == 0.0) continue;
     const int32_t u = pad_index[col[e]];
     const int d = band_offset(v, u);
@@ -689,6 +724,8 @@ __global__ void k_band_fill(int32_t n, const int64_t* __restrict__ rp, const int
 
 // Tile fill (also used after a refinement sign inversion): J = -w into the
 // FP32 tiles and the BF16 hi (+ lo remainder) tiles.
+// Warp per vertex, the lanes striding over the row: neighbouring entries of a row land
+// in neighbouring columns of a tile row, so the stores of a warp coalesce.
 __global__ void k_tile_fill(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                             const double* __restrict__ w, const int32_t* __restrict__ block_of,
                             const int32_t* __restrict__ local, const int64_t* __restrict__ slot_off,
@@ -696,7 +733,8 @@ __global__ void k_tile_fill(int32_t n, const int64_t* __restrict__ rp, const int
                             const int64_t* __restrict__ slot_tile, const RowTile* __restrict__ rt,
                             const int32_t* __restrict__ rt_of_block, int has_lo,
                             __nv_bfloat16* tb, float* tf) {
-  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (a >= n) return;
   int32_t b = block_of[a];
   if (b < 0) return;
@@ -704,7 +742,7 @@ __global__ void k_tile_fill(int32_t n, const int64_t* __restrict__ rp, const int
   int32_t la = local[a];
   int32_t ra = la / TILE;
   const RowTile& r = rt[rt_of_block[b] + ra];
-  for (int64_t e = rp[a]; e < rp[a + 1]; ++e) {
+  for (int64_t e = rp[a] + lane; e < rp[a + 1]; e += 32) {
     double wv = w[e];
     if (wv == 0.0) continue;
     int32_t lb = local[col[e]];
@@ -1107,7 +1145,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     if (!pcnt || !g->prow_ptr) return set_err(ctx, QH_ENOMEM, "allocation failed (padded CSR)");
     QH_CUDA_TRY(cudaMemsetAsync(pcnt, 0, sizeof(int64_t) * (g->n_pad + 1), s));
     if (N > 0)
-      k_pcsr_count<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->w, g->pad_index, pcnt);
+      k_pcsr_count<<<::qh::counted(nblk((int64_t)N * 32)), 256, 0, s>>>(N, g->row_ptr, g->w, g->pad_index, pcnt);
     if (!scan_i64(ctx, s, pcnt, g->prow_ptr, g->n_pad)) return set_err(ctx, QH_ENOMEM, "allocation failed (scan)");
     int64_t pnnz = 0;
     QH_CUDA_TRY(cudaMemcpyAsync(&pnnz, g->prow_ptr + g->n_pad, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -1117,7 +1155,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     g->pval = (float*)dalloc(*g, sizeof(float) * std::max<int64_t>(pnnz, 1));
     if (!g->pcol || !g->pval) return set_err(ctx, QH_ENOMEM, "allocation failed (padded CSR)");
     if (N > 0)
-      k_pcsr_fill<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, g->pad_index,
+      k_pcsr_fill<<<::qh::counted(nblk((int64_t)N * 32)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, g->pad_index,
                                                          g->prow_ptr, g->pcol, g->pval);
   }
   // CSR mode: band tiles and the remainder CSR
@@ -1129,7 +1167,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     if (!rcnt || !g->rrow_ptr || !g->band) return set_err(ctx, QH_ENOMEM, "allocation failed (band)");
     QH_CUDA_TRY(cudaMemsetAsync(rcnt, 0, sizeof(int64_t) * (g->n_pad + 1), s));
     if (N > 0)
-      k_rem_count<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, g->pad_index, rcnt);
+      k_rem_count<<<::qh::counted(nblk((int64_t)N * 32)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, g->pad_index, rcnt);
     if (!scan_i64(ctx, s, rcnt, g->rrow_ptr, g->n_pad)) return set_err(ctx, QH_ENOMEM, "allocation failed (scan)");
     int64_t rnnz = 0;
     QH_CUDA_TRY(cudaMemcpyAsync(&rnnz, g->rrow_ptr + g->n_pad, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -1139,7 +1177,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     g->rval = (float*)dalloc(*g, sizeof(float) * std::max<int64_t>(rnnz, 1));
     if (!g->rcol || !g->rval) return set_err(ctx, QH_ENOMEM, "allocation failed (band)");
     if (N > 0)
-      k_rem_fill<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, g->pad_index,
+      k_rem_fill<<<::qh::counted(nblk((int64_t)N * 32)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, g->pad_index,
                                                         g->rrow_ptr, g->rcol, g->rval);
     qh_status st = reband(ctx, g, g->w, g->band, nullptr);
     if (st != QH_OK) return st;
@@ -1179,11 +1217,11 @@ qh_status reband(Ctx* ctx, const Graph* g, const double* w, __nv_bfloat16* band,
   if (band != nullptr) {
     QH_CUDA_TRY(cudaMemsetAsync(band, 0, sizeof(__nv_bfloat16) * TILE * TILE * 3 * g->n_row_tiles, s));
     if (g->n_nodes > 0)
-      k_band_fill<<<::qh::counted(nblk(g->n_nodes)), 256, 0, s>>>(g->n_nodes, g->row_ptr, g->col, w,
+      k_band_fill<<<::qh::counted(nblk((int64_t)g->n_nodes * 32)), 256, 0, s>>>(g->n_nodes, g->row_ptr, g->col, w,
                                                                 g->pad_index, band);
   }
   if (rval != nullptr && g->n_nodes > 0)
-    k_rem_fill<<<::qh::counted(nblk(g->n_nodes)), 256, 0, s>>>(g->n_nodes, g->row_ptr, g->col, w,
+    k_rem_fill<<<::qh::counted(nblk((int64_t)g->n_nodes * 32)), 256, 0, s>>>(g->n_nodes, g->row_ptr, g->col, w,
                                                              g->pad_index, g->rrow_ptr, nullptr, rval);
   QH_CUDA_TRY(cudaGetLastError());
   return QH_OK;
@@ -1192,7 +1230,7 @@ qh_status reband(Ctx* ctx, const Graph* g, const double* w, __nv_bfloat16* band,
 qh_status retile(Ctx* ctx, Graph* g, const double* w, __nv_bfloat16* tb, float* tf, float* pval) {
   cudaStream_t s = ctx->stream;
   if (pval != nullptr && g->n_nodes > 0)  // padded CSR values (pattern unchanged)
-    k_pcsr_fill<<<::qh::counted(nblk(g->n_nodes)), 256, 0, s>>>(g->n_nodes, g->row_ptr, g->col, w,
+    k_pcsr_fill<<<::qh::counted(nblk((int64_t)g->n_nodes * 32)), 256, 0, s>>>(g->n_nodes, g->row_ptr, g->col, w,
                                                               g->pad_index, g->prow_ptr, nullptr,
                                                               pval);
   if (g->n_tiles > 0)
@@ -1200,7 +1238,7 @@ qh_status retile(Ctx* ctx, Graph* g, const double* w, __nv_bfloat16* tb, float* 
   if (g->n_tiles_hi > 0)
     QH_CUDA_TRY(cudaMemsetAsync(tf, 0, sizeof(float) * TILE * TILE * g->n_tiles_hi, s));
   if (g->n_nodes > 0 && g->n_tiles > 0)
-    k_tile_fill<<<::qh::counted(nblk(g->n_nodes)), 256, 0, s>>>(g->n_nodes, g->row_ptr, g->col, w, g->block_of,
+    k_tile_fill<<<::qh::counted(nblk((int64_t)g->n_nodes * 32)), 256, 0, s>>>(g->n_nodes, g->row_ptr, g->col, w, g->block_of,
                                                  g->local, g->slot_off, g->tiles_per_block,
                                                  g->slot_tile, g->rt, g->rt_of_block,
                                                  g->has_lo ? 1 : 0, tb, tf);
