@@ -84,3 +84,10 @@ def test_spin_update_work_follows_the_measurement_model(bench):
     assert b == pytest.approx(18.0 + 52.8 * 2 / 1024) and f == pytest.approx(105.6)
     assert bench.kernel_bound("k_step_f32") == "alu"
     assert bench.kernel_bound("multistep-stream-tile") == "latency"
+
+
+def test_paper_context_speedups(bench):
+    # Table 1's HiFi row: QHap's SNP mode 45.278 s against HapCUT2's 858.700 s
+    sp = bench.paper_speedups()
+    assert sp["hifi"]["vs_hapcut2"] == 19.0 and sp["ont"]["vs_hapcut2"] == 20.2
+    assert sp["cycloneseq"]["vs_whatshap"] == 4.8
