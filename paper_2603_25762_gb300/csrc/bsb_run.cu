@@ -983,9 +983,10 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
     // ------------------------------------------------------------ J producer
     // Stream mode without checks, when the host asks for it: the J K-slices depend on no
     // other CTA, so they go into a ring of their own as soon as the MMAs free a slot,
-    // ahead of the X_hat copies that wait for the neighbours' releases.  The warp walks the MMA issuer's sequence of
-    // (step, item, K-slice), lanes 0 .. ST-1 one K-slice each.  Lane s < ST keeps the
-    // latest use of ring slot s, so that the copies still in flight land before the exit.
+    // ahead of the X_hat copies that wait for the neighbours' releases.  The warp walks
+    // the MMA issuer's sequence of (step, item, K-slice), lanes 0 .. ST-1 one K-slice
+    // each.  Lane s < ST keeps the latest use of ring slot s, so that the copies still in
+    // flight land before the exit.
     if (jsplit && n_items > 0) {
       uint32_t q = 0;
       int32_t last_use = -1;
