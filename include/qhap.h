@@ -259,6 +259,52 @@ qh_status qh_bsb_solve(qh_ctx* ctx, const qh_graph* g, const qh_bsb_opts* opts,
 qh_status qh_bsb_solve_blocks(qh_ctx* ctx, const qh_graph* g, const qh_bsb_opts* opts,
                               const int32_t* blocks, int32_t n_blocks, qh_solution** out);
 
+/* Checkpoint of the SNP refinement (SB algorithm solution, the refinement loop: flip
+ * counts C on the smaller subset, sign inversion of the edges crossing each solve's
+ * partition).  The state after a solve is what the next solve of the loop starts from;
+ * host arrays, caller-owned:
+ *  iterations_done : solves of the loop run over the graph so far (>= 1); the next
+ *                    solve's random draws are keyed by this iteration index
+ *  flips    int32[n_nodes] : C, the times each vertex was in the smaller subset
+ *                            (-1 for a vertex in no block or in an unsolved block)
+ *  gauge    int8[n_nodes]  : +1 / -1, the product of the partitions whose sign
+ *                            inversions the next solve's weights carry: its graph is
+ *                            w'_ab = g_a w_ab g_b (+1 outside the blocks)
+ *  refining int32[n_blocks]: 1 while the block's refinement goes on
+ *  solves   int32[n_blocks]: solves the block has run
+ *  deform   float[n_blocks]: the field strength of the block's next (deformed) solve,
+ *                            0 for none (qh_bsb_opts.deform_h)
+ *  tries    int32[n_blocks]: deformed re-solves the block has used */
+typedef struct {
+  int32_t iterations_done;
+  int32_t* flips;
+  int8_t* gauge;
+  int32_t* refining;
+  int32_t* solves;
+  float* deform;
+  int32_t* tries;
+} qh_refine_state;
+
+/* Save: write a SNP-mode solution's refinement state into the caller's arrays (every
+ * pointer non-NULL, lengths as above).  A solve with refine_max = k followed by
+ * qh_bsb_solve_resume with refine_max = K > k from this state gives the same flip
+ * counts, parity partition, final cuts and haplotypes as one solve with refine_max = K.
+ * Errors: QH_EINVAL (READ-mode solution, NULL pointer, a solution imported block by
+ * block). */
+qh_status qh_solution_refine_state(const qh_solution* sol, qh_refine_state* state);
+
+/* Resume: continue the SNP refinement of `g` from a saved state, for the solves
+ * iterations_done .. opts->refine_max - 1 (refine_max counts every solve of the loop,
+ * those before the checkpoint included), with the same options as the solve that made
+ * the state (replicas, steps, seed, precision, deform_h, ...).  The blocks that are no
+ * longer refining keep their flip counts.  The result is a solution as qh_bsb_solve
+ * returns it, except that qh_solution_cuts, the best replica and steps_run describe the
+ * first solve of this call.  Errors: as qh_bsb_solve; QH_EINVAL for a READ-mode graph,
+ * a NULL array, iterations_done < 1 or >= refine_max, a gauge value other than +-1, a
+ * negative count, or a deformation field in the state without opts->deform_h > 0. */
+qh_status qh_bsb_solve_resume(qh_ctx* ctx, const qh_graph* g, const qh_bsb_opts* opts,
+                              const qh_refine_state* state, qh_solution** out);
+
 /* Import one block's result into a solution, e.g. a block solved by another process
  * of a sharded run (host values as qh_solution_block returns them there).
  *  spins        : int8[block size], +1 / -1 in local vertex order (SNP mode: the

@@ -93,7 +93,7 @@ enum {
   S_STEPSB, S_C0, S_SEEN, S_STALL, S_STEPSRUN, S_SPINS, S_C, S_WWORK, S_TBWORK, S_TFWORK,
   S_SUMW, S_SUMJ2, S_NODETMP, S_SIGNS1, S_NODEVAL1, S_CUT1, S_DBG0, S_DBG1, S_DBG2, S_RUNNING,
   S_PVWORK, S_TR0, S_TR1, S_F8H, S_F8L, S_F8FLAG, S_X8, S_DEFORM, S_TRIES, S_DBGDEF,
-  S_ZBAND, S_BANDWORK, S_RVWORK, S_TRACE, S_KCUT, S_KR, S_KFLAG, S_KSPINS
+  S_ZBAND, S_BANDWORK, S_RVWORK, S_TRACE, S_KCUT, S_KR, S_KFLAG, S_KSPINS, S_GAUGE
 };
 
 struct SolveBufs {
@@ -112,6 +112,7 @@ struct SolveBufs {
   double* kept_cut;
   int32_t *kept_r, *kept_flag;
   int8_t* kept_spins;
+  int8_t* gauge;    // SNP mode: product of the partitions the weights are inverted by
 };
 
 qh_status run_step(Ctx* ctx, const Graph& g, int precision, const TcPlan& plan, StepArgs a,
@@ -447,7 +448,8 @@ qh_status qh_graph_blocks(qh_ctx* h, const qh_graph* gh, int32_t* block_of, int3
 
 // The solve of every block (sel == nullptr) or of the listed blocks only.
 static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
-                            const int32_t* sel, int32_t n_sel, qh_solution** out) {
+                            const int32_t* sel, int32_t n_sel, qh_solution** out,
+                            const qh_refine_state* rs = nullptr) {
   NvtxRange nvtx_range("qh_bsb_solve");
   if (!h) return QH_EINVAL;
   Ctx* ctx = &h->c;
@@ -492,6 +494,25 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
   const bool snp = G.mode == QH_MODE_SNP;
   const int32_t refine_max = snp ? o->refine_max : 1;
   if (refine_max < 1) return set_err(ctx, QH_EINVAL, "refine_max must be >= 1");
+  // a resumed refinement: the saved state must fit the graph and the options
+  const int32_t it0 = rs ? rs->iterations_done : 0;
+  if (rs) {
+    if (!snp) return set_err(ctx, QH_EINVAL, "only a SNP-mode refinement can be resumed");
+    if (!rs->flips || !rs->gauge || !rs->refining || !rs->solves || !rs->deform || !rs->tries)
+      return set_err(ctx, QH_EINVAL, "NULL array in the refinement state");
+    if (it0 < 1 || it0 >= refine_max)
+      return set_err(ctx, QH_EINVAL, "iterations_done must be >= 1 and below refine_max");
+    const bool dfm = o->deform_h > 0.0 && o->deform_tries > 0;
+    for (int32_t v = 0; v < G.n_nodes; ++v)
+      if (rs->gauge[v] != 1 && rs->gauge[v] != -1)
+        return set_err(ctx, QH_EINVAL, "gauge values must be +1 or -1");
+    for (int32_t b = 0; b < nb; ++b)
+      if (rs->solves[b] < 0 || rs->tries[b] < 0 || !(rs->deform[b] >= 0.f) ||
+          !std::isfinite(rs->deform[b]) || (!dfm && (rs->deform[b] != 0.f || rs->tries[b] != 0)))
+        return set_err(ctx, QH_EINVAL,
+                       "negative count or deformation in the refinement state (a deformation "
+                       "needs deform_h > 0 and deform_tries > 0)");
+  }
   const TcPlan plan = pick_plan(R);
   if (G.csr_mode && R % 4 != 0)
     return set_err(ctx, QH_EINVAL, "CSR storage needs replicas to be a multiple of 4");
@@ -578,6 +599,7 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
   B.steps_run = (int32_t*)sc(nb * 4, S_STEPSRUN);
   B.spins = (int8_t*)sc(G.n_nodes + 16, S_SPINS);
   B.C = (int32_t*)sc((G.n_nodes + 1) * 4, S_C);
+  B.gauge = snp ? (int8_t*)sc((size_t)G.n_nodes + 16, S_GAUGE) : nullptr;
   // the refinement's adaptive deformation: per-block field strength and re-solve count
   const bool deform_on = snp && o->deform_h > 0.0 && o->deform_tries > 0;
   // CSR storage: the step variant (the band-tile step needs the band product buffer and,
@@ -596,6 +618,7 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
   B.kept_spins = track ? (int8_t*)sc(G.n_nodes + 16, S_KSPINS) : nullptr;
   bool okb = B.x && B.y && B.signs && B.node_val && B.cuts && B.best_r && B.best_cut && B.active && B.running &&
              B.steps_b && B.c0 && B.seen && B.stall && B.steps_run && B.spins && B.C &&
+             (!snp || B.gauge) &&
              (!deform_on || (B.deform && B.tries)) && (!band_on || B.zband) &&
              (!track || (B.kept_cut && B.kept_r && B.kept_flag && B.kept_spins)) &&
              (o->precision == QH_PREC_FP32 ? B.x1 != nullptr : (B.xh0 && B.xh1));
@@ -686,6 +709,36 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
   QH_CUDA_TRY(cudaMemsetAsync(B.best_cut, 0, nb * 8, s));
   QH_CUDA_TRY(cudaMemsetAsync(B.spins, 0, G.n_nodes + 16, s));
   QH_CUDA_TRY(cudaMemcpyAsync(B.active, sel_mask.data(), nb * 4, cudaMemcpyHostToDevice, s));
+  if (snp) QH_CUDA_TRY(cudaMemsetAsync(B.gauge, 1, (size_t)G.n_nodes + 16, s));
+  std::vector<int32_t> h_active0(sel_mask.begin(), sel_mask.begin() + nb);
+  if (rs) {
+    // the saved flip counts, gauge, refining blocks and deformation; the working graph
+    // becomes the gauged one, as the solve after the checkpoint would have found it
+    std::vector<int32_t> hC(std::max(G.n_nodes, 1), 0);
+    for (int32_t v = 0; v < G.n_nodes; ++v) hC[v] = std::max(rs->flips[v], 0);
+    for (int32_t b = 0; b < nb; ++b) {
+      h_active0[b] = sel_mask[b] && rs->refining[b] ? 1 : 0;
+      if (sel_mask[b]) sol.iters[b] = rs->solves[b];
+    }
+    if (G.n_nodes) {
+      QH_CUDA_TRY(cudaMemcpyAsync(B.C, hC.data(), (size_t)G.n_nodes * 4, cudaMemcpyHostToDevice, s));
+      QH_CUDA_TRY(cudaMemcpyAsync(B.gauge, rs->gauge, G.n_nodes, cudaMemcpyHostToDevice, s));
+    }
+    QH_CUDA_TRY(cudaMemcpyAsync(B.active, h_active0.data(), nb * 4, cudaMemcpyHostToDevice, s));
+    if (B.deform) {
+      QH_CUDA_TRY(cudaMemcpyAsync(B.deform, rs->deform, nb * 4, cudaMemcpyHostToDevice, s));
+      QH_CUDA_TRY(cudaMemcpyAsync(B.tries, rs->tries, nb * 4, cudaMemcpyHostToDevice, s));
+    }
+    launch_apply_gauge(s, W, G.w, B.gauge, W.w);
+    qh_status st = retile(ctx, &W, W.w, W.tile_bf16, W.tile_f32, W.csr_mode ? W.pval : nullptr);
+    if (st == QH_OK && band_on) st = reband(ctx, &W, W.w, W.band, W.rval);
+    if (st == QH_OK && fp8) st = convert_fp8_tiles();
+    if (st != QH_OK) return st;
+    launch_block_sums(s, W, W.w, sum_w_work, (double*)ctx->scratch(nb * 8, S_SUMJ2),
+                      (double*)ctx->scratch((size_t)std::max(G.n_nodes, 1) * 16, S_NODETMP));
+    // the host's copies of these arrays must not change before the copies above ran
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+  }
   QH_CUDA_TRY(cudaEventRecord(ctx->ev[0], s));
 
   // energy checks every check_every steps: for the early stop (patience > 0) and for
@@ -864,8 +917,12 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
   }
   double step_ms_total = 0.0, spin_updates = 0.0;
   int64_t launches = 0;
-  std::vector<int32_t> h_active(sel_mask.begin(), sel_mask.begin() + nb), h_steps_run(nb);
-  for (int32_t it = 0; it < refine_max; ++it) {
+  std::vector<int32_t> h_active(h_active0), h_steps_run(nb);
+  int32_t it_last = it0 - 1;
+  bool any0 = false;
+  for (int32_t b = 0; b < nb; ++b) any0 = any0 || h_active0[b];
+  for (int32_t it = it0; it < refine_max && any0; ++it) {
+    it_last = it;
     NvtxRange nvtx_iter("qh_bsb_solve: solve of every active block");
     for (int32_t b = 0; b < nb; ++b)
       if (h_active[b]) sol.iters[b] += 1;
@@ -929,10 +986,10 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
       launch_track_final(s, W, B.best_cut, B.best_r, B.active, B.kept_cut, B.kept_r, B.kept_flag,
                          B.kept_spins, B.spins);
     QH_STAGE_CHECK("solve: signs, cut, replica pick");
-    if (it == 0)
+    if (it == it0)
       QH_CUDA_TRY(cudaMemcpyAsync(sol.cuts_first.data(), B.cuts, (size_t)nb * R * 8, cudaMemcpyDeviceToHost, s));
     QH_CUDA_TRY(cudaMemcpyAsync(h_steps_run.data(), B.steps_run, nb * 4, cudaMemcpyDeviceToHost, s));
-    if (it == 0 || !snp) {
+    if (it == it0 || !snp) {
       QH_CUDA_TRY(cudaMemcpyAsync(sol.best_r.data(), B.best_r, nb * 4, cudaMemcpyDeviceToHost, s));
       QH_CUDA_TRY(cudaMemcpyAsync(sol.best_cut.data(), B.best_cut, nb * 8, cudaMemcpyDeviceToHost, s));
     }
@@ -951,7 +1008,7 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
     for (int32_t b = 0; b < nb; ++b)
       if (h_active[b]) {
         spin_updates += (double)G.h_block_size[b] * R * h_steps_run[b];
-        if (it == 0 || !snp) sol.steps_run[b] = h_steps_run[b];
+        if (it == it0 || !snp) sol.steps_run[b] = h_steps_run[b];
       }
     if (!snp) break;
     // ---- SNP refinement: termination test, flip counter, sign inversion
@@ -963,7 +1020,7 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
     int32_t n_active = 0;
     for (int32_t b = 0; b < nb; ++b) n_active += h_active[b] != 0;
     if (n_active == 0 || it + 1 == refine_max) break;
-    launch_gauge(s, W, B.spins, W.w, B.active, B.deform);
+    launch_gauge(s, W, B.spins, W.w, B.active, B.deform, B.gauge);
     {
       qh_status st = retile(ctx, &W, W.w, W.tile_bf16, W.tile_f32, W.csr_mode ? W.pval : nullptr);
       if (st == QH_OK && band_on) st = reband(ctx, &W, W.w, W.band, W.rval);
@@ -972,6 +1029,38 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
     }
     launch_block_sums(s, W, W.w, sum_w_work, (double*)ctx->scratch(nb * 8, S_SUMJ2),
                       (double*)ctx->scratch((size_t)std::max(G.n_nodes, 1) * 16, S_NODETMP));
+  }
+  // ---- the refinement state after the last solve, for a call that continues the loop:
+  // the gauge the next solve would start from applies the last partition to the blocks
+  // that go on refining without a deformed re-solve (as launch_gauge would)
+  if (snp) {
+    const size_t nn = (size_t)std::max(G.n_nodes, 1);
+    std::vector<int8_t> hg(nn, 1), hs(nn, 0);
+    std::vector<int32_t> ha(nb, 0), ht(nb, 0), hb(nn, -1);
+    std::vector<float> hd(nb, 0.f);
+    if (G.n_nodes) {
+      QH_CUDA_TRY(cudaMemcpyAsync(hg.data(), B.gauge, G.n_nodes, cudaMemcpyDeviceToHost, s));
+      QH_CUDA_TRY(cudaMemcpyAsync(hs.data(), B.spins, G.n_nodes, cudaMemcpyDeviceToHost, s));
+      QH_CUDA_TRY(cudaMemcpyAsync(hb.data(), G.block_of, (size_t)G.n_nodes * 4,
+                                  cudaMemcpyDeviceToHost, s));
+    }
+    QH_CUDA_TRY(cudaMemcpyAsync(ha.data(), B.active, nb * 4, cudaMemcpyDeviceToHost, s));
+    if (B.deform) {
+      QH_CUDA_TRY(cudaMemcpyAsync(hd.data(), B.deform, nb * 4, cudaMemcpyDeviceToHost, s));
+      QH_CUDA_TRY(cudaMemcpyAsync(ht.data(), B.tries, nb * 4, cudaMemcpyDeviceToHost, s));
+    }
+    QH_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int32_t b = 0; b < nb; ++b) ha[b] = ha[b] && sel_mask[b] ? 1 : 0;
+    sol.refine_gauge.assign(G.n_nodes, 1);
+    for (int32_t v = 0; v < G.n_nodes; ++v) {
+      const int32_t b = hb[v];
+      const bool flip = b >= 0 && ha[b] && hd[b] == 0.f && hs[v] < 0;
+      sol.refine_gauge[v] = (int8_t)(flip ? -hg[v] : hg[v]);
+    }
+    sol.refine_done = it_last + 1;
+    sol.refining = ha;
+    sol.refine_deform = hd;
+    sol.refine_tries = ht;
   }
   // ---- final spins and cut on the original graph
   if (snp) {
@@ -1055,6 +1144,34 @@ qh_status qh_bsb_solve(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o, qh_s
   return solve_impl(h, gh, o, nullptr, -1, out);
 }
 
+qh_status qh_bsb_solve_resume(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
+                              const qh_refine_state* state, qh_solution** out) {
+  if (h && !state) return set_err(&h->c, QH_EINVAL, "NULL refinement state");
+  return solve_impl(h, gh, o, nullptr, -1, out, state);
+}
+
+qh_status qh_solution_refine_state(const qh_solution* sh, qh_refine_state* st) {
+  if (!sh || !st || !st->flips || !st->gauge || !st->refining || !st->solves || !st->deform ||
+      !st->tries)
+    return QH_EINVAL;
+  const Solution& s = sh->s;
+  if (s.mode != QH_MODE_SNP || s.refine_done < 1 ||
+      (int32_t)s.refine_gauge.size() != s.n_nodes)
+    return QH_EINVAL;
+  st->iterations_done = s.refine_done;
+  for (int32_t v = 0; v < s.n_nodes; ++v) {
+    st->flips[v] = s.C[v];
+    st->gauge[v] = s.refine_gauge[v];
+  }
+  for (int32_t b = 0; b < s.n_blocks; ++b) {
+    st->refining[b] = s.refining[b];
+    st->solves[b] = s.iters[b];
+    st->deform[b] = s.refine_deform[b];
+    st->tries[b] = s.refine_tries[b];
+  }
+  return QH_OK;
+}
+
 qh_status qh_bsb_solve_blocks(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
                               const int32_t* blocks, int32_t n_blocks, qh_solution** out) {
   if (h && !blocks && n_blocks > 0) return set_err(&h->c, QH_EINVAL, "NULL block list");
@@ -1089,6 +1206,7 @@ qh_status qh_solution_set_block(qh_ctx* h, qh_solution* sh, int32_t b, const int
   for (int32_t r = 0; r < s.R; ++r) s.cuts_first[(size_t)b * s.R + r] = 0.0;
   s.solved[b] = 1;
   s.device_stale = true;
+  s.refine_done = 0;  // an imported block carries no refinement state
   return QH_OK;
 }
 

@@ -917,17 +917,33 @@ __global__ void __launch_bounds__(256) k_refine_prepare(int32_t nb, const int64_
 
 // w'_ab = -w_ab for edges crossing the partition (s_a != s_b) of active blocks.
 // Blocks waiting for a deformed re-solve (deform[b] != 0) keep their weights.
+// Warp per vertex, the lanes striding over its row.  gauge (or nullptr): the product of
+// the partitions that inverted each vertex's weights so far, updated with this one.
 __global__ void k_gauge(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                         const int32_t* __restrict__ block_of, const int8_t* __restrict__ spins,
                         double* w, const int32_t* __restrict__ active,
-                        const float* __restrict__ deform) {
-  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+                        const float* __restrict__ deform, int8_t* gauge) {
+  const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (a >= n) return;
   int32_t b = block_of[a];
   if (b < 0 || !active[b] || (deform != nullptr && deform[b] != 0.f)) return;
   int8_t sa = spins[a];
-  for (int64_t e = rp[a]; e < rp[a + 1]; ++e)
+  for (int64_t e = rp[a] + lane; e < rp[a + 1]; e += 32)
     if (spins[col[e]] != sa) w[e] = -w[e];
+  if (gauge != nullptr && lane == 0) gauge[a] = (int8_t)(gauge[a] * sa);
+}
+
+// The weights under a gauge: w[e] = w0[e] g_a g_b (a resumed refinement's starting graph).
+__global__ void k_apply_gauge(int32_t n, const int64_t* __restrict__ rp,
+                              const int32_t* __restrict__ col, const double* __restrict__ w0,
+                              const int8_t* __restrict__ gauge, double* w) {
+  const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (a >= n) return;
+  const int8_t ga = gauge[a];
+  for (int64_t e = rp[a] + lane; e < rp[a + 1]; e += 32)
+    w[e] = ga * gauge[col[e]] < 0 ? -w0[e] : w0[e];
 }
 
 // ------------------------------------------------------------------ phase
@@ -1177,10 +1193,17 @@ void launch_refine_prepare(cudaStream_t s, const Graph& g, const int8_t* spins,
 }
 
 void launch_gauge(cudaStream_t s, const Graph& g, const int8_t* spins, double* w,
-                  const int32_t* active, const float* deform) {
+                  const int32_t* active, const float* deform, int8_t* gauge) {
   if (g.n_nodes > 0)
-    k_gauge<<<::qh::counted(nblk(g.n_nodes)), 256, 0, s>>>(g.n_nodes, g.row_ptr, g.col, g.block_of, spins, w,
-                                            active, deform);
+    k_gauge<<<::qh::counted(nblk((int64_t)g.n_nodes * 32)), 256, 0, s>>>(
+        g.n_nodes, g.row_ptr, g.col, g.block_of, spins, w, active, deform, gauge);
+}
+
+void launch_apply_gauge(cudaStream_t s, const Graph& g, const double* w0, const int8_t* gauge,
+                        double* w) {
+  if (g.n_nodes > 0)
+    k_apply_gauge<<<::qh::counted(nblk((int64_t)g.n_nodes * 32)), 256, 0, s>>>(
+        g.n_nodes, g.row_ptr, g.col, w0, gauge, w);
 }
 
 void launch_vote(cudaStream_t s, const Graph& g, const int8_t* spins, int8_t* hap1, int8_t* hap2,

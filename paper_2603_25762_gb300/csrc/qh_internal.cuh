@@ -148,6 +148,13 @@ struct Solution {
   std::vector<int8_t> spins;             // [n_nodes] best spins by vertex (0 = dropped)
   std::vector<int32_t> C;                // SNP mode flip counts [n_nodes] (-1: block not solved)
   std::vector<uint8_t> solved;           // [n_blocks] 1 = solved here or imported
+  // SNP refinement state after the last solve, for a later call that continues it:
+  // solves run over the graph, and per block whether it still refines, its deformation
+  // field and re-solves used; per vertex the gauge the next solve starts from
+  int32_t refine_done = 0;
+  std::vector<int32_t> refining, refine_tries;
+  std::vector<float> refine_deform;
+  std::vector<int8_t> refine_gauge;
   mutable bool device_stale = false;     // host spins / C changed after the device copies
   double solve_ms = 0, step_ms = 0, spin_updates = 0;
   int64_t n_step_launches = 0;
@@ -334,8 +341,12 @@ qh_status reband(Ctx* ctx, const Graph* g, const double* w, __nv_bfloat16* band,
 void launch_refine_prepare(cudaStream_t s, const Graph& g, const int8_t* spins,
                            const double* best_cut, int32_t* active, int32_t* C, float* deform,
                            int32_t* tries, float deform_h, int32_t deform_tries);
+// w <- D_s w D_s on the active, undeformed blocks; gauge (or nullptr) *= s there
 void launch_gauge(cudaStream_t s, const Graph& g, const int8_t* spins, double* w,
-                  const int32_t* active, const float* deform);
+                  const int32_t* active, const float* deform, int8_t* gauge);
+// w = D_g w0 D_g (g = +-1 per vertex)
+void launch_apply_gauge(cudaStream_t s, const Graph& g, const double* w0, const int8_t* gauge,
+                        double* w);
 void launch_vote(cudaStream_t s, const Graph& g, const int8_t* spins, int8_t* hap1, int8_t* hap2,
                  int32_t* block_id);
 void launch_parity(cudaStream_t s, const Graph& g, const int32_t* C, int8_t* hap1, int8_t* hap2,

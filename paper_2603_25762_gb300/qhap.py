@@ -52,6 +52,12 @@ class QhBsbOpts(C.Structure):
                 ("deform_h", C.c_double), ("deform_tries", C.c_int32), ("check_mode", C.c_int32),
                 ("track_best", C.c_int32)]
 
+class QhRefineState(C.Structure):
+    _fields_ = [("iterations_done", C.c_int32), ("flips", C.c_void_p), ("gauge", C.c_void_p),
+                ("refining", C.c_void_p), ("solves", C.c_void_p), ("deform", C.c_void_p),
+                ("tries", C.c_void_p)]
+
+
 # simulated-bifurcation variants (QH_SB_*)
 SB_VARIANTS = {"ballistic": 0, "discrete": 1, "adiabatic": 2}
 
@@ -91,6 +97,8 @@ _SIGS = {
     "qh_graph_free": (None, [P]),
     "qh_bsb_solve": (C.c_int, [P, P, C.POINTER(QhBsbOpts), PP]),
     "qh_bsb_solve_blocks": (C.c_int, [P, P, C.POINTER(QhBsbOpts), P, I32, PP]),
+    "qh_bsb_solve_resume": (C.c_int, [P, P, C.POINTER(QhBsbOpts), C.POINTER(QhRefineState), PP]),
+    "qh_solution_refine_state": (C.c_int, [P, C.POINTER(QhRefineState)]),
     "qh_solution_set_block": (C.c_int, [P, P, I32, P, D, I32, I32, I32]),
     "qh_solution_block": (C.c_int, [P, P, I32, P, P, P, P, P]),
     "qh_solution_spins": (C.c_int, [P, P, P]),
@@ -201,6 +209,11 @@ class Graph:
             pass
 
 
+def _refine_struct(done, st):
+    return QhRefineState(int(done), _ptr(st["flips"]), _ptr(st["gauge"]), _ptr(st["refining"]),
+                         _ptr(st["solves"]), _ptr(st["deform"]), _ptr(st["tries"]))
+
+
 class Solution:
     def __init__(self, ctx, handle, n_blocks, R):
         self.ctx, self.h, self.n_blocks, self.R = ctx, handle, n_blocks, R
@@ -220,6 +233,23 @@ class Solution:
         self.ctx._check(lib().qh_solution_set_block(self.ctx.h, self.h, b, _ptr(sp),
                                                     float(best_cut), int(best_replica),
                                                     int(steps_run), int(iterations)))
+
+    def refine_state(self, n_nodes):
+        """The SNP refinement's state after this solve (qh_solution_refine_state), as a
+        dict of host arrays that Context.solve(resume=...) continues from."""
+        n = max(n_nodes, 1)
+        nb = max(self.n_blocks, 1)
+        st = {"flips": np.zeros(n, np.int32), "gauge": np.zeros(n, np.int8),
+              "refining": np.zeros(nb, np.int32), "solves": np.zeros(nb, np.int32),
+              "deform": np.zeros(nb, np.float32), "tries": np.zeros(nb, np.int32)}
+        rs = _refine_struct(0, st)
+        r = lib().qh_solution_refine_state(self.h, C.byref(rs))
+        if r != QH_OK:
+            raise QhError(r, "no refinement state (READ mode, or blocks imported)")
+        out = {k: (v[:n_nodes] if k in ("flips", "gauge") else v[: self.n_blocks])
+               for k, v in st.items()}
+        out["iterations_done"] = rs.iterations_done
+        return out
 
     def spins(self, n_nodes):
         s = np.zeros(max(n_nodes, 1), np.int8)
@@ -283,7 +313,7 @@ class Context:
     def solve(self, g, replicas=32, steps=1000, precision=PREC_FP32, seed=1, dt=1.0, a0=1.0,
               c0=0.0, schedule=SCHED_LINEAR, replica_base=0, check_every=0, patience=0,
               refine_max=15, step_kernel=None, variant="ballistic", deform_h=0.0,
-              deform_tries=0, blocks=None, check_mode=0, track_best=False):
+              deform_tries=0, blocks=None, check_mode=0, track_best=False, resume=None):
         """step_kernel: None = the default (autotuned on BF16 tile storage), or a name
         from STEP_KERNELS: the tile variants for BF16 tile storage, "csr-lane4" /
         "csr-lane8" for CSR storage.
@@ -297,13 +327,24 @@ class Context:
         check_mode: where early-stop checks run, 0 = inside the multi-step launch when it
         applies, 1 = between launches (qh_bsb_opts.check_mode).
         track_best: report the best result reached at any check (every check_every
-        steps) or at the end, instead of the final state's."""
+        steps) or at the end, instead of the final state's.
+        resume: a SNP refinement state (Solution.refine_state()) to continue from, up to
+        refine_max solves in all (qh_bsb_solve_resume)."""
         sk = -1 if step_kernel is None else STEP_KERNELS.index(step_kernel)
         o = QhBsbOpts(replicas, steps, schedule, precision, dt, a0, c0, seed, replica_base,
                       check_every, patience, refine_max, sk, _sb(variant), deform_h,
                       deform_tries, check_mode, 1 if track_best else 0)
         s = C.c_void_p()
-        if blocks is None:
+        if resume is not None:
+            st = {"flips": _np(resume["flips"], np.int32), "gauge": _np(resume["gauge"], np.int8),
+                  "refining": _np(resume["refining"], np.int32),
+                  "solves": _np(resume["solves"], np.int32),
+                  "deform": _np(resume["deform"], np.float32),
+                  "tries": _np(resume["tries"], np.int32)}
+            rs = _refine_struct(resume["iterations_done"], st)
+            self._check(lib().qh_bsb_solve_resume(self.h, g.h, C.byref(o), C.byref(rs),
+                                                  C.byref(s)))
+        elif blocks is None:
             self._check(lib().qh_bsb_solve(self.h, g.h, C.byref(o), C.byref(s)))
         else:
             sel = _np(blocks, np.int32)

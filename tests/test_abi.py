@@ -55,6 +55,8 @@ def test_struct_layouts_match_header():
     # replicas .. precision, dt a0 c0, seed, replica_base .. refine_max, step_kernel and
     # sb_variant, deform_h, deform_tries and check_mode, track_best (+ padding)
     assert ctypes.sizeof(qhap.QhBsbOpts) == 4 * 4 + 3 * 8 + 8 + 4 * 4 + 8 + 8 + 8 + 8
+    # iterations_done (+ padding), six array pointers
+    assert ctypes.sizeof(qhap.QhRefineState) == 8 + 6 * 8
 
 
 def test_struct_layouts_match_the_c_compiler(tmp_path):
@@ -67,7 +69,7 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
         pytest.skip("no gcc")
     lines = []
     for py, c in ((qhap.QhFragments, "qh_fragments"), (qhap.QhGraphOpts, "qh_graph_opts"),
-                  (qhap.QhBsbOpts, "qh_bsb_opts")):
+                  (qhap.QhBsbOpts, "qh_bsb_opts"), (qhap.QhRefineState, "qh_refine_state")):
         lines.append(f'printf("{c} %zu\\n", sizeof({c}));')
         for name, _ in py._fields_:
             lines.append(f'printf("{c}.{name} %zu\\n", offsetof({c}, {name}));')
@@ -80,7 +82,7 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
     got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
                                                  check=True).stdout.splitlines())
     for py, c in ((qhap.QhFragments, "qh_fragments"), (qhap.QhGraphOpts, "qh_graph_opts"),
-                  (qhap.QhBsbOpts, "qh_bsb_opts")):
+                  (qhap.QhBsbOpts, "qh_bsb_opts"), (qhap.QhRefineState, "qh_refine_state")):
         assert int(got[c]) == ctypes.sizeof(py), c
         for name, _ in py._fields_:
             assert int(got[f"{c}.{name}"]) == getattr(py, name).offset, (c, name)

@@ -1,7 +1,11 @@
-"""Resume from a saved state: steps t0 .. t0+2n run in one call and as two calls of n
+"""Resume from a saved state.  Steps t0 .. t0+2n run in one call and as two calls of n
 steps (the state x, y copied out and back in between, as a checkpoint would) give
 bit-identical states, on every step-kernel family.  The product operand is not part
 of the saved state: every kernel rebuilds it from x exactly as its epilogue writes it.
+
+At the solve level, the SNP refinement's state after k solves (flip counts, the gauge of
+the weights, the blocks still refining, their deformation) saved and resumed ends where
+one uninterrupted loop ends.
 """
 import numpy as np
 import pytest
@@ -65,3 +69,74 @@ def test_split_step_range_is_bit_identical(q, ctx, precision, kernel, storage, R
     assert np.isfinite(xa.cpu().numpy()).all() and np.isfinite(ya.cpu().numpy()).all()
     assert np.array_equal(xc.cpu().numpy(), xa.cpu().numpy())
     assert np.array_equal(yc.cpu().numpy(), ya.cpu().numpy())
+
+
+# ----------------------------------------------------------------------------- refinement
+def _refine_case(ctx, g, n_snps, k, **kw):
+    """One SNP-mode solve with refine_max = kw's, and the same loop stopped after k
+    solves, saved (refine_state) and resumed: both must end in the same place."""
+    full = ctx.solve(g, **kw)
+    part = ctx.solve(g, **dict(kw, refine_max=k))
+    st = part.refine_state(g.n_nodes)
+    assert st["iterations_done"] == k
+    rest = ctx.solve(g, resume=st, **kw)
+    sf, sr = full.refine_state(g.n_nodes), rest.refine_state(g.n_nodes)
+    assert sr["iterations_done"] == sf["iterations_done"]
+    for key in ("flips", "gauge", "refining", "solves", "deform", "tries"):
+        assert np.array_equal(sr[key], sf[key]), key
+    assert np.array_equal(rest.spins(g.n_nodes), full.spins(g.n_nodes))
+    for b in range(g.n_blocks):
+        bf, br = full.block(b), rest.block(b)
+        assert br["best_cut"] == bf["best_cut"] and br["iterations"] == bf["iterations"], b
+    hf, hr = ctx.phase(g, full, n_snps), ctx.phase(g, rest, n_snps)
+    for a, c in zip(hf, hr):
+        assert np.array_equal(a, c)
+    return sf
+
+
+@pytest.mark.parametrize("precision,storage,R,kernel", [(1, 1, 64, None), (0, 1, 64, None),
+                                                        (1, 2, 128, "csr-band8")])
+def test_refinement_checkpoint_resumes_to_the_same_result(q, ctx, precision, storage, R, kernel):
+    """SNP refinement (flip counts C, sign inversions of the crossing edges) saved after
+    k solves and resumed gives the flip counts, parity partition, final cuts and
+    haplotypes of one uninterrupted loop."""
+    fr = synth.region_reads(32, n_snps=400, region=130_000, n_reads=110, len_mean=8000,
+                            len_sd=2000, flip_p=0.08, miss_p=0.0, qual=(7, 30))
+    g = ctx.build_graph(fr, mode=q.MODE_SNP, storage=storage)
+    kw = dict(replicas=R, steps=300, precision=precision, seed=6, refine_max=15,
+              step_kernel=kernel)
+    sf = _refine_case(ctx, g, fr.n_snps, 1, **kw)
+    assert sf["solves"].max() >= 2  # the loop went on past the checkpoint in some block
+    if sf["solves"].max() >= 3:
+        _refine_case(ctx, g, fr.n_snps, 2, **kw)
+
+
+def test_refinement_checkpoint_with_deformation(q, ctx):
+    """The same with the deformed re-solves: the state carries each block's field and
+    the re-solves it has used."""
+    fr = synth.ont_region(1003, scale=0.06)
+    g = ctx.build_graph(fr, mode=q.MODE_SNP)
+    kw = dict(replicas=64, steps=300, precision=1, seed=3, refine_max=8, deform_h=0.025,
+              deform_tries=2)
+    sf = _refine_case(ctx, g, fr.n_snps, 1, **kw)
+    assert sf["solves"].max() >= 2
+    _refine_case(ctx, g, fr.n_snps, 2, **kw)
+
+
+def test_refinement_state_rejections(q, ctx):
+    fr = synth.region_reads(32, n_snps=150, region=50_000, n_reads=40, len_mean=8000,
+                            len_sd=2000, flip_p=0.08, miss_p=0.0, qual=(7, 30))
+    g = ctx.build_graph(fr, mode=q.MODE_SNP)
+    kw = dict(replicas=64, steps=100, precision=1, seed=6, refine_max=4)
+    st = ctx.solve(g, **dict(kw, refine_max=1)).refine_state(g.n_nodes)
+    bad = dict(st, gauge=np.zeros_like(st["gauge"]))
+    with pytest.raises(q.QhError) as e:
+        ctx.solve(g, resume=bad, **kw)
+    assert e.value.status == q.QH_EINVAL
+    with pytest.raises(q.QhError):  # iterations_done must stay below refine_max
+        ctx.solve(g, resume=st, **dict(kw, refine_max=1))
+    with pytest.raises(q.QhError):  # a deformation field without deform_h
+        ctx.solve(g, resume=dict(st, deform=np.full_like(st["deform"], 0.5)), **kw)
+    gr = ctx.build_graph(fr, mode=q.MODE_READ)
+    with pytest.raises(q.QhError):  # READ mode has no refinement
+        ctx.solve(gr, replicas=64, steps=100, precision=1).refine_state(gr.n_nodes)
