@@ -338,6 +338,19 @@ qh_status qh_solution_spins(qh_ctx* ctx, const qh_solution* sol, int8_t* spins);
  * cuts float64[n_blocks * R], row b = block b (values on the block's graph). */
 qh_status qh_solution_cuts(qh_ctx* ctx, const qh_solution* sol, double* cuts);
 
+/* Energy-check trace of the first solve (Results: the energy against the iterations;
+ * the checks of qh_bsb_opts.check_every, with early stop or track_best on): the best
+ * cut over the replicas of each block at steps check_every, 2 check_every, ... below
+ * the longest block schedule.
+ *  n_checks     : the number of checks (0 when no checks ran)
+ *  check_every  : their period in steps (may be NULL)
+ *  trace float64[n_checks * n_blocks] (may be NULL): row c = check c + 1; NaN for a
+ *                 block that was not running at that check (it had stopped early, its
+ *                 schedule had ended, or it was not solved)
+ * Errors: QH_EINVAL (NULL solution or n_checks). */
+qh_status qh_solution_check_trace(const qh_solution* sol, int32_t* n_checks, int32_t* check_every,
+                                  double* trace);
+
 /* Timing of the last solve in milliseconds (CUDA events on the context stream):
  *  solve_ms : whole qh_bsb_solve device time
  *  step_ms  : the bSB step launches only; n_step_launches launches

@@ -93,7 +93,7 @@ enum {
   S_STEPSB, S_C0, S_SEEN, S_STALL, S_STEPSRUN, S_SPINS, S_C, S_WWORK, S_TBWORK, S_TFWORK,
   S_SUMW, S_SUMJ2, S_NODETMP, S_SIGNS1, S_NODEVAL1, S_CUT1, S_DBG0, S_DBG1, S_DBG2, S_RUNNING,
   S_PVWORK, S_TR0, S_TR1, S_F8H, S_F8L, S_F8FLAG, S_X8, S_DEFORM, S_TRIES, S_DBGDEF,
-  S_ZBAND, S_BANDWORK, S_RVWORK, S_TRACE, S_KCUT, S_KR, S_KFLAG, S_KSPINS, S_GAUGE
+  S_ZBAND, S_BANDWORK, S_RVWORK, S_TRACE, S_KCUT, S_KR, S_KFLAG, S_KSPINS, S_GAUGE, S_CTRACE
 };
 
 struct SolveBufs {
@@ -113,6 +113,7 @@ struct SolveBufs {
   int32_t *kept_r, *kept_flag;
   int8_t* kept_spins;
   int8_t* gauge;    // SNP mode: product of the partitions the weights are inverted by
+  double* trace;    // energy checks: [checks][n_blocks] best cut of each check (NaN: none)
 };
 
 qh_status run_step(Ctx* ctx, const Graph& g, int precision, const TcPlan& plan, StepArgs a,
@@ -745,6 +746,11 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
   // the best result during the run (track_best)
   const bool early = o->check_every > 0 && o->patience > 0;
   const bool checking = early || track;
+  // the energy-check trace of each solve: the best cut over the replicas per block at
+  // each check t = check_every, 2 check_every, ... < max_steps
+  const int32_t n_checks = checking ? (max_steps - 1) / o->check_every : 0;
+  B.trace = n_checks > 0 ? (double*)ctx->scratch((size_t)n_checks * nb * 8, S_CTRACE) : nullptr;
+  if (n_checks > 0 && !B.trace) return set_err(ctx, QH_ENOMEM, "allocation failed (check trace)");
   // ---- the step loop, captured once per shape and replayed
   // The captured step loop bakes in pointers and sizes; it is replayed only when every
   // one of them is unchanged (a rebuilt graph at other addresses is captured anew).
@@ -778,7 +784,7 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
                           (const void*)B.cuts, (const void*)B.best_r, (const void*)B.best_cut,
                           (const void*)B.running, (const void*)B.steps_b, (const void*)B.c0,
                           (const void*)B.seen, (const void*)B.stall, (const void*)B.steps_run,
-                          (const void*)ctx->d_err, (const void*)B.deform})
+                          (const void*)ctx->d_err, (const void*)B.deform, (const void*)B.trace})
       add(p);
   }
   StepArgs a{};
@@ -864,6 +870,7 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
     chk.e_cnt = (uint32_t*)ctx->scratch((size_t)4 * nb * 4, S_RUN_EC);  // e_cnt, decided, stop_t
     chk.seen = B.seen;
     chk.stall = B.stall;
+    chk.trace = B.trace;
     if (!chk.s || !chk.e_sum || !chk.e_cnt)
       return set_err(ctx, QH_ENOMEM, "allocation failed (early-stop checks)");
     chk.decided = chk.e_cnt + 2 * nb;
@@ -890,6 +897,8 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
         launch_signs(s, W, R, xc, B.signs);
         launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.running);
         launch_pick_best(s, nb, R, B.cuts, B.best_r, B.best_cut, B.running);
+        launch_trace_check(s, nb, B.best_cut, B.running, t + 1, B.steps_b,
+                           B.trace + (size_t)((t + 1) / o->check_every - 1) * nb);
         if (track)
           launch_track_check(s, W, R, B.signs, B.best_cut, B.best_r, B.running, t + 1, B.steps_b,
                              B.kept_cut, B.kept_r, B.kept_flag, B.kept_spins);
@@ -939,6 +948,8 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
       QH_CUDA_TRY(cudaMemsetAsync(B.kept_r, 0xff, nb * 4, s));
     }
     QH_CUDA_TRY(cudaMemcpyAsync(B.running, B.active, nb * 4, cudaMemcpyDeviceToDevice, s));
+    if (B.trace)  // NaN until a check records a block
+      QH_CUDA_TRY(cudaMemsetAsync(B.trace, 0xff, (size_t)n_checks * nb * 8, s));
     launch_init_state(s, W, R, o->replica_base, o->seed, it, B.x, B.y,
                       is_tc_precision(o->precision) ? B.xh0 : nullptr, B.active, o->sb_variant);
     if (fp8)
@@ -965,6 +976,8 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
           launch_signs(s, W, R, B.x, B.signs);
           launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.running);
           launch_pick_best(s, nb, R, B.cuts, B.best_r, B.best_cut, B.running);
+          launch_trace_check(s, nb, B.best_cut, B.running, t1, B.steps_b,
+                             B.trace + (size_t)(t1 / o->check_every - 1) * nb);
           if (track)
             launch_track_check(s, W, R, B.signs, B.best_cut, B.best_r, B.running, t1, B.steps_b,
                                B.kept_cut, B.kept_r, B.kept_flag, B.kept_spins);
@@ -988,6 +1001,12 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
     QH_STAGE_CHECK("solve: signs, cut, replica pick");
     if (it == it0)
       QH_CUDA_TRY(cudaMemcpyAsync(sol.cuts_first.data(), B.cuts, (size_t)nb * R * 8, cudaMemcpyDeviceToHost, s));
+    if (it == it0 && B.trace) {
+      sol.check_every = o->check_every;
+      sol.check_trace.assign((size_t)n_checks * nb, 0.0);
+      QH_CUDA_TRY(cudaMemcpyAsync(sol.check_trace.data(), B.trace, (size_t)n_checks * nb * 8,
+                                  cudaMemcpyDeviceToHost, s));
+    }
     QH_CUDA_TRY(cudaMemcpyAsync(h_steps_run.data(), B.steps_run, nb * 4, cudaMemcpyDeviceToHost, s));
     if (it == it0 || !snp) {
       QH_CUDA_TRY(cudaMemcpyAsync(sol.best_r.data(), B.best_r, nb * 4, cudaMemcpyDeviceToHost, s));
@@ -1148,6 +1167,18 @@ qh_status qh_bsb_solve_resume(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* 
                               const qh_refine_state* state, qh_solution** out) {
   if (h && !state) return set_err(&h->c, QH_EINVAL, "NULL refinement state");
   return solve_impl(h, gh, o, nullptr, -1, out, state);
+}
+
+qh_status qh_solution_check_trace(const qh_solution* sh, int32_t* n_checks, int32_t* check_every,
+                                  double* trace) {
+  if (!sh || !n_checks) return QH_EINVAL;
+  const Solution& s = sh->s;
+  const int32_t nb = std::max(s.n_blocks, 1);
+  *n_checks = (int32_t)(s.check_trace.size() / (size_t)nb);
+  if (check_every) *check_every = s.check_every;
+  if (trace && !s.check_trace.empty())
+    memcpy(trace, s.check_trace.data(), s.check_trace.size() * sizeof(double));
+  return QH_OK;
 }
 
 qh_status qh_solution_refine_state(const qh_solution* sh, qh_refine_state* st) {

@@ -128,6 +128,7 @@ struct RunArgs {
   double* seen;             // [n_blocks] best cut seen at a check
   int32_t* stall;           // [n_blocks] checks since it last improved
   int32_t* stop_t;          // [n_blocks] the step count the block stopped at, or -1
+  double* check_trace;      // [checks][n_blocks] best cut of each check, or nullptr
   // step timeline (test hook; nullptr in the solver): per CTA, traced step u0 + j and
   // item slot i, TRACE_EVENTS global-timer stamps followed by TRACE_EVENTS SM-clock
   // stamps at trace[((cta * trace_nu + j) * MAX_ITEMS + i) * 2 * TRACE_EVENTS + ...]
@@ -392,7 +393,7 @@ __device__ __forceinline__ bool check_energy(
     unsigned long long* e_next, uint32_t* cnt, uint32_t* cnt_next, uint32_t total, int32_t R,
     double sum_w, double* seen, int32_t* stall, int32_t* stop_t, uint32_t* decided, int t,
     int check_every, int patience, uint32_t sfull, uint32_t sfree, uint32_t n_chk,
-    int32_t* err, volatile int32_t* abort, int lane) {
+    int32_t* err, volatile int32_t* abort, int lane, double* trace_slot) {
   if (!__all_sync(0xffffffffu, rwait(sfull, n_chk & 1u, err, abort))) return false;
   tc_fence_after();
 #pragma unroll 1
@@ -441,6 +442,7 @@ __device__ __forceinline__ bool check_energy(
   // decision, is done: every contributor above waited for it)
   for (int rho = lane; rho < R; rho += 32) st_relaxed_u64(e_next + rho, 0ull);
   if (lane == 0) {
+    if (trace_slot != nullptr) st_relaxed_f64(trace_slot, best);  // the check's best cut
     if (best > ld_relaxed_f64(seen)) {
       st_relaxed_f64(seen, best);
       st_relaxed_s32(stall, 0);
@@ -973,7 +975,9 @@ __global__ void __launch_bounds__(RUN_THREADS, 1)
             a.e_cnt + (size_t)(par ^ 1) * a.n_blocks + it.block,
             it.rows_b * (uint32_t)a.n_kt * EPI_WARPS, R, a.sum_w[it.block], a.seen + it.block,
             a.stall + it.block, a.stop_t + it.block, a.decided + it.block, t, a.check_every,
-            a.patience, sfull, sfree, n_chk, a.err, abort_flag, lane);
+            a.patience, sfull, sfree, n_chk, a.err, abort_flag, lane,
+            a.check_trace ? a.check_trace + (size_t)(t / a.check_every - 1) * a.n_blocks + it.block
+                          : nullptr);
         if (!cok) break;
         ++n_chk;
       }
@@ -1301,6 +1305,7 @@ qh_status launch_run_impl(Ctx* ctx, const Graph& g, const StepArgs& s, const Run
     a.seen = chk->seen;
     a.stall = chk->stall;
     a.stop_t = chk->stop_t;
+    a.check_trace = chk->trace;
   }
   // every wave's counters start from zero; waves use disjoint counters
   QH_CUDA_TRY(cudaMemsetAsync(rb.done, 0, (size_t)rb.n_done * 4, ctx->stream));

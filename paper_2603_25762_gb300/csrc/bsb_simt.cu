@@ -1138,6 +1138,25 @@ void launch_pick_best(cudaStream_t s, int32_t n_blocks, int32_t R, const double*
   if (n_blocks > 0) k_pick_best<<<::qh::counted(n_blocks), 256, 0, s>>>(n_blocks, R, cuts, best_r, best_cut, active);
 }
 
+// One row of the energy-check trace: each block's best cut over the replicas at the check
+// after t_done steps, NaN for a block that is not running (stopped early, or not solved)
+// or whose schedule has ended (the checks inside the multi-step launch skip those too).
+__global__ void k_trace_check(int32_t n_blocks, const double* __restrict__ best_cut,
+                              const int32_t* __restrict__ running, int32_t t_done,
+                              const int32_t* __restrict__ steps_b, double* row) {
+  const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < n_blocks)
+    row[b] = running[b] && t_done < steps_b[b] ? best_cut[b] : __longlong_as_double(-1ll);
+}
+
+void launch_trace_check(cudaStream_t s, int32_t n_blocks, const double* best_cut,
+                        const int32_t* running, int32_t t_done, const int32_t* steps_b,
+                        double* row) {
+  if (n_blocks > 0)
+    k_trace_check<<<::qh::counted(nblk(n_blocks)), 256, 0, s>>>(n_blocks, best_cut, running,
+                                                                t_done, steps_b, row);
+}
+
 void launch_early_stop(cudaStream_t s, int32_t n_blocks, const double* best_cut, double* best_seen,
                        int32_t* stall, int32_t* active, int32_t* steps_run, int32_t patience,
                        int32_t t_done, const int32_t* steps_b) {

@@ -152,6 +152,10 @@ struct Solution {
   // solves run over the graph, and per block whether it still refines, its deformation
   // field and re-solves used; per vertex the gauge the next solve starts from
   int32_t refine_done = 0;
+  // energy checks of the first solve: [checks][n_blocks] best cut per check (NaN: the
+  // block was not running), checks every check_every steps
+  std::vector<double> check_trace;
+  int32_t check_every = 0;
   std::vector<int32_t> refining, refine_tries;
   std::vector<float> refine_deform;
   std::vector<int8_t> refine_gauge;
@@ -318,6 +322,11 @@ void launch_cut(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t
                 const double* sum_w, double* node_val, double* cuts, const int32_t* active);
 void launch_pick_best(cudaStream_t s, int32_t n_blocks, int32_t R, const double* cuts,
                       int32_t* best_r, double* best_cut, const int32_t* active);
+// row[b] = best_cut[b] where running[b] and t_done < steps_b[b], else NaN (one check of
+// the energy trace)
+void launch_trace_check(cudaStream_t s, int32_t n_blocks, const double* best_cut,
+                        const int32_t* running, int32_t t_done, const int32_t* steps_b,
+                        double* row);
 void launch_early_stop(cudaStream_t s, int32_t n_blocks, const double* best_cut, double* best_seen,
                        int32_t* stall, int32_t* active, int32_t* steps_run, int32_t patience,
                        int32_t t_done, const int32_t* steps_b);
@@ -436,6 +445,7 @@ struct RunCheck {
   double* seen = nullptr;            // [n_blocks]
   int32_t* stall = nullptr;          // [n_blocks]
   int32_t* stop_t = nullptr;         // [n_blocks]
+  double* trace = nullptr;           // [checks][n_blocks] best cut per check, or nullptr
 };
 // Steps t0 .. t1-1 in one launch.  X_hat_t is read from xh0 (t even) or xh1 (t odd);
 // x, y of `s` are updated in place.

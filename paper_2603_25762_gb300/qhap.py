@@ -99,6 +99,7 @@ _SIGS = {
     "qh_bsb_solve_blocks": (C.c_int, [P, P, C.POINTER(QhBsbOpts), P, I32, PP]),
     "qh_bsb_solve_resume": (C.c_int, [P, P, C.POINTER(QhBsbOpts), C.POINTER(QhRefineState), PP]),
     "qh_solution_refine_state": (C.c_int, [P, C.POINTER(QhRefineState)]),
+    "qh_solution_check_trace": (C.c_int, [P, P, P, P]),
     "qh_solution_set_block": (C.c_int, [P, P, I32, P, D, I32, I32, I32]),
     "qh_solution_block": (C.c_int, [P, P, I32, P, P, P, P, P]),
     "qh_solution_spins": (C.c_int, [P, P, P]),
@@ -250,6 +251,15 @@ class Solution:
                for k, v in st.items()}
         out["iterations_done"] = rs.iterations_done
         return out
+
+    def check_trace(self):
+        """The first solve's energy checks: (check_every, array [checks][n_blocks] of each
+        block's best cut per check, NaN where the block was not running)."""
+        n, ce = I32(), I32()
+        self.ctx._check(lib().qh_solution_check_trace(self.h, C.byref(n), C.byref(ce), None))
+        tr = np.zeros(max(n.value * self.n_blocks, 1))
+        self.ctx._check(lib().qh_solution_check_trace(self.h, C.byref(n), None, _ptr(tr)))
+        return ce.value, tr[: n.value * self.n_blocks].reshape(n.value, self.n_blocks)
 
     def spins(self, n_nodes):
         s = np.zeros(max(n_nodes, 1), np.int8)

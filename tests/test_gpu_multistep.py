@@ -163,6 +163,20 @@ def _stop_case(q, ctx, g, R, steps, seed, kernel, check_every, patience, blocks=
         for key in ("steps_run", "best_cut", "best_replica"):
             assert bi[key] == bb[key], (b, key, bi[key], bb[key])
         runs.append(bi["steps_run"])
+    # the energy-check trace: the same best cut per block and check on both paths, a value
+    # up to the check a block stopped at and NaN after it
+    (cei, tri), (ceb, trb) = inside.check_trace(), between.check_trace()
+    assert cei == ceb == check_every and tri.shape == ((steps - 1) // check_every, g.n_blocks)
+    assert np.array_equal(tri, trb, equal_nan=True)
+    for b in range(g.n_blocks):
+        col = tri[:, b]
+        if blocks is not None and b not in blocks:
+            assert np.isnan(col).all()
+            continue
+        n_rec = runs[b] // check_every if runs[b] < steps else col.size
+        assert np.isfinite(col[:n_rec]).all() and np.isnan(col[n_rec:]).all(), b
+        if runs[b] < steps:  # stopped: its last `patience` checks did not beat the best before
+            assert col[n_rec - patience:n_rec].max() <= col[:n_rec - patience].max(), b
     return runs
 
 

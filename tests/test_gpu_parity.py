@@ -520,6 +520,30 @@ def test_early_stop_steps_run_matches_oracle(q, ctx, oracle, precision, R):
         assert info["best_cut"] >= 0.999 * best
 
 
+def test_check_trace_matches_oracle(q, ctx, oracle):
+    """The energy-check trace (Results: the energy against the iterations) at FP32: each
+    check's best cut over the replicas equals the oracle's, whose replicas are advanced
+    check by check and cut-evaluated exactly (same seed, steps and replica indices)."""
+    fr = synth.tiny_reads(1001)
+    g = ctx.build_graph(fr)
+    R, steps, seed, ce = 32, 600, 2, 50
+    sol = ctx.solve(g, replicas=R, steps=steps, precision=q.PREC_FP32, seed=seed,
+                    check_every=ce, patience=1000)  # checks on, no block stops
+    got_ce, tr = sol.check_trace()
+    assert got_ce == ce and tr.shape == ((steps - 1) // ce, g.n_blocks)
+    og = oracle.read_graph(fr, oracle.READ_SIGNED)
+    for b, nodes in enumerate(oracle.blocks_of(og)):
+        sub = og.subgraph(nodes)
+        x, y = oracle.bsb_init(sub.n, list(range(R)), seed, b)
+        t = 0
+        for c in range(tr.shape[0]):
+            x, y = oracle.bsb_run(sub, x, y, t, (c + 1) * ce, steps)
+            t = (c + 1) * ce
+            best = max(oracle.cut(sub, np.where(x[r] >= 0, 1, -1).astype(np.int8))
+                       for r in range(R))
+            assert tr[c, b] == pytest.approx(best, rel=1e-3), (b, c, tr[c, b], best)
+
+
 @pytest.mark.parametrize("precision,R,pat,kernel", [(0, 32, 0, None), (0, 32, 3, None),
                                                      (1, 64, 0, None),
                                                      (1, 128, 3, "multistep-stream-tile")])
