@@ -189,6 +189,28 @@ __device__ __forceinline__ void cand_range(int32_t m, const int32_t* sfirst, con
 
 // Warp per fragment a: pass 0 counts w != 0 partners, pass 1 writes them in
 // first-SNP order (deterministic positions from warp ballots).
+// Fragment a's alleles as a dense window over its SNP range (0 where a has no allele),
+// in shared memory, when the range spans at most READ_WIN SNPs: a pair's weight is then
+// one walk over the other fragment's SNP list with a lookup per SNP, in place of a
+// merge of both lists.
+constexpr int READ_WIN = 1024;
+
+// Exact weight of the pair (a, b) from a's allele window (SNPs fa .. fa + READ_WIN - 1).
+__device__ __forceinline__ int32_t pair_weight_win(const int32_t* __restrict__ snp,
+                                                   const int8_t* __restrict__ allele,
+                                                   const int8_t* win, int32_t fa, int32_t la,
+                                                   int64_t bb, int64_t be, int mode) {
+  int32_t w = 0;
+  for (int64_t k = bb; k < be; ++k) {
+    const int32_t j = snp[k];
+    if (j > la) break;  // b's list is sorted
+    if (j < fa) continue;
+    const int prod = (int)win[j - fa] * (int)allele[k];
+    w += (mode == QH_WEIGHT_CONFLICT) ? (prod == -1 ? 1 : 0) : -prod;
+  }
+  return w;
+}
+
 template <int PASS>
 __global__ void k_read_edges(int32_t m, const int64_t* __restrict__ fp, const int32_t* __restrict__ snp,
                              const int8_t* __restrict__ allele, const int32_t* __restrict__ first,
@@ -196,6 +218,7 @@ __global__ void k_read_edges(int32_t m, const int64_t* __restrict__ fp, const in
                              const int32_t* __restrict__ sfirst, const int32_t* __restrict__ slast,
                              const int32_t* __restrict__ pmax_last, int mode, int64_t* cnt,
                              const int64_t* __restrict__ row_ptr, int32_t* col, double* w) {
+  __shared__ int8_t win_all[256 / 32][READ_WIN];
   int32_t a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (a >= m) return;
@@ -205,6 +228,14 @@ __global__ void k_read_edges(int32_t m, const int64_t* __restrict__ fp, const in
     return;
   }
   int32_t fa = first[a], la = last[a];
+  int8_t* win = win_all[threadIdx.x >> 5];
+  const bool use_win = la - fa < READ_WIN;  // warp-uniform
+  if (use_win) {
+    for (int32_t j = lane; j <= la - fa; j += 32) win[j] = 0;
+    __syncwarp();
+    for (int64_t k = ab + lane; k < ae; k += 32) win[snp[k] - fa] = allele[k];
+    __syncwarp();
+  }
   int32_t lo, hi;
   cand_range(m, sfirst, pmax_last, fa, la, &lo, &hi);
   int64_t count = 0;
@@ -216,7 +247,8 @@ __global__ void k_read_edges(int32_t m, const int64_t* __restrict__ fp, const in
     if (q < hi) {
       b = order[q];
       if (b != a && slast[q] >= fa && sfirst[q] <= la)
-        wv = pair_weight(snp, allele, ab, ae, fp[b], fp[b + 1], mode);
+        wv = use_win ? pair_weight_win(snp, allele, win, fa, la, fp[b], fp[b + 1], mode)
+                     : pair_weight(snp, allele, ab, ae, fp[b], fp[b + 1], mode);
     }
     unsigned mask = __ballot_sync(0xffffffffu, wv != 0);
     if (PASS == 1 && wv != 0) {
@@ -538,8 +570,12 @@ __global__ void k_uf_hook(int32_t n, const int64_t* __restrict__ rp, const int32
         x = y;
         y = t;
       }
-      // x > y: hook root x under y
-      if (atomicCAS(&parent[x], x, y) == x) break;
+      // x > y: hook root x under y.  A failed CAS returns x's current parent, read at
+      // L2: continue from there, so that a stale root cached in this SM's L1 cannot make
+      // the loop retry forever (each retry starts from a strictly smaller vertex).
+      const int32_t old = atomicCAS(&parent[x], x, y);
+      if (old == x) break;
+      x = old;
     }
   }
 }

@@ -59,6 +59,30 @@ def test_read_graph_bitexact(q, ctx, oracle, make, mode):
     assert np.array_equal(w1, w2)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_read_graph_wide_fragments_bitexact(q, ctx, oracle, mode):
+    # fragments whose SNPs spread over more than 1,024 SNP indices (linked-read-like
+    # spans) take the merge of both SNP lists instead of the allele window
+    rng = np.random.default_rng(12)
+    n, rows = 6000, []
+    for i in range(150):
+        k = int(rng.integers(2, 40))
+        lo = int(rng.integers(0, n - 3000))
+        span = int(rng.choice([200, 3000]))
+        rows.append(np.sort(rng.choice(np.arange(lo, lo + span), size=k, replace=False)))
+    ptr = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    snp = np.concatenate(rows).astype(np.int32)
+    allele = np.where(rng.random(snp.size) < 0.5, 1, -1).astype(np.int8)
+    qual = np.full(snp.size, 30, np.uint8)
+    fr = synth.Fragments(n, ptr, snp, allele, qual, np.zeros(len(rows), np.uint8),
+                         np.arange(n), np.ones(n, np.int8))
+    g = ctx.build_graph(fr, mode=q.MODE_READ, weight_mode=mode)
+    r1, c1, w1 = _sorted_csr(*g.edges())
+    r2, c2, w2 = _oracle_edges(oracle.read_graph(fr, mode))
+    assert r1.size > 0
+    assert np.array_equal(r1, r2) and np.array_equal(c1, c2) and np.array_equal(w1, w2)
+
+
 @pytest.mark.parametrize("k", [10, 4])
 def test_snp_graph_parity(q, ctx, oracle, k):
     fr = synth.ont_region(1003, scale=0.06)
