@@ -93,7 +93,8 @@ enum {
   S_STEPSB, S_C0, S_SEEN, S_STALL, S_STEPSRUN, S_SPINS, S_C, S_WWORK, S_TBWORK, S_TFWORK,
   S_SUMW, S_SUMJ2, S_NODETMP, S_SIGNS1, S_NODEVAL1, S_CUT1, S_DBG0, S_DBG1, S_DBG2, S_RUNNING,
   S_PVWORK, S_TR0, S_TR1, S_F8H, S_F8L, S_F8FLAG, S_X8, S_DEFORM, S_TRIES, S_DBGDEF,
-  S_ZBAND, S_BANDWORK, S_RVWORK, S_TRACE, S_KCUT, S_KR, S_KFLAG, S_KSPINS, S_GAUGE, S_CTRACE
+  S_ZBAND, S_BANDWORK, S_RVWORK, S_TRACE, S_KCUT, S_KR, S_KFLAG, S_KSPINS, S_GAUGE, S_CTRACE,
+  S_CUTS_S, S_CUTS_Z
 };
 
 struct SolveBufs {
@@ -114,6 +115,9 @@ struct SolveBufs {
   int8_t* kept_spins;
   int8_t* gauge;    // SNP mode: product of the partitions the weights are inverted by
   double* trace;    // energy checks: [checks][n_blocks] best cut of each check (NaN: none)
+  // per-replica cuts on the tensor cores: the signs S in BF16 and z = J S, [R][n_pad]
+  __nv_bfloat16* cut_s;
+  float* cut_z;
 };
 
 qh_status run_step(Ctx* ctx, const Graph& g, int precision, const TcPlan& plan, StepArgs a,
@@ -751,6 +755,20 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
   const int32_t n_checks = checking ? (max_steps - 1) / o->check_every : 0;
   B.trace = n_checks > 0 ? (double*)ctx->scratch((size_t)n_checks * nb * 8, S_CTRACE) : nullptr;
   if (n_checks > 0 && !B.trace) return set_err(ctx, QH_ENOMEM, "allocation failed (check trace)");
+  // The replicas' cuts (every check and the end of each solve) as one product z = J S on
+  // the tensor cores, S = sgn(x) in BF16, instead of a gather per edge: exact when the
+  // weights are integers and every row sum of |J| stays below 2^24 (FP32 accumulation),
+  // on tile storage with R a multiple of 64.
+  bool tc_cut = !W.csr_mode && W.integer_weights && W.n_tiles > 0 && R % 64 == 0;
+  if (tc_cut) {
+    int32_t max_n = 0;
+    for (int32_t b = 0; b < nb; ++b) max_n = std::max(max_n, W.h_block_size[b]);
+    tc_cut = W.max_abs_w * (double)max_n < 16777216.0;
+  }
+  B.cut_s = tc_cut ? (__nv_bfloat16*)ctx->scratch(NS * 2, S_CUTS_S) : nullptr;
+  B.cut_z = tc_cut ? (float*)ctx->scratch(NS * 4, S_CUTS_Z) : nullptr;
+  if (tc_cut && (!B.cut_s || !B.cut_z))
+    return set_err(ctx, QH_ENOMEM, "allocation failed (tensor-core cuts)");
   // ---- the step loop, captured once per shape and replayed
   // The captured step loop bakes in pointers and sizes; it is replayed only when every
   // one of them is unchanged (a rebuilt graph at other addresses is captured anew).
@@ -784,7 +802,8 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
                           (const void*)B.cuts, (const void*)B.best_r, (const void*)B.best_cut,
                           (const void*)B.running, (const void*)B.steps_b, (const void*)B.c0,
                           (const void*)B.seen, (const void*)B.stall, (const void*)B.steps_run,
-                          (const void*)ctx->d_err, (const void*)B.deform, (const void*)B.trace})
+                          (const void*)ctx->d_err, (const void*)B.deform, (const void*)B.trace,
+                          (const void*)B.cut_s, (const void*)B.cut_z})
       add(p);
   }
   StepArgs a{};
@@ -876,6 +895,24 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
     chk.decided = chk.e_cnt + 2 * nb;
     chk.stop_t = reinterpret_cast<int32_t*>(chk.e_cnt + 3 * nb);
   }
+  // every replica's cut of the state x (signs into B.signs for the picks and spins)
+  auto replica_cuts = [&](const float* xc, const int32_t* act) -> qh_status {
+    launch_signs(s, W, R, xc, B.signs);
+    if (!tc_cut) {
+      launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, act);
+      return QH_OK;
+    }
+    launch_x_operand(s, W, QH_SB_DISCRETE, xc, B.cut_s, (int64_t)NS);
+    StepArgs az = a;
+    az.z_out = B.cut_z;
+    az.t = 0;
+    az.active = act;
+    az.use_lo = W.has_lo ? 1 : 0;
+    qh_status st = launch_step_tc(ctx, W, az, B.cut_s, pick_plan(R));
+    if (st != QH_OK) return st;
+    launch_cut_from_product(s, W, R, B.cut_z, B.cut_s, sum_w_work, B.node_val, B.cuts, act);
+    return QH_OK;
+  };
   if (!multistep && (ctx->loop_key != skey || !ctx->loop_exec)) {
     if (ctx->loop_exec) {
       cudaGraphExecDestroy(ctx->loop_exec);
@@ -894,8 +931,7 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
                     even ? B.xh0 : B.xh1, even ? B.xh1 : B.xh0, &f8, (int64_t)NS, B.zband);
       if (checking && (t + 1) % o->check_every == 0 && t + 1 < max_steps) {
         const float* xc = (o->precision == QH_PREC_FP32 && even) ? B.x1 : B.x;
-        launch_signs(s, W, R, xc, B.signs);
-        launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.running);
+        if (st == QH_OK) st = replica_cuts(xc, B.running);
         launch_pick_best(s, nb, R, B.cuts, B.best_r, B.best_cut, B.running);
         launch_trace_check(s, nb, B.best_cut, B.running, t + 1, B.steps_b,
                            B.trace + (size_t)((t + 1) / o->check_every - 1) * nb);
@@ -973,8 +1009,8 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
         qh_status st = launch_run(ctx, W, a, rb, B.xh0, B.xh1, t0, t1);
         if (st != QH_OK) return st;
         if (checking && t1 < max_steps) {
-          launch_signs(s, W, R, B.x, B.signs);
-          launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.running);
+          st = replica_cuts(B.x, B.running);
+          if (st != QH_OK) return st;
           launch_pick_best(s, nb, R, B.cuts, B.best_r, B.best_cut, B.running);
           launch_trace_check(s, nb, B.best_cut, B.running, t1, B.steps_b,
                              B.trace + (size_t)(t1 / o->check_every - 1) * nb);
@@ -991,8 +1027,10 @@ static qh_status solve_impl(qh_ctx* h, const qh_graph* gh, const qh_bsb_opts* o,
       note_launch(ctx->loop_kernels);
     }
     QH_CUDA_TRY(cudaEventRecord(ctx->ev[3], s));
-    launch_signs(s, W, R, x_final, B.signs);
-    launch_cut(s, W, R, B.signs, W.w, sum_w_work, B.node_val, B.cuts, B.active);
+    {
+      qh_status st = replica_cuts(x_final, B.active);
+      if (st != QH_OK) return st;
+    }
     launch_pick_best(s, nb, R, B.cuts, B.best_r, B.best_cut, B.active);
     launch_extract_spins(s, W, R, B.signs, B.best_r, B.spins, B.active);
     if (track)  // the best result during the run, unless the final one is strictly better

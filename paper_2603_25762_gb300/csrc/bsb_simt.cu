@@ -711,6 +711,45 @@ __global__ void __launch_bounds__(1024) k_cut_reduce(int32_t nb, const int32_t* 
   }
 }
 
+// Cuts from the product z = J S of the replicas' signs (tensor cores, exact for integer
+// weights whose row sums of |J| stay below 2^24): cut_r = (sum W + sum_a s_a z_a) / 4
+// (J = -W).  z, S in the state layout [R][n_pad].  CTA (replica group, chunk, block): a
+// warp per replica, the lanes striding over the chunk's CUT_CHUNK padded columns; each
+// warp's integer partial sum goes into acc[b][r] by an FP64 atomic add, exact and so
+// independent of the order.  k_cut_finish then forms the cuts.
+constexpr int CUT_CHUNK = 512;
+
+__global__ void __launch_bounds__(1024) k_cut_from_product(
+    const int32_t* __restrict__ pad_off, const int64_t* __restrict__ block_ptr, int32_t R,
+    int32_t n_pad, const float* __restrict__ z, const __nv_bfloat16* __restrict__ s,
+    double* acc, const int32_t* __restrict__ active) {
+  const int32_t b = blockIdx.z;
+  if (active != nullptr && !active[b]) return;
+  const int32_t sz = (int32_t)(block_ptr[b + 1] - block_ptr[b]);
+  const int32_t c0 = blockIdx.y * CUT_CHUNK;
+  if (c0 >= sz) return;
+  const int lane = threadIdx.x & 31;
+  const int32_t r = blockIdx.x * 32 + (threadIdx.x >> 5);
+  if (r >= R) return;
+  const int32_t c1 = min(sz, c0 + CUT_CHUNK);
+  const size_t row = (size_t)r * n_pad + pad_off[b];
+  double t = 0.0;
+  for (int32_t p = c0 + lane; p < c1; p += 32) t += (double)(__bfloat162float(s[row + p]) * z[row + p]);
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) atomicAdd(acc + (size_t)b * R + r, t);
+}
+
+__global__ void k_cut_finish(int32_t nb, int32_t R, const double* __restrict__ acc,
+                             const double* __restrict__ sum_w, double* cuts,
+                             const int32_t* __restrict__ active) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)nb * R) return;
+  const int32_t b = (int32_t)(i / R);
+  if (active != nullptr && !active[b]) return;
+  cuts[i] = 0.25 * (sum_w[b] + acc[i]);
+}
+
 __global__ void k_pick_best(int32_t nb, int32_t R, const double* __restrict__ cuts, int32_t* best_r,
                             double* best_cut, const int32_t* __restrict__ active) {
   __shared__ double sv[256];
@@ -1131,6 +1170,20 @@ void launch_cut(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t
   dim3 grid((R + 31) / 32, g.n_blocks);
   k_cut_reduce<<<::qh::counted(grid), 1024, 0, s>>>(g.n_blocks, g.pad_off, g.block_ptr, R, node_val, sum_w, cuts,
                                      active);
+}
+
+void launch_cut_from_product(cudaStream_t s, const Graph& g, int32_t R, const float* z,
+                             const __nv_bfloat16* signs, const double* sum_w, double* acc,
+                             double* cuts, const int32_t* active) {
+  if (g.n_blocks == 0) return;
+  int32_t max_n = 0;
+  for (int32_t b = 0; b < g.n_blocks; ++b) max_n = std::max(max_n, g.h_block_size[b]);
+  cudaMemsetAsync(acc, 0, (size_t)g.n_blocks * R * 8, s);
+  dim3 grid((R + 31) / 32, (max_n + CUT_CHUNK - 1) / CUT_CHUNK, g.n_blocks);
+  k_cut_from_product<<<::qh::counted(grid), 1024, 0, s>>>(g.pad_off, g.block_ptr, R, g.n_pad, z,
+                                                          signs, acc, active);
+  k_cut_finish<<<::qh::counted(nblk((int64_t)g.n_blocks * R)), 256, 0, s>>>(g.n_blocks, R, acc,
+                                                                          sum_w, cuts, active);
 }
 
 void launch_pick_best(cudaStream_t s, int32_t n_blocks, int32_t R, const double* cuts,

@@ -323,6 +323,12 @@ void launch_cut(cudaStream_t s, const Graph& g, int32_t R, const int8_t* signs_t
 void launch_pick_best(cudaStream_t s, int32_t n_blocks, int32_t R, const double* cuts,
                       int32_t* best_r, double* best_cut, const int32_t* active);
 // row[b] = best_cut[b] where running[b] and t_done < steps_b[b], else NaN (one check of
+// Per-replica cuts from z = J S (S = the replicas' signs in BF16, both [R][n_pad]):
+// cut = (sum_w + sum_a s_a z_a) / 4, exact for integer weights (row sums of |J| < 2^24).
+// acc: n_blocks * R doubles of scratch.
+void launch_cut_from_product(cudaStream_t s, const Graph& g, int32_t R, const float* z,
+                             const __nv_bfloat16* signs, const double* sum_w, double* acc,
+                             double* cuts, const int32_t* active);
 // the energy trace)
 void launch_trace_check(cudaStream_t s, int32_t n_blocks, const double* best_cut,
                         const int32_t* running, int32_t t_done, const int32_t* steps_b,
