@@ -994,15 +994,27 @@ __global__ void k_vote(int32_t n, const int64_t* __restrict__ cov_ptr, const int
   int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   int64_t b0 = cov_ptr[j], b1 = cov_ptr[j + 1];
+  // the block most of the SNP's fragments belong to (ties: the lower block); usually
+  // they all belong to one, which one pass finds
   int32_t best = -1, bestc = 0;
-  for (int64_t k = b0; k < b1; ++k) {
-    int32_t bk = block_of[cov_frag[k]];
+  bool one = true;
+  for (int64_t k = b0; k < b1 && one; ++k) {
+    const int32_t bk = block_of[cov_frag[k]];
     if (bk < 0) continue;
-    int32_t c = 0;
-    for (int64_t q = b0; q < b1; ++q) c += block_of[cov_frag[q]] == bk;
-    if (c > bestc || (c == bestc && bk < best)) {
-      bestc = c;
-      best = bk;
+    if (best < 0) best = bk;
+    one = bk == best;
+  }
+  if (!one) {
+    best = -1;
+    for (int64_t k = b0; k < b1; ++k) {
+      int32_t bk = block_of[cov_frag[k]];
+      if (bk < 0) continue;
+      int32_t c = 0;
+      for (int64_t q = b0; q < b1; ++q) c += block_of[cov_frag[q]] == bk;
+      if (c > bestc || (c == bestc && bk < best)) {
+        bestc = c;
+        best = bk;
+      }
     }
   }
   int8_t h = 0;
