@@ -23,26 +23,29 @@ namespace qh {
 namespace {
 
 // ------------------------------------------------------------------ validate
-__global__ void k_validate(int32_t m, int32_t n, const int64_t* __restrict__ fp,
+// Warp per fragment, the lanes striding over its entries (each compares its SNP with the
+// entry before it).  A fragment range outside [0, nnz] is flagged before any entry of it
+// is read.
+__global__ void k_validate(int32_t m, int32_t n, int64_t nnz, const int64_t* __restrict__ fp,
                            const int32_t* __restrict__ snp, const int8_t* __restrict__ allele,
                            const uint8_t* __restrict__ qual, int check_qual, int32_t* err) {
-  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (i >= m) return;
   int64_t b = fp[i], e = fp[i + 1];
-  if (e < b) {
-    atomicOr(err, ERR_INPUT);
+  if (e < b || b < 0 || e > nnz) {
+    if (lane == 0) atomicOr(err, ERR_INPUT);
     return;
   }
-  int32_t prev = -1;
-  for (int64_t k = b; k < e; ++k) {
+  for (int64_t k = b + lane; k < e; k += 32) {
     int32_t s = snp[k];
     int8_t a = allele[k];
-    if (s < 0 || s >= n || s <= prev || (a != 1 && a != -1)) atomicOr(err, ERR_INPUT);
+    if (s < 0 || s >= n || (k > b && s <= snp[k - 1]) || (a != 1 && a != -1))
+      atomicOr(err, ERR_INPUT);
     if (check_qual) {
       uint8_t q = qual[k];
       if (q < 4 || q > 93) atomicOr(err, ERR_QUAL);
     }
-    prev = s;
   }
 }
 
@@ -52,12 +55,15 @@ __global__ void k_cov_count(int64_t nnz, const int32_t* __restrict__ snp, int32_
   if (k < nnz) atomicAdd(&cnt[snp[k]], 1);
 }
 
+// Warp per fragment, the lanes taking its entries in parallel: the order within a SNP's
+// list is set afterwards by k_cov_sort.
 __global__ void k_cov_fill(int32_t m, const int64_t* __restrict__ fp, const int32_t* __restrict__ snp,
                            const int8_t* __restrict__ allele, const int64_t* __restrict__ cov_ptr,
                            int32_t* cursor, int32_t* cov_frag, int8_t* cov_allele) {
-  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  for (int64_t k = fp[i]; k < fp[i + 1]; ++k) {
+  const int64_t i64 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (i64 >= m) return;
+  const int32_t i = (int32_t)i64;
+  for (int64_t k = fp[i] + (threadIdx.x & 31); k < fp[i + 1]; k += 32) {
     int32_t s = snp[k];
     int64_t slot = cov_ptr[s] + atomicAdd(&cursor[s], 1);
     cov_frag[slot] = i;
@@ -873,7 +879,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
   // ---- validate
   QH_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), s));
   if (m > 0)
-    k_validate<<<::qh::counted(nblk(m)), 256, 0, s>>>(m, n, g->frag_ptr, g->snp, g->allele, g->qual,
+    k_validate<<<::qh::counted(nblk((int64_t)m * 32)), 256, 0, s>>>(m, n, nnz_f, g->frag_ptr, g->snp, g->allele, g->qual,
                                        o->mode == QH_MODE_SNP && f->qual != nullptr ? 1 : 0,
                                        ctx->d_err);
   int32_t herr = 0;
@@ -897,7 +903,7 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
     if (!scan_i32_to_i64(ctx, s, cnt, g->cov_ptr, n)) return set_err(ctx, QH_ENOMEM, "allocation failed (scan)");
     QH_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), s));
     if (m > 0)
-      k_cov_fill<<<::qh::counted(nblk(m)), 256, 0, s>>>(m, g->frag_ptr, g->snp, g->allele, g->cov_ptr, cnt,
+      k_cov_fill<<<::qh::counted(nblk((int64_t)m * 32)), 256, 0, s>>>(m, g->frag_ptr, g->snp, g->allele, g->cov_ptr, cnt,
                                          g->cov_frag, g->cov_allele);
     if (n > 0) k_cov_sort<<<::qh::counted(nblk((int64_t)n * 32)), 256, 0, s>>>(n, g->cov_ptr, g->cov_frag, g->cov_allele);
   }

@@ -168,6 +168,15 @@ def test_invalid_inputs_rejected(q, ctx):
     bad3.qual[2] = 3
     with pytest.raises(q.QhError):
         ctx.build_graph(bad3, mode=q.MODE_SNP)
+    # a fragment range past the end of the entries (frag_ptr not monotone): rejected
+    # before any of its entries is read
+    fp4 = fr.frag_ptr.copy()
+    fp4[1] = fp4[-1] + 40
+    bad4 = synth.Fragments(fr.n_snps, fp4, fr.snp, fr.allele, fr.qual, fr.is_porec,
+                           fr.positions, fr.truth)
+    with pytest.raises(q.QhError) as e:
+        ctx.build_graph(bad4)
+    assert e.value.status == q.QH_EINVAL
     # the context stays usable after rejected inputs
     g = ctx.build_graph(fr)
     assert g.n_nodes == fr.n_frags
