@@ -1,5 +1,6 @@
-"""The library's initial-state draw (csrc/draw.cuh) evaluates the FP64 expression
-u * 0.2 - 0.1, rounded once to FP32, in integer arithmetic. The header is plain C++,
+"""The library's initial-state draw (csrc/draw.cuh) obtains the FP32 rounding of the
+FP64 expression u * 0.2 - 0.1 with one FP32 multiply and one fused multiply-add, and
+rests that on an exhaustive comparison rather than an error bound. The header is plain C++,
 so the host compiler checks it here against that FP64 expression for every one of
 the 2^24 values the draw's 24-bit uniform takes, and checks its SplitMix64 stream
 against the published first outputs for seed 0.
