@@ -559,30 +559,86 @@ __global__ void k_uf_init(int32_t n, int32_t* parent) {
   if (v < n) parent[v] = v;
 }
 
-__global__ void k_uf_hook(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                          const double* __restrict__ w, int32_t* parent) {
+// Union of the sets of x and y: the larger root is hooked under the smaller, so every
+// component ends with its smallest vertex as root, whatever order the unions run in.
+__device__ __forceinline__ void uf_union(int32_t* parent, int32_t x, int32_t y) {
+  while (true) {
+    x = uf_find(parent, x);
+    y = uf_find(parent, y);
+    if (x == y) return;
+    if (x < y) {
+      int32_t t = x;
+      x = y;
+      y = t;
+    }
+    // x > y: hook root x under y.  A failed CAS returns x's current parent, read at
+    // L2: continue from there, so that a stale root cached in this SM's L1 cannot make
+    // the loop retry forever (each retry starts from a strictly smaller vertex).
+    const int32_t old = atomicCAS(&parent[x], x, y);
+    if (old == x) return;
+    x = old;
+  }
+}
+
+// Components by subgraph sampling (Sutton, Ben-Nun & Barak, "Optimizing parallel graph
+// connectivity computation via subgraph sampling", IPDPS 2018): each vertex first links
+// its first UF_LINK_FIRST adjacency entries; a sample of the vertices then names the
+// largest component so far; only vertices outside it go through their other entries.
+// An entry (a, b) past a's first ones is taken by a when b > a or b is in the sampled
+// component, so every edge not already inside that component is taken by at least one
+// endpoint (or by a phase-one link), and the partition is the one all edges give.
+constexpr int UF_LINK_FIRST = 2;
+constexpr int UF_SAMPLES = 1024;
+
+__global__ void k_uf_link_first(int32_t n, const int64_t* __restrict__ rp,
+                                const int32_t* __restrict__ col, const double* __restrict__ w,
+                                int32_t* parent) {
   int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= n) return;
-  for (int64_t e = rp[a]; e < rp[a + 1]; ++e) {
-    int32_t b = col[e];
-    if (b <= a || w[e] == 0.0) continue;
-    int32_t x = a, y = b;
-    while (true) {
-      x = uf_find(parent, x);
-      y = uf_find(parent, y);
-      if (x == y) break;
-      if (x < y) {
-        int32_t t = x;
-        x = y;
-        y = t;
-      }
-      // x > y: hook root x under y.  A failed CAS returns x's current parent, read at
-      // L2: continue from there, so that a stale root cached in this SM's L1 cannot make
-      // the loop retry forever (each retry starts from a strictly smaller vertex).
-      const int32_t old = atomicCAS(&parent[x], x, y);
-      if (old == x) break;
-      x = old;
-    }
+  const int64_t e1 = min(rp[a] + UF_LINK_FIRST, rp[a + 1]);
+  for (int64_t e = rp[a]; e < e1; ++e) {
+    const int32_t b = col[e];
+    if (b != a && w[e] != 0.0) uf_union(parent, a, b);
+  }
+}
+
+// One block of UF_SAMPLES threads: the root that most of the evenly spaced sample
+// vertices reach (ties to the larger root; any choice is correct).
+__global__ void __launch_bounds__(UF_SAMPLES) k_uf_sample(int32_t n, int32_t* parent,
+                                                          int32_t* giant) {
+  __shared__ int32_t roots[UF_SAMPLES];
+  __shared__ unsigned long long best;
+  const int i = threadIdx.x;
+  const int64_t v = n >= UF_SAMPLES ? (int64_t)i * n / UF_SAMPLES : (i < n ? i : -1);
+  const int32_t r = v >= 0 ? uf_find(parent, (int32_t)v) : -1;
+  roots[i] = r;
+  if (i == 0) best = 0ull;
+  __syncthreads();
+  if (r >= 0) {
+    uint32_t c = 0;
+    for (int j = 0; j < UF_SAMPLES; ++j) c += roots[j] == r ? 1u : 0u;
+    atomicMax(&best, ((unsigned long long)c << 32) | (uint32_t)r);
+  }
+  __syncthreads();
+  if (i == 0) giant[0] = best != 0ull ? (int32_t)(best & 0xFFFFFFFFull) : -1;
+}
+
+__global__ void k_uf_flag(int32_t n, int32_t* parent, const int32_t* __restrict__ giant,
+                          int32_t* in_giant) {
+  int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) in_giant[v] = uf_find(parent, v) == giant[0] ? 1 : 0;
+}
+
+__global__ void k_uf_link_rest(int32_t n, const int64_t* __restrict__ rp,
+                               const int32_t* __restrict__ col, const double* __restrict__ w,
+                               const int32_t* __restrict__ in_giant, int32_t* parent) {
+  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n || in_giant[a]) return;
+  const int64_t e1 = rp[a + 1];
+  for (int64_t e = rp[a] + UF_LINK_FIRST; e < e1; ++e) {
+    const int32_t b = col[e];
+    if (b == a || (b < a && !in_giant[b]) || w[e] == 0.0) continue;
+    uf_union(parent, a, b);
   }
 }
 
@@ -1034,7 +1090,13 @@ qh_status build_graph_device(Ctx* ctx, const qh_fragments* f, const qh_graph_opt
   QH_CUDA_TRY(cudaMemsetAsync(g->pad_index, 0xff, sizeof(int32_t) * std::max(N, 1), s));
   if (N > 0) {
     k_uf_init<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, parent);
-    k_uf_hook<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, parent);
+    // label holds the sampled-component flags and isroot[0] the sampled root until
+    // the compression and the root marks below overwrite them
+    k_uf_link_first<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, parent);
+    k_uf_sample<<<::qh::counted(1), UF_SAMPLES, 0, s>>>(N, parent, isroot);
+    k_uf_flag<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, parent, isroot, label);
+    k_uf_link_rest<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, g->row_ptr, g->col, g->w, label,
+                                                           parent);
     k_uf_compress<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, parent, label, csize);
     k_block_roots<<<::qh::counted(nblk(N)), 256, 0, s>>>(N, label, csize, isroot);
   }
