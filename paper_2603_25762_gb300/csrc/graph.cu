@@ -588,7 +588,7 @@ __device__ __forceinline__ void uf_union(int32_t* parent, int32_t x, int32_t y) 
 // component, so every edge not already inside that component is taken by at least one
 // endpoint (or by a phase-one link), and the partition is the one all edges give.
 constexpr int UF_LINK_FIRST = 2;
-constexpr int UF_SAMPLES = 1024;
+constexpr int UF_SAMPLES = 256;
 
 __global__ void k_uf_link_first(int32_t n, const int64_t* __restrict__ rp,
                                 const int32_t* __restrict__ col, const double* __restrict__ w,
